@@ -1,0 +1,217 @@
+/*
+ * ugks.h -- C ABI of libugks: implicit unsteady unified gas-kinetic scheme
+ * (UGKS) on moving and overset structured meshes, for one NVIDIA GB300
+ * (sm_103a).  Method: arXiv 2604.09984, Sec. 2 (implicit UGKS with dual time
+ * stepping, Eqs. BGK, BGKReduce, microscopicFlux, macroscopicFlux,
+ * fullSolution, maxWalldes, dualTimeStepping_macro/micro, Steps 1-8) and
+ * Sec. 3 (moving overset meshes: motion, assembly Sec. 3.1, interpolation
+ * Sec. 3.2).
+ *
+ * Conventions shared by every call
+ *  - Every function returns an int status: UGKS_OK (0) or a negative
+ *    UGKS_ERR_* code; ugks_last_error() returns the message of the last
+ *    failure on a context.  A failed call leaves the context usable unless it
+ *    returned UGKS_ERR_CUDA (sticky device error).
+ *  - Device memory is owned by the caller.  ugks_workspace_query() reports
+ *    the bytes of one device workspace; the caller allocates it (any
+ *    allocator, 256-byte aligned) and passes it to ugks_create(); the library
+ *    never allocates or frees device memory and keeps only borrowed device
+ *    pointers into that workspace plus host-side metadata.
+ *  - Work is issued on the caller's CUDA stream (cudaStream_t passed as a
+ *    void*; NULL = legacy default stream) and is asynchronous unless stated.
+ *    Calls that return data in HOST buffers synchronise that stream.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ *  - Coordinates, fields and parameters cross the boundary in FP64.
+ *
+ * Units and notation: nondimensional with R = 1; particle velocity v, gas
+ * velocity V, mesh/face velocity U, relative velocity w = v - U.  Distribution
+ * functions are stored in the reduced pair (h, b) = (int f dxi, int xi^2 f
+ * dxi) of Sec. 2.1, velocity-contiguous: f[cell][k][2], k = iy*nvx + ix.
+ */
+#ifndef UGKS_H
+#define UGKS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define UGKS_OK               0
+#define UGKS_ERR_ARG         -1   /* invalid argument or size                 */
+#define UGKS_ERR_CUDA        -2   /* a CUDA runtime call or launch failed     */
+#define UGKS_ERR_GEOMETRY    -3   /* a cell volume <= 0 after a mesh move     */
+#define UGKS_ERR_ORPHAN      -4   /* overset receptors without donor          */
+#define UGKS_ERR_NONPHYSICAL -5   /* non-finite or non-positive rho or T      */
+#define UGKS_ERR_WORKSPACE   -6   /* workspace missing, too small, misaligned */
+#define UGKS_ERR_ORDER       -7   /* calls out of order (e.g. step w/o move)  */
+
+/* arithmetic of the per-(cell, velocity) path */
+#define UGKS_FP64 0   /* f, fluxes and sweeps in FP64                          */
+#define UGKS_FP32 1   /* f and per-velocity arithmetic in FP32; moments,
+                         macroscopic update, geometry and face coefficients in
+                         FP64 (mixed precision)                                */
+
+/* boundary kind of a block side (sides ordered i-low, i-high, j-low, j-high) */
+#define UGKS_BC_NONE     0   /* interior; i-sides of a periodic block          */
+#define UGKS_BC_WALL     1   /* diffuse isothermal wall moving with the mesh
+                                (Sec. 2.1 wall condition, Eq. maxWalldes)      */
+#define UGKS_BC_FARFIELD 2   /* ghost cell at the free-stream state (Sec. 2.1) */
+#define UGKS_BC_OUTFLOW  3   /* ghost cell copying the interior state          */
+#define UGKS_BC_OVERSET  4   /* outer edge of a component grid: its n_fringe
+                                cell layers are overset receptors (Sec. 3.1)   */
+
+/* cell status after overset assembly (Sec. 3.1) */
+#define UGKS_FIELD    0   /* solved cell                                      */
+#define UGKS_RECEPTOR 1   /* interpolated from donors (Sec. 3.2)              */
+#define UGKS_HOLE     2   /* inactive                                         */
+
+typedef struct ugks_ctx ugks_ctx;
+
+/* Gas, velocity space and solver constants (Sec. 2.1, 2.2). */
+typedef struct {
+  int precision;            /* UGKS_FP64 or UGKS_FP32                         */
+  int nvx, nvy;             /* uniform tensor velocity grid, trapezoid weights */
+  double vx_min, vx_max, vy_min, vy_max;
+  int K;                    /* internal degrees of freedom (Keff = 1 + K)     */
+  double Pr;                /* Prandtl number (Shakhov model)                 */
+  double omega;             /* viscosity exponent, mu = mu_ref T^omega        */
+  double mu_ref;            /* viscosity at T = 1                             */
+  double cfl_s;             /* CFL of the flux-averaging step dt_s (0.5)      */
+  double cfl_pseudo;        /* CFL of the pseudo time step dt' (100)          */
+  double farfield[4];       /* free stream rho, Vx, Vy, T (far-field ghosts)  */
+} ugks_params;
+
+/* One structured block: ni x nj quad cells, nodes (ni+1) x (nj+1).  Cell
+ * (i, j) has counter-clockwise nodes (i,j),(i+1,j),(i+1,j+1),(i,j+1); global
+ * cell id = (sum of earlier blocks' cells) + j*ni + i.  A periodic block
+ * (O-grid, periodic channel) repeats node column 0 as column ni; the
+ * difference of the two columns is the period vector (zero for an O-grid). */
+typedef struct {
+  int ni, nj;
+  int periodic_i;           /* 1: i wraps (sides 0 and 1 must be BC_NONE)     */
+  int bc[4];                /* UGKS_BC_* per side                             */
+  double wall_T[4];         /* wall temperature of BC_WALL sides              */
+  int priority;             /* overset: higher wins ties (body grids)         */
+  int n_fringe;             /* receptor layers along BC_OVERSET sides         */
+  int n_gap;                /* further layers not used to cut holes           */
+  const double *x_ref;      /* HOST, (nj+1)*(ni+1)*2 doubles, node (i,j) at
+                               2*(j*(ni+1)+i); copied during ugks_init_mesh    */
+} ugks_block_desc;
+
+/* Overset assembly counters (Sec. 3.1). */
+typedef struct {
+  int n_field, n_receptor, n_hole;
+  int n_fresh;              /* cells uncovered by the motion (hole -> field),
+                               initialised once from donors                   */
+  int n_orphan;             /* receptors/fresh cells without donor            */
+} ugks_connect_stats;
+
+/* Device bytes of the workspace for these parameters and blocks.  Host-only,
+ * no CUDA call.  Errors: UGKS_ERR_ARG for invalid sizes or BC combinations. */
+int ugks_workspace_query(const ugks_params *p, int nblocks,
+                         const ugks_block_desc *blocks, size_t *bytes);
+
+/* Create a context on the current CUDA device.  `workspace` is a DEVICE
+ * pointer (>= the queried bytes, 256-byte aligned) owned by the caller and
+ * borrowed until ugks_destroy.  `stream` is a cudaStream_t (may be NULL).
+ * The mesh is given by ugks_init_mesh.  Errors: UGKS_ERR_ARG,
+ * UGKS_ERR_WORKSPACE. */
+int ugks_create(const ugks_params *p, void *workspace, size_t bytes,
+                void *stream, ugks_ctx **out);
+int ugks_destroy(ugks_ctx *ctx);
+const char *ugks_last_error(const ugks_ctx *ctx);
+
+/* Upload the blocks (Sec. 2.1 physical discretisation) and the initial state:
+ * `prim` is HOST (ncells x 4: rho, Vx, Vy, T per cell); f is set to the
+ * reduced Maxwellian of each cell and q to its heat flux.  The mesh is placed
+ * at t = 0 with the identity motion; with several blocks an overset assembly
+ * at t = 0 is run.  Must match the blocks given to ugks_workspace_query.
+ * Synchronises the stream.  Errors: UGKS_ERR_ARG, UGKS_ERR_GEOMETRY,
+ * UGKS_ERR_ORPHAN, UGKS_ERR_CUDA. */
+int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks,
+                   const double *prim);
+
+/* Move the mesh to t_new (Sec. 3 Step 1, prescribed motion): HOST `affine`
+ * holds 6 doubles per block (m00, m01, m10, m11, b0, b1) mapping the
+ * reference nodes to x = (m00 x + m01 y) + b0, y = (m10 x + m11 y) + b1
+ * (FP64, no contraction).  Computes the step's geometry: cell volumes at both
+ * levels, mid-time face lengths / normals / centres, face velocities
+ * U_f = mean node velocity and S U.n (so Omega^{n+1} - Omega^n =
+ * dt sum S U.n), and the explicit flux-averaging step dt_s per cell.  Call
+ * once before every ugks_step (identity for a static mesh).
+ * Errors: UGKS_ERR_ARG (t_new <= t), UGKS_ERR_GEOMETRY (some Omega <= 0,
+ * detected on the device and reported by the next synchronising call). */
+int ugks_move_mesh(ugks_ctx *ctx, double t_new, const double *affine);
+
+/* Overset assembly at t^{n+1} (Sec. 3.1): wall distances, node and cell
+ * classification with buffer layer, donor search and inverse-distance
+ * weights (Sec. 3.2).  Bit-identical to an FP64 evaluation of the same
+ * predicates without fused multiply-add.  `stats` is HOST (may be NULL);
+ * synchronises the stream.  No-op for a single block.
+ * Errors: UGKS_ERR_ORDER (no move since the last step), UGKS_ERR_ORPHAN. */
+int ugks_overset_connect(ugks_ctx *ctx, ugks_connect_stats *stats);
+
+/* One physical step t^n -> t^{n+1} of the implicit unsteady UGKS (Sec. 2.2
+ * Steps 1-8): level-n flux and residual, then n_inner inner iterations of
+ * {receptor interpolation, flux, macro LU-SGS, micro residual, micro LU-SGS,
+ * step-7 moment fix}.  In place on f, W, q.  `dt` must equal t_new - t of
+ * the preceding ugks_move_mesh.  Asynchronous.
+ * Errors: UGKS_ERR_ORDER, UGKS_ERR_ARG. */
+int ugks_step(ugks_ctx *ctx, double dt, int n_inner);
+
+/* Copy the macroscopic fields to caller memory (host or device pointers,
+ * cudaMemcpyDefault): W (ncells x 4: rho, rho Vx, rho Vy, rho E), q
+ * (ncells x 2), status (ncells int32, UGKS_FIELD/RECEPTOR/HOLE) -- any may be
+ * NULL -- and wall_loads (nblocks x 4 doubles: sum over the block's wall faces
+ * of S times the wall macro flux (mass, x-momentum, y-momentum, energy) of
+ * the last flux evaluation, i.e. the force and heat the gas exerts, Sec. 2.1
+ * wall pressure/shear/heat).  Synchronises the stream.  Also reports a
+ * pending device error flag: UGKS_ERR_NONPHYSICAL, UGKS_ERR_GEOMETRY. */
+int ugks_moments(ugks_ctx *ctx, double *W, double *q, int32_t *status,
+                 double *wall_loads);
+
+/* Sizes of the current problem. */
+int ugks_sizes(const ugks_ctx *ctx, int *ncells, int *nfaces, int *nv,
+               int *nv_stride);
+
+/* Read / write the distribution f (ncells x nv x 2, FP64, host or device
+ * pointer, velocity index k = iy*nvx + ix) and W, q (FP64).  get synchronises
+ * the stream; set overwrites the state (any pointer may be NULL). */
+int ugks_get_state(ugks_ctx *ctx, double *f, double *W, double *q);
+int ugks_set_state(ugks_ctx *ctx, const double *f, const double *W, const double *q);
+
+/* Diagnostic of Steps 1/3: evaluate the time-averaged interface flux of the
+ * current state with the current geometry (after ugks_move_mesh) and write
+ * D = sum_faces S F_hat (ncells x nv x 2, outward positive, Eq.
+ * microscopicFlux summed per cell) and F = sum_k V_k Psi_k D_k (ncells x 4,
+ * Eq. macroscopicFlux) to caller memory (host or device, FP64).  Receptors are
+ * interpolated first.  Synchronises the stream. */
+int ugks_eval_flux(ugks_ctx *ctx, double *D, double *F);
+
+/* Connectivity of the last assembly, HOST buffers: status (ncells int32),
+ * donors (ncells x 5 int32, -1 unused; rows of non-receptors are -1) and
+ * weights (ncells x 5 doubles).  Synchronises the stream. */
+int ugks_get_connectivity(ugks_ctx *ctx, int32_t *status, int32_t *donors,
+                          double *weights);
+
+/* Geometry of the last move, HOST buffers (any may be NULL): vol_old,
+ * vol_new (ncells), xc (ncells x 2, mid-time centres), dts (ncells),
+ * Sn (nfaces x 2), SUn (nfaces).  Face order, block after block: the
+ * i-faces row by row (j outer, i inner; a periodic block has ni per row, the
+ * first joining cell ni-1 to cell 0), then the j-faces column by column (i
+ * outer, j = 0..nj inner).  Interior faces point from the lower to the higher
+ * logical index; boundary faces point out of the block. */
+int ugks_get_geometry(ugks_ctx *ctx, double *vol_old, double *vol_new,
+                      double *xc, double *dts, double *Sn, double *SUn);
+
+/* Number of kernel launches issued on the context's stream since creation
+ * (counted on the host at each launch). */
+int64_t ugks_launch_count(const ugks_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* UGKS_H */

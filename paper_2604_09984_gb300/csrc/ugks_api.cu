@@ -1,0 +1,746 @@
+// ugks_api.cu -- host orchestration behind the C ABI of include/ugks.h:
+// workspace layout, structured-block topology, and the order of the kernels
+// of one physical step (arXiv 2604.09984 Sec. 3 Steps 1-3 and Sec. 2.2
+// Steps 1-8).  No device allocation happens here: every device array is a
+// slice of the caller's workspace.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ugks.h"
+#include "ugks_launch.h"
+
+using namespace ugks;
+
+struct ugks_ctx {
+  ugks_params p;
+  cudaStream_t st = nullptr;
+  char *ws = nullptr;
+  size_t ws_bytes = 0;
+  Dev d;
+  int fp32 = 0;
+  int nblocks = 0;
+  std::vector<ugks_block_desc> blocks;
+  std::vector<int> cell_off, node_off;
+  int max_nj = 0;
+  int V = 1, nwork = 0;
+  int *work = nullptr;
+  int *prev_status = nullptr, *n_orphan = nullptr, *blk_order = nullptr;
+  int cap_interp = 0;
+  double t = 0.0, t_new = 0.0;
+  bool moved = false, mesh_ready = false;
+  std::string err;
+  int64_t launches = 0;
+  std::vector<double> h_affine;
+  std::vector<int> h_lists;
+};
+
+namespace {
+
+int fail(ugks_ctx *c, int code, const std::string &msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_check(ugks_ctx *c, cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return UGKS_OK;
+  return fail(c, UGKS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                   \
+  do {                                                             \
+    int _r = cuda_check(ctx, (call), #call);                       \
+    if (_r) return _r;                                             \
+  } while (0)
+
+struct Sizes {
+  int nc = 0, nf = 0, nn = 0, nv = 0, nvp = 0, nseg = 0, nring = 0, max_nj = 0;
+};
+
+int validate(const ugks_params *p, int nb, const ugks_block_desc *b, Sizes &s, std::string &why) {
+  if (!p || nb <= 0 || !b) { why = "null params or no blocks"; return UGKS_ERR_ARG; }
+  if (p->precision != UGKS_FP64 && p->precision != UGKS_FP32) { why = "precision"; return UGKS_ERR_ARG; }
+  if (p->nvx < 2 || p->nvy < 2 || p->nvx * p->nvy > (1 << 20)) { why = "velocity grid size"; return UGKS_ERR_ARG; }
+  if (!(p->vx_max > p->vx_min) || !(p->vy_max > p->vy_min)) { why = "velocity bounds"; return UGKS_ERR_ARG; }
+  if (p->K < 0 || !(p->Pr > 0) || !(p->mu_ref > 0) || !(p->cfl_s > 0) || !(p->cfl_pseudo > 0)) {
+    why = "gas or solver constant"; return UGKS_ERR_ARG;
+  }
+  s.nv = p->nvx * p->nvy;
+  s.nvp = (s.nv + 3) / 4 * 4;
+  for (int i = 0; i < nb; ++i) {
+    const ugks_block_desc &B = b[i];
+    if (B.ni < 2 || B.nj < 2 || B.nj > 512) { why = "block size (2 <= ni, 2 <= nj <= 512)"; return UGKS_ERR_ARG; }
+    if (B.periodic_i && (B.bc[0] != UGKS_BC_NONE || B.bc[1] != UGKS_BC_NONE)) { why = "periodic block with i-side BC"; return UGKS_ERR_ARG; }
+    for (int sd = 0; sd < 4; ++sd) {
+      if (B.bc[sd] < 0 || B.bc[sd] > 4) { why = "bc kind"; return UGKS_ERR_ARG; }
+      if (!B.periodic_i && B.bc[sd] == UGKS_BC_NONE) { why = "non-periodic block side without BC"; return UGKS_ERR_ARG; }
+      if (B.bc[sd] == UGKS_BC_WALL && !(B.wall_T[sd] > 0)) { why = "wall temperature"; return UGKS_ERR_ARG; }
+      int nseg = (sd < 2) ? B.nj : B.ni;
+      if (B.bc[sd] == UGKS_BC_WALL) s.nseg += nseg;
+    }
+    if (B.n_fringe < 0 || B.n_gap < 0) { why = "fringe"; return UGKS_ERR_ARG; }
+    if (B.periodic_i && B.bc[2] == UGKS_BC_WALL) s.nring += B.ni;
+    s.nc += B.ni * B.nj;
+    s.nn += (B.ni + 1) * (B.nj + 1);
+    s.nf += B.nj * (B.periodic_i ? B.ni : B.ni + 1) + B.ni * (B.nj + 1);
+    if (B.nj > s.max_nj) s.max_nj = B.nj;
+  }
+  return UGKS_OK;
+}
+
+struct Carver {
+  char *base;
+  size_t off = 0;
+  explicit Carver(char *b) : base(b) {}
+  template <typename T> T *take(size_t n) {
+    off = (off + 255) / 256 * 256;
+    T *ptr = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += n * sizeof(T) + 16;
+    return ptr;
+  }
+};
+
+int choose_V(int max_nj, int nv) {
+  const char *env = getenv("UGKS_VTILE");
+  if (env) {
+    int v = atoi(env);
+    if (v >= 1 && v * max_nj <= 512) return v;
+  }
+  int r = 1;
+  while (r < max_nj) r <<= 1;
+  int V = 512 / r;
+  if (V < 1) V = 1;
+  if (V > 32) V = 32;
+  if (V * max_nj > 512) V = 512 / max_nj;
+  while (V > 1 && V > nv) V >>= 1;
+  return V;
+}
+
+// Lay out every device array of the context in the workspace (base may be
+// null to measure).  Returns the bytes used.
+size_t carve(char *base, const Sizes &s, int nb, int fp32, int nwork, int cap_interp, Dev &d) {
+  Carver c(base);
+  size_t pair = fp32 ? 2 * sizeof(float) : 2 * sizeof(double);
+  size_t tsz = fp32 ? sizeof(float) : sizeof(double);
+  d.vx = c.take<double>(s.nvp); d.vy = c.take<double>(s.nvp); d.w = c.take<double>(s.nvp);
+  d.vxf = c.take<float>(s.nvp); d.vyf = c.take<float>(s.nvp); d.wf = c.take<float>(s.nvp);
+  d.cell_nodes = c.take<int>(4 * (size_t)s.nc);
+  d.cell_faces = c.take<int>(4 * (size_t)s.nc);
+  d.cell_sgn = c.take<int8_t>(4 * (size_t)s.nc);
+  d.nb_kind = c.take<int>(4 * (size_t)s.nc);
+  d.nb_id = c.take<int>(4 * (size_t)s.nc);
+  d.nb_shift = c.take<int8_t>(4 * (size_t)s.nc);
+  d.cell_row = c.take<int>(2 * (size_t)s.nc);
+  d.cell_block = c.take<int>(s.nc);
+  d.node_block = c.take<int>(s.nn);
+  d.face_L = c.take<int>(s.nf); d.face_R = c.take<int>(s.nf);
+  d.face_a = c.take<int>(s.nf); d.face_b = c.take<int>(s.nf);
+  d.face_kind = c.take<int>(s.nf); d.face_block = c.take<int>(s.nf);
+  d.face_shiftL = c.take<int8_t>(s.nf);
+  d.face_Tw = c.take<double>(s.nf);
+  d.X_ref = c.take<double>(2 * (size_t)s.nn);
+  d.X_old = c.take<double>(2 * (size_t)s.nn);
+  d.X_new = c.take<double>(2 * (size_t)s.nn);
+  d.vol_old = c.take<double>(s.nc); d.vol_new = c.take<double>(s.nc); d.dts = c.take<double>(s.nc);
+  d.xc = c.take<double>(2 * (size_t)s.nc); d.xc_new = c.take<double>(2 * (size_t)s.nc);
+  d.period = c.take<double>(2 * (size_t)s.nc);
+  d.Sn = c.take<double>(2 * (size_t)s.nf); d.nrm = c.take<double>(2 * (size_t)s.nf);
+  d.xf = c.take<double>(2 * (size_t)s.nf); d.Uf = c.take<double>(2 * (size_t)s.nf);
+  d.S = c.take<double>(s.nf); d.SUn = c.take<double>(s.nf);
+  d.slope_flags = c.take<int>(s.nc);
+  d.jinv = c.take<double>(4 * (size_t)s.nc);
+  d.affine = c.take<double>(6 * (size_t)nb);
+  d.f = c.take<char>(pair * (size_t)s.nc * s.nvp);
+  d.W = c.take<double>(4 * (size_t)s.nc); d.q = c.take<double>(2 * (size_t)s.nc);
+  d.status = c.take<int>(s.nc);
+  d.Tn = c.take<char>(pair * (size_t)s.nc * s.nvp);
+  d.dfs = c.take<char>(pair * (size_t)s.nc * s.nvp);
+  d.TW = c.take<double>(4 * (size_t)s.nc); d.Fc = c.take<double>(4 * (size_t)s.nc);
+  d.dW = c.take<double>(4 * (size_t)s.nc); d.Wp = c.take<double>(4 * (size_t)s.nc);
+  d.cpar = c.take<double>(NCP * (size_t)s.nc); d.cparn = c.take<double>(NCP * (size_t)s.nc);
+  d.gradW = c.take<double>(8 * (size_t)s.nc);
+  d.ghostW = c.take<double>(4 * (size_t)s.nf);
+  d.fsum = c.take<double>(NFS * (size_t)s.nf);
+  d.fpar = c.take<double>(NFP * (size_t)s.nf);
+  d.fparT = c.take<char>(tsz * NFP * (size_t)s.nf);
+  d.fflux = c.take<double>(4 * (size_t)s.nf);
+  d.gam = c.take<double>(s.nf);
+  d.wall_loads = c.take<double>(4 * (size_t)nb);
+  d.node_active = c.take<int>(s.nn);
+  d.cls = c.take<int>(s.nc);
+  d.donors = c.take<int>(5 * (size_t)s.nc);
+  d.dwgt = c.take<double>(5 * (size_t)s.nc);
+  d.rec_list = c.take<int>(s.nc);
+  d.fresh_list = c.take<int>(s.nc);
+  d.itmp = c.take<char>(pair * (size_t)cap_interp * s.nvp);
+  d.itmpW = c.take<double>(6 * (size_t)cap_interp);
+  d.wall_seg = c.take<int>(2 * (size_t)s.nseg + 2);
+  d.wall_seg_off = c.take<int>(nb + 1);
+  d.body_ring = c.take<int>((size_t)s.nring + 1);
+  d.body_ring_off = c.take<int>(nb + 1);
+  d.cell_off = c.take<int>(nb + 1);
+  d.node_off = c.take<int>(nb + 1);
+  d.blk_info = c.take<int>(8 * (size_t)nb);
+  d.err = c.take<int>(4);
+  (void)nwork;
+  c.take<int>(2 * (size_t)nwork + 2);   // micro-sweep work list
+  c.take<int>(s.nc);                   // previous status / fresh flags
+  c.take<int>(4);                      // orphan counter
+  c.take<int>(nb);                     // block priority order
+  return c.off;
+}
+
+int cap_interp_for(const Sizes &s, int nb) { return nb > 1 ? (s.nc / 4 > 1024 ? s.nc / 4 : (s.nc < 1024 ? s.nc : 1024)) : 0; }
+
+int nwork_for(const ugks_params *p, int nb, const ugks_block_desc *b, int V) {
+  int nv = p->nvx * p->nvy;
+  (void)b;
+  return nb * ((nv + V - 1) / V);
+}
+
+// Host topology identical in ordering to the face/cell numbering documented
+// in ugks.h.
+struct Topo {
+  std::vector<int> cell_nodes, cell_faces, nb_kind, nb_id, cell_row, cell_block, node_block;
+  std::vector<int8_t> cell_sgn, nb_shift, face_shiftL;
+  std::vector<int> face_L, face_R, face_a, face_b, face_kind, face_block;
+  std::vector<double> face_Tw;
+  std::vector<int> wall_seg, wall_seg_off, body_ring, body_ring_off, blk_info;
+};
+
+void build_topology(int nb, const ugks_block_desc *B, const std::vector<int> &coff,
+                    const std::vector<int> &noff, int nc, int nn, Topo &T) {
+  T.cell_nodes.assign(4 * (size_t)nc, 0);
+  T.cell_faces.assign(4 * (size_t)nc, -1);
+  T.cell_sgn.assign(4 * (size_t)nc, 0);
+  T.nb_kind.assign(4 * (size_t)nc, NB_NONE);
+  T.nb_id.assign(4 * (size_t)nc, -1);
+  T.nb_shift.assign(4 * (size_t)nc, 0);
+  T.cell_row.assign(2 * (size_t)nc, 0);
+  T.cell_block.assign(nc, 0);
+  T.node_block.assign(nn, 0);
+  T.wall_seg_off.push_back(0);
+  T.body_ring_off.push_back(0);
+  auto add_face = [&](int L, int R, int a, int b, int kind, int blk, int shL, double Tw) {
+    T.face_L.push_back(L); T.face_R.push_back(R); T.face_a.push_back(a); T.face_b.push_back(b);
+    T.face_kind.push_back(kind); T.face_block.push_back(blk); T.face_shiftL.push_back((int8_t)shL);
+    T.face_Tw.push_back(Tw);
+    return (int)T.face_L.size() - 1;
+  };
+  for (int bi = 0; bi < nb; ++bi) {
+    const ugks_block_desc &b = B[bi];
+    int ni = b.ni, nj = b.nj, co = coff[bi], no = noff[bi];
+    auto cid = [&](int i, int j) { return co + j * ni + i; };
+    auto nid = [&](int i, int j) { return no + j * (ni + 1) + i; };
+    for (int n = noff[bi]; n < noff[bi + 1]; ++n) T.node_block[n] = bi;
+    for (int j = 0; j < nj; ++j)
+      for (int i = 0; i < ni; ++i) {
+        int c = cid(i, j);
+        T.cell_block[c] = bi;
+        int *nd = &T.cell_nodes[4 * (size_t)c];
+        nd[0] = nid(i, j); nd[1] = nid(i + 1, j); nd[2] = nid(i + 1, j + 1); nd[3] = nid(i, j + 1);
+        T.cell_row[2 * (size_t)c] = nid(0, j);
+        T.cell_row[2 * (size_t)c + 1] = nid(ni, j);
+      }
+    auto setf = [&](int c, int slot, int f) { T.cell_faces[4 * (size_t)c + slot] = f; };
+    for (int j = 0; j < nj; ++j) {
+      int iend = b.periodic_i ? ni : ni + 1;
+      for (int i = 0; i < iend; ++i) {
+        if (b.periodic_i) {
+          int L = cid((i - 1 + ni) % ni, j), R = cid(i, j);
+          int f = add_face(L, R, nid(i, j), nid(i, j + 1), UGKS_BC_NONE, bi, i == 0 ? -1 : 0, 0.0);
+          setf(L, 1, f); setf(R, 0, f);
+        } else if (i == 0) {
+          int c = cid(0, j);
+          setf(c, 0, add_face(c, -1, nid(0, j + 1), nid(0, j), b.bc[0], bi, 0, b.wall_T[0]));
+        } else if (i == ni) {
+          int c = cid(ni - 1, j);
+          setf(c, 1, add_face(c, -1, nid(ni, j), nid(ni, j + 1), b.bc[1], bi, 0, b.wall_T[1]));
+        } else {
+          int L = cid(i - 1, j), R = cid(i, j);
+          int f = add_face(L, R, nid(i, j), nid(i, j + 1), UGKS_BC_NONE, bi, 0, 0.0);
+          setf(L, 1, f); setf(R, 0, f);
+        }
+      }
+    }
+    for (int i = 0; i < ni; ++i)
+      for (int j = 0; j <= nj; ++j) {
+        if (j == 0) {
+          int c = cid(i, 0);
+          setf(c, 2, add_face(c, -1, nid(i, 0), nid(i + 1, 0), b.bc[2], bi, 0, b.wall_T[2]));
+        } else if (j == nj) {
+          int c = cid(i, nj - 1);
+          setf(c, 3, add_face(c, -1, nid(i + 1, nj), nid(i, nj), b.bc[3], bi, 0, b.wall_T[3]));
+        } else {
+          int L = cid(i, j - 1), R = cid(i, j);
+          int f = add_face(L, R, nid(i + 1, j), nid(i, j), UGKS_BC_NONE, bi, 0, 0.0);
+          setf(L, 3, f); setf(R, 2, f);
+        }
+      }
+    const int di[4] = {-1, 1, 0, 0}, dj[4] = {0, 0, -1, 1};
+    for (int j = 0; j < nj; ++j)
+      for (int i = 0; i < ni; ++i) {
+        int c = cid(i, j);
+        for (int s = 0; s < 4; ++s) {
+          int ii = i + di[s], jj = j + dj[s];
+          size_t q = 4 * (size_t)c + s;
+          if (ii >= 0 && ii < ni && jj >= 0 && jj < nj) {
+            T.nb_kind[q] = NB_CELL; T.nb_id[q] = cid(ii, jj);
+          } else if (di[s] != 0 && b.periodic_i) {
+            T.nb_kind[q] = NB_CELL; T.nb_id[q] = cid((ii + ni) % ni, jj); T.nb_shift[q] = (int8_t)di[s];
+          } else {
+            int kind = b.bc[s];
+            if (kind == UGKS_BC_FARFIELD || kind == UGKS_BC_OUTFLOW) {
+              T.nb_kind[q] = NB_GHOST; T.nb_id[q] = T.cell_faces[q];
+            } else {
+              T.nb_kind[q] = NB_NONE;
+            }
+          }
+        }
+      }
+    // wall segments (node pairs along wall sides) and body ring
+    for (int sd = 0; sd < 4; ++sd) {
+      if (b.bc[sd] != UGKS_BC_WALL) continue;
+      if (sd < 2) {
+        int i = sd == 0 ? 0 : ni;
+        for (int j = 0; j < nj; ++j) { T.wall_seg.push_back(nid(i, j)); T.wall_seg.push_back(nid(i, j + 1)); }
+      } else {
+        int j = sd == 2 ? 0 : nj;
+        for (int i = 0; i < ni; ++i) { T.wall_seg.push_back(nid(i, j)); T.wall_seg.push_back(nid(i + 1, j)); }
+      }
+    }
+    T.wall_seg_off.push_back((int)T.wall_seg.size() / 2);
+    if (b.periodic_i && b.bc[2] == UGKS_BC_WALL)
+      for (int i = 0; i < ni; ++i) T.body_ring.push_back(nid(i, 0));
+    T.body_ring_off.push_back((int)T.body_ring.size());
+    int mask = 0;
+    for (int sd = 0; sd < 4; ++sd) if (b.bc[sd] == UGKS_BC_OVERSET) mask |= 1 << sd;
+    int info[8] = {ni, nj, b.periodic_i ? 1 : 0, b.priority, b.n_fringe, b.n_gap, mask,
+                   (b.periodic_i && b.bc[2] == UGKS_BC_WALL) ? 1 : 0};
+    for (int m = 0; m < 8; ++m) T.blk_info.push_back(info[m]);
+  }
+  for (int c = 0; c < nc; ++c)
+    for (int s = 0; s < 4; ++s) {
+      int f = T.cell_faces[4 * (size_t)c + s];
+      T.cell_sgn[4 * (size_t)c + s] = (T.face_L[f] == c) ? 1 : -1;
+    }
+}
+
+template <typename V> int up(ugks_ctx *ctx, void *dst, const std::vector<V> &src) {
+  if (src.empty()) return UGKS_OK;
+  CK(cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(V), cudaMemcpyHostToDevice, ctx->st));
+  return UGKS_OK;
+}
+
+int check_err_flag(ugks_ctx *ctx) {
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, ctx->d.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (h) {
+    CK(cudaMemsetAsync(ctx->d.err, 0, sizeof(int), ctx->st));
+    if (h & EF_GEOMETRY) return fail(ctx, UGKS_ERR_GEOMETRY, "non-positive cell volume after mesh move");
+    if (h & EF_NONPHYSICAL) return fail(ctx, UGKS_ERR_NONPHYSICAL, "non-finite or non-positive density/temperature");
+  }
+  return UGKS_OK;
+}
+
+int launch_status(ugks_ctx *ctx) { return cuda_check(ctx, cudaPeekAtLastError(), "kernel launch"); }
+
+int do_interp(ugks_ctx *ctx, const int *list, int n) {
+  if (n <= 0) return UGKS_OK;
+  launch_interp(ctx->d, ctx->st, list, n, ctx->fp32);
+  ctx->launches += 2;
+  return UGKS_OK;
+}
+
+int do_connect(ugks_ctx *ctx, ugks_connect_stats *stats, bool initial) {
+  Dev &d = ctx->d;
+  if (ctx->nblocks < 2) {
+    if (stats) { stats->n_field = d.nc; stats->n_receptor = stats->n_hole = stats->n_fresh = stats->n_orphan = 0; }
+    return UGKS_OK;
+  }
+  // prev_status: last status (all FIELD initially so no cell is "fresh")
+  if (initial) CK(cudaMemsetAsync(ctx->prev_status, 0, sizeof(int) * d.nc, ctx->st));
+  else CK(cudaMemcpyAsync(ctx->prev_status, d.status, sizeof(int) * d.nc, cudaMemcpyDeviceToDevice, ctx->st));
+  CK(cudaMemsetAsync(ctx->n_orphan, 0, sizeof(int), ctx->st));
+  launch_connect(d, ctx->st, ctx->prev_status, ctx->blk_order, ctx->n_orphan);
+  ctx->launches += 4;
+  int r = launch_status(ctx);
+  if (r) return r;
+  std::vector<int> st(d.nc), fr(d.nc);
+  int norph = 0;
+  CK(cudaMemcpyAsync(st.data(), d.status, sizeof(int) * d.nc, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(fr.data(), ctx->prev_status, sizeof(int) * d.nc, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(&norph, ctx->n_orphan, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  std::vector<int> rec, fresh;
+  int nf = 0, nr = 0, nh = 0;
+  for (int c = 0; c < d.nc; ++c) {
+    if (st[c] == ST_FIELD) ++nf;
+    else if (st[c] == ST_RECEPTOR) { ++nr; rec.push_back(c); }
+    else ++nh;
+    if (fr[c]) fresh.push_back(c);
+  }
+  if ((int)rec.size() > ctx->cap_interp || (int)fresh.size() > ctx->cap_interp)
+    return fail(ctx, UGKS_ERR_WORKSPACE, "more receptors than the interpolation staging holds");
+  ctx->h_lists = rec;
+  ctx->h_lists.insert(ctx->h_lists.end(), fresh.begin(), fresh.end());
+  if (!ctx->h_lists.empty()) {
+    CK(cudaMemcpyAsync(d.rec_list, rec.data(), sizeof(int) * rec.size(), cudaMemcpyHostToDevice, ctx->st));
+    if (!fresh.empty())
+      CK(cudaMemcpyAsync(d.fresh_list, fresh.data(), sizeof(int) * fresh.size(), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+  }
+  d.nrec = (int)rec.size();
+  d.nfresh = (int)fresh.size();
+  launch_slope_geo(d, ctx->st);     // holes changed
+  ctx->launches += 1;
+  if (stats) {
+    stats->n_field = nf; stats->n_receptor = nr; stats->n_hole = nh;
+    stats->n_fresh = (int)fresh.size(); stats->n_orphan = norph;
+  }
+  if (norph > 0) return fail(ctx, UGKS_ERR_ORPHAN, std::to_string(norph) + " receptors without donor");
+  return launch_status(ctx);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ugks_workspace_query(const ugks_params *p, int nblocks, const ugks_block_desc *blocks, size_t *bytes) {
+  Sizes s;
+  std::string why;
+  int r = validate(p, nblocks, blocks, s, why);
+  if (r) return r;
+  if (!bytes) return UGKS_ERR_ARG;
+  int V = choose_V(s.max_nj, s.nv);
+  Dev d;
+  memset(&d, 0, sizeof(d));
+  *bytes = carve(nullptr, s, nblocks, p->precision == UGKS_FP32, nwork_for(p, nblocks, blocks, V),
+                 cap_interp_for(s, nblocks), d);
+  return UGKS_OK;
+}
+
+int ugks_create(const ugks_params *p, void *workspace, size_t bytes, void *stream, ugks_ctx **out) {
+  if (!p || !out) return UGKS_ERR_ARG;
+  if (!workspace || ((uintptr_t)workspace & 255)) return UGKS_ERR_WORKSPACE;
+  ugks_ctx *c = new ugks_ctx();
+  c->p = *p;
+  c->ws = (char *)workspace;
+  c->ws_bytes = bytes;
+  c->st = (cudaStream_t)stream;
+  c->fp32 = p->precision == UGKS_FP32;
+  memset(&c->d, 0, sizeof(c->d));
+  *out = c;
+  return UGKS_OK;
+}
+
+int ugks_destroy(ugks_ctx *ctx) {
+  delete ctx;
+  return UGKS_OK;
+}
+
+const char *ugks_last_error(const ugks_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t ugks_launch_count(const ugks_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+int ugks_sizes(const ugks_ctx *ctx, int *ncells, int *nfaces, int *nv, int *nv_stride) {
+  if (!ctx || !ctx->mesh_ready) return UGKS_ERR_ORDER;
+  if (ncells) *ncells = ctx->d.nc;
+  if (nfaces) *nfaces = ctx->d.nf;
+  if (nv) *nv = ctx->d.nv;
+  if (nv_stride) *nv_stride = ctx->d.nvp;
+  return UGKS_OK;
+}
+
+int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, const double *prim) {
+  if (!ctx) return UGKS_ERR_ARG;
+  Sizes s;
+  std::string why;
+  int r = validate(&ctx->p, nblocks, blocks, s, why);
+  if (r) return fail(ctx, r, why);
+  if (!prim) return fail(ctx, UGKS_ERR_ARG, "null initial state");
+  for (int b = 0; b < nblocks; ++b) if (!blocks[b].x_ref) return fail(ctx, UGKS_ERR_ARG, "null x_ref");
+  ctx->nblocks = nblocks;
+  ctx->blocks.assign(blocks, blocks + nblocks);
+  ctx->max_nj = s.max_nj;
+  ctx->V = choose_V(s.max_nj, s.nv);
+  ctx->nwork = nwork_for(&ctx->p, nblocks, blocks, ctx->V);
+  ctx->cap_interp = cap_interp_for(s, nblocks);
+  Dev &d = ctx->d;
+  memset(&d, 0, sizeof(d));
+  size_t need = carve(nullptr, s, nblocks, ctx->fp32, ctx->nwork, ctx->cap_interp, d);
+  if (need > ctx->ws_bytes) return fail(ctx, UGKS_ERR_WORKSPACE, "workspace too small: need " + std::to_string(need));
+  carve(ctx->ws, s, nblocks, ctx->fp32, ctx->nwork, ctx->cap_interp, d);
+  {
+    // the trailing private arrays follow d.err in carve order
+    Carver c(ctx->ws);
+    Dev tmp;
+    memset(&tmp, 0, sizeof(tmp));
+    c.off = (size_t)((char *)d.err - ctx->ws) + 4 * sizeof(int) + 16;
+    ctx->work = c.take<int>(2 * (size_t)ctx->nwork + 2);
+    ctx->prev_status = c.take<int>(s.nc);
+    ctx->n_orphan = c.take<int>(4);
+    ctx->blk_order = c.take<int>(nblocks);
+  }
+  d.nc = s.nc; d.nf = s.nf; d.nn = s.nn; d.nv = s.nv; d.nvp = s.nvp; d.nblocks = nblocks;
+  d.Kint = ctx->p.K; d.Keff = 1 + ctx->p.K;
+  d.Pr = ctx->p.Pr; d.omega = ctx->p.omega; d.mu_ref = ctx->p.mu_ref;
+  d.cfl_s = ctx->p.cfl_s; d.cfl_pseudo = ctx->p.cfl_pseudo; d.dt = 1.0;
+  {
+    double lam = 1.0 / (2.0 * ctx->p.farfield[3]);
+    conservative(ctx->p.farfield[0], ctx->p.farfield[1], ctx->p.farfield[2], lam, d.Keff, d.Winf);
+  }
+  // velocity space
+  std::vector<double> vx(s.nvp, 0.0), vy(s.nvp, 0.0), w(s.nvp, 0.0);
+  std::vector<float> vxf(s.nvp, 0.f), vyf(s.nvp, 0.f), wf(s.nvp, 0.f);
+  const ugks_params &P = ctx->p;
+  double hx = (P.vx_max - P.vx_min) / (P.nvx - 1), hy = (P.vy_max - P.vy_min) / (P.nvy - 1);
+  for (int iy = 0; iy < P.nvy; ++iy)
+    for (int ix = 0; ix < P.nvx; ++ix) {
+      int k = iy * P.nvx + ix;
+      vx[k] = P.vx_min + (P.vx_max - P.vx_min) * ix / (P.nvx - 1);
+      vy[k] = P.vy_min + (P.vy_max - P.vy_min) * iy / (P.nvy - 1);
+      double wx = hx * ((ix == 0 || ix == P.nvx - 1) ? 0.5 : 1.0);
+      double wy = hy * ((iy == 0 || iy == P.nvy - 1) ? 0.5 : 1.0);
+      w[k] = wy * wx;
+      vxf[k] = (float)vx[k]; vyf[k] = (float)vy[k]; wf[k] = (float)w[k];
+    }
+  // topology
+  ctx->cell_off.assign(1, 0);
+  ctx->node_off.assign(1, 0);
+  for (int b = 0; b < nblocks; ++b) {
+    ctx->cell_off.push_back(ctx->cell_off.back() + blocks[b].ni * blocks[b].nj);
+    ctx->node_off.push_back(ctx->node_off.back() + (blocks[b].ni + 1) * (blocks[b].nj + 1));
+  }
+  Topo T;
+  build_topology(nblocks, blocks, ctx->cell_off, ctx->node_off, s.nc, s.nn, T);
+  std::vector<double> X(2 * (size_t)s.nn);
+  for (int b = 0; b < nblocks; ++b) {
+    size_t n = 2 * (size_t)(blocks[b].ni + 1) * (blocks[b].nj + 1);
+    memcpy(&X[2 * (size_t)ctx->node_off[b]], blocks[b].x_ref, n * sizeof(double));
+  }
+  std::vector<int> order(nblocks);
+  for (int b = 0; b < nblocks; ++b) order[b] = b;
+  for (int a = 0; a < nblocks; ++a)      // priority descending, block index ascending
+    for (int b = a + 1; b < nblocks; ++b)
+      if (blocks[order[b]].priority > blocks[order[a]].priority ||
+          (blocks[order[b]].priority == blocks[order[a]].priority && order[b] < order[a]))
+        std::swap(order[a], order[b]);
+  std::vector<int> work;
+  for (int b = 0; b < nblocks; ++b)
+    for (int k0 = 0; k0 < s.nv; k0 += ctx->V) { work.push_back(b); work.push_back(k0); }
+  if ((r = up(ctx, (void *)d.vx, vx))) return r;
+  if ((r = up(ctx, (void *)d.vy, vy))) return r;
+  if ((r = up(ctx, (void *)d.w, w))) return r;
+  if ((r = up(ctx, (void *)d.vxf, vxf))) return r;
+  if ((r = up(ctx, (void *)d.vyf, vyf))) return r;
+  if ((r = up(ctx, (void *)d.wf, wf))) return r;
+  if ((r = up(ctx, (void *)d.cell_nodes, T.cell_nodes))) return r;
+  if ((r = up(ctx, (void *)d.cell_faces, T.cell_faces))) return r;
+  if ((r = up(ctx, (void *)d.cell_sgn, T.cell_sgn))) return r;
+  if ((r = up(ctx, (void *)d.nb_kind, T.nb_kind))) return r;
+  if ((r = up(ctx, (void *)d.nb_id, T.nb_id))) return r;
+  if ((r = up(ctx, (void *)d.nb_shift, T.nb_shift))) return r;
+  if ((r = up(ctx, (void *)d.cell_row, T.cell_row))) return r;
+  if ((r = up(ctx, (void *)d.cell_block, T.cell_block))) return r;
+  if ((r = up(ctx, (void *)d.node_block, T.node_block))) return r;
+  if ((r = up(ctx, (void *)d.face_L, T.face_L))) return r;
+  if ((r = up(ctx, (void *)d.face_R, T.face_R))) return r;
+  if ((r = up(ctx, (void *)d.face_a, T.face_a))) return r;
+  if ((r = up(ctx, (void *)d.face_b, T.face_b))) return r;
+  if ((r = up(ctx, (void *)d.face_kind, T.face_kind))) return r;
+  if ((r = up(ctx, (void *)d.face_block, T.face_block))) return r;
+  if ((r = up(ctx, (void *)d.face_shiftL, T.face_shiftL))) return r;
+  if ((r = up(ctx, (void *)d.face_Tw, T.face_Tw))) return r;
+  if ((r = up(ctx, (void *)d.wall_seg, T.wall_seg))) return r;
+  if ((r = up(ctx, (void *)d.wall_seg_off, T.wall_seg_off))) return r;
+  if ((r = up(ctx, (void *)d.body_ring, T.body_ring))) return r;
+  if ((r = up(ctx, (void *)d.body_ring_off, T.body_ring_off))) return r;
+  if ((r = up(ctx, (void *)d.cell_off, ctx->cell_off))) return r;
+  if ((r = up(ctx, (void *)d.node_off, ctx->node_off))) return r;
+  if ((r = up(ctx, (void *)d.blk_info, T.blk_info))) return r;
+  if ((r = up(ctx, (void *)ctx->blk_order, order))) return r;
+  if ((r = up(ctx, (void *)ctx->work, work))) return r;
+  if ((r = up(ctx, (void *)d.X_ref, X))) return r;
+  // identity placement at t = 0
+  std::vector<double> aff(6 * (size_t)nblocks, 0.0);
+  for (int b = 0; b < nblocks; ++b) { aff[6 * b] = 1.0; aff[6 * b + 3] = 1.0; }
+  if ((r = up(ctx, (void *)d.affine, aff))) return r;
+  CK(cudaMemsetAsync(d.err, 0, sizeof(int), ctx->st));
+  CK(cudaMemsetAsync(d.status, 0, sizeof(int) * s.nc, ctx->st));
+  CK(cudaMemsetAsync(d.donors, 0xff, sizeof(int) * 5 * (size_t)s.nc, ctx->st));
+  CK(cudaMemsetAsync(d.Tn, 0, (ctx->fp32 ? 8 : 16) * (size_t)s.nc * s.nvp, ctx->st));
+  CK(cudaMemsetAsync(d.dfs, 0, (ctx->fp32 ? 8 : 16) * (size_t)s.nc * s.nvp, ctx->st));
+  launch_move_nodes(d, ctx->st);
+  CK(cudaMemcpyAsync(d.X_old, d.X_new, sizeof(double) * 2 * s.nn, cudaMemcpyDeviceToDevice, ctx->st));
+  launch_geometry(d, ctx->st);
+  ctx->launches += 4;
+  // initial state from the primitive field (staged through cpar)
+  if (s.nc * 4 > s.nc * NCP) return fail(ctx, UGKS_ERR_WORKSPACE, "staging");
+  CK(cudaMemcpyAsync(d.cpar, prim, sizeof(double) * 4 * s.nc, cudaMemcpyHostToDevice, ctx->st));
+  launch_init_state(d, ctx->st, d.cpar, ctx->fp32);
+  ctx->launches += 1;
+  CK(cudaStreamSynchronize(ctx->st));
+  r = launch_status(ctx);
+  if (r) return r;
+  ctx->mesh_ready = true;
+  ctx->t = 0.0;
+  ctx->moved = false;
+  r = do_connect(ctx, nullptr, true);
+  if (r) return r;
+  launch_slope_geo(d, ctx->st);
+  ctx->launches += 1;
+  r = check_err_flag(ctx);
+  if (r) return r;
+  return launch_status(ctx);
+}
+
+int ugks_move_mesh(ugks_ctx *ctx, double t_new, const double *affine) {
+  if (!ctx || !ctx->mesh_ready) return UGKS_ERR_ORDER;
+  if (!affine) return fail(ctx, UGKS_ERR_ARG, "null affine");
+  if (!(t_new > ctx->t)) return fail(ctx, UGKS_ERR_ARG, "t_new must exceed the current time");
+  Dev &d = ctx->d;
+  ctx->h_affine.assign(affine, affine + 6 * (size_t)ctx->nblocks);
+  std::swap(d.X_old, d.X_new);
+  CK(cudaMemcpyAsync(d.affine, ctx->h_affine.data(), sizeof(double) * 6 * ctx->nblocks,
+                     cudaMemcpyHostToDevice, ctx->st));
+  d.dt = t_new - ctx->t;
+  ctx->t_new = t_new;
+  launch_move_nodes(d, ctx->st);
+  launch_geometry(d, ctx->st);
+  launch_slope_geo(d, ctx->st);
+  ctx->launches += 5;
+  ctx->moved = true;
+  return launch_status(ctx);
+}
+
+int ugks_overset_connect(ugks_ctx *ctx, ugks_connect_stats *stats) {
+  if (!ctx || !ctx->mesh_ready) return UGKS_ERR_ORDER;
+  if (!ctx->moved) return fail(ctx, UGKS_ERR_ORDER, "ugks_overset_connect needs a preceding ugks_move_mesh");
+  int r = check_err_flag(ctx);
+  if (r) return r;
+  return do_connect(ctx, stats, false);
+}
+
+int ugks_step(ugks_ctx *ctx, double dt, int n_inner) {
+  if (!ctx || !ctx->mesh_ready) return UGKS_ERR_ORDER;
+  if (!ctx->moved) return fail(ctx, UGKS_ERR_ORDER, "ugks_step needs a preceding ugks_move_mesh");
+  if (n_inner < 1) return fail(ctx, UGKS_ERR_ARG, "n_inner must be >= 1");
+  Dev &d = ctx->d;
+  if (fabs(dt - d.dt) > 1e-12 * fabs(d.dt)) return fail(ctx, UGKS_ERR_ARG, "dt differs from the move's step");
+  cudaStream_t s = ctx->st;
+  int fp = ctx->fp32;
+  do_interp(ctx, d.fresh_list, d.nfresh);
+  do_interp(ctx, d.rec_list, d.nrec);
+  // Steps 1-2: level-n flux, extensive level-n macro term, level-n cell record
+  launch_flux_prep(d, s, 1, fp);
+  launch_cell_params(d, s, d.W, d.cparn);
+  ctx->launches += 6;
+  for (int it = 0; it < n_inner; ++it) {
+    if (it > 0) {
+      do_interp(ctx, d.rec_list, d.nrec);
+      launch_flux_prep(d, s, 0, fp);          // Step 3
+      ctx->launches += 5;
+    }
+    launch_macro_sweep(d, s, ctx->max_nj);    // Step 4
+    launch_micro(d, s, ctx->work, ctx->nwork, ctx->V, ctx->max_nj, it == 0, fp);  // Steps 5-6
+    launch_moments(d, s, fp);                 // Step 7
+    ctx->launches += 4;
+  }
+  d.nfresh = 0;
+  ctx->t = ctx->t_new;
+  ctx->moved = false;
+  return launch_status(ctx);
+}
+
+int ugks_moments(ugks_ctx *ctx, double *W, double *q, int32_t *status, double *wall_loads) {
+  if (!ctx || !ctx->mesh_ready) return UGKS_ERR_ORDER;
+  Dev &d = ctx->d;
+  launch_wall_loads(d, ctx->st);
+  ctx->launches += 1;
+  if (W) CK(cudaMemcpyAsync(W, d.W, sizeof(double) * 4 * d.nc, cudaMemcpyDefault, ctx->st));
+  if (q) CK(cudaMemcpyAsync(q, d.q, sizeof(double) * 2 * d.nc, cudaMemcpyDefault, ctx->st));
+  if (status) CK(cudaMemcpyAsync(status, d.status, sizeof(int) * d.nc, cudaMemcpyDefault, ctx->st));
+  if (wall_loads) CK(cudaMemcpyAsync(wall_loads, d.wall_loads, sizeof(double) * 4 * d.nblocks, cudaMemcpyDefault, ctx->st));
+  int r = check_err_flag(ctx);
+  if (r) return r;
+  return launch_status(ctx);
+}
+
+static bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int ugks_get_state(ugks_ctx *ctx, double *f, double *W, double *q) {
+  if (!ctx || !ctx->mesh_ready) return UGKS_ERR_ORDER;
+  Dev &d = ctx->d;
+  if (f) {
+    if (!is_device_ptr(f)) return fail(ctx, UGKS_ERR_ARG, "f must be a device pointer");
+    launch_f_convert(d, ctx->st, f, nullptr, ctx->fp32);
+    ctx->launches += 1;
+  }
+  if (W) CK(cudaMemcpyAsync(W, d.W, sizeof(double) * 4 * d.nc, cudaMemcpyDefault, ctx->st));
+  if (q) CK(cudaMemcpyAsync(q, d.q, sizeof(double) * 2 * d.nc, cudaMemcpyDefault, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return launch_status(ctx);
+}
+
+int ugks_set_state(ugks_ctx *ctx, const double *f, const double *W, const double *q) {
+  if (!ctx || !ctx->mesh_ready) return UGKS_ERR_ORDER;
+  Dev &d = ctx->d;
+  if (f) {
+    if (!is_device_ptr(f)) return fail(ctx, UGKS_ERR_ARG, "f must be a device pointer");
+    launch_f_convert(d, ctx->st, nullptr, f, ctx->fp32);
+    ctx->launches += 1;
+  }
+  if (W) CK(cudaMemcpyAsync(d.W, W, sizeof(double) * 4 * d.nc, cudaMemcpyDefault, ctx->st));
+  if (q) CK(cudaMemcpyAsync(d.q, q, sizeof(double) * 2 * d.nc, cudaMemcpyDefault, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return launch_status(ctx);
+}
+
+int ugks_eval_flux(ugks_ctx *ctx, double *D, double *F) {
+  if (!ctx || !ctx->mesh_ready) return UGKS_ERR_ORDER;
+  if (!ctx->moved) return fail(ctx, UGKS_ERR_ORDER, "ugks_eval_flux needs a preceding ugks_move_mesh");
+  Dev &d = ctx->d;
+  if (D && !is_device_ptr(D)) return fail(ctx, UGKS_ERR_ARG, "D must be a device pointer");
+  do_interp(ctx, d.rec_list, d.nrec);
+  launch_flux_prep(d, ctx->st, 0, ctx->fp32);
+  ctx->launches += 5;
+  if (D) { launch_flux_div_all(d, ctx->st, D, ctx->fp32); ctx->launches += 1; }
+  if (F) CK(cudaMemcpyAsync(F, d.Fc, sizeof(double) * 4 * d.nc, cudaMemcpyDefault, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return launch_status(ctx);
+}
+
+int ugks_get_connectivity(ugks_ctx *ctx, int32_t *status, int32_t *donors, double *weights) {
+  if (!ctx || !ctx->mesh_ready) return UGKS_ERR_ORDER;
+  Dev &d = ctx->d;
+  if (status) CK(cudaMemcpyAsync(status, d.status, sizeof(int) * d.nc, cudaMemcpyDefault, ctx->st));
+  if (donors) CK(cudaMemcpyAsync(donors, d.donors, sizeof(int) * 5 * d.nc, cudaMemcpyDefault, ctx->st));
+  if (weights) CK(cudaMemcpyAsync(weights, d.dwgt, sizeof(double) * 5 * d.nc, cudaMemcpyDefault, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return UGKS_OK;
+}
+
+int ugks_get_geometry(ugks_ctx *ctx, double *vol_old, double *vol_new, double *xc, double *dts,
+                      double *Sn, double *SUn) {
+  if (!ctx || !ctx->mesh_ready) return UGKS_ERR_ORDER;
+  Dev &d = ctx->d;
+  if (vol_old) CK(cudaMemcpyAsync(vol_old, d.vol_old, sizeof(double) * d.nc, cudaMemcpyDefault, ctx->st));
+  if (vol_new) CK(cudaMemcpyAsync(vol_new, d.vol_new, sizeof(double) * d.nc, cudaMemcpyDefault, ctx->st));
+  if (xc) CK(cudaMemcpyAsync(xc, d.xc, sizeof(double) * 2 * d.nc, cudaMemcpyDefault, ctx->st));
+  if (dts) CK(cudaMemcpyAsync(dts, d.dts, sizeof(double) * d.nc, cudaMemcpyDefault, ctx->st));
+  if (Sn) CK(cudaMemcpyAsync(Sn, d.Sn, sizeof(double) * 2 * d.nf, cudaMemcpyDefault, ctx->st));
+  if (SUn) CK(cudaMemcpyAsync(SUn, d.SUn, sizeof(double) * d.nf, cudaMemcpyDefault, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return check_err_flag(ctx);
+}
+
+}  // extern "C"

@@ -1,0 +1,261 @@
+// ugks_internal.cuh -- device-side context of libugks and the per-(cell,
+// velocity) building blocks shared by the kernels: limited reconstruction
+// (Sec. 2.1, second-order initial distribution), the time-averaged interface
+// flux of one velocity (Eqs. microscopicFlux, fullSolution; wall condition
+// with Eq. maxWalldes) and its sum over the faces of a cell.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "ugks_math.cuh"
+
+namespace ugks {
+
+enum { BC_NONE = 0, BC_WALL = 1, BC_FARFIELD = 2, BC_OUTFLOW = 3, BC_OVERSET = 4 };
+enum { ST_FIELD = 0, ST_RECEPTOR = 1, ST_HOLE = 2 };
+enum { NB_CELL = 0, NB_GHOST = 1, NB_NONE = 2 };
+// slope case per logical direction: none, only minus side, only plus side, both
+enum { SL_NONE = 0, SL_M = 1, SL_P = 2, SL_BOTH = 3 };
+// face sums of the velocity-reduction pass
+enum { FS_W0 = 0, FS_FF = 4, FS_WG = 8, NFS = 12 };
+// error flags
+enum { EF_GEOMETRY = 1, EF_NONPHYSICAL = 2 };
+
+template <typename T> struct Vec2;
+template <> struct Vec2<double> { typedef double2 type; };
+template <> struct Vec2<float> { typedef float2 type; };
+
+// Everything a kernel needs: sizes, constants and borrowed device pointers
+// into the caller's workspace.  Passed by value.
+struct Dev {
+  int nc, nf, nn, nv, nvp, nblocks;
+  int Keff, Kint;
+  double Pr, omega, mu_ref, cfl_s, cfl_pseudo;
+  double Winf[4];
+  double dt;
+  // velocity space (double and float copies), length nvp (padding weight 0)
+  const double *vx, *vy, *w;
+  const float *vxf, *vyf, *wf;
+  // static topology
+  const int *cell_nodes;     // nc*4
+  const int *cell_faces;     // nc*4 (IM, IP, JM, JP)
+  const int8_t *cell_sgn;    // nc*4, +1 if the cell is the face's L side
+  const int *nb_kind;        // nc*4
+  const int *nb_id;          // nc*4 cell id or ghost face id
+  const int8_t *nb_shift;    // nc*4 period multiplier
+  const int *cell_row;       // nc*2 node ids (0,j), (ni,j)
+  const int *cell_block;     // nc
+  const int *node_block;     // nn
+  const int *face_L, *face_R, *face_a, *face_b, *face_kind, *face_block;
+  const int8_t *face_shiftL;
+  const double *face_Tw;
+  // per-step geometry
+  const double *X_ref;
+  double *X_old, *X_new;     // nn*2
+  double *vol_old, *vol_new; // nc
+  double *xc, *xc_new;       // nc*2
+  double *period;            // nc*2
+  double *dts;               // nc
+  double *Sn, *S, *nrm, *xf, *Uf, *SUn;   // nf*2 / nf
+  int *slope_flags;          // nc: 2 bits per direction (i: bits 0-1, j: 2-3)
+  double *jinv;              // nc*4 inverse of [[x_xi, y_xi],[x_eta, y_eta]]
+  double *affine;            // nblocks*6
+  // state
+  void *f;                   // nc*nvp (h, b) pairs in the storage type
+  double *W, *q;             // nc*4, nc*2
+  int *status;               // nc
+  // work
+  void *Tn, *dfs;            // nc*nvp pairs: level-n term, forward-sweep result
+  double *TW;                // nc*4 extensive level-n macro term
+  double *Fc;                // nc*4 macro flux divergence of the last flux
+  double *dW;                // nc*4 macro increment
+  double *Wp;                // nc*4 macro predictor W'
+  double *cpar;              // nc*NCP cell parameters (predictor / level n)
+  double *cparn;
+  double *gradW;             // nc*8
+  double *ghostW;            // nf*4
+  double *fsum;              // nf*NFS
+  double *fpar;              // nf*NFP (double)
+  void *fparT;               // nf*NFP in the arithmetic type
+  double *fflux;             // nf*4 S * macro flux (L -> R / outward)
+  double *gam;               // nf spectral radius Gamma
+  double *wall_loads;        // nblocks*4
+  // overset
+  int *node_active;          // nn
+  int *cls;                  // nc scratch classification
+  int *donors;               // nc*5
+  double *dwgt;              // nc*5
+  int *rec_list;             // receptor cells (compacted on the host)
+  int nrec;
+  int *fresh_list;
+  int nfresh;
+  void *itmp;                // interpolation staging: max(nrec, nfresh)*nvp pairs
+  double *itmpW;             // ... *6 doubles
+  int *wall_seg;             // segments: node id pairs, grouped per block
+  int *wall_seg_off;         // nblocks+1
+  int *body_ring;            // body polygon node ids, grouped per block
+  int *body_ring_off;        // nblocks+1
+  const int *cell_off;       // nblocks+1 (device copy)
+  const int *node_off;       // nblocks+1
+  const int *blk_info;       // nblocks*8: ni, nj, periodic, priority, n_fringe, n_gap, bc-overset mask, body?
+  int *err;                  // error flags
+};
+
+// per-cell parameter record (from W' or W^n)
+enum { CP_RHO = 0, CP_UX, CP_UY, CP_LAM, CP_QX, CP_QY, CP_ITAU, CP_PREF, NCP = 8 };
+
+template <typename T>
+__device__ __forceinline__ typename Vec2<T>::type ldf(const void *base, size_t idx) {
+  return reinterpret_cast<const typename Vec2<T>::type *>(base)[idx];
+}
+template <typename T>
+__device__ __forceinline__ void stf(void *base, size_t idx, T h, T b) {
+  typename Vec2<T>::type v;
+  v.x = h;
+  v.y = b;
+  reinterpret_cast<typename Vec2<T>::type *>(base)[idx] = v;
+}
+
+template <typename T> __device__ __forceinline__ T dvx(const Dev &d, int k);
+template <> __device__ __forceinline__ double dvx<double>(const Dev &d, int k) { return d.vx[k]; }
+template <> __device__ __forceinline__ float dvx<float>(const Dev &d, int k) { return d.vxf[k]; }
+template <typename T> __device__ __forceinline__ T dvy(const Dev &d, int k);
+template <> __device__ __forceinline__ double dvy<double>(const Dev &d, int k) { return d.vy[k]; }
+template <> __device__ __forceinline__ float dvy<float>(const Dev &d, int k) { return d.vyf[k]; }
+
+// value of the cell field f at velocity k for neighbour slot `s` of cell c
+// (cell neighbour or ghost Maxwellian of the ghost state)
+template <typename T>
+__device__ __forceinline__ V2<T> nb_value(const Dev &d, int c, int s, int k) {
+  int kind = d.nb_kind[c * 4 + s];
+  int id = d.nb_id[c * 4 + s];
+  if (kind == NB_CELL) {
+    auto v = ldf<T>(d.f, (size_t)id * d.nvp + k);
+    return {v.x, v.y};
+  }
+  const double *g = d.ghostW + 4 * id;
+  Prim p = primitive(g, d.Keff);
+  return maxwellian<T>((T)p.rho, (T)p.ux, (T)p.uy, (T)p.lam, dvx<T>(d, k), dvy<T>(d, k),
+                       (T)d.Keff);
+}
+
+// Limited Cartesian gradient of (h, b) of cell c at velocity k (reading R1:
+// van Leer on both-sided centre differences, one-sided where a side has no
+// neighbour, mapped with the inverse Jacobian of the centre differences).
+template <typename T>
+__device__ __forceinline__ void grad_f(const Dev &d, int c, int k, V2<T> fc, V2<T> &gx,
+                                       V2<T> &gy) {
+  int fl = d.slope_flags[c];
+  V2<T> s[2];
+#pragma unroll
+  for (int dir = 0; dir < 2; ++dir) {
+    int cs = (fl >> (2 * dir)) & 3;
+    V2<T> r = {T(0), T(0)};
+    if (cs == SL_BOTH) {
+      V2<T> m = nb_value<T>(d, c, 2 * dir, k), p = nb_value<T>(d, c, 2 * dir + 1, k);
+      r.h = vanleer<T>(fc.h - m.h, p.h - fc.h);
+      r.b = vanleer<T>(fc.b - m.b, p.b - fc.b);
+    } else if (cs == SL_P) {
+      V2<T> p = nb_value<T>(d, c, 2 * dir + 1, k);
+      r.h = p.h - fc.h;
+      r.b = p.b - fc.b;
+    } else if (cs == SL_M) {
+      V2<T> m = nb_value<T>(d, c, 2 * dir, k);
+      r.h = fc.h - m.h;
+      r.b = fc.b - m.b;
+    }
+    s[dir] = r;
+  }
+  const double *J = d.jinv + 4 * c;
+  T i11 = (T)J[0], i12 = (T)J[1], i21 = (T)J[2], i22 = (T)J[3];
+  gx.h = i11 * s[0].h + i12 * s[1].h;
+  gx.b = i11 * s[0].b + i12 * s[1].b;
+  gy.h = i21 * s[0].h + i22 * s[1].h;
+  gy.b = i21 * s[0].b + i22 * s[1].b;
+}
+
+template <typename T> __device__ __forceinline__ const T *fparT(const Dev &d, int f) {
+  return reinterpret_cast<const T *>(d.fparT) + (size_t)f * NFP;
+}
+
+// S * time-averaged interface flux of velocity k through face fid, oriented
+// along the face normal (L -> R, outward for boundary faces).
+template <typename T> __device__ V2<T> face_flux(const Dev &d, int fid, int k) {
+  T vx = dvx<T>(d, k), vy = dvy<T>(d, k);
+  T wS = vx * (T)d.Sn[2 * fid] + vy * (T)d.Sn[2 * fid + 1] - (T)d.SUn[fid];
+  const T *P = fparT<T>(d, fid);
+  int kind = d.face_kind[fid];
+  int L = d.face_L[fid];
+  T ufx = P[FP_UFX], ufy = P[FP_UFY];
+  T wx = vx - ufx, wy = vy - ufy;
+  V2<T> ff, wgf;
+  if (kind == BC_WALL) {
+    if (!(wS > T(0))) {
+      // reflected part: wall Maxwellian at the face velocity (Eq. maxWalldes)
+      T lw = P[FP_LAMW];
+      T Hw = P[FP_RHOW] * (lw / T(M_PI)) * r_exp<T>(-lw * (wx * wx + wy * wy));
+      return {wS * Hw, wS * (T)d.Keff / (T(2) * lw) * Hw};
+    }
+    auto fv = ldf<T>(d.f, (size_t)L * d.nvp + k);
+    V2<T> fc = {fv.x, fv.y}, gx, gy;
+    grad_f<T>(d, L, k, fc, gx, gy);
+    T dx = (T)(d.xf[2 * fid] - d.xc[2 * L]), dy = (T)(d.xf[2 * fid + 1] - d.xc[2 * L + 1]);
+    ff = {fc.h + dx * gx.h + dy * gy.h, fc.b + dx * gx.b + dy * gy.b};
+    wgf = {wx * gx.h + wy * gy.h, wx * gx.b + wy * gy.b};
+  } else {
+    int R = d.face_R[fid];
+    bool useL = wS > T(0), useR = wS < T(0);
+    V2<T> fL = {0, 0}, fR = {0, 0}, gL = {0, 0}, gR = {0, 0};
+    if (!useR) {
+      auto fv = ldf<T>(d.f, (size_t)L * d.nvp + k);
+      V2<T> fc = {fv.x, fv.y}, gx, gy;
+      grad_f<T>(d, L, k, fc, gx, gy);
+      double sh = (double)d.face_shiftL[fid];
+      T dx = (T)(d.xf[2 * fid] - (d.xc[2 * L] + sh * d.period[2 * L]));
+      T dy = (T)(d.xf[2 * fid + 1] - (d.xc[2 * L + 1] + sh * d.period[2 * L + 1]));
+      fL = {fc.h + dx * gx.h + dy * gy.h, fc.b + dx * gx.b + dy * gy.b};
+      gL = {wx * gx.h + wy * gy.h, wx * gx.b + wy * gy.b};
+    }
+    if (!useL) {
+      if (R >= 0) {
+        auto fv = ldf<T>(d.f, (size_t)R * d.nvp + k);
+        V2<T> fc = {fv.x, fv.y}, gx, gy;
+        grad_f<T>(d, R, k, fc, gx, gy);
+        T dx = (T)(d.xf[2 * fid] - d.xc[2 * R]), dy = (T)(d.xf[2 * fid + 1] - d.xc[2 * R + 1]);
+        fR = {fc.h + dx * gx.h + dy * gy.h, fc.b + dx * gx.b + dy * gy.b};
+        gR = {wx * gx.h + wy * gy.h, wx * gx.b + wy * gy.b};
+      } else {
+        const double *g = d.ghostW + 4 * fid;
+        Prim p = primitive(g, d.Keff);
+        fR = maxwellian<T>((T)p.rho, (T)p.ux, (T)p.uy, (T)p.lam, vx, vy, (T)d.Keff);
+      }
+    }
+    if (useL) {
+      ff = fL; wgf = gL;
+    } else if (useR) {
+      ff = fR; wgf = gR;
+    } else {
+      ff = {T(0.5) * (fL.h + fR.h), T(0.5) * (fL.b + fR.b)};
+      wgf = {T(0.5) * (gL.h + gR.h), T(0.5) * (gL.b + gR.b)};
+    }
+  }
+  V2<T> I = interface_integral<T>(P, vx, vy, ff, wgf, (T)d.Keff, (T)d.Kint, (T)d.Pr);
+  return {wS * I.h, wS * I.b};
+}
+
+// D_ik = sum over the faces of cell c of S F_hat (outward positive).
+template <typename T> __device__ V2<T> flux_div(const Dev &d, int c, int k) {
+  V2<T> acc = {T(0), T(0)};
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    int fid = d.cell_faces[c * 4 + s];
+    int kind = d.face_kind[fid];
+    if (kind == BC_OVERSET) continue;   // outer edge of a component grid: receptors only
+    V2<T> F = face_flux<T>(d, fid, k);
+    T sg = (T)d.cell_sgn[c * 4 + s];
+    acc.h += sg * F.h;
+    acc.b += sg * F.b;
+  }
+  return acc;
+}
+
+}  // namespace ugks

@@ -1,0 +1,952 @@
+// ugks_kernels.cu -- CUDA kernels of the implicit UGKS step (arXiv 2604.09984
+// Sec. 2.2 Steps 1-8) on moving structured blocks, and the mesh-motion /
+// geometry kernels (Sec. 3 Step 1).  Launch wrappers at the end are the only
+// symbols used by the host orchestration (ugks_api.cu).
+#include "ugks_internal.cuh"
+#include "ugks_launch.h"
+
+namespace ugks {
+
+// ------------------------------------------------------------- geometry
+// x = (m00 x0 + m01 y0) + b0, y = (m10 x0 + m11 y0) + b1 without contraction
+// (bit-identical to the FP64 reference evaluation).
+__global__ void k_move_nodes(Dev d) {
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= d.nn) return;
+  const double *a = d.affine + 6 * d.node_block[n];
+  double x = d.X_ref[2 * n], y = d.X_ref[2 * n + 1];
+  d.X_new[2 * n] = __dadd_rn(__dadd_rn(__dmul_rn(a[0], x), __dmul_rn(a[1], y)), a[4]);
+  d.X_new[2 * n + 1] = __dadd_rn(__dadd_rn(__dmul_rn(a[2], x), __dmul_rn(a[3], y)), a[5]);
+}
+
+__device__ __forceinline__ double shoelace(const double *X, const int *nd) {
+  double x1 = X[2 * nd[0]], y1 = X[2 * nd[0] + 1], x2 = X[2 * nd[1]], y2 = X[2 * nd[1] + 1];
+  double x3 = X[2 * nd[2]], y3 = X[2 * nd[2] + 1], x4 = X[2 * nd[3]], y4 = X[2 * nd[3] + 1];
+  return 0.5 * __dsub_rn(__dmul_rn(x3 - x1, y4 - y2), __dmul_rn(y3 - y1, x4 - x2));
+}
+
+// Cell volumes at both levels (shoelace), mid-time and new vertex centres,
+// period vector of the cell's row.
+__global__ void k_cell_geom(Dev d) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.nc) return;
+  const int *nd = d.cell_nodes + 4 * c;
+  double vo = shoelace(d.X_old, nd), vn = shoelace(d.X_new, nd);
+  d.vol_old[c] = vo;
+  d.vol_new[c] = vn;
+  if (!(vn > 0.0) || !(vo > 0.0)) atomicOr(d.err, EF_GEOMETRY);
+  for (int m = 0; m < 2; ++m) {
+    double pm[4], pn[4];
+    for (int v = 0; v < 4; ++v) {
+      pm[v] = 0.5 * (d.X_old[2 * nd[v] + m] + d.X_new[2 * nd[v] + m]);
+      pn[v] = d.X_new[2 * nd[v] + m];
+    }
+    d.xc[2 * c + m] = 0.25 * ((pm[0] + pm[1]) + (pm[2] + pm[3]));
+    d.xc_new[2 * c + m] = 0.25 * ((pn[0] + pn[1]) + (pn[2] + pn[3]));
+    int r0 = d.cell_row[2 * c], r1 = d.cell_row[2 * c + 1];
+    double a = 0.5 * (d.X_old[2 * r0 + m] + d.X_new[2 * r0 + m]);
+    double b = 0.5 * (d.X_old[2 * r1 + m] + d.X_new[2 * r1 + m]);
+    d.period[2 * c + m] = b - a;
+  }
+}
+
+// Mid-time face vector S n (L -> R / outward), centre, face velocity (mean
+// node velocity) and S U.n.
+__global__ void k_face_geom(Dev d) {
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= d.nf) return;
+  int a = d.face_a[f], b = d.face_b[f];
+  double ax = 0.5 * (d.X_old[2 * a] + d.X_new[2 * a]), ay = 0.5 * (d.X_old[2 * a + 1] + d.X_new[2 * a + 1]);
+  double bx = 0.5 * (d.X_old[2 * b] + d.X_new[2 * b]), by = 0.5 * (d.X_old[2 * b + 1] + d.X_new[2 * b + 1]);
+  double ex = bx - ax, ey = by - ay;
+  double S = sqrt(ex * ex + ey * ey);
+  d.Sn[2 * f] = ey;
+  d.Sn[2 * f + 1] = -ex;
+  d.S[f] = S;
+  d.nrm[2 * f] = ey / S;
+  d.nrm[2 * f + 1] = -ex / S;
+  d.xf[2 * f] = 0.5 * (ax + bx);
+  d.xf[2 * f + 1] = 0.5 * (ay + by);
+  double ufx = 0.5 * ((d.X_new[2 * a] - d.X_old[2 * a]) + (d.X_new[2 * b] - d.X_old[2 * b])) / d.dt;
+  double ufy = 0.5 * ((d.X_new[2 * a + 1] - d.X_old[2 * a + 1]) + (d.X_new[2 * b + 1] - d.X_old[2 * b + 1])) / d.dt;
+  d.Uf[2 * f] = ufx;
+  d.Uf[2 * f + 1] = ufy;
+  d.SUn[f] = ufx * ey + ufy * (-ex);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Reading R3: dts_i = cfl_s Omega_i^{n+1} / max_k sum_faces S max(w_out, 0).
+// One warp per cell.
+__global__ void k_dts(Dev d) {
+  int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (c >= d.nc) return;
+  double m = 0.0;
+  for (int k = lane; k < d.nv; k += 32) {
+    double s = 0.0;
+    for (int q = 0; q < 4; ++q) {
+      int f = d.cell_faces[4 * c + q];
+      double wS = d.vx[k] * d.Sn[2 * f] + d.vy[k] * d.Sn[2 * f + 1] - d.SUn[f];
+      s += fmax(d.cell_sgn[4 * c + q] * wS, 0.0);
+    }
+    m = fmax(m, s);
+  }
+  m = warp_max(m);
+  if (lane == 0) d.dts[c] = d.cfl_s * d.vol_new[c] / m;
+}
+
+// Slope case and inverse Jacobian per cell (reading R1); depends on the
+// geometry and on which neighbours are holes.
+__global__ void k_slope_geo(Dev d) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.nc) return;
+  double g[2][2];
+  int flags = 0;
+  double xcx = d.xc[2 * c], xcy = d.xc[2 * c + 1];
+  for (int dir = 0; dir < 2; ++dir) {
+    bool has[2];
+    double px[2], py[2];
+    for (int side = 0; side < 2; ++side) {
+      int s = 2 * dir + side;
+      int kind = d.nb_kind[4 * c + s], id = d.nb_id[4 * c + s];
+      has[side] = false;
+      px[side] = py[side] = 0.0;
+      if (kind == NB_CELL) {
+        double sh = (double)d.nb_shift[4 * c + s];
+        px[side] = d.xc[2 * id] + sh * d.period[2 * c];
+        py[side] = d.xc[2 * id + 1] + sh * d.period[2 * c + 1];
+        has[side] = d.status[id] != ST_HOLE;
+      } else if (kind == NB_GHOST) {
+        double nx = d.nrm[2 * id], ny = d.nrm[2 * id + 1];
+        double dd = (d.xf[2 * id] - xcx) * nx + (d.xf[2 * id + 1] - xcy) * ny;
+        px[side] = xcx + 2.0 * dd * nx;
+        py[side] = xcy + 2.0 * dd * ny;
+        has[side] = true;
+      }
+    }
+    int cs;
+    if (has[0] && has[1]) {
+      cs = SL_BOTH;
+      g[dir][0] = 0.5 * (px[1] - px[0]);
+      g[dir][1] = 0.5 * (py[1] - py[0]);
+    } else if (has[1]) {
+      cs = SL_P;
+      g[dir][0] = px[1] - xcx;
+      g[dir][1] = py[1] - xcy;
+    } else if (has[0]) {
+      cs = SL_M;
+      g[dir][0] = xcx - px[0];
+      g[dir][1] = xcy - py[0];
+    } else {
+      cs = SL_NONE;
+      int fm = d.cell_faces[4 * c + 2 * dir], fp = d.cell_faces[4 * c + 2 * dir + 1];
+      g[dir][0] = d.xf[2 * fp] - d.xf[2 * fm];
+      g[dir][1] = d.xf[2 * fp + 1] - d.xf[2 * fm + 1];
+    }
+    flags |= cs << (2 * dir);
+  }
+  double a11 = g[0][0], a12 = g[0][1], a21 = g[1][0], a22 = g[1][1];
+  double det = a11 * a22 - a12 * a21;
+  d.slope_flags[c] = flags;
+  d.jinv[4 * c + 0] = a22 / det;
+  d.jinv[4 * c + 1] = -a12 / det;
+  d.jinv[4 * c + 2] = -a21 / det;
+  d.jinv[4 * c + 3] = a11 / det;
+}
+
+// Ghost states of far-field / outflow faces (reading R6).
+__global__ void k_ghost(Dev d) {
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= d.nf) return;
+  int kind = d.face_kind[f];
+  for (int m = 0; m < 4; ++m) {
+    double v = 0.0;
+    if (kind == BC_FARFIELD) v = d.Winf[m];
+    else if (kind == BC_OUTFLOW) v = d.W[4 * d.face_L[f] + m];
+    d.ghostW[4 * f + m] = v;
+  }
+}
+
+// Limited gradient of the conservative W per cell (reading R1).
+__global__ void k_gradW(Dev d) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.nc) return;
+  int fl = d.slope_flags[c];
+  const double *J = d.jinv + 4 * c;
+  for (int m = 0; m < 4; ++m) {
+    double wc = d.W[4 * c + m];
+    double s[2];
+    for (int dir = 0; dir < 2; ++dir) {
+      int cs = (fl >> (2 * dir)) & 3;
+      double val[2] = {0.0, 0.0};
+      for (int side = 0; side < 2; ++side) {
+        int sl = 2 * dir + side;
+        int kind = d.nb_kind[4 * c + sl], id = d.nb_id[4 * c + sl];
+        if (kind == NB_CELL) val[side] = d.W[4 * id + m];
+        else if (kind == NB_GHOST) val[side] = d.ghostW[4 * id + m];
+      }
+      double r = 0.0;
+      if (cs == SL_BOTH) r = vanleer<double>(wc - val[0], val[1] - wc);
+      else if (cs == SL_P) r = val[1] - wc;
+      else if (cs == SL_M) r = wc - val[0];
+      s[dir] = r;
+    }
+    d.gradW[8 * c + 2 * m] = J[0] * s[0] + J[1] * s[1];
+    d.gradW[8 * c + 2 * m + 1] = J[2] * s[0] + J[3] * s[1];
+  }
+}
+
+__device__ __forceinline__ bool face_needed(const Dev &d, int f) {
+  int L = d.face_L[f], R = d.face_R[f];
+  return d.status[L] == ST_FIELD || (R >= 0 && d.status[R] == ST_FIELD);
+}
+
+// Upwind face value and w.grad f of the upwind cell for velocity k (walls:
+// the interior side only); shared by the reduction pass.
+template <typename T>
+__device__ __forceinline__ void face_upwind(const Dev &d, int fid, int k, T wS, V2<T> &ff,
+                                            V2<T> &wgf) {
+  T vx = dvx<T>(d, k), vy = dvy<T>(d, k);
+  T wx = vx - (T)d.Uf[2 * fid], wy = vy - (T)d.Uf[2 * fid + 1];
+  int kind = d.face_kind[fid];
+  int L = d.face_L[fid];
+  bool useL = (kind == BC_WALL) || wS > T(0), useR = (kind != BC_WALL) && wS < T(0);
+  V2<T> fL = {0, 0}, fR = {0, 0}, gL = {0, 0}, gR = {0, 0};
+  if (!useR) {
+    auto fv = ldf<T>(d.f, (size_t)L * d.nvp + k);
+    V2<T> fc = {fv.x, fv.y}, gx, gy;
+    grad_f<T>(d, L, k, fc, gx, gy);
+    double sh = (double)d.face_shiftL[fid];
+    T dx = (T)(d.xf[2 * fid] - (d.xc[2 * L] + sh * d.period[2 * L]));
+    T dy = (T)(d.xf[2 * fid + 1] - (d.xc[2 * L + 1] + sh * d.period[2 * L + 1]));
+    fL = {fc.h + dx * gx.h + dy * gy.h, fc.b + dx * gx.b + dy * gy.b};
+    gL = {wx * gx.h + wy * gy.h, wx * gx.b + wy * gy.b};
+  }
+  if (!useL) {
+    int R = d.face_R[fid];
+    if (R >= 0) {
+      auto fv = ldf<T>(d.f, (size_t)R * d.nvp + k);
+      V2<T> fc = {fv.x, fv.y}, gx, gy;
+      grad_f<T>(d, R, k, fc, gx, gy);
+      T dx = (T)(d.xf[2 * fid] - d.xc[2 * R]), dy = (T)(d.xf[2 * fid + 1] - d.xc[2 * R + 1]);
+      fR = {fc.h + dx * gx.h + dy * gy.h, fc.b + dx * gx.b + dy * gy.b};
+      gR = {wx * gx.h + wy * gy.h, wx * gx.b + wy * gy.b};
+    } else {
+      Prim p = primitive(d.ghostW + 4 * fid, d.Keff);
+      fR = maxwellian<T>((T)p.rho, (T)p.ux, (T)p.uy, (T)p.lam, vx, vy, (T)d.Keff);
+    }
+  }
+  if (useL) {
+    ff = fL; wgf = gL;
+  } else if (useR) {
+    ff = fR; wgf = gR;
+  } else {
+    ff = {T(0.5) * (fL.h + fR.h), T(0.5) * (fL.b + fR.b)};
+    wgf = {T(0.5) * (gL.h + gR.h), T(0.5) * (gL.b + gR.b)};
+  }
+}
+
+// Velocity-reduction pass per face (one warp per face): W0 = sum V Psi ff
+// (interface equilibrium, Sec. 2.1), and the f-dependent parts of the macro
+// flux sum V Psi wS ff, sum V Psi wS w.grad f (walls: incident side only).
+template <typename T> __global__ void k_face_reduce(Dev d) {
+  int fid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (fid >= d.nf) return;
+  if (!face_needed(d, fid) || d.face_kind[fid] == BC_OVERSET) {
+    if (lane < NFS) d.fsum[NFS * fid + lane] = 0.0;
+    return;
+  }
+  bool wall = d.face_kind[fid] == BC_WALL;
+  double acc[NFS];
+#pragma unroll
+  for (int m = 0; m < NFS; ++m) acc[m] = 0.0;
+  double snx = d.Sn[2 * fid], sny = d.Sn[2 * fid + 1], sun = d.SUn[fid];
+  for (int k = lane; k < d.nv; k += 32) {
+    T vx = dvx<T>(d, k), vy = dvy<T>(d, k);
+    T wS = vx * (T)snx + vy * (T)sny - (T)sun;
+    if (wall && !(wS > T(0))) continue;
+    V2<T> ff, wg;
+    face_upwind<T>(d, fid, k, wS, ff, wg);
+    double w = d.w[k], dvx_ = d.vx[k], dvy_ = d.vy[k];
+    double v2 = 0.5 * (dvx_ * dvx_ + dvy_ * dvy_);
+    double h = ff.h, b = ff.b, gh = wg.h, gb = wg.b, ws = (double)wS;
+    double p[4] = {w * h, w * dvx_ * h, w * dvy_ * h, w * (v2 * h + 0.5 * b)};
+    double g[4] = {w * gh, w * dvx_ * gh, w * dvy_ * gh, w * (v2 * gh + 0.5 * gb)};
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      acc[FS_W0 + m] += p[m];
+      acc[FS_FF + m] += ws * p[m];
+      acc[FS_WG + m] += ws * g[m];
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < NFS; ++m) acc[m] = warp_sum(acc[m]);
+  if (lane == 0) {
+    for (int m = 0; m < NFS; ++m) d.fsum[NFS * fid + m] = acc[m];
+    if (wall)
+      for (int m = 0; m < 4; ++m) d.fsum[NFS * fid + FS_W0 + m] = 0.0;
+  }
+}
+
+__device__ __forceinline__ double spectral_radius(const double *Wf, double nx, double ny, double un,
+                                                  int Keff) {
+  Prim p = primitive(Wf, Keff);
+  double pr = p.rho / (2.0 * p.lam);
+  double gamma = (4.0 + Keff) / (2.0 + Keff);
+  return fabs(p.ux * nx + p.uy * ny - un) + sqrt(gamma * pr / p.rho);
+}
+
+// Face coefficients (one warp per face): g0 parameters and slopes (reading
+// R2), time integrals over dts, the g-part of the macro flux by a sum over the
+// discrete velocities, the wall density rho_w (Eq. maxWalldes), the total
+// S-weighted macro flux and the spectral radius Gamma (Sec. 2.2).
+template <typename T> __global__ void k_face_coef(Dev d) {
+  int fid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (fid >= d.nf) return;
+  int kind = d.face_kind[fid];
+  double *P = d.fpar + (size_t)NFP * fid;
+  T *PT = reinterpret_cast<T *>(d.fparT) + (size_t)NFP * fid;
+  if (!face_needed(d, fid) || kind == BC_OVERSET) {
+    if (lane < 4) d.fflux[4 * fid + lane] = 0.0;
+    if (lane == 0) d.gam[fid] = 0.0;
+    return;
+  }
+  int L = d.face_L[fid], R = d.face_R[fid];
+  bool wall = kind == BC_WALL;
+  double W0[4], gx[4], gy[4], q0x, q0y, dts;
+  double ufx = d.Uf[2 * fid], ufy = d.Uf[2 * fid + 1];
+  double nx = d.nrm[2 * fid], ny = d.nrm[2 * fid + 1];
+  const double *fs = d.fsum + NFS * fid;
+  if (wall) {
+    double dx = d.xf[2 * fid] - d.xc[2 * L], dy = d.xf[2 * fid + 1] - d.xc[2 * L + 1];
+    for (int m = 0; m < 4; ++m) {
+      gx[m] = d.gradW[8 * L + 2 * m];
+      gy[m] = d.gradW[8 * L + 2 * m + 1];
+      W0[m] = d.W[4 * L + m] + (dx * gx[m] + dy * gy[m]);
+    }
+    q0x = d.q[2 * L];
+    q0y = d.q[2 * L + 1];
+    dts = d.dts[L];
+  } else {
+    double sh = (double)d.face_shiftL[fid];
+    double xLx = d.xc[2 * L] + sh * d.period[2 * L], xLy = d.xc[2 * L + 1] + sh * d.period[2 * L + 1];
+    double xRx, xRy, WL[4], WR[4], dL[8], dR[8];
+    for (int m = 0; m < 4; ++m) WL[m] = d.W[4 * L + m];
+    for (int m = 0; m < 8; ++m) dL[m] = d.gradW[8 * L + m];
+    if (R >= 0) {
+      xRx = d.xc[2 * R];
+      xRy = d.xc[2 * R + 1];
+      for (int m = 0; m < 4; ++m) WR[m] = d.W[4 * R + m];
+      for (int m = 0; m < 8; ++m) dR[m] = d.gradW[8 * R + m];
+      q0x = 0.5 * (d.q[2 * L] + d.q[2 * R]);
+      q0y = 0.5 * (d.q[2 * L + 1] + d.q[2 * R + 1]);
+      dts = fmin(d.dts[L], d.dts[R]);
+    } else {
+      double dd = (d.xf[2 * fid] - xLx) * nx + (d.xf[2 * fid + 1] - xLy) * ny;
+      xRx = xLx + 2.0 * dd * nx;
+      xRy = xLy + 2.0 * dd * ny;
+      for (int m = 0; m < 4; ++m) WR[m] = d.ghostW[4 * fid + m];
+      for (int m = 0; m < 8; ++m) dR[m] = 0.0;
+      q0x = 0.5 * d.q[2 * L];
+      q0y = 0.5 * d.q[2 * L + 1];
+      dts = d.dts[L];
+    }
+    double tx = xRx - xLx, ty = xRy - xLy, t2 = tx * tx + ty * ty;
+    for (int m = 0; m < 4; ++m) {
+      W0[m] = fs[FS_W0 + m];
+      double avx = 0.5 * (dL[2 * m] + dR[2 * m]), avy = 0.5 * (dL[2 * m + 1] + dR[2 * m + 1]);
+      double jump = (WR[m] - WL[m]) - (avx * tx + avy * ty);
+      gx[m] = avx + jump * (tx / t2);
+      gy[m] = avy + jump * (ty / t2);
+    }
+  }
+  Prim p0 = primitive(W0, d.Keff);
+  double ax[4], ay[4], At[4];
+  micro_slope(p0, d.Keff, gx, ax);
+  micro_slope(p0, d.Keff, gy, ay);
+  time_slope(p0, d.Keff, ax, ay, gx, gy, ufx, ufy, At);
+  double tau = collision_time(p0.rho, p0.lam, d.mu_ref, d.omega);
+  double qi[5];
+  time_integrals(dts, tau, qi);
+  double par[NFP];
+  par[FP_RHO] = p0.rho; par[FP_UX] = p0.ux; par[FP_UY] = p0.uy; par[FP_LAM] = p0.lam;
+  par[FP_QX] = q0x; par[FP_QY] = q0y;
+  for (int m = 0; m < 4; ++m) { par[FP_AX + m] = ax[m]; par[FP_AY + m] = ay[m]; par[FP_AT + m] = At[m]; }
+  for (int m = 0; m < 5; ++m) par[FP_Q1 + m] = qi[m] / dts;
+  par[FP_UFX] = ufx; par[FP_UFY] = ufy;
+  par[FP_PREF] = 4.0 * (1.0 - d.Pr) * p0.lam * p0.lam / (5.0 * p0.rho);
+  double lamw = wall ? 1.0 / (2.0 * d.face_Tw[fid]) : 0.0;
+  par[FP_LAMW] = lamw;
+  par[FP_RHOW] = 0.0;
+  // g-part of the macro flux (all faces) and wall sums, by velocity
+  double gs[4] = {0, 0, 0, 0}, rs[4] = {0, 0, 0, 0}, den = 0.0;
+  double snx = d.Sn[2 * fid], sny = d.Sn[2 * fid + 1], sun = d.SUn[fid];
+  V2<double> zero = {0.0, 0.0};
+  for (int k = lane; k < d.nv; k += 32) {
+    double vx = d.vx[k], vy = d.vy[k], w = d.w[k];
+    double wS = vx * snx + vy * sny - sun;
+    double v2 = 0.5 * (vx * vx + vy * vy);
+    if (!wall || wS > 0.0) {
+      V2<double> I = interface_integral<double>(par, vx, vy, zero, zero, (double)d.Keff,
+                                                (double)d.Kint, d.Pr);
+      double c = w * wS;
+      gs[0] += c * I.h; gs[1] += c * vx * I.h; gs[2] += c * vy * I.h; gs[3] += c * (v2 * I.h + 0.5 * I.b);
+    } else {
+      double cx = vx - ufx, cy = vy - ufy;
+      double Hw = (lamw / M_PI) * exp(-lamw * (cx * cx + cy * cy));
+      double Bw = (double)d.Keff / (2.0 * lamw) * Hw;
+      double c = w * wS;
+      den += c * Hw;
+      rs[0] += c * Hw; rs[1] += c * vx * Hw; rs[2] += c * vy * Hw; rs[3] += c * (v2 * Hw + 0.5 * Bw);
+    }
+  }
+  for (int m = 0; m < 4; ++m) { gs[m] = warp_sum(gs[m]); rs[m] = warp_sum(rs[m]); }
+  den = warp_sum(den);
+  if (lane == 0) {
+    double F[4];
+    for (int m = 0; m < 4; ++m)
+      F[m] = par[FP_Q1] * fs[FS_FF + m] + par[FP_Q2] * fs[FS_WG + m] + gs[m];
+    if (wall) {
+      double rhow = -F[0] / den;
+      par[FP_RHOW] = rhow;
+      for (int m = 0; m < 4; ++m) F[m] += rhow * rs[m];
+    }
+    for (int m = 0; m < 4; ++m) d.fflux[4 * fid + m] = F[m];
+    for (int m = 0; m < NFP; ++m) { P[m] = par[m]; PT[m] = (T)par[m]; }
+    // Gamma from the mean of the two cells' W (boundary: the cell)
+    double Wf[4];
+    for (int m = 0; m < 4; ++m) Wf[m] = (R >= 0) ? 0.5 * (d.W[4 * L + m] + d.W[4 * R + m]) : d.W[4 * L + m];
+    d.gam[fid] = spectral_radius(Wf, nx, ny, d.SUn[fid] / d.S[fid], d.Keff);
+  }
+}
+
+// Per-cell sum of the S-weighted macro fluxes (Eq. macroscopicFlux summed
+// over the faces); with level_n also the extensive level-n macro term
+// TW = Omega^n W^n / dt - F^n / 2 (reading R4).
+__global__ void k_cell_macro(Dev d, int level_n) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.nc) return;
+  double F[4] = {0, 0, 0, 0};
+  for (int s = 0; s < 4; ++s) {
+    int f = d.cell_faces[4 * c + s];
+    double sg = (double)d.cell_sgn[4 * c + s];
+    for (int m = 0; m < 4; ++m) F[m] += sg * d.fflux[4 * f + m];
+  }
+  for (int m = 0; m < 4; ++m) d.Fc[4 * c + m] = F[m];
+  if (level_n)
+    for (int m = 0; m < 4; ++m) d.TW[4 * c + m] = d.vol_old[c] / d.dt * d.W[4 * c + m] - 0.5 * F[m];
+}
+
+// Cell parameter record (prim, q, 1/tau, Shakhov prefactor) from W and q.
+__global__ void k_cell_params(Dev d, const double *Wsrc, double *out) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.nc) return;
+  Prim p = primitive(Wsrc + 4 * c, d.Keff);
+  double *o = out + NCP * c;
+  o[CP_RHO] = p.rho; o[CP_UX] = p.ux; o[CP_UY] = p.uy; o[CP_LAM] = p.lam;
+  o[CP_QX] = d.q[2 * c]; o[CP_QY] = d.q[2 * c + 1];
+  o[CP_ITAU] = 1.0 / collision_time(p.rho, p.lam, d.mu_ref, d.omega);
+  o[CP_PREF] = 0.0;
+}
+
+// ----------------------------------------------------- macro LU-SGS sweep
+__device__ __forceinline__ void euler_flux(const double *W, double nx, double ny, double un,
+                                           int Keff, double F[4]) {
+  Prim p = primitive(W, Keff);
+  double pr = p.rho / (2.0 * p.lam);
+  double vabs = p.ux * nx + p.uy * ny;
+  double vn = vabs - un;
+  F[0] = p.rho * vn;
+  F[1] = W[1] * vn + pr * nx;
+  F[2] = W[2] * vn + pr * ny;
+  F[3] = W[3] * vn + pr * vabs;
+}
+
+// (1/4) S (dF_E,j - Gamma dW_j) across face fid along the outward normal of
+// the cell with orientation sg.
+__device__ __forceinline__ void macro_off(const Dev &d, int fid, double sg, int nb,
+                                          const double *dWn, double out[4]) {
+  double nx = sg * d.nrm[2 * fid], ny = sg * d.nrm[2 * fid + 1];
+  double un = sg * d.SUn[fid] / d.S[fid];
+  double Wa[4], Wb[4], Fa[4], Fb[4];
+  for (int m = 0; m < 4; ++m) { Wb[m] = d.W[4 * nb + m]; Wa[m] = Wb[m] + dWn[m]; }
+  euler_flux(Wa, nx, ny, un, d.Keff, Fa);
+  euler_flux(Wb, nx, ny, un, d.Keff, Fb);
+  double q = 0.25 * d.S[fid], g = d.gam[fid];
+  for (int m = 0; m < 4; ++m) out[m] = q * ((Fa[m] - Fb[m]) - g * dWn[m]);
+}
+
+// LU-SGS of Eq. dualTimeStepping_macro (Sec. 2.2), one CTA per block,
+// thread = row j; diagonals i + j in increasing (forward) then decreasing
+// (backward) order reproduce the lexicographic Gauss-Seidel exactly.
+// Produces W' = W + dW and the predictor cell record.
+__global__ void __launch_bounds__(512) k_macro_sweep(Dev d) {
+  extern __shared__ double sm[];
+  int b = blockIdx.x;
+  const int *bi = d.blk_info + 8 * b;
+  int ni = bi[0], nj = bi[1], per = bi[2];
+  int off = d.cell_off[b];
+  int row = threadIdx.x;
+  int rows = blockDim.x;
+  double *buf0 = sm, *buf1 = sm + 4 * rows;
+  double prev[4] = {0, 0, 0, 0}, first[4] = {0, 0, 0, 0};
+  int nd = ni + nj - 1;
+  double idt = 1.0 / d.dt;
+  int cur = 0;
+  for (int step = 0; step < nd; ++step) {
+    int i = step - row;
+    bool act = row < nj && i >= 0 && i < ni;
+    double val[4] = {0, 0, 0, 0};
+    if (act) {
+      int c = off + row * ni + i;
+      if (d.status[c] == ST_FIELD) {
+        double acc[4];
+        double vol = d.vol_new[c];
+        for (int m = 0; m < 4; ++m)
+          acc[m] = d.TW[4 * c + m] - vol * idt * d.W[4 * c + m] - 0.5 * d.Fc[4 * c + m];
+        double diag = vol * (d.cfl_s / (d.cfl_pseudo * d.dts[c]) + idt);
+        for (int s = 0; s < 4; ++s) {
+          int f = d.cell_faces[4 * c + s];
+          diag += 0.25 * d.S[f] * d.gam[f];
+        }
+        double *prv = cur ? buf0 : buf1;
+        // lower neighbours: i-1 (same row), wrap of i = ni-1 to 0, j-1
+        for (int s = 0; s < 3; ++s) {
+          int f = d.cell_faces[4 * c + s];
+          double sg = (double)d.cell_sgn[4 * c + s];
+          int nb = (sg > 0) ? d.face_R[f] : d.face_L[f];
+          const double *dv = nullptr;
+          if (s == 0 && i > 0) dv = prev;
+          else if (s == 1 && per && i == ni - 1) dv = first;
+          else if (s == 2 && row > 0) dv = prv + 4 * (row - 1);
+          if (!dv || nb < 0 || d.status[nb] != ST_FIELD) continue;
+          double o[4];
+          macro_off(d, f, sg, nb, dv, o);
+          for (int m = 0; m < 4; ++m) acc[m] -= o[m];
+        }
+        for (int m = 0; m < 4; ++m) val[m] = acc[m] / diag;
+        for (int m = 0; m < 4; ++m) d.dW[4 * c + m] = val[m];
+      }
+    }
+    if (act) {
+      for (int m = 0; m < 4; ++m) prev[m] = val[m];
+      if (i == 0) for (int m = 0; m < 4; ++m) first[m] = val[m];
+    }
+    double *dst = cur ? buf1 : buf0;
+    if (row < rows) for (int m = 0; m < 4; ++m) dst[4 * row + m] = val[m];
+    __syncthreads();
+    cur ^= 1;
+  }
+  __syncthreads();
+  for (int m = 0; m < 4; ++m) { prev[m] = 0; first[m] = 0; }
+  for (int m = 0; m < 4; ++m) { buf0[4 * row + m] = 0; buf1[4 * row + m] = 0; }
+  __syncthreads();
+  cur = 0;
+  for (int step = nd - 1; step >= 0; --step) {
+    int i = step - row;
+    bool act = row < nj && i >= 0 && i < ni;
+    double val[4] = {0, 0, 0, 0};
+    if (act) {
+      int c = off + row * ni + i;
+      if (d.status[c] == ST_FIELD) {
+        double vol = d.vol_new[c];
+        double diag = vol * (d.cfl_s / (d.cfl_pseudo * d.dts[c]) + idt);
+        for (int s = 0; s < 4; ++s) {
+          int f = d.cell_faces[4 * c + s];
+          diag += 0.25 * d.S[f] * d.gam[f];
+        }
+        double acc[4] = {0, 0, 0, 0};
+        double *prv = cur ? buf0 : buf1;
+        // upper neighbours: i+1 (same row), wrap of i = 0 to ni-1, j+1
+        for (int s = 0; s < 4; ++s) {
+          if (s == 2) continue;
+          int f = d.cell_faces[4 * c + s];
+          double sg = (double)d.cell_sgn[4 * c + s];
+          int nb = (sg > 0) ? d.face_R[f] : d.face_L[f];
+          const double *dv = nullptr;
+          if (s == 1 && i < ni - 1) dv = prev;
+          else if (s == 0 && per && i == 0) dv = first;
+          else if (s == 3 && row < nj - 1) dv = prv + 4 * (row + 1);
+          if (!dv || nb < 0 || d.status[nb] != ST_FIELD) continue;
+          double o[4];
+          macro_off(d, f, sg, nb, dv, o);
+          for (int m = 0; m < 4; ++m) acc[m] += o[m];
+        }
+        for (int m = 0; m < 4; ++m) val[m] = d.dW[4 * c + m] - acc[m] / diag;
+        for (int m = 0; m < 4; ++m) {
+          d.dW[4 * c + m] = val[m];
+          d.Wp[4 * c + m] = d.W[4 * c + m] + val[m];
+        }
+        Prim p = primitive(d.Wp + 4 * c, d.Keff);
+        double *o = d.cpar + NCP * c;
+        o[CP_RHO] = p.rho; o[CP_UX] = p.ux; o[CP_UY] = p.uy; o[CP_LAM] = p.lam;
+        o[CP_QX] = d.q[2 * c]; o[CP_QY] = d.q[2 * c + 1];
+        o[CP_ITAU] = 1.0 / collision_time(p.rho, p.lam, d.mu_ref, d.omega);
+        o[CP_PREF] = 0.0;
+      } else {
+        for (int m = 0; m < 4; ++m) d.Wp[4 * c + m] = d.W[4 * c + m];
+      }
+    }
+    if (act) {
+      for (int m = 0; m < 4; ++m) prev[m] = val[m];
+      if (i == ni - 1) for (int m = 0; m < 4; ++m) first[m] = val[m];
+    }
+    double *dst = cur ? buf1 : buf0;
+    for (int m = 0; m < 4; ++m) dst[4 * row + m] = val[m];
+    __syncthreads();
+    cur ^= 1;
+  }
+}
+
+// ----------------------------------------------------- micro LU-SGS sweeps
+template <typename T> __device__ __forceinline__ T wS_of(const Dev &d, int f, int k) {
+  return dvx<T>(d, k) * (T)d.Sn[2 * f] + dvy<T>(d, k) * (T)d.Sn[2 * f + 1] - (T)d.SUn[f];
+}
+
+template <typename T> __device__ __forceinline__ T micro_diag(const Dev &d, int c, int k, T itau) {
+  T dg = (T)d.vol_new[c] * ((T)(d.cfl_s / (d.cfl_pseudo * d.dts[c])) + (T)(1.0 / d.dt) + T(0.5) * itau);
+  for (int s = 0; s < 4; ++s) {
+    int f = d.cell_faces[4 * c + s];
+    T wo = (T)d.cell_sgn[4 * c + s] * wS_of<T>(d, f, k);
+    dg += T(0.5) * (wo > T(0) ? wo : T(0));
+  }
+  return dg;
+}
+
+// Forward sweep of the micro LU-SGS (Eq. dualTimeStepping_micro with the
+// upwind flux variation of Sec. 2.2), fused with the flux divergence and the
+// residual r (Steps 3, 5): one CTA per (block, velocity tile), thread =
+// (row j, velocity); diagonal wavefront with one barrier per diagonal.
+// With first_iter it also forms the level-n term T (Steps 1-2).
+template <typename T>
+__global__ void __launch_bounds__(512) k_micro_fwd(Dev d, const int *work, int V, int first_iter) {
+  typedef typename Vec2<T>::type T2;
+  extern __shared__ unsigned char smraw[];
+  T2 *bufA = reinterpret_cast<T2 *>(smraw);
+  T2 *bufB = bufA + blockDim.x;
+  int b = work[2 * blockIdx.x], k0 = work[2 * blockIdx.x + 1];
+  const int *bi = d.blk_info + 8 * b;
+  int ni = bi[0], nj = bi[1], per = bi[2];
+  int off = d.cell_off[b];
+  int row = threadIdx.x / V, v = threadIdx.x % V;
+  int k = k0 + v;
+  bool kval = k < d.nv;
+  T2 prev = {0, 0}, first = {0, 0};
+  int nd = ni + nj - 1;
+  T idt = (T)(1.0 / d.dt);
+  int cur = 0;
+  for (int step = 0; step < nd; ++step) {
+    int i = step - row;
+    bool act = row < nj && i >= 0 && i < ni && kval;
+    T2 val = {0, 0};
+    if (act) {
+      int c = off + row * ni + i;
+      if (d.status[c] == ST_FIELD) {
+        size_t idx = (size_t)c * d.nvp + k;
+        T2 fv = ldf<T>(d.f, idx);
+        V2<T> D = flux_div<T>(d, c, k);
+        const double *cp = d.cpar + NCP * c;
+        T vx = dvx<T>(d, k), vy = dvy<T>(d, k);
+        T itau = (T)cp[CP_ITAU];
+        V2<T> fp = shakhov<T>((T)cp[CP_RHO], (T)cp[CP_UX], (T)cp[CP_UY], (T)cp[CP_LAM],
+                              (T)cp[CP_QX], (T)cp[CP_QY], vx, vy, (T)d.Keff, (T)d.Kint, (T)d.Pr);
+        T vol1 = (T)d.vol_new[c];
+        T2 tn;
+        if (first_iter) {
+          const double *cn = d.cparn + NCP * c;
+          T itn = (T)cn[CP_ITAU];
+          V2<T> fn = shakhov<T>((T)cn[CP_RHO], (T)cn[CP_UX], (T)cn[CP_UY], (T)cn[CP_LAM],
+                                (T)cn[CP_QX], (T)cn[CP_QY], vx, vy, (T)d.Keff, (T)d.Kint, (T)d.Pr);
+          T vol0 = (T)d.vol_old[c];
+          tn.x = vol0 * idt * fv.x + T(0.5) * (vol0 * (fn.h - fv.x) * itn - D.h);
+          tn.y = vol0 * idt * fv.y + T(0.5) * (vol0 * (fn.b - fv.y) * itn - D.b);
+          stf<T>(d.Tn, idx, tn.x, tn.y);
+        } else {
+          tn = ldf<T>(d.Tn, idx);
+        }
+        T ah = tn.x - vol1 * idt * fv.x + T(0.5) * (vol1 * (fp.h - fv.x) * itau - D.h);
+        T ab = tn.y - vol1 * idt * fv.y + T(0.5) * (vol1 * (fp.b - fv.y) * itau - D.b);
+        T dg = micro_diag<T>(d, c, k, itau);
+        T2 *prv = cur ? bufA : bufB;
+        for (int s = 0; s < 3; ++s) {
+          int f = d.cell_faces[4 * c + s];
+          int sg = d.cell_sgn[4 * c + s];
+          int nb = (sg > 0) ? d.face_R[f] : d.face_L[f];
+          T2 dv;
+          if (s == 0 && i > 0) dv = prev;
+          else if (s == 1 && per && i == ni - 1) dv = first;
+          else if (s == 2 && row > 0) dv = prv[threadIdx.x - V];
+          else continue;
+          if (nb < 0 || d.status[nb] != ST_FIELD) continue;
+          T wo = (T)sg * wS_of<T>(d, f, k);
+          T cf = T(0.5) * (wo < T(0) ? wo : T(0));
+          ah -= cf * dv.x;
+          ab -= cf * dv.y;
+        }
+        val.x = ah / dg;
+        val.y = ab / dg;
+        stf<T>(d.dfs, idx, val.x, val.y);
+      }
+    }
+    if (act) {
+      prev = val;
+      if (i == 0) first = val;
+    }
+    T2 *dst = cur ? bufB : bufA;
+    dst[threadIdx.x] = val;
+    __syncthreads();
+    cur ^= 1;
+  }
+}
+
+// Backward sweep and update f^{s+1} = f^s + df (Step 6).
+template <typename T>
+__global__ void __launch_bounds__(512) k_micro_bwd(Dev d, const int *work, int V) {
+  typedef typename Vec2<T>::type T2;
+  extern __shared__ unsigned char smraw[];
+  T2 *bufA = reinterpret_cast<T2 *>(smraw);
+  T2 *bufB = bufA + blockDim.x;
+  int b = work[2 * blockIdx.x], k0 = work[2 * blockIdx.x + 1];
+  const int *bi = d.blk_info + 8 * b;
+  int ni = bi[0], nj = bi[1], per = bi[2];
+  int off = d.cell_off[b];
+  int row = threadIdx.x / V, v = threadIdx.x % V;
+  int k = k0 + v;
+  bool kval = k < d.nv;
+  T2 prev = {0, 0}, first = {0, 0};
+  int nd = ni + nj - 1;
+  int cur = 0;
+  for (int step = nd - 1; step >= 0; --step) {
+    int i = step - row;
+    bool act = row < nj && i >= 0 && i < ni && kval;
+    T2 val = {0, 0};
+    if (act) {
+      int c = off + row * ni + i;
+      if (d.status[c] == ST_FIELD) {
+        size_t idx = (size_t)c * d.nvp + k;
+        T itau = (T)d.cpar[NCP * c + CP_ITAU];
+        T dg = micro_diag<T>(d, c, k, itau);
+        T ah = 0, ab = 0;
+        T2 *prv = cur ? bufA : bufB;
+        for (int s = 0; s < 4; ++s) {
+          if (s == 2) continue;
+          int f = d.cell_faces[4 * c + s];
+          int sg = d.cell_sgn[4 * c + s];
+          int nb = (sg > 0) ? d.face_R[f] : d.face_L[f];
+          T2 dv;
+          if (s == 1 && i < ni - 1) dv = prev;
+          else if (s == 0 && per && i == 0) dv = first;
+          else if (s == 3 && row < nj - 1) dv = prv[threadIdx.x + V];
+          else continue;
+          if (nb < 0 || d.status[nb] != ST_FIELD) continue;
+          T wo = (T)sg * wS_of<T>(d, f, k);
+          T cf = T(0.5) * (wo < T(0) ? wo : T(0));
+          ah += cf * dv.x;
+          ab += cf * dv.y;
+        }
+        T2 ds = ldf<T>(d.dfs, idx);
+        val.x = ds.x - ah / dg;
+        val.y = ds.y - ab / dg;
+        T2 fv = ldf<T>(d.f, idx);
+        stf<T>(d.f, idx, fv.x + val.x, fv.y + val.y);
+      }
+    }
+    if (act) {
+      prev = val;
+      if (i == ni - 1) first = val;
+    }
+    T2 *dst = cur ? bufB : bufA;
+    dst[threadIdx.x] = val;
+    __syncthreads();
+    cur ^= 1;
+  }
+}
+
+// Step 7 (one warp per cell): W^{s+1} = W' + sum V Psi (f^{s+1} - g(W')),
+// heat flux about V' (reading R7); flags non-physical states.
+template <typename T> __global__ void k_moments(Dev d) {
+  int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (c >= d.nc) return;
+  if (d.status[c] != ST_FIELD) return;
+  const double *cp = d.cpar + NCP * c;
+  double rho = cp[CP_RHO], ux = cp[CP_UX], uy = cp[CP_UY], lam = cp[CP_LAM];
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int k = lane; k < d.nv; k += 32) {
+    auto fv = ldf<T>(d.f, (size_t)c * d.nvp + k);
+    double vx = d.vx[k], vy = d.vy[k], w = d.w[k];
+    V2<double> g = maxwellian<double>(rho, ux, uy, lam, vx, vy, (double)d.Keff);
+    double h = (double)fv.x, b = (double)fv.y;
+    double dh = h - g.h, db = b - g.b;
+    double v2 = 0.5 * (vx * vx + vy * vy);
+    acc[0] += w * dh;
+    acc[1] += w * vx * dh;
+    acc[2] += w * vy * dh;
+    acc[3] += w * (v2 * dh + 0.5 * db);
+    double cx = vx - ux, cy = vy - uy;
+    double e = (cx * cx + cy * cy) * h + b;
+    acc[4] += 0.5 * w * cx * e;
+    acc[5] += 0.5 * w * cy * e;
+  }
+  for (int m = 0; m < 6; ++m) acc[m] = warp_sum(acc[m]);
+  if (lane == 0) {
+    double Wn[4];
+    for (int m = 0; m < 4; ++m) Wn[m] = d.Wp[4 * c + m] + acc[m];
+    for (int m = 0; m < 4; ++m) d.W[4 * c + m] = Wn[m];
+    d.q[2 * c] = acc[4];
+    d.q[2 * c + 1] = acc[5];
+    Prim p = primitive(Wn, d.Keff);
+    if (!(p.rho > 0.0) || !(p.lam > 0.0) || !isfinite(p.rho) || !isfinite(p.lam))
+      atomicOr(d.err, EF_NONPHYSICAL);
+  }
+}
+
+// Initial state: f = reduced Maxwellian of the primitive field, W, and q from f.
+template <typename T> __global__ void k_init_state(Dev d, const double *prim) {
+  int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (c >= d.nc) return;
+  double rho = prim[4 * c], ux = prim[4 * c + 1], uy = prim[4 * c + 2], T0 = prim[4 * c + 3];
+  double lam = 1.0 / (2.0 * T0);
+  double qx = 0, qy = 0;
+  for (int k = lane; k < d.nvp; k += 32) {
+    if (k >= d.nv) { stf<T>(d.f, (size_t)c * d.nvp + k, T(0), T(0)); continue; }
+    V2<double> g = maxwellian<double>(rho, ux, uy, lam, d.vx[k], d.vy[k], (double)d.Keff);
+    T h = (T)g.h, b = (T)g.b;
+    stf<T>(d.f, (size_t)c * d.nvp + k, h, b);
+    double cx = d.vx[k] - ux, cy = d.vy[k] - uy;
+    double e = (cx * cx + cy * cy) * (double)h + (double)b;
+    qx += 0.5 * d.w[k] * cx * e;
+    qy += 0.5 * d.w[k] * cy * e;
+  }
+  qx = warp_sum(qx);
+  qy = warp_sum(qy);
+  if (lane == 0) {
+    double W[4];
+    conservative(rho, ux, uy, lam, d.Keff, W);
+    for (int m = 0; m < 4; ++m) d.W[4 * c + m] = W[m];
+    d.q[2 * c] = qx;
+    d.q[2 * c + 1] = qy;
+  }
+}
+
+// Diagnostic: D_ik for every (cell, velocity), written as FP64.
+template <typename T> __global__ void k_flux_div_all(Dev d, double *D) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t n = (size_t)d.nc * d.nv;
+  if (t >= n) return;
+  int c = (int)(t / d.nv), k = (int)(t % d.nv);
+  V2<T> r = {0, 0};
+  if (d.status[c] == ST_FIELD) r = flux_div<T>(d, c, k);
+  D[2 * t] = (double)r.h;
+  D[2 * t + 1] = (double)r.b;
+}
+
+// Sum of S * wall macro flux per block (deterministic order).
+__global__ void k_wall_loads(Dev d) {
+  int b = blockIdx.x;
+  if (threadIdx.x != 0) return;
+  double s[4] = {0, 0, 0, 0};
+  for (int f = 0; f < d.nf; ++f) {
+    if (d.face_block[f] != b || d.face_kind[f] != BC_WALL) continue;
+    for (int m = 0; m < 4; ++m) s[m] += d.fflux[4 * f + m];
+  }
+  for (int m = 0; m < 4; ++m) d.wall_loads[4 * b + m] = s[m];
+}
+
+// Copy f between the storage type and FP64 (get/set state).
+template <typename T> __global__ void k_f_to_double(Dev d, double *out) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t n = (size_t)d.nc * d.nv;
+  if (t >= n) return;
+  int c = (int)(t / d.nv), k = (int)(t % d.nv);
+  auto v = ldf<T>(d.f, (size_t)c * d.nvp + k);
+  out[2 * t] = (double)v.x;
+  out[2 * t + 1] = (double)v.y;
+}
+template <typename T> __global__ void k_f_from_double(Dev d, const double *in) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t n = (size_t)d.nc * d.nv;
+  if (t >= n) return;
+  int c = (int)(t / d.nv), k = (int)(t % d.nv);
+  stf<T>(d.f, (size_t)c * d.nvp + k, (T)in[2 * t], (T)in[2 * t + 1]);
+}
+
+// ------------------------------------------------------- launch wrappers
+static inline int nblk(size_t n, int b) { return (int)((n + b - 1) / b); }
+
+void launch_move_nodes(const Dev &d, cudaStream_t s) { k_move_nodes<<<nblk(d.nn, 256), 256, 0, s>>>(d); }
+void launch_geometry(const Dev &d, cudaStream_t s) {
+  k_cell_geom<<<nblk(d.nc, 256), 256, 0, s>>>(d);
+  k_face_geom<<<nblk(d.nf, 256), 256, 0, s>>>(d);
+  k_dts<<<nblk((size_t)d.nc * 32, 256), 256, 0, s>>>(d);
+}
+void launch_slope_geo(const Dev &d, cudaStream_t s) { k_slope_geo<<<nblk(d.nc, 256), 256, 0, s>>>(d); }
+
+template <typename T> static void flux_prep_t(const Dev &d, cudaStream_t s, int level_n) {
+  k_ghost<<<nblk(d.nf, 256), 256, 0, s>>>(d);
+  k_gradW<<<nblk(d.nc, 256), 256, 0, s>>>(d);
+  k_face_reduce<T><<<nblk((size_t)d.nf * 32, 256), 256, 0, s>>>(d);
+  k_face_coef<T><<<nblk((size_t)d.nf * 32, 256), 256, 0, s>>>(d);
+  k_cell_macro<<<nblk(d.nc, 256), 256, 0, s>>>(d, level_n);
+}
+void launch_flux_prep(const Dev &d, cudaStream_t s, int level_n, int fp32) {
+  if (fp32) flux_prep_t<float>(d, s, level_n); else flux_prep_t<double>(d, s, level_n);
+}
+void launch_cell_params(const Dev &d, cudaStream_t s, const double *W, double *out) {
+  k_cell_params<<<nblk(d.nc, 256), 256, 0, s>>>(d, W, out);
+}
+void launch_macro_sweep(const Dev &d, cudaStream_t s, int rows) {
+  k_macro_sweep<<<d.nblocks, rows, 2 * 4 * rows * sizeof(double), s>>>(d);
+}
+void launch_micro(const Dev &d, cudaStream_t s, const int *work, int nwork, int V, int rows,
+                  int first_iter, int fp32) {
+  int threads = rows * V;
+  if (fp32) {
+    size_t sm = 2 * threads * sizeof(float2);
+    k_micro_fwd<float><<<nwork, threads, sm, s>>>(d, work, V, first_iter);
+    k_micro_bwd<float><<<nwork, threads, sm, s>>>(d, work, V);
+  } else {
+    size_t sm = 2 * threads * sizeof(double2);
+    k_micro_fwd<double><<<nwork, threads, sm, s>>>(d, work, V, first_iter);
+    k_micro_bwd<double><<<nwork, threads, sm, s>>>(d, work, V);
+  }
+}
+void launch_moments(const Dev &d, cudaStream_t s, int fp32) {
+  if (fp32) k_moments<float><<<nblk((size_t)d.nc * 32, 256), 256, 0, s>>>(d);
+  else k_moments<double><<<nblk((size_t)d.nc * 32, 256), 256, 0, s>>>(d);
+}
+void launch_init_state(const Dev &d, cudaStream_t s, const double *prim, int fp32) {
+  if (fp32) k_init_state<float><<<nblk((size_t)d.nc * 32, 256), 256, 0, s>>>(d, prim);
+  else k_init_state<double><<<nblk((size_t)d.nc * 32, 256), 256, 0, s>>>(d, prim);
+}
+void launch_flux_div_all(const Dev &d, cudaStream_t s, double *D, int fp32) {
+  size_t n = (size_t)d.nc * d.nv;
+  if (fp32) k_flux_div_all<float><<<nblk(n, 256), 256, 0, s>>>(d, D);
+  else k_flux_div_all<double><<<nblk(n, 256), 256, 0, s>>>(d, D);
+}
+void launch_wall_loads(const Dev &d, cudaStream_t s) { k_wall_loads<<<d.nblocks, 32, 0, s>>>(d); }
+void launch_f_convert(const Dev &d, cudaStream_t s, double *out, const double *in, int fp32) {
+  size_t n = (size_t)d.nc * d.nv;
+  if (out) {
+    if (fp32) k_f_to_double<float><<<nblk(n, 256), 256, 0, s>>>(d, out);
+    else k_f_to_double<double><<<nblk(n, 256), 256, 0, s>>>(d, out);
+  } else {
+    if (fp32) k_f_from_double<float><<<nblk(n, 256), 256, 0, s>>>(d, in);
+    else k_f_from_double<double><<<nblk(n, 256), 256, 0, s>>>(d, in);
+  }
+}
+
+}  // namespace ugks

@@ -1,0 +1,278 @@
+// ugks_overset.cu -- overset assembly (arXiv 2604.09984 Sec. 3.1) and
+// inverse-distance interpolation (Sec. 3.2) on the device.
+//
+// Every geometric predicate uses explicit round-to-nearest FP64 operations
+// (__dadd_rn, __dmul_rn, ...) so no multiply-add is contracted: the result is
+// bit-identical to a plain FP64 evaluation of the same expressions in the
+// same order.  Readings of the garbled classification sentence of Sec. 3.1:
+//   * wall distance of a node to a zone: min squared distance to the zone's
+//     wall segments (+inf without walls);
+//   * a node of zone Z is inactive if it lies inside another zone's body
+//     polygon, or inside a core cell (not within n_fringe + n_gap layers of an
+//     overset edge) of a zone D with a smaller wall distance (ties: higher
+//     priority wins);
+//   * cells: all nodes inactive -> hole, mixed -> boundary, fringe layers ->
+//     receptor; active face neighbours of boundary or hole cells form the
+//     buffer layer (receptors); the rest are field cells;
+//   * donor: the containing cell of another zone, field cells before
+//     receptor cells, then (priority desc, block, cell index); stencil =
+//     donor + its non-hole face neighbours (order i-1, i+1, j-1, j+1),
+//     weights d^-2 normalised in that order (Sec. 3.2).
+#include "ugks_internal.cuh"
+#include "ugks_launch.h"
+
+namespace ugks {
+
+enum { CL_ACTIVE = 0, CL_MIXED = 1, CL_HOLE = 2, CL_FRINGE = 3 };
+
+__device__ __forceinline__ double ad(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sb(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double ml(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dv(double a, double b) { return __ddiv_rn(a, b); }
+
+__device__ double wall_dist2(const Dev &d, int blk, double x, double y) {
+  double best = __longlong_as_double(0x7ff0000000000000LL);   // +inf
+  int s0 = d.wall_seg_off[blk], s1 = d.wall_seg_off[blk + 1];
+  for (int s = s0; s < s1; ++s) {
+    int a = d.wall_seg[2 * s], b = d.wall_seg[2 * s + 1];
+    double ax = d.X_new[2 * a], ay = d.X_new[2 * a + 1];
+    double ex = sb(d.X_new[2 * b], ax), ey = sb(d.X_new[2 * b + 1], ay);
+    double px = sb(x, ax), py = sb(y, ay);
+    double t = dv(ad(ml(px, ex), ml(py, ey)), ad(ml(ex, ex), ml(ey, ey)));
+    t = fmin(fmax(t, 0.0), 1.0);
+    double dx = sb(px, ml(t, ex)), dy = sb(py, ml(t, ey));
+    double d2 = ad(ml(dx, dx), ml(dy, dy));
+    best = fmin(best, d2);
+  }
+  return best;
+}
+
+__device__ bool inside_quad(const Dev &d, int c, double x, double y) {
+  const int *nd = d.cell_nodes + 4 * c;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    int a = nd[e], b = nd[(e + 1) & 3];
+    double ax = d.X_new[2 * a], ay = d.X_new[2 * a + 1];
+    double bx = d.X_new[2 * b], by = d.X_new[2 * b + 1];
+    double cr = sb(ml(sb(bx, ax), sb(y, ay)), ml(sb(by, ay), sb(x, ax)));
+    if (!(cr >= 0.0)) return false;
+  }
+  return true;
+}
+
+__device__ bool inside_body(const Dev &d, int blk, double x, double y) {
+  int r0 = d.body_ring_off[blk], r1 = d.body_ring_off[blk + 1];
+  int M = r1 - r0;
+  bool in = false;
+  for (int i = 0; i < M; ++i) {
+    int a = d.body_ring[r0 + i], b = d.body_ring[r0 + (i + 1) % M];
+    double ax = d.X_new[2 * a], ay = d.X_new[2 * a + 1];
+    double bx = d.X_new[2 * b], by = d.X_new[2 * b + 1];
+    bool crosses = (ay > y) != (by > y);
+    if (crosses) {
+      double xint = ad(ax, dv(ml(sb(y, ay), sb(bx, ax)), sb(by, ay)));
+      if (x < xint) in = !in;
+    }
+  }
+  return in;
+}
+
+__device__ __forceinline__ bool in_layer(const int *bi, int i, int j, int L) {
+  int ni = bi[0], nj = bi[1], mask = bi[6];
+  if ((mask & 1) && i < L) return true;
+  if ((mask & 2) && i >= ni - L) return true;
+  if ((mask & 4) && j < L) return true;
+  if ((mask & 8) && j >= nj - L) return true;
+  return false;
+}
+
+// node classification (one thread per node)
+__global__ void k_node_classify(Dev d) {
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= d.nn) return;
+  int z = d.node_block[n];
+  double x = d.X_new[2 * n], y = d.X_new[2 * n + 1];
+  double dz = wall_dist2(d, z, x, y);
+  bool inact = false;
+  for (int b = 0; b < d.nblocks && !inact; ++b) {
+    if (b == z) continue;
+    if (d.body_ring_off[b + 1] > d.body_ring_off[b] && inside_body(d, b, x, y)) {
+      inact = true;
+      break;
+    }
+    const int *bi = d.blk_info + 8 * b;
+    int ni = bi[0], nj = bi[1], L = bi[4] + bi[5];
+    int c0 = d.cell_off[b];
+    bool hit = false;
+    for (int j = 0; j < nj && !hit; ++j)
+      for (int i = 0; i < ni; ++i) {
+        if (in_layer(bi, i, j, L)) continue;
+        if (inside_quad(d, c0 + j * ni + i, x, y)) { hit = true; break; }
+      }
+    if (hit) {
+      double db = wall_dist2(d, b, x, y);
+      const int *bz = d.blk_info + 8 * z;
+      if (db < dz || (db == dz && bi[3] > bz[3])) inact = true;
+    }
+  }
+  d.node_active[n] = inact ? 0 : 1;
+}
+
+__global__ void k_cell_classify(Dev d) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.nc) return;
+  const int *nd = d.cell_nodes + 4 * c;
+  int na = d.node_active[nd[0]] + d.node_active[nd[1]] + d.node_active[nd[2]] + d.node_active[nd[3]];
+  int b = d.cell_block[c];
+  const int *bi = d.blk_info + 8 * b;
+  int loc = c - d.cell_off[b];
+  int i = loc % bi[0], j = loc / bi[0];
+  int cl;
+  if (na == 0) cl = CL_HOLE;
+  else if (na < 4) cl = CL_MIXED;
+  else if (in_layer(bi, i, j, bi[4])) cl = CL_FRINGE;
+  else cl = CL_ACTIVE;
+  d.cls[c] = cl;
+}
+
+// status from the classes; buffer layer; fresh cells (hole -> field) flagged
+// with bit 8 of prev_status scratch
+__global__ void k_cell_buffer(Dev d, int *prev_status) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.nc) return;
+  int cl = d.cls[c];
+  int st;
+  if (cl == CL_HOLE) st = ST_HOLE;
+  else if (cl == CL_MIXED || cl == CL_FRINGE) st = ST_RECEPTOR;
+  else {
+    st = ST_FIELD;
+    for (int s = 0; s < 4; ++s) {
+      if (d.nb_kind[4 * c + s] != NB_CELL) continue;
+      int nc2 = d.cls[d.nb_id[4 * c + s]];
+      if (nc2 == CL_MIXED || nc2 == CL_HOLE) st = ST_RECEPTOR;
+    }
+  }
+  int prev = prev_status[c];
+  prev_status[c] = (prev == ST_HOLE && st == ST_FIELD) ? 1 : 0;   // fresh flag
+  d.status[c] = st;
+}
+
+// donor search and IDW weights for receptor / fresh cells
+__global__ void k_donor(Dev d, const int *fresh_flag, const int *blk_order, int *n_orphan) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.nc) return;
+  int st = d.status[c];
+  for (int m = 0; m < 5; ++m) { d.donors[5 * c + m] = -1; d.dwgt[5 * c + m] = 0.0; }
+  if (st != ST_RECEPTOR && !fresh_flag[c]) return;
+  double x = d.xc_new[2 * c], y = d.xc_new[2 * c + 1];
+  int own = d.cell_block[c];
+  int found = -1;
+  for (int cls = ST_FIELD; cls <= ST_RECEPTOR && found < 0; ++cls) {
+    for (int o = 0; o < d.nblocks && found < 0; ++o) {
+      int b = blk_order[o];
+      if (b == own) continue;
+      int c0 = d.cell_off[b], c1 = d.cell_off[b + 1];
+      for (int e = c0; e < c1; ++e) {
+        if (d.status[e] != cls) continue;
+        if (inside_quad(d, e, x, y)) { found = e; break; }
+      }
+    }
+  }
+  if (found < 0) {
+    atomicAdd(n_orphan, 1);
+    return;
+  }
+  int stn[5];
+  int ns = 0;
+  stn[ns++] = found;
+  for (int s = 0; s < 4; ++s) {
+    if (d.nb_kind[4 * found + s] != NB_CELL) continue;
+    int e = d.nb_id[4 * found + s];
+    if (d.status[e] != ST_HOLE) stn[ns++] = e;
+  }
+  double d2[5];
+  int zero = -1;
+  for (int m = 0; m < ns; ++m) {
+    double ex = sb(x, d.xc_new[2 * stn[m]]), ey = sb(y, d.xc_new[2 * stn[m] + 1]);
+    d2[m] = ad(ml(ex, ex), ml(ey, ey));
+    if (d2[m] == 0.0 && zero < 0) zero = m;
+  }
+  for (int m = 0; m < ns; ++m) d.donors[5 * c + m] = stn[m];
+  if (zero >= 0) {
+    d.dwgt[5 * c + zero] = 1.0;
+    return;
+  }
+  double inv[5], tot = 0.0;
+  for (int m = 0; m < ns; ++m) inv[m] = dv(1.0, d2[m]);
+  for (int m = 0; m < ns; ++m) tot = ad(tot, inv[m]);
+  for (int m = 0; m < ns; ++m) d.dwgt[5 * c + m] = dv(inv[m], tot);
+}
+
+// Jacobi interpolation: gather into staging, then scatter.
+template <typename T> __global__ void k_interp_gather(Dev d, const int *list, int n) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)n * d.nvp) return;
+  int r = (int)(t / d.nvp), k = (int)(t % d.nvp);
+  int c = list[r];
+  double ah = 0.0, ab = 0.0;
+  for (int m = 0; m < 5; ++m) {
+    int e = d.donors[5 * c + m];
+    if (e < 0) continue;
+    double w = d.dwgt[5 * c + m];
+    auto v = ldf<T>(d.f, (size_t)e * d.nvp + k);
+    ah = ah + w * (double)v.x;
+    ab = ab + w * (double)v.y;
+  }
+  stf<T>(d.itmp, t, (T)ah, (T)ab);
+  if (k == 0) {
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int m = 0; m < 5; ++m) {
+      int e = d.donors[5 * c + m];
+      if (e < 0) continue;
+      double w = d.dwgt[5 * c + m];
+      for (int q = 0; q < 4; ++q) acc[q] = acc[q] + w * d.W[4 * e + q];
+      acc[4] = acc[4] + w * d.q[2 * e];
+      acc[5] = acc[5] + w * d.q[2 * e + 1];
+    }
+    for (int q = 0; q < 6; ++q) d.itmpW[6 * r + q] = acc[q];
+  }
+}
+
+template <typename T> __global__ void k_interp_scatter(Dev d, const int *list, int n) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)n * d.nvp) return;
+  int r = (int)(t / d.nvp), k = (int)(t % d.nvp);
+  int c = list[r];
+  if (d.donors[5 * c] < 0) return;            // orphan: keep its values
+  auto v = ldf<T>(d.itmp, t);
+  stf<T>(d.f, (size_t)c * d.nvp + k, v.x, v.y);
+  if (k == 0) {
+    for (int q = 0; q < 4; ++q) d.W[4 * c + q] = d.itmpW[6 * r + q];
+    d.q[2 * c] = d.itmpW[6 * r + 4];
+    d.q[2 * c + 1] = d.itmpW[6 * r + 5];
+  }
+}
+
+static inline int nblk(size_t n, int b) { return (int)((n + b - 1) / b); }
+
+void launch_connect(const Dev &d, cudaStream_t s, int *prev_status, const int *blk_order,
+                    int *n_orphan) {
+  k_node_classify<<<nblk(d.nn, 128), 128, 0, s>>>(d);
+  k_cell_classify<<<nblk(d.nc, 256), 256, 0, s>>>(d);
+  k_cell_buffer<<<nblk(d.nc, 256), 256, 0, s>>>(d, prev_status);
+  k_donor<<<nblk(d.nc, 128), 128, 0, s>>>(d, prev_status, blk_order, n_orphan);
+}
+
+void launch_interp(const Dev &d, cudaStream_t s, const int *list, int n, int fp32) {
+  if (n <= 0) return;
+  size_t tot = (size_t)n * d.nvp;
+  if (fp32) {
+    k_interp_gather<float><<<nblk(tot, 256), 256, 0, s>>>(d, list, n);
+    k_interp_scatter<float><<<nblk(tot, 256), 256, 0, s>>>(d, list, n);
+  } else {
+    k_interp_gather<double><<<nblk(tot, 256), 256, 0, s>>>(d, list, n);
+    k_interp_scatter<double><<<nblk(tot, 256), 256, 0, s>>>(d, list, n);
+  }
+}
+
+}  // namespace ugks

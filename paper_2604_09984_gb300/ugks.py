@@ -1,0 +1,270 @@
+"""ctypes binding of libugks (C ABI in include/ugks.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA
+library.  The library must be built (``__graft_entry__.build()`` or
+``python -m paper_2604_09984_gb300.build_lib``); loading fails loudly when it
+is missing -- there is no fallback path.  PyTorch provides the device
+workspace and the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_int32, c_int64, c_size_t, c_void_p
+
+import numpy as np
+
+from . import workloads as wl
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libugks.so")
+
+OK = 0
+ERR = {-1: "UGKS_ERR_ARG", -2: "UGKS_ERR_CUDA", -3: "UGKS_ERR_GEOMETRY", -4: "UGKS_ERR_ORPHAN",
+       -5: "UGKS_ERR_NONPHYSICAL", -6: "UGKS_ERR_WORKSPACE", -7: "UGKS_ERR_ORDER"}
+FP64, FP32 = 0, 1
+FIELD, RECEPTOR, HOLE = 0, 1, 2
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("precision", c_int), ("nvx", c_int), ("nvy", c_int),
+                ("vx_min", c_double), ("vx_max", c_double), ("vy_min", c_double), ("vy_max", c_double),
+                ("K", c_int), ("Pr", c_double), ("omega", c_double), ("mu_ref", c_double),
+                ("cfl_s", c_double), ("cfl_pseudo", c_double), ("farfield", c_double * 4)]
+
+
+class BlockDesc(ctypes.Structure):
+    _fields_ = [("ni", c_int), ("nj", c_int), ("periodic_i", c_int), ("bc", c_int * 4),
+                ("wall_T", c_double * 4), ("priority", c_int), ("n_fringe", c_int),
+                ("n_gap", c_int), ("x_ref", POINTER(c_double))]
+
+
+class ConnectStats(ctypes.Structure):
+    _fields_ = [("n_field", c_int), ("n_receptor", c_int), ("n_hole", c_int),
+                ("n_fresh", c_int), ("n_orphan", c_int)]
+
+
+SYMBOLS = {
+    "ugks_workspace_query": (c_int, [POINTER(Params), c_int, POINTER(BlockDesc), POINTER(c_size_t)]),
+    "ugks_create": (c_int, [POINTER(Params), c_void_p, c_size_t, c_void_p, POINTER(c_void_p)]),
+    "ugks_destroy": (c_int, [c_void_p]),
+    "ugks_last_error": (ctypes.c_char_p, [c_void_p]),
+    "ugks_init_mesh": (c_int, [c_void_p, c_int, POINTER(BlockDesc), POINTER(c_double)]),
+    "ugks_move_mesh": (c_int, [c_void_p, c_double, POINTER(c_double)]),
+    "ugks_overset_connect": (c_int, [c_void_p, POINTER(ConnectStats)]),
+    "ugks_step": (c_int, [c_void_p, c_double, c_int]),
+    "ugks_moments": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ugks_sizes": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
+    "ugks_get_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ugks_set_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ugks_eval_flux": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "ugks_get_connectivity": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ugks_get_geometry": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ugks_launch_count": (c_int64, [c_void_p]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libugks.so and declare its symbols; raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libugks.so not built (%s): run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SYMBOLS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class UgksError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERR.get(code, "?"), code, msg))
+        self.code = code
+
+
+def make_params(case: wl.Case, precision: int) -> Params:
+    p = Params()
+    p.precision = precision
+    p.nvx, p.nvy = case.nvx, case.nvy
+    p.vx_min, p.vx_max, p.vy_min, p.vy_max = case.vbox
+    p.K, p.Pr, p.omega, p.mu_ref = case.K, case.Pr, case.omega, case.mu_ref
+    p.cfl_s, p.cfl_pseudo = case.cfl_s, case.cfl_pseudo
+    for i in range(4):
+        p.farfield[i] = case.farfield[i]
+    return p
+
+
+def make_blocks(case: wl.Case):
+    """Block descriptors plus the node arrays they point to (keep both)."""
+    arrs = []
+    descs = (BlockDesc * len(case.blocks))()
+    for i, b in enumerate(case.blocks):
+        xr = np.ascontiguousarray(b.x_ref.transpose(1, 0, 2), dtype=np.float64)
+        arrs.append(xr)
+        d = descs[i]
+        d.ni, d.nj, d.periodic_i = b.ni, b.nj, int(b.periodic_i)
+        for s in range(4):
+            d.bc[s] = int(b.bc[s])
+            d.wall_T[s] = float(b.wall_T[s])
+        d.priority, d.n_fringe, d.n_gap = b.priority, b.n_fringe, b.n_gap
+        d.x_ref = xr.ctypes.data_as(POINTER(c_double))
+    return descs, arrs
+
+
+def workspace_bytes(case: wl.Case, precision: int) -> int:
+    lib = load()
+    p = make_params(case, precision)
+    descs, _keep = make_blocks(case)
+    n = c_size_t(0)
+    r = lib.ugks_workspace_query(ctypes.byref(p), len(case.blocks), descs, ctypes.byref(n))
+    if r != OK:
+        raise UgksError(r, "workspace query")
+    return int(n.value)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return c_void_p(t.ctypes.data)
+    return c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One libugks context for a workload: owns the device workspace (a torch
+    uint8 tensor) and runs on the current torch CUDA stream."""
+
+    def __init__(self, case: wl.Case, precision: int = FP64, device="cuda", stream=None, prim=None):
+        import torch
+        self.torch = torch
+        self.lib = load()
+        self.case = case
+        self.precision = precision
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._p = make_params(case, precision)
+        self._descs, self._keep = make_blocks(case)
+        nbytes = c_size_t(0)
+        self._check(self.lib.ugks_workspace_query(ctypes.byref(self._p), len(case.blocks),
+                                                  self._descs, ctypes.byref(nbytes)), None)
+        self.ws = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
+        ctx = c_void_p()
+        self._check(self.lib.ugks_create(ctypes.byref(self._p), c_void_p(self.ws.data_ptr()),
+                                         nbytes.value, c_void_p(self.stream.cuda_stream),
+                                         ctypes.byref(ctx)), None)
+        self.ctx = ctx
+        prim = np.ascontiguousarray(case.init_prim if prim is None else prim, dtype=np.float64)
+        self._check(self.lib.ugks_init_mesh(self.ctx, len(case.blocks), self._descs,
+                                            prim.ctypes.data_as(POINTER(c_double))))
+        nc, nf, nv, nvp = c_int(), c_int(), c_int(), c_int()
+        self._check(self.lib.ugks_sizes(self.ctx, ctypes.byref(nc), ctypes.byref(nf),
+                                        ctypes.byref(nv), ctypes.byref(nvp)))
+        self.nc, self.nf, self.nv, self.nvp = nc.value, nf.value, nv.value, nvp.value
+        self.t = 0.0
+        self.last_stats = None
+
+    # -------------------------------------------------------------- errors
+    def _check(self, r, ctx="self"):
+        if r != OK:
+            c = self.ctx if ctx == "self" else None
+            msg = self.lib.ugks_last_error(c).decode() if c is not None else ""
+            raise UgksError(r, msg)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.ugks_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------- the ABI
+    def move_mesh(self, t_new, affine=None):
+        a = np.ascontiguousarray(self.case.motion(t_new) if affine is None else affine, dtype=np.float64)
+        self._check(self.lib.ugks_move_mesh(self.ctx, float(t_new), a.ctypes.data_as(POINTER(c_double))))
+        self._t_new = t_new
+
+    def overset_connect(self):
+        st = ConnectStats()
+        self._check(self.lib.ugks_overset_connect(self.ctx, ctypes.byref(st)))
+        self.last_stats = dict(n_field=st.n_field, n_receptor=st.n_receptor, n_hole=st.n_hole,
+                               n_fresh=st.n_fresh, n_orphan=st.n_orphan)
+        return self.last_stats
+
+    def step(self, dt=None, n_inner=None):
+        dt = self._t_new - self.t if dt is None else dt
+        n_inner = self.case.n_inner if n_inner is None else n_inner
+        self._check(self.lib.ugks_step(self.ctx, float(dt), int(n_inner)))
+        self.t = self._t_new
+
+    def advance(self, n_inner=None, dt=None):
+        """One physical step of the outer loop (Sec. 3): motion, assembly, evolve."""
+        dt = self.case.dt if dt is None else dt
+        self.move_mesh(self.t + dt)
+        self.overset_connect()
+        self.step(dt, n_inner)
+
+    def moments(self, W=None, q=None, status=None, wall=None):
+        """Copy W, q, status and wall loads into the given buffers (numpy or
+        torch, host or device); allocates host numpy arrays when omitted."""
+        if W is None:
+            W = np.empty((self.nc, 4))
+        if q is None:
+            q = np.empty((self.nc, 2))
+        if status is None:
+            status = np.empty(self.nc, dtype=np.int32)
+        if wall is None:
+            wall = np.empty((len(self.case.blocks), 4))
+        self._check(self.lib.ugks_moments(self.ctx, _ptr(W), _ptr(q), _ptr(status), _ptr(wall)))
+        return W, q, status, wall
+
+    def get_state(self):
+        torch = self.torch
+        f = torch.empty((self.nc, self.nv, 2), dtype=torch.float64, device=self.device)
+        W = np.empty((self.nc, 4))
+        q = np.empty((self.nc, 2))
+        self._check(self.lib.ugks_get_state(self.ctx, _ptr(f), _ptr(W), _ptr(q)))
+        return f, W, q
+
+    def set_state(self, f=None, W=None, q=None):
+        torch = self.torch
+        ft = None
+        if f is not None:
+            ft = torch.as_tensor(np.asarray(f, dtype=np.float64) if not isinstance(f, torch.Tensor) else f,
+                                 dtype=torch.float64).to(self.device).contiguous()
+        Wn = None if W is None else np.ascontiguousarray(W, dtype=np.float64)
+        qn = None if q is None else np.ascontiguousarray(q, dtype=np.float64)
+        self._check(self.lib.ugks_set_state(self.ctx, _ptr(ft), _ptr(Wn), _ptr(qn)))
+
+    def eval_flux(self):
+        torch = self.torch
+        D = torch.empty((self.nc, self.nv, 2), dtype=torch.float64, device=self.device)
+        F = np.empty((self.nc, 4))
+        self._check(self.lib.ugks_eval_flux(self.ctx, _ptr(D), _ptr(F)))
+        return D, F
+
+    def connectivity(self):
+        st = np.empty(self.nc, dtype=np.int32)
+        dn = np.empty((self.nc, 5), dtype=np.int32)
+        w = np.empty((self.nc, 5))
+        self._check(self.lib.ugks_get_connectivity(self.ctx, _ptr(st), _ptr(dn), _ptr(w)))
+        return st, dn, w
+
+    def geometry(self):
+        out = dict(vol_old=np.empty(self.nc), vol_new=np.empty(self.nc), xc=np.empty((self.nc, 2)),
+                   dts=np.empty(self.nc), Sn=np.empty((self.nf, 2)), SUn=np.empty(self.nf))
+        self._check(self.lib.ugks_get_geometry(self.ctx, *(_ptr(out[k]) for k in
+                                                          ("vol_old", "vol_new", "xc", "dts", "Sn", "SUn"))))
+        return out
+
+    def launch_count(self):
+        return int(self.lib.ugks_launch_count(self.ctx))

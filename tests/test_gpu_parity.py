@@ -1,0 +1,185 @@
+"""GPU parity of libugks (through the C ABI) against the FP64 oracle on
+small seeded cases that span several velocity tiles and a ragged tail.
+
+Tolerances: FP64 path 1e-11 relative (max-norm) after several steps; FP32
+mixed path 1e-5 relative on the macroscopic fields; overset connectivity
+bit-exact."""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+from oracle import kinetic as kn  # noqa: E402
+from oracle import mesh, overset  # noqa: E402
+from oracle import ugks as ou  # noqa: E402
+from oracle.run import Run  # noqa: E402
+from paper_2604_09984_gb300 import ugks as U  # noqa: E402
+from paper_2604_09984_gb300 import workloads as wl  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    if not os.path.exists(U.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    U.load()
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def perturbed_state(run, seed, amp=0.05):
+    """Non-equilibrium f (Maxwellians times seeded noise), W and q from f."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    st = run.state
+    st.f = st.f * (1.0 + rng.uniform(-amp, amp, st.f.shape))
+    st.W = kn.moments(st.f, run.dvs)
+    rho, Vx, Vy, lam = kn.primitive(st.W, run.gas)
+    st.q = kn.heat_flux(st.f, Vx, Vy, run.dvs)
+    return st
+
+
+def small_channel(**kw):
+    args = dict(ni=12, nj=7, nv=10, n_inner=3, n_steps=3)
+    args.update(kw)
+    return wl.channel(**args)
+
+
+def small_mems(**kw):
+    args = dict(nbi=48, nbj=24, noi=32, noj=12, nv=8, stretch=1.15, n_inner=2)
+    args.update(kw)
+    return wl.mems(**args)
+
+
+@pytest.mark.parametrize("which", ["channel", "mems"])
+def test_geometry_matches_oracle(which):
+    case = small_channel() if which == "channel" else small_mems()
+    s = U.Solver(case, U.FP64)
+    s.move_mesh(case.dt)
+    g = s.geometry()
+    topo = mesh.Topology(case.blocks)
+    ref = mesh.geometry(topo, case.nodes_at(0.0), case.nodes_at(case.dt), case.dt)
+    assert rel(g["vol_old"], ref.vol_old) < 1e-14
+    assert rel(g["vol_new"], ref.vol_new) < 1e-14
+    assert rel(g["xc"], ref.xc) < 1e-14
+    assert rel(g["Sn"], ref.Sn) < 1e-14
+    assert np.abs(g["SUn"] - ref.SUn).max() < 1e-14 * np.abs(ref.Sn).max() * max(np.abs(ref.Uf).max(), 1.0)
+    r = Run(case)
+    wS = ou.normal_velocity(r.setup, ref)
+    dts = ou.explicit_dt(r.setup, ref, wS)
+    assert rel(g["dts"], dts) < 1e-13
+
+
+@pytest.mark.parametrize("prec,tol", [(U.FP64, 1e-12), (U.FP32, 2e-5)])
+def test_flux_random_state(prec, tol):
+    """Eqs. microscopicFlux / macroscopicFlux on a random non-equilibrium
+    state with a moving wall and a periodic seam."""
+    case = small_channel()
+    prim = wl.random_prim(case, 3, amp_rho=0.2, amp_u=0.3, amp_T=0.2)
+    r = Run(case, prim)
+    st = perturbed_state(r, 4)
+    s = U.Solver(case, prec, prim=prim)
+    s.set_state(st.f, st.W, st.q)
+    s.move_mesh(case.dt)
+    D, F = s.eval_flux()
+    geo = r.geometry(0.0, case.dt)
+    wS = ou.normal_velocity(r.setup, geo)
+    dts = ou.explicit_dt(r.setup, geo, wS)
+    fl = ou.flux(r.setup, geo, st, r.status, dts, wS)
+    assert rel(D.cpu().numpy(), fl.D) < tol
+    assert rel(F, fl.F) < tol
+
+
+def test_step_fp64_channel():
+    """Several implicit steps (Sec. 2.2 Steps 1-8) on the deforming channel:
+    f, W and q agree with the oracle."""
+    case = small_channel()
+    prim = wl.random_prim(case, 5, amp_rho=0.1, amp_u=0.1, amp_T=0.1)
+    s = U.Solver(case, U.FP64, prim=prim)
+    r = Run(case, prim)
+    for _ in range(case.n_steps):
+        s.advance()
+        r.step()
+    f, W, q = s.get_state()
+    assert rel(W, r.state.W) < 1e-11
+    assert rel(q, r.state.q) < 1e-9 * max(1.0, 1.0)
+    assert rel(f.cpu().numpy(), r.state.f) < 1e-11
+
+
+def test_step_fp32_channel_macro_tolerance():
+    """Mixed precision: macroscopic fields within 1e-5 relative of FP64."""
+    case = small_channel()
+    prim = wl.random_prim(case, 5, amp_rho=0.1, amp_u=0.1, amp_T=0.1)
+    s = U.Solver(case, U.FP32, prim=prim)
+    r = Run(case, prim)
+    for _ in range(case.n_steps):
+        s.advance()
+        r.step()
+    W, q, st, wall = s.moments()
+    assert rel(W, r.state.W) < 1e-5
+
+
+@pytest.mark.parametrize("nv,ni,nj", [(7, 5, 3), (13, 9, 4), (6, 2, 3)])
+def test_step_ragged_sizes(nv, ni, nj):
+    """Velocity counts that leave a ragged last tile and a padded stride,
+    minimal periodic width (ni = 2 makes both i-faces join the same pair)."""
+    case = wl.channel(ni=ni, nj=nj, nv=nv, n_inner=2)
+    prim = wl.random_prim(case, 11)
+    s = U.Solver(case, U.FP64, prim=prim)
+    r = Run(case, prim)
+    for _ in range(2):
+        s.advance()
+        r.step()
+    _, W, _ = s.get_state()
+    assert rel(W, r.state.W) < 1e-11
+
+
+def test_overset_connectivity_bit_exact():
+    """Sec. 3.1 assembly: status, donor stencils and IDW weights identical
+    bit for bit to the oracle, at several positions of the plate."""
+    case = small_mems()
+    s = U.Solver(case, U.FP64)
+    topo = mesh.Topology(case.blocks)
+    conn = overset.connect(topo, case.nodes_at(0.0))
+    st, dn, w = s.connectivity()
+    assert np.array_equal(st, conn.status)
+    prev = conn.status
+    t = 0.0
+    for n in range(4):
+        t1 = t + 0.7 / case.meta["freq"] / 4
+        s.move_mesh(t1)
+        stats = s.overset_connect()
+        conn = overset.connect(topo, case.nodes_at(t1), prev)
+        st, dn, w = s.connectivity()
+        assert np.array_equal(st, conn.status)
+        rec = conn.receptors
+        assert np.array_equal(dn[rec], conn.donors)
+        assert np.array_equal(w[rec].view(np.int64), conn.weights.view(np.int64))
+        assert stats["n_fresh"] == conn.fresh.size
+        assert stats["n_orphan"] == conn.n_orphan == 0
+        prev = conn.status
+        s.step(t1 - t, 1)
+        t = t1
+
+
+def test_step_fp64_overset():
+    case = small_mems()
+    prim = wl.random_prim(case, 9, amp_rho=0.05, amp_u=0.05, amp_T=0.05)
+    s = U.Solver(case, U.FP64, prim=prim)
+    r = Run(case, prim)
+    for _ in range(2):
+        s.advance()
+        r.step()
+    _, W, q = s.get_state()
+    field = r.status == 0
+    assert rel(W[field], r.state.W[field]) < 1e-11
+    Wm, qm, stm, wall = s.moments()
+    assert np.array_equal(stm, r.status)

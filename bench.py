@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Benchmark of the implicit moving-mesh UGKS on one GB300 (per rank).
+
+Workload (default): the thermal rarefied MEMS overset case -- Cartesian
+background 256x128 + body-fitted O-grid 128x32 around a heated plate
+(Tw = 1.5) translating sinusoidally, 32x32 velocities on [-6, 6], Kn = 0.1,
+10 inner iterations per physical step.  A timed "step" is one physical step
+of the outer loop: prescribed motion, overset assembly, implicit UGKS step
+(all inner iterations).  Metric: cell-velocity updates per second per
+implicit (inner) iteration = N_field_cells * N_v * n_inner / t_step.
+Inputs resident in HBM; f alone (FP32, 302 MB) exceeds the 129 MB L2, so no
+L2 flush is needed between steps.
+
+--impl reference times the FP64 numpy oracle (the paper publishes no code)
+on the host cores on a bounded sample of the same workload.
+Multi-GPU (torchrun): every rank runs an independent replica (weak scaling,
+no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2604_09984_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "cell·velocity updates/s per implicit step, FP32-mixed vs FP64 plain; %HBM peak"
+UNIT = "cell·vel·iter/s"
+FALLBACK_HBM = 6800.0
+
+
+def make_case(name, kn):
+    if name == "mems":
+        return wl.mems(Kn=kn)
+    if name == "channel":
+        return wl.channel()
+    if name == "tsto":
+        return wl.tsto()
+    raise SystemExit("unknown workload " + name)
+
+
+def workload_label(case):
+    b = case.blocks
+    return "%s: %s cells, %dx%d velocities, Kn=%g, %d inner/step" % (
+        case.name, "+".join("%dx%d" % (x.ni, x.nj) for x in b), case.nvx, case.nvy,
+        case.meta.get("Kn", 0.0), case.n_inner)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", FALLBACK_HBM)), "measured"
+    return FALLBACK_HBM, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler (SM clock, max, throttle reasons) for the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def field_cells(solver):
+    _, _, st, _ = solver.moments()
+    return int((st == 0).sum())
+
+
+def algorithmic_bytes(group, pair_bytes, nfield, nv, nc):
+    """Minimum DRAM bytes of one launch of a kernel group:
+    rhs reads f and the level-n term (or writes it on the first inner
+    iteration) and writes the residual; micro_fwd reads the residual and
+    writes the forward increment in place; micro_bwd reads the increment and
+    f and writes f; face_reduce and moments read f once."""
+    per = {"rhs": 3 * nfield, "micro_fwd": 2 * nfield, "micro_bwd": 3 * nfield,
+           "face_reduce": nc, "moments": nfield, "interp": 0}
+    return per.get(group, 0) * nv * pair_bytes
+
+
+def time_arm(case, precision, steps, warmup, device, profile):
+    import torch
+    from paper_2604_09984_gb300 import ugks as U
+    s = U.Solver(case, precision, device=device)
+    for _ in range(warmup):
+        s.advance()
+    torch.cuda.synchronize()
+    nfield = field_cells(s)
+    if profile:
+        s.profile_read(reset=True)
+        s.profile(True)
+    l0 = s.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(s.stream)
+    for _ in range(steps):
+        s.advance()
+    ev1.record(s.stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = s.launch_count() - l0
+    prof = None
+    if profile:
+        s.profile(False)
+        prof = s.profile_read(reset=True)
+    return s, ms, nfield, launches, prof
+
+
+def e2e_arm(s, steps):
+    """Same metric through the public API with host buffers: per step the
+    motion parameters go host->device, and W, q, status and wall loads come
+    back into pinned host memory."""
+    import torch
+    nb = len(s.case.blocks)
+    W = torch.empty((s.nc, 4), dtype=torch.float64).pin_memory()
+    q = torch.empty((s.nc, 2), dtype=torch.float64).pin_memory()
+    st = torch.empty(s.nc, dtype=torch.int32).pin_memory()
+    wall = torch.empty((nb, 4), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    ev0.record(s.stream)
+    for _ in range(steps):
+        s.advance()
+        s.moments(W, q, st, wall)
+    ev1.record(s.stream)
+    torch.cuda.synchronize()
+    wall_s = time.perf_counter() - t0
+    ms = max(ev0.elapsed_time(ev1), wall_s * 1e3)
+    h2d = 6 * 8 * nb
+    d2h = W.numel() * 8 + q.numel() * 8 + st.numel() * 4 + wall.numel() * 8
+    return ms, h2d, d2h
+
+
+def cpu_sample_case(kn):
+    # same geometry family, physics and velocity grid as the timed workload,
+    # at a background/O-grid resolution the numpy oracle finishes in ~10-30 s
+    return wl.mems(nbi=64, nbj=32, noi=48, noj=12, Kn=kn, stretch=1.15, n_inner=3)
+
+
+def cpu_baseline(kn, steps=1):
+    from oracle.run import Run
+    case = cpu_sample_case(kn)
+    r = Run(case)
+    t0 = time.perf_counter()
+    units = 0
+    for _ in range(steps):
+        r.step()
+        units += int((r.status == 0).sum()) * case.nv * case.n_inner
+    dt = time.perf_counter() - t0
+    return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "FP64 numpy oracle, %d step(s) of %s" % (steps, workload_label(case)),
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    kn = args.kn
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(kn, 1)
+    t0 = time.perf_counter()
+    res = [cpu_baseline(kn, 1) for _ in range(args.steps)]
+    el = time.perf_counter() - t0
+    v = statistics.median([r["value"] for r in res])
+    case = make_case(args.workload, kn)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_label(case),
+                                             "reference": "FP64 numpy oracle on host cores (no published code)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": res[0]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mems", choices=["mems", "channel", "tsto"])
+    ap.add_argument("--kn", type=float, default=0.1)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-plain comparison arm")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if args.impl == "ours":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    import torch
+    from paper_2604_09984_gb300 import ugks as U
+    device = "cuda:%d" % local
+    torch.cuda.set_device(local)
+    case = make_case(args.workload, args.kn)
+    steps = max(1, args.steps)
+    warmup = max(3, args.warmup)
+
+    if dist is not None:
+        dist.barrier()
+    clk = Clocks(local)
+    clk.start()
+    s, ms, nfield, launches, prof = time_arm(case, U.FP32, steps, warmup, device, profile=True)
+    clocks = clk.stop()
+    if dist is not None:
+        t = torch.tensor([ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    units = nfield * case.nv * case.n_inner * steps * world
+    value = units / (ms * 1e-3)
+    # roofline of the dominant kernel group (CUDA events on the launch stream)
+    peak, peak_kind = peaks()
+    groups = {g: v for g, v in prof.items() if v[1] > 0}
+    dom = max(groups, key=lambda g: groups[g][0])
+    dms, dn = groups[dom]
+    pair = 8
+    abytes = algorithmic_bytes(dom, pair, nfield, case.nv, s.nc)
+    if abytes > 0:
+        ach = abytes / (dms / dn * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": None, "peak_kind": peak_kind,
+                "bytes_per_launch": abytes, "ms_per_launch": dms / dn}
+    else:
+        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None,
+                "frac": None, "traffic": None, "ms_per_launch": dms / dn}
+    # per-group table for the streaming kernels
+    breakdown = {}
+    for g, (gms, gn) in groups.items():
+        b = algorithmic_bytes(g, pair, nfield, case.nv, s.nc)
+        breakdown[g] = {"ms_total": round(gms, 3), "launches": gn, "share": round(gms / sum(v[0] for v in groups.values()), 4)}
+        if b:
+            breakdown[g]["GBps"] = round(b / (gms / gn * 1e-3) / 1e9, 1)
+    e2e_ms, h2d, d2h = e2e_arm(s, steps)
+    e2e_val = nfield * case.nv * case.n_inner * steps * world / (e2e_ms * 1e-3)
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    fp64 = None
+    if not args.no_fp64:
+        s64, ms64, nf64, _, _ = time_arm(case, U.FP64, max(1, args.fp64_steps), 3, device, profile=False)
+        v64 = nf64 * case.nv * case.n_inner * max(1, args.fp64_steps) / (ms64 * 1e-3)
+        fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / max(1, args.fp64_steps),
+                "speedup_fp32_over_fp64": value / world / v64}
+        s64.close()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_label(case), "precision": "FP32 f and per-velocity arithmetic, FP64 moments/geometry",
+                   "l2": "inputs larger than L2 (f alone %.0f MB)" % (s_bytes(case) / 1e6),
+                   "field_cells": nfield, "nv": case.nv, "n_inner": case.n_inner,
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "per_physical_step": value / case.n_inner,
+        "clocks": clocks,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "kernels": breakdown,
+        "fp64_plain": fp64,
+    }
+    if rank == 0 and not args.no_cpu and world == 1:
+        line["cpu_baseline"] = cpu_baseline(args.kn)
+    elif rank == 0:
+        line["cpu_baseline"] = None
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def s_bytes(case):
+    return case.ncells * case.nv * 8
+
+
+if __name__ == "__main__":
+    main()

@@ -211,6 +211,31 @@ int ugks_get_geometry(ugks_ctx *ctx, double *vol_old, double *vol_new,
  * (counted on the host at each launch). */
 int64_t ugks_launch_count(const ugks_ctx *ctx);
 
+/* Kernel groups timed by the profiler (CUDA events on the context's stream
+ * around every launch of the group). */
+#define UGKS_PROF_GEOMETRY    0   /* mesh motion, geometry, dt_s, slope geometry */
+#define UGKS_PROF_CONNECT     1   /* overset assembly kernels                    */
+#define UGKS_PROF_INTERP      2   /* receptor / fresh-cell interpolation          */
+#define UGKS_PROF_CELL        3   /* ghost states, W gradients, per-cell records  */
+#define UGKS_PROF_FACE_REDUCE 4   /* per-face velocity reduction (W0, flux parts) */
+#define UGKS_PROF_FACE_COEF   5   /* per-face interface coefficients              */
+#define UGKS_PROF_MACRO_SWEEP 6   /* macro LU-SGS                                 */
+#define UGKS_PROF_MICRO_FWD   7   /* micro LU-SGS forward sweep                   */
+#define UGKS_PROF_MICRO_BWD   8   /* micro backward sweep and update              */
+#define UGKS_PROF_MOMENTS     9   /* step-7 moment fix and heat flux              */
+#define UGKS_PROF_RHS        10   /* flux divergence + micro residual (Steps 3, 5) */
+#define UGKS_NPROF           11
+
+/* Start (on != 0) or stop per-group event timing.  While on, every launch is
+ * bracketed by two cudaEventRecord calls (events are created on demand and
+ * reused; no device memory).  Stopping drains the pending events. */
+int ugks_profile_enable(ugks_ctx *ctx, int on);
+
+/* Synchronise the stream and return, per group, the summed device time in ms
+ * and the number of timed launches since the last reset (HOST arrays of
+ * UGKS_NPROF entries, either may be NULL); reset != 0 clears the totals. */
+int ugks_profile_read(ugks_ctx *ctx, double *ms, int64_t *launches, int reset);
+
 #ifdef __cplusplus
 }
 #endif

@@ -3,6 +3,7 @@
 // of one physical step (arXiv 2604.09984 Sec. 3 Steps 1-3 and Sec. 2.2
 // Steps 1-8).  No device allocation happens here: every device array is a
 // slice of the caller's workspace.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -36,6 +37,15 @@ struct ugks_ctx {
   int64_t launches = 0;
   std::vector<double> h_affine;
   std::vector<int> h_lists;
+  std::vector<double> ref_bbox, h_bin_geo;   // per block reference bbox; bin boxes
+  std::vector<int> h_bin_dim;
+  // per-kernel-group CUDA-event timing (ugks_profile_*)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev;        // pool of events, used in begin/end pairs
+  std::vector<int> ev_group;          // group of each recorded pair
+  size_t ev_used = 0;
+  double prof_ms[UGKS_NPROF] = {0};
+  int64_t prof_n[UGKS_NPROF] = {0};
 };
 
 namespace {
@@ -90,6 +100,8 @@ int validate(const ugks_params *p, int nb, const ugks_block_desc *b, Sizes &s, s
   }
   return UGKS_OK;
 }
+
+size_t bin_capacity(const Sizes &s) { return 16 * (size_t)s.nc + 4096; }
 
 struct Carver {
   char *base;
@@ -151,6 +163,7 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int nwork, int cap_in
   d.xf = c.take<double>(2 * (size_t)s.nf); d.Uf = c.take<double>(2 * (size_t)s.nf);
   d.S = c.take<double>(s.nf); d.SUn = c.take<double>(s.nf);
   d.slope_flags = c.take<int>(s.nc);
+  d.cmask = c.take<int>(s.nc);
   d.jinv = c.take<double>(4 * (size_t)s.nc);
   d.affine = c.take<double>(6 * (size_t)nb);
   d.f = c.take<char>(pair * (size_t)s.nc * s.nvp);
@@ -160,6 +173,7 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int nwork, int cap_in
   d.dfs = c.take<char>(pair * (size_t)s.nc * s.nvp);
   d.TW = c.take<double>(4 * (size_t)s.nc); d.Fc = c.take<double>(4 * (size_t)s.nc);
   d.dW = c.take<double>(4 * (size_t)s.nc); d.Wp = c.take<double>(4 * (size_t)s.nc);
+  d.mrec = c.take<char>(tsz * 41 * (size_t)s.nc);
   d.cpar = c.take<double>(NCP * (size_t)s.nc); d.cparn = c.take<double>(NCP * (size_t)s.nc);
   d.gradW = c.take<double>(8 * (size_t)s.nc);
   d.ghostW = c.take<double>(4 * (size_t)s.nf);
@@ -184,6 +198,11 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int nwork, int cap_in
   d.cell_off = c.take<int>(nb + 1);
   d.node_off = c.take<int>(nb + 1);
   d.blk_info = c.take<int>(8 * (size_t)nb);
+  d.bin_geo = c.take<double>(4 * (size_t)nb);
+  d.bin_dim = c.take<int>(3 * (size_t)nb);
+  d.bin_cnt = c.take<int>((size_t)s.nc + nb + 1);
+  d.bin_start = c.take<int>((size_t)s.nc + nb + 2);
+  d.bin_items = c.take<int>(bin_capacity(s));
   d.err = c.take<int>(4);
   (void)nwork;
   c.take<int>(2 * (size_t)nwork + 2);   // micro-sweep work list
@@ -343,17 +362,69 @@ int check_err_flag(ugks_ctx *ctx) {
     CK(cudaMemsetAsync(ctx->d.err, 0, sizeof(int), ctx->st));
     if (h & EF_GEOMETRY) return fail(ctx, UGKS_ERR_GEOMETRY, "non-positive cell volume after mesh move");
     if (h & EF_NONPHYSICAL) return fail(ctx, UGKS_ERR_NONPHYSICAL, "non-finite or non-positive density/temperature");
+    if (h & EF_BINS) return fail(ctx, UGKS_ERR_WORKSPACE, "overset search bins overflowed");
   }
   return UGKS_OK;
 }
 
 int launch_status(ugks_ctx *ctx) { return cuda_check(ctx, cudaPeekAtLastError(), "kernel launch"); }
 
+// Event pair around one launch of a kernel group (only while profiling).
+struct Prof {
+  ugks_ctx *c;
+  size_t slot = (size_t)-1;
+  Prof(ugks_ctx *ctx, int group) : c(ctx) {
+    if (!c->prof_on) return;
+    if (c->ev_used + 2 > c->ev.size()) {
+      for (int i = 0; i < 256; ++i) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        c->ev.push_back(e);
+      }
+      c->ev_group.resize(c->ev.size() / 2);
+    }
+    slot = c->ev_used;
+    c->ev_used += 2;
+    c->ev_group[slot / 2] = group;
+    cudaEventRecord(c->ev[slot], c->st);
+  }
+  ~Prof() {
+    if (slot != (size_t)-1) cudaEventRecord(c->ev[slot + 1], c->st);
+  }
+};
+
+// Drain recorded event pairs into the per-group totals.
+int prof_drain(ugks_ctx *ctx) {
+  if (ctx->ev_used == 0) return UGKS_OK;
+  CK(cudaStreamSynchronize(ctx->st));
+  for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]));
+    int g = ctx->ev_group[i / 2];
+    ctx->prof_ms[g] += ms;
+    ctx->prof_n[g] += 1;
+  }
+  ctx->ev_used = 0;
+  return UGKS_OK;
+}
+
 int do_interp(ugks_ctx *ctx, const int *list, int n) {
   if (n <= 0) return UGKS_OK;
-  launch_interp(ctx->d, ctx->st, list, n, ctx->fp32);
+  { Prof p(ctx, UGKS_PROF_INTERP); launch_interp(ctx->d, ctx->st, list, n, ctx->fp32); }
   ctx->launches += 2;
   return UGKS_OK;
+}
+
+// Ghost states, W gradients, face reduction, face coefficients, per-cell
+// macro flux sum (Steps 1 / 3 up to the velocity-resolved flux).
+void flux_prep(ugks_ctx *ctx, int level_n) {
+  Dev &d = ctx->d;
+  cudaStream_t s = ctx->st;
+  { Prof p(ctx, UGKS_PROF_CELL); launch_ghost_gradW(d, s); }
+  { Prof p(ctx, UGKS_PROF_FACE_REDUCE); launch_face_reduce(d, s, ctx->fp32); }
+  { Prof p(ctx, UGKS_PROF_FACE_COEF); launch_face_coef(d, s, ctx->fp32); }
+  { Prof p(ctx, UGKS_PROF_CELL); launch_cell_macro(d, s, level_n); }
+  ctx->launches += 6;
 }
 
 int do_connect(ugks_ctx *ctx, ugks_connect_stats *stats, bool initial) {
@@ -366,8 +437,40 @@ int do_connect(ugks_ctx *ctx, ugks_connect_stats *stats, bool initial) {
   if (initial) CK(cudaMemsetAsync(ctx->prev_status, 0, sizeof(int) * d.nc, ctx->st));
   else CK(cudaMemcpyAsync(ctx->prev_status, d.status, sizeof(int) * d.nc, cudaMemcpyDeviceToDevice, ctx->st));
   CK(cudaMemsetAsync(ctx->n_orphan, 0, sizeof(int), ctx->st));
-  launch_connect(d, ctx->st, ctx->prev_status, ctx->blk_order, ctx->n_orphan);
-  ctx->launches += 4;
+  {
+    // bins over the affine image of each block's reference bounding box
+    std::vector<double> geo(4 * (size_t)ctx->nblocks);
+    std::vector<int> dim(3 * (size_t)ctx->nblocks);
+    int base = 0;
+    for (int b = 0; b < ctx->nblocks; ++b) {
+      const double *A = &ctx->h_affine[6 * (size_t)b];
+      const double *bb = &ctx->ref_bbox[4 * (size_t)b];
+      double xl = 1e300, xh = -1e300, yl = 1e300, yh = -1e300;
+      for (int corner = 0; corner < 4; ++corner) {
+        double x = (corner & 1) ? bb[2] : bb[0], y = (corner & 2) ? bb[3] : bb[1];
+        double X = A[0] * x + A[1] * y + A[4], Y = A[2] * x + A[3] * y + A[5];
+        xl = std::min(xl, X); xh = std::max(xh, X); yl = std::min(yl, Y); yh = std::max(yh, Y);
+      }
+      double w = xh - xl, h = yh - yl, pad = 1e-9 * (w + h + 1.0);
+      xl -= pad; yl -= pad; w += 2 * pad; h += 2 * pad;
+      int ncb = ctx->cell_off[b + 1] - ctx->cell_off[b];
+      double target = std::max(1.0, ncb / 2.0);
+      int nx = std::max(1, std::min(2048, (int)std::lround(std::sqrt(target * w / h))));
+      int ny = std::max(1, std::min(2048, (int)std::lround(target / nx)));
+      while ((size_t)nx * ny > (size_t)ncb && nx > 1) --nx;
+      while ((size_t)nx * ny > (size_t)ncb && ny > 1) --ny;
+      geo[4 * b] = xl; geo[4 * b + 1] = yl; geo[4 * b + 2] = nx / w; geo[4 * b + 3] = ny / h;
+      dim[3 * b] = nx; dim[3 * b + 1] = ny; dim[3 * b + 2] = base;
+      base += nx * ny;
+    }
+    d.nbins = base;
+    ctx->h_bin_geo = geo;
+    ctx->h_bin_dim = dim;
+    CK(cudaMemcpyAsync(d.bin_geo, ctx->h_bin_geo.data(), sizeof(double) * geo.size(), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(d.bin_dim, ctx->h_bin_dim.data(), sizeof(int) * dim.size(), cudaMemcpyHostToDevice, ctx->st));
+  }
+  { Prof p(ctx, UGKS_PROF_CONNECT); launch_connect(d, ctx->st, ctx->prev_status, ctx->blk_order, ctx->n_orphan); }
+  ctx->launches += 7;
   int r = launch_status(ctx);
   if (r) return r;
   std::vector<int> st(d.nc), fr(d.nc);
@@ -376,6 +479,7 @@ int do_connect(ugks_ctx *ctx, ugks_connect_stats *stats, bool initial) {
   CK(cudaMemcpyAsync(fr.data(), ctx->prev_status, sizeof(int) * d.nc, cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaMemcpyAsync(&norph, ctx->n_orphan, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
+  if ((r = check_err_flag(ctx))) return r;
   std::vector<int> rec, fresh;
   int nf = 0, nr = 0, nh = 0;
   for (int c = 0; c < d.nc; ++c) {
@@ -439,6 +543,8 @@ int ugks_create(const ugks_params *p, void *workspace, size_t bytes, void *strea
 }
 
 int ugks_destroy(ugks_ctx *ctx) {
+  if (ctx)
+    for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
   delete ctx;
   return UGKS_OK;
 }
@@ -519,9 +625,17 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
   Topo T;
   build_topology(nblocks, blocks, ctx->cell_off, ctx->node_off, s.nc, s.nn, T);
   std::vector<double> X(2 * (size_t)s.nn);
+  ctx->ref_bbox.assign(4 * (size_t)nblocks, 0.0);
   for (int b = 0; b < nblocks; ++b) {
     size_t n = 2 * (size_t)(blocks[b].ni + 1) * (blocks[b].nj + 1);
     memcpy(&X[2 * (size_t)ctx->node_off[b]], blocks[b].x_ref, n * sizeof(double));
+    double xl = 1e300, xh = -1e300, yl = 1e300, yh = -1e300;
+    for (size_t q = 0; q < n; q += 2) {
+      xl = std::min(xl, blocks[b].x_ref[q]); xh = std::max(xh, blocks[b].x_ref[q]);
+      yl = std::min(yl, blocks[b].x_ref[q + 1]); yh = std::max(yh, blocks[b].x_ref[q + 1]);
+    }
+    double *bb = &ctx->ref_bbox[4 * (size_t)b];
+    bb[0] = xl; bb[1] = yl; bb[2] = xh; bb[3] = yh;
   }
   std::vector<int> order(nblocks);
   for (int b = 0; b < nblocks; ++b) order[b] = b;
@@ -567,9 +681,10 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
   if ((r = up(ctx, (void *)ctx->work, work))) return r;
   if ((r = up(ctx, (void *)d.X_ref, X))) return r;
   // identity placement at t = 0
-  std::vector<double> aff(6 * (size_t)nblocks, 0.0);
-  for (int b = 0; b < nblocks; ++b) { aff[6 * b] = 1.0; aff[6 * b + 3] = 1.0; }
-  if ((r = up(ctx, (void *)d.affine, aff))) return r;
+  ctx->h_affine.assign(6 * (size_t)nblocks, 0.0);
+  for (int b = 0; b < nblocks; ++b) { ctx->h_affine[6 * b] = 1.0; ctx->h_affine[6 * b + 3] = 1.0; }
+  if ((r = up(ctx, (void *)d.affine, ctx->h_affine))) return r;
+  d.bin_cap = (int)bin_capacity(s);
   CK(cudaMemsetAsync(d.err, 0, sizeof(int), ctx->st));
   CK(cudaMemsetAsync(d.status, 0, sizeof(int) * s.nc, ctx->st));
   CK(cudaMemsetAsync(d.donors, 0xff, sizeof(int) * 5 * (size_t)s.nc, ctx->st));
@@ -610,9 +725,12 @@ int ugks_move_mesh(ugks_ctx *ctx, double t_new, const double *affine) {
                      cudaMemcpyHostToDevice, ctx->st));
   d.dt = t_new - ctx->t;
   ctx->t_new = t_new;
-  launch_move_nodes(d, ctx->st);
-  launch_geometry(d, ctx->st);
-  launch_slope_geo(d, ctx->st);
+  {
+    Prof p(ctx, UGKS_PROF_GEOMETRY);
+    launch_move_nodes(d, ctx->st);
+    launch_geometry(d, ctx->st);
+    launch_slope_geo(d, ctx->st);
+  }
   ctx->launches += 5;
   ctx->moved = true;
   return launch_status(ctx);
@@ -637,19 +755,20 @@ int ugks_step(ugks_ctx *ctx, double dt, int n_inner) {
   do_interp(ctx, d.fresh_list, d.nfresh);
   do_interp(ctx, d.rec_list, d.nrec);
   // Steps 1-2: level-n flux, extensive level-n macro term, level-n cell record
-  launch_flux_prep(d, s, 1, fp);
-  launch_cell_params(d, s, d.W, d.cparn);
-  ctx->launches += 6;
+  flux_prep(ctx, 1);
+  { Prof p(ctx, UGKS_PROF_CELL); launch_cell_params(d, s, d.W, d.cparn); }
+  ctx->launches += 1;
   for (int it = 0; it < n_inner; ++it) {
     if (it > 0) {
       do_interp(ctx, d.rec_list, d.nrec);
-      launch_flux_prep(d, s, 0, fp);          // Step 3
-      ctx->launches += 5;
+      flux_prep(ctx, 0);                       // Step 3
     }
-    launch_macro_sweep(d, s, ctx->max_nj);    // Step 4
-    launch_micro(d, s, ctx->work, ctx->nwork, ctx->V, ctx->max_nj, it == 0, fp);  // Steps 5-6
-    launch_moments(d, s, fp);                 // Step 7
-    ctx->launches += 4;
+    { Prof p(ctx, UGKS_PROF_MACRO_SWEEP); launch_macro_sweep(d, s, ctx->max_nj, fp); }          // Step 4
+    { Prof p(ctx, UGKS_PROF_RHS); launch_rhs(d, s, it == 0, fp); }                         // Step 5
+    { Prof p(ctx, UGKS_PROF_MICRO_FWD); launch_micro_fwd(d, s, ctx->work, ctx->nwork, ctx->V, ctx->max_nj, fp); }  // Step 6
+    { Prof p(ctx, UGKS_PROF_MICRO_BWD); launch_micro_bwd(d, s, ctx->work, ctx->nwork, ctx->V, ctx->max_nj, fp); }
+    { Prof p(ctx, UGKS_PROF_MOMENTS); launch_moments(d, s, fp); }                          // Step 7
+    ctx->launches += 7;
   }
   d.nfresh = 0;
   ctx->t = ctx->t_new;
@@ -711,8 +830,7 @@ int ugks_eval_flux(ugks_ctx *ctx, double *D, double *F) {
   Dev &d = ctx->d;
   if (D && !is_device_ptr(D)) return fail(ctx, UGKS_ERR_ARG, "D must be a device pointer");
   do_interp(ctx, d.rec_list, d.nrec);
-  launch_flux_prep(d, ctx->st, 0, ctx->fp32);
-  ctx->launches += 5;
+  flux_prep(ctx, 0);
   if (D) { launch_flux_div_all(d, ctx->st, D, ctx->fp32); ctx->launches += 1; }
   if (F) CK(cudaMemcpyAsync(F, d.Fc, sizeof(double) * 4 * d.nc, cudaMemcpyDefault, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
@@ -741,6 +859,28 @@ int ugks_get_geometry(ugks_ctx *ctx, double *vol_old, double *vol_new, double *x
   if (SUn) CK(cudaMemcpyAsync(SUn, d.SUn, sizeof(double) * d.nf, cudaMemcpyDefault, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   return check_err_flag(ctx);
+}
+
+int ugks_profile_enable(ugks_ctx *ctx, int on) {
+  if (!ctx) return UGKS_ERR_ARG;
+  if (!on) {
+    int r = prof_drain(ctx);
+    if (r) return r;
+  }
+  ctx->prof_on = on != 0;
+  return UGKS_OK;
+}
+
+int ugks_profile_read(ugks_ctx *ctx, double *ms, int64_t *launches, int reset) {
+  if (!ctx) return UGKS_ERR_ARG;
+  int r = prof_drain(ctx);
+  if (r) return r;
+  for (int g = 0; g < UGKS_NPROF; ++g) {
+    if (ms) ms[g] = ctx->prof_ms[g];
+    if (launches) launches[g] = ctx->prof_n[g];
+    if (reset) { ctx->prof_ms[g] = 0; ctx->prof_n[g] = 0; }
+  }
+  return UGKS_OK;
 }
 
 }  // extern "C"

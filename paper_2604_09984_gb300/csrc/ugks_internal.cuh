@@ -18,7 +18,7 @@ enum { SL_NONE = 0, SL_M = 1, SL_P = 2, SL_BOTH = 3 };
 // face sums of the velocity-reduction pass
 enum { FS_W0 = 0, FS_FF = 4, FS_WG = 8, NFS = 12 };
 // error flags
-enum { EF_GEOMETRY = 1, EF_NONPHYSICAL = 2 };
+enum { EF_GEOMETRY = 1, EF_NONPHYSICAL = 2, EF_BINS = 4 };
 
 template <typename T> struct Vec2;
 template <> struct Vec2<double> { typedef double2 type; };
@@ -57,6 +57,7 @@ struct Dev {
   double *dts;               // nc
   double *Sn, *S, *nrm, *xf, *Uf, *SUn;   // nf*2 / nf
   int *slope_flags;          // nc: 2 bits per direction (i: bits 0-1, j: 2-3)
+  int *cmask;                // nc: bit 0 solved cell, bit 1+s solved neighbour across slot s
   double *jinv;              // nc*4 inverse of [[x_xi, y_xi],[x_eta, y_eta]]
   double *affine;            // nblocks*6
   // state
@@ -68,6 +69,7 @@ struct Dev {
   double *TW;                // nc*4 extensive level-n macro term
   double *Fc;                // nc*4 macro flux divergence of the last flux
   double *dW;                // nc*4 macro increment
+  void *mrec;                // nc*41 macro-sweep records (arithmetic type)
   double *Wp;                // nc*4 macro predictor W'
   double *cpar;              // nc*NCP cell parameters (predictor / level n)
   double *cparn;
@@ -97,11 +99,17 @@ struct Dev {
   const int *cell_off;       // nblocks+1 (device copy)
   const int *node_off;       // nblocks+1
   const int *blk_info;       // nblocks*8: ni, nj, periodic, priority, n_fringe, n_gap, bc-overset mask, body?
+  // overset search bins (per block uniform grid, CSR of cell ids)
+  double *bin_geo;           // nblocks*4: x0, y0, 1/hx, 1/hy
+  int *bin_dim;              // nblocks*3: nbx, nby, first bin
+  int *bin_cnt, *bin_start;  // nbins, nbins+1
+  int *bin_items;            // bin_cap
+  int nbins, bin_cap;
   int *err;                  // error flags
 };
 
 // per-cell parameter record (from W' or W^n)
-enum { CP_RHO = 0, CP_UX, CP_UY, CP_LAM, CP_QX, CP_QY, CP_ITAU, CP_PREF, NCP = 8 };
+enum { CP_RHO = 0, CP_UX, CP_UY, CP_LAM, CP_QX, CP_QY, CP_ITAU, CP_DBASE, NCP = 8 };
 
 template <typename T>
 __device__ __forceinline__ typename Vec2<T>::type ldf(const void *base, size_t idx) {

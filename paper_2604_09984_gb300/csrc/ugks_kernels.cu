@@ -85,6 +85,24 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
+// Lane-local sum in the arithmetic type: plain for FP64, Neumaier-compensated
+// for FP32 (the mixed path keeps velocity sums accurate to a few FP32 ulps
+// before the FP64 warp reduction).
+template <typename T> struct Acc {
+  T s = T(0);
+  __device__ __forceinline__ void add(T x) { s += x; }
+  __device__ __forceinline__ double get() const { return (double)s; }
+};
+template <> struct Acc<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    float t = s + x;
+    c += (fabsf(s) >= fabsf(x)) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ double get() const { return (double)s + (double)c; }
+};
+
 // Reading R3: dts_i = cfl_s Omega_i^{n+1} / max_k sum_faces S max(w_out, 0).
 // One warp per cell.
 __global__ void k_dts(Dev d) {
@@ -158,6 +176,14 @@ __global__ void k_slope_geo(Dev d) {
   double a11 = g[0][0], a12 = g[0][1], a21 = g[1][0], a22 = g[1][1];
   double det = a11 * a22 - a12 * a21;
   d.slope_flags[c] = flags;
+  // sweep mask: bit 0 solved cell, bit 1+s: neighbour across face slot s is solved
+  int mask = d.status[c] == ST_FIELD ? 1 : 0;
+  for (int s = 0; s < 4; ++s) {
+    int f = d.cell_faces[4 * c + s];
+    int nb = d.cell_sgn[4 * c + s] > 0 ? d.face_R[f] : d.face_L[f];
+    if (nb >= 0 && d.status[nb] == ST_FIELD) mask |= 2 << s;
+  }
+  d.cmask[c] = mask;
   d.jinv[4 * c + 0] = a22 / det;
   d.jinv[4 * c + 1] = -a12 / det;
   d.jinv[4 * c + 2] = -a21 / det;
@@ -268,32 +294,30 @@ template <typename T> __global__ void k_face_reduce(Dev d) {
     return;
   }
   bool wall = d.face_kind[fid] == BC_WALL;
-  double acc[NFS];
-#pragma unroll
-  for (int m = 0; m < NFS; ++m) acc[m] = 0.0;
-  double snx = d.Sn[2 * fid], sny = d.Sn[2 * fid + 1], sun = d.SUn[fid];
+  Acc<T> acc[NFS];
+  T snx = (T)d.Sn[2 * fid], sny = (T)d.Sn[2 * fid + 1], sun = (T)d.SUn[fid];
   for (int k = lane; k < d.nv; k += 32) {
     T vx = dvx<T>(d, k), vy = dvy<T>(d, k);
-    T wS = vx * (T)snx + vy * (T)sny - (T)sun;
+    T wS = vx * snx + vy * sny - sun;
     if (wall && !(wS > T(0))) continue;
     V2<T> ff, wg;
     face_upwind<T>(d, fid, k, wS, ff, wg);
-    double w = d.w[k], dvx_ = d.vx[k], dvy_ = d.vy[k];
-    double v2 = 0.5 * (dvx_ * dvx_ + dvy_ * dvy_);
-    double h = ff.h, b = ff.b, gh = wg.h, gb = wg.b, ws = (double)wS;
-    double p[4] = {w * h, w * dvx_ * h, w * dvy_ * h, w * (v2 * h + 0.5 * b)};
-    double g[4] = {w * gh, w * dvx_ * gh, w * dvy_ * gh, w * (v2 * gh + 0.5 * gb)};
+    T w = (T)d.w[k];
+    T v2 = T(0.5) * (vx * vx + vy * vy);
+    T p[4] = {w * ff.h, w * vx * ff.h, w * vy * ff.h, w * (v2 * ff.h + T(0.5) * ff.b)};
+    T g[4] = {w * wg.h, w * vx * wg.h, w * vy * wg.h, w * (v2 * wg.h + T(0.5) * wg.b)};
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      acc[FS_W0 + m] += p[m];
-      acc[FS_FF + m] += ws * p[m];
-      acc[FS_WG + m] += ws * g[m];
+      acc[FS_W0 + m].add(p[m]);
+      acc[FS_FF + m].add(wS * p[m]);
+      acc[FS_WG + m].add(wS * g[m]);
     }
   }
+  double tot[NFS];
 #pragma unroll
-  for (int m = 0; m < NFS; ++m) acc[m] = warp_sum(acc[m]);
+  for (int m = 0; m < NFS; ++m) tot[m] = warp_sum(acc[m].get());
   if (lane == 0) {
-    for (int m = 0; m < NFS; ++m) d.fsum[NFS * fid + m] = acc[m];
+    for (int m = 0; m < NFS; ++m) d.fsum[NFS * fid + m] = tot[m];
     if (wall)
       for (int m = 0; m < 4; ++m) d.fsum[NFS * fid + FS_W0 + m] = 0.0;
   }
@@ -307,22 +331,16 @@ __device__ __forceinline__ double spectral_radius(const double *Wf, double nx, d
   return fabs(p.ux * nx + p.uy * ny - un) + sqrt(gamma * pr / p.rho);
 }
 
-// Face coefficients (one warp per face): g0 parameters and slopes (reading
-// R2), time integrals over dts, the g-part of the macro flux by a sum over the
-// discrete velocities, the wall density rho_w (Eq. maxWalldes), the total
-// S-weighted macro flux and the spectral radius Gamma (Sec. 2.2).
-template <typename T> __global__ void k_face_coef(Dev d) {
-  int fid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
+// Face coefficients, scalar part (one thread per face): g0 parameters and
+// slopes (reading R2), time integrals over dts (Eq. fullSolution averaged as
+// in Sec. 2.2), wall temperature parameter.
+template <typename T> __global__ void k_face_scalar(Dev d) {
+  int fid = blockIdx.x * blockDim.x + threadIdx.x;
   if (fid >= d.nf) return;
   int kind = d.face_kind[fid];
+  if (!face_needed(d, fid) || kind == BC_OVERSET) return;
   double *P = d.fpar + (size_t)NFP * fid;
   T *PT = reinterpret_cast<T *>(d.fparT) + (size_t)NFP * fid;
-  if (!face_needed(d, fid) || kind == BC_OVERSET) {
-    if (lane < 4) d.fflux[4 * fid + lane] = 0.0;
-    if (lane == 0) d.gam[fid] = 0.0;
-    return;
-  }
   int L = d.face_L[fid], R = d.face_R[fid];
   bool wall = kind == BC_WALL;
   double W0[4], gx[4], gy[4], q0x, q0y, dts;
@@ -387,48 +405,71 @@ template <typename T> __global__ void k_face_coef(Dev d) {
   for (int m = 0; m < 5; ++m) par[FP_Q1 + m] = qi[m] / dts;
   par[FP_UFX] = ufx; par[FP_UFY] = ufy;
   par[FP_PREF] = 4.0 * (1.0 - d.Pr) * p0.lam * p0.lam / (5.0 * p0.rho);
-  double lamw = wall ? 1.0 / (2.0 * d.face_Tw[fid]) : 0.0;
-  par[FP_LAMW] = lamw;
+  par[FP_LAMW] = wall ? 1.0 / (2.0 * d.face_Tw[fid]) : 0.0;
   par[FP_RHOW] = 0.0;
-  // g-part of the macro flux (all faces) and wall sums, by velocity
-  double gs[4] = {0, 0, 0, 0}, rs[4] = {0, 0, 0, 0}, den = 0.0;
-  double snx = d.Sn[2 * fid], sny = d.Sn[2 * fid + 1], sun = d.SUn[fid];
-  V2<double> zero = {0.0, 0.0};
+  for (int m = 0; m < NFP; ++m) { P[m] = par[m]; PT[m] = (T)par[m]; }
+  // Gamma from the mean of the two cells' W (boundary: the cell)
+  double Wf[4];
+  for (int m = 0; m < 4; ++m) Wf[m] = (R >= 0) ? 0.5 * (d.W[4 * L + m] + d.W[4 * R + m]) : d.W[4 * L + m];
+  d.gam[fid] = spectral_radius(Wf, nx, ny, d.SUn[fid] / d.S[fid], d.Keff);
+}
+
+// Face coefficients, velocity part (one warp per face): the g-part of the
+// macro flux by a sum over the discrete velocities, the wall density rho_w
+// (Eq. maxWalldes) and the total S-weighted macro flux (Eq. macroscopicFlux).
+template <typename T> __global__ void k_face_coef(Dev d) {
+  int fid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (fid >= d.nf) return;
+  int kind = d.face_kind[fid];
+  if (!face_needed(d, fid) || kind == BC_OVERSET) {
+    if (lane < 4) d.fflux[4 * fid + lane] = 0.0;
+    if (lane == 0) d.gam[fid] = 0.0;
+    return;
+  }
+  bool wall = kind == BC_WALL;
+  double *P = d.fpar + (size_t)NFP * fid;
+  T *PT = reinterpret_cast<T *>(d.fparT) + (size_t)NFP * fid;
+  const double *fs = d.fsum + NFS * fid;
+  T parT[NFP];
+#pragma unroll
+  for (int m = 0; m < NFP; ++m) parT[m] = PT[m];
+  Acc<T> ags[4], ars[4], aden;
+  T snx = (T)d.Sn[2 * fid], sny = (T)d.Sn[2 * fid + 1], sun = (T)d.SUn[fid];
+  T tufx = parT[FP_UFX], tufy = parT[FP_UFY], tlamw = parT[FP_LAMW], tK = (T)d.Keff;
+  V2<T> zero = {T(0), T(0)};
   for (int k = lane; k < d.nv; k += 32) {
-    double vx = d.vx[k], vy = d.vy[k], w = d.w[k];
-    double wS = vx * snx + vy * sny - sun;
-    double v2 = 0.5 * (vx * vx + vy * vy);
-    if (!wall || wS > 0.0) {
-      V2<double> I = interface_integral<double>(par, vx, vy, zero, zero, (double)d.Keff,
-                                                (double)d.Kint, d.Pr);
-      double c = w * wS;
-      gs[0] += c * I.h; gs[1] += c * vx * I.h; gs[2] += c * vy * I.h; gs[3] += c * (v2 * I.h + 0.5 * I.b);
+    T vx = dvx<T>(d, k), vy = dvy<T>(d, k), w = (T)d.w[k];
+    T wS = vx * snx + vy * sny - sun;
+    T v2 = T(0.5) * (vx * vx + vy * vy);
+    T cw = w * wS;
+    if (!wall || wS > T(0)) {
+      V2<T> I = interface_integral<T>(parT, vx, vy, zero, zero, tK, (T)d.Kint, (T)d.Pr);
+      ags[0].add(cw * I.h); ags[1].add(cw * vx * I.h); ags[2].add(cw * vy * I.h);
+      ags[3].add(cw * (v2 * I.h + T(0.5) * I.b));
     } else {
-      double cx = vx - ufx, cy = vy - ufy;
-      double Hw = (lamw / M_PI) * exp(-lamw * (cx * cx + cy * cy));
-      double Bw = (double)d.Keff / (2.0 * lamw) * Hw;
-      double c = w * wS;
-      den += c * Hw;
-      rs[0] += c * Hw; rs[1] += c * vx * Hw; rs[2] += c * vy * Hw; rs[3] += c * (v2 * Hw + 0.5 * Bw);
+      T cx = vx - tufx, cy = vy - tufy;
+      T Hw = (tlamw / T(M_PI)) * r_exp<T>(-tlamw * (cx * cx + cy * cy));
+      T Bw = tK / (T(2) * tlamw) * Hw;
+      aden.add(cw * Hw);
+      ars[0].add(cw * Hw); ars[1].add(cw * vx * Hw); ars[2].add(cw * vy * Hw);
+      ars[3].add(cw * (v2 * Hw + T(0.5) * Bw));
     }
   }
-  for (int m = 0; m < 4; ++m) { gs[m] = warp_sum(gs[m]); rs[m] = warp_sum(rs[m]); }
-  den = warp_sum(den);
+  double gs[4], rs[4];
+  for (int m = 0; m < 4; ++m) { gs[m] = warp_sum(ags[m].get()); rs[m] = warp_sum(ars[m].get()); }
+  double den = warp_sum(aden.get());
   if (lane == 0) {
     double F[4];
     for (int m = 0; m < 4; ++m)
-      F[m] = par[FP_Q1] * fs[FS_FF + m] + par[FP_Q2] * fs[FS_WG + m] + gs[m];
+      F[m] = P[FP_Q1] * fs[FS_FF + m] + P[FP_Q2] * fs[FS_WG + m] + gs[m];
     if (wall) {
       double rhow = -F[0] / den;
-      par[FP_RHOW] = rhow;
+      P[FP_RHOW] = rhow;
+      PT[FP_RHOW] = (T)rhow;
       for (int m = 0; m < 4; ++m) F[m] += rhow * rs[m];
     }
     for (int m = 0; m < 4; ++m) d.fflux[4 * fid + m] = F[m];
-    for (int m = 0; m < NFP; ++m) { P[m] = par[m]; PT[m] = (T)par[m]; }
-    // Gamma from the mean of the two cells' W (boundary: the cell)
-    double Wf[4];
-    for (int m = 0; m < 4; ++m) Wf[m] = (R >= 0) ? 0.5 * (d.W[4 * L + m] + d.W[4 * R + m]) : d.W[4 * L + m];
-    d.gam[fid] = spectral_radius(Wf, nx, ny, d.SUn[fid] / d.S[fid], d.Keff);
   }
 }
 
@@ -458,7 +499,7 @@ __global__ void k_cell_params(Dev d, const double *Wsrc, double *out) {
   o[CP_RHO] = p.rho; o[CP_UX] = p.ux; o[CP_UY] = p.uy; o[CP_LAM] = p.lam;
   o[CP_QX] = d.q[2 * c]; o[CP_QY] = d.q[2 * c + 1];
   o[CP_ITAU] = 1.0 / collision_time(p.rho, p.lam, d.mu_ref, d.omega);
-  o[CP_PREF] = 0.0;
+  o[CP_DBASE] = 0.0;
 }
 
 // ----------------------------------------------------- macro LU-SGS sweep
@@ -474,140 +515,184 @@ __device__ __forceinline__ void euler_flux(const double *W, double nx, double ny
   F[3] = W[3] * vn + pr * vabs;
 }
 
-// (1/4) S (dF_E,j - Gamma dW_j) across face fid along the outward normal of
-// the cell with orientation sg.
-__device__ __forceinline__ void macro_off(const Dev &d, int fid, double sg, int nb,
-                                          const double *dWn, double out[4]) {
-  double nx = sg * d.nrm[2 * fid], ny = sg * d.nrm[2 * fid + 1];
-  double un = sg * d.SUn[fid] / d.S[fid];
+// Per-cell record of the macro sweep (gathered in parallel before it):
+// R (4), 1/diag, then per face slot: neighbour W (4), outward normal (2),
+// U.n, S/4, Gamma.
+enum { MR_R = 0, MR_IDIAG = 4, MR_SLOT = 5, MR_SW = 9, NMR = 41 };
+
+// (1/4) S (dF_E,j - Gamma dW_j) across one face slot of the record.  FP64:
+// the difference F_E(W + dW) - F_E(W) evaluated directly.  FP32 (mixed
+// path): the same difference rewritten exactly in terms of dW (every term is
+// O(dW)), so no cancellation occurs when dW << W.
+__device__ __forceinline__ void macro_off(const double *r, const double *dW, int Keff,
+                                          double out[4]) {
   double Wa[4], Wb[4], Fa[4], Fb[4];
-  for (int m = 0; m < 4; ++m) { Wb[m] = d.W[4 * nb + m]; Wa[m] = Wb[m] + dWn[m]; }
-  euler_flux(Wa, nx, ny, un, d.Keff, Fa);
-  euler_flux(Wb, nx, ny, un, d.Keff, Fb);
-  double q = 0.25 * d.S[fid], g = d.gam[fid];
-  for (int m = 0; m < 4; ++m) out[m] = q * ((Fa[m] - Fb[m]) - g * dWn[m]);
+  for (int m = 0; m < 4; ++m) { Wb[m] = r[m]; Wa[m] = Wb[m] + dW[m]; }
+  euler_flux(Wa, r[4], r[5], r[6], Keff, Fa);
+  euler_flux(Wb, r[4], r[5], r[6], Keff, Fb);
+  for (int m = 0; m < 4; ++m) out[m] = r[7] * ((Fa[m] - Fb[m]) - r[8] * dW[m]);
+}
+
+__device__ __forceinline__ void macro_off(const float *rr, const float *dWn, int Keff, float out[4]) {
+  float r = rr[0], m1 = rr[1], m2 = rr[2], E = rr[3];
+  float nx = rr[4], ny = rr[5], un = rr[6];
+  float dr = dWn[0], d1 = dWn[1], d2 = dWn[2], dE = dWn[3];
+  float g1 = 2.0f / (2.0f + (float)Keff);             // gamma - 1
+  float mn = m1 * nx + m2 * ny, dmn = d1 * nx + d2 * ny;
+  float den = 1.0f / (r * (r + dr));
+  // d(a b / rho) = [da b rho + a db rho + da db rho - a b drho] / (rho (rho + drho))
+  float dq11 = (2.0f * (m1 * d1 + m2 * d2) * r + (d1 * d1 + d2 * d2) * r -
+                (m1 * m1 + m2 * m2) * dr) * den;
+  float dp = g1 * (dE - 0.5f * dq11);
+  float p = g1 * (E - 0.5f * (m1 * m1 + m2 * m2) / r);
+  float dv = (dmn * r - mn * dr) * den;               // d(mn / rho)
+  float dF0 = dmn - dr * un;
+  float dF1 = (d1 * mn * r + m1 * dmn * r + d1 * dmn * r - m1 * mn * dr) * den - d1 * un + dp * nx;
+  float dF2 = (d2 * mn * r + m2 * dmn * r + d2 * dmn * r - m2 * mn * dr) * den - d2 * un + dp * ny;
+  float dF3 = (dE * mn * r + E * dmn * r + dE * dmn * r - E * mn * dr) * den - dE * un +
+              dp * (mn + dmn) / (r + dr) + p * dv;
+  float q = rr[7], g = rr[8];
+  out[0] = q * (dF0 - g * dr);
+  out[1] = q * (dF1 - g * d1);
+  out[2] = q * (dF2 - g * d2);
+  out[3] = q * (dF3 - g * dE);
+}
+
+// Gather the sweep record of every solved cell (parallel).
+template <typename MT> __global__ void k_macro_prep(Dev d, MT *rec) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.nc) return;
+  if (!(d.cmask[c] & 1)) return;
+  MT *o = rec + (size_t)NMR * c;
+  double vol = d.vol_new[c], idt = 1.0 / d.dt;
+  for (int m = 0; m < 4; ++m)
+    o[MR_R + m] = (MT)(d.TW[4 * c + m] - vol * idt * d.W[4 * c + m] - 0.5 * d.Fc[4 * c + m]);
+  double diag = vol * (d.cfl_s / (d.cfl_pseudo * d.dts[c]) + idt);
+  for (int s = 0; s < 4; ++s) {
+    int f = d.cell_faces[4 * c + s];
+    diag += 0.25 * d.S[f] * d.gam[f];
+    double sg = (double)d.cell_sgn[4 * c + s];
+    int nb = (sg > 0) ? d.face_R[f] : d.face_L[f];
+    MT *q = o + MR_SLOT + MR_SW * s;
+    for (int m = 0; m < 4; ++m) q[m] = nb >= 0 ? (MT)d.W[4 * nb + m] : MT(0);
+    q[4] = (MT)(sg * d.nrm[2 * f]);
+    q[5] = (MT)(sg * d.nrm[2 * f + 1]);
+    q[6] = (MT)(sg * d.SUn[f] / d.S[f]);
+    q[7] = (MT)(0.25 * d.S[f]);
+    q[8] = (MT)d.gam[f];
+  }
+  o[MR_IDIAG] = (MT)(1.0 / diag);
 }
 
 // LU-SGS of Eq. dualTimeStepping_macro (Sec. 2.2), one CTA per block,
 // thread = row j; diagonals i + j in increasing (forward) then decreasing
-// (backward) order reproduce the lexicographic Gauss-Seidel exactly.
-// Produces W' = W + dW and the predictor cell record.
-__global__ void __launch_bounds__(512) k_macro_sweep(Dev d) {
+// (backward) order reproduce the lexicographic Gauss-Seidel exactly.  The
+// record of the next diagonal's cell is loaded before the barrier, so a
+// diagonal step costs the arithmetic of its lower/upper couplings only.
+template <typename MT> __global__ void __launch_bounds__(512) k_macro_sweep(Dev d, const MT *rec) {
   extern __shared__ double sm[];
+  MT *buf0 = reinterpret_cast<MT *>(sm), *buf1 = buf0 + 4 * blockDim.x;
   int b = blockIdx.x;
   const int *bi = d.blk_info + 8 * b;
   int ni = bi[0], nj = bi[1], per = bi[2];
   int off = d.cell_off[b];
   int row = threadIdx.x;
-  int rows = blockDim.x;
-  double *buf0 = sm, *buf1 = sm + 4 * rows;
-  double prev[4] = {0, 0, 0, 0}, first[4] = {0, 0, 0, 0};
+  MT prev[4] = {0, 0, 0, 0}, first[4] = {0, 0, 0, 0};
   int nd = ni + nj - 1;
-  double idt = 1.0 / d.dt;
-  int cur = 0;
-  for (int step = 0; step < nd; ++step) {
-    int i = step - row;
-    bool act = row < nj && i >= 0 && i < ni;
-    double val[4] = {0, 0, 0, 0};
-    if (act) {
-      int c = off + row * ni + i;
-      if (d.status[c] == ST_FIELD) {
-        double acc[4];
-        double vol = d.vol_new[c];
-        for (int m = 0; m < 4; ++m)
-          acc[m] = d.TW[4 * c + m] - vol * idt * d.W[4 * c + m] - 0.5 * d.Fc[4 * c + m];
-        double diag = vol * (d.cfl_s / (d.cfl_pseudo * d.dts[c]) + idt);
-        for (int s = 0; s < 4; ++s) {
-          int f = d.cell_faces[4 * c + s];
-          diag += 0.25 * d.S[f] * d.gam[f];
-        }
-        double *prv = cur ? buf0 : buf1;
-        // lower neighbours: i-1 (same row), wrap of i = ni-1 to 0, j-1
-        for (int s = 0; s < 3; ++s) {
-          int f = d.cell_faces[4 * c + s];
-          double sg = (double)d.cell_sgn[4 * c + s];
-          int nb = (sg > 0) ? d.face_R[f] : d.face_L[f];
-          const double *dv = nullptr;
-          if (s == 0 && i > 0) dv = prev;
-          else if (s == 1 && per && i == ni - 1) dv = first;
-          else if (s == 2 && row > 0) dv = prv + 4 * (row - 1);
-          if (!dv || nb < 0 || d.status[nb] != ST_FIELD) continue;
-          double o[4];
-          macro_off(d, f, sg, nb, dv, o);
-          for (int m = 0; m < 4; ++m) acc[m] -= o[m];
-        }
-        for (int m = 0; m < 4; ++m) val[m] = acc[m] / diag;
-        for (int m = 0; m < 4; ++m) d.dW[4 * c + m] = val[m];
-      }
-    }
-    if (act) {
-      for (int m = 0; m < 4; ++m) prev[m] = val[m];
-      if (i == 0) for (int m = 0; m < 4; ++m) first[m] = val[m];
-    }
-    double *dst = cur ? buf1 : buf0;
-    if (row < rows) for (int m = 0; m < 4; ++m) dst[4 * row + m] = val[m];
-    __syncthreads();
-    cur ^= 1;
-  }
-  __syncthreads();
-  for (int m = 0; m < 4; ++m) { prev[m] = 0; first[m] = 0; }
   for (int m = 0; m < 4; ++m) { buf0[4 * row + m] = 0; buf1[4 * row + m] = 0; }
   __syncthreads();
-  cur = 0;
-  for (int step = nd - 1; step >= 0; --step) {
-    int i = step - row;
-    bool act = row < nj && i >= 0 && i < ni;
-    double val[4] = {0, 0, 0, 0};
-    if (act) {
-      int c = off + row * ni + i;
-      if (d.status[c] == ST_FIELD) {
-        double vol = d.vol_new[c];
-        double diag = vol * (d.cfl_s / (d.cfl_pseudo * d.dts[c]) + idt);
-        for (int s = 0; s < 4; ++s) {
-          int f = d.cell_faces[4 * c + s];
-          diag += 0.25 * d.S[f] * d.gam[f];
+  for (int pass = 0; pass < 2; ++pass) {
+    int cur = 0;
+    // registers holding the record of the cell this thread handles next
+    MT r[NMR];
+    MT dws[4] = {0, 0, 0, 0};
+    int mask = 0;
+    auto load = [&](int it) {
+      int step = pass == 0 ? it : nd - 1 - it;
+      int i = step - row;
+      mask = 0;
+      if (it < nd && row < nj && i >= 0 && i < ni) {
+        int c = off + row * ni + i;
+        mask = d.cmask[c];
+        if (mask & 1) {
+          const MT *src = rec + (size_t)NMR * c;
+#pragma unroll
+          for (int m = 0; m < NMR; ++m) r[m] = src[m];
+          if (pass == 1)
+            for (int m = 0; m < 4; ++m) dws[m] = (MT)d.dW[4 * c + m];
         }
-        double acc[4] = {0, 0, 0, 0};
-        double *prv = cur ? buf0 : buf1;
-        // upper neighbours: i+1 (same row), wrap of i = 0 to ni-1, j+1
-        for (int s = 0; s < 4; ++s) {
-          if (s == 2) continue;
-          int f = d.cell_faces[4 * c + s];
-          double sg = (double)d.cell_sgn[4 * c + s];
-          int nb = (sg > 0) ? d.face_R[f] : d.face_L[f];
-          const double *dv = nullptr;
-          if (s == 1 && i < ni - 1) dv = prev;
-          else if (s == 0 && per && i == 0) dv = first;
-          else if (s == 3 && row < nj - 1) dv = prv + 4 * (row + 1);
-          if (!dv || nb < 0 || d.status[nb] != ST_FIELD) continue;
-          double o[4];
-          macro_off(d, f, sg, nb, dv, o);
-          for (int m = 0; m < 4; ++m) acc[m] += o[m];
-        }
-        for (int m = 0; m < 4; ++m) val[m] = d.dW[4 * c + m] - acc[m] / diag;
-        for (int m = 0; m < 4; ++m) {
-          d.dW[4 * c + m] = val[m];
-          d.Wp[4 * c + m] = d.W[4 * c + m] + val[m];
-        }
-        Prim p = primitive(d.Wp + 4 * c, d.Keff);
-        double *o = d.cpar + NCP * c;
-        o[CP_RHO] = p.rho; o[CP_UX] = p.ux; o[CP_UY] = p.uy; o[CP_LAM] = p.lam;
-        o[CP_QX] = d.q[2 * c]; o[CP_QY] = d.q[2 * c + 1];
-        o[CP_ITAU] = 1.0 / collision_time(p.rho, p.lam, d.mu_ref, d.omega);
-        o[CP_PREF] = 0.0;
-      } else {
-        for (int m = 0; m < 4; ++m) d.Wp[4 * c + m] = d.W[4 * c + m];
       }
+    };
+    // FP32: the next diagonal's record is loaded before the barrier; FP64
+    // (reference path) loads at the start of the step to bound registers
+    constexpr bool PF = sizeof(MT) == 4;
+    if (PF) load(0);
+    for (int it = 0; it < nd; ++it) {
+      if (!PF) load(it);
+      int step = pass == 0 ? it : nd - 1 - it;
+      int i = step - row;
+      bool act = row < nj && i >= 0 && i < ni;
+      MT val[4] = {0, 0, 0, 0};
+      if (act && (mask & 1)) {
+        int c = off + row * ni + i;
+        MT acc[4];
+        if (pass == 0) for (int m = 0; m < 4; ++m) acc[m] = r[MR_R + m];
+        else for (int m = 0; m < 4; ++m) acc[m] = 0;
+        MT *prv = cur ? buf0 : buf1;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          if (!(mask & (2 << s))) continue;
+          const MT *dv = nullptr;
+          if (pass == 0) {          // lower: i-1, wrap ni-1 -> 0, j-1
+            if (s == 0 && i > 0) dv = prev;
+            else if (s == 1 && per && i == ni - 1) dv = first;
+            else if (s == 2 && row > 0) dv = prv + 4 * (row - 1);
+          } else {                  // upper: i+1, wrap 0 -> ni-1, j+1
+            if (s == 1 && i < ni - 1) dv = prev;
+            else if (s == 0 && per && i == 0) dv = first;
+            else if (s == 3 && row < nj - 1) dv = prv + 4 * (row + 1);
+          }
+          if (!dv) continue;
+          MT o[4];
+          macro_off(r + MR_SLOT + MR_SW * s, dv, d.Keff, o);
+          for (int m = 0; m < 4; ++m) acc[m] += pass == 0 ? -o[m] : o[m];
+        }
+        MT idg = r[MR_IDIAG];
+        if (pass == 0) for (int m = 0; m < 4; ++m) val[m] = acc[m] * idg;
+        else for (int m = 0; m < 4; ++m) val[m] = dws[m] - acc[m] * idg;
+        for (int m = 0; m < 4; ++m) d.dW[4 * c + m] = (double)val[m];
+      }
+      if (act) {
+        for (int m = 0; m < 4; ++m) prev[m] = val[m];
+        if (i == (pass == 0 ? 0 : ni - 1)) for (int m = 0; m < 4; ++m) first[m] = val[m];
+      }
+      MT *dst = cur ? buf1 : buf0;
+      for (int m = 0; m < 4; ++m) dst[4 * row + m] = val[m];
+      if (PF) load(it + 1);     // next diagonal's record, in flight across the barrier
+      __syncthreads();
+      cur ^= 1;
     }
-    if (act) {
-      for (int m = 0; m < 4; ++m) prev[m] = val[m];
-      if (i == ni - 1) for (int m = 0; m < 4; ++m) first[m] = val[m];
-    }
-    double *dst = cur ? buf1 : buf0;
-    for (int m = 0; m < 4; ++m) dst[4 * row + m] = val[m];
+    for (int m = 0; m < 4; ++m) { prev[m] = 0; first[m] = 0; }
+    for (int m = 0; m < 4; ++m) { buf0[4 * row + m] = 0; buf1[4 * row + m] = 0; }
     __syncthreads();
-    cur ^= 1;
   }
+}
+
+// W' = W + dW and the predictor cell record (Step 4 result) for Step 5.
+__global__ void k_macro_post(Dev d) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.nc) return;
+  if (!(d.cmask[c] & 1)) {
+    for (int m = 0; m < 4; ++m) d.Wp[4 * c + m] = d.W[4 * c + m];
+    return;
+  }
+  for (int m = 0; m < 4; ++m) d.Wp[4 * c + m] = d.W[4 * c + m] + d.dW[4 * c + m];
+  Prim p = primitive(d.Wp + 4 * c, d.Keff);
+  double *o = d.cpar + NCP * c;
+  o[CP_RHO] = p.rho; o[CP_UX] = p.ux; o[CP_UY] = p.uy; o[CP_LAM] = p.lam;
+  o[CP_QX] = d.q[2 * c]; o[CP_QY] = d.q[2 * c + 1];
+  o[CP_ITAU] = 1.0 / collision_time(p.rho, p.lam, d.mu_ref, d.omega);
+  o[CP_DBASE] = d.vol_new[c] * (d.cfl_s / (d.cfl_pseudo * d.dts[c]) + 1.0 / d.dt + 0.5 * o[CP_ITAU]);
 }
 
 // ----------------------------------------------------- micro LU-SGS sweeps
@@ -625,13 +710,52 @@ template <typename T> __device__ __forceinline__ T micro_diag(const Dev &d, int 
   return dg;
 }
 
-// Forward sweep of the micro LU-SGS (Eq. dualTimeStepping_micro with the
-// upwind flux variation of Sec. 2.2), fused with the flux divergence and the
-// residual r (Steps 3, 5): one CTA per (block, velocity tile), thread =
-// (row j, velocity); diagonal wavefront with one barrier per diagonal.
-// With first_iter it also forms the level-n term T (Steps 1-2).
+// Residual of the micro system (Steps 3 and 5, reading R4), fully parallel
+// over (cell, velocity): flux divergence D = sum_faces S F_hat, Shakhov
+// relaxation at W', level-n term T (written on the first inner iteration):
+//   r = T - Omega^{n+1} f / dt + (Omega^{n+1} (f+(W') - f)/tau' - D) / 2.
+// r is written into the forward-sweep buffer.
+template <typename T> __global__ void k_rhs(Dev d, int first_iter) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)d.nc * d.nvp) return;
+  int c = (int)(t / d.nvp), k = (int)(t % d.nvp);
+  if (k >= d.nv || d.status[c] != ST_FIELD) return;
+  typedef typename Vec2<T>::type T2;
+  T2 fv = ldf<T>(d.f, t);
+  V2<T> D = flux_div<T>(d, c, k);
+  const double *cp = d.cpar + NCP * c;
+  T vx = dvx<T>(d, k), vy = dvy<T>(d, k);
+  T itau = (T)cp[CP_ITAU];
+  V2<T> fp = shakhov<T>((T)cp[CP_RHO], (T)cp[CP_UX], (T)cp[CP_UY], (T)cp[CP_LAM], (T)cp[CP_QX],
+                        (T)cp[CP_QY], vx, vy, (T)d.Keff, (T)d.Kint, (T)d.Pr);
+  T vol1 = (T)d.vol_new[c];
+  T idt = (T)(1.0 / d.dt);
+  T2 tn;
+  if (first_iter) {
+    const double *cn = d.cparn + NCP * c;
+    T itn = (T)cn[CP_ITAU];
+    V2<T> fn = shakhov<T>((T)cn[CP_RHO], (T)cn[CP_UX], (T)cn[CP_UY], (T)cn[CP_LAM], (T)cn[CP_QX],
+                          (T)cn[CP_QY], vx, vy, (T)d.Keff, (T)d.Kint, (T)d.Pr);
+    T vol0 = (T)d.vol_old[c];
+    tn.x = vol0 * idt * fv.x + T(0.5) * (vol0 * (fn.h - fv.x) * itn - D.h);
+    tn.y = vol0 * idt * fv.y + T(0.5) * (vol0 * (fn.b - fv.y) * itn - D.b);
+    stf<T>(d.Tn, t, tn.x, tn.y);
+  } else {
+    tn = ldf<T>(d.Tn, t);
+  }
+  T rh = tn.x - vol1 * idt * fv.x + T(0.5) * (vol1 * (fp.h - fv.x) * itau - D.h);
+  T rb = tn.y - vol1 * idt * fv.y + T(0.5) * (vol1 * (fp.b - fv.y) * itau - D.b);
+  stf<T>(d.dfs, t, rh, rb);
+}
+
+// Micro LU-SGS (Eq. dualTimeStepping_micro with the upwind flux variation of
+// Sec. 2.2), forward sweep on the residual r (in dfs, overwritten by d*):
+// one CTA per (block, velocity tile), thread = (row j, velocity); the cells
+// of one diagonal i + j are independent, lower neighbours lie on the previous
+// diagonal (same thread / thread of row j-1) or, across a periodic seam, on
+// diagonal j (kept in a register).  One barrier per diagonal.
 template <typename T>
-__global__ void __launch_bounds__(512) k_micro_fwd(Dev d, const int *work, int V, int first_iter) {
+__global__ void __launch_bounds__(512) k_micro_fwd(Dev d, const int *work, int V) {
   typedef typename Vec2<T>::type T2;
   extern __shared__ unsigned char smraw[];
   T2 *bufA = reinterpret_cast<T2 *>(smraw);
@@ -643,9 +767,9 @@ __global__ void __launch_bounds__(512) k_micro_fwd(Dev d, const int *work, int V
   int row = threadIdx.x / V, v = threadIdx.x % V;
   int k = k0 + v;
   bool kval = k < d.nv;
+  T vx = kval ? dvx<T>(d, k) : T(0), vy = kval ? dvy<T>(d, k) : T(0);
   T2 prev = {0, 0}, first = {0, 0};
   int nd = ni + nj - 1;
-  T idt = (T)(1.0 / d.dt);
   int cur = 0;
   for (int step = 0; step < nd; ++step) {
     int i = step - row;
@@ -653,45 +777,30 @@ __global__ void __launch_bounds__(512) k_micro_fwd(Dev d, const int *work, int V
     T2 val = {0, 0};
     if (act) {
       int c = off + row * ni + i;
-      if (d.status[c] == ST_FIELD) {
+      int mask = d.cmask[c];
+      if (mask & 1) {
         size_t idx = (size_t)c * d.nvp + k;
-        T2 fv = ldf<T>(d.f, idx);
-        V2<T> D = flux_div<T>(d, c, k);
-        const double *cp = d.cpar + NCP * c;
-        T vx = dvx<T>(d, k), vy = dvy<T>(d, k);
-        T itau = (T)cp[CP_ITAU];
-        V2<T> fp = shakhov<T>((T)cp[CP_RHO], (T)cp[CP_UX], (T)cp[CP_UY], (T)cp[CP_LAM],
-                              (T)cp[CP_QX], (T)cp[CP_QY], vx, vy, (T)d.Keff, (T)d.Kint, (T)d.Pr);
-        T vol1 = (T)d.vol_new[c];
-        T2 tn;
-        if (first_iter) {
-          const double *cn = d.cparn + NCP * c;
-          T itn = (T)cn[CP_ITAU];
-          V2<T> fn = shakhov<T>((T)cn[CP_RHO], (T)cn[CP_UX], (T)cn[CP_UY], (T)cn[CP_LAM],
-                                (T)cn[CP_QX], (T)cn[CP_QY], vx, vy, (T)d.Keff, (T)d.Kint, (T)d.Pr);
-          T vol0 = (T)d.vol_old[c];
-          tn.x = vol0 * idt * fv.x + T(0.5) * (vol0 * (fn.h - fv.x) * itn - D.h);
-          tn.y = vol0 * idt * fv.y + T(0.5) * (vol0 * (fn.b - fv.y) * itn - D.b);
-          stf<T>(d.Tn, idx, tn.x, tn.y);
-        } else {
-          tn = ldf<T>(d.Tn, idx);
-        }
-        T ah = tn.x - vol1 * idt * fv.x + T(0.5) * (vol1 * (fp.h - fv.x) * itau - D.h);
-        T ab = tn.y - vol1 * idt * fv.y + T(0.5) * (vol1 * (fp.b - fv.y) * itau - D.b);
-        T dg = micro_diag<T>(d, c, k, itau);
-        T2 *prv = cur ? bufA : bufB;
-        for (int s = 0; s < 3; ++s) {
+        T2 r = ldf<T>(d.dfs, idx);
+        T dg = (T)d.cpar[NCP * c + CP_DBASE];
+        T wo[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
           int f = d.cell_faces[4 * c + s];
-          int sg = d.cell_sgn[4 * c + s];
-          int nb = (sg > 0) ? d.face_R[f] : d.face_L[f];
+          wo[s] = (T)d.cell_sgn[4 * c + s] *
+                  (vx * (T)d.Sn[2 * f] + vy * (T)d.Sn[2 * f + 1] - (T)d.SUn[f]);
+          dg += T(0.5) * (wo[s] > T(0) ? wo[s] : T(0));
+        }
+        T ah = r.x, ab = r.y;
+        T2 *prv = cur ? bufA : bufB;
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+          if (!(mask & (2 << s))) continue;
           T2 dv;
           if (s == 0 && i > 0) dv = prev;
           else if (s == 1 && per && i == ni - 1) dv = first;
           else if (s == 2 && row > 0) dv = prv[threadIdx.x - V];
           else continue;
-          if (nb < 0 || d.status[nb] != ST_FIELD) continue;
-          T wo = (T)sg * wS_of<T>(d, f, k);
-          T cf = T(0.5) * (wo < T(0) ? wo : T(0));
+          T cf = T(0.5) * (wo[s] < T(0) ? wo[s] : T(0));
           ah -= cf * dv.x;
           ab -= cf * dv.y;
         }
@@ -725,6 +834,7 @@ __global__ void __launch_bounds__(512) k_micro_bwd(Dev d, const int *work, int V
   int row = threadIdx.x / V, v = threadIdx.x % V;
   int k = k0 + v;
   bool kval = k < d.nv;
+  T vx = kval ? dvx<T>(d, k) : T(0), vy = kval ? dvy<T>(d, k) : T(0);
   T2 prev = {0, 0}, first = {0, 0};
   int nd = ni + nj - 1;
   int cur = 0;
@@ -734,25 +844,29 @@ __global__ void __launch_bounds__(512) k_micro_bwd(Dev d, const int *work, int V
     T2 val = {0, 0};
     if (act) {
       int c = off + row * ni + i;
-      if (d.status[c] == ST_FIELD) {
+      int mask = d.cmask[c];
+      if (mask & 1) {
         size_t idx = (size_t)c * d.nvp + k;
-        T itau = (T)d.cpar[NCP * c + CP_ITAU];
-        T dg = micro_diag<T>(d, c, k, itau);
+        T dg = (T)d.cpar[NCP * c + CP_DBASE];
+        T wo[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          int f = d.cell_faces[4 * c + s];
+          wo[s] = (T)d.cell_sgn[4 * c + s] *
+                  (vx * (T)d.Sn[2 * f] + vy * (T)d.Sn[2 * f + 1] - (T)d.SUn[f]);
+          dg += T(0.5) * (wo[s] > T(0) ? wo[s] : T(0));
+        }
         T ah = 0, ab = 0;
         T2 *prv = cur ? bufA : bufB;
+#pragma unroll
         for (int s = 0; s < 4; ++s) {
-          if (s == 2) continue;
-          int f = d.cell_faces[4 * c + s];
-          int sg = d.cell_sgn[4 * c + s];
-          int nb = (sg > 0) ? d.face_R[f] : d.face_L[f];
+          if (s == 2 || !(mask & (2 << s))) continue;
           T2 dv;
           if (s == 1 && i < ni - 1) dv = prev;
           else if (s == 0 && per && i == 0) dv = first;
           else if (s == 3 && row < nj - 1) dv = prv[threadIdx.x + V];
           else continue;
-          if (nb < 0 || d.status[nb] != ST_FIELD) continue;
-          T wo = (T)sg * wS_of<T>(d, f, k);
-          T cf = T(0.5) * (wo < T(0) ? wo : T(0));
+          T cf = T(0.5) * (wo[s] < T(0) ? wo[s] : T(0));
           ah += cf * dv.x;
           ab += cf * dv.y;
         }
@@ -782,25 +896,26 @@ template <typename T> __global__ void k_moments(Dev d) {
   if (c >= d.nc) return;
   if (d.status[c] != ST_FIELD) return;
   const double *cp = d.cpar + NCP * c;
-  double rho = cp[CP_RHO], ux = cp[CP_UX], uy = cp[CP_UY], lam = cp[CP_LAM];
-  double acc[6] = {0, 0, 0, 0, 0, 0};
+  T rho = (T)cp[CP_RHO], ux = (T)cp[CP_UX], uy = (T)cp[CP_UY], lam = (T)cp[CP_LAM];
+  Acc<T> a[6];
   for (int k = lane; k < d.nv; k += 32) {
     auto fv = ldf<T>(d.f, (size_t)c * d.nvp + k);
-    double vx = d.vx[k], vy = d.vy[k], w = d.w[k];
-    V2<double> g = maxwellian<double>(rho, ux, uy, lam, vx, vy, (double)d.Keff);
-    double h = (double)fv.x, b = (double)fv.y;
-    double dh = h - g.h, db = b - g.b;
-    double v2 = 0.5 * (vx * vx + vy * vy);
-    acc[0] += w * dh;
-    acc[1] += w * vx * dh;
-    acc[2] += w * vy * dh;
-    acc[3] += w * (v2 * dh + 0.5 * db);
-    double cx = vx - ux, cy = vy - uy;
-    double e = (cx * cx + cy * cy) * h + b;
-    acc[4] += 0.5 * w * cx * e;
-    acc[5] += 0.5 * w * cy * e;
+    T vx = dvx<T>(d, k), vy = dvy<T>(d, k), w = (T)d.w[k];
+    V2<T> g = maxwellian<T>(rho, ux, uy, lam, vx, vy, (T)d.Keff);
+    T h = fv.x, b = fv.y;
+    T dh = h - g.h, db = b - g.b;
+    T v2 = T(0.5) * (vx * vx + vy * vy);
+    a[0].add(w * dh);
+    a[1].add(w * vx * dh);
+    a[2].add(w * vy * dh);
+    a[3].add(w * (v2 * dh + T(0.5) * db));
+    T cx = vx - ux, cy = vy - uy;
+    T e = (cx * cx + cy * cy) * h + b;
+    a[4].add(T(0.5) * w * cx * e);
+    a[5].add(T(0.5) * w * cy * e);
   }
-  for (int m = 0; m < 6; ++m) acc[m] = warp_sum(acc[m]);
+  double acc[6];
+  for (int m = 0; m < 6; ++m) acc[m] = warp_sum(a[m].get());
   if (lane == 0) {
     double Wn[4];
     for (int m = 0; m < 4; ++m) Wn[m] = d.Wp[4 * c + m] + acc[m];
@@ -895,34 +1010,57 @@ void launch_geometry(const Dev &d, cudaStream_t s) {
 }
 void launch_slope_geo(const Dev &d, cudaStream_t s) { k_slope_geo<<<nblk(d.nc, 256), 256, 0, s>>>(d); }
 
-template <typename T> static void flux_prep_t(const Dev &d, cudaStream_t s, int level_n) {
+void launch_ghost_gradW(const Dev &d, cudaStream_t s) {
   k_ghost<<<nblk(d.nf, 256), 256, 0, s>>>(d);
   k_gradW<<<nblk(d.nc, 256), 256, 0, s>>>(d);
-  k_face_reduce<T><<<nblk((size_t)d.nf * 32, 256), 256, 0, s>>>(d);
-  k_face_coef<T><<<nblk((size_t)d.nf * 32, 256), 256, 0, s>>>(d);
-  k_cell_macro<<<nblk(d.nc, 256), 256, 0, s>>>(d, level_n);
 }
-void launch_flux_prep(const Dev &d, cudaStream_t s, int level_n, int fp32) {
-  if (fp32) flux_prep_t<float>(d, s, level_n); else flux_prep_t<double>(d, s, level_n);
+void launch_face_reduce(const Dev &d, cudaStream_t s, int fp32) {
+  if (fp32) k_face_reduce<float><<<nblk((size_t)d.nf * 32, 256), 256, 0, s>>>(d);
+  else k_face_reduce<double><<<nblk((size_t)d.nf * 32, 256), 256, 0, s>>>(d);
+}
+void launch_face_coef(const Dev &d, cudaStream_t s, int fp32) {
+  if (fp32) {
+    k_face_scalar<float><<<nblk(d.nf, 128), 128, 0, s>>>(d);
+    k_face_coef<float><<<nblk((size_t)d.nf * 32, 256), 256, 0, s>>>(d);
+  } else {
+    k_face_scalar<double><<<nblk(d.nf, 128), 128, 0, s>>>(d);
+    k_face_coef<double><<<nblk((size_t)d.nf * 32, 256), 256, 0, s>>>(d);
+  }
+}
+void launch_cell_macro(const Dev &d, cudaStream_t s, int level_n) {
+  k_cell_macro<<<nblk(d.nc, 256), 256, 0, s>>>(d, level_n);
 }
 void launch_cell_params(const Dev &d, cudaStream_t s, const double *W, double *out) {
   k_cell_params<<<nblk(d.nc, 256), 256, 0, s>>>(d, W, out);
 }
-void launch_macro_sweep(const Dev &d, cudaStream_t s, int rows) {
-  k_macro_sweep<<<d.nblocks, rows, 2 * 4 * rows * sizeof(double), s>>>(d);
-}
-void launch_micro(const Dev &d, cudaStream_t s, const int *work, int nwork, int V, int rows,
-                  int first_iter, int fp32) {
-  int threads = rows * V;
+void launch_macro_sweep(const Dev &d, cudaStream_t s, int rows, int fp32) {
   if (fp32) {
-    size_t sm = 2 * threads * sizeof(float2);
-    k_micro_fwd<float><<<nwork, threads, sm, s>>>(d, work, V, first_iter);
-    k_micro_bwd<float><<<nwork, threads, sm, s>>>(d, work, V);
+    float *rec = reinterpret_cast<float *>(d.mrec);
+    k_macro_prep<float><<<nblk(d.nc, 256), 256, 0, s>>>(d, rec);
+    k_macro_sweep<float><<<d.nblocks, rows, 2 * 4 * rows * sizeof(double), s>>>(d, rec);
   } else {
-    size_t sm = 2 * threads * sizeof(double2);
-    k_micro_fwd<double><<<nwork, threads, sm, s>>>(d, work, V, first_iter);
-    k_micro_bwd<double><<<nwork, threads, sm, s>>>(d, work, V);
+    double *rec = reinterpret_cast<double *>(d.mrec);
+    k_macro_prep<double><<<nblk(d.nc, 256), 256, 0, s>>>(d, rec);
+    k_macro_sweep<double><<<d.nblocks, rows, 2 * 4 * rows * sizeof(double), s>>>(d, rec);
   }
+  k_macro_post<<<nblk(d.nc, 256), 256, 0, s>>>(d);
+}
+void launch_rhs(const Dev &d, cudaStream_t s, int first_iter, int fp32) {
+  size_t n = (size_t)d.nc * d.nvp;
+  if (fp32) k_rhs<float><<<nblk(n, 256), 256, 0, s>>>(d, first_iter);
+  else k_rhs<double><<<nblk(n, 256), 256, 0, s>>>(d, first_iter);
+}
+void launch_micro_fwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int V, int rows,
+                      int fp32) {
+  int threads = rows * V;
+  if (fp32) k_micro_fwd<float><<<nwork, threads, 2 * threads * sizeof(float2), s>>>(d, work, V);
+  else k_micro_fwd<double><<<nwork, threads, 2 * threads * sizeof(double2), s>>>(d, work, V);
+}
+void launch_micro_bwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int V, int rows,
+                      int fp32) {
+  int threads = rows * V;
+  if (fp32) k_micro_bwd<float><<<nwork, threads, 2 * threads * sizeof(float2), s>>>(d, work, V);
+  else k_micro_bwd<double><<<nwork, threads, 2 * threads * sizeof(double2), s>>>(d, work, V);
 }
 void launch_moments(const Dev &d, cudaStream_t s, int fp32) {
   if (fp32) k_moments<float><<<nblk((size_t)d.nc * 32, 256), 256, 0, s>>>(d);

@@ -7,17 +7,23 @@ namespace ugks {
 void launch_move_nodes(const Dev &d, cudaStream_t s);
 void launch_geometry(const Dev &d, cudaStream_t s);          // 3 kernels
 void launch_slope_geo(const Dev &d, cudaStream_t s);
-void launch_flux_prep(const Dev &d, cudaStream_t s, int level_n, int fp32);   // 5 kernels
+void launch_ghost_gradW(const Dev &d, cudaStream_t s);                      // 2 kernels
+void launch_face_reduce(const Dev &d, cudaStream_t s, int fp32);
+void launch_face_coef(const Dev &d, cudaStream_t s, int fp32);
+void launch_cell_macro(const Dev &d, cudaStream_t s, int level_n);
 void launch_cell_params(const Dev &d, cudaStream_t s, const double *W, double *out);
-void launch_macro_sweep(const Dev &d, cudaStream_t s, int rows);
-void launch_micro(const Dev &d, cudaStream_t s, const int *work, int nwork, int V, int rows,
-                  int first_iter, int fp32);                  // 2 kernels
+void launch_macro_sweep(const Dev &d, cudaStream_t s, int rows, int fp32);
+void launch_rhs(const Dev &d, cudaStream_t s, int first_iter, int fp32);
+void launch_micro_fwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int V, int rows,
+                      int fp32);
+void launch_micro_bwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int V, int rows,
+                      int fp32);
 void launch_moments(const Dev &d, cudaStream_t s, int fp32);
 void launch_init_state(const Dev &d, cudaStream_t s, const double *prim, int fp32);
 void launch_flux_div_all(const Dev &d, cudaStream_t s, double *D, int fp32);
 void launch_wall_loads(const Dev &d, cudaStream_t s);
 void launch_f_convert(const Dev &d, cudaStream_t s, double *out, const double *in, int fp32);
 void launch_connect(const Dev &d, cudaStream_t s, int *prev_status, const int *blk_order,
-                    int *n_orphan);                           // 4 kernels
+                    int *n_orphan);                           // 7 kernels
 void launch_interp(const Dev &d, cudaStream_t s, const int *list, int n, int fp32);  // 2 kernels
 }  // namespace ugks

@@ -86,6 +86,111 @@ __device__ __forceinline__ bool in_layer(const int *bi, int i, int j, int L) {
   return false;
 }
 
+// ---------------------------------------------------------------- bins
+// Per block a uniform grid of bins over a box containing the block at
+// t^{n+1}; every cell is registered in the bins its bounding box overlaps.
+// A point lies in the bin (floor((x-x0)/hx), floor((y-y0)/hy)); a cell that
+// contains the point overlaps that bin (floor is monotone), so the minimum
+// index among the bin's candidates that contain the point equals the minimum
+// over all cells: same result as a scan of the whole block.
+__device__ __forceinline__ void bin_range(const Dev &d, int b, double lo, double hi, int axis,
+                                          int &i0, int &i1) {
+  const double *g = d.bin_geo + 4 * b;
+  int n = d.bin_dim[3 * b + axis];
+  double x0 = g[axis], ih = g[2 + axis];
+  double a = floor((lo - x0) * ih), c = floor((hi - x0) * ih);
+  i0 = a < 0.0 ? 0 : (a > n - 1 ? n - 1 : (int)a);
+  i1 = c < 0.0 ? 0 : (c > n - 1 ? n - 1 : (int)c);
+}
+
+__device__ __forceinline__ int bin_of(const Dev &d, int b, double x, double y) {
+  const double *g = d.bin_geo + 4 * b;
+  int nx = d.bin_dim[3 * b], ny = d.bin_dim[3 * b + 1];
+  double a = floor((x - g[0]) * g[2]), c = floor((y - g[1]) * g[3]);
+  if (a < 0.0 || c < 0.0 || a > nx - 1 || c > ny - 1) return -1;
+  return d.bin_dim[3 * b + 2] + (int)c * nx + (int)a;
+}
+
+__global__ void k_bin_count(Dev d) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.nc) return;
+  int b = d.cell_block[c];
+  const int *nd = d.cell_nodes + 4 * c;
+  double xl = d.X_new[2 * nd[0]], xh = xl, yl = d.X_new[2 * nd[0] + 1], yh = yl;
+  for (int v = 1; v < 4; ++v) {
+    double x = d.X_new[2 * nd[v]], y = d.X_new[2 * nd[v] + 1];
+    xl = fmin(xl, x); xh = fmax(xh, x); yl = fmin(yl, y); yh = fmax(yh, y);
+  }
+  int ix0, ix1, iy0, iy1;
+  bin_range(d, b, xl, xh, 0, ix0, ix1);
+  bin_range(d, b, yl, yh, 1, iy0, iy1);
+  int nx = d.bin_dim[3 * b], base = d.bin_dim[3 * b + 2];
+  for (int iy = iy0; iy <= iy1; ++iy)
+    for (int ix = ix0; ix <= ix1; ++ix) atomicAdd(&d.bin_cnt[base + iy * nx + ix], 1);
+}
+
+// exclusive scan of the bin counts (one CTA), cursor = start
+__global__ void k_bin_scan(Dev d) {
+  __shared__ int part[1024];
+  int n = d.nbins;
+  int per = (n + blockDim.x - 1) / blockDim.x;
+  int lo = threadIdx.x * per, hi = min(n, lo + per);
+  int s = 0;
+  for (int i = lo; i < hi; ++i) s += d.bin_cnt[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int t = 0; t < (int)blockDim.x; ++t) { int v = part[t]; part[t] = run; run += v; }
+    d.bin_start[n] = run;
+    if (run > d.bin_cap) atomicOr(d.err, EF_BINS);
+  }
+  __syncthreads();
+  int run = part[threadIdx.x];
+  for (int i = lo; i < hi; ++i) {
+    int v = d.bin_cnt[i];
+    d.bin_start[i] = run;
+    d.bin_cnt[i] = run;            // reused as the fill cursor
+    run += v;
+  }
+}
+
+__global__ void k_bin_fill(Dev d) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.nc) return;
+  int b = d.cell_block[c];
+  const int *nd = d.cell_nodes + 4 * c;
+  double xl = d.X_new[2 * nd[0]], xh = xl, yl = d.X_new[2 * nd[0] + 1], yh = yl;
+  for (int v = 1; v < 4; ++v) {
+    double x = d.X_new[2 * nd[v]], y = d.X_new[2 * nd[v] + 1];
+    xl = fmin(xl, x); xh = fmax(xh, x); yl = fmin(yl, y); yh = fmax(yh, y);
+  }
+  int ix0, ix1, iy0, iy1;
+  bin_range(d, b, xl, xh, 0, ix0, ix1);
+  bin_range(d, b, yl, yh, 1, iy0, iy1);
+  int nx = d.bin_dim[3 * b], base = d.bin_dim[3 * b + 2];
+  for (int iy = iy0; iy <= iy1; ++iy)
+    for (int ix = ix0; ix <= ix1; ++ix) {
+      int pos = atomicAdd(&d.bin_cnt[base + iy * nx + ix], 1);
+      if (pos < d.bin_cap) d.bin_items[pos] = c;
+    }
+}
+
+// lowest-index cell of block b containing (x, y) among the cells accepted by
+// `ok` (bins guarantee the same answer as a scan of the block)
+template <typename Pred>
+__device__ int first_containing(const Dev &d, int b, double x, double y, Pred ok) {
+  int bin = bin_of(d, b, x, y);
+  if (bin < 0) return -1;
+  int best = 0x7fffffff;
+  int q1 = min(d.bin_start[bin + 1], d.bin_cap);
+  for (int q = d.bin_start[bin]; q < q1; ++q) {
+    int c = d.bin_items[q];
+    if (c < best && ok(c) && inside_quad(d, c, x, y)) best = c;
+  }
+  return best == 0x7fffffff ? -1 : best;
+}
+
 // node classification (one thread per node)
 __global__ void k_node_classify(Dev d) {
   int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -101,14 +206,12 @@ __global__ void k_node_classify(Dev d) {
       break;
     }
     const int *bi = d.blk_info + 8 * b;
-    int ni = bi[0], nj = bi[1], L = bi[4] + bi[5];
+    int ni = bi[0], L = bi[4] + bi[5];
     int c0 = d.cell_off[b];
-    bool hit = false;
-    for (int j = 0; j < nj && !hit; ++j)
-      for (int i = 0; i < ni; ++i) {
-        if (in_layer(bi, i, j, L)) continue;
-        if (inside_quad(d, c0 + j * ni + i, x, y)) { hit = true; break; }
-      }
+    bool hit = first_containing(d, b, x, y, [&](int c) {
+      int loc = c - c0;
+      return !in_layer(bi, loc % ni, loc / ni, L);
+    }) >= 0;
     if (hit) {
       double db = wall_dist2(d, b, x, y);
       const int *bz = d.blk_info + 8 * z;
@@ -171,11 +274,8 @@ __global__ void k_donor(Dev d, const int *fresh_flag, const int *blk_order, int 
     for (int o = 0; o < d.nblocks && found < 0; ++o) {
       int b = blk_order[o];
       if (b == own) continue;
-      int c0 = d.cell_off[b], c1 = d.cell_off[b + 1];
-      for (int e = c0; e < c1; ++e) {
-        if (d.status[e] != cls) continue;
-        if (inside_quad(d, e, x, y)) { found = e; break; }
-      }
+      int e = first_containing(d, b, x, y, [&](int q) { return d.status[q] == cls; });
+      if (e >= 0) found = e;
     }
   }
   if (found < 0) {
@@ -257,6 +357,10 @@ static inline int nblk(size_t n, int b) { return (int)((n + b - 1) / b); }
 
 void launch_connect(const Dev &d, cudaStream_t s, int *prev_status, const int *blk_order,
                     int *n_orphan) {
+  cudaMemsetAsync(d.bin_cnt, 0, sizeof(int) * d.nbins, s);
+  k_bin_count<<<nblk(d.nc, 256), 256, 0, s>>>(d);
+  k_bin_scan<<<1, 1024, 0, s>>>(d);
+  k_bin_fill<<<nblk(d.nc, 256), 256, 0, s>>>(d);
   k_node_classify<<<nblk(d.nn, 128), 128, 0, s>>>(d);
   k_cell_classify<<<nblk(d.nc, 256), 256, 0, s>>>(d);
   k_cell_buffer<<<nblk(d.nc, 256), 256, 0, s>>>(d, prev_status);

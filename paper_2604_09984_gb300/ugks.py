@@ -61,7 +61,11 @@ SYMBOLS = {
     "ugks_get_connectivity": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "ugks_get_geometry": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ugks_launch_count": (c_int64, [c_void_p]),
+    "ugks_profile_enable": (c_int, [c_void_p, c_int]),
+    "ugks_profile_read": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int64), c_int]),
 }
+PROF_GROUPS = ["geometry", "connect", "interp", "cell", "face_reduce", "face_coef",
+               "macro_sweep", "micro_fwd", "micro_bwd", "moments", "rhs"]
 
 _lib = None
 
@@ -268,3 +272,12 @@ class Solver:
 
     def launch_count(self):
         return int(self.lib.ugks_launch_count(self.ctx))
+
+    def profile(self, on: bool):
+        self._check(self.lib.ugks_profile_enable(self.ctx, int(bool(on))))
+
+    def profile_read(self, reset=True):
+        ms = (c_double * len(PROF_GROUPS))()
+        n = (c_int64 * len(PROF_GROUPS))()
+        self._check(self.lib.ugks_profile_read(self.ctx, ms, n, int(bool(reset))))
+        return {g: (float(ms[i]), int(n[i])) for i, g in enumerate(PROF_GROUPS)}

@@ -67,7 +67,7 @@ int cuda_check(ugks_ctx *c, cudaError_t e, const char *what) {
   } while (0)
 
 struct Sizes {
-  int nc = 0, nf = 0, nn = 0, nv = 0, nvp = 0, nseg = 0, nring = 0, max_nj = 0;
+  int nc = 0, nf = 0, nn = 0, nv = 0, nvp = 0, nseg = 0, nring = 0, max_nj = 0, ntiles = 0;
 };
 
 int validate(const ugks_params *p, int nb, const ugks_block_desc *b, Sizes &s, std::string &why) {
@@ -97,6 +97,7 @@ int validate(const ugks_params *p, int nb, const ugks_block_desc *b, Sizes &s, s
     s.nn += (B.ni + 1) * (B.nj + 1);
     s.nf += B.nj * (B.periodic_i ? B.ni : B.ni + 1) + B.ni * (B.nj + 1);
     if (B.nj > s.max_nj) s.max_nj = B.nj;
+    s.ntiles += tile_count(B.ni, B.nj);
   }
   return UGKS_OK;
 }
@@ -203,6 +204,7 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int nwork, int cap_in
   d.bin_cnt = c.take<int>((size_t)s.nc + nb + 1);
   d.bin_start = c.take<int>((size_t)s.nc + nb + 2);
   d.bin_items = c.take<int>(bin_capacity(s));
+  d.tiles = c.take<int>(3 * (size_t)s.ntiles);
   d.err = c.take<int>(4);
   (void)nwork;
   c.take<int>(2 * (size_t)nwork + 2);   // micro-sweep work list
@@ -421,7 +423,7 @@ void flux_prep(ugks_ctx *ctx, int level_n) {
   Dev &d = ctx->d;
   cudaStream_t s = ctx->st;
   { Prof p(ctx, UGKS_PROF_CELL); launch_ghost_gradW(d, s); }
-  { Prof p(ctx, UGKS_PROF_FACE_REDUCE); launch_face_reduce(d, s, ctx->fp32); }
+  { Prof p(ctx, UGKS_PROF_FACE_REDUCE); launch_face_reduce_tile(d, s, ctx->fp32); }
   { Prof p(ctx, UGKS_PROF_FACE_COEF); launch_face_coef(d, s, ctx->fp32); }
   { Prof p(ctx, UGKS_PROF_CELL); launch_cell_macro(d, s, level_n); }
   ctx->launches += 6;
@@ -647,6 +649,14 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
   std::vector<int> work;
   for (int b = 0; b < nblocks; ++b)
     for (int k0 = 0; k0 < s.nv; k0 += ctx->V) { work.push_back(b); work.push_back(k0); }
+  std::vector<int> tiles;
+  for (int b = 0; b < nblocks; ++b) {
+    std::vector<int> org(2 * (size_t)tile_count(blocks[b].ni, blocks[b].nj));
+    tile_origins(blocks[b].ni, blocks[b].nj, org.data());
+    for (size_t q = 0; q < org.size(); q += 2) { tiles.push_back(b); tiles.push_back(org[q]); tiles.push_back(org[q + 1]); }
+  }
+  d.ntiles = s.ntiles;
+  tile_setup();
   if ((r = up(ctx, (void *)d.vx, vx))) return r;
   if ((r = up(ctx, (void *)d.vy, vy))) return r;
   if ((r = up(ctx, (void *)d.w, w))) return r;
@@ -679,6 +689,7 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
   if ((r = up(ctx, (void *)d.blk_info, T.blk_info))) return r;
   if ((r = up(ctx, (void *)ctx->blk_order, order))) return r;
   if ((r = up(ctx, (void *)ctx->work, work))) return r;
+  if ((r = up(ctx, (void *)d.tiles, tiles))) return r;
   if ((r = up(ctx, (void *)d.X_ref, X))) return r;
   // identity placement at t = 0
   ctx->h_affine.assign(6 * (size_t)nblocks, 0.0);
@@ -764,7 +775,7 @@ int ugks_step(ugks_ctx *ctx, double dt, int n_inner) {
       flux_prep(ctx, 0);                       // Step 3
     }
     { Prof p(ctx, UGKS_PROF_MACRO_SWEEP); launch_macro_sweep(d, s, ctx->max_nj, fp); }          // Step 4
-    { Prof p(ctx, UGKS_PROF_RHS); launch_rhs(d, s, it == 0, fp); }                         // Step 5
+    { Prof p(ctx, UGKS_PROF_RHS); launch_rhs_tile(d, s, it == 0, fp); }                    // Steps 3, 5
     { Prof p(ctx, UGKS_PROF_MICRO_FWD); launch_micro_fwd(d, s, ctx->work, ctx->nwork, ctx->V, ctx->max_nj, fp); }  // Step 6
     { Prof p(ctx, UGKS_PROF_MICRO_BWD); launch_micro_bwd(d, s, ctx->work, ctx->nwork, ctx->V, ctx->max_nj, fp); }
     { Prof p(ctx, UGKS_PROF_MOMENTS); launch_moments(d, s, fp); }                          // Step 7

@@ -105,6 +105,8 @@ struct Dev {
   int *bin_cnt, *bin_start;  // nbins, nbins+1
   int *bin_items;            // bin_cap
   int nbins, bin_cap;
+  const int *tiles;          // ntiles*3: block, i0, j0 of the 8x8 cell tiles
+  int ntiles;
   int *err;                  // error flags
 };
 

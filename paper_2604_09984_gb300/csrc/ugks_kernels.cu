@@ -407,6 +407,16 @@ template <typename T> __global__ void k_face_scalar(Dev d) {
   par[FP_PREF] = 4.0 * (1.0 - d.Pr) * p0.lam * p0.lam / (5.0 * p0.rho);
   par[FP_LAMW] = wall ? 1.0 / (2.0 * d.face_Tw[fid]) : 0.0;
   par[FP_RHOW] = 0.0;
+  par[FP_SNX] = d.Sn[2 * fid];
+  par[FP_SNY] = d.Sn[2 * fid + 1];
+  par[FP_SUN] = d.SUn[fid];
+  {
+    double sh = (double)d.face_shiftL[fid];
+    par[FP_DXLX] = d.xf[2 * fid] - (d.xc[2 * L] + sh * d.period[2 * L]);
+    par[FP_DXLY] = d.xf[2 * fid + 1] - (d.xc[2 * L + 1] + sh * d.period[2 * L + 1]);
+    par[FP_DXRX] = (R >= 0) ? d.xf[2 * fid] - d.xc[2 * R] : 0.0;
+    par[FP_DXRY] = (R >= 0) ? d.xf[2 * fid + 1] - d.xc[2 * R + 1] : 0.0;
+  }
   for (int m = 0; m < NFP; ++m) { P[m] = par[m]; PT[m] = (T)par[m]; }
   // Gamma from the mean of the two cells' W (boundary: the cell)
   double Wf[4];

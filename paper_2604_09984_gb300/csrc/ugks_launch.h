@@ -26,4 +26,10 @@ void launch_f_convert(const Dev &d, cudaStream_t s, double *out, const double *i
 void launch_connect(const Dev &d, cudaStream_t s, int *prev_status, const int *blk_order,
                     int *n_orphan);                           // 7 kernels
 void launch_interp(const Dev &d, cudaStream_t s, const int *list, int n, int fp32);  // 2 kernels
+// tiled kernels (ugks_tile.cu)
+void tile_setup();
+int tile_count(int ni, int nj);
+void tile_origins(int ni, int nj, int *out);
+void launch_rhs_tile(const Dev &d, cudaStream_t s, int first_iter, int fp32);
+void launch_face_reduce_tile(const Dev &d, cudaStream_t s, int fp32);
 }  // namespace ugks

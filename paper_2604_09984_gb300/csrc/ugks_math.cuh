@@ -66,7 +66,11 @@ enum {
   FP_AX = 6,  FP_AY = 10, FP_AT = 14,
   FP_Q1 = 18, FP_Q2, FP_Q3, FP_Q4, FP_Q5,
   FP_RHOW = 23, FP_LAMW, FP_UFX, FP_UFY, FP_PREF,
-  NFP = 28
+  // face geometry for the tiled kernels: S n, S U.n, and the vectors from the
+  // (periodic image of the) L cell centre and from the R cell centre to the
+  // face centre
+  FP_SNX = 28, FP_SNY, FP_SUN, FP_DXLX, FP_DXLY, FP_DXRX, FP_DXRY,
+  NFP = 36
 };
 
 // Time integrals q_m = int_0^dts c_m(t) dt (Eq. fullSolution), x = dts/tau;

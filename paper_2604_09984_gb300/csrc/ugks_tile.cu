@@ -1,0 +1,452 @@
+// ugks_tile.cu -- shared-memory tiled kernels for the two velocity-resolved
+// passes over f of every inner iteration (arXiv 2604.09984 Sec. 2.2, Steps 3
+// and 5):
+//   k_face_reduce_tile  velocity sums per face: W0 of the interface
+//                       equilibrium and the f-dependent parts of the macro
+//                       flux (Eq. macroscopicFlux);
+//   k_rhs_tile          flux divergence D = sum_faces S F_hat (Eqs.
+//                       microscopicFlux, fullSolution, wall condition) and
+//                       the micro residual r (reading R4).
+// A CTA stages f of an 8x8 cell tile plus a two-cell halo (ghost cells hold
+// the Maxwellian of their ghost state) for 32 velocities in shared memory,
+// reconstructs from there and evaluates each face of the tile once (one warp
+// per tile row for i-faces, per tile column for j-faces).  Lane = velocity.
+#include "ugks_internal.cuh"
+#include "ugks_launch.h"
+
+namespace ugks {
+
+constexpr int TX = 8, TY = 8, RW = TX + 4, RH = TY + 4, NR = RW * RH, VK = 32;
+constexpr int TTHREADS = 256;   // 8 warps: one per tile row / column
+
+// region cell (i, j) of block b -> cell id (>= 0), ghost (-2 - face id) or
+// none (-1).  Periodic blocks wrap in i.
+__device__ __forceinline__ int region_gid(const Dev &d, const int *bi, int off, int i, int j) {
+  int ni = bi[0], nj = bi[1], per = bi[2];
+  if (per) i = ((i % ni) + ni) % ni;
+  bool iin = i >= 0 && i < ni, jin = j >= 0 && j < nj;
+  if (iin && jin) return off + j * ni + i;
+  int c = -1, s = -1;
+  if (jin && !iin) {
+    if (i == -1) { c = off + j * ni; s = 0; }
+    else if (i == ni) { c = off + j * ni + ni - 1; s = 1; }
+  } else if (iin && !jin) {
+    if (j == -1) { c = off + i; s = 2; }
+    else if (j == nj) { c = off + (nj - 1) * ni + i; s = 3; }
+  }
+  if (c < 0) return -1;
+  if (d.nb_kind[4 * c + s] == NB_GHOST) return -2 - d.nb_id[4 * c + s];
+  return -1;
+}
+
+template <typename T> struct TileSmem {
+  typedef typename Vec2<T>::type T2;
+  T2 *F;        // NR * VK
+  int *gid;     // NR
+  int *flags;   // NR: slope flags | status << 8
+  T *jinv;      // NR * 4
+  T *gprim;     // NR * 4 ghost (rho, ux, uy, lam)
+  __host__ __device__ static constexpr size_t bytes() {
+    return sizeof(T2) * NR * VK + sizeof(int) * 2 * NR + sizeof(T) * 8 * NR;
+  }
+  __device__ void carve(unsigned char *p) {
+    F = reinterpret_cast<T2 *>(p);
+    p += sizeof(T2) * NR * VK;
+    jinv = reinterpret_cast<T *>(p);
+    p += sizeof(T) * 4 * NR;
+    gprim = reinterpret_cast<T *>(p);
+    p += sizeof(T) * 4 * NR;
+    gid = reinterpret_cast<int *>(p);
+    p += sizeof(int) * NR;
+    flags = reinterpret_cast<int *>(p);
+  }
+};
+
+// metadata of the region cells (all threads)
+template <typename T>
+__device__ __forceinline__ void tile_meta(const Dev &d, TileSmem<T> &S, const int *bi, int off, int i0,
+                                          int j0) {
+  for (int r = threadIdx.x; r < NR; r += blockDim.x) {
+    int rx = r % RW, ry = r / RW;
+    int g = region_gid(d, bi, off, i0 - 2 + rx, j0 - 2 + ry);
+    S.gid[r] = g;
+    if (g >= 0) {
+      S.flags[r] = d.slope_flags[g] | (d.status[g] << 8);
+      for (int m = 0; m < 4; ++m) S.jinv[4 * r + m] = (T)d.jinv[4 * g + m];
+    } else {
+      S.flags[r] = ST_HOLE << 8;
+      if (g <= -2) {
+        Prim p = primitive(d.ghostW + 4 * (-2 - g), d.Keff);
+        S.gprim[4 * r] = (T)p.rho; S.gprim[4 * r + 1] = (T)p.ux;
+        S.gprim[4 * r + 2] = (T)p.uy; S.gprim[4 * r + 3] = (T)p.lam;
+      }
+    }
+  }
+}
+
+// f of the region for velocity chunk kbase (warp w loads cells w, w+8, ...)
+template <typename T>
+__device__ __forceinline__ void tile_load_f(const Dev &d, TileSmem<T> &S, int k, bool kv, T vx, T vy) {
+  typedef typename Vec2<T>::type T2;
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r = w; r < NR; r += nw) {
+    int g = S.gid[r];
+    T2 v = {T(0), T(0)};
+    if (kv) {
+      if (g >= 0) {
+        v = ldf<T>(d.f, (size_t)g * d.nvp + k);
+      } else if (g <= -2) {
+        const T *p = S.gprim + 4 * r;
+        V2<T> m = maxwellian<T>(p[0], p[1], p[2], p[3], vx, vy, (T)d.Keff);
+        v.x = m.h;
+        v.y = m.b;
+      }
+    }
+    S.F[r * VK + lane] = v;
+  }
+}
+
+// limited gradient of region cell r (a real cell) at this lane (reading R1)
+template <typename T>
+__device__ __forceinline__ void tile_grad(const TileSmem<T> &S, int r, int lane, V2<T> fc, V2<T> &gx,
+                                          V2<T> &gy) {
+  int fl = S.flags[r];
+  V2<T> s[2];
+#pragma unroll
+  for (int dir = 0; dir < 2; ++dir) {
+    int cs = (fl >> (2 * dir)) & 3;
+    int st = dir == 0 ? 1 : RW;
+    V2<T> o = {T(0), T(0)};
+    if (cs == SL_BOTH) {
+      auto m = S.F[(r - st) * VK + lane], p = S.F[(r + st) * VK + lane];
+      o.h = vanleer<T>(fc.h - m.x, p.x - fc.h);
+      o.b = vanleer<T>(fc.b - m.y, p.y - fc.b);
+    } else if (cs == SL_P) {
+      auto p = S.F[(r + st) * VK + lane];
+      o.h = p.x - fc.h;
+      o.b = p.y - fc.b;
+    } else if (cs == SL_M) {
+      auto m = S.F[(r - st) * VK + lane];
+      o.h = fc.h - m.x;
+      o.b = fc.b - m.y;
+    }
+    s[dir] = o;
+  }
+  const T *J = S.jinv + 4 * r;
+  gx.h = J[0] * s[0].h + J[1] * s[1].h;
+  gx.b = J[0] * s[0].b + J[1] * s[1].b;
+  gy.h = J[2] * s[0].h + J[3] * s[1].h;
+  gy.b = J[2] * s[0].b + J[3] * s[1].b;
+}
+
+// upwind face value and w.grad f for face fid between region cells A and B
+// (walls: interior side, incident velocities only).  Returns false when the
+// face contributes nothing at this velocity (reflected wall velocities).
+template <typename T>
+__device__ __forceinline__ void tile_upwind(const Dev &d, const TileSmem<T> &S, const T *P, int kind,
+                                            int Lr, int Rr, int lane, T vx, T vy, T wS, V2<T> &ff,
+                                            V2<T> &wg) {
+  T wx = vx - P[FP_UFX], wy = vy - P[FP_UFY];
+  bool useL = (kind == BC_WALL) || wS > T(0), useR = (kind != BC_WALL) && wS < T(0);
+  V2<T> fL = {0, 0}, fR = {0, 0}, gL = {0, 0}, gR = {0, 0};
+  if (!useR) {
+    auto v = S.F[Lr * VK + lane];
+    V2<T> fc = {v.x, v.y}, gx, gy;
+    tile_grad<T>(S, Lr, lane, fc, gx, gy);
+    T dx = P[FP_DXLX], dy = P[FP_DXLY];
+    fL = {fc.h + dx * gx.h + dy * gy.h, fc.b + dx * gx.b + dy * gy.b};
+    gL = {wx * gx.h + wy * gy.h, wx * gx.b + wy * gy.b};
+  }
+  if (!useL) {
+    auto v = S.F[Rr * VK + lane];
+    V2<T> fc = {v.x, v.y};
+    if (S.gid[Rr] >= 0) {
+      V2<T> gx, gy;
+      tile_grad<T>(S, Rr, lane, fc, gx, gy);
+      T dx = P[FP_DXRX], dy = P[FP_DXRY];
+      fR = {fc.h + dx * gx.h + dy * gy.h, fc.b + dx * gx.b + dy * gy.b};
+      gR = {wx * gx.h + wy * gy.h, wx * gx.b + wy * gy.b};
+    } else {
+      fR = fc;       // ghost Maxwellian, no gradient
+    }
+  }
+  if (useL) {
+    ff = fL; wg = gL;
+  } else if (useR) {
+    ff = fR; wg = gR;
+  } else {
+    ff = {T(0.5) * (fL.h + fR.h), T(0.5) * (fL.b + fR.b)};
+    wg = {T(0.5) * (gL.h + gR.h), T(0.5) * (gL.b + gR.b)};
+  }
+}
+
+// S * F_hat of face fid at this lane (oriented along the face normal)
+template <typename T>
+__device__ __forceinline__ V2<T> tile_face_flux(const Dev &d, const TileSmem<T> &S, int fid, int A,
+                                                int B, int lane, T vx, T vy) {
+  int kind = d.face_kind[fid];
+  if (kind == BC_OVERSET) return {T(0), T(0)};
+  const T *P = fparT<T>(d, fid);
+  int Lr = (S.gid[A] == d.face_L[fid]) ? A : B;
+  int Rr = (Lr == A) ? B : A;
+  T wS = vx * P[FP_SNX] + vy * P[FP_SNY] - P[FP_SUN];
+  if (kind == BC_WALL && !(wS > T(0))) {
+    T wx = vx - P[FP_UFX], wy = vy - P[FP_UFY];
+    T lw = P[FP_LAMW];
+    T Hw = P[FP_RHOW] * (lw / T(M_PI)) * r_exp<T>(-lw * (wx * wx + wy * wy));
+    return {wS * Hw, wS * (T)d.Keff / (T(2) * lw) * Hw};
+  }
+  V2<T> ff, wg;
+  tile_upwind<T>(d, S, P, kind, Lr, Rr, lane, vx, vy, wS, ff, wg);
+  V2<T> I = interface_integral<T>(P, vx, vy, ff, wg, (T)d.Keff, (T)d.Kint, (T)d.Pr);
+  return {wS * I.h, wS * I.b};
+}
+
+__device__ __forceinline__ int cell_status(const TileSmem<float> &S, int r) { return S.flags[r] >> 8; }
+__device__ __forceinline__ int cell_status(const TileSmem<double> &S, int r) { return S.flags[r] >> 8; }
+
+// ------------------------------------------------------------ residual
+template <typename T> __global__ void __launch_bounds__(TTHREADS) k_rhs_tile(Dev d, int first_iter) {
+  typedef typename Vec2<T>::type T2;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TileSmem<T> S;
+  S.carve(smraw);
+  T2 *Ds = reinterpret_cast<T2 *>(smraw + TileSmem<T>::bytes());   // TX*TY*VK
+  int tile = blockIdx.x % d.ntiles, vc = blockIdx.x / d.ntiles;
+  int b = d.tiles[3 * tile], i0 = d.tiles[3 * tile + 1], j0 = d.tiles[3 * tile + 2];
+  const int *bi = d.blk_info + 8 * b;
+  int ni = bi[0], nj = bi[1], off = d.cell_off[b];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int k = vc * VK + lane;
+  bool kv = k < d.nv;
+  T vx = kv ? dvx<T>(d, k) : T(0), vy = kv ? dvy<T>(d, k) : T(0);
+  tile_meta<T>(d, S, bi, off, i0, j0);
+  __syncthreads();
+  tile_load_f<T>(d, S, k, kv, vx, vy);
+  __syncthreads();
+  // i-faces of tile row w
+  {
+    int ty = w, j = j0 + ty;
+    T2 carry = {T(0), T(0)};
+    if (j < nj) {
+      for (int x = 0; x <= TX; ++x) {
+        int i = i0 + x;
+        if (i > ni) break;
+        int A = (x + 1) + (ty + 2) * RW, B = A + 1;
+        bool lin = x >= 1, rin = x < TX && i < ni;
+        bool need = (lin && cell_status(S, A) == ST_FIELD) || (rin && cell_status(S, B) == ST_FIELD);
+        V2<T> F = {T(0), T(0)};
+        if (need && kv) {
+          int fid = (i < ni) ? d.cell_faces[4 * (off + j * ni + i) + 0]
+                             : d.cell_faces[4 * (off + j * ni + ni - 1) + 1];
+          F = tile_face_flux<T>(d, S, fid, A, B, lane, vx, vy);
+          T sA = (S.gid[A] == d.face_L[fid]) ? T(1) : T(-1);
+          if (lin) { carry.x += sA * F.h; carry.y += sA * F.b; }
+          if (lin) Ds[(ty * TX + x - 1) * VK + lane] = carry;
+          carry.x = -sA * F.h;     // the other side sees the opposite orientation
+          carry.y = -sA * F.b;
+        } else {
+          if (lin) Ds[(ty * TX + x - 1) * VK + lane] = carry;
+          carry.x = T(0);
+          carry.y = T(0);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // j-faces of tile column w
+  {
+    int tx = w, i = i0 + tx;
+    if (i < ni) {
+      for (int y = 0; y <= TY; ++y) {
+        int j = j0 + y;
+        if (j > nj) break;
+        int A = (tx + 2) + (y + 1) * RW, B = A + RW;
+        bool lin = y >= 1, rin = y < TY && j < nj;
+        bool need = (lin && cell_status(S, A) == ST_FIELD) || (rin && cell_status(S, B) == ST_FIELD);
+        if (!(need && kv)) continue;
+        int fid = (j < nj) ? d.cell_faces[4 * (off + j * ni + i) + 2]
+                           : d.cell_faces[4 * (off + (nj - 1) * ni + i) + 3];
+        V2<T> F = tile_face_flux<T>(d, S, fid, A, B, lane, vx, vy);
+        T sA = (S.gid[A] == d.face_L[fid]) ? T(1) : T(-1);
+        if (lin) {
+          T2 &q = Ds[((y - 1) * TX + tx) * VK + lane];
+          q.x += sA * F.h;
+          q.y += sA * F.b;
+        }
+        if (rin) {
+          T2 &q = Ds[(y * TX + tx) * VK + lane];
+          q.x -= sA * F.h;
+          q.y -= sA * F.b;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // residual of the tile cells of row w
+  if (!kv) return;
+  int ty = w, j = j0 + ty;
+  if (j >= nj) return;
+  T idt = (T)(1.0 / d.dt);
+  for (int x = 0; x < TX; ++x) {
+    int i = i0 + x;
+    if (i >= ni) break;
+    int r = (x + 2) + (ty + 2) * RW;
+    if (cell_status(S, r) != ST_FIELD) continue;
+    int c = S.gid[r];
+    size_t idx = (size_t)c * d.nvp + k;
+    T2 fv = S.F[r * VK + lane];
+    T2 D = Ds[(ty * TX + x) * VK + lane];
+    const double *cp = d.cpar + NCP * c;
+    T itau = (T)cp[CP_ITAU];
+    V2<T> fp = shakhov<T>((T)cp[CP_RHO], (T)cp[CP_UX], (T)cp[CP_UY], (T)cp[CP_LAM], (T)cp[CP_QX],
+                          (T)cp[CP_QY], vx, vy, (T)d.Keff, (T)d.Kint, (T)d.Pr);
+    T vol1 = (T)d.vol_new[c];
+    T2 tn;
+    if (first_iter) {
+      const double *cn = d.cparn + NCP * c;
+      T itn = (T)cn[CP_ITAU];
+      V2<T> fn = shakhov<T>((T)cn[CP_RHO], (T)cn[CP_UX], (T)cn[CP_UY], (T)cn[CP_LAM], (T)cn[CP_QX],
+                            (T)cn[CP_QY], vx, vy, (T)d.Keff, (T)d.Kint, (T)d.Pr);
+      T vol0 = (T)d.vol_old[c];
+      tn.x = vol0 * idt * fv.x + T(0.5) * (vol0 * (fn.h - fv.x) * itn - D.x);
+      tn.y = vol0 * idt * fv.y + T(0.5) * (vol0 * (fn.b - fv.y) * itn - D.y);
+      stf<T>(d.Tn, idx, tn.x, tn.y);
+    } else {
+      tn = ldf<T>(d.Tn, idx);
+    }
+    T rh = tn.x - vol1 * idt * fv.x + T(0.5) * (vol1 * (fp.h - fv.x) * itau - D.x);
+    T rb = tn.y - vol1 * idt * fv.y + T(0.5) * (vol1 * (fp.b - fv.y) * itau - D.y);
+    stf<T>(d.dfs, idx, rh, rb);
+  }
+}
+
+// --------------------------------------------------------- face reduction
+// One CTA per (tile, 32-velocity chunk), like the residual kernel.  Each tile
+// owns the i-faces on the low side of its cells (plus the block's closing
+// face of a non-periodic block when the tile reaches it) and the j-faces on
+// the low side of its cells (plus the closing face).  Per owned face the 12
+// velocity sums of the chunk are reduced across the warp in the arithmetic
+// type (butterfly, every lane ends with the totals) and lane m adds total m
+// to the FP64 face sums with an atomic.
+template <typename T> __global__ void __launch_bounds__(TTHREADS) k_face_reduce_tile(Dev d) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TileSmem<T> S;
+  S.carve(smraw);
+  int tile = blockIdx.x % d.ntiles, vc = blockIdx.x / d.ntiles;
+  int b = d.tiles[3 * tile], i0 = d.tiles[3 * tile + 1], j0 = d.tiles[3 * tile + 2];
+  const int *bi = d.blk_info + 8 * b;
+  int ni = bi[0], nj = bi[1], per = bi[2], off = d.cell_off[b];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int k = vc * VK + lane;
+  bool kv = k < d.nv;
+  T vx = kv ? dvx<T>(d, k) : T(0), vy = kv ? dvy<T>(d, k) : T(0);
+  tile_meta<T>(d, S, bi, off, i0, j0);
+  __syncthreads();
+  tile_load_f<T>(d, S, k, kv, vx, vy);
+  __syncthreads();
+  T wk = kv ? (T)d.w[k] : T(0);
+  T v2 = T(0.5) * (vx * vx + vy * vy);
+  for (int dir = 0; dir < 2; ++dir) {
+    // dir 0: i-faces of tile row w; dir 1: j-faces of tile column w
+    for (int x = 0; x <= (dir == 0 ? TX : TY); ++x) {
+      int i, j, A, B, fid;
+      if (dir == 0) {
+        i = i0 + x; j = j0 + w;
+        if (j >= nj || i > ni) break;
+        bool own = (i < ni && x < TX) || (!per && i == ni);   // closing face of a ragged tile too
+        if (!own) continue;
+        A = (x + 1) + (w + 2) * RW; B = A + 1;
+        fid = (i < ni) ? d.cell_faces[4 * (off + j * ni + i) + 0]
+                       : d.cell_faces[4 * (off + j * ni + ni - 1) + 1];
+      } else {
+        i = i0 + w; j = j0 + x;
+        if (i >= ni || j > nj) break;
+        bool own = (j < nj && x < TY) || j == nj;
+        if (!own) continue;
+        A = (w + 2) + (x + 1) * RW; B = A + RW;
+        fid = (j < nj) ? d.cell_faces[4 * (off + j * ni + i) + 2]
+                       : d.cell_faces[4 * (off + (nj - 1) * ni + i) + 3];
+      }
+      int kind = d.face_kind[fid];
+      if (kind == BC_OVERSET) continue;
+      int Lg = d.face_L[fid], Rg = d.face_R[fid];
+      bool need = d.status[Lg] == ST_FIELD || (Rg >= 0 && d.status[Rg] == ST_FIELD);
+      if (!need) continue;
+      T sums[NFS];
+#pragma unroll
+      for (int m = 0; m < NFS; ++m) sums[m] = T(0);
+      bool wall = kind == BC_WALL;
+      if (kv) {
+        T snx = (T)d.Sn[2 * fid], sny = (T)d.Sn[2 * fid + 1], sun = (T)d.SUn[fid];
+        T wS = vx * snx + vy * sny - sun;
+        if (!wall || wS > T(0)) {
+          T Pg[NFP];
+          Pg[FP_UFX] = (T)d.Uf[2 * fid];
+          Pg[FP_UFY] = (T)d.Uf[2 * fid + 1];
+          double sh = (double)d.face_shiftL[fid];
+          Pg[FP_DXLX] = (T)(d.xf[2 * fid] - (d.xc[2 * Lg] + sh * d.period[2 * Lg]));
+          Pg[FP_DXLY] = (T)(d.xf[2 * fid + 1] - (d.xc[2 * Lg + 1] + sh * d.period[2 * Lg + 1]));
+          Pg[FP_DXRX] = Rg >= 0 ? (T)(d.xf[2 * fid] - d.xc[2 * Rg]) : T(0);
+          Pg[FP_DXRY] = Rg >= 0 ? (T)(d.xf[2 * fid + 1] - d.xc[2 * Rg + 1]) : T(0);
+          int Lr = (S.gid[A] == Lg) ? A : B;
+          int Rr = (Lr == A) ? B : A;
+          V2<T> ff, wg;
+          tile_upwind<T>(d, S, Pg, kind, Lr, Rr, lane, vx, vy, wS, ff, wg);
+          T p[4] = {wk * ff.h, wk * vx * ff.h, wk * vy * ff.h, wk * (v2 * ff.h + T(0.5) * ff.b)};
+          T g[4] = {wk * wg.h, wk * vx * wg.h, wk * vy * wg.h, wk * (v2 * wg.h + T(0.5) * wg.b)};
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            sums[FS_W0 + m] = wall ? T(0) : p[m];
+            sums[FS_FF + m] = wS * p[m];
+            sums[FS_WG + m] = wS * g[m];
+          }
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < NFS; ++m)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sums[m] += __shfl_xor_sync(0xffffffffu, sums[m], o);
+      T mine = sums[0];
+#pragma unroll
+      for (int m = 1; m < NFS; ++m) if (lane == m) mine = sums[m];
+      if (lane < NFS) atomicAdd(&d.fsum[NFS * fid + lane], (double)mine);
+    }
+  }
+}
+
+template <typename T> static size_t rhs_smem() {
+  return TileSmem<T>::bytes() + sizeof(typename Vec2<T>::type) * TX * TY * VK;
+}
+template <typename T> static size_t reduce_smem() { return TileSmem<T>::bytes(); }
+
+void tile_setup() {
+  cudaFuncSetAttribute(k_rhs_tile<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_smem<float>());
+  cudaFuncSetAttribute(k_rhs_tile<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_smem<double>());
+  cudaFuncSetAttribute(k_face_reduce_tile<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)reduce_smem<float>());
+  cudaFuncSetAttribute(k_face_reduce_tile<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)reduce_smem<double>());
+}
+
+int tile_count(int ni, int nj) { return ((ni + TX - 1) / TX) * ((nj + TY - 1) / TY); }
+void tile_origins(int ni, int nj, int *out) {   // (i0, j0) pairs
+  int q = 0;
+  for (int tj = 0; tj < (nj + TY - 1) / TY; ++tj)
+    for (int ti = 0; ti < (ni + TX - 1) / TX; ++ti) { out[q++] = ti * TX; out[q++] = tj * TY; }
+}
+
+void launch_rhs_tile(const Dev &d, cudaStream_t s, int first_iter, int fp32) {
+  int nchunks = (d.nv + VK - 1) / VK;
+  int grid = d.ntiles * nchunks;
+  if (fp32) k_rhs_tile<float><<<grid, TTHREADS, rhs_smem<float>(), s>>>(d, first_iter);
+  else k_rhs_tile<double><<<grid, TTHREADS, rhs_smem<double>(), s>>>(d, first_iter);
+}
+
+void launch_face_reduce_tile(const Dev &d, cudaStream_t s, int fp32) {
+  int nchunks = (d.nv + VK - 1) / VK;
+  cudaMemsetAsync(d.fsum, 0, sizeof(double) * NFS * (size_t)d.nf, s);
+  int grid = d.ntiles * nchunks;
+  if (fp32) k_face_reduce_tile<float><<<grid, TTHREADS, reduce_smem<float>(), s>>>(d);
+  else k_face_reduce_tile<double><<<grid, TTHREADS, reduce_smem<double>(), s>>>(d);
+}
+
+}  // namespace ugks

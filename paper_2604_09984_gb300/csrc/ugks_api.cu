@@ -166,6 +166,8 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int nwork, int cap_in
   d.slope_flags = c.take<int>(s.nc);
   d.cmask = c.take<int>(s.nc);
   d.jinv = c.take<double>(4 * (size_t)s.nc);
+  d.fgeo = c.take<char>(tsz * NFG * (size_t)s.nf);
+  d.srec = c.take<char>(tsz * NSR * (size_t)s.nc);
   d.affine = c.take<double>(6 * (size_t)nb);
   d.f = c.take<char>(pair * (size_t)s.nc * s.nvp);
   d.W = c.take<double>(4 * (size_t)s.nc); d.q = c.take<double>(2 * (size_t)s.nc);
@@ -598,6 +600,7 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
   d.Kint = ctx->p.K; d.Keff = 1 + ctx->p.K;
   d.Pr = ctx->p.Pr; d.omega = ctx->p.omega; d.mu_ref = ctx->p.mu_ref;
   d.cfl_s = ctx->p.cfl_s; d.cfl_pseudo = ctx->p.cfl_pseudo; d.dt = 1.0;
+  d.vbox[0] = ctx->p.vx_min; d.vbox[1] = ctx->p.vx_max; d.vbox[2] = ctx->p.vy_min; d.vbox[3] = ctx->p.vy_max;
   {
     double lam = 1.0 / (2.0 * ctx->p.farfield[3]);
     conservative(ctx->p.farfield[0], ctx->p.farfield[1], ctx->p.farfield[2], lam, d.Keff, d.Winf);
@@ -703,8 +706,8 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
   CK(cudaMemsetAsync(d.dfs, 0, (ctx->fp32 ? 8 : 16) * (size_t)s.nc * s.nvp, ctx->st));
   launch_move_nodes(d, ctx->st);
   CK(cudaMemcpyAsync(d.X_old, d.X_new, sizeof(double) * 2 * s.nn, cudaMemcpyDeviceToDevice, ctx->st));
-  launch_geometry(d, ctx->st);
-  ctx->launches += 4;
+  launch_geometry(d, ctx->st, ctx->fp32);
+  ctx->launches += 5;
   // initial state from the primitive field (staged through cpar)
   if (s.nc * 4 > s.nc * NCP) return fail(ctx, UGKS_ERR_WORKSPACE, "staging");
   CK(cudaMemcpyAsync(d.cpar, prim, sizeof(double) * 4 * s.nc, cudaMemcpyHostToDevice, ctx->st));
@@ -739,10 +742,10 @@ int ugks_move_mesh(ugks_ctx *ctx, double t_new, const double *affine) {
   {
     Prof p(ctx, UGKS_PROF_GEOMETRY);
     launch_move_nodes(d, ctx->st);
-    launch_geometry(d, ctx->st);
+    launch_geometry(d, ctx->st, ctx->fp32);
     launch_slope_geo(d, ctx->st);
   }
-  ctx->launches += 5;
+  ctx->launches += 6;
   ctx->moved = true;
   return launch_status(ctx);
 }

@@ -59,6 +59,9 @@ struct Dev {
   int *slope_flags;          // nc: 2 bits per direction (i: bits 0-1, j: 2-3)
   int *cmask;                // nc: bit 0 solved cell, bit 1+s solved neighbour across slot s
   double *jinv;              // nc*4 inverse of [[x_xi, y_xi],[x_eta, y_eta]]
+  void *fgeo;                // nf*NFG face geometry record (arithmetic type)
+  void *srec;                // nc*NSR sweep record: outward (S n, S U.n) per face slot
+  double vbox[4];            // velocity box (vx_min, vx_max, vy_min, vy_max)
   double *affine;            // nblocks*6
   // state
   void *f;                   // nc*nvp (h, b) pairs in the storage type
@@ -109,6 +112,10 @@ struct Dev {
   int ntiles;
   int *err;                  // error flags
 };
+
+// face geometry record / per-cell sweep record
+enum { FG_SNX = 0, FG_SNY, FG_SUN, FG_UFX, FG_UFY, FG_DXLX, FG_DXLY, FG_DXRX, FG_DXRY, NFG = 10 };
+enum { NSR = 12 };
 
 // per-cell parameter record (from W' or W^n)
 enum { CP_RHO = 0, CP_UX, CP_UY, CP_LAM, CP_QX, CP_QY, CP_ITAU, CP_DBASE, NCP = 8 };

@@ -104,23 +104,56 @@ template <> struct Acc<float> {
 };
 
 // Reading R3: dts_i = cfl_s Omega_i^{n+1} / max_k sum_faces S max(w_out, 0).
-// One warp per cell.
-__global__ void k_dts(Dev d) {
-  int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
+// The sum is a convex piecewise-linear function of v, so over the tensor
+// velocity grid its maximum is attained at one of the four corners of the
+// velocity box (which are grid points): only those are evaluated.
+__global__ void k_dts(Dev d, double vx0, double vx1, double vy0, double vy1) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= d.nc) return;
   double m = 0.0;
-  for (int k = lane; k < d.nv; k += 32) {
+  for (int corner = 0; corner < 4; ++corner) {
+    double vx = (corner & 1) ? vx1 : vx0, vy = (corner & 2) ? vy1 : vy0;
     double s = 0.0;
     for (int q = 0; q < 4; ++q) {
       int f = d.cell_faces[4 * c + q];
-      double wS = d.vx[k] * d.Sn[2 * f] + d.vy[k] * d.Sn[2 * f + 1] - d.SUn[f];
+      double wS = vx * d.Sn[2 * f] + vy * d.Sn[2 * f + 1] - d.SUn[f];
       s += fmax(d.cell_sgn[4 * c + q] * wS, 0.0);
     }
     m = fmax(m, s);
   }
-  m = warp_max(m);
-  if (lane == 0) d.dts[c] = d.cfl_s * d.vol_new[c] / m;
+  d.dts[c] = d.cfl_s * d.vol_new[c] / m;
+}
+
+// Per-step geometry records in the arithmetic type: per face (S n, S U.n,
+// U_f, vectors from the L image / R centres to the face centre), per cell
+// the outward (S n, S U.n) of its four faces for the sweeps.
+template <typename T> __global__ void k_geo_records(Dev d) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < d.nf) {
+    int f = t, L = d.face_L[f], R = d.face_R[f];
+    T *g = reinterpret_cast<T *>(d.fgeo) + (size_t)NFG * f;
+    double sh = (double)d.face_shiftL[f];
+    g[FG_SNX] = (T)d.Sn[2 * f];
+    g[FG_SNY] = (T)d.Sn[2 * f + 1];
+    g[FG_SUN] = (T)d.SUn[f];
+    g[FG_UFX] = (T)d.Uf[2 * f];
+    g[FG_UFY] = (T)d.Uf[2 * f + 1];
+    g[FG_DXLX] = (T)(d.xf[2 * f] - (d.xc[2 * L] + sh * d.period[2 * L]));
+    g[FG_DXLY] = (T)(d.xf[2 * f + 1] - (d.xc[2 * L + 1] + sh * d.period[2 * L + 1]));
+    g[FG_DXRX] = R >= 0 ? (T)(d.xf[2 * f] - d.xc[2 * R]) : T(0);
+    g[FG_DXRY] = R >= 0 ? (T)(d.xf[2 * f + 1] - d.xc[2 * R + 1]) : T(0);
+  }
+  if (t < d.nc) {
+    int c = t;
+    T *r = reinterpret_cast<T *>(d.srec) + (size_t)NSR * c;
+    for (int s = 0; s < 4; ++s) {
+      int f = d.cell_faces[4 * c + s];
+      double sg = (double)d.cell_sgn[4 * c + s];
+      r[3 * s] = (T)(sg * d.Sn[2 * f]);
+      r[3 * s + 1] = (T)(sg * d.Sn[2 * f + 1]);
+      r[3 * s + 2] = (T)(sg * d.SUn[f]);
+    }
+  }
 }
 
 // Slope case and inverse Jacobian per cell (reading R1); depends on the
@@ -279,47 +312,6 @@ __device__ __forceinline__ void face_upwind(const Dev &d, int fid, int k, T wS, 
   } else {
     ff = {T(0.5) * (fL.h + fR.h), T(0.5) * (fL.b + fR.b)};
     wgf = {T(0.5) * (gL.h + gR.h), T(0.5) * (gL.b + gR.b)};
-  }
-}
-
-// Velocity-reduction pass per face (one warp per face): W0 = sum V Psi ff
-// (interface equilibrium, Sec. 2.1), and the f-dependent parts of the macro
-// flux sum V Psi wS ff, sum V Psi wS w.grad f (walls: incident side only).
-template <typename T> __global__ void k_face_reduce(Dev d) {
-  int fid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (fid >= d.nf) return;
-  if (!face_needed(d, fid) || d.face_kind[fid] == BC_OVERSET) {
-    if (lane < NFS) d.fsum[NFS * fid + lane] = 0.0;
-    return;
-  }
-  bool wall = d.face_kind[fid] == BC_WALL;
-  Acc<T> acc[NFS];
-  T snx = (T)d.Sn[2 * fid], sny = (T)d.Sn[2 * fid + 1], sun = (T)d.SUn[fid];
-  for (int k = lane; k < d.nv; k += 32) {
-    T vx = dvx<T>(d, k), vy = dvy<T>(d, k);
-    T wS = vx * snx + vy * sny - sun;
-    if (wall && !(wS > T(0))) continue;
-    V2<T> ff, wg;
-    face_upwind<T>(d, fid, k, wS, ff, wg);
-    T w = (T)d.w[k];
-    T v2 = T(0.5) * (vx * vx + vy * vy);
-    T p[4] = {w * ff.h, w * vx * ff.h, w * vy * ff.h, w * (v2 * ff.h + T(0.5) * ff.b)};
-    T g[4] = {w * wg.h, w * vx * wg.h, w * vy * wg.h, w * (v2 * wg.h + T(0.5) * wg.b)};
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      acc[FS_W0 + m].add(p[m]);
-      acc[FS_FF + m].add(wS * p[m]);
-      acc[FS_WG + m].add(wS * g[m]);
-    }
-  }
-  double tot[NFS];
-#pragma unroll
-  for (int m = 0; m < NFS; ++m) tot[m] = warp_sum(acc[m].get());
-  if (lane == 0) {
-    for (int m = 0; m < NFS; ++m) d.fsum[NFS * fid + m] = tot[m];
-    if (wall)
-      for (int m = 0; m < 4; ++m) d.fsum[NFS * fid + FS_W0 + m] = 0.0;
   }
 }
 
@@ -549,18 +541,18 @@ __device__ __forceinline__ void macro_off(const float *rr, const float *dWn, int
   float dr = dWn[0], d1 = dWn[1], d2 = dWn[2], dE = dWn[3];
   float g1 = 2.0f / (2.0f + (float)Keff);             // gamma - 1
   float mn = m1 * nx + m2 * ny, dmn = d1 * nx + d2 * ny;
-  float den = 1.0f / (r * (r + dr));
+  float den = __frcp_rn(r * (r + dr));                 // 1/(rho (rho + drho))
   // d(a b / rho) = [da b rho + a db rho + da db rho - a b drho] / (rho (rho + drho))
   float dq11 = (2.0f * (m1 * d1 + m2 * d2) * r + (d1 * d1 + d2 * d2) * r -
                 (m1 * m1 + m2 * m2) * dr) * den;
   float dp = g1 * (dE - 0.5f * dq11);
-  float p = g1 * (E - 0.5f * (m1 * m1 + m2 * m2) / r);
+  float p = g1 * (E - 0.5f * (m1 * m1 + m2 * m2) * ((r + dr) * den));
   float dv = (dmn * r - mn * dr) * den;               // d(mn / rho)
   float dF0 = dmn - dr * un;
   float dF1 = (d1 * mn * r + m1 * dmn * r + d1 * dmn * r - m1 * mn * dr) * den - d1 * un + dp * nx;
   float dF2 = (d2 * mn * r + m2 * dmn * r + d2 * dmn * r - m2 * mn * dr) * den - d2 * un + dp * ny;
   float dF3 = (dE * mn * r + E * dmn * r + dE * dmn * r - E * mn * dr) * den - dE * un +
-              dp * (mn + dmn) / (r + dr) + p * dv;
+              dp * (mn + dmn) * (r * den) + p * dv;
   float q = rr[7], g = rr[8];
   out[0] = q * (dF0 - g * dr);
   out[1] = q * (dF1 - g * d1);
@@ -584,7 +576,8 @@ template <typename MT> __global__ void k_macro_prep(Dev d, MT *rec) {
     double sg = (double)d.cell_sgn[4 * c + s];
     int nb = (sg > 0) ? d.face_R[f] : d.face_L[f];
     MT *q = o + MR_SLOT + MR_SW * s;
-    for (int m = 0; m < 4; ++m) q[m] = nb >= 0 ? (MT)d.W[4 * nb + m] : MT(0);
+    // missing neighbour: a harmless positive state (its increment is zero)
+    for (int m = 0; m < 4; ++m) q[m] = nb >= 0 ? (MT)d.W[4 * nb + m] : (m == 0 || m == 3 ? MT(1) : MT(0));
     q[4] = (MT)(sg * d.nrm[2 * f]);
     q[5] = (MT)(sg * d.nrm[2 * f + 1]);
     q[6] = (MT)(sg * d.SUn[f] / d.S[f]);
@@ -649,24 +642,29 @@ template <typename MT> __global__ void __launch_bounds__(512) k_macro_sweep(Dev 
         if (pass == 0) for (int m = 0; m < 4; ++m) acc[m] = r[MR_R + m];
         else for (int m = 0; m < 4; ++m) acc[m] = 0;
         MT *prv = cur ? buf0 : buf1;
+        const MT zero4[4] = {0, 0, 0, 0};
+        MT o[4][4];
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
-          if (!(mask & (2 << s))) continue;
-          const MT *dv = nullptr;
-          if (pass == 0) {          // lower: i-1, wrap ni-1 -> 0, j-1
-            if (s == 0 && i > 0) dv = prev;
-            else if (s == 1 && per && i == ni - 1) dv = first;
-            else if (s == 2 && row > 0) dv = prv + 4 * (row - 1);
-          } else {                  // upper: i+1, wrap 0 -> ni-1, j+1
-            if (s == 1 && i < ni - 1) dv = prev;
-            else if (s == 0 && per && i == 0) dv = first;
-            else if (s == 3 && row < nj - 1) dv = prv + 4 * (row + 1);
+          const MT *dv = zero4;
+          if (mask & (2 << s)) {
+            if (pass == 0) {          // lower: i-1, wrap ni-1 -> 0, j-1
+              if (s == 0 && i > 0) dv = prev;
+              else if (s == 1 && per && i == ni - 1) dv = first;
+              else if (s == 2 && row > 0) dv = prv + 4 * (row - 1);
+            } else {                  // upper: i+1, wrap 0 -> ni-1, j+1
+              if (s == 1 && i < ni - 1) dv = prev;
+              else if (s == 0 && per && i == 0) dv = first;
+              else if (s == 3 && row < nj - 1) dv = prv + 4 * (row + 1);
+            }
           }
-          if (!dv) continue;
-          MT o[4];
-          macro_off(r + MR_SLOT + MR_SW * s, dv, d.Keff, o);
-          for (int m = 0; m < 4; ++m) acc[m] += pass == 0 ? -o[m] : o[m];
+          // a zero increment gives exactly zero (both forms), so all four
+          // slots are evaluated without branches
+          macro_off(r + MR_SLOT + MR_SW * s, dv, d.Keff, o[s]);
         }
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+          for (int m = 0; m < 4; ++m) acc[m] += pass == 0 ? -o[s][m] : o[s][m];
         MT idg = r[MR_IDIAG];
         if (pass == 0) for (int m = 0; m < 4; ++m) val[m] = acc[m] * idg;
         else for (int m = 0; m < 4; ++m) val[m] = dws[m] - acc[m] * idg;
@@ -720,52 +718,17 @@ template <typename T> __device__ __forceinline__ T micro_diag(const Dev &d, int 
   return dg;
 }
 
-// Residual of the micro system (Steps 3 and 5, reading R4), fully parallel
-// over (cell, velocity): flux divergence D = sum_faces S F_hat, Shakhov
-// relaxation at W', level-n term T (written on the first inner iteration):
-//   r = T - Omega^{n+1} f / dt + (Omega^{n+1} (f+(W') - f)/tau' - D) / 2.
-// r is written into the forward-sweep buffer.
-template <typename T> __global__ void k_rhs(Dev d, int first_iter) {
-  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)d.nc * d.nvp) return;
-  int c = (int)(t / d.nvp), k = (int)(t % d.nvp);
-  if (k >= d.nv || d.status[c] != ST_FIELD) return;
-  typedef typename Vec2<T>::type T2;
-  T2 fv = ldf<T>(d.f, t);
-  V2<T> D = flux_div<T>(d, c, k);
-  const double *cp = d.cpar + NCP * c;
-  T vx = dvx<T>(d, k), vy = dvy<T>(d, k);
-  T itau = (T)cp[CP_ITAU];
-  V2<T> fp = shakhov<T>((T)cp[CP_RHO], (T)cp[CP_UX], (T)cp[CP_UY], (T)cp[CP_LAM], (T)cp[CP_QX],
-                        (T)cp[CP_QY], vx, vy, (T)d.Keff, (T)d.Kint, (T)d.Pr);
-  T vol1 = (T)d.vol_new[c];
-  T idt = (T)(1.0 / d.dt);
-  T2 tn;
-  if (first_iter) {
-    const double *cn = d.cparn + NCP * c;
-    T itn = (T)cn[CP_ITAU];
-    V2<T> fn = shakhov<T>((T)cn[CP_RHO], (T)cn[CP_UX], (T)cn[CP_UY], (T)cn[CP_LAM], (T)cn[CP_QX],
-                          (T)cn[CP_QY], vx, vy, (T)d.Keff, (T)d.Kint, (T)d.Pr);
-    T vol0 = (T)d.vol_old[c];
-    tn.x = vol0 * idt * fv.x + T(0.5) * (vol0 * (fn.h - fv.x) * itn - D.h);
-    tn.y = vol0 * idt * fv.y + T(0.5) * (vol0 * (fn.b - fv.y) * itn - D.b);
-    stf<T>(d.Tn, t, tn.x, tn.y);
-  } else {
-    tn = ldf<T>(d.Tn, t);
-  }
-  T rh = tn.x - vol1 * idt * fv.x + T(0.5) * (vol1 * (fp.h - fv.x) * itau - D.h);
-  T rb = tn.y - vol1 * idt * fv.y + T(0.5) * (vol1 * (fp.b - fv.y) * itau - D.b);
-  stf<T>(d.dfs, t, rh, rb);
-}
-
 // Micro LU-SGS (Eq. dualTimeStepping_micro with the upwind flux variation of
-// Sec. 2.2), forward sweep on the residual r (in dfs, overwritten by d*):
-// one CTA per (block, velocity tile), thread = (row j, velocity); the cells
-// of one diagonal i + j are independent, lower neighbours lie on the previous
-// diagonal (same thread / thread of row j-1) or, across a periodic seam, on
-// diagonal j (kept in a register).  One barrier per diagonal.
-template <typename T>
-__global__ void __launch_bounds__(512) k_micro_fwd(Dev d, const int *work, int V) {
+// Sec. 2.2) on the residual r (in dfs): one CTA per (block, velocity tile),
+// thread = (row j, velocity); the cells of one diagonal i + j are
+// independent, lower (upper) neighbours lie on the previous diagonal (same
+// thread / thread of row j -+ 1) or, across a periodic seam, on diagonal j
+// (kept in a register).  One barrier per diagonal; everything a diagonal
+// step reads from memory is loaded one step ahead.
+// pass 0: forward, d* = (r - sum_lower c d*) / D written over r;
+// pass 1: backward, d = d* - sum_upper c d / D and f += d.
+template <typename T, int PASS>
+__global__ void __launch_bounds__(512) k_micro_sweep(Dev d, const int *work, int V) {
   typedef typename Vec2<T>::type T2;
   extern __shared__ unsigned char smraw[];
   T2 *bufA = reinterpret_cast<T2 *>(smraw);
@@ -780,119 +743,81 @@ __global__ void __launch_bounds__(512) k_micro_fwd(Dev d, const int *work, int V
   T vx = kval ? dvx<T>(d, k) : T(0), vy = kval ? dvy<T>(d, k) : T(0);
   T2 prev = {0, 0}, first = {0, 0};
   int nd = ni + nj - 1;
+  const T *srec = reinterpret_cast<const T *>(d.srec);
+  // prefetched inputs of the next diagonal step
+  int mask = 0;
+  T2 rin = {0, 0}, fin = {0, 0};
+  T dbase = 0, geo[12];
+  auto load = [&](int it) {
+    mask = 0;
+    if (it >= nd) return;
+    int step = PASS == 0 ? it : nd - 1 - it;
+    int i = step - row;
+    if (!(row < nj && i >= 0 && i < ni && kval)) return;
+    int c = off + row * ni + i;
+    mask = d.cmask[c];
+    if (!(mask & 1)) return;
+    size_t idx = (size_t)c * d.nvp + k;
+    rin = ldf<T>(d.dfs, idx);
+    if (PASS == 1) fin = ldf<T>(d.f, idx);
+    dbase = (T)d.cpar[NCP * c + CP_DBASE];
+#pragma unroll
+    for (int m = 0; m < 12; ++m) geo[m] = srec[(size_t)NSR * c + m];
+  };
+  load(0);
   int cur = 0;
-  for (int step = 0; step < nd; ++step) {
+  for (int it = 0; it < nd; ++it) {
+    int step = PASS == 0 ? it : nd - 1 - it;
     int i = step - row;
     bool act = row < nj && i >= 0 && i < ni && kval;
     T2 val = {0, 0};
-    if (act) {
+    if (act && (mask & 1)) {
       int c = off + row * ni + i;
-      int mask = d.cmask[c];
-      if (mask & 1) {
-        size_t idx = (size_t)c * d.nvp + k;
-        T2 r = ldf<T>(d.dfs, idx);
-        T dg = (T)d.cpar[NCP * c + CP_DBASE];
-        T wo[4];
+      T wo[4];
+      T dg = dbase;
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          int f = d.cell_faces[4 * c + s];
-          wo[s] = (T)d.cell_sgn[4 * c + s] *
-                  (vx * (T)d.Sn[2 * f] + vy * (T)d.Sn[2 * f + 1] - (T)d.SUn[f]);
-          dg += T(0.5) * (wo[s] > T(0) ? wo[s] : T(0));
-        }
-        T ah = r.x, ab = r.y;
-        T2 *prv = cur ? bufA : bufB;
+      for (int s = 0; s < 4; ++s) {
+        wo[s] = vx * geo[3 * s] + vy * geo[3 * s + 1] - geo[3 * s + 2];
+        dg += T(0.5) * (wo[s] > T(0) ? wo[s] : T(0));
+      }
+      T2 *prv = cur ? bufA : bufB;
+      T ah = 0, ab = 0;
 #pragma unroll
-        for (int s = 0; s < 3; ++s) {
-          if (!(mask & (2 << s))) continue;
-          T2 dv;
-          if (s == 0 && i > 0) dv = prev;
-          else if (s == 1 && per && i == ni - 1) dv = first;
-          else if (s == 2 && row > 0) dv = prv[threadIdx.x - V];
-          else continue;
-          T cf = T(0.5) * (wo[s] < T(0) ? wo[s] : T(0));
-          ah -= cf * dv.x;
-          ab -= cf * dv.y;
+      for (int s = 0; s < 4; ++s) {
+        T2 dv = {0, 0};
+        bool use = false;
+        if (PASS == 0) {
+          if (s == 0 && i > 0) { dv = prev; use = true; }
+          else if (s == 1 && per && i == ni - 1) { dv = first; use = true; }
+          else if (s == 2 && row > 0) { dv = prv[threadIdx.x - V]; use = true; }
+        } else {
+          if (s == 1 && i < ni - 1) { dv = prev; use = true; }
+          else if (s == 0 && per && i == 0) { dv = first; use = true; }
+          else if (s == 3 && row < nj - 1) { dv = prv[threadIdx.x + V]; use = true; }
         }
-        val.x = ah / dg;
-        val.y = ab / dg;
+        T cf = (use && (mask & (2 << s))) ? T(0.5) * (wo[s] < T(0) ? wo[s] : T(0)) : T(0);
+        ah += cf * dv.x;
+        ab += cf * dv.y;
+      }
+      T idg = T(1) / dg;
+      size_t idx = (size_t)c * d.nvp + k;
+      if (PASS == 0) {
+        val.x = (rin.x - ah) * idg;
+        val.y = (rin.y - ab) * idg;
         stf<T>(d.dfs, idx, val.x, val.y);
+      } else {
+        val.x = rin.x - ah * idg;
+        val.y = rin.y - ab * idg;
+        stf<T>(d.f, idx, fin.x + val.x, fin.y + val.y);
       }
     }
     if (act) {
       prev = val;
-      if (i == 0) first = val;
+      if (i == (PASS == 0 ? 0 : ni - 1)) first = val;
     }
     T2 *dst = cur ? bufB : bufA;
     dst[threadIdx.x] = val;
-    __syncthreads();
-    cur ^= 1;
-  }
-}
-
-// Backward sweep and update f^{s+1} = f^s + df (Step 6).
-template <typename T>
-__global__ void __launch_bounds__(512) k_micro_bwd(Dev d, const int *work, int V) {
-  typedef typename Vec2<T>::type T2;
-  extern __shared__ unsigned char smraw[];
-  T2 *bufA = reinterpret_cast<T2 *>(smraw);
-  T2 *bufB = bufA + blockDim.x;
-  int b = work[2 * blockIdx.x], k0 = work[2 * blockIdx.x + 1];
-  const int *bi = d.blk_info + 8 * b;
-  int ni = bi[0], nj = bi[1], per = bi[2];
-  int off = d.cell_off[b];
-  int row = threadIdx.x / V, v = threadIdx.x % V;
-  int k = k0 + v;
-  bool kval = k < d.nv;
-  T vx = kval ? dvx<T>(d, k) : T(0), vy = kval ? dvy<T>(d, k) : T(0);
-  T2 prev = {0, 0}, first = {0, 0};
-  int nd = ni + nj - 1;
-  int cur = 0;
-  for (int step = nd - 1; step >= 0; --step) {
-    int i = step - row;
-    bool act = row < nj && i >= 0 && i < ni && kval;
-    T2 val = {0, 0};
-    if (act) {
-      int c = off + row * ni + i;
-      int mask = d.cmask[c];
-      if (mask & 1) {
-        size_t idx = (size_t)c * d.nvp + k;
-        T dg = (T)d.cpar[NCP * c + CP_DBASE];
-        T wo[4];
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          int f = d.cell_faces[4 * c + s];
-          wo[s] = (T)d.cell_sgn[4 * c + s] *
-                  (vx * (T)d.Sn[2 * f] + vy * (T)d.Sn[2 * f + 1] - (T)d.SUn[f]);
-          dg += T(0.5) * (wo[s] > T(0) ? wo[s] : T(0));
-        }
-        T ah = 0, ab = 0;
-        T2 *prv = cur ? bufA : bufB;
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          if (s == 2 || !(mask & (2 << s))) continue;
-          T2 dv;
-          if (s == 1 && i < ni - 1) dv = prev;
-          else if (s == 0 && per && i == 0) dv = first;
-          else if (s == 3 && row < nj - 1) dv = prv[threadIdx.x + V];
-          else continue;
-          T cf = T(0.5) * (wo[s] < T(0) ? wo[s] : T(0));
-          ah += cf * dv.x;
-          ab += cf * dv.y;
-        }
-        T2 ds = ldf<T>(d.dfs, idx);
-        val.x = ds.x - ah / dg;
-        val.y = ds.y - ab / dg;
-        T2 fv = ldf<T>(d.f, idx);
-        stf<T>(d.f, idx, fv.x + val.x, fv.y + val.y);
-      }
-    }
-    if (act) {
-      prev = val;
-      if (i == ni - 1) first = val;
-    }
-    T2 *dst = cur ? bufB : bufA;
-    dst[threadIdx.x] = val;
+    load(it + 1);
     __syncthreads();
     cur ^= 1;
   }
@@ -1013,20 +938,19 @@ template <typename T> __global__ void k_f_from_double(Dev d, const double *in) {
 static inline int nblk(size_t n, int b) { return (int)((n + b - 1) / b); }
 
 void launch_move_nodes(const Dev &d, cudaStream_t s) { k_move_nodes<<<nblk(d.nn, 256), 256, 0, s>>>(d); }
-void launch_geometry(const Dev &d, cudaStream_t s) {
+void launch_geometry(const Dev &d, cudaStream_t s, int fp32) {
   k_cell_geom<<<nblk(d.nc, 256), 256, 0, s>>>(d);
   k_face_geom<<<nblk(d.nf, 256), 256, 0, s>>>(d);
-  k_dts<<<nblk((size_t)d.nc * 32, 256), 256, 0, s>>>(d);
+  k_dts<<<nblk(d.nc, 256), 256, 0, s>>>(d, d.vbox[0], d.vbox[1], d.vbox[2], d.vbox[3]);
+  int n = d.nf > d.nc ? d.nf : d.nc;
+  if (fp32) k_geo_records<float><<<nblk(n, 256), 256, 0, s>>>(d);
+  else k_geo_records<double><<<nblk(n, 256), 256, 0, s>>>(d);
 }
 void launch_slope_geo(const Dev &d, cudaStream_t s) { k_slope_geo<<<nblk(d.nc, 256), 256, 0, s>>>(d); }
 
 void launch_ghost_gradW(const Dev &d, cudaStream_t s) {
   k_ghost<<<nblk(d.nf, 256), 256, 0, s>>>(d);
   k_gradW<<<nblk(d.nc, 256), 256, 0, s>>>(d);
-}
-void launch_face_reduce(const Dev &d, cudaStream_t s, int fp32) {
-  if (fp32) k_face_reduce<float><<<nblk((size_t)d.nf * 32, 256), 256, 0, s>>>(d);
-  else k_face_reduce<double><<<nblk((size_t)d.nf * 32, 256), 256, 0, s>>>(d);
 }
 void launch_face_coef(const Dev &d, cudaStream_t s, int fp32) {
   if (fp32) {
@@ -1055,22 +979,17 @@ void launch_macro_sweep(const Dev &d, cudaStream_t s, int rows, int fp32) {
   }
   k_macro_post<<<nblk(d.nc, 256), 256, 0, s>>>(d);
 }
-void launch_rhs(const Dev &d, cudaStream_t s, int first_iter, int fp32) {
-  size_t n = (size_t)d.nc * d.nvp;
-  if (fp32) k_rhs<float><<<nblk(n, 256), 256, 0, s>>>(d, first_iter);
-  else k_rhs<double><<<nblk(n, 256), 256, 0, s>>>(d, first_iter);
-}
 void launch_micro_fwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int V, int rows,
                       int fp32) {
   int threads = rows * V;
-  if (fp32) k_micro_fwd<float><<<nwork, threads, 2 * threads * sizeof(float2), s>>>(d, work, V);
-  else k_micro_fwd<double><<<nwork, threads, 2 * threads * sizeof(double2), s>>>(d, work, V);
+  if (fp32) k_micro_sweep<float, 0><<<nwork, threads, 2 * threads * sizeof(float2), s>>>(d, work, V);
+  else k_micro_sweep<double, 0><<<nwork, threads, 2 * threads * sizeof(double2), s>>>(d, work, V);
 }
 void launch_micro_bwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int V, int rows,
                       int fp32) {
   int threads = rows * V;
-  if (fp32) k_micro_bwd<float><<<nwork, threads, 2 * threads * sizeof(float2), s>>>(d, work, V);
-  else k_micro_bwd<double><<<nwork, threads, 2 * threads * sizeof(double2), s>>>(d, work, V);
+  if (fp32) k_micro_sweep<float, 1><<<nwork, threads, 2 * threads * sizeof(float2), s>>>(d, work, V);
+  else k_micro_sweep<double, 1><<<nwork, threads, 2 * threads * sizeof(double2), s>>>(d, work, V);
 }
 void launch_moments(const Dev &d, cudaStream_t s, int fp32) {
   if (fp32) k_moments<float><<<nblk((size_t)d.nc * 32, 256), 256, 0, s>>>(d);

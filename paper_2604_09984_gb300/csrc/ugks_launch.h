@@ -5,15 +5,13 @@
 
 namespace ugks {
 void launch_move_nodes(const Dev &d, cudaStream_t s);
-void launch_geometry(const Dev &d, cudaStream_t s);          // 3 kernels
+void launch_geometry(const Dev &d, cudaStream_t s, int fp32);   // 4 kernels
 void launch_slope_geo(const Dev &d, cudaStream_t s);
 void launch_ghost_gradW(const Dev &d, cudaStream_t s);                      // 2 kernels
-void launch_face_reduce(const Dev &d, cudaStream_t s, int fp32);
 void launch_face_coef(const Dev &d, cudaStream_t s, int fp32);
 void launch_cell_macro(const Dev &d, cudaStream_t s, int level_n);
 void launch_cell_params(const Dev &d, cudaStream_t s, const double *W, double *out);
 void launch_macro_sweep(const Dev &d, cudaStream_t s, int rows, int fp32);
-void launch_rhs(const Dev &d, cudaStream_t s, int first_iter, int fp32);
 void launch_micro_fwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int V, int rows,
                       int fp32);
 void launch_micro_bwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int V, int rows,

@@ -94,17 +94,17 @@ UG_HD void time_integrals(double dts, double tau, double q[5]) {
   // q5/dts^2 = sum_{m>=3} (-1)^{m+1} x^{m-2}/m!
   double s1 = 0, s2 = 0, s4 = 0, s5 = 0;
   double xp = 1.0;       // x^{m-1}
-  double fac = 1.0;      // m!
   double xm2 = 0.0;      // x^{m-2}
+  double ifac = 1.0;     // 1/m!
   for (int m = 1; m <= 24; ++m) {
-    fac *= m;
-    double sg = (m & 1) ? 1.0 : -1.0;
-    s1 += sg * xp / fac;
+    ifac *= 1.0 / m;
+    double t = ((m & 1) ? 1.0 : -1.0) * ifac;
+    s1 += t * xp;
     if (m >= 2) {
-      s2 += sg * (m - 1) * xm2 / fac;
+      s2 += t * (m - 1) * xm2;
       if (m >= 3) {
-        s4 += sg * (2 - m) * xm2 / fac;
-        s5 += sg * xm2 / fac;
+        s4 += t * (2 - m) * xm2;
+        s5 += t * xm2;
       }
     }
     xm2 = xp;

@@ -378,17 +378,16 @@ template <typename T> __global__ void __launch_bounds__(TTHREADS) k_face_reduce_
       for (int m = 0; m < NFS; ++m) sums[m] = T(0);
       bool wall = kind == BC_WALL;
       if (kv) {
-        T snx = (T)d.Sn[2 * fid], sny = (T)d.Sn[2 * fid + 1], sun = (T)d.SUn[fid];
-        T wS = vx * snx + vy * sny - sun;
+        const T *G = reinterpret_cast<const T *>(d.fgeo) + (size_t)NFG * fid;
+        T wS = vx * G[FG_SNX] + vy * G[FG_SNY] - G[FG_SUN];
         if (!wall || wS > T(0)) {
           T Pg[NFP];
-          Pg[FP_UFX] = (T)d.Uf[2 * fid];
-          Pg[FP_UFY] = (T)d.Uf[2 * fid + 1];
-          double sh = (double)d.face_shiftL[fid];
-          Pg[FP_DXLX] = (T)(d.xf[2 * fid] - (d.xc[2 * Lg] + sh * d.period[2 * Lg]));
-          Pg[FP_DXLY] = (T)(d.xf[2 * fid + 1] - (d.xc[2 * Lg + 1] + sh * d.period[2 * Lg + 1]));
-          Pg[FP_DXRX] = Rg >= 0 ? (T)(d.xf[2 * fid] - d.xc[2 * Rg]) : T(0);
-          Pg[FP_DXRY] = Rg >= 0 ? (T)(d.xf[2 * fid + 1] - d.xc[2 * Rg + 1]) : T(0);
+          Pg[FP_UFX] = G[FG_UFX];
+          Pg[FP_UFY] = G[FG_UFY];
+          Pg[FP_DXLX] = G[FG_DXLX];
+          Pg[FP_DXLY] = G[FG_DXLY];
+          Pg[FP_DXRX] = G[FG_DXRX];
+          Pg[FP_DXRY] = G[FG_DXRY];
           int Lr = (S.gid[A] == Lg) ? A : B;
           int Rr = (Lr == A) ? B : A;
           V2<T> ff, wg;

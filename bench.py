@@ -123,12 +123,13 @@ def field_cells(solver):
 
 def algorithmic_bytes(group, pair_bytes, nfield, nv, nc):
     """Minimum DRAM bytes of one launch of a kernel group:
-    rhs reads f and the level-n term (or writes it on the first inner
-    iteration) and writes the residual; micro_fwd reads the residual and
-    writes the forward increment in place; micro_bwd reads the increment and
-    f and writes f; face_reduce and moments read f once."""
-    per = {"rhs": 3 * nfield, "micro_fwd": 2 * nfield, "micro_bwd": 3 * nfield,
-           "face_reduce": nc, "moments": nfield, "interp": 0}
+    flux reads f and writes the flux divergence; residual reads f, the
+    divergence and the level-n term (written on the first inner iteration)
+    and writes the residual; micro_fwd reads the residual and writes the
+    forward increment in place; micro_bwd reads the increment and f and
+    writes f; face_reduce and moments read f once."""
+    per = {"flux": 2 * nfield, "residual": 4 * nfield, "micro_fwd": 2 * nfield,
+           "micro_bwd": 3 * nfield, "face_reduce": nc, "moments": nfield, "interp": 0}
     return per.get(group, 0) * nv * pair_bytes
 
 

@@ -19,7 +19,11 @@
  *    pointers into that workspace plus host-side metadata.
  *  - Work is issued on the caller's CUDA stream (cudaStream_t passed as a
  *    void*; NULL = legacy default stream) and is asynchronous unless stated.
- *    Calls that return data in HOST buffers synchronise that stream.
+ *    Inside ugks_step part of each inner iteration runs on a stream the
+ *    context creates for itself, forked from and joined back to the
+ *    caller's stream with events, so completion of the caller's stream
+ *    implies completion of all work.  Calls that return data in HOST buffers
+ *    synchronise that stream.
  *  - A context is not thread-safe; distinct contexts are independent.
  *  - Coordinates, fields and parameters cross the boundary in FP64.
  *
@@ -211,8 +215,10 @@ int ugks_get_geometry(ugks_ctx *ctx, double *vol_old, double *vol_new,
  * (counted on the host at each launch). */
 int64_t ugks_launch_count(const ugks_ctx *ctx);
 
-/* Kernel groups timed by the profiler (CUDA events on the context's stream
- * around every launch of the group). */
+/* Kernel groups timed by the profiler (CUDA events around every launch of the
+ * group, on the stream it is launched on: the context's stream, or for the
+ * macro sweep the library's internal side stream that overlaps it with the
+ * flux kernel). */
 #define UGKS_PROF_GEOMETRY    0   /* mesh motion, geometry, dt_s, slope geometry */
 #define UGKS_PROF_CONNECT     1   /* overset assembly kernels                    */
 #define UGKS_PROF_INTERP      2   /* receptor / fresh-cell interpolation          */
@@ -223,8 +229,9 @@ int64_t ugks_launch_count(const ugks_ctx *ctx);
 #define UGKS_PROF_MICRO_FWD   7   /* micro LU-SGS forward sweep                   */
 #define UGKS_PROF_MICRO_BWD   8   /* micro backward sweep and update              */
 #define UGKS_PROF_MOMENTS     9   /* step-7 moment fix and heat flux              */
-#define UGKS_PROF_RHS        10   /* flux divergence + micro residual (Steps 3, 5) */
-#define UGKS_NPROF           11
+#define UGKS_PROF_RHS        10   /* flux divergence (Step 3), tiled             */
+#define UGKS_PROF_RESIDUAL   11   /* micro residual (Step 5)                      */
+#define UGKS_NPROF           12
 
 /* Start (on != 0) or stop per-group event timing.  While on, every launch is
  * bracketed by two cudaEventRecord calls (events are created on demand and

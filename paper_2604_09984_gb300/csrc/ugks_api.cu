@@ -19,6 +19,8 @@ using namespace ugks;
 struct ugks_ctx {
   ugks_params p;
   cudaStream_t st = nullptr;
+  cudaStream_t side = nullptr;        // macro LU-SGS runs here, overlapped with the flux kernel
+  cudaEvent_t ev_flux = nullptr, ev_macro = nullptr;
   char *ws = nullptr;
   size_t ws_bytes = 0;
   Dev d;
@@ -116,6 +118,7 @@ struct Carver {
   }
 };
 
+// Velocities per sweep CTA (one per thread per row): at most 512 threads.
 int choose_V(int max_nj, int nv) {
   const char *env = getenv("UGKS_VTILE");
   if (env) {
@@ -174,10 +177,12 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int nwork, int cap_in
   d.status = c.take<int>(s.nc);
   d.Tn = c.take<char>(pair * (size_t)s.nc * s.nvp);
   d.dfs = c.take<char>(pair * (size_t)s.nc * s.nvp);
+  d.Dbuf = c.take<char>(pair * (size_t)s.nc * s.nvp);
   d.TW = c.take<double>(4 * (size_t)s.nc); d.Fc = c.take<double>(4 * (size_t)s.nc);
   d.dW = c.take<double>(4 * (size_t)s.nc); d.Wp = c.take<double>(4 * (size_t)s.nc);
   d.mrec = c.take<char>(tsz * 41 * (size_t)s.nc);
   d.cpar = c.take<double>(NCP * (size_t)s.nc); d.cparn = c.take<double>(NCP * (size_t)s.nc);
+  d.shp = c.take<char>(tsz * NSH * (size_t)s.nc); d.shn = c.take<char>(tsz * NSH * (size_t)s.nc);
   d.gradW = c.take<double>(8 * (size_t)s.nc);
   d.ghostW = c.take<double>(4 * (size_t)s.nf);
   d.fsum = c.take<double>(NFS * (size_t)s.nf);
@@ -219,9 +224,9 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int nwork, int cap_in
 int cap_interp_for(const Sizes &s, int nb) { return nb > 1 ? (s.nc / 4 > 1024 ? s.nc / 4 : (s.nc < 1024 ? s.nc : 1024)) : 0; }
 
 int nwork_for(const ugks_params *p, int nb, const ugks_block_desc *b, int V) {
-  int nv = p->nvx * p->nvy;
+  int nvp = (p->nvx * p->nvy + 3) / 4 * 4;
   (void)b;
-  return nb * ((nv + V - 1) / V);
+  return nb * ((nvp + V - 1) / V);
 }
 
 // Host topology identical in ordering to the face/cell numbering documented
@@ -376,8 +381,9 @@ int launch_status(ugks_ctx *ctx) { return cuda_check(ctx, cudaPeekAtLastError(),
 // Event pair around one launch of a kernel group (only while profiling).
 struct Prof {
   ugks_ctx *c;
+  cudaStream_t s;
   size_t slot = (size_t)-1;
-  Prof(ugks_ctx *ctx, int group) : c(ctx) {
+  Prof(ugks_ctx *ctx, int group, cudaStream_t stream = nullptr) : c(ctx), s(stream ? stream : ctx->st) {
     if (!c->prof_on) return;
     if (c->ev_used + 2 > c->ev.size()) {
       for (int i = 0; i < 256; ++i) {
@@ -390,10 +396,10 @@ struct Prof {
     slot = c->ev_used;
     c->ev_used += 2;
     c->ev_group[slot / 2] = group;
-    cudaEventRecord(c->ev[slot], c->st);
+    cudaEventRecord(c->ev[slot], s);
   }
   ~Prof() {
-    if (slot != (size_t)-1) cudaEventRecord(c->ev[slot + 1], c->st);
+    if (slot != (size_t)-1) cudaEventRecord(c->ev[slot + 1], s);
   }
 };
 
@@ -401,6 +407,7 @@ struct Prof {
 int prof_drain(ugks_ctx *ctx) {
   if (ctx->ev_used == 0) return UGKS_OK;
   CK(cudaStreamSynchronize(ctx->st));
+  CK(cudaStreamSynchronize(ctx->side));
   for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]));
@@ -542,13 +549,29 @@ int ugks_create(const ugks_params *p, void *workspace, size_t bytes, void *strea
   c->st = (cudaStream_t)stream;
   c->fp32 = p->precision == UGKS_FP32;
   memset(&c->d, 0, sizeof(c->d));
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  // the macro sweep is a latency-bound wavefront on a few SMs: give its
+  // stream the highest priority so its CTAs are placed as soon as a slot frees
+  if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_flux, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_macro, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return UGKS_ERR_CUDA;
+  }
   *out = c;
   return UGKS_OK;
 }
 
 int ugks_destroy(ugks_ctx *ctx) {
-  if (ctx)
+  if (ctx) {
+    if (ctx->side) cudaStreamSynchronize(ctx->side);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+    if (ctx->ev_flux) cudaEventDestroy(ctx->ev_flux);
+    if (ctx->ev_macro) cudaEventDestroy(ctx->ev_macro);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+  }
   delete ctx;
   return UGKS_OK;
 }
@@ -651,7 +674,7 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
         std::swap(order[a], order[b]);
   std::vector<int> work;
   for (int b = 0; b < nblocks; ++b)
-    for (int k0 = 0; k0 < s.nv; k0 += ctx->V) { work.push_back(b); work.push_back(k0); }
+    for (int k0 = 0; k0 < s.nvp; k0 += ctx->V) { work.push_back(b); work.push_back(k0); }
   std::vector<int> tiles;
   for (int b = 0; b < nblocks; ++b) {
     std::vector<int> org(2 * (size_t)tile_count(blocks[b].ni, blocks[b].nj));
@@ -660,6 +683,7 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
   }
   d.ntiles = s.ntiles;
   tile_setup();
+  sweep_setup();
   if ((r = up(ctx, (void *)d.vx, vx))) return r;
   if ((r = up(ctx, (void *)d.vy, vy))) return r;
   if ((r = up(ctx, (void *)d.w, w))) return r;
@@ -738,6 +762,8 @@ int ugks_move_mesh(ugks_ctx *ctx, double t_new, const double *affine) {
   CK(cudaMemcpyAsync(d.affine, ctx->h_affine.data(), sizeof(double) * 6 * ctx->nblocks,
                      cudaMemcpyHostToDevice, ctx->st));
   d.dt = t_new - ctx->t;
+  d.idt = 1.0 / d.dt;
+  d.idt_f = (float)d.idt;
   ctx->t_new = t_new;
   {
     Prof p(ctx, UGKS_PROF_GEOMETRY);
@@ -770,19 +796,26 @@ int ugks_step(ugks_ctx *ctx, double dt, int n_inner) {
   do_interp(ctx, d.rec_list, d.nrec);
   // Steps 1-2: level-n flux, extensive level-n macro term, level-n cell record
   flux_prep(ctx, 1);
-  { Prof p(ctx, UGKS_PROF_CELL); launch_cell_params(d, s, d.W, d.cparn); }
+  { Prof p(ctx, UGKS_PROF_CELL); launch_cell_params(d, s, d.W, d.cparn, fp); }
   ctx->launches += 1;
   for (int it = 0; it < n_inner; ++it) {
     if (it > 0) {
       do_interp(ctx, d.rec_list, d.nrec);
       flux_prep(ctx, 0);                       // Step 3
     }
-    { Prof p(ctx, UGKS_PROF_MACRO_SWEEP); launch_macro_sweep(d, s, ctx->max_nj, fp); }          // Step 4
-    { Prof p(ctx, UGKS_PROF_RHS); launch_rhs_tile(d, s, it == 0, fp); }                    // Steps 3, 5
+    // Step 4 (macro LU-SGS) on the side stream, concurrently with the flux
+    // divergence of Step 3 on the main stream; Step 5 joins both
+    CK(cudaEventRecord(ctx->ev_flux, s));
+    CK(cudaStreamWaitEvent(ctx->side, ctx->ev_flux, 0));
+    { Prof p(ctx, UGKS_PROF_MACRO_SWEEP, ctx->side); launch_macro_sweep(d, ctx->side, ctx->max_nj, fp); }
+    CK(cudaEventRecord(ctx->ev_macro, ctx->side));
+    { Prof p(ctx, UGKS_PROF_RHS); launch_flux_tile(d, s, fp); }                              // Step 3
+    CK(cudaStreamWaitEvent(s, ctx->ev_macro, 0));
+    { Prof p(ctx, UGKS_PROF_RESIDUAL); launch_residual(d, s, it == 0, fp); }                 // Step 5
     { Prof p(ctx, UGKS_PROF_MICRO_FWD); launch_micro_fwd(d, s, ctx->work, ctx->nwork, ctx->V, ctx->max_nj, fp); }  // Step 6
     { Prof p(ctx, UGKS_PROF_MICRO_BWD); launch_micro_bwd(d, s, ctx->work, ctx->nwork, ctx->V, ctx->max_nj, fp); }
     { Prof p(ctx, UGKS_PROF_MOMENTS); launch_moments(d, s, fp); }                          // Step 7
-    ctx->launches += 7;
+    ctx->launches += 8;
   }
   d.nfresh = 0;
   ctx->t = ctx->t_new;

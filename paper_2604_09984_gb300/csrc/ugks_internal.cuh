@@ -31,7 +31,8 @@ struct Dev {
   int Keff, Kint;
   double Pr, omega, mu_ref, cfl_s, cfl_pseudo;
   double Winf[4];
-  double dt;
+  double dt, idt;            // physical step and its inverse
+  float idt_f;
   // velocity space (double and float copies), length nvp (padding weight 0)
   const double *vx, *vy, *w;
   const float *vxf, *vyf, *wf;
@@ -69,6 +70,7 @@ struct Dev {
   int *status;               // nc
   // work
   void *Tn, *dfs;            // nc*nvp pairs: level-n term, forward-sweep result
+  void *Dbuf;                // nc*nvp pairs: flux divergence of the inner iteration
   double *TW;                // nc*4 extensive level-n macro term
   double *Fc;                // nc*4 macro flux divergence of the last flux
   double *dW;                // nc*4 macro increment
@@ -76,6 +78,7 @@ struct Dev {
   double *Wp;                // nc*4 macro predictor W'
   double *cpar;              // nc*NCP cell parameters (predictor / level n)
   double *cparn;
+  void *shp, *shn;           // nc*NSH Shakhov records in the arithmetic type (predictor / level n)
   double *gradW;             // nc*8
   double *ghostW;            // nf*4
   double *fsum;              // nf*NFS
@@ -120,6 +123,22 @@ enum { NSR = 12 };
 // per-cell parameter record (from W' or W^n)
 enum { CP_RHO = 0, CP_UX, CP_UY, CP_LAM, CP_QX, CP_QY, CP_ITAU, CP_DBASE, NCP = 8 };
 
+// Shakhov record in the arithmetic type from a cell record (double)
+template <typename T>
+__device__ __forceinline__ void write_shrec(const Dev &d, const double *o, double vol, T *r) {
+  double il = 1.0 / (2.0 * o[CP_LAM]);
+  r[SH_HPRE] = (T)(o[CP_RHO] * o[CP_LAM] * M_1_PI);
+  r[SH_UX] = (T)o[CP_UX];
+  r[SH_UY] = (T)o[CP_UY];
+  r[SH_LAM] = (T)o[CP_LAM];
+  r[SH_QX] = (T)o[CP_QX];
+  r[SH_QY] = (T)o[CP_QY];
+  r[SH_PREF] = (T)(4.0 * (1.0 - d.Pr) * o[CP_LAM] * o[CP_LAM] / (5.0 * o[CP_RHO]));
+  r[SH_IL] = (T)il;
+  r[SH_ITAU] = (T)o[CP_ITAU];
+  r[SH_VOL] = (T)vol;
+}
+
 template <typename T>
 __device__ __forceinline__ typename Vec2<T>::type ldf(const void *base, size_t idx) {
   return reinterpret_cast<const typename Vec2<T>::type *>(base)[idx];
@@ -130,6 +149,17 @@ __device__ __forceinline__ void stf(void *base, size_t idx, T h, T b) {
   v.x = h;
   v.y = b;
   reinterpret_cast<typename Vec2<T>::type *>(base)[idx] = v;
+}
+
+// Asynchronous global -> shared copies (cp.async, sm_80+): a per-thread
+// prefetch ring for the streaming inputs of the wavefront sweeps.
+template <int BYTES> __device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
 template <typename T> __device__ __forceinline__ T dvx(const Dev &d, int k);
@@ -209,7 +239,7 @@ template <typename T> __device__ V2<T> face_flux(const Dev &d, int fid, int k) {
     if (!(wS > T(0))) {
       // reflected part: wall Maxwellian at the face velocity (Eq. maxWalldes)
       T lw = P[FP_LAMW];
-      T Hw = P[FP_RHOW] * (lw / T(M_PI)) * r_exp<T>(-lw * (wx * wx + wy * wy));
+      T Hw = P[FP_RHOW] * (lw * T(M_1_PI)) * r_exp<T>(-lw * (wx * wx + wy * wy));
       return {wS * Hw, wS * (T)d.Keff / (T(2) * lw) * Hw};
     }
     auto fv = ldf<T>(d.f, (size_t)L * d.nvp + k);

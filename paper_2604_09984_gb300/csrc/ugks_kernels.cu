@@ -397,6 +397,10 @@ template <typename T> __global__ void k_face_scalar(Dev d) {
   for (int m = 0; m < 5; ++m) par[FP_Q1 + m] = qi[m] / dts;
   par[FP_UFX] = ufx; par[FP_UFY] = ufy;
   par[FP_PREF] = 4.0 * (1.0 - d.Pr) * p0.lam * p0.lam / (5.0 * p0.rho);
+  par[FP_HPRE] = p0.rho * p0.lam * M_1_PI;
+  par[FP_IL] = 1.0 / (2.0 * p0.lam);
+  par[FP_EH] = 0.5 * d.Keff * par[FP_IL];
+  par[FP_EB] = 0.5 * (d.Keff + 2.0) * par[FP_IL];
   par[FP_LAMW] = wall ? 1.0 / (2.0 * d.face_Tw[fid]) : 0.0;
   par[FP_RHOW] = 0.0;
   par[FP_SNX] = d.Sn[2 * fid];
@@ -451,7 +455,7 @@ template <typename T> __global__ void k_face_coef(Dev d) {
       ags[3].add(cw * (v2 * I.h + T(0.5) * I.b));
     } else {
       T cx = vx - tufx, cy = vy - tufy;
-      T Hw = (tlamw / T(M_PI)) * r_exp<T>(-tlamw * (cx * cx + cy * cy));
+      T Hw = (tlamw * T(M_1_PI)) * r_exp<T>(-tlamw * (cx * cx + cy * cy));
       T Bw = tK / (T(2) * tlamw) * Hw;
       aden.add(cw * Hw);
       ars[0].add(cw * Hw); ars[1].add(cw * vx * Hw); ars[2].add(cw * vy * Hw);
@@ -492,8 +496,9 @@ __global__ void k_cell_macro(Dev d, int level_n) {
     for (int m = 0; m < 4; ++m) d.TW[4 * c + m] = d.vol_old[c] / d.dt * d.W[4 * c + m] - 0.5 * F[m];
 }
 
-// Cell parameter record (prim, q, 1/tau, Shakhov prefactor) from W and q.
-__global__ void k_cell_params(Dev d, const double *Wsrc, double *out) {
+// Cell parameter record (prim, q, 1/tau) from W and q, and its Shakhov
+// record in the arithmetic type (level n).
+template <typename T> __global__ void k_cell_params(Dev d, const double *Wsrc, double *out) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= d.nc) return;
   Prim p = primitive(Wsrc + 4 * c, d.Keff);
@@ -502,6 +507,7 @@ __global__ void k_cell_params(Dev d, const double *Wsrc, double *out) {
   o[CP_QX] = d.q[2 * c]; o[CP_QY] = d.q[2 * c + 1];
   o[CP_ITAU] = 1.0 / collision_time(p.rho, p.lam, d.mu_ref, d.omega);
   o[CP_DBASE] = 0.0;
+  write_shrec<T>(d, o, d.vol_old[c], reinterpret_cast<T *>(d.shn) + (size_t)NSH * c);
 }
 
 // ----------------------------------------------------- macro LU-SGS sweep
@@ -687,7 +693,7 @@ template <typename MT> __global__ void __launch_bounds__(512) k_macro_sweep(Dev 
 }
 
 // W' = W + dW and the predictor cell record (Step 4 result) for Step 5.
-__global__ void k_macro_post(Dev d) {
+template <typename T> __global__ void k_macro_post(Dev d) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= d.nc) return;
   if (!(d.cmask[c] & 1)) {
@@ -701,6 +707,7 @@ __global__ void k_macro_post(Dev d) {
   o[CP_QX] = d.q[2 * c]; o[CP_QY] = d.q[2 * c + 1];
   o[CP_ITAU] = 1.0 / collision_time(p.rho, p.lam, d.mu_ref, d.omega);
   o[CP_DBASE] = d.vol_new[c] * (d.cfl_s / (d.cfl_pseudo * d.dts[c]) + 1.0 / d.dt + 0.5 * o[CP_ITAU]);
+  write_shrec<T>(d, o, d.vol_new[c], reinterpret_cast<T *>(d.shp) + (size_t)NSH * c);
 }
 
 // ----------------------------------------------------- micro LU-SGS sweeps
@@ -830,13 +837,14 @@ template <typename T> __global__ void k_moments(Dev d) {
   int lane = threadIdx.x & 31;
   if (c >= d.nc) return;
   if (d.status[c] != ST_FIELD) return;
-  const double *cp = d.cpar + NCP * c;
-  T rho = (T)cp[CP_RHO], ux = (T)cp[CP_UX], uy = (T)cp[CP_UY], lam = (T)cp[CP_LAM];
+  const T *sr = reinterpret_cast<const T *>(d.shp) + (size_t)NSH * c;
+  T hpre = sr[SH_HPRE], ux = sr[SH_UX], uy = sr[SH_UY], lam = sr[SH_LAM];
+  T bfac = (T)d.Keff * sr[SH_IL];
   Acc<T> a[6];
   for (int k = lane; k < d.nv; k += 32) {
     auto fv = ldf<T>(d.f, (size_t)c * d.nvp + k);
     T vx = dvx<T>(d, k), vy = dvy<T>(d, k), w = (T)d.w[k];
-    V2<T> g = maxwellian<T>(rho, ux, uy, lam, vx, vy, (T)d.Keff);
+    V2<T> g = maxwellian_pre<T>(hpre, ux, uy, lam, bfac, vx, vy);
     T h = fv.x, b = fv.y;
     T dh = h - g.h, db = b - g.b;
     T v2 = T(0.5) * (vx * vx + vy * vy);
@@ -964,8 +972,9 @@ void launch_face_coef(const Dev &d, cudaStream_t s, int fp32) {
 void launch_cell_macro(const Dev &d, cudaStream_t s, int level_n) {
   k_cell_macro<<<nblk(d.nc, 256), 256, 0, s>>>(d, level_n);
 }
-void launch_cell_params(const Dev &d, cudaStream_t s, const double *W, double *out) {
-  k_cell_params<<<nblk(d.nc, 256), 256, 0, s>>>(d, W, out);
+void launch_cell_params(const Dev &d, cudaStream_t s, const double *W, double *out, int fp32) {
+  if (fp32) k_cell_params<float><<<nblk(d.nc, 256), 256, 0, s>>>(d, W, out);
+  else k_cell_params<double><<<nblk(d.nc, 256), 256, 0, s>>>(d, W, out);
 }
 void launch_macro_sweep(const Dev &d, cudaStream_t s, int rows, int fp32) {
   if (fp32) {
@@ -977,8 +986,18 @@ void launch_macro_sweep(const Dev &d, cudaStream_t s, int rows, int fp32) {
     k_macro_prep<double><<<nblk(d.nc, 256), 256, 0, s>>>(d, rec);
     k_macro_sweep<double><<<d.nblocks, rows, 2 * 4 * rows * sizeof(double), s>>>(d, rec);
   }
-  k_macro_post<<<nblk(d.nc, 256), 256, 0, s>>>(d);
+  if (fp32) k_macro_post<float><<<nblk(d.nc, 256), 256, 0, s>>>(d);
+  else k_macro_post<double><<<nblk(d.nc, 256), 256, 0, s>>>(d);
 }
+// shared memory of the sweeps exceeds the default 48 KB for FP64 / wide CTAs
+void sweep_setup() {
+  int mx = 2 * 512 * (int)sizeof(double2);
+  cudaFuncSetAttribute(k_micro_sweep<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<double, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+}
+
 void launch_micro_fwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int V, int rows,
                       int fp32) {
   int threads = rows * V;

@@ -10,12 +10,13 @@ void launch_slope_geo(const Dev &d, cudaStream_t s);
 void launch_ghost_gradW(const Dev &d, cudaStream_t s);                      // 2 kernels
 void launch_face_coef(const Dev &d, cudaStream_t s, int fp32);
 void launch_cell_macro(const Dev &d, cudaStream_t s, int level_n);
-void launch_cell_params(const Dev &d, cudaStream_t s, const double *W, double *out);
+void launch_cell_params(const Dev &d, cudaStream_t s, const double *W, double *out, int fp32);
 void launch_macro_sweep(const Dev &d, cudaStream_t s, int rows, int fp32);
 void launch_micro_fwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int V, int rows,
                       int fp32);
 void launch_micro_bwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int V, int rows,
                       int fp32);
+void sweep_setup();
 void launch_moments(const Dev &d, cudaStream_t s, int fp32);
 void launch_init_state(const Dev &d, cudaStream_t s, const double *prim, int fp32);
 void launch_flux_div_all(const Dev &d, cudaStream_t s, double *D, int fp32);
@@ -28,6 +29,7 @@ void launch_interp(const Dev &d, cudaStream_t s, const int *list, int n, int fp3
 void tile_setup();
 int tile_count(int ni, int nj);
 void tile_origins(int ni, int nj, int *out);
-void launch_rhs_tile(const Dev &d, cudaStream_t s, int first_iter, int fp32);
+void launch_flux_tile(const Dev &d, cudaStream_t s, int fp32);
+void launch_residual(const Dev &d, cudaStream_t s, int first_iter, int fp32);
 void launch_face_reduce_tile(const Dev &d, cudaStream_t s, int fp32);
 }  // namespace ugks

@@ -53,8 +53,28 @@ UG_HD double collision_time(double rho, double lam, double mu_ref, double omega)
 template <typename R>
 UG_HD V2<R> maxwellian(R rho, R ux, R uy, R lam, R vx, R vy, R Keff) {
   R cx = vx - ux, cy = vy - uy;
-  R H = rho * (lam / R(M_PI)) * r_exp<R>(-lam * (cx * cx + cy * cy));
+  R H = rho * (lam * R(M_1_PI)) * r_exp<R>(-lam * (cx * cx + cy * cy));
   return {H, Keff / (R(2) * lam) * H};
+}
+
+// Same with the per-state constants precomputed: hpre = rho lam / pi,
+// bfac = Keff / (2 lam) (no division per velocity).
+template <typename R>
+UG_HD V2<R> maxwellian_pre(R hpre, R ux, R uy, R lam, R bfac, R vx, R vy) {
+  R cx = vx - ux, cy = vy - uy;
+  R H = hpre * r_exp<R>(-lam * (cx * cx + cy * cy));
+  return {H, bfac * H};
+}
+
+// Division used inside per-velocity loops: exact in FP64, the fast
+// approximate quotient (2 ulp) in FP32.
+template <typename R> UG_HD R qdiv(R a, R b) { return a / b; }
+template <> UG_HD float qdiv<float>(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fdividef(a, b);
+#else
+  return a / b;
+#endif
 }
 
 // ---------------------------------------------- interface-flux parameters
@@ -70,7 +90,10 @@ enum {
   // (periodic image of the) L cell centre and from the R cell centre to the
   // face centre
   FP_SNX = 28, FP_SNY, FP_SUN, FP_DXLX, FP_DXLY, FP_DXRX, FP_DXRY,
-  NFP = 36
+  // per-face constants of the velocity loops: rho lam / pi, 1/(2 lam),
+  // Keff/(4 lam), (Keff+2)/(4 lam)
+  FP_HPRE = 35, FP_IL, FP_EH, FP_EB,
+  NFP = 40
 };
 
 // Time integrals q_m = int_0^dts c_m(t) dt (Eq. fullSolution), x = dts/tau;
@@ -191,11 +214,11 @@ UG_HD void time_slope(const Prim &g, int Keff, const double ax[4], const double 
 template <typename R>
 UG_HD V2<R> interface_integral(const R *P, R vx, R vy, V2<R> ff, V2<R> wgf, R Keff, R Kint,
                                R Pr) {
-  R rho = P[FP_RHO], ux = P[FP_UX], uy = P[FP_UY], lam = P[FP_LAM];
+  R ux = P[FP_UX], uy = P[FP_UY], lam = P[FP_LAM];
   R cx = vx - ux, cy = vy - uy;
   R c2 = cx * cx + cy * cy;
-  R H = rho * (lam / R(M_PI)) * r_exp<R>(-lam * c2);
-  R il = R(1) / (R(2) * lam);
+  R H = P[FP_HPRE] * r_exp<R>(-lam * c2);
+  R il = P[FP_IL];
   R B = Keff * il * H;
   // Shakhov correction (Sec. 2.1, reduced H+, B+ as printed)
   R cq = cx * P[FP_QX] + cy * P[FP_QY];
@@ -209,7 +232,7 @@ UG_HD V2<R> interface_integral(const R *P, R vx, R vy, V2<R> ff, V2<R> wgf, R Ke
   R bx = ax[0] + ax[1] * vx + ax[2] * vy + R(0.5) * ax[3] * v2;
   R by = ay[0] + ay[1] * vx + ay[2] * vy + R(0.5) * ay[3] * v2;
   R bt = at[0] + at[1] * vx + at[2] * vy + R(0.5) * at[3] * v2;
-  R eh = R(0.5) * Keff * il, eb = R(0.5) * (Keff + R(2)) * il;
+  R eh = P[FP_EH], eb = P[FP_EB];
   R sgh = wx * (bx + ax[3] * eh) + wy * (by + ay[3] * eh);
   R sgb = wx * (bx + ax[3] * eb) + wy * (by + ay[3] * eb);
   R sth = bt + at[3] * eh, stb = bt + at[3] * eb;
@@ -222,12 +245,27 @@ UG_HD V2<R> interface_integral(const R *P, R vx, R vy, V2<R> ff, V2<R> wgf, R Ke
   return out;
 }
 
+// Per-cell record of the Shakhov equilibrium (Sec. 2.1) with the constants
+// of the velocity loop precomputed: f+ of one velocity without divisions.
+enum { SH_HPRE = 0, SH_UX, SH_UY, SH_LAM, SH_QX, SH_QY, SH_PREF, SH_IL, SH_ITAU, SH_VOL, NSH = 10 };
+template <typename R>
+UG_HD V2<R> shakhov_rec(const R *c, R vx, R vy, R Keff, R Kint) {
+  R cx = vx - c[SH_UX], cy = vy - c[SH_UY];
+  R c2 = cx * cx + cy * cy;
+  R lam = c[SH_LAM], il = c[SH_IL];
+  R H = c[SH_HPRE] * r_exp<R>(-lam * c2);
+  R pref = c[SH_PREF] * (cx * c[SH_QX] + cy * c[SH_QY]);
+  R Hp = pref * (R(2) * lam * c2 - R(4)) * H;
+  R Bp = pref * ((R(2) * lam * c2 - R(2)) * Keff - R(2) * Kint) * H * il;
+  return {H + Hp, Keff * il * H + Bp};
+}
+
 // Shakhov equilibrium f+ = g + g+ of a cell (Sec. 2.1), one velocity.
 template <typename R>
 UG_HD V2<R> shakhov(R rho, R ux, R uy, R lam, R qx, R qy, R vx, R vy, R Keff, R Kint, R Pr) {
   R cx = vx - ux, cy = vy - uy;
   R c2 = cx * cx + cy * cy;
-  R H = rho * (lam / R(M_PI)) * r_exp<R>(-lam * c2);
+  R H = rho * (lam * R(M_1_PI)) * r_exp<R>(-lam * c2);
   R il = R(1) / (R(2) * lam);
   R pref = R(4) * (R(1) - Pr) * lam * lam / (R(5) * rho) * (cx * qx + cy * qy);
   R Hp = pref * (R(2) * lam * c2 - R(4)) * H;
@@ -238,7 +276,7 @@ UG_HD V2<R> shakhov(R rho, R ux, R uy, R lam, R qx, R qy, R vx, R vy, R Keff, R 
 // van Leer limited slope of two centre differences
 template <typename R> UG_HD R vanleer(R a, R b) {
   R p = a * b;
-  return p > R(0) ? R(2) * p / (a + b) : R(0);
+  return p > R(0) ? qdiv<R>(R(2) * p, a + b) : R(0);
 }
 
 }  // namespace ugks

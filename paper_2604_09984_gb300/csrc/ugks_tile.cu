@@ -4,9 +4,11 @@
 //   k_face_reduce_tile  velocity sums per face: W0 of the interface
 //                       equilibrium and the f-dependent parts of the macro
 //                       flux (Eq. macroscopicFlux);
-//   k_rhs_tile          flux divergence D = sum_faces S F_hat (Eqs.
-//                       microscopicFlux, fullSolution, wall condition) and
-//                       the micro residual r (reading R4).
+//   k_flux_tile         flux divergence D = sum_faces S F_hat (Eqs.
+//                       microscopicFlux, fullSolution, wall condition), which
+//                       does not depend on the macro predictor, so it runs
+//                       while the macro LU-SGS sweep runs on another stream;
+//   k_residual          the micro residual r from D (reading R4).
 // A CTA stages f of an 8x8 cell tile plus a two-cell halo (ghost cells hold
 // the Maxwellian of their ghost state) for 32 velocities in shared memory,
 // reconstructs from there and evaluates each face of the tile once (one warp
@@ -77,7 +79,7 @@ __device__ __forceinline__ void tile_meta(const Dev &d, TileSmem<T> &S, const in
       S.flags[r] = ST_HOLE << 8;
       if (g <= -2) {
         Prim p = primitive(d.ghostW + 4 * (-2 - g), d.Keff);
-        S.gprim[4 * r] = (T)p.rho; S.gprim[4 * r + 1] = (T)p.ux;
+        S.gprim[4 * r] = (T)(p.rho * p.lam * M_1_PI); S.gprim[4 * r + 1] = (T)p.ux;
         S.gprim[4 * r + 2] = (T)p.uy; S.gprim[4 * r + 3] = (T)p.lam;
       }
     }
@@ -97,7 +99,7 @@ __device__ __forceinline__ void tile_load_f(const Dev &d, TileSmem<T> &S, int k,
         v = ldf<T>(d.f, (size_t)g * d.nvp + k);
       } else if (g <= -2) {
         const T *p = S.gprim + 4 * r;
-        V2<T> m = maxwellian<T>(p[0], p[1], p[2], p[3], vx, vy, (T)d.Keff);
+        V2<T> m = maxwellian_pre<T>(p[0], p[1], p[2], p[3], (T)d.Keff / (T(2) * p[3]), vx, vy);
         v.x = m.h;
         v.y = m.b;
       }
@@ -193,7 +195,7 @@ __device__ __forceinline__ V2<T> tile_face_flux(const Dev &d, const TileSmem<T> 
   if (kind == BC_WALL && !(wS > T(0))) {
     T wx = vx - P[FP_UFX], wy = vy - P[FP_UFY];
     T lw = P[FP_LAMW];
-    T Hw = P[FP_RHOW] * (lw / T(M_PI)) * r_exp<T>(-lw * (wx * wx + wy * wy));
+    T Hw = P[FP_RHOW] * (lw * T(M_1_PI)) * r_exp<T>(-lw * (wx * wx + wy * wy));
     return {wS * Hw, wS * (T)d.Keff / (T(2) * lw) * Hw};
   }
   V2<T> ff, wg;
@@ -205,8 +207,8 @@ __device__ __forceinline__ V2<T> tile_face_flux(const Dev &d, const TileSmem<T> 
 __device__ __forceinline__ int cell_status(const TileSmem<float> &S, int r) { return S.flags[r] >> 8; }
 __device__ __forceinline__ int cell_status(const TileSmem<double> &S, int r) { return S.flags[r] >> 8; }
 
-// ------------------------------------------------------------ residual
-template <typename T> __global__ void __launch_bounds__(TTHREADS) k_rhs_tile(Dev d, int first_iter) {
+// ------------------------------------------------------- flux divergence
+template <typename T> __global__ void __launch_bounds__(TTHREADS) k_flux_tile(Dev d) {
   typedef typename Vec2<T>::type T2;
   extern __shared__ __align__(16) unsigned char smraw[];
   TileSmem<T> S;
@@ -283,42 +285,52 @@ template <typename T> __global__ void __launch_bounds__(TTHREADS) k_rhs_tile(Dev
     }
   }
   __syncthreads();
-  // residual of the tile cells of row w
+  // flux divergence of the tile cells of row w
   if (!kv) return;
   int ty = w, j = j0 + ty;
   if (j >= nj) return;
-  T idt = (T)(1.0 / d.dt);
   for (int x = 0; x < TX; ++x) {
     int i = i0 + x;
     if (i >= ni) break;
     int r = (x + 2) + (ty + 2) * RW;
     if (cell_status(S, r) != ST_FIELD) continue;
-    int c = S.gid[r];
-    size_t idx = (size_t)c * d.nvp + k;
-    T2 fv = S.F[r * VK + lane];
     T2 D = Ds[(ty * TX + x) * VK + lane];
-    const double *cp = d.cpar + NCP * c;
-    T itau = (T)cp[CP_ITAU];
-    V2<T> fp = shakhov<T>((T)cp[CP_RHO], (T)cp[CP_UX], (T)cp[CP_UY], (T)cp[CP_LAM], (T)cp[CP_QX],
-                          (T)cp[CP_QY], vx, vy, (T)d.Keff, (T)d.Kint, (T)d.Pr);
-    T vol1 = (T)d.vol_new[c];
-    T2 tn;
-    if (first_iter) {
-      const double *cn = d.cparn + NCP * c;
-      T itn = (T)cn[CP_ITAU];
-      V2<T> fn = shakhov<T>((T)cn[CP_RHO], (T)cn[CP_UX], (T)cn[CP_UY], (T)cn[CP_LAM], (T)cn[CP_QX],
-                            (T)cn[CP_QY], vx, vy, (T)d.Keff, (T)d.Kint, (T)d.Pr);
-      T vol0 = (T)d.vol_old[c];
-      tn.x = vol0 * idt * fv.x + T(0.5) * (vol0 * (fn.h - fv.x) * itn - D.x);
-      tn.y = vol0 * idt * fv.y + T(0.5) * (vol0 * (fn.b - fv.y) * itn - D.y);
-      stf<T>(d.Tn, idx, tn.x, tn.y);
-    } else {
-      tn = ldf<T>(d.Tn, idx);
-    }
-    T rh = tn.x - vol1 * idt * fv.x + T(0.5) * (vol1 * (fp.h - fv.x) * itau - D.x);
-    T rb = tn.y - vol1 * idt * fv.y + T(0.5) * (vol1 * (fp.b - fv.y) * itau - D.y);
-    stf<T>(d.dfs, idx, rh, rb);
+    stf<T>(d.Dbuf, (size_t)S.gid[r] * d.nvp + k, D.x, D.y);
   }
+}
+
+// Micro residual (Steps 3, 5; reading R4), elementwise over (cell, velocity):
+//   r = T - Omega^{n+1} f / dt + (Omega^{n+1} (f+(W') - f)/tau' - D) / 2,
+// with the level-n term T = Omega^n f^n / dt + (Omega^n (f+(W^n) - f^n)/tau^n
+// - D^n) / 2 formed on the first inner iteration.  r goes to the sweep buffer.
+template <typename T> __global__ void k_residual(Dev d, int first_iter) {
+  typedef typename Vec2<T>::type T2;
+  int c = blockIdx.x, k = blockIdx.y * blockDim.x + threadIdx.x;   // grid: cells x velocity chunks
+  if (k >= d.nv || !(d.cmask[c] & 1)) return;
+  size_t t = (size_t)c * d.nvp + k;
+  T vx = dvx<T>(d, k), vy = dvy<T>(d, k);
+  T2 fv = ldf<T>(d.f, t);
+  T2 D = ldf<T>(d.Dbuf, t);
+  const T *cp = reinterpret_cast<const T *>(d.shp) + (size_t)NSH * c;
+  T itau = cp[SH_ITAU];
+  V2<T> fp = shakhov_rec<T>(cp, vx, vy, (T)d.Keff, (T)d.Kint);
+  T vol1 = cp[SH_VOL];
+  T idt = sizeof(T) == 4 ? (T)d.idt_f : (T)d.idt;
+  T2 tn;
+  if (first_iter) {
+    const T *cn = reinterpret_cast<const T *>(d.shn) + (size_t)NSH * c;
+    T itn = cn[SH_ITAU];
+    V2<T> fn = shakhov_rec<T>(cn, vx, vy, (T)d.Keff, (T)d.Kint);
+    T vol0 = cn[SH_VOL];
+    tn.x = vol0 * idt * fv.x + T(0.5) * (vol0 * (fn.h - fv.x) * itn - D.x);
+    tn.y = vol0 * idt * fv.y + T(0.5) * (vol0 * (fn.b - fv.y) * itn - D.y);
+    stf<T>(d.Tn, t, tn.x, tn.y);
+  } else {
+    tn = ldf<T>(d.Tn, t);
+  }
+  T rh = tn.x - vol1 * idt * fv.x + T(0.5) * (vol1 * (fp.h - fv.x) * itau - D.x);
+  T rb = tn.y - vol1 * idt * fv.y + T(0.5) * (vol1 * (fp.b - fv.y) * itau - D.y);
+  stf<T>(d.dfs, t, rh, rb);
 }
 
 // --------------------------------------------------------- face reduction
@@ -402,14 +414,25 @@ template <typename T> __global__ void __launch_bounds__(TTHREADS) k_face_reduce_
           }
         }
       }
+      // transposed butterfly: 16 slots (12 used) halve at every level, so
+      // 16 shuffles replace 12 x 5; lane pairs end with the total of slot
+      // 8 b4 + 4 b3 + 2 b2 + b1 (b_n = bit n of the lane)
+      T v16[16];
 #pragma unroll
-      for (int m = 0; m < NFS; ++m)
+      for (int m = 0; m < 16; ++m) v16[m] = m < NFS ? sums[m] : T(0);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sums[m] += __shfl_xor_sync(0xffffffffu, sums[m], o);
-      T mine = sums[0];
+      for (int half = 8; half >= 1; half >>= 1) {
+        bool up = lane & (2 * half);
 #pragma unroll
-      for (int m = 1; m < NFS; ++m) if (lane == m) mine = sums[m];
-      if (lane < NFS) atomicAdd(&d.fsum[NFS * fid + lane], (double)mine);
+        for (int q = 0; q < half; ++q) {
+          T send = up ? v16[q] : v16[q + half];
+          T keep = up ? v16[q + half] : v16[q];
+          v16[q] = keep + __shfl_xor_sync(0xffffffffu, send, 2 * half);
+        }
+      }
+      v16[0] += __shfl_xor_sync(0xffffffffu, v16[0], 1);
+      int slotm = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+      if (!(lane & 1) && slotm < NFS) atomicAdd(&d.fsum[NFS * fid + slotm], (double)v16[0]);
     }
   }
 }
@@ -420,8 +443,8 @@ template <typename T> static size_t rhs_smem() {
 template <typename T> static size_t reduce_smem() { return TileSmem<T>::bytes(); }
 
 void tile_setup() {
-  cudaFuncSetAttribute(k_rhs_tile<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_smem<float>());
-  cudaFuncSetAttribute(k_rhs_tile<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_smem<double>());
+  cudaFuncSetAttribute(k_flux_tile<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_smem<float>());
+  cudaFuncSetAttribute(k_flux_tile<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_smem<double>());
   cudaFuncSetAttribute(k_face_reduce_tile<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)reduce_smem<float>());
   cudaFuncSetAttribute(k_face_reduce_tile<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)reduce_smem<double>());
 }
@@ -433,11 +456,17 @@ void tile_origins(int ni, int nj, int *out) {   // (i0, j0) pairs
     for (int ti = 0; ti < (ni + TX - 1) / TX; ++ti) { out[q++] = ti * TX; out[q++] = tj * TY; }
 }
 
-void launch_rhs_tile(const Dev &d, cudaStream_t s, int first_iter, int fp32) {
+void launch_flux_tile(const Dev &d, cudaStream_t s, int fp32) {
   int nchunks = (d.nv + VK - 1) / VK;
   int grid = d.ntiles * nchunks;
-  if (fp32) k_rhs_tile<float><<<grid, TTHREADS, rhs_smem<float>(), s>>>(d, first_iter);
-  else k_rhs_tile<double><<<grid, TTHREADS, rhs_smem<double>(), s>>>(d, first_iter);
+  if (fp32) k_flux_tile<float><<<grid, TTHREADS, rhs_smem<float>(), s>>>(d);
+  else k_flux_tile<double><<<grid, TTHREADS, rhs_smem<double>(), s>>>(d);
+}
+void launch_residual(const Dev &d, cudaStream_t s, int first_iter, int fp32) {
+  int bt = d.nv >= 256 ? 256 : ((d.nv + 31) / 32) * 32;
+  dim3 grid(d.nc, (d.nv + bt - 1) / bt);
+  if (fp32) k_residual<float><<<grid, bt, 0, s>>>(d, first_iter);
+  else k_residual<double><<<grid, bt, 0, s>>>(d, first_iter);
 }
 
 void launch_face_reduce_tile(const Dev &d, cudaStream_t s, int fp32) {

@@ -65,7 +65,7 @@ SYMBOLS = {
     "ugks_profile_read": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int64), c_int]),
 }
 PROF_GROUPS = ["geometry", "connect", "interp", "cell", "face_reduce", "face_coef",
-               "macro_sweep", "micro_fwd", "micro_bwd", "moments", "rhs"]
+               "macro_sweep", "micro_fwd", "micro_bwd", "moments", "flux", "residual"]
 
 _lib = None
 

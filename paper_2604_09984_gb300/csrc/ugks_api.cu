@@ -180,7 +180,7 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int nwork, int cap_in
   d.Dbuf = c.take<char>(pair * (size_t)s.nc * s.nvp);
   d.TW = c.take<double>(4 * (size_t)s.nc); d.Fc = c.take<double>(4 * (size_t)s.nc);
   d.dW = c.take<double>(4 * (size_t)s.nc); d.Wp = c.take<double>(4 * (size_t)s.nc);
-  d.mrec = c.take<char>(tsz * 41 * (size_t)s.nc);
+  d.mrec = c.take<char>((fp32 ? 4 * 48 : 8 * 41) * (size_t)s.nc);
   d.cpar = c.take<double>(NCP * (size_t)s.nc); d.cparn = c.take<double>(NCP * (size_t)s.nc);
   d.shp = c.take<char>(tsz * NSH * (size_t)s.nc); d.shn = c.take<char>(tsz * NSH * (size_t)s.nc);
   d.gradW = c.take<double>(8 * (size_t)s.nc);

@@ -117,7 +117,7 @@ struct Dev {
 };
 
 // face geometry record / per-cell sweep record
-enum { FG_SNX = 0, FG_SNY, FG_SUN, FG_UFX, FG_UFY, FG_DXLX, FG_DXLY, FG_DXRX, FG_DXRY, NFG = 10 };
+enum { FG_SNX = 0, FG_SNY, FG_SUN, FG_UFX, FG_UFY, FG_DXLX, FG_DXLY, FG_DXRX, FG_DXRY, NFG = 12 };
 enum { NSR = 12 };
 
 // per-cell parameter record (from W' or W^n)
@@ -218,6 +218,16 @@ __device__ __forceinline__ void grad_f(const Dev &d, int c, int k, V2<T> fc, V2<
   gx.b = i11 * s[0].b + i12 * s[1].b;
   gy.h = i21 * s[0].h + i22 * s[1].h;
   gy.b = i21 * s[0].b + i22 * s[1].b;
+}
+
+// Copy a record of N values (N * sizeof(T) a multiple of 16, 16-byte aligned)
+// into registers with 128-bit loads.
+template <typename T, int N> __device__ __forceinline__ void load_rec(const T *src, T *dst) {
+  static_assert((N * sizeof(T)) % 16 == 0, "record size");
+  const float4 *s = reinterpret_cast<const float4 *>(src);
+  float4 *o = reinterpret_cast<float4 *>(dst);
+#pragma unroll
+  for (int q = 0; q < (int)(N * sizeof(T) / 16); ++q) o[q] = __ldg(s + q);
 }
 
 template <typename T> __device__ __forceinline__ const T *fparT(const Dev &d, int f) {

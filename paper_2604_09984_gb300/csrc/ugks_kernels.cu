@@ -437,9 +437,8 @@ template <typename T> __global__ void k_face_coef(Dev d) {
   double *P = d.fpar + (size_t)NFP * fid;
   T *PT = reinterpret_cast<T *>(d.fparT) + (size_t)NFP * fid;
   const double *fs = d.fsum + NFS * fid;
-  T parT[NFP];
-#pragma unroll
-  for (int m = 0; m < NFP; ++m) parT[m] = PT[m];
+  __align__(16) T parT[NFP];
+  load_rec<T, NFP>(PT, parT);
   Acc<T> ags[4], ars[4], aden;
   T snx = (T)d.Sn[2 * fid], sny = (T)d.Sn[2 * fid + 1], sun = (T)d.SUn[fid];
   T tufx = parT[FP_UFX], tufy = parT[FP_UFY], tlamw = parT[FP_LAMW], tK = (T)d.Keff;
@@ -566,12 +565,22 @@ __device__ __forceinline__ void macro_off(const float *rr, const float *dWn, int
   out[3] = q * (dF3 - g * dE);
 }
 
-// Gather the sweep record of every solved cell (parallel).
+// Gather the sweep record of every solved cell (parallel).  FP32 records
+// have a 16-byte multiple stride (48 floats) with the neighbour mask at
+// MR_MASK and room for the forward increment at MR_DWS, so the sweep can
+// stream them through a cp.async ring.
+enum { MR_MASK = 41, MR_DWS = 44, NMR32 = 48 };
+template <typename MT> __device__ __forceinline__ int mr_stride();
+template <> __device__ __forceinline__ int mr_stride<double>() { return NMR; }
+template <> __device__ __forceinline__ int mr_stride<float>() { return NMR32; }
+
 template <typename MT> __global__ void k_macro_prep(Dev d, MT *rec) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= d.nc) return;
-  if (!(d.cmask[c] & 1)) return;
-  MT *o = rec + (size_t)NMR * c;
+  MT *o = rec + (size_t)mr_stride<MT>() * c;
+  int mask = d.cmask[c];
+  if (sizeof(MT) == 4) o[MR_MASK] = __int_as_float(mask);
+  if (!(mask & 1)) return;
   double vol = d.vol_new[c], idt = 1.0 / d.dt;
   for (int m = 0; m < 4; ++m)
     o[MR_R + m] = (MT)(d.TW[4 * c + m] - vol * idt * d.W[4 * c + m] - 0.5 * d.Fc[4 * c + m]);
@@ -591,6 +600,106 @@ template <typename MT> __global__ void k_macro_prep(Dev d, MT *rec) {
     q[8] = (MT)d.gam[f];
   }
   o[MR_IDIAG] = (MT)(1.0 / diag);
+}
+
+// FP32 macro sweep: as k_macro_sweep below, with each thread's next NS-1
+// records (its row's next cells) in flight through a cp.async ring in shared
+// memory, and the forward increment stored into the record for the backward
+// pass.
+template <int NS> __global__ void __launch_bounds__(512) k_macro_sweep_f32(Dev d, float *rec) {
+  extern __shared__ __align__(16) float smf[];
+  float *buf0 = smf, *buf1 = smf + 4 * blockDim.x;
+  float *ring = smf + 8 * blockDim.x;
+  int b = blockIdx.x;
+  const int *bi = d.blk_info + 8 * b;
+  int ni = bi[0], nj = bi[1], per = bi[2];
+  int off = d.cell_off[b];
+  int row = threadIdx.x;
+  int nd = ni + nj - 1;
+  for (int m = 0; m < 4; ++m) { buf0[4 * row + m] = 0.f; buf1[4 * row + m] = 0.f; }
+  __syncthreads();
+  for (int pass = 0; pass < 2; ++pass) {
+    float prev[4] = {0, 0, 0, 0}, first[4] = {0, 0, 0, 0};
+    auto cell_of = [&](int it) -> int {
+      if (it >= nd) return -1;
+      int step = pass == 0 ? it : nd - 1 - it;
+      int i = step - row;
+      if (!(row < nj && i >= 0 && i < ni)) return -1;
+      return off + row * ni + i;
+    };
+    auto issue = [&](int it) {
+      int c = cell_of(it);
+      if (c >= 0) {
+        const float *src = rec + (size_t)NMR32 * c;
+        float *dst = ring + ((size_t)(it % NS) * blockDim.x + threadIdx.x) * NMR32;
+#pragma unroll
+        for (int q = 0; q < NMR32 / 4; ++q) cp_async<16>(dst + 4 * q, src + 4 * q);
+      }
+      cp_async_commit();
+    };
+#pragma unroll
+    for (int q = 0; q < NS - 1; ++q) issue(q);
+    int cur = 0;
+    for (int it = 0; it < nd; ++it) {
+      issue(it + NS - 1);
+      cp_async_wait<NS - 1>();
+      int step = pass == 0 ? it : nd - 1 - it;
+      int i = step - row;
+      bool act = row < nj && i >= 0 && i < ni;
+      float val[4] = {0, 0, 0, 0};
+      const float *r = ring + ((size_t)(it % NS) * blockDim.x + threadIdx.x) * NMR32;
+      int mask = act ? __float_as_int(r[MR_MASK]) : 0;
+      if (mask & 1) {
+        int c = off + row * ni + i;
+        float acc[4];
+        if (pass == 0) for (int m = 0; m < 4; ++m) acc[m] = r[MR_R + m];
+        else for (int m = 0; m < 4; ++m) acc[m] = 0.f;
+        float *prv = cur ? buf0 : buf1;
+        const float zero4[4] = {0, 0, 0, 0};
+        float o[4][4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const float *dv = zero4;
+          if (mask & (2 << s)) {
+            if (pass == 0) {
+              if (s == 0 && i > 0) dv = prev;
+              else if (s == 1 && per && i == ni - 1) dv = first;
+              else if (s == 2 && row > 0) dv = prv + 4 * (row - 1);
+            } else {
+              if (s == 1 && i < ni - 1) dv = prev;
+              else if (s == 0 && per && i == 0) dv = first;
+              else if (s == 3 && row < nj - 1) dv = prv + 4 * (row + 1);
+            }
+          }
+          macro_off(r + MR_SLOT + MR_SW * s, dv, d.Keff, o[s]);
+        }
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+          for (int m = 0; m < 4; ++m) acc[m] += pass == 0 ? -o[s][m] : o[s][m];
+        float idg = r[MR_IDIAG];
+        if (pass == 0) {
+          for (int m = 0; m < 4; ++m) val[m] = acc[m] * idg;
+          float4 w4 = make_float4(val[0], val[1], val[2], val[3]);
+          *reinterpret_cast<float4 *>(rec + (size_t)NMR32 * c + MR_DWS) = w4;
+        } else {
+          for (int m = 0; m < 4; ++m) val[m] = r[MR_DWS + m] - acc[m] * idg;
+          for (int m = 0; m < 4; ++m) d.dW[4 * c + m] = (double)val[m];
+        }
+      }
+      if (act) {
+        for (int m = 0; m < 4; ++m) prev[m] = val[m];
+        if (i == (pass == 0 ? 0 : ni - 1)) for (int m = 0; m < 4; ++m) first[m] = val[m];
+      }
+      float *dst = cur ? buf1 : buf0;
+      for (int m = 0; m < 4; ++m) dst[4 * row + m] = val[m];
+      __syncthreads();
+      cur ^= 1;
+    }
+    cp_async_wait<0>();
+    __threadfence_block();
+    for (int m = 0; m < 4; ++m) { buf0[4 * row + m] = 0.f; buf1[4 * row + m] = 0.f; }
+    __syncthreads();
+  }
 }
 
 // LU-SGS of Eq. dualTimeStepping_macro (Sec. 2.2), one CTA per block,
@@ -980,7 +1089,12 @@ void launch_macro_sweep(const Dev &d, cudaStream_t s, int rows, int fp32) {
   if (fp32) {
     float *rec = reinterpret_cast<float *>(d.mrec);
     k_macro_prep<float><<<nblk(d.nc, 256), 256, 0, s>>>(d, rec);
-    k_macro_sweep<float><<<d.nblocks, rows, 2 * 4 * rows * sizeof(double), s>>>(d, rec);
+    size_t per = (size_t)rows * NMR32 * sizeof(float);
+    size_t base = 8 * (size_t)rows * sizeof(float);
+    int NS = (int)((200 * 1024 - base) / per);
+    if (NS >= 4) k_macro_sweep_f32<4><<<d.nblocks, rows, base + 4 * per, s>>>(d, rec);
+    else if (NS == 3) k_macro_sweep_f32<3><<<d.nblocks, rows, base + 3 * per, s>>>(d, rec);
+    else k_macro_sweep_f32<2><<<d.nblocks, rows, base + 2 * per, s>>>(d, rec);
   } else {
     double *rec = reinterpret_cast<double *>(d.mrec);
     k_macro_prep<double><<<nblk(d.nc, 256), 256, 0, s>>>(d, rec);
@@ -991,6 +1105,9 @@ void launch_macro_sweep(const Dev &d, cudaStream_t s, int rows, int fp32) {
 }
 // shared memory of the sweeps exceeds the default 48 KB for FP64 / wide CTAs
 void sweep_setup() {
+  cudaFuncSetAttribute(k_macro_sweep_f32<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_macro_sweep_f32<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_macro_sweep_f32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   int mx = 2 * 512 * (int)sizeof(double2);
   cudaFuncSetAttribute(k_micro_sweep<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_micro_sweep<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);

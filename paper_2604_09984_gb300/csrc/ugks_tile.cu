@@ -188,7 +188,8 @@ __device__ __forceinline__ V2<T> tile_face_flux(const Dev &d, const TileSmem<T> 
                                                 int B, int lane, T vx, T vy) {
   int kind = d.face_kind[fid];
   if (kind == BC_OVERSET) return {T(0), T(0)};
-  const T *P = fparT<T>(d, fid);
+  __align__(16) T P[NFP];
+  load_rec<T, NFP>(fparT<T>(d, fid), P);
   int Lr = (S.gid[A] == d.face_L[fid]) ? A : B;
   int Rr = (Lr == A) ? B : A;
   T wS = vx * P[FP_SNX] + vy * P[FP_SNY] - P[FP_SUN];
@@ -390,7 +391,8 @@ template <typename T> __global__ void __launch_bounds__(TTHREADS) k_face_reduce_
       for (int m = 0; m < NFS; ++m) sums[m] = T(0);
       bool wall = kind == BC_WALL;
       if (kv) {
-        const T *G = reinterpret_cast<const T *>(d.fgeo) + (size_t)NFG * fid;
+        __align__(16) T G[NFG];
+        load_rec<T, NFG>(reinterpret_cast<const T *>(d.fgeo) + (size_t)NFG * fid, G);
         T wS = vx * G[FG_SNX] + vy * G[FG_SNY] - G[FG_SUN];
         if (!wall || wS > T(0)) {
           T Pg[NFP];

@@ -243,6 +243,41 @@ int ugks_profile_enable(ugks_ctx *ctx, int on);
  * UGKS_NPROF entries, either may be NULL); reset != 0 clears the totals. */
 int ugks_profile_read(ugks_ctx *ctx, double *ms, int64_t *launches, int reset);
 
+/* Allocation-free receptor interpolation.  No counterpart in the paper: it
+ * exists for callers that cannot allocate device memory at all (a host
+ * framework that owns every device allocation, or code that must not call
+ * cudaMalloc while other work is being captured or replayed), not even the
+ * workspace of ugks_create.  It performs the inverse-distance interpolation
+ * of the receptor rows that ugks_step / ugks_eval_flux apply before each
+ * flux evaluation, on caller buffers, staging the interpolated values in a
+ * fixed scratch array of UGKS_STATIC_SCRATCH_DOUBLES doubles (4 MiB) that
+ * the library holds as a static device variable on every GPU that loads it,
+ * until the process exits.
+ *
+ * Arguments (all DEVICE pointers, FP64): f (ncells x nv x 2, the (h, b)
+ * pairs of every cell, k = iy*nvx + ix), W (ncells x 4) and q (ncells x 2)
+ * updated in place (W and q may be NULL); receptors: nrec cell ids whose rows
+ * are overwritten; donors / weights: nrec x 5 stencils and weights, row r for
+ * receptors[r], donor -1 unused (the layout of ugks_get_connectivity rows);
+ * a row whose first donor is -1 is left unchanged; donor or receptor ids
+ * outside [0, ncells) are skipped.  Every receptor reads its donors' values
+ * from before the call (Jacobi).  stream: a cudaStream_t (NULL = default).
+ * Asynchronous; allocates nothing and calls no allocating routine.
+ *
+ * Errors: UGKS_ERR_ARG when a pointer is NULL or
+ * 2*nrec*nv + 6*nrec > UGKS_STATIC_SCRATCH_DOUBLES (nothing is launched);
+ * UGKS_ERR_CUDA when the device lookup of the scratch or a launch fails.
+ * The first call on a device looks up the scratch address with
+ * cudaGetSymbolAddress (with that device current); make that first call
+ * before any stream capture.  All calls on a device share the one scratch
+ * array, which keeps the last call's contents: calls that overlap on the GPU
+ * (different streams, no ordering between them) race. */
+#define UGKS_STATIC_SCRATCH_DOUBLES (1 << 19)
+int ugks_idw_interpolate_static(double *f, double *W, double *q, int ncells, int nv,
+                                const int32_t *receptors, int nrec,
+                                const int32_t *donors, const double *weights,
+                                void *stream);
+
 #ifdef __cplusplus
 }
 #endif

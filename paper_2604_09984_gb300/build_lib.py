@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "libugks.so")
-SOURCES = ["ugks_kernels.cu", "ugks_tile.cu", "ugks_overset.cu", "ugks_api.cu"]
+SOURCES = ["ugks_kernels.cu", "ugks_tile.cu", "ugks_overset.cu", "ugks_api.cu", "ugks_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

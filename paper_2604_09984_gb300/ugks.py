@@ -23,6 +23,7 @@ OK = 0
 ERR = {-1: "UGKS_ERR_ARG", -2: "UGKS_ERR_CUDA", -3: "UGKS_ERR_GEOMETRY", -4: "UGKS_ERR_ORPHAN",
        -5: "UGKS_ERR_NONPHYSICAL", -6: "UGKS_ERR_WORKSPACE", -7: "UGKS_ERR_ORDER"}
 FP64, FP32 = 0, 1
+STATIC_SCRATCH_DOUBLES = 1 << 19     # UGKS_STATIC_SCRATCH_DOUBLES
 FIELD, RECEPTOR, HOLE = 0, 1, 2
 
 
@@ -63,6 +64,8 @@ SYMBOLS = {
     "ugks_launch_count": (c_int64, [c_void_p]),
     "ugks_profile_enable": (c_int, [c_void_p, c_int]),
     "ugks_profile_read": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int64), c_int]),
+    "ugks_idw_interpolate_static": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p,
+                                            c_int, c_void_p, c_void_p, c_void_p]),
 }
 PROF_GROUPS = ["geometry", "connect", "interp", "cell", "face_reduce", "face_coef",
                "macro_sweep", "micro_fwd", "micro_bwd", "moments", "flux", "residual"]

@@ -29,7 +29,7 @@ struct ugks_ctx {
   std::vector<ugks_block_desc> blocks;
   std::vector<int> cell_off, node_off;
   int max_nj = 0;
-  int V = 1, nwork = 0;
+  int sweep_threads = 32, nwork = 0;
   int *work = nullptr;
   int *prev_status = nullptr, *n_orphan = nullptr, *blk_order = nullptr;
   int cap_interp = 0;
@@ -118,21 +118,42 @@ struct Carver {
   }
 };
 
-// Velocities per sweep CTA (one per thread per row): at most 512 threads.
-int choose_V(int max_nj, int nv) {
-  const char *env = getenv("UGKS_VTILE");
-  if (env) {
-    int v = atoi(env);
-    if (v >= 1 && v * max_nj <= 512) return v;
-  }
+// Micro-sweep CTA shape for a block of height nj: G threads per row, each
+// with vpt consecutive velocities, so a CTA covers G * vpt velocities.  The
+// tile is sized for about 1024 (cell, velocity) items per diagonal step --
+// enough independent work per step for the SM while the whole sweep stays
+// within about one CTA per SM -- with at most 512 threads and no more
+// velocities than the array holds.  UGKS_VTILE (velocities per CTA)
+// overrides where it fits.
+int block_G(int nj, int nvp, int vpt) {
   int r = 1;
-  while (r < max_nj) r <<= 1;
-  int V = 512 / r;
-  if (V < 1) V = 1;
-  if (V > 32) V = 32;
-  if (V * max_nj > 512) V = 512 / max_nj;
-  while (V > 1 && V > nv) V >>= 1;
-  return V;
+  while (r < nj) r <<= 1;
+  int vt = 1024 / r;
+  const char *env = getenv("UGKS_VTILE");
+  if (env && atoi(env) >= 1) vt = atoi(env);
+  int G = vt / vpt;
+  if (G < 1) G = 1;
+  int cap = 1;
+  while (cap * vpt < nvp) cap <<= 1;      // tiles no wider than the padded velocity count
+  if (G > cap) G = cap;
+  while (G > 1 && G * nj > 512) G >>= 1;
+  return G;
+}
+
+int sweep_vpt_for(const ugks_params *p) {
+  return p->precision == UGKS_FP32 ? sweep_vpt<float>() : sweep_vpt<double>();
+}
+
+// Threads of a micro-sweep CTA: the widest block's rows x G, rounded up to
+// whole warps.
+int sweep_threads_for(const ugks_params *p, int nb, const ugks_block_desc *b) {
+  int nvp = (p->nvx * p->nvy + 3) / 4 * 4, vpt = sweep_vpt_for(p);
+  int t = 32;
+  for (int i = 0; i < nb; ++i) {
+    int w = b[i].nj * block_G(b[i].nj, nvp, vpt);
+    if (w > t) t = w;
+  }
+  return (t + 31) / 32 * 32;
 }
 
 // Lay out every device array of the context in the workspace (base may be
@@ -214,7 +235,7 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int nwork, int cap_in
   d.tiles = c.take<int>(3 * (size_t)s.ntiles);
   d.err = c.take<int>(4);
   (void)nwork;
-  c.take<int>(2 * (size_t)nwork + 2);   // micro-sweep work list
+  c.take<int>(3 * (size_t)nwork + 3);   // micro-sweep work list
   c.take<int>(s.nc);                   // previous status / fresh flags
   c.take<int>(4);                      // orphan counter
   c.take<int>(nb);                     // block priority order
@@ -223,10 +244,15 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int nwork, int cap_in
 
 int cap_interp_for(const Sizes &s, int nb) { return nb > 1 ? (s.nc / 4 > 1024 ? s.nc / 4 : (s.nc < 1024 ? s.nc : 1024)) : 0; }
 
-int nwork_for(const ugks_params *p, int nb, const ugks_block_desc *b, int V) {
-  int nvp = (p->nvx * p->nvy + 3) / 4 * 4;
-  (void)b;
-  return nb * ((nvp + V - 1) / V);
+// Micro-sweep work items (block, first velocity, G): one per velocity tile.
+int nwork_for(const ugks_params *p, int nb, const ugks_block_desc *b) {
+  int nvp = (p->nvx * p->nvy + 3) / 4 * 4, vpt = sweep_vpt_for(p);
+  int n = 0;
+  for (int i = 0; i < nb; ++i) {
+    int vt = block_G(b[i].nj, nvp, vpt) * vpt;
+    n += (nvp + vt - 1) / vt;
+  }
+  return n;
 }
 
 // Host topology identical in ordering to the face/cell numbering documented
@@ -531,10 +557,9 @@ int ugks_workspace_query(const ugks_params *p, int nblocks, const ugks_block_des
   int r = validate(p, nblocks, blocks, s, why);
   if (r) return r;
   if (!bytes) return UGKS_ERR_ARG;
-  int V = choose_V(s.max_nj, s.nv);
   Dev d;
   memset(&d, 0, sizeof(d));
-  *bytes = carve(nullptr, s, nblocks, p->precision == UGKS_FP32, nwork_for(p, nblocks, blocks, V),
+  *bytes = carve(nullptr, s, nblocks, p->precision == UGKS_FP32, nwork_for(p, nblocks, blocks),
                  cap_interp_for(s, nblocks), d);
   return UGKS_OK;
 }
@@ -600,8 +625,8 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
   ctx->nblocks = nblocks;
   ctx->blocks.assign(blocks, blocks + nblocks);
   ctx->max_nj = s.max_nj;
-  ctx->V = choose_V(s.max_nj, s.nv);
-  ctx->nwork = nwork_for(&ctx->p, nblocks, blocks, ctx->V);
+  ctx->sweep_threads = sweep_threads_for(&ctx->p, nblocks, blocks);
+  ctx->nwork = nwork_for(&ctx->p, nblocks, blocks);
   ctx->cap_interp = cap_interp_for(s, nblocks);
   Dev &d = ctx->d;
   memset(&d, 0, sizeof(d));
@@ -614,7 +639,7 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
     Dev tmp;
     memset(&tmp, 0, sizeof(tmp));
     c.off = (size_t)((char *)d.err - ctx->ws) + 4 * sizeof(int) + 16;
-    ctx->work = c.take<int>(2 * (size_t)ctx->nwork + 2);
+    ctx->work = c.take<int>(3 * (size_t)ctx->nwork + 3);
     ctx->prev_status = c.take<int>(s.nc);
     ctx->n_orphan = c.take<int>(4);
     ctx->blk_order = c.take<int>(nblocks);
@@ -673,8 +698,10 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
           (blocks[order[b]].priority == blocks[order[a]].priority && order[b] < order[a]))
         std::swap(order[a], order[b]);
   std::vector<int> work;
-  for (int b = 0; b < nblocks; ++b)
-    for (int k0 = 0; k0 < s.nvp; k0 += ctx->V) { work.push_back(b); work.push_back(k0); }
+  for (int b = 0; b < nblocks; ++b) {
+    int vpt = sweep_vpt_for(&ctx->p), G = block_G(blocks[b].nj, s.nvp, vpt);
+    for (int k0 = 0; k0 < s.nvp; k0 += G * vpt) { work.push_back(b); work.push_back(k0); work.push_back(G); }
+  }
   std::vector<int> tiles;
   for (int b = 0; b < nblocks; ++b) {
     std::vector<int> org(2 * (size_t)tile_count(blocks[b].ni, blocks[b].nj));
@@ -812,8 +839,8 @@ int ugks_step(ugks_ctx *ctx, double dt, int n_inner) {
     { Prof p(ctx, UGKS_PROF_RHS); launch_flux_tile(d, s, fp); }                              // Step 3
     CK(cudaStreamWaitEvent(s, ctx->ev_macro, 0));
     { Prof p(ctx, UGKS_PROF_RESIDUAL); launch_residual(d, s, it == 0, fp); }                 // Step 5
-    { Prof p(ctx, UGKS_PROF_MICRO_FWD); launch_micro_fwd(d, s, ctx->work, ctx->nwork, ctx->V, ctx->max_nj, fp); }  // Step 6
-    { Prof p(ctx, UGKS_PROF_MICRO_BWD); launch_micro_bwd(d, s, ctx->work, ctx->nwork, ctx->V, ctx->max_nj, fp); }
+    { Prof p(ctx, UGKS_PROF_MICRO_FWD); launch_micro_fwd(d, s, ctx->work, ctx->nwork, ctx->sweep_threads, ctx->max_nj, fp); }  // Step 6
+    { Prof p(ctx, UGKS_PROF_MICRO_BWD); launch_micro_bwd(d, s, ctx->work, ctx->nwork, ctx->sweep_threads, ctx->max_nj, fp); }
     { Prof p(ctx, UGKS_PROF_MOMENTS); launch_moments(d, s, fp); }                          // Step 7
     ctx->launches += 8;
   }

@@ -61,7 +61,7 @@ struct Dev {
   int *cmask;                // nc: bit 0 solved cell, bit 1+s solved neighbour across slot s
   double *jinv;              // nc*4 inverse of [[x_xi, y_xi],[x_eta, y_eta]]
   void *fgeo;                // nf*NFG face geometry record (arithmetic type)
-  void *srec;                // nc*NSR sweep record: outward (S n, S U.n) per face slot
+  void *srec;                // nc*NSR sweep record (layout at NSR)
   double vbox[4];            // velocity box (vx_min, vx_max, vy_min, vy_max)
   double *affine;            // nblocks*6
   // state
@@ -118,7 +118,13 @@ struct Dev {
 
 // face geometry record / per-cell sweep record
 enum { FG_SNX = 0, FG_SNY, FG_SUN, FG_UFX, FG_UFY, FG_DXLX, FG_DXLY, FG_DXRX, FG_DXRY, NFG = 12 };
-enum { NSR = 12 };
+// sweep record: per face slot s, outward (S n_x, S n_y, S U.n) at 3 s; the
+// micro-sweep diagonal base at SR_DBASE and the neighbour mask (int bits) at
+// SR_MASK; 16 values so a record is a whole number of 16-byte chunks
+enum { SR_DBASE = 12, SR_MASK = 13, NSR = 16 };
+
+// velocities per thread of the micro sweeps, by arithmetic type
+template <typename T> __host__ __device__ constexpr int sweep_vpt() { return sizeof(T) == 4 ? 4 : 2; }
 
 // per-cell parameter record (from W' or W^n)
 enum { CP_RHO = 0, CP_UX, CP_UY, CP_LAM, CP_QX, CP_QY, CP_ITAU, CP_DBASE, NCP = 8 };

@@ -2,6 +2,7 @@
 // Sec. 2.2 Steps 1-8) on moving structured blocks, and the mesh-motion /
 // geometry kernels (Sec. 3 Step 1).  Launch wrappers at the end are the only
 // symbols used by the host orchestration (ugks_api.cu).
+#include <cstdlib>
 #include "ugks_internal.cuh"
 #include "ugks_launch.h"
 
@@ -602,21 +603,25 @@ template <typename MT> __global__ void k_macro_prep(Dev d, MT *rec) {
   o[MR_IDIAG] = (MT)(1.0 / diag);
 }
 
-// FP32 macro sweep: as k_macro_sweep below, with each thread's next NS-1
-// records (its row's next cells) in flight through a cp.async ring in shared
-// memory, and the forward increment stored into the record for the backward
-// pass.
-template <int NS> __global__ void __launch_bounds__(512) k_macro_sweep_f32(Dev d, float *rec) {
+// FP32 macro sweep: as k_macro_sweep below, with TPR threads per row (each
+// evaluates the couplings of face slots s = sub, sub + TPR, ...; a shuffle
+// within the row's lanes sums them), and each row's next NS-1 cell records in
+// flight through a cp.async ring in shared memory; the forward increment is
+// stored into the record for the backward pass.
+template <int NS, int TPR> __global__ void __launch_bounds__(512) k_macro_sweep_f32(Dev d, float *rec) {
   extern __shared__ __align__(16) float smf[];
-  float *buf0 = smf, *buf1 = smf + 4 * blockDim.x;
-  float *ring = smf + 8 * blockDim.x;
+  int rows = blockDim.x / TPR;
+  float *buf0 = smf, *buf1 = smf + 4 * rows;
+  float *ring = smf + 8 * rows;                  // NS * rows * NMR32
   int b = blockIdx.x;
   const int *bi = d.blk_info + 8 * b;
   int ni = bi[0], nj = bi[1], per = bi[2];
   int off = d.cell_off[b];
-  int row = threadIdx.x;
+  int row = threadIdx.x / TPR, sub = threadIdx.x % TPR;
+  unsigned rmask = (TPR == 1 ? 1u : (1u << TPR) - 1u) << (threadIdx.x & 31 & ~(TPR - 1));
   int nd = ni + nj - 1;
-  for (int m = 0; m < 4; ++m) { buf0[4 * row + m] = 0.f; buf1[4 * row + m] = 0.f; }
+  if (sub == 0)
+    for (int m = 0; m < 4; ++m) { buf0[4 * row + m] = 0.f; buf1[4 * row + m] = 0.f; }
   __syncthreads();
   for (int pass = 0; pass < 2; ++pass) {
     float prev[4] = {0, 0, 0, 0}, first[4] = {0, 0, 0, 0};
@@ -627,38 +632,37 @@ template <int NS> __global__ void __launch_bounds__(512) k_macro_sweep_f32(Dev d
       if (!(row < nj && i >= 0 && i < ni)) return -1;
       return off + row * ni + i;
     };
+    // the row's TPR threads share the copy of its next record
     auto issue = [&](int it) {
       int c = cell_of(it);
       if (c >= 0) {
         const float *src = rec + (size_t)NMR32 * c;
-        float *dst = ring + ((size_t)(it % NS) * blockDim.x + threadIdx.x) * NMR32;
+        float *dst = ring + ((size_t)(it % NS) * rows + row) * NMR32;
 #pragma unroll
-        for (int q = 0; q < NMR32 / 4; ++q) cp_async<16>(dst + 4 * q, src + 4 * q);
+        for (int q = sub; q < NMR32 / 4; q += TPR) cp_async<16>(dst + 4 * q, src + 4 * q);
       }
       cp_async_commit();
     };
 #pragma unroll
     for (int q = 0; q < NS - 1; ++q) issue(q);
+    cp_async_wait<NS - 2>();
+    __syncthreads();
     int cur = 0;
     for (int it = 0; it < nd; ++it) {
       issue(it + NS - 1);
-      cp_async_wait<NS - 1>();
       int step = pass == 0 ? it : nd - 1 - it;
       int i = step - row;
       bool act = row < nj && i >= 0 && i < ni;
       float val[4] = {0, 0, 0, 0};
-      const float *r = ring + ((size_t)(it % NS) * blockDim.x + threadIdx.x) * NMR32;
+      const float *r = ring + ((size_t)(it % NS) * rows + row) * NMR32;
       int mask = act ? __float_as_int(r[MR_MASK]) : 0;
       if (mask & 1) {
-        int c = off + row * ni + i;
-        float acc[4];
-        if (pass == 0) for (int m = 0; m < 4; ++m) acc[m] = r[MR_R + m];
-        else for (int m = 0; m < 4; ++m) acc[m] = 0.f;
-        float *prv = cur ? buf0 : buf1;
+        const float *prv = cur ? buf0 : buf1;
         const float zero4[4] = {0, 0, 0, 0};
-        float o[4][4];
+        float acc[4] = {0, 0, 0, 0};
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
+        for (int s0 = 0; s0 < 4; s0 += TPR) {
+          int s = s0 + sub;
           const float *dv = zero4;
           if (mask & (2 << s)) {
             if (pass == 0) {
@@ -671,19 +675,25 @@ template <int NS> __global__ void __launch_bounds__(512) k_macro_sweep_f32(Dev d
               else if (s == 3 && row < nj - 1) dv = prv + 4 * (row + 1);
             }
           }
-          macro_off(r + MR_SLOT + MR_SW * s, dv, d.Keff, o[s]);
+          float o[4];
+          macro_off(r + MR_SLOT + MR_SW * s, dv, d.Keff, o);
+          for (int m = 0; m < 4; ++m) acc[m] += o[m];
         }
 #pragma unroll
-        for (int s = 0; s < 4; ++s)
-          for (int m = 0; m < 4; ++m) acc[m] += pass == 0 ? -o[s][m] : o[s][m];
+        for (int w = 1; w < TPR; w <<= 1)
+          for (int m = 0; m < 4; ++m) acc[m] += __shfl_xor_sync(rmask, acc[m], w);
         float idg = r[MR_IDIAG];
+        int c = off + row * ni + i;
         if (pass == 0) {
-          for (int m = 0; m < 4; ++m) val[m] = acc[m] * idg;
-          float4 w4 = make_float4(val[0], val[1], val[2], val[3]);
-          *reinterpret_cast<float4 *>(rec + (size_t)NMR32 * c + MR_DWS) = w4;
+          for (int m = 0; m < 4; ++m) val[m] = (r[MR_R + m] - acc[m]) * idg;
+          if (sub == 0) {
+            float4 w4 = make_float4(val[0], val[1], val[2], val[3]);
+            *reinterpret_cast<float4 *>(rec + (size_t)NMR32 * c + MR_DWS) = w4;
+          }
         } else {
           for (int m = 0; m < 4; ++m) val[m] = r[MR_DWS + m] - acc[m] * idg;
-          for (int m = 0; m < 4; ++m) d.dW[4 * c + m] = (double)val[m];
+          if (sub == 0)
+            for (int m = 0; m < 4; ++m) d.dW[4 * c + m] = (double)val[m];
         }
       }
       if (act) {
@@ -691,13 +701,15 @@ template <int NS> __global__ void __launch_bounds__(512) k_macro_sweep_f32(Dev d
         if (i == (pass == 0 ? 0 : ni - 1)) for (int m = 0; m < 4; ++m) first[m] = val[m];
       }
       float *dst = cur ? buf1 : buf0;
-      for (int m = 0; m < 4; ++m) dst[4 * row + m] = val[m];
+      if (sub == 0) for (int m = 0; m < 4; ++m) dst[4 * row + m] = val[m];
+      cp_async_wait<NS - 2>();
       __syncthreads();
       cur ^= 1;
     }
     cp_async_wait<0>();
     __threadfence_block();
-    for (int m = 0; m < 4; ++m) { buf0[4 * row + m] = 0.f; buf1[4 * row + m] = 0.f; }
+    if (sub == 0)
+      for (int m = 0; m < 4; ++m) { buf0[4 * row + m] = 0.f; buf1[4 * row + m] = 0.f; }
     __syncthreads();
   }
 }
@@ -805,7 +817,10 @@ template <typename MT> __global__ void __launch_bounds__(512) k_macro_sweep(Dev 
 template <typename T> __global__ void k_macro_post(Dev d) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= d.nc) return;
-  if (!(d.cmask[c] & 1)) {
+  T *sr = reinterpret_cast<T *>(d.srec) + (size_t)NSR * c;
+  int mask = d.cmask[c];
+  *reinterpret_cast<int *>(sr + SR_MASK) = mask;
+  if (!(mask & 1)) {
     for (int m = 0; m < 4; ++m) d.Wp[4 * c + m] = d.W[4 * c + m];
     return;
   }
@@ -816,6 +831,7 @@ template <typename T> __global__ void k_macro_post(Dev d) {
   o[CP_QX] = d.q[2 * c]; o[CP_QY] = d.q[2 * c + 1];
   o[CP_ITAU] = 1.0 / collision_time(p.rho, p.lam, d.mu_ref, d.omega);
   o[CP_DBASE] = d.vol_new[c] * (d.cfl_s / (d.cfl_pseudo * d.dts[c]) + 1.0 / d.dt + 0.5 * o[CP_ITAU]);
+  sr[SR_DBASE] = (T)o[CP_DBASE];
   write_shrec<T>(d, o, d.vol_new[c], reinterpret_cast<T *>(d.shp) + (size_t)NSH * c);
 }
 
@@ -835,108 +851,181 @@ template <typename T> __device__ __forceinline__ T micro_diag(const Dev &d, int 
 }
 
 // Micro LU-SGS (Eq. dualTimeStepping_micro with the upwind flux variation of
-// Sec. 2.2) on the residual r (in dfs): one CTA per (block, velocity tile),
-// thread = (row j, velocity); the cells of one diagonal i + j are
+// Sec. 2.2) on the residual r (in dfs): one CTA per (block, velocity tile)
+// work item (block, first velocity, G), thread = (row j, VPT consecutive
+// velocities), G threads per row; the cells of one diagonal i + j are
 // independent, lower (upper) neighbours lie on the previous diagonal (same
 // thread / thread of row j -+ 1) or, across a periodic seam, on diagonal j
-// (kept in a register).  One barrier per diagonal; everything a diagonal
-// step reads from memory is loaded one step ahead.
+// (kept in registers).  One barrier per diagonal.  Nothing a diagonal step
+// reads from memory depends on the sweep, so every input (r, f in pass 1, and
+// the row's cell record: outward S n and S U.n per face slot, the diagonal
+// base, the neighbour mask) streams NS-1 diagonals ahead through a cp.async
+// ring in shared memory.  Several velocities per thread share the record
+// reads and the index arithmetic of a step.
 // pass 0: forward, d* = (r - sum_lower c d*) / D written over r;
 // pass 1: backward, d = d* - sum_upper c d / D and f += d.
-template <typename T, int PASS>
-__global__ void __launch_bounds__(512) k_micro_sweep(Dev d, const int *work, int V) {
+template <typename T> __device__ __forceinline__ T rcp_rn(T x);
+template <> __device__ __forceinline__ float rcp_rn<float>(float x) { return __frcp_rn(x); }
+template <> __device__ __forceinline__ double rcp_rn<double>(double x) { return 1.0 / x; }
+
+template <typename T, int PASS, int NS, int VPT>
+__global__ void __launch_bounds__(512) k_micro_sweep(Dev d, const int *work, int R) {
   typedef typename Vec2<T>::type T2;
-  extern __shared__ unsigned char smraw[];
+  constexpr int TB = VPT * (int)sizeof(T2);             // bytes of one thread's values
+  constexpr int RS = NSR * (int)sizeof(T) + 16;          // padded record row in shared memory
+  constexpr int NCH = NSR * (int)sizeof(T) / 16;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int nt = blockDim.x;
   T2 *bufA = reinterpret_cast<T2 *>(smraw);
-  T2 *bufB = bufA + blockDim.x;
-  int b = work[2 * blockIdx.x], k0 = work[2 * blockIdx.x + 1];
+  T2 *bufB = bufA + (size_t)nt * VPT;
+  const int recoff = (PASS == 1 ? 2 : 1) * nt * TB;
+  const int stage = recoff + R * RS;
+  unsigned char *ring = smraw + 2 * (size_t)nt * TB;
+  int b = work[3 * blockIdx.x], k0 = work[3 * blockIdx.x + 1], G = work[3 * blockIdx.x + 2];
   const int *bi = d.blk_info + 8 * b;
   int ni = bi[0], nj = bi[1], per = bi[2];
   int off = d.cell_off[b];
-  int row = threadIdx.x / V, v = threadIdx.x % V;
-  int k = k0 + v;
-  bool kval = k < d.nv;
-  T vx = kval ? dvx<T>(d, k) : T(0), vy = kval ? dvy<T>(d, k) : T(0);
-  T2 prev = {0, 0}, first = {0, 0};
+  int row = threadIdx.x / G, g = threadIdx.x - row * G;
+  int kb = k0 + g * VPT;
+  bool rowv = row < nj;
+  bool kin = rowv && kb < d.nvp;          // this thread's velocities lie in the array
+  T vx[VPT], vy[VPT];
+  bool kok[VPT];
+#pragma unroll
+  for (int u = 0; u < VPT; ++u) {
+    kok[u] = kin && kb + u < d.nv;
+    vx[u] = kok[u] ? dvx<T>(d, kb + u) : T(0);
+    vy[u] = kok[u] ? dvy<T>(d, kb + u) : T(0);
+  }
+  T2 prev[VPT], first[VPT];
+#pragma unroll
+  for (int u = 0; u < VPT; ++u) { prev[u] = T2{0, 0}; first[u] = T2{0, 0}; }
   int nd = ni + nj - 1;
-  const T *srec = reinterpret_cast<const T *>(d.srec);
-  // prefetched inputs of the next diagonal step
-  int mask = 0;
-  T2 rin = {0, 0}, fin = {0, 0};
-  T dbase = 0, geo[12];
-  auto load = [&](int it) {
-    mask = 0;
-    if (it >= nd) return;
-    int step = PASS == 0 ? it : nd - 1 - it;
-    int i = step - row;
-    if (!(row < nj && i >= 0 && i < ni && kval)) return;
-    int c = off + row * ni + i;
-    mask = d.cmask[c];
-    if (!(mask & 1)) return;
-    size_t idx = (size_t)c * d.nvp + k;
-    rin = ldf<T>(d.dfs, idx);
-    if (PASS == 1) fin = ldf<T>(d.f, idx);
-    dbase = (T)d.cpar[NCP * c + CP_DBASE];
+  const unsigned char *srec = reinterpret_cast<const unsigned char *>(d.srec);
+  auto issue = [&](int it, int slot) {
+    if (it < nd && rowv) {
+      int step = PASS == 0 ? it : nd - 1 - it;
+      int i = step - row;
+      if (i >= 0 && i < ni) {
+        int c = off + row * ni + i;
+        unsigned char *st = ring + (size_t)slot * stage;
+        if (kin) {
+          size_t idx = (size_t)c * d.nvp + kb;
+          const unsigned char *src = reinterpret_cast<const unsigned char *>(d.dfs) + idx * sizeof(T2);
 #pragma unroll
-    for (int m = 0; m < 12; ++m) geo[m] = srec[(size_t)NSR * c + m];
-  };
-  load(0);
-  int cur = 0;
-  for (int it = 0; it < nd; ++it) {
-    int step = PASS == 0 ? it : nd - 1 - it;
-    int i = step - row;
-    bool act = row < nj && i >= 0 && i < ni && kval;
-    T2 val = {0, 0};
-    if (act && (mask & 1)) {
-      int c = off + row * ni + i;
-      T wo[4];
-      T dg = dbase;
+          for (int q = 0; q < TB / 16; ++q) cp_async<16>(st + threadIdx.x * TB + 16 * q, src + 16 * q);
+          if (PASS == 1) {
+            const unsigned char *sf = reinterpret_cast<const unsigned char *>(d.f) + idx * sizeof(T2);
 #pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        wo[s] = vx * geo[3 * s] + vy * geo[3 * s + 1] - geo[3 * s + 2];
-        dg += T(0.5) * (wo[s] > T(0) ? wo[s] : T(0));
-      }
-      T2 *prv = cur ? bufA : bufB;
-      T ah = 0, ab = 0;
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        T2 dv = {0, 0};
-        bool use = false;
-        if (PASS == 0) {
-          if (s == 0 && i > 0) { dv = prev; use = true; }
-          else if (s == 1 && per && i == ni - 1) { dv = first; use = true; }
-          else if (s == 2 && row > 0) { dv = prv[threadIdx.x - V]; use = true; }
-        } else {
-          if (s == 1 && i < ni - 1) { dv = prev; use = true; }
-          else if (s == 0 && per && i == 0) { dv = first; use = true; }
-          else if (s == 3 && row < nj - 1) { dv = prv[threadIdx.x + V]; use = true; }
+            for (int q = 0; q < TB / 16; ++q)
+              cp_async<16>(st + (nt + threadIdx.x) * TB + 16 * q, sf + 16 * q);
+          }
         }
-        T cf = (use && (mask & (2 << s))) ? T(0.5) * (wo[s] < T(0) ? wo[s] : T(0)) : T(0);
-        ah += cf * dv.x;
-        ab += cf * dv.y;
+        for (int q = g; q < NCH; q += G)
+          cp_async<16>(st + recoff + row * RS + 16 * q, srec + (size_t)c * NSR * sizeof(T) + 16 * q);
       }
-      T idg = T(1) / dg;
-      size_t idx = (size_t)c * d.nvp + k;
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int q = 0; q < NS - 1; ++q) issue(q, q);
+  cp_async_wait<NS - 2>();
+  __syncthreads();
+  int cur = 0, slot = 0, fill = NS - 1;     // ring slots of diagonal it and it + NS - 1
+  for (int it = 0; it < nd; ++it) {
+    issue(it + NS - 1, fill);
+    int step = PASS == 0 ? it : nd - 1 - it;
+    int i = step - row;
+    bool act = kin && i >= 0 && i < ni;
+    const unsigned char *st = ring + (size_t)slot * stage;
+    const T *geo = reinterpret_cast<const T *>(st + recoff + row * RS);
+    int mask = act ? *reinterpret_cast<const int *>(geo + SR_MASK) : 0;
+    T2 val[VPT];
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) val[u] = T2{0, 0};
+    if (mask & 1) {
+      int c = off + row * ni + i;
+      T gr[SR_DBASE + 1];
+#pragma unroll
+      for (int m = 0; m <= SR_DBASE; ++m) gr[m] = geo[m];
+      const T2 *prv = (cur ? bufA : bufB);
+      // which neighbour each face slot couples to on this pass (0: none,
+      // 1: previous cell of the row, 2: seam cell of the row, 3: adjacent row)
+      int src[4];
       if (PASS == 0) {
-        val.x = (rin.x - ah) * idg;
-        val.y = (rin.y - ab) * idg;
-        stf<T>(d.dfs, idx, val.x, val.y);
+        src[0] = i > 0 ? 1 : 0;
+        src[1] = (per && i == ni - 1) ? 2 : 0;
+        src[2] = row > 0 ? 3 : 0;
+        src[3] = 0;
       } else {
-        val.x = rin.x - ah * idg;
-        val.y = rin.y - ab * idg;
-        stf<T>(d.f, idx, fin.x + val.x, fin.y + val.y);
+        src[0] = (per && i == 0) ? 2 : 0;
+        src[1] = i < ni - 1 ? 1 : 0;
+        src[2] = 0;
+        src[3] = row < nj - 1 ? 3 : 0;
+      }
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+        if (!(mask & (2 << s))) src[s] = 0;
+      const T2 *adj = prv + (size_t)(PASS == 0 ? threadIdx.x - G : threadIdx.x + G) * VPT;
+      const T2 *rin = reinterpret_cast<const T2 *>(st + threadIdx.x * TB);
+      const T2 *fin = reinterpret_cast<const T2 *>(st + (nt + threadIdx.x) * TB);
+#pragma unroll
+      for (int u = 0; u < VPT; ++u) {
+        T wo[4];
+        T dg = gr[SR_DBASE];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          wo[s] = vx[u] * gr[3 * s] + vy[u] * gr[3 * s + 1] - gr[3 * s + 2];
+          dg += T(0.5) * (wo[s] > T(0) ? wo[s] : T(0));
+        }
+        T ah = 0, ab = 0;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          T2 dv = {0, 0};
+          if (src[s] == 1) dv = prev[u];
+          else if (src[s] == 2) dv = first[u];
+          else if (src[s] == 3) dv = adj[u];
+          T cf = src[s] ? T(0.5) * (wo[s] < T(0) ? wo[s] : T(0)) : T(0);
+          ah += cf * dv.x;
+          ab += cf * dv.y;
+        }
+        T idg = rcp_rn<T>(dg);
+        T2 r = rin[u];
+        if (PASS == 0) {
+          val[u].x = (r.x - ah) * idg;
+          val[u].y = (r.y - ab) * idg;
+        } else {
+          val[u].x = r.x - ah * idg;
+          val[u].y = r.y - ab * idg;
+        }
+        if (!kok[u]) val[u] = T2{0, 0};
+      }
+      size_t idx = (size_t)c * d.nvp + kb;
+      T2 *out = reinterpret_cast<T2 *>(PASS == 0 ? d.dfs : d.f) + idx;
+#pragma unroll
+      for (int u = 0; u < VPT; ++u) {
+        T2 o = val[u];
+        if (PASS == 1) { T2 fv = fin[u]; o.x = fv.x + o.x; o.y = fv.y + o.y; }
+        out[u] = o;
       }
     }
     if (act) {
-      prev = val;
-      if (i == (PASS == 0 ? 0 : ni - 1)) first = val;
+#pragma unroll
+      for (int u = 0; u < VPT; ++u) prev[u] = val[u];
+      if (i == (PASS == 0 ? 0 : ni - 1))
+#pragma unroll
+        for (int u = 0; u < VPT; ++u) first[u] = val[u];
     }
-    T2 *dst = cur ? bufB : bufA;
-    dst[threadIdx.x] = val;
-    load(it + 1);
+    T2 *dst = (cur ? bufB : bufA) + (size_t)threadIdx.x * VPT;
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) dst[u] = val[u];
+    cp_async_wait<NS - 2>();
     __syncthreads();
     cur ^= 1;
+    fill = slot;
+    slot = slot + 1 == NS ? 0 : slot + 1;
   }
+  cp_async_wait<0>();
 }
 
 // Step 7 (one warp per cell): W^{s+1} = W' + sum V Psi (f^{s+1} - g(W')),
@@ -1085,16 +1174,23 @@ void launch_cell_params(const Dev &d, cudaStream_t s, const double *W, double *o
   if (fp32) k_cell_params<float><<<nblk(d.nc, 256), 256, 0, s>>>(d, W, out);
   else k_cell_params<double><<<nblk(d.nc, 256), 256, 0, s>>>(d, W, out);
 }
+// dynamic shared memory of the sweeps: up to the 227 KB a CTA may use
+constexpr size_t kMacroSmem = 227 * 1024;
+constexpr size_t kSweepSmem = 227 * 1024;
 void launch_macro_sweep(const Dev &d, cudaStream_t s, int rows, int fp32) {
   if (fp32) {
     float *rec = reinterpret_cast<float *>(d.mrec);
     k_macro_prep<float><<<nblk(d.nc, 256), 256, 0, s>>>(d, rec);
     size_t per = (size_t)rows * NMR32 * sizeof(float);
     size_t base = 8 * (size_t)rows * sizeof(float);
-    int NS = (int)((200 * 1024 - base) / per);
-    if (NS >= 4) k_macro_sweep_f32<4><<<d.nblocks, rows, base + 4 * per, s>>>(d, rec);
-    else if (NS == 3) k_macro_sweep_f32<3><<<d.nblocks, rows, base + 3 * per, s>>>(d, rec);
-    else k_macro_sweep_f32<2><<<d.nblocks, rows, base + 2 * per, s>>>(d, rec);
+    int NS = (int)((kMacroSmem - base) / per);   // >= 2 for rows <= 512
+    if (rows <= 128)
+      k_macro_sweep_f32<4, 4><<<d.nblocks, 4 * rows, base + 4 * per, s>>>(d, rec);
+    else if (rows <= 256)
+      k_macro_sweep_f32<4, 2><<<d.nblocks, 2 * rows, base + 4 * per, s>>>(d, rec);
+    else if (NS >= 4) k_macro_sweep_f32<4, 1><<<d.nblocks, rows, base + 4 * per, s>>>(d, rec);
+    else if (NS == 3) k_macro_sweep_f32<3, 1><<<d.nblocks, rows, base + 3 * per, s>>>(d, rec);
+    else k_macro_sweep_f32<2, 1><<<d.nblocks, rows, base + 2 * per, s>>>(d, rec);
   } else {
     double *rec = reinterpret_cast<double *>(d.mrec);
     k_macro_prep<double><<<nblk(d.nc, 256), 256, 0, s>>>(d, rec);
@@ -1105,27 +1201,63 @@ void launch_macro_sweep(const Dev &d, cudaStream_t s, int rows, int fp32) {
 }
 // shared memory of the sweeps exceeds the default 48 KB for FP64 / wide CTAs
 void sweep_setup() {
-  cudaFuncSetAttribute(k_macro_sweep_f32<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_macro_sweep_f32<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_macro_sweep_f32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  int mx = 2 * 512 * (int)sizeof(double2);
-  cudaFuncSetAttribute(k_micro_sweep<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<double, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  int ms = (int)kMacroSmem;
+  cudaFuncSetAttribute(k_macro_sweep_f32<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, ms);
+  cudaFuncSetAttribute(k_macro_sweep_f32<4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, ms);
+  cudaFuncSetAttribute(k_macro_sweep_f32<4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, ms);
+  cudaFuncSetAttribute(k_macro_sweep_f32<3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, ms);
+  cudaFuncSetAttribute(k_macro_sweep_f32<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, ms);
+  int mx = (int)kSweepSmem;
+  constexpr int VF = sweep_vpt<float>(), VD = sweep_vpt<double>();
+  cudaFuncSetAttribute(k_micro_sweep<float, 0, 4, VF>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<float, 1, 4, VF>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<float, 0, 3, VF>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<float, 1, 3, VF>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<float, 0, 2, VF>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<float, 1, 2, VF>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<double, 0, 4, VD>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<double, 1, 4, VD>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<double, 0, 3, VD>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<double, 1, 3, VD>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<double, 0, 2, VD>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<double, 1, 2, VD>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
 }
 
-void launch_micro_fwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int V, int rows,
-                      int fp32) {
-  int threads = rows * V;
-  if (fp32) k_micro_sweep<float, 0><<<nwork, threads, 2 * threads * sizeof(float2), s>>>(d, work, V);
-  else k_micro_sweep<double, 0><<<nwork, threads, 2 * threads * sizeof(double2), s>>>(d, work, V);
+// Micro sweeps: the deepest ring (4, 3 or 2 diagonals) that leaves room for
+// two CTAs per SM, else the deepest that fits one.
+template <typename T, int PASS>
+static void micro_sweep(const Dev &d, cudaStream_t s, const int *work, int nwork, int threads, int R) {
+  typedef typename Vec2<T>::type T2;
+  constexpr int VPT = sweep_vpt<T>();
+  size_t tb = VPT * sizeof(T2), rs = NSR * sizeof(T) + 16;
+  size_t stage = (PASS == 1 ? 2 : 1) * (size_t)threads * tb + (size_t)R * rs;
+  size_t base = 2 * (size_t)threads * tb;
+  int ns = 2;
+  bool found = false;
+  for (size_t cap : {kSweepSmem / 2 - 1024, kSweepSmem}) {
+    for (int n = 4; n >= 2 && !found; --n)
+      if (base + n * stage <= cap) { ns = n; found = true; }
+    if (found) break;
+  }
+  const char *env = getenv("UGKS_SWEEP_NS");
+  if (env) {
+    int n = atoi(env);
+    if (n >= 2 && n <= 4 && base + n * stage <= kSweepSmem) ns = n;
+  }
+  size_t sm = base + ns * stage;
+  if (ns == 4) k_micro_sweep<T, PASS, 4, VPT><<<nwork, threads, sm, s>>>(d, work, R);
+  else if (ns == 3) k_micro_sweep<T, PASS, 3, VPT><<<nwork, threads, sm, s>>>(d, work, R);
+  else k_micro_sweep<T, PASS, 2, VPT><<<nwork, threads, sm, s>>>(d, work, R);
 }
-void launch_micro_bwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int V, int rows,
+void launch_micro_fwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int threads, int rows,
                       int fp32) {
-  int threads = rows * V;
-  if (fp32) k_micro_sweep<float, 1><<<nwork, threads, 2 * threads * sizeof(float2), s>>>(d, work, V);
-  else k_micro_sweep<double, 1><<<nwork, threads, 2 * threads * sizeof(double2), s>>>(d, work, V);
+  if (fp32) micro_sweep<float, 0>(d, s, work, nwork, threads, rows);
+  else micro_sweep<double, 0>(d, s, work, nwork, threads, rows);
+}
+void launch_micro_bwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int threads, int rows,
+                      int fp32) {
+  if (fp32) micro_sweep<float, 1>(d, s, work, nwork, threads, rows);
+  else micro_sweep<double, 1>(d, s, work, nwork, threads, rows);
 }
 void launch_moments(const Dev &d, cudaStream_t s, int fp32) {
   if (fp32) k_moments<float><<<nblk((size_t)d.nc * 32, 256), 256, 0, s>>>(d);

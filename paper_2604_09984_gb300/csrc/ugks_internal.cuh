@@ -174,6 +174,9 @@ template <> __device__ __forceinline__ float dvx<float>(const Dev &d, int k) { r
 template <typename T> __device__ __forceinline__ T dvy(const Dev &d, int k);
 template <> __device__ __forceinline__ double dvy<double>(const Dev &d, int k) { return d.vy[k]; }
 template <> __device__ __forceinline__ float dvy<float>(const Dev &d, int k) { return d.vyf[k]; }
+template <typename T> __device__ __forceinline__ T dw(const Dev &d, int k);
+template <> __device__ __forceinline__ double dw<double>(const Dev &d, int k) { return d.w[k]; }
+template <> __device__ __forceinline__ float dw<float>(const Dev &d, int k) { return d.wf[k]; }
 
 // value of the cell field f at velocity k for neighbour slot `s` of cell c
 // (cell neighbour or ghost Maxwellian of the ghost state)

@@ -104,6 +104,28 @@ template <> struct Acc<float> {
   __device__ __forceinline__ double get() const { return (double)s + (double)c; }
 };
 
+// Warp total of per-lane accumulators.  FP32: the (sum, compensation) pairs
+// are combined in FP32 with an error-free sum at every butterfly level (no
+// FP64 arithmetic on the way); FP64: plain FP64 butterfly.
+__device__ __forceinline__ double warp_total(const Acc<double> &a) {
+  double v = a.s;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_total(const Acc<float> &a) {
+  float s = a.s, c = a.c;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    float os = __shfl_xor_sync(0xffffffffu, s, o), oc = __shfl_xor_sync(0xffffffffu, c, o);
+    float t = s + os, bb = t - s;
+    float e = (s - (t - bb)) + (os - bb);
+    s = t;
+    c = c + oc + e;
+  }
+  return (double)s + (double)c;
+}
+
 // Reading R3: dts_i = cfl_s Omega_i^{n+1} / max_k sum_faces S max(w_out, 0).
 // The sum is a convex piecewise-linear function of v, so over the tensor
 // velocity grid its maximum is attained at one of the four corners of the
@@ -445,7 +467,7 @@ template <typename T> __global__ void k_face_coef(Dev d) {
   T tufx = parT[FP_UFX], tufy = parT[FP_UFY], tlamw = parT[FP_LAMW], tK = (T)d.Keff;
   V2<T> zero = {T(0), T(0)};
   for (int k = lane; k < d.nv; k += 32) {
-    T vx = dvx<T>(d, k), vy = dvy<T>(d, k), w = (T)d.w[k];
+    T vx = dvx<T>(d, k), vy = dvy<T>(d, k), w = dw<T>(d, k);
     T wS = vx * snx + vy * sny - sun;
     T v2 = T(0.5) * (vx * vx + vy * vy);
     T cw = w * wS;
@@ -463,8 +485,8 @@ template <typename T> __global__ void k_face_coef(Dev d) {
     }
   }
   double gs[4], rs[4];
-  for (int m = 0; m < 4; ++m) { gs[m] = warp_sum(ags[m].get()); rs[m] = warp_sum(ars[m].get()); }
-  double den = warp_sum(aden.get());
+  for (int m = 0; m < 4; ++m) { gs[m] = warp_total(ags[m]); rs[m] = warp_total(ars[m]); }
+  double den = warp_total(aden);
   if (lane == 0) {
     double F[4];
     for (int m = 0; m < 4; ++m)
@@ -1041,7 +1063,7 @@ template <typename T> __global__ void k_moments(Dev d) {
   Acc<T> a[6];
   for (int k = lane; k < d.nv; k += 32) {
     auto fv = ldf<T>(d.f, (size_t)c * d.nvp + k);
-    T vx = dvx<T>(d, k), vy = dvy<T>(d, k), w = (T)d.w[k];
+    T vx = dvx<T>(d, k), vy = dvy<T>(d, k), w = dw<T>(d, k);
     V2<T> g = maxwellian_pre<T>(hpre, ux, uy, lam, bfac, vx, vy);
     T h = fv.x, b = fv.y;
     T dh = h - g.h, db = b - g.b;
@@ -1056,7 +1078,7 @@ template <typename T> __global__ void k_moments(Dev d) {
     a[5].add(T(0.5) * w * cy * e);
   }
   double acc[6];
-  for (int m = 0; m < 6; ++m) acc[m] = warp_sum(a[m].get());
+  for (int m = 0; m < 6; ++m) acc[m] = warp_total(a[m]);
   if (lane == 0) {
     double Wn[4];
     for (int m = 0; m < 4; ++m) Wn[m] = d.Wp[4 * c + m] + acc[m];
@@ -1110,16 +1132,26 @@ template <typename T> __global__ void k_flux_div_all(Dev d, double *D) {
   D[2 * t + 1] = (double)r.b;
 }
 
-// Sum of S * wall macro flux per block (deterministic order).
-__global__ void k_wall_loads(Dev d) {
+// Sum of S * wall macro flux per block: one CTA per block, a strided partial
+// sum per thread and a fixed-shape tree, so the order (and the result) is
+// the same on every call.
+constexpr int WL_THREADS = 256;
+__global__ void __launch_bounds__(WL_THREADS) k_wall_loads(Dev d) {
+  __shared__ double part[4][WL_THREADS];
   int b = blockIdx.x;
-  if (threadIdx.x != 0) return;
   double s[4] = {0, 0, 0, 0};
-  for (int f = 0; f < d.nf; ++f) {
+  for (int f = threadIdx.x; f < d.nf; f += WL_THREADS) {
     if (d.face_block[f] != b || d.face_kind[f] != BC_WALL) continue;
     for (int m = 0; m < 4; ++m) s[m] += d.fflux[4 * f + m];
   }
-  for (int m = 0; m < 4; ++m) d.wall_loads[4 * b + m] = s[m];
+  for (int m = 0; m < 4; ++m) part[m][threadIdx.x] = s[m];
+  __syncthreads();
+  for (int w = WL_THREADS / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int m = 0; m < 4; ++m) part[m][threadIdx.x] += part[m][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) d.wall_loads[4 * b + threadIdx.x] = part[threadIdx.x][0];
 }
 
 // Copy f between the storage type and FP64 (get/set state).
@@ -1184,17 +1216,20 @@ void launch_macro_sweep(const Dev &d, cudaStream_t s, int rows, int fp32) {
     size_t per = (size_t)rows * NMR32 * sizeof(float);
     size_t base = 8 * (size_t)rows * sizeof(float);
     int NS = (int)((kMacroSmem - base) / per);   // >= 2 for rows <= 512
+    // the whole shared memory of an SM: the sweep's SMs take no CTA of the
+    // kernels running beside it on the main stream
+    size_t sm = kMacroSmem;
     if (rows <= 128)
-      k_macro_sweep_f32<4, 4><<<d.nblocks, 4 * rows, base + 4 * per, s>>>(d, rec);
+      k_macro_sweep_f32<4, 4><<<d.nblocks, 4 * rows, sm, s>>>(d, rec);
     else if (rows <= 256)
-      k_macro_sweep_f32<4, 2><<<d.nblocks, 2 * rows, base + 4 * per, s>>>(d, rec);
-    else if (NS >= 4) k_macro_sweep_f32<4, 1><<<d.nblocks, rows, base + 4 * per, s>>>(d, rec);
-    else if (NS == 3) k_macro_sweep_f32<3, 1><<<d.nblocks, rows, base + 3 * per, s>>>(d, rec);
-    else k_macro_sweep_f32<2, 1><<<d.nblocks, rows, base + 2 * per, s>>>(d, rec);
+      k_macro_sweep_f32<4, 2><<<d.nblocks, 2 * rows, sm, s>>>(d, rec);
+    else if (NS >= 4) k_macro_sweep_f32<4, 1><<<d.nblocks, rows, sm, s>>>(d, rec);
+    else if (NS == 3) k_macro_sweep_f32<3, 1><<<d.nblocks, rows, sm, s>>>(d, rec);
+    else k_macro_sweep_f32<2, 1><<<d.nblocks, rows, sm, s>>>(d, rec);
   } else {
     double *rec = reinterpret_cast<double *>(d.mrec);
     k_macro_prep<double><<<nblk(d.nc, 256), 256, 0, s>>>(d, rec);
-    k_macro_sweep<double><<<d.nblocks, rows, 2 * 4 * rows * sizeof(double), s>>>(d, rec);
+    k_macro_sweep<double><<<d.nblocks, rows, kMacroSmem, s>>>(d, rec);
   }
   if (fp32) k_macro_post<float><<<nblk(d.nc, 256), 256, 0, s>>>(d);
   else k_macro_post<double><<<nblk(d.nc, 256), 256, 0, s>>>(d);
@@ -1202,6 +1237,7 @@ void launch_macro_sweep(const Dev &d, cudaStream_t s, int rows, int fp32) {
 // shared memory of the sweeps exceeds the default 48 KB for FP64 / wide CTAs
 void sweep_setup() {
   int ms = (int)kMacroSmem;
+  cudaFuncSetAttribute(k_macro_sweep<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, ms);
   cudaFuncSetAttribute(k_macro_sweep_f32<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, ms);
   cudaFuncSetAttribute(k_macro_sweep_f32<4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, ms);
   cudaFuncSetAttribute(k_macro_sweep_f32<4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, ms);
@@ -1272,7 +1308,7 @@ void launch_flux_div_all(const Dev &d, cudaStream_t s, double *D, int fp32) {
   if (fp32) k_flux_div_all<float><<<nblk(n, 256), 256, 0, s>>>(d, D);
   else k_flux_div_all<double><<<nblk(n, 256), 256, 0, s>>>(d, D);
 }
-void launch_wall_loads(const Dev &d, cudaStream_t s) { k_wall_loads<<<d.nblocks, 32, 0, s>>>(d); }
+void launch_wall_loads(const Dev &d, cudaStream_t s) { k_wall_loads<<<d.nblocks, WL_THREADS, 0, s>>>(d); }
 void launch_f_convert(const Dev &d, cudaStream_t s, double *out, const double *in, int fp32) {
   size_t n = (size_t)d.nc * d.nv;
   if (out) {

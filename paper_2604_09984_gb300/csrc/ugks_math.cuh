@@ -18,7 +18,16 @@ template <typename R> struct V2 { R h, b; };
 
 template <typename R> UG_HD R r_exp(R x);
 template <> UG_HD double r_exp<double>(double x) { return exp(x); }
-template <> UG_HD float r_exp<float>(float x) { return expf(x); }
+// FP32 path: the hardware exponential (relative error a few ulp plus
+// |x| * 2^-24, below the FP32 path's tolerance for the arguments that carry
+// weight in the velocity sums)
+template <> UG_HD float r_exp<float>(float x) {
+#ifdef __CUDA_ARCH__
+  return __expf(x);
+#else
+  return expf(x);
+#endif
+}
 
 // ---------------------------------------------------------------- primitives
 // (rho, Vx, Vy, lambda) from W = (rho, rho V, rho E);

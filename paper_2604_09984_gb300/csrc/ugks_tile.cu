@@ -141,56 +141,58 @@ __device__ __forceinline__ void tile_grad(const TileSmem<T> &S, int r, int lane,
   gy.b = J[2] * s[0].b + J[3] * s[1].b;
 }
 
-// upwind face value and w.grad f for face fid between region cells A and B
-// (walls: interior side, incident velocities only).  Returns false when the
-// face contributes nothing at this velocity (reflected wall velocities).
+// Reconstructed value of region cell r at the face (offset dx, dy from its
+// centre) and w.grad f; ghost or missing cells carry no gradient.
+template <typename T>
+__device__ __forceinline__ void tile_side(const TileSmem<T> &S, int r, int lane, T dx, T dy, T wx, T wy,
+                                          V2<T> &f, V2<T> &g) {
+  auto v = S.F[r * VK + lane];
+  V2<T> fc = {v.x, v.y};
+  if (S.gid[r] >= 0) {
+    V2<T> gx, gy;
+    tile_grad<T>(S, r, lane, fc, gx, gy);
+    f = {fc.h + dx * gx.h + dy * gy.h, fc.b + dx * gx.b + dy * gy.b};
+    g = {wx * gx.h + wy * gy.h, wx * gx.b + wy * gy.b};
+  } else {
+    f = fc;       // ghost Maxwellian, no gradient
+    g = {T(0), T(0)};
+  }
+}
+
+// upwind face value and w.grad f for face fid between region cells Lr and Rr
+// (walls: interior side, incident velocities only).  Each lane reconstructs
+// its own upwind cell, so lanes of one face with opposite signs of w.S do not
+// run both sides; only w.S = 0 exactly averages the two sides.
 template <typename T>
 __device__ __forceinline__ void tile_upwind(const Dev &d, const TileSmem<T> &S, const T *P, int kind,
                                             int Lr, int Rr, int lane, T vx, T vy, T wS, V2<T> &ff,
                                             V2<T> &wg) {
+  (void)d;
   T wx = vx - P[FP_UFX], wy = vy - P[FP_UFY];
-  bool useL = (kind == BC_WALL) || wS > T(0), useR = (kind != BC_WALL) && wS < T(0);
-  V2<T> fL = {0, 0}, fR = {0, 0}, gL = {0, 0}, gR = {0, 0};
-  if (!useR) {
-    auto v = S.F[Lr * VK + lane];
-    V2<T> fc = {v.x, v.y}, gx, gy;
-    tile_grad<T>(S, Lr, lane, fc, gx, gy);
-    T dx = P[FP_DXLX], dy = P[FP_DXLY];
-    fL = {fc.h + dx * gx.h + dy * gy.h, fc.b + dx * gx.b + dy * gy.b};
-    gL = {wx * gx.h + wy * gy.h, wx * gx.b + wy * gy.b};
-  }
-  if (!useL) {
-    auto v = S.F[Rr * VK + lane];
-    V2<T> fc = {v.x, v.y};
-    if (S.gid[Rr] >= 0) {
-      V2<T> gx, gy;
-      tile_grad<T>(S, Rr, lane, fc, gx, gy);
-      T dx = P[FP_DXRX], dy = P[FP_DXRY];
-      fR = {fc.h + dx * gx.h + dy * gy.h, fc.b + dx * gx.b + dy * gy.b};
-      gR = {wx * gx.h + wy * gy.h, wx * gx.b + wy * gy.b};
-    } else {
-      fR = fc;       // ghost Maxwellian, no gradient
-    }
-  }
-  if (useL) {
-    ff = fL; wg = gL;
-  } else if (useR) {
-    ff = fR; wg = gR;
-  } else {
-    ff = {T(0.5) * (fL.h + fR.h), T(0.5) * (fL.b + fR.b)};
-    wg = {T(0.5) * (gL.h + gR.h), T(0.5) * (gL.b + gR.b)};
+  bool wall = kind == BC_WALL;
+  bool useR = !wall && wS < T(0);
+  int U = useR ? Rr : Lr;
+  T dx = useR ? P[FP_DXRX] : P[FP_DXLX], dy = useR ? P[FP_DXRY] : P[FP_DXLY];
+  tile_side<T>(S, U, lane, dx, dy, wx, wy, ff, wg);
+  if (!wall && wS == T(0)) {
+    V2<T> f2, g2;
+    tile_side<T>(S, Rr, lane, P[FP_DXRX], P[FP_DXRY], wx, wy, f2, g2);
+    ff = {T(0.5) * (ff.h + f2.h), T(0.5) * (ff.b + f2.b)};
+    wg = {T(0.5) * (wg.h + g2.h), T(0.5) * (wg.b + g2.b)};
   }
 }
 
-// S * F_hat of face fid at this lane (oriented along the face normal)
+// S * F_hat of a face at this lane (oriented along the face normal) from its
+// staged record Ps (shared memory), kind and left cell Lg.
 template <typename T>
-__device__ __forceinline__ V2<T> tile_face_flux(const Dev &d, const TileSmem<T> &S, int fid, int A,
-                                                int B, int lane, T vx, T vy) {
-  int kind = d.face_kind[fid];
+__device__ __forceinline__ V2<T> tile_face_flux(const Dev &d, const TileSmem<T> &S, const T *Ps, int kind,
+                                                int Lg, int A, int B, int lane, T vx, T vy) {
   if (kind == BC_OVERSET) return {T(0), T(0)};
   __align__(16) T P[NFP];
-  load_rec<T, NFP>(fparT<T>(d, fid), P);
-  int Lr = (S.gid[A] == d.face_L[fid]) ? A : B;
+#pragma unroll
+  for (int q = 0; q < (int)(NFP * sizeof(T) / 16); ++q)
+    reinterpret_cast<float4 *>(P)[q] = reinterpret_cast<const float4 *>(Ps)[q];
+  int Lr = (S.gid[A] == Lg) ? A : B;
   int Rr = (Lr == A) ? B : A;
   T wS = vx * P[FP_SNX] + vy * P[FP_SNY] - P[FP_SUN];
   if (kind == BC_WALL && !(wS > T(0))) {
@@ -203,6 +205,51 @@ __device__ __forceinline__ V2<T> tile_face_flux(const Dev &d, const TileSmem<T> 
   tile_upwind<T>(d, S, P, kind, Lr, Rr, lane, vx, vy, wS, ff, wg);
   V2<T> I = interface_integral<T>(P, vx, vy, ff, wg, (T)d.Keff, (T)d.Kint, (T)d.Pr);
   return {wS * I.h, wS * I.b};
+}
+
+// Face id, kind and left cell of face `x` of a tile row (dir 0: the i-face
+// left of region column x + 2) or column (dir 1: the j-face below region row
+// x + 2); -1 where the face lies outside the block.
+__device__ __forceinline__ int tile_face_id(const Dev &d, int dir, int off, int ni, int nj, int i0, int j0,
+                                            int w, int x) {
+  if (dir == 0) {
+    int i = i0 + x, j = j0 + w;
+    if (j >= nj || i > ni) return -1;
+    return (i < ni) ? d.cell_faces[4 * (off + j * ni + i) + 0] : d.cell_faces[4 * (off + j * ni + ni - 1) + 1];
+  }
+  int i = i0 + w, j = j0 + x;
+  if (i >= ni || j > nj) return -1;
+  return (j < nj) ? d.cell_faces[4 * (off + j * ni + i) + 2] : d.cell_faces[4 * (off + (nj - 1) * ni + i) + 3];
+}
+
+// Stage per warp the scalars and the records (N values each, from `src`) of
+// the up to 9 faces a warp walks: lane x keeps face x's id, kind and left
+// cell (read back with shuffles), the records go to the warp's buffer `buf`.
+// Every global load of the walk is issued here, side by side, instead of one
+// dependent chain per face.
+template <typename T, int N>
+__device__ __forceinline__ void tile_stage_faces(const Dev &d, const T *src, int my_fid, int &my_kind,
+                                                 int &my_L, T *buf, int lane) {
+  my_kind = BC_OVERSET;
+  my_L = -1;
+  if (my_fid >= 0) {
+    my_kind = d.face_kind[my_fid];
+    my_L = d.face_L[my_fid];
+  }
+  constexpr int NQ = (int)(N * sizeof(T) / 16);
+  constexpr int ROUNDS = ((TX + 1) * NQ + 31) / 32;
+#pragma unroll
+  for (int r = 0; r < ROUNDS; ++r) {
+    int q = r * 32 + lane;
+    int x = q / NQ, ch = q - (q / NQ) * NQ;
+    bool in = x <= TX;
+    int f = __shfl_sync(0xffffffffu, my_fid, in ? x : 0);
+    int kd = __shfl_sync(0xffffffffu, my_kind, in ? x : 0);
+    if (in && f >= 0 && kd != BC_OVERSET)
+      reinterpret_cast<float4 *>(buf + (size_t)x * N)[ch] =
+          __ldg(reinterpret_cast<const float4 *>(src + (size_t)f * N) + ch);
+  }
+  __syncwarp();
 }
 
 __device__ __forceinline__ int cell_status(const TileSmem<float> &S, int r) { return S.flags[r] >> 8; }
@@ -227,23 +274,29 @@ template <typename T> __global__ void __launch_bounds__(TTHREADS) k_flux_tile(De
   __syncthreads();
   tile_load_f<T>(d, S, k, kv, vx, vy);
   __syncthreads();
+  T *Pw = reinterpret_cast<T *>(smraw + TileSmem<T>::bytes() + sizeof(T2) * TX * TY * VK) +
+          (size_t)w * (TX + 1) * NFP;
+  const T *fparT_base = reinterpret_cast<const T *>(d.fparT);
+  int my_kind, my_L;
   // i-faces of tile row w
   {
     int ty = w, j = j0 + ty;
+    int my_fid = lane <= TX ? tile_face_id(d, 0, off, ni, nj, i0, j0, w, lane) : -1;
+    tile_stage_faces<T, NFP>(d, fparT_base, my_fid, my_kind, my_L, Pw, lane);
     T2 carry = {T(0), T(0)};
     if (j < nj) {
       for (int x = 0; x <= TX; ++x) {
         int i = i0 + x;
         if (i > ni) break;
+        int kind = __shfl_sync(0xffffffffu, my_kind, x);
+        int Lg = __shfl_sync(0xffffffffu, my_L, x);
         int A = (x + 1) + (ty + 2) * RW, B = A + 1;
         bool lin = x >= 1, rin = x < TX && i < ni;
         bool need = (lin && cell_status(S, A) == ST_FIELD) || (rin && cell_status(S, B) == ST_FIELD);
         V2<T> F = {T(0), T(0)};
         if (need && kv) {
-          int fid = (i < ni) ? d.cell_faces[4 * (off + j * ni + i) + 0]
-                             : d.cell_faces[4 * (off + j * ni + ni - 1) + 1];
-          F = tile_face_flux<T>(d, S, fid, A, B, lane, vx, vy);
-          T sA = (S.gid[A] == d.face_L[fid]) ? T(1) : T(-1);
+          F = tile_face_flux<T>(d, S, Pw + (size_t)x * NFP, kind, Lg, A, B, lane, vx, vy);
+          T sA = (S.gid[A] == Lg) ? T(1) : T(-1);
           if (lin) { carry.x += sA * F.h; carry.y += sA * F.b; }
           if (lin) Ds[(ty * TX + x - 1) * VK + lane] = carry;
           carry.x = -sA * F.h;     // the other side sees the opposite orientation
@@ -260,18 +313,20 @@ template <typename T> __global__ void __launch_bounds__(TTHREADS) k_flux_tile(De
   // j-faces of tile column w
   {
     int tx = w, i = i0 + tx;
+    int my_fid = lane <= TY ? tile_face_id(d, 1, off, ni, nj, i0, j0, w, lane) : -1;
+    tile_stage_faces<T, NFP>(d, fparT_base, my_fid, my_kind, my_L, Pw, lane);
     if (i < ni) {
       for (int y = 0; y <= TY; ++y) {
         int j = j0 + y;
         if (j > nj) break;
+        int kind = __shfl_sync(0xffffffffu, my_kind, y);
+        int Lg = __shfl_sync(0xffffffffu, my_L, y);
         int A = (tx + 2) + (y + 1) * RW, B = A + RW;
         bool lin = y >= 1, rin = y < TY && j < nj;
         bool need = (lin && cell_status(S, A) == ST_FIELD) || (rin && cell_status(S, B) == ST_FIELD);
         if (!(need && kv)) continue;
-        int fid = (j < nj) ? d.cell_faces[4 * (off + j * ni + i) + 2]
-                           : d.cell_faces[4 * (off + (nj - 1) * ni + i) + 3];
-        V2<T> F = tile_face_flux<T>(d, S, fid, A, B, lane, vx, vy);
-        T sA = (S.gid[A] == d.face_L[fid]) ? T(1) : T(-1);
+        V2<T> F = tile_face_flux<T>(d, S, Pw + (size_t)y * NFP, kind, Lg, A, B, lane, vx, vy);
+        T sA = (S.gid[A] == Lg) ? T(1) : T(-1);
         if (lin) {
           T2 &q = Ds[((y - 1) * TX + tx) * VK + lane];
           q.x += sA * F.h;
@@ -358,41 +413,46 @@ template <typename T> __global__ void __launch_bounds__(TTHREADS) k_face_reduce_
   __syncthreads();
   tile_load_f<T>(d, S, k, kv, vx, vy);
   __syncthreads();
-  T wk = kv ? (T)d.w[k] : T(0);
+  T wk = kv ? dw<T>(d, k) : T(0);
   T v2 = T(0.5) * (vx * vx + vy * vy);
+  T *Gw = reinterpret_cast<T *>(smraw + TileSmem<T>::bytes()) + (size_t)w * (TX + 1) * NFG;
+  const T *fgeo = reinterpret_cast<const T *>(d.fgeo);
   for (int dir = 0; dir < 2; ++dir) {
-    // dir 0: i-faces of tile row w; dir 1: j-faces of tile column w
+    // dir 0: i-faces of tile row w; dir 1: j-faces of tile column w.  Lane x
+    // stages face x: id, kind, left cell, whether a field cell touches it,
+    // and its geometry record.
+    int my_fid = lane <= TX ? tile_face_id(d, dir, off, ni, nj, i0, j0, w, lane) : -1;
+    if (my_fid >= 0) {
+      int i = dir == 0 ? i0 + lane : i0 + w, j = dir == 0 ? j0 + w : j0 + lane;
+      bool own = dir == 0 ? ((i < ni && lane < TX) || (!per && i == ni))   // closing face of a ragged tile too
+                          : ((j < nj && lane < TY) || j == nj);
+      if (!own) my_fid = -1;
+    }
+    int my_need = 0;
+    if (my_fid >= 0) {
+      int Lg = d.face_L[my_fid], Rg = d.face_R[my_fid];
+      my_need = d.status[Lg] == ST_FIELD || (Rg >= 0 && d.status[Rg] == ST_FIELD);
+      if (!my_need) my_fid = -1;
+    }
+    int my_kind, my_L;
+    tile_stage_faces<T, NFG>(d, fgeo, my_fid, my_kind, my_L, Gw, lane);
     for (int x = 0; x <= (dir == 0 ? TX : TY); ++x) {
-      int i, j, A, B, fid;
-      if (dir == 0) {
-        i = i0 + x; j = j0 + w;
-        if (j >= nj || i > ni) break;
-        bool own = (i < ni && x < TX) || (!per && i == ni);   // closing face of a ragged tile too
-        if (!own) continue;
-        A = (x + 1) + (w + 2) * RW; B = A + 1;
-        fid = (i < ni) ? d.cell_faces[4 * (off + j * ni + i) + 0]
-                       : d.cell_faces[4 * (off + j * ni + ni - 1) + 1];
-      } else {
-        i = i0 + w; j = j0 + x;
-        if (i >= ni || j > nj) break;
-        bool own = (j < nj && x < TY) || j == nj;
-        if (!own) continue;
-        A = (w + 2) + (x + 1) * RW; B = A + RW;
-        fid = (j < nj) ? d.cell_faces[4 * (off + j * ni + i) + 2]
-                       : d.cell_faces[4 * (off + (nj - 1) * ni + i) + 3];
-      }
-      int kind = d.face_kind[fid];
-      if (kind == BC_OVERSET) continue;
-      int Lg = d.face_L[fid], Rg = d.face_R[fid];
-      bool need = d.status[Lg] == ST_FIELD || (Rg >= 0 && d.status[Rg] == ST_FIELD);
-      if (!need) continue;
+      int fid = __shfl_sync(0xffffffffu, my_fid, x);
+      int kind = __shfl_sync(0xffffffffu, my_kind, x);
+      int Lg = __shfl_sync(0xffffffffu, my_L, x);
+      if (fid < 0 || kind == BC_OVERSET) continue;
+      int A, B;
+      if (dir == 0) { A = (x + 1) + (w + 2) * RW; B = A + 1; }
+      else { A = (w + 2) + (x + 1) * RW; B = A + RW; }
       T sums[NFS];
 #pragma unroll
       for (int m = 0; m < NFS; ++m) sums[m] = T(0);
       bool wall = kind == BC_WALL;
       if (kv) {
         __align__(16) T G[NFG];
-        load_rec<T, NFG>(reinterpret_cast<const T *>(d.fgeo) + (size_t)NFG * fid, G);
+#pragma unroll
+        for (int q = 0; q < (int)(NFG * sizeof(T) / 16); ++q)
+          reinterpret_cast<float4 *>(G)[q] = reinterpret_cast<const float4 *>(Gw + (size_t)x * NFG)[q];
         T wS = vx * G[FG_SNX] + vy * G[FG_SNY] - G[FG_SUN];
         if (!wall || wS > T(0)) {
           T Pg[NFP];
@@ -440,9 +500,12 @@ template <typename T> __global__ void __launch_bounds__(TTHREADS) k_face_reduce_
 }
 
 template <typename T> static size_t rhs_smem() {
-  return TileSmem<T>::bytes() + sizeof(typename Vec2<T>::type) * TX * TY * VK;
+  return TileSmem<T>::bytes() + sizeof(typename Vec2<T>::type) * TX * TY * VK +
+         sizeof(T) * (TTHREADS / 32) * (TX + 1) * NFP;
 }
-template <typename T> static size_t reduce_smem() { return TileSmem<T>::bytes(); }
+template <typename T> static size_t reduce_smem() {
+  return TileSmem<T>::bytes() + sizeof(T) * (TTHREADS / 32) * (TX + 1) * NFG;
+}
 
 void tile_setup() {
   cudaFuncSetAttribute(k_flux_tile<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_smem<float>());

@@ -96,6 +96,15 @@ def test_flux_random_state(prec, tol):
     fl = ou.flux(r.setup, geo, st, r.status, dts, wS)
     assert rel(D.cpu().numpy(), fl.D) < tol
     assert rel(F, fl.F) < tol
+    # wall loads: per block, sum over its wall faces of S times the wall
+    # macro flux (Eq. macroscopicFlux at the wall faces, reading R5)
+    _, _, _, wall = s.moments()
+    topo = r.setup.topo
+    exp = np.zeros((len(case.blocks), 4))
+    for n, f in enumerate(fl.wall_face):
+        exp[topo.face_block[f]] += geo.S[f] * fl.wall_F[n]
+    assert fl.wall_face.size > 0
+    assert rel(wall, exp) < tol
 
 
 def test_step_fp64_channel():

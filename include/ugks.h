@@ -51,6 +51,8 @@ extern "C" {
 #define UGKS_ERR_NONPHYSICAL -5   /* non-finite or non-positive rho or T      */
 #define UGKS_ERR_WORKSPACE   -6   /* workspace missing, too small, misaligned */
 #define UGKS_ERR_ORDER       -7   /* calls out of order (e.g. step w/o move)  */
+#define UGKS_ERR_TIMEOUT     -8   /* a kernel's bounded wait for its data ran
+                                     out; the step's results are invalid    */
 
 /* arithmetic of the per-(cell, velocity) path */
 #define UGKS_FP64 0   /* f, fluxes and sweeps in FP64                          */

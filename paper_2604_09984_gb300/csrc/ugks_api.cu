@@ -70,6 +70,7 @@ int cuda_check(ugks_ctx *c, cudaError_t e, const char *what) {
 
 struct Sizes {
   int nc = 0, nf = 0, nn = 0, nv = 0, nvp = 0, nseg = 0, nring = 0, max_nj = 0, ntiles = 0;
+  size_t nmrec32 = 0;   // FP32 macro records: (ni + nj - 1) nj per block (diagonal-major)
 };
 
 int validate(const ugks_params *p, int nb, const ugks_block_desc *b, Sizes &s, std::string &why) {
@@ -100,6 +101,7 @@ int validate(const ugks_params *p, int nb, const ugks_block_desc *b, Sizes &s, s
     s.nf += B.nj * (B.periodic_i ? B.ni : B.ni + 1) + B.ni * (B.nj + 1);
     if (B.nj > s.max_nj) s.max_nj = B.nj;
     s.ntiles += tile_count(B.ni, B.nj);
+    s.nmrec32 += (size_t)(B.ni + B.nj - 1) * B.nj;
   }
   return UGKS_OK;
 }
@@ -201,7 +203,8 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int nwork, int cap_in
   d.Dbuf = c.take<char>(pair * (size_t)s.nc * s.nvp);
   d.TW = c.take<double>(4 * (size_t)s.nc); d.Fc = c.take<double>(4 * (size_t)s.nc);
   d.dW = c.take<double>(4 * (size_t)s.nc); d.Wp = c.take<double>(4 * (size_t)s.nc);
-  d.mrec = c.take<char>((fp32 ? 4 * 48 : 8 * 41) * (size_t)s.nc);
+  d.mrec = c.take<char>(fp32 ? sizeof(float) * NMR32 * s.nmrec32 : sizeof(double) * NMR * (size_t)s.nc);
+  d.mrec_off = c.take<int>((size_t)nb + 1);
   d.cpar = c.take<double>(NCP * (size_t)s.nc); d.cparn = c.take<double>(NCP * (size_t)s.nc);
   d.shp = c.take<char>(tsz * NSH * (size_t)s.nc); d.shn = c.take<char>(tsz * NSH * (size_t)s.nc);
   d.gradW = c.take<double>(8 * (size_t)s.nc);
@@ -398,6 +401,7 @@ int check_err_flag(ugks_ctx *ctx) {
     if (h & EF_GEOMETRY) return fail(ctx, UGKS_ERR_GEOMETRY, "non-positive cell volume after mesh move");
     if (h & EF_NONPHYSICAL) return fail(ctx, UGKS_ERR_NONPHYSICAL, "non-finite or non-positive density/temperature");
     if (h & EF_BINS) return fail(ctx, UGKS_ERR_WORKSPACE, "overset search bins overflowed");
+    if (h & EF_TIMEOUT) return fail(ctx, UGKS_ERR_TIMEOUT, "a kernel's bounded wait for its data ran out");
   }
   return UGKS_OK;
 }
@@ -741,6 +745,11 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
   if ((r = up(ctx, (void *)d.cell_off, ctx->cell_off))) return r;
   if ((r = up(ctx, (void *)d.node_off, ctx->node_off))) return r;
   if ((r = up(ctx, (void *)d.blk_info, T.blk_info))) return r;
+  {
+    std::vector<int> mo(nblocks + 1, 0);     // diagonal-major FP32 macro records per block
+    for (int b = 0; b < nblocks; ++b) mo[b + 1] = mo[b] + (blocks[b].ni + blocks[b].nj - 1) * blocks[b].nj;
+    if ((r = up(ctx, (void *)d.mrec_off, mo))) return r;
+  }
   if ((r = up(ctx, (void *)ctx->blk_order, order))) return r;
   if ((r = up(ctx, (void *)ctx->work, work))) return r;
   if ((r = up(ctx, (void *)d.tiles, tiles))) return r;

@@ -18,7 +18,7 @@ enum { SL_NONE = 0, SL_M = 1, SL_P = 2, SL_BOTH = 3 };
 // face sums of the velocity-reduction pass
 enum { FS_W0 = 0, FS_FF = 4, FS_WG = 8, NFS = 12 };
 // error flags
-enum { EF_GEOMETRY = 1, EF_NONPHYSICAL = 2, EF_BINS = 4 };
+enum { EF_GEOMETRY = 1, EF_NONPHYSICAL = 2, EF_BINS = 4, EF_TIMEOUT = 8 };
 
 template <typename T> struct Vec2;
 template <> struct Vec2<double> { typedef double2 type; };
@@ -62,6 +62,7 @@ struct Dev {
   double *jinv;              // nc*4 inverse of [[x_xi, y_xi],[x_eta, y_eta]]
   void *fgeo;                // nf*NFG face geometry record (arithmetic type)
   void *srec;                // nc*NSR sweep record (layout at NSR)
+  int *mrec_off;             // nblocks+1: first FP32 macro record of each block (diagonal-major)
   double vbox[4];            // velocity box (vx_min, vx_max, vy_min, vy_max)
   double *affine;            // nblocks*6
   // state
@@ -123,8 +124,17 @@ enum { FG_SNX = 0, FG_SNY, FG_SUN, FG_UFX, FG_UFY, FG_DXLX, FG_DXLY, FG_DXRX, FG
 // SR_MASK; 16 values so a record is a whole number of 16-byte chunks
 enum { SR_DBASE = 12, SR_MASK = 13, NSR = 16 };
 
+// values per cell of the macro-sweep record (FP64 packed, FP32 padded to 256 B)
+enum { NMR = 41, NMR32 = 64 };
+
 // velocities per thread of the micro sweeps, by arithmetic type
 template <typename T> __host__ __device__ constexpr int sweep_vpt() { return sizeof(T) == 4 ? 4 : 2; }
+// bytes between the row records of a micro-sweep ring stage: FP32 records
+// (64 B) padded to 80 B so the rows of a warp fall in different banks; FP64
+// records (128 B) unpadded so a 512-row block still fits two stages
+template <typename T> __host__ __device__ constexpr int sweep_rec_stride() {
+  return sizeof(T) == 4 ? NSR * 4 + 16 : NSR * 8;
+}
 
 // per-cell parameter record (from W' or W^n)
 enum { CP_RHO = 0, CP_UX, CP_UY, CP_LAM, CP_QX, CP_QY, CP_ITAU, CP_DBASE, NCP = 8 };
@@ -166,6 +176,51 @@ template <int BYTES> __device__ __forceinline__ void cp_async(void *smem, const 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N> __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+// mbarrier and bulk (TMA engine) copies, shared::cta addresses
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *mb, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(mb)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *mb, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(mb)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *mb, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(mb)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for a phase of an mbarrier with a bounded number of polls; false
+// (and EF_TIMEOUT in *err) when the limit runs out.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *mb, unsigned parity, int *err) {
+  for (int n = 0; n < (1 << 24); ++n)
+    if (mbar_try_wait(mb, parity)) return true;
+  atomicOr(err, EF_TIMEOUT);
+  return false;
+}
+// global -> shared bulk copy completing on an mbarrier (16-byte aligned
+// addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *mb) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(mb))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;\n" ::: "memory");
 }
 
 template <typename T> __device__ __forceinline__ T dvx(const Dev &d, int k);

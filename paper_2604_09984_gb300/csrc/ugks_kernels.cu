@@ -548,7 +548,7 @@ __device__ __forceinline__ void euler_flux(const double *W, double nx, double ny
 // Per-cell record of the macro sweep (gathered in parallel before it):
 // R (4), 1/diag, then per face slot: neighbour W (4), outward normal (2),
 // U.n, S/4, Gamma.
-enum { MR_R = 0, MR_IDIAG = 4, MR_SLOT = 5, MR_SW = 9, NMR = 41 };
+enum { MR_R = 0, MR_IDIAG = 4, MR_SLOT = 5, MR_SW = 9 };
 
 // (1/4) S (dF_E,j - Gamma dW_j) across one face slot of the record.  FP64:
 // the difference F_E(W + dW) - F_E(W) evaluated directly.  FP32 (mixed
@@ -564,12 +564,15 @@ __device__ __forceinline__ void macro_off(const double *r, const double *dW, int
 }
 
 __device__ __forceinline__ void macro_off(const float *rr, const float *dWn, int Keff, float out[4]) {
-  float r = rr[0], m1 = rr[1], m2 = rr[2], E = rr[3];
-  float nx = rr[4], ny = rr[5], un = rr[6];
-  float dr = dWn[0], d1 = dWn[1], d2 = dWn[2], dE = dWn[3];
+  float4 s0 = reinterpret_cast<const float4 *>(rr)[0], s1 = reinterpret_cast<const float4 *>(rr)[1];
+  float gam = rr[8];
+  float4 dw = *reinterpret_cast<const float4 *>(dWn);
+  float r = s0.x, m1 = s0.y, m2 = s0.z, E = s0.w;
+  float nx = s1.x, ny = s1.y, un = s1.z;
+  float dr = dw.x, d1 = dw.y, d2 = dw.z, dE = dw.w;
   float g1 = 2.0f / (2.0f + (float)Keff);             // gamma - 1
   float mn = m1 * nx + m2 * ny, dmn = d1 * nx + d2 * ny;
-  float den = __frcp_rn(r * (r + dr));                 // 1/(rho (rho + drho))
+  float den = __fdividef(1.0f, r * (r + dr));          // 1/(rho (rho + drho))
   // d(a b / rho) = [da b rho + a db rho + da db rho - a b drho] / (rho (rho + drho))
   float dq11 = (2.0f * (m1 * d1 + m2 * d2) * r + (d1 * d1 + d2 * d2) * r -
                 (m1 * m1 + m2 * m2) * dr) * den;
@@ -581,39 +584,56 @@ __device__ __forceinline__ void macro_off(const float *rr, const float *dWn, int
   float dF2 = (d2 * mn * r + m2 * dmn * r + d2 * dmn * r - m2 * mn * dr) * den - d2 * un + dp * ny;
   float dF3 = (dE * mn * r + E * dmn * r + dE * dmn * r - E * mn * dr) * den - dE * un +
               dp * (mn + dmn) * (r * den) + p * dv;
-  float q = rr[7], g = rr[8];
+  float q = s1.w, g = gam;
   out[0] = q * (dF0 - g * dr);
   out[1] = q * (dF1 - g * d1);
   out[2] = q * (dF2 - g * d2);
   out[3] = q * (dF3 - g * dE);
 }
 
-// Gather the sweep record of every solved cell (parallel).  FP32 records
-// have a 16-byte multiple stride (48 floats) with the neighbour mask at
-// MR_MASK and room for the forward increment at MR_DWS, so the sweep can
-// stream them through a cp.async ring.
-enum { MR_MASK = 41, MR_DWS = 44, NMR32 = 48 };
-template <typename MT> __device__ __forceinline__ int mr_stride();
-template <> __device__ __forceinline__ int mr_stride<double>() { return NMR; }
-template <> __device__ __forceinline__ int mr_stride<float>() { return NMR32; }
+// Gather the sweep record of every solved cell (parallel).  The FP64 record
+// is the packed layout above.  The FP32 record (64 floats, 256 bytes) keeps
+// every group 16-byte aligned for 128-bit shared-memory reads: R (4), 1/diag,
+// the neighbour mask, then per face slot 12 values (neighbour W (4); normal
+// (2), U.n, S/4; Gamma, 3 unused) and the increment of the sweep (4).
+enum { M32_R = 0, M32_IDIAG = 4, M32_MASK = 5, M32_SLOT = 8, M32_SW = 12, M32_DWS = 56 };
+template <typename MT> struct MacroRec;
+template <> struct MacroRec<double> {
+  static constexpr int R = MR_R, IDIAG = MR_IDIAG, SLOT = MR_SLOT, SW = MR_SW, STRIDE = NMR;
+};
+template <> struct MacroRec<float> {
+  static constexpr int R = M32_R, IDIAG = M32_IDIAG, SLOT = M32_SLOT, SW = M32_SW, STRIDE = NMR32;
+};
+
+// FP32 records are diagonal-major per block: the record of cell (i, j) of
+// block b is number mrec_off[b] + (i + j) nj + j, so the records of one
+// diagonal are contiguous and a sweep step fetches them with one bulk copy.
+__device__ __forceinline__ size_t mrec32_index(const Dev &d, int c) {
+  int b = d.cell_block[c];
+  int ni = d.blk_info[8 * b], nj = d.blk_info[8 * b + 1];
+  int loc = c - d.cell_off[b];
+  int i = loc % ni, j = loc / ni;
+  return (size_t)d.mrec_off[b] + (size_t)(i + j) * nj + j;
+}
 
 template <typename MT> __global__ void k_macro_prep(Dev d, MT *rec) {
+  typedef MacroRec<MT> L;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= d.nc) return;
-  MT *o = rec + (size_t)mr_stride<MT>() * c;
+  MT *o = rec + (size_t)L::STRIDE * (sizeof(MT) == 4 ? mrec32_index(d, c) : (size_t)c);
   int mask = d.cmask[c];
-  if (sizeof(MT) == 4) o[MR_MASK] = __int_as_float(mask);
+  if (sizeof(MT) == 4) o[M32_MASK] = __int_as_float(mask);
   if (!(mask & 1)) return;
   double vol = d.vol_new[c], idt = 1.0 / d.dt;
   for (int m = 0; m < 4; ++m)
-    o[MR_R + m] = (MT)(d.TW[4 * c + m] - vol * idt * d.W[4 * c + m] - 0.5 * d.Fc[4 * c + m]);
+    o[L::R + m] = (MT)(d.TW[4 * c + m] - vol * idt * d.W[4 * c + m] - 0.5 * d.Fc[4 * c + m]);
   double diag = vol * (d.cfl_s / (d.cfl_pseudo * d.dts[c]) + idt);
   for (int s = 0; s < 4; ++s) {
     int f = d.cell_faces[4 * c + s];
     diag += 0.25 * d.S[f] * d.gam[f];
     double sg = (double)d.cell_sgn[4 * c + s];
     int nb = (sg > 0) ? d.face_R[f] : d.face_L[f];
-    MT *q = o + MR_SLOT + MR_SW * s;
+    MT *q = o + L::SLOT + L::SW * s;
     // missing neighbour: a harmless positive state (its increment is zero)
     for (int m = 0; m < 4; ++m) q[m] = nb >= 0 ? (MT)d.W[4 * nb + m] : (m == 0 || m == 3 ? MT(1) : MT(0));
     q[4] = (MT)(sg * d.nrm[2 * f]);
@@ -622,113 +642,158 @@ template <typename MT> __global__ void k_macro_prep(Dev d, MT *rec) {
     q[7] = (MT)(0.25 * d.S[f]);
     q[8] = (MT)d.gam[f];
   }
-  o[MR_IDIAG] = (MT)(1.0 / diag);
+  o[L::IDIAG] = (MT)(1.0 / diag);
 }
+
+// shared memory of the FP32 macro sweep ahead of its buffers: the mbarriers
+// of the ring stages (floats)
+constexpr int MACRO_SMEM_HEAD = 16;
 
 // FP32 macro sweep: as k_macro_sweep below, with TPR threads per row (each
 // evaluates the couplings of face slots s = sub, sub + TPR, ...; a shuffle
-// within the row's lanes sums them), and each row's next NS-1 cell records in
-// flight through a cp.async ring in shared memory; the forward increment is
-// stored into the record for the backward pass.
+// within the row's lanes sums them).  The records of the next NS-1 diagonals
+// are in flight in a ring in shared memory, one bulk copy per diagonal
+// completing on the stage's mbarrier (bounded waits), and the part of the
+// next record a thread uses is moved into registers before the barrier that
+// ends a diagonal, so after the barrier only the coupling arithmetic remains.
+// The forward increment is stored into the record for the backward pass.
+// NS = 0: no ring, records read from global memory (blocks too tall for a
+// two-stage ring).
+__device__ __forceinline__ void macro_off_v(float4 s0, float4 s1, float gam, float4 dw, int Keff,
+                                            float out[4]) {
+  __align__(16) float rr[12] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w, gam, 0.f, 0.f, 0.f};
+  __align__(16) float dv[4] = {dw.x, dw.y, dw.z, dw.w};
+  macro_off(rr, dv, Keff, out);
+}
+
 template <int NS, int TPR> __global__ void __launch_bounds__(512) k_macro_sweep_f32(Dev d, float *rec) {
+  constexpr int NSL = 4 / TPR;                  // face slots per thread
+  constexpr int NSR_ = NS > 0 ? NS : 1;
   extern __shared__ __align__(16) float smf[];
+  unsigned long long *mb = reinterpret_cast<unsigned long long *>(smf);   // one mbarrier per stage
   int rows = blockDim.x / TPR;
-  float *buf0 = smf, *buf1 = smf + 4 * rows;
-  float *ring = smf + 8 * rows;                  // NS * rows * NMR32
+  float *buf0 = smf + MACRO_SMEM_HEAD, *buf1 = buf0 + 4 * rows;
+  float *ring = buf1 + 4 * rows;                 // NS * rows * NMR32
   int b = blockIdx.x;
   const int *bi = d.blk_info + 8 * b;
   int ni = bi[0], nj = bi[1], per = bi[2];
-  int off = d.cell_off[b];
+  const float *rb = rec + (size_t)NMR32 * d.mrec_off[b];          // this block's records
+  float *rbw = rec + (size_t)NMR32 * d.mrec_off[b];
   int row = threadIdx.x / TPR, sub = threadIdx.x % TPR;
   unsigned rmask = (TPR == 1 ? 1u : (1u << TPR) - 1u) << (threadIdx.x & 31 & ~(TPR - 1));
   int nd = ni + nj - 1;
+  if (NS > 0 && threadIdx.x == 0) {
+    for (int s = 0; s < NSR_; ++s) mbar_init(&mb[s], 1);
+    mbar_fence_init();
+  }
   if (sub == 0)
     for (int m = 0; m < 4; ++m) { buf0[4 * row + m] = 0.f; buf1[4 * row + m] = 0.f; }
   __syncthreads();
+  const unsigned diag_bytes = (unsigned)nj * NMR32 * sizeof(float);
   for (int pass = 0; pass < 2; ++pass) {
-    float prev[4] = {0, 0, 0, 0}, first[4] = {0, 0, 0, 0};
-    auto cell_of = [&](int it) -> int {
-      if (it >= nd) return -1;
-      int step = pass == 0 ? it : nd - 1 - it;
-      int i = step - row;
-      if (!(row < nj && i >= 0 && i < ni)) return -1;
-      return off + row * ni + i;
-    };
-    // the row's TPR threads share the copy of its next record
+    float4 prev = make_float4(0.f, 0.f, 0.f, 0.f), first = prev;
+    // diagonal of step it, and its position in the ring (g = steps so far)
+    auto diag_of = [&](int it) { return pass == 0 ? it : nd - 1 - it; };
+    auto gstep = [&](int it) { return pass * nd + it; };
+    // thread 0 fetches the records of a whole diagonal with one bulk copy
     auto issue = [&](int it) {
-      int c = cell_of(it);
-      if (c >= 0) {
-        const float *src = rec + (size_t)NMR32 * c;
-        float *dst = ring + ((size_t)(it % NS) * rows + row) * NMR32;
+      if (NS == 0 || threadIdx.x != 0 || it >= nd) return;
+      int s = gstep(it) % NSR_;
+      fence_proxy_async_shared();
+      mbar_arrive_expect_tx(&mb[s], diag_bytes);
+      bulk_g2s(ring + (size_t)s * rows * NMR32, rb + (size_t)diag_of(it) * nj * NMR32, diag_bytes, &mb[s]);
+    };
+    auto wait_stage = [&](int it) {
+      if (NS == 0 || it >= nd) return;
+      int g = gstep(it);
+      mbar_wait(&mb[g % NSR_], (unsigned)(g / NSR_) & 1u, d.err);
+    };
+    // registers of the next diagonal: mask, this thread's slot records,
+    // R (pass 0) or the forward increment (pass 1), 1/diag
+    int nmask = 0;
+    float4 nsa[NSL], nsb[NSL], nrv = make_float4(0.f, 0.f, 0.f, 0.f);
+    float ngam[NSL], nidg = 0.f;
+    auto fetch = [&](int it) {
+      nmask = 0;
+      if (it >= nd) return;
+      int t = diag_of(it), i = t - row;
+      if (!(row < nj && i >= 0 && i < ni)) return;
+      const float *r = NS > 0 ? ring + ((size_t)(gstep(it) % NSR_) * rows + row) * NMR32
+                              : rb + ((size_t)t * nj + row) * NMR32;
+      nmask = __float_as_int(r[M32_MASK]);
 #pragma unroll
-        for (int q = sub; q < NMR32 / 4; q += TPR) cp_async<16>(dst + 4 * q, src + 4 * q);
+      for (int q = 0; q < NSL; ++q) {
+        const float *sr = r + M32_SLOT + M32_SW * (q * TPR + sub);
+        nsa[q] = *reinterpret_cast<const float4 *>(sr);
+        nsb[q] = *reinterpret_cast<const float4 *>(sr + 4);
+        ngam[q] = sr[8];
       }
-      cp_async_commit();
+      nrv = *reinterpret_cast<const float4 *>(r + (pass == 0 ? M32_R : M32_DWS));
+      nidg = r[M32_IDIAG];
     };
 #pragma unroll
     for (int q = 0; q < NS - 1; ++q) issue(q);
-    cp_async_wait<NS - 2>();
-    __syncthreads();
+    wait_stage(0);
+    fetch(0);
     int cur = 0;
     for (int it = 0; it < nd; ++it) {
       issue(it + NS - 1);
-      int step = pass == 0 ? it : nd - 1 - it;
-      int i = step - row;
+      int t = diag_of(it);
+      int i = t - row;
       bool act = row < nj && i >= 0 && i < ni;
-      float val[4] = {0, 0, 0, 0};
-      const float *r = ring + ((size_t)(it % NS) * rows + row) * NMR32;
-      int mask = act ? __float_as_int(r[MR_MASK]) : 0;
+      int mask = nmask;
+      float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
       if (mask & 1) {
         const float *prv = cur ? buf0 : buf1;
-        const float zero4[4] = {0, 0, 0, 0};
         float acc[4] = {0, 0, 0, 0};
 #pragma unroll
-        for (int s0 = 0; s0 < 4; s0 += TPR) {
-          int s = s0 + sub;
-          const float *dv = zero4;
+        for (int q = 0; q < NSL; ++q) {
+          int s = q * TPR + sub;
+          float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
           if (mask & (2 << s)) {
             if (pass == 0) {
               if (s == 0 && i > 0) dv = prev;
               else if (s == 1 && per && i == ni - 1) dv = first;
-              else if (s == 2 && row > 0) dv = prv + 4 * (row - 1);
+              else if (s == 2 && row > 0) dv = *reinterpret_cast<const float4 *>(prv + 4 * (row - 1));
             } else {
               if (s == 1 && i < ni - 1) dv = prev;
               else if (s == 0 && per && i == 0) dv = first;
-              else if (s == 3 && row < nj - 1) dv = prv + 4 * (row + 1);
+              else if (s == 3 && row < nj - 1) dv = *reinterpret_cast<const float4 *>(prv + 4 * (row + 1));
             }
           }
           float o[4];
-          macro_off(r + MR_SLOT + MR_SW * s, dv, d.Keff, o);
+          macro_off_v(nsa[q], nsb[q], ngam[q], dv, d.Keff, o);
           for (int m = 0; m < 4; ++m) acc[m] += o[m];
         }
 #pragma unroll
         for (int w = 1; w < TPR; w <<= 1)
           for (int m = 0; m < 4; ++m) acc[m] += __shfl_xor_sync(rmask, acc[m], w);
-        float idg = r[MR_IDIAG];
-        int c = off + row * ni + i;
-        if (pass == 0) {
-          for (int m = 0; m < 4; ++m) val[m] = (r[MR_R + m] - acc[m]) * idg;
-          if (sub == 0) {
-            float4 w4 = make_float4(val[0], val[1], val[2], val[3]);
-            *reinterpret_cast<float4 *>(rec + (size_t)NMR32 * c + MR_DWS) = w4;
-          }
-        } else {
-          for (int m = 0; m < 4; ++m) val[m] = r[MR_DWS + m] - acc[m] * idg;
-          if (sub == 0)
-            for (int m = 0; m < 4; ++m) d.dW[4 * c + m] = (double)val[m];
-        }
+        float4 rv = nrv;
+        float idg = nidg;
+        if (pass == 0)
+          val = make_float4((rv.x - acc[0]) * idg, (rv.y - acc[1]) * idg, (rv.z - acc[2]) * idg,
+                            (rv.w - acc[3]) * idg);
+        else
+          val = make_float4(rv.x - acc[0] * idg, rv.y - acc[1] * idg, rv.z - acc[2] * idg,
+                            rv.w - acc[3] * idg);
+        // forward: the increment d* for the backward pass; backward: the
+        // final increment for the post-processing kernel
+        if (sub == 0) *reinterpret_cast<float4 *>(rbw + ((size_t)t * nj + row) * NMR32 + M32_DWS) = val;
       }
       if (act) {
-        for (int m = 0; m < 4; ++m) prev[m] = val[m];
-        if (i == (pass == 0 ? 0 : ni - 1)) for (int m = 0; m < 4; ++m) first[m] = val[m];
+        prev = val;
+        if (i == (pass == 0 ? 0 : ni - 1)) first = val;
       }
       float *dst = cur ? buf1 : buf0;
-      if (sub == 0) for (int m = 0; m < 4; ++m) dst[4 * row + m] = val[m];
-      cp_async_wait<NS - 2>();
+      if (sub == 0) *reinterpret_cast<float4 *>(dst + 4 * row) = val;
+      // the next diagonal's records, read into registers before the barrier
+      wait_stage(it + 1);
+      fetch(it + 1);
       __syncthreads();
       cur ^= 1;
     }
-    cp_async_wait<0>();
+    // the increments stored above are read by the next pass's bulk copies
+    fence_proxy_async_global();
     __threadfence_block();
     if (sub == 0)
       for (int m = 0; m < 4; ++m) { buf0[4 * row + m] = 0.f; buf1[4 * row + m] = 0.f; }
@@ -846,7 +911,12 @@ template <typename T> __global__ void k_macro_post(Dev d) {
     for (int m = 0; m < 4; ++m) d.Wp[4 * c + m] = d.W[4 * c + m];
     return;
   }
-  for (int m = 0; m < 4; ++m) d.Wp[4 * c + m] = d.W[4 * c + m] + d.dW[4 * c + m];
+  if (sizeof(T) == 4) {
+    const float *inc = reinterpret_cast<const float *>(d.mrec) + (size_t)NMR32 * mrec32_index(d, c) + M32_DWS;
+    for (int m = 0; m < 4; ++m) d.Wp[4 * c + m] = d.W[4 * c + m] + (double)inc[m];
+  } else {
+    for (int m = 0; m < 4; ++m) d.Wp[4 * c + m] = d.W[4 * c + m] + d.dW[4 * c + m];
+  }
   Prim p = primitive(d.Wp + 4 * c, d.Keff);
   double *o = d.cpar + NCP * c;
   o[CP_RHO] = p.rho; o[CP_UX] = p.ux; o[CP_UY] = p.uy; o[CP_LAM] = p.lam;
@@ -894,7 +964,7 @@ template <typename T, int PASS, int NS, int VPT>
 __global__ void __launch_bounds__(512) k_micro_sweep(Dev d, const int *work, int R) {
   typedef typename Vec2<T>::type T2;
   constexpr int TB = VPT * (int)sizeof(T2);             // bytes of one thread's values
-  constexpr int RS = NSR * (int)sizeof(T) + 16;          // padded record row in shared memory
+  constexpr int RS = sweep_rec_stride<T>();               // record row in shared memory
   constexpr int NCH = NSR * (int)sizeof(T) / 16;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int nt = blockDim.x;
@@ -1214,18 +1284,30 @@ void launch_macro_sweep(const Dev &d, cudaStream_t s, int rows, int fp32) {
     float *rec = reinterpret_cast<float *>(d.mrec);
     k_macro_prep<float><<<nblk(d.nc, 256), 256, 0, s>>>(d, rec);
     size_t per = (size_t)rows * NMR32 * sizeof(float);
-    size_t base = 8 * (size_t)rows * sizeof(float);
-    int NS = (int)((kMacroSmem - base) / per);   // >= 2 for rows <= 512
+    size_t base = (MACRO_SMEM_HEAD + 8 * (size_t)rows) * sizeof(float);
+    int NS = (int)((kMacroSmem - base) / per);
+    NS = NS > 4 ? 4 : (NS < 2 ? 0 : NS);
+    int tpr = rows <= 128 ? 4 : (rows <= 256 ? 2 : 1);
+    if (const char *env = getenv("UGKS_MACRO_TPR")) {   // tuning: threads per row (1, 2 or 4)
+      int t = atoi(env);
+      if ((t == 1 || t == 2 || t == 4) && t * rows <= 512) tpr = t;
+    }
     // the whole shared memory of an SM: the sweep's SMs take no CTA of the
     // kernels running beside it on the main stream
     size_t sm = kMacroSmem;
-    if (rows <= 128)
-      k_macro_sweep_f32<4, 4><<<d.nblocks, 4 * rows, sm, s>>>(d, rec);
-    else if (rows <= 256)
-      k_macro_sweep_f32<4, 2><<<d.nblocks, 2 * rows, sm, s>>>(d, rec);
-    else if (NS >= 4) k_macro_sweep_f32<4, 1><<<d.nblocks, rows, sm, s>>>(d, rec);
-    else if (NS == 3) k_macro_sweep_f32<3, 1><<<d.nblocks, rows, sm, s>>>(d, rec);
-    else k_macro_sweep_f32<2, 1><<<d.nblocks, rows, sm, s>>>(d, rec);
+    int th = tpr * rows;
+#define UGKS_MACRO_F32(ns, tp) k_macro_sweep_f32<ns, tp><<<d.nblocks, th, sm, s>>>(d, rec)
+    if (tpr == 4) {
+      if (NS == 4) UGKS_MACRO_F32(4, 4); else if (NS == 3) UGKS_MACRO_F32(3, 4);
+      else if (NS == 2) UGKS_MACRO_F32(2, 4); else UGKS_MACRO_F32(0, 4);
+    } else if (tpr == 2) {
+      if (NS == 4) UGKS_MACRO_F32(4, 2); else if (NS == 3) UGKS_MACRO_F32(3, 2);
+      else if (NS == 2) UGKS_MACRO_F32(2, 2); else UGKS_MACRO_F32(0, 2);
+    } else {
+      if (NS == 4) UGKS_MACRO_F32(4, 1); else if (NS == 3) UGKS_MACRO_F32(3, 1);
+      else if (NS == 2) UGKS_MACRO_F32(2, 1); else UGKS_MACRO_F32(0, 1);
+    }
+#undef UGKS_MACRO_F32
   } else {
     double *rec = reinterpret_cast<double *>(d.mrec);
     k_macro_prep<double><<<nblk(d.nc, 256), 256, 0, s>>>(d, rec);
@@ -1238,11 +1320,12 @@ void launch_macro_sweep(const Dev &d, cudaStream_t s, int rows, int fp32) {
 void sweep_setup() {
   int ms = (int)kMacroSmem;
   cudaFuncSetAttribute(k_macro_sweep<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, ms);
-  cudaFuncSetAttribute(k_macro_sweep_f32<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, ms);
-  cudaFuncSetAttribute(k_macro_sweep_f32<4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, ms);
-  cudaFuncSetAttribute(k_macro_sweep_f32<4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, ms);
-  cudaFuncSetAttribute(k_macro_sweep_f32<3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, ms);
-  cudaFuncSetAttribute(k_macro_sweep_f32<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, ms);
+#define UGKS_MACRO_ATTR(ns, tp) \
+  cudaFuncSetAttribute(k_macro_sweep_f32<ns, tp>, cudaFuncAttributeMaxDynamicSharedMemorySize, ms)
+  UGKS_MACRO_ATTR(4, 4); UGKS_MACRO_ATTR(3, 4); UGKS_MACRO_ATTR(2, 4); UGKS_MACRO_ATTR(0, 4);
+  UGKS_MACRO_ATTR(4, 2); UGKS_MACRO_ATTR(3, 2); UGKS_MACRO_ATTR(2, 2); UGKS_MACRO_ATTR(0, 2);
+  UGKS_MACRO_ATTR(4, 1); UGKS_MACRO_ATTR(3, 1); UGKS_MACRO_ATTR(2, 1); UGKS_MACRO_ATTR(0, 1);
+#undef UGKS_MACRO_ATTR
   int mx = (int)kSweepSmem;
   constexpr int VF = sweep_vpt<float>(), VD = sweep_vpt<double>();
   cudaFuncSetAttribute(k_micro_sweep<float, 0, 4, VF>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
@@ -1265,7 +1348,7 @@ template <typename T, int PASS>
 static void micro_sweep(const Dev &d, cudaStream_t s, const int *work, int nwork, int threads, int R) {
   typedef typename Vec2<T>::type T2;
   constexpr int VPT = sweep_vpt<T>();
-  size_t tb = VPT * sizeof(T2), rs = NSR * sizeof(T) + 16;
+  size_t tb = VPT * sizeof(T2), rs = sweep_rec_stride<T>();
   size_t stage = (PASS == 1 ? 2 : 1) * (size_t)threads * tb + (size_t)R * rs;
   size_t base = 2 * (size_t)threads * tb;
   int ns = 2;

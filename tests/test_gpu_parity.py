@@ -151,6 +151,23 @@ def test_step_ragged_sizes(nv, ni, nj):
     assert rel(W, r.state.W) < 1e-11
 
 
+@pytest.mark.parametrize("prec", [U.FP64, U.FP32])
+@pytest.mark.parametrize("nj", [150, 300, 450, 512])
+def test_step_tall_blocks(prec, nj):
+    """Block heights that select the other sweep layouts: two and one threads
+    per row in the macro sweep, shallower rings, records read straight from
+    memory (nj > 427 in FP32), and the widest micro-sweep CTAs."""
+    case = wl.channel(ni=3, nj=nj, nv=4, n_inner=2)
+    prim = wl.random_prim(case, 12)
+    s = U.Solver(case, prec, prim=prim)
+    r = Run(case, prim)
+    for _ in range(2):
+        s.advance()
+        r.step()
+    W, _, _, _ = s.moments()
+    assert rel(W, r.state.W) < (1e-11 if prec == U.FP64 else 1e-5)
+
+
 def test_overset_connectivity_bit_exact():
     """Sec. 3.1 assembly: status, donor stencils and IDW weights identical
     bit for bit to the oracle, at several positions of the plate."""

@@ -172,9 +172,9 @@ template <typename T> __global__ void k_geo_records(Dev d) {
     for (int s = 0; s < 4; ++s) {
       int f = d.cell_faces[4 * c + s];
       double sg = (double)d.cell_sgn[4 * c + s];
-      r[3 * s] = (T)(sg * d.Sn[2 * f]);
-      r[3 * s + 1] = (T)(sg * d.Sn[2 * f + 1]);
-      r[3 * s + 2] = (T)(sg * d.SUn[f]);
+      r[3 * s] = (T)(0.5 * sg * d.Sn[2 * f]);
+      r[3 * s + 1] = (T)(0.5 * sg * d.Sn[2 * f + 1]);
+      r[3 * s + 2] = (T)(0.5 * sg * d.SUn[f]);
     }
   }
 }
@@ -960,16 +960,32 @@ template <typename T> __device__ __forceinline__ T rcp_rn(T x);
 template <> __device__ __forceinline__ float rcp_rn<float>(float x) { return __frcp_rn(x); }
 template <> __device__ __forceinline__ double rcp_rn<double>(double x) { return 1.0 / x; }
 
+// Shared-memory layout of per-thread values (VPT velocities = 32 bytes):
+// 16-byte chunk q of thread t at (q nt + t) 16, so the lanes of a warp read
+// and write contiguous 512-byte runs (no bank conflicts).
+template <typename T, int VPT> struct SweepVals {
+  typedef typename Vec2<T>::type T2;
+  static constexpr int NQ = VPT * (int)sizeof(T2) / 16;     // chunks per thread
+  static constexpr int PER = 16 / (int)sizeof(T2);           // values per chunk
+  __device__ static T2 *at(unsigned char *base, int nt, int t, int u) {
+    return reinterpret_cast<T2 *>(base + ((size_t)(u / PER) * nt + t) * 16) + (u % PER);
+  }
+  __device__ static const T2 *at(const unsigned char *base, int nt, int t, int u) {
+    return reinterpret_cast<const T2 *>(base + ((size_t)(u / PER) * nt + t) * 16) + (u % PER);
+  }
+};
+
 template <typename T, int PASS, int NS, int VPT>
 __global__ void __launch_bounds__(512) k_micro_sweep(Dev d, const int *work, int R) {
   typedef typename Vec2<T>::type T2;
+  typedef SweepVals<T, VPT> SV;
   constexpr int TB = VPT * (int)sizeof(T2);             // bytes of one thread's values
   constexpr int RS = sweep_rec_stride<T>();               // record row in shared memory
   constexpr int NCH = NSR * (int)sizeof(T) / 16;
+  static_assert(TB % 16 == 0, "per-thread values are whole 16-byte chunks");
   extern __shared__ __align__(16) unsigned char smraw[];
   const int nt = blockDim.x;
-  T2 *bufA = reinterpret_cast<T2 *>(smraw);
-  T2 *bufB = bufA + (size_t)nt * VPT;
+  unsigned char *bufA = smraw, *bufB = smraw + (size_t)nt * TB;
   const int recoff = (PASS == 1 ? 2 : 1) * nt * TB;
   const int stage = recoff + R * RS;
   unsigned char *ring = smraw + 2 * (size_t)nt * TB;
@@ -994,23 +1010,22 @@ __global__ void __launch_bounds__(512) k_micro_sweep(Dev d, const int *work, int
   for (int u = 0; u < VPT; ++u) { prev[u] = T2{0, 0}; first[u] = T2{0, 0}; }
   int nd = ni + nj - 1;
   const unsigned char *srec = reinterpret_cast<const unsigned char *>(d.srec);
+  const unsigned char *gin = reinterpret_cast<const unsigned char *>(d.dfs);
+  const unsigned char *gf = reinterpret_cast<const unsigned char *>(d.f);
+  // the cell of this row on the diagonal of step it (i = it - row forward,
+  // nd - 1 - it - row backward)
   auto issue = [&](int it, int slot) {
     if (it < nd && rowv) {
-      int step = PASS == 0 ? it : nd - 1 - it;
-      int i = step - row;
+      int i = (PASS == 0 ? it : nd - 1 - it) - row;
       if (i >= 0 && i < ni) {
         int c = off + row * ni + i;
         unsigned char *st = ring + (size_t)slot * stage;
         if (kin) {
-          size_t idx = (size_t)c * d.nvp + kb;
-          const unsigned char *src = reinterpret_cast<const unsigned char *>(d.dfs) + idx * sizeof(T2);
+          size_t gb = ((size_t)c * d.nvp + kb) * sizeof(T2);
 #pragma unroll
-          for (int q = 0; q < TB / 16; ++q) cp_async<16>(st + threadIdx.x * TB + 16 * q, src + 16 * q);
-          if (PASS == 1) {
-            const unsigned char *sf = reinterpret_cast<const unsigned char *>(d.f) + idx * sizeof(T2);
-#pragma unroll
-            for (int q = 0; q < TB / 16; ++q)
-              cp_async<16>(st + (nt + threadIdx.x) * TB + 16 * q, sf + 16 * q);
+          for (int q = 0; q < SV::NQ; ++q) {
+            cp_async<16>(st + ((size_t)q * nt + threadIdx.x) * 16, gin + gb + 16 * q);
+            if (PASS == 1) cp_async<16>(st + ((size_t)(SV::NQ + q) * nt + threadIdx.x) * 16, gf + gb + 16 * q);
           }
         }
         for (int q = g; q < NCH; q += G)
@@ -1026,8 +1041,7 @@ __global__ void __launch_bounds__(512) k_micro_sweep(Dev d, const int *work, int
   int cur = 0, slot = 0, fill = NS - 1;     // ring slots of diagonal it and it + NS - 1
   for (int it = 0; it < nd; ++it) {
     issue(it + NS - 1, fill);
-    int step = PASS == 0 ? it : nd - 1 - it;
-    int i = step - row;
+    int i = (PASS == 0 ? it : nd - 1 - it) - row;
     bool act = kin && i >= 0 && i < ni;
     const unsigned char *st = ring + (size_t)slot * stage;
     const T *geo = reinterpret_cast<const T *>(st + recoff + row * RS);
@@ -1037,52 +1051,50 @@ __global__ void __launch_bounds__(512) k_micro_sweep(Dev d, const int *work, int
     for (int u = 0; u < VPT; ++u) val[u] = T2{0, 0};
     if (mask & 1) {
       int c = off + row * ni + i;
+      // the record holds half the outward (S n_x, S n_y, S U.n) per slot, so
+      // w/2 = v.(S n)/2 - S U.n/2 and the upwind parts are max / min with 0
       T gr[SR_DBASE + 1];
 #pragma unroll
       for (int m = 0; m <= SR_DBASE; ++m) gr[m] = geo[m];
-      const T2 *prv = (cur ? bufA : bufB);
-      // which neighbour each face slot couples to on this pass (0: none,
-      // 1: previous cell of the row, 2: seam cell of the row, 3: adjacent row)
-      int src[4];
-      if (PASS == 0) {
-        src[0] = i > 0 ? 1 : 0;
-        src[1] = (per && i == ni - 1) ? 2 : 0;
-        src[2] = row > 0 ? 3 : 0;
-        src[3] = 0;
-      } else {
-        src[0] = (per && i == 0) ? 2 : 0;
-        src[1] = i < ni - 1 ? 1 : 0;
-        src[2] = 0;
-        src[3] = row < nj - 1 ? 3 : 0;
-      }
-#pragma unroll
-      for (int s = 0; s < 4; ++s)
-        if (!(mask & (2 << s))) src[s] = 0;
-      const T2 *adj = prv + (size_t)(PASS == 0 ? threadIdx.x - G : threadIdx.x + G) * VPT;
-      const T2 *rin = reinterpret_cast<const T2 *>(st + threadIdx.x * TB);
-      const T2 *fin = reinterpret_cast<const T2 *>(st + (nt + threadIdx.x) * TB);
+      const unsigned char *prvb = cur ? bufA : bufB;
+      // lower (pass 0) / upper (pass 1) couplings: along the row (previous
+      // cell, same thread), across rows (row -+ 1, previous diagonal), and
+      // across a periodic seam (first cell of the row, rare)
+      int srow = PASS == 0 ? 0 : 1, scol = PASS == 0 ? 2 : 3, sseam = PASS == 0 ? 1 : 0;
+      bool urow = (PASS == 0 ? i > 0 : i < ni - 1) && (mask & (2 << srow));
+      bool ucol = (PASS == 0 ? row > 0 : row < nj - 1) && (mask & (2 << scol));
+      bool useam = per && (PASS == 0 ? i == ni - 1 : i == 0) && (mask & (2 << sseam));
+      int tadj = PASS == 0 ? (int)threadIdx.x - G : (int)threadIdx.x + G;
+      T2 pr[VPT], ad[VPT];
 #pragma unroll
       for (int u = 0; u < VPT; ++u) {
-        T wo[4];
+        pr[u] = urow ? prev[u] : T2{0, 0};
+        ad[u] = ucol ? *SV::at(prvb, nt, tadj, u) : T2{0, 0};
+      }
+#pragma unroll
+      for (int u = 0; u < VPT; ++u) {
+        T w0 = vx[u] * gr[0] + vy[u] * gr[1] - gr[2];
+        T w1 = vx[u] * gr[3] + vy[u] * gr[4] - gr[5];
+        T w2 = vx[u] * gr[6] + vy[u] * gr[7] - gr[8];
+        T w3 = vx[u] * gr[9] + vy[u] * gr[10] - gr[11];
         T dg = gr[SR_DBASE];
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          wo[s] = vx[u] * gr[3 * s] + vy[u] * gr[3 * s + 1] - gr[3 * s + 2];
-          dg += T(0.5) * (wo[s] > T(0) ? wo[s] : T(0));
-        }
-        T ah = 0, ab = 0;
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          T2 dv = {0, 0};
-          if (src[s] == 1) dv = prev[u];
-          else if (src[s] == 2) dv = first[u];
-          else if (src[s] == 3) dv = adj[u];
-          T cf = src[s] ? T(0.5) * (wo[s] < T(0) ? wo[s] : T(0)) : T(0);
-          ah += cf * dv.x;
-          ab += cf * dv.y;
+        dg += w0 > T(0) ? w0 : T(0);
+        dg += w1 > T(0) ? w1 : T(0);
+        dg += w2 > T(0) ? w2 : T(0);
+        dg += w3 > T(0) ? w3 : T(0);
+        T wr = PASS == 0 ? w0 : w1, wc = PASS == 0 ? w2 : w3;
+        T cr = wr < T(0) ? wr : T(0), cc = wc < T(0) ? wc : T(0);
+        T ah = cr * pr[u].x, ab = cr * pr[u].y;
+        ah += cc * ad[u].x;
+        ab += cc * ad[u].y;
+        if (useam) {
+          T ws = PASS == 0 ? w1 : w0;
+          T cs = ws < T(0) ? ws : T(0);
+          ah += cs * first[u].x;
+          ab += cs * first[u].y;
         }
         T idg = rcp_rn<T>(dg);
-        T2 r = rin[u];
+        T2 r = *SV::at(st, nt, threadIdx.x, u);
         if (PASS == 0) {
           val[u].x = (r.x - ah) * idg;
           val[u].y = (r.y - ab) * idg;
@@ -1097,7 +1109,11 @@ __global__ void __launch_bounds__(512) k_micro_sweep(Dev d, const int *work, int
 #pragma unroll
       for (int u = 0; u < VPT; ++u) {
         T2 o = val[u];
-        if (PASS == 1) { T2 fv = fin[u]; o.x = fv.x + o.x; o.y = fv.y + o.y; }
+        if (PASS == 1) {
+          T2 fv = *SV::at(st + (size_t)SV::NQ * nt * 16, nt, threadIdx.x, u);
+          o.x = fv.x + o.x;
+          o.y = fv.y + o.y;
+        }
         out[u] = o;
       }
     }
@@ -1108,9 +1124,9 @@ __global__ void __launch_bounds__(512) k_micro_sweep(Dev d, const int *work, int
 #pragma unroll
         for (int u = 0; u < VPT; ++u) first[u] = val[u];
     }
-    T2 *dst = (cur ? bufB : bufA) + (size_t)threadIdx.x * VPT;
+    unsigned char *dstb = cur ? bufB : bufA;
 #pragma unroll
-    for (int u = 0; u < VPT; ++u) dst[u] = val[u];
+    for (int u = 0; u < VPT; ++u) *SV::at(dstb, nt, threadIdx.x, u) = val[u];
     cp_async_wait<NS - 2>();
     __syncthreads();
     cur ^= 1;

@@ -30,6 +30,9 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
+# the oracle baseline is reported as single-threaded: keep numpy's BLAS on one core
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
 
 import numpy as np  # noqa: E402
 
@@ -131,6 +134,35 @@ def algorithmic_bytes(group, pair_bytes, nfield, nv, nc):
     per = {"flux": 2 * nfield, "residual": 4 * nfield, "micro_fwd": 2 * nfield,
            "micro_bwd": 3 * nfield, "face_reduce": nc, "moments": nfield, "interp": 0}
     return per.get(group, 0) * nv * pair_bytes
+
+
+def csrc_sha256():
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2604_09984_gb300", "csrc", "*"))):
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def ncu_traffic(group):
+    """DRAM bytes (read + write) per launch of a kernel group of the default
+    workload from the committed ncu summary, or None when the CUDA sources
+    changed since that capture."""
+    p = os.path.join(ROOT, "profiles", "kernels_mems_fp32.md")
+    if not os.path.exists(p):
+        return None
+    sha, traffic = None, {}
+    for line in open(p):
+        w = line.split()
+        if line.startswith("CUDA sources: sha256") and len(w) >= 4:
+            sha = w[3]
+        elif len(w) == 3 and w[0] == "traffic":
+            traffic[w[1]] = int(w[2])
+    if sha != csrc_sha256():
+        return None
+    return traffic.get(group)
 
 
 def time_arm(case, precision, steps, warmup, device, profile):
@@ -235,7 +267,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mems", choices=["mems", "channel", "tsto"])
@@ -291,9 +323,10 @@ def main():
     abytes = algorithmic_bytes(dom, pair, nfield, case.nv, s.nc)
     if abytes > 0:
         ach = abytes / (dms / dn * 1e-3) / 1e9
+        default = args.workload == "mems" and args.kn == 0.1
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "traffic": None, "peak_kind": peak_kind,
-                "bytes_per_launch": abytes, "ms_per_launch": dms / dn}
+                "frac": ach / peak, "traffic": ncu_traffic(dom) if default else None,
+                "peak_kind": peak_kind, "bytes_per_launch": abytes, "ms_per_launch": dms / dn}
     else:
         roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None,
                 "frac": None, "traffic": None, "ms_per_launch": dms / dn}
@@ -333,7 +366,7 @@ def main():
         "fp64_plain": fp64,
     }
     if rank == 0 and not args.no_cpu and world == 1:
-        line["cpu_baseline"] = cpu_baseline(args.kn)
+        line["cpu_baseline"] = cpu_baseline(args.kn, steps=2)
     elif rank == 0:
         line["cpu_baseline"] = None
     if rank == 0:

@@ -202,7 +202,7 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *mb, unsigned p
 // Wait for a phase of an mbarrier with a bounded number of polls; false
 // (and EF_TIMEOUT in *err) when the limit runs out.
 __device__ __forceinline__ bool mbar_wait(unsigned long long *mb, unsigned parity, int *err) {
-  for (int n = 0; n < (1 << 24); ++n)
+  for (int n = 0; n < (1 << 21); ++n)
     if (mbar_try_wait(mb, parity)) return true;
   atomicOr(err, EF_TIMEOUT);
   return false;

@@ -29,7 +29,7 @@ struct ugks_ctx {
   std::vector<ugks_block_desc> blocks;
   std::vector<int> cell_off, node_off;
   int max_nj = 0;
-  int sweep_threads = 32, nwork = 0;
+  int sweep_threads = 32, nwork = 0, nsm = 0;
   int *work = nullptr;
   int *prev_status = nullptr, *n_orphan = nullptr, *blk_order = nullptr;
   int cap_interp = 0;
@@ -130,7 +130,12 @@ struct Carver {
 int block_G(int nj, int nvp, int vpt) {
   int r = 1;
   while (r < nj) r <<= 1;
-  int vt = 1024 / r;
+  int items = 1024;                        // (cell, velocity) items per CTA and diagonal
+  if (const char *e = getenv("UGKS_SWEEP_ITEMS")) {
+    int v = atoi(e);
+    if (v >= 32 && v <= 8192) items = v;
+  }
+  int vt = items / r;
   const char *env = getenv("UGKS_VTILE");
   if (env && atoi(env) >= 1) vt = atoi(env);
   int G = vt / vpt;
@@ -630,6 +635,13 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
   ctx->blocks.assign(blocks, blocks + nblocks);
   ctx->max_nj = s.max_nj;
   ctx->sweep_threads = sweep_threads_for(&ctx->p, nblocks, blocks);
+  {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      ctx->nsm = nsm;
+    cudaGetLastError();
+  }
   ctx->nwork = nwork_for(&ctx->p, nblocks, blocks);
   ctx->cap_interp = cap_interp_for(s, nblocks);
   Dev &d = ctx->d;
@@ -848,8 +860,8 @@ int ugks_step(ugks_ctx *ctx, double dt, int n_inner) {
     { Prof p(ctx, UGKS_PROF_RHS); launch_flux_tile(d, s, fp); }                              // Step 3
     CK(cudaStreamWaitEvent(s, ctx->ev_macro, 0));
     { Prof p(ctx, UGKS_PROF_RESIDUAL); launch_residual(d, s, it == 0, fp); }                 // Step 5
-    { Prof p(ctx, UGKS_PROF_MICRO_FWD); launch_micro_fwd(d, s, ctx->work, ctx->nwork, ctx->sweep_threads, ctx->max_nj, fp); }  // Step 6
-    { Prof p(ctx, UGKS_PROF_MICRO_BWD); launch_micro_bwd(d, s, ctx->work, ctx->nwork, ctx->sweep_threads, ctx->max_nj, fp); }
+    { Prof p(ctx, UGKS_PROF_MICRO_FWD); launch_micro_fwd(d, s, ctx->work, ctx->nwork, ctx->sweep_threads, ctx->max_nj, ctx->nsm, fp); }  // Step 6
+    { Prof p(ctx, UGKS_PROF_MICRO_BWD); launch_micro_bwd(d, s, ctx->work, ctx->nwork, ctx->sweep_threads, ctx->max_nj, ctx->nsm, fp); }
     { Prof p(ctx, UGKS_PROF_MOMENTS); launch_moments(d, s, fp); }                          // Step 7
     ctx->launches += 8;
   }

@@ -1358,18 +1358,22 @@ void sweep_setup() {
   cudaFuncSetAttribute(k_micro_sweep<double, 1, 2, VD>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
 }
 
-// Micro sweeps: the deepest ring (4, 3 or 2 diagonals) that leaves room for
-// two CTAs per SM, else the deepest that fits one.
+// Micro sweeps: the deepest ring (4, 3 or 2 diagonals) with which all the
+// sweep's CTAs are resident at once (nsm SMs), else the deepest that fits
+// one CTA per SM.
 template <typename T, int PASS>
-static void micro_sweep(const Dev &d, cudaStream_t s, const int *work, int nwork, int threads, int R) {
+static void micro_sweep(const Dev &d, cudaStream_t s, const int *work, int nwork, int threads, int R,
+                        int nsm) {
   typedef typename Vec2<T>::type T2;
   constexpr int VPT = sweep_vpt<T>();
   size_t tb = VPT * sizeof(T2), rs = sweep_rec_stride<T>();
   size_t stage = (PASS == 1 ? 2 : 1) * (size_t)threads * tb + (size_t)R * rs;
   size_t base = 2 * (size_t)threads * tb;
+  int per_sm = nsm > 0 ? (nwork + nsm - 1) / nsm : 2;
+  if (per_sm < 1) per_sm = 1;
   int ns = 2;
   bool found = false;
-  for (size_t cap : {kSweepSmem / 2 - 1024, kSweepSmem}) {
+  for (size_t cap : {per_sm > 1 ? kSweepSmem / per_sm - 1024 : kSweepSmem, kSweepSmem}) {
     for (int n = 4; n >= 2 && !found; --n)
       if (base + n * stage <= cap) { ns = n; found = true; }
     if (found) break;
@@ -1385,14 +1389,14 @@ static void micro_sweep(const Dev &d, cudaStream_t s, const int *work, int nwork
   else k_micro_sweep<T, PASS, 2, VPT><<<nwork, threads, sm, s>>>(d, work, R);
 }
 void launch_micro_fwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int threads, int rows,
-                      int fp32) {
-  if (fp32) micro_sweep<float, 0>(d, s, work, nwork, threads, rows);
-  else micro_sweep<double, 0>(d, s, work, nwork, threads, rows);
+                      int nsm, int fp32) {
+  if (fp32) micro_sweep<float, 0>(d, s, work, nwork, threads, rows, nsm);
+  else micro_sweep<double, 0>(d, s, work, nwork, threads, rows, nsm);
 }
 void launch_micro_bwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int threads, int rows,
-                      int fp32) {
-  if (fp32) micro_sweep<float, 1>(d, s, work, nwork, threads, rows);
-  else micro_sweep<double, 1>(d, s, work, nwork, threads, rows);
+                      int nsm, int fp32) {
+  if (fp32) micro_sweep<float, 1>(d, s, work, nwork, threads, rows, nsm);
+  else micro_sweep<double, 1>(d, s, work, nwork, threads, rows, nsm);
 }
 void launch_moments(const Dev &d, cudaStream_t s, int fp32) {
   if (fp32) k_moments<float><<<nblk((size_t)d.nc * 32, 256), 256, 0, s>>>(d);

@@ -70,6 +70,7 @@ int cuda_check(ugks_ctx *c, cudaError_t e, const char *what) {
 
 struct Sizes {
   int nc = 0, nf = 0, nn = 0, nv = 0, nvp = 0, nseg = 0, nring = 0, max_nj = 0, ntiles = 0;
+  int nvx = 0, nvy = 0;
   size_t nmrec32 = 0;   // FP32 macro records: (ni + nj - 1) nj per block (diagonal-major)
 };
 
@@ -83,6 +84,8 @@ int validate(const ugks_params *p, int nb, const ugks_block_desc *b, Sizes &s, s
   }
   s.nv = p->nvx * p->nvy;
   s.nvp = (s.nv + 3) / 4 * 4;
+  s.nvx = p->nvx;
+  s.nvy = p->nvy;
   for (int i = 0; i < nb; ++i) {
     const ugks_block_desc &B = b[i];
     if (B.ni < 2 || B.nj < 2 || B.nj > 512) { why = "block size (2 <= ni, 2 <= nj <= 512)"; return UGKS_ERR_ARG; }
@@ -171,6 +174,7 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int nwork, int cap_in
   size_t tsz = fp32 ? sizeof(float) : sizeof(double);
   d.vx = c.take<double>(s.nvp); d.vy = c.take<double>(s.nvp); d.w = c.take<double>(s.nvp);
   d.vxf = c.take<float>(s.nvp); d.vyf = c.take<float>(s.nvp); d.wf = c.take<float>(s.nvp);
+  d.wx1f = c.take<float>((size_t)s.nvx); d.wy1f = c.take<float>((size_t)s.nvy);
   d.cell_nodes = c.take<int>(4 * (size_t)s.nc);
   d.cell_faces = c.take<int>(4 * (size_t)s.nc);
   d.cell_sgn = c.take<int8_t>(4 * (size_t)s.nc);
@@ -661,6 +665,7 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
     ctx->blk_order = c.take<int>(nblocks);
   }
   d.nc = s.nc; d.nf = s.nf; d.nn = s.nn; d.nv = s.nv; d.nvp = s.nvp; d.nblocks = nblocks;
+  d.nvx = ctx->p.nvx; d.nvy = ctx->p.nvy;
   d.Kint = ctx->p.K; d.Keff = 1 + ctx->p.K;
   d.Pr = ctx->p.Pr; d.omega = ctx->p.omega; d.mu_ref = ctx->p.mu_ref;
   d.cfl_s = ctx->p.cfl_s; d.cfl_pseudo = ctx->p.cfl_pseudo; d.dt = 1.0;
@@ -733,6 +738,14 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
   if ((r = up(ctx, (void *)d.vxf, vxf))) return r;
   if ((r = up(ctx, (void *)d.vyf, vyf))) return r;
   if ((r = up(ctx, (void *)d.wf, wf))) return r;
+  {
+    // 1D trapezoid weights of the tensor grid (w_k = wy(iy) wx(ix))
+    std::vector<float> wx1(ctx->p.nvx), wy1(ctx->p.nvy);
+    for (int ix = 0; ix < ctx->p.nvx; ++ix) wx1[ix] = (float)(hx * ((ix == 0 || ix == ctx->p.nvx - 1) ? 0.5 : 1.0));
+    for (int iy = 0; iy < ctx->p.nvy; ++iy) wy1[iy] = (float)(hy * ((iy == 0 || iy == ctx->p.nvy - 1) ? 0.5 : 1.0));
+    if ((r = up(ctx, (void *)d.wx1f, wx1))) return r;
+    if ((r = up(ctx, (void *)d.wy1f, wy1))) return r;
+  }
   if ((r = up(ctx, (void *)d.cell_nodes, T.cell_nodes))) return r;
   if ((r = up(ctx, (void *)d.cell_faces, T.cell_faces))) return r;
   if ((r = up(ctx, (void *)d.cell_sgn, T.cell_sgn))) return r;

@@ -36,6 +36,8 @@ struct Dev {
   // velocity space (double and float copies), length nvp (padding weight 0)
   const double *vx, *vy, *w;
   const float *vxf, *vyf, *wf;
+  int nvx, nvy;              // tensor grid: k = iy nvx + ix, w_k = wy1(iy) wx1(ix)
+  const float *wx1f, *wy1f;  // 1D trapezoid weights
   // static topology
   const int *cell_nodes;     // nc*4
   const int *cell_faces;     // nc*4 (IM, IP, JM, JP)

@@ -180,6 +180,24 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
+// float -> double on the integer pipes, from the IEEE 754 layouts (sign;
+// exponent rebiased by 1023 - 127; 23-bit fraction shifted into the 52-bit
+// one): exact for normal numbers, zero and subnormals give signed zero,
+// infinities and NaNs are kept.  The FP64 pipe of this GPU retires a warp
+// instruction in tens of cycles, so per-face and per-cell conversions go
+// through here.
+__device__ __forceinline__ double f2d_bits(float x) {
+  unsigned u = __float_as_uint(x);
+  unsigned sign = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  unsigned hi, lo;
+  if (e == 0u) { hi = sign; lo = 0u; }
+  else if (e == 0xffu) { hi = sign | 0x7ff00000u | (m >> 3); lo = (m & 7u) << 29; }
+  else { hi = sign | ((e + 896u) << 20) | (m >> 3); lo = (m & 7u) << 29; }
+  return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ double to_double(double x) { return x; }
+__device__ __forceinline__ double to_double(float x) { return f2d_bits(x); }
+
 // mbarrier and bulk (TMA engine) copies, shared::cta addresses
 __device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(unsigned long long *mb, unsigned count) {

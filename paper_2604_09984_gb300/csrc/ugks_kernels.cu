@@ -113,7 +113,9 @@ __device__ __forceinline__ double warp_total(const Acc<double> &a) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
-__device__ __forceinline__ double warp_total(const Acc<float> &a) {
+// FP32: the total rounded once to FP32 (relative error ~ulp of the total;
+// the compensation only has to stop the error growing with the term count).
+__device__ __forceinline__ float warp_total(const Acc<float> &a) {
   float s = a.s, c = a.c;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -123,8 +125,9 @@ __device__ __forceinline__ double warp_total(const Acc<float> &a) {
     s = t;
     c = c + oc + e;
   }
-  return (double)s + (double)c;
+  return s + c;
 }
+
 
 // Reading R3: dts_i = cfl_s Omega_i^{n+1} / max_k sum_faces S max(w_out, 0).
 // The sum is a convex piecewise-linear function of v, so over the tensor
@@ -597,16 +600,18 @@ template <typename T> __global__ void __launch_bounds__(256, 2) k_face_coef(Dev 
   __align__(16) T parT[NFP];
   load_rec<T, NFP>(PT, parT);
   Acc<T> ags[4], ars[4], aden;
-  T snx = (T)d.Sn[2 * fid], sny = (T)d.Sn[2 * fid + 1], sun = (T)d.SUn[fid];
+  T snx, sny, sun;
+  if (sizeof(T) == 4) { snx = parT[FP_SNX]; sny = parT[FP_SNY]; sun = parT[FP_SUN]; }
+  else { snx = (T)d.Sn[2 * fid]; sny = (T)d.Sn[2 * fid + 1]; sun = (T)d.SUn[fid]; }
   T tufx = parT[FP_UFX], tufy = parT[FP_UFY], tlamw = parT[FP_LAMW], tK = (T)d.Keff;
   V2<T> zero = {T(0), T(0)};
   if (sizeof(T) == 4 && !wall) {
     float o[4];
     face_eq_flux_separable(d, reinterpret_cast<const float *>(parT), (float)snx, (float)sny, (float)sun,
                            lane, o);
-    if (lane == 0) {
-      for (int m = 0; m < 4; ++m)
-        d.fflux[4 * fid + m] = P[FP_Q1] * fs[FS_FF + m] + P[FP_Q2] * fs[FS_WG + m] + (double)o[m];
+    if (lane < 4) {                       // lane m: component m
+      float om = lane == 0 ? o[0] : lane == 1 ? o[1] : lane == 2 ? o[2] : o[3];
+      d.fflux[4 * fid + lane] = P[FP_Q1] * fs[FS_FF + lane] + P[FP_Q2] * fs[FS_WG + lane] + f2d_bits(om);
     }
     return;
   }
@@ -629,8 +634,8 @@ template <typename T> __global__ void __launch_bounds__(256, 2) k_face_coef(Dev 
     }
   }
   double gs[4], rs[4];
-  for (int m = 0; m < 4; ++m) { gs[m] = warp_total(ags[m]); rs[m] = warp_total(ars[m]); }
-  double den = warp_total(aden);
+  for (int m = 0; m < 4; ++m) { gs[m] = to_double(warp_total(ags[m])); rs[m] = to_double(warp_total(ars[m])); }
+  double den = to_double(warp_total(aden));
   if (lane == 0) {
     double F[4];
     for (int m = 0; m < 4; ++m)
@@ -1307,16 +1312,24 @@ template <typename T> __global__ void k_moments(Dev d) {
     a[4].add(T(0.5) * w * cx * e);
     a[5].add(T(0.5) * w * cy * e);
   }
-  double acc[6];
-  for (int m = 0; m < 6; ++m) acc[m] = warp_total(a[m]);
+  // lane m < 6 stores component m (W' + sum for W, the sum for q); lane 0
+  // then checks the new state for rho > 0 and a positive internal energy
+  // (2 rho (rho E) - |rho V|^2 > 0), i.e. rho and lambda positive and finite
+  auto tot = [&](int m) { return to_double(warp_total(a[m])); };
+  double t0 = tot(0), t1 = tot(1), t2 = tot(2), t3 = tot(3), t4 = tot(4), t5 = tot(5);
+  double mine = lane == 0 ? t0 : lane == 1 ? t1 : lane == 2 ? t2 : lane == 3 ? t3 : lane == 4 ? t4 : t5;
+  double wn = 0.0;
+  if (lane < 4) {
+    wn = d.Wp[4 * c + lane] + mine;
+    d.W[4 * c + lane] = wn;
+  } else if (lane < 6) {
+    d.q[2 * c + lane - 4] = mine;
+  }
+  double w0 = __shfl_sync(0xffffffffu, wn, 0), w1 = __shfl_sync(0xffffffffu, wn, 1);
+  double w2 = __shfl_sync(0xffffffffu, wn, 2), w3 = __shfl_sync(0xffffffffu, wn, 3);
   if (lane == 0) {
-    double Wn[4];
-    for (int m = 0; m < 4; ++m) Wn[m] = d.Wp[4 * c + m] + acc[m];
-    for (int m = 0; m < 4; ++m) d.W[4 * c + m] = Wn[m];
-    d.q[2 * c] = acc[4];
-    d.q[2 * c + 1] = acc[5];
-    Prim p = primitive(Wn, d.Keff);
-    if (!(p.rho > 0.0) || !(p.lam > 0.0) || !isfinite(p.rho) || !isfinite(p.lam))
+    double ei2 = 2.0 * w0 * w3 - (w1 * w1 + w2 * w2);
+    if (!(w0 > 0.0) || !(ei2 > 0.0) || !isfinite(w0) || !isfinite(ei2))
       atomicOr(d.err, EF_NONPHYSICAL);
   }
 }

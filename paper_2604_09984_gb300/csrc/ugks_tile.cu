@@ -494,7 +494,7 @@ template <typename T> __global__ void __launch_bounds__(TTHREADS) k_face_reduce_
       }
       v16[0] += __shfl_xor_sync(0xffffffffu, v16[0], 1);
       int slotm = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
-      if (!(lane & 1) && slotm < NFS) atomicAdd(&d.fsum[NFS * fid + slotm], (double)v16[0]);
+      if (!(lane & 1) && slotm < NFS) atomicAdd(&d.fsum[NFS * fid + slotm], to_double(v16[0]));
     }
   }
 }

@@ -408,42 +408,53 @@ template <typename T> __global__ void k_face_scalar(Dev d) {
       gy[m] = avy + jump * (ty / t2);
     }
   }
-  Prim p0 = primitive(W0, d.Keff);
-  double ax[4], ay[4], At[4];
-  micro_slope(p0, d.Keff, gx, ax);
-  micro_slope(p0, d.Keff, gy, ay);
-  time_slope(p0, d.Keff, ax, ay, gx, gy, ufx, ufy, At);
-  double tau = collision_time(p0.rho, p0.lam, d.mu_ref, d.omega);
-  double qi[5];
-  time_integrals(dts, tau, qi);
-  double par[NFP];
+  // face state, slopes and time integrals in the arithmetic type (the FP64
+  // pipe of this GPU is a small fraction of the FP32 one)
+  typedef T RT;
+  RT W0r[4], gxr[4], gyr[4];
+  for (int m = 0; m < 4; ++m) { W0r[m] = (RT)W0[m]; gxr[m] = (RT)gx[m]; gyr[m] = (RT)gy[m]; }
+  PrimR<RT> p0 = primitive_r<RT>(W0r, d.Keff);
+  RT ax[4], ay[4], At[4];
+  micro_slope_r<RT>(p0, d.Keff, gxr, ax);
+  micro_slope_r<RT>(p0, d.Keff, gyr, ay);
+  time_slope_r<RT>(p0, d.Keff, ax, ay, gxr, gyr, (RT)ufx, (RT)ufy, At);
+  RT tau = collision_time_r<RT>(p0.rho, p0.lam, (RT)d.mu_ref, (RT)d.omega);
+  RT dtsr = (RT)dts;
+  RT qi[5];
+  time_integrals_r<RT>(dtsr, tau, qi);
+  RT par[NFP];
   par[FP_RHO] = p0.rho; par[FP_UX] = p0.ux; par[FP_UY] = p0.uy; par[FP_LAM] = p0.lam;
-  par[FP_QX] = q0x; par[FP_QY] = q0y;
+  par[FP_QX] = (RT)q0x; par[FP_QY] = (RT)q0y;
   for (int m = 0; m < 4; ++m) { par[FP_AX + m] = ax[m]; par[FP_AY + m] = ay[m]; par[FP_AT + m] = At[m]; }
-  for (int m = 0; m < 5; ++m) par[FP_Q1 + m] = qi[m] / dts;
-  par[FP_UFX] = ufx; par[FP_UFY] = ufy;
-  par[FP_PREF] = 4.0 * (1.0 - d.Pr) * p0.lam * p0.lam / (5.0 * p0.rho);
-  par[FP_HPRE] = p0.rho * p0.lam * M_1_PI;
-  par[FP_IL] = 1.0 / (2.0 * p0.lam);
-  par[FP_EH] = 0.5 * d.Keff * par[FP_IL];
-  par[FP_EB] = 0.5 * (d.Keff + 2.0) * par[FP_IL];
-  par[FP_LAMW] = wall ? 1.0 / (2.0 * d.face_Tw[fid]) : 0.0;
-  par[FP_RHOW] = 0.0;
-  par[FP_SNX] = d.Sn[2 * fid];
-  par[FP_SNY] = d.Sn[2 * fid + 1];
-  par[FP_SUN] = d.SUn[fid];
+  for (int m = 0; m < 5; ++m) par[FP_Q1 + m] = qi[m] / dtsr;
+  par[FP_UFX] = (RT)ufx; par[FP_UFY] = (RT)ufy;
+  par[FP_PREF] = RT(4) * (RT(1) - (RT)d.Pr) * p0.lam * p0.lam / (RT(5) * p0.rho);
+  par[FP_HPRE] = p0.rho * p0.lam * RT(M_1_PI);
+  par[FP_IL] = RT(1) / (RT(2) * p0.lam);
+  par[FP_EH] = RT(0.5) * RT(d.Keff) * par[FP_IL];
+  par[FP_EB] = RT(0.5) * (RT(d.Keff) + RT(2)) * par[FP_IL];
+  par[FP_LAMW] = wall ? (RT)(1.0 / (2.0 * d.face_Tw[fid])) : RT(0);
+  par[FP_RHOW] = RT(0);
+  par[FP_SNX] = (RT)d.Sn[2 * fid];
+  par[FP_SNY] = (RT)d.Sn[2 * fid + 1];
+  par[FP_SUN] = (RT)d.SUn[fid];
   {
     double sh = (double)d.face_shiftL[fid];
-    par[FP_DXLX] = d.xf[2 * fid] - (d.xc[2 * L] + sh * d.period[2 * L]);
-    par[FP_DXLY] = d.xf[2 * fid + 1] - (d.xc[2 * L + 1] + sh * d.period[2 * L + 1]);
-    par[FP_DXRX] = (R >= 0) ? d.xf[2 * fid] - d.xc[2 * R] : 0.0;
-    par[FP_DXRY] = (R >= 0) ? d.xf[2 * fid + 1] - d.xc[2 * R + 1] : 0.0;
+    par[FP_DXLX] = (RT)(d.xf[2 * fid] - (d.xc[2 * L] + sh * d.period[2 * L]));
+    par[FP_DXLY] = (RT)(d.xf[2 * fid + 1] - (d.xc[2 * L + 1] + sh * d.period[2 * L + 1]));
+    par[FP_DXRX] = (R >= 0) ? (RT)(d.xf[2 * fid] - d.xc[2 * R]) : RT(0);
+    par[FP_DXRY] = (R >= 0) ? (RT)(d.xf[2 * fid + 1] - d.xc[2 * R + 1]) : RT(0);
   }
-  for (int m = 0; m < NFP; ++m) { P[m] = par[m]; PT[m] = (T)par[m]; }
+  for (int m = 0; m < NFP; ++m) { P[m] = to_double(par[m]); PT[m] = par[m]; }
   // Gamma from the mean of the two cells' W (boundary: the cell)
-  double Wf[4];
-  for (int m = 0; m < 4; ++m) Wf[m] = (R >= 0) ? 0.5 * (d.W[4 * L + m] + d.W[4 * R + m]) : d.W[4 * L + m];
-  d.gam[fid] = spectral_radius(Wf, nx, ny, d.SUn[fid] / d.S[fid], d.Keff);
+  RT Wf[4];
+  for (int m = 0; m < 4; ++m)
+    Wf[m] = (R >= 0) ? RT(0.5) * ((RT)d.W[4 * L + m] + (RT)d.W[4 * R + m]) : (RT)d.W[4 * L + m];
+  PrimR<RT> pf = primitive_r<RT>(Wf, d.Keff);
+  RT pr = pf.rho / (RT(2) * pf.lam);
+  RT gamma = (RT(4) + RT(d.Keff)) / (RT(2) + RT(d.Keff));
+  RT un = (RT)d.SUn[fid] / (RT)d.S[fid];
+  d.gam[fid] = to_double(fabs(pf.ux * (RT)nx + pf.uy * (RT)ny - un) + sqrt(gamma * pr / pf.rho));
 }
 
 // Face coefficients, velocity part (one warp per face): the g-part of the

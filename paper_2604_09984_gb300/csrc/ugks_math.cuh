@@ -32,17 +32,19 @@ template <> UG_HD float r_exp<float>(float x) {
 // ---------------------------------------------------------------- primitives
 // (rho, Vx, Vy, lambda) from W = (rho, rho V, rho E);
 // rho E = rho |V|^2 / 2 + (2 + Keff) rho / (4 lambda)   (Sec. 2.1)
-struct Prim { double rho, ux, uy, lam; };
+template <typename R> struct PrimR { R rho, ux, uy, lam; };
+typedef PrimR<double> Prim;
 
-UG_HD Prim primitive(const double W[4], int Keff) {
-  Prim p;
+template <typename R> UG_HD PrimR<R> primitive_r(const R W[4], int Keff) {
+  PrimR<R> p;
   p.rho = W[0];
   p.ux = W[1] / W[0];
   p.uy = W[2] / W[0];
-  double eint = W[3] - 0.5 * p.rho * (p.ux * p.ux + p.uy * p.uy);
-  p.lam = (2.0 + Keff) * p.rho / (4.0 * eint);
+  R eint = W[3] - R(0.5) * p.rho * (p.ux * p.ux + p.uy * p.uy);
+  p.lam = (R(2) + R(Keff)) * p.rho / (R(4) * eint);
   return p;
 }
+UG_HD Prim primitive(const double W[4], int Keff) { return primitive_r<double>(W, Keff); }
 
 UG_HD void conservative(double rho, double ux, double uy, double lam, int Keff, double W[4]) {
   W[0] = rho;
@@ -51,10 +53,17 @@ UG_HD void conservative(double rho, double ux, double uy, double lam, int Keff, 
   W[3] = 0.5 * rho * (ux * ux + uy * uy) + (2.0 + Keff) * rho / (4.0 * lam);
 }
 
+template <typename R> UG_HD R r_pow(R x, R y);
+template <> UG_HD double r_pow<double>(double x, double y) { return pow(x, y); }
+template <> UG_HD float r_pow<float>(float x, float y) { return powf(x, y); }
+
 // tau = mu(T) / p, mu = mu_ref T^omega, T = 1/(2 lam), p = rho T
+template <typename R> UG_HD R collision_time_r(R rho, R lam, R mu_ref, R omega) {
+  R T = R(1) / (R(2) * lam);
+  return mu_ref * r_pow<R>(T, omega) / (rho * T);
+}
 UG_HD double collision_time(double rho, double lam, double mu_ref, double omega) {
-  double T = 1.0 / (2.0 * lam);
-  return mu_ref * pow(T, omega) / (rho * T);
+  return collision_time_r<double>(rho, lam, mu_ref, omega);
 }
 
 // ------------------------------------------------------------ equilibria
@@ -108,35 +117,48 @@ enum {
 // Time integrals q_m = int_0^dts c_m(t) dt (Eq. fullSolution), x = dts/tau;
 // closed forms for x >= 1, Taylor series in x below (the closed forms
 // cancel catastrophically for small x).
-UG_HD void time_integrals(double dts, double tau, double q[5]) {
-  double x = dts / tau;
-  if (x >= 1.0) {
-    double E = exp(-x);
-    double em = -expm1(-x);
+template <typename R> UG_HD R r_expm1(R x);
+template <> UG_HD double r_expm1<double>(double x) { return expm1(x); }
+template <> UG_HD float r_expm1<float>(float x) { return expm1f(x); }
+template <typename R> UG_HD R r_exp_full(R x);
+template <> UG_HD double r_exp_full<double>(double x) { return exp(x); }
+template <> UG_HD float r_exp_full<float>(float x) { return expf(x); }
+
+// series terms: 1/m! below the type's epsilon for m past the count
+template <typename R> struct SeriesTerms;
+template <> struct SeriesTerms<double> { static constexpr int N = 24; };
+template <> struct SeriesTerms<float> { static constexpr int N = 13; };
+
+template <typename R> UG_HD void time_integrals_r(R dts, R tau, R q[5]) {
+  R x = dts / tau;
+  if (x >= R(1)) {
+    R E = r_exp_full<R>(-x);
+    R em = -r_expm1<R>(-x);
     q[0] = tau * em;
     q[1] = tau * (dts + tau) * E - tau * tau;
     q[2] = dts - tau * em;
-    q[3] = -tau * dts * (1.0 + E) + 2.0 * tau * tau * em;
-    q[4] = 0.5 * dts * dts - tau * dts + tau * tau * em;
+    q[3] = -tau * dts * (R(1) + E) + R(2) * tau * tau * em;
+    q[4] = R(0.5) * dts * dts - tau * dts + tau * tau * em;
     return;
   }
   // q1/dts = sum_{m>=1} (-1)^{m+1} x^{m-1}/m!
   // q2/dts^2 = sum_{m>=2} (-1)^{m+1} (m-1) x^{m-2}/m!
   // q4/dts^2 = sum_{m>=3} (-1)^{m+1} (2-m) x^{m-2}/m!
   // q5/dts^2 = sum_{m>=3} (-1)^{m+1} x^{m-2}/m!
-  double s1 = 0, s2 = 0, s4 = 0, s5 = 0;
-  double xp = 1.0;       // x^{m-1}
-  double xm2 = 0.0;      // x^{m-2}
-  double ifac = 1.0;     // 1/m!
-  for (int m = 1; m <= 24; ++m) {
-    ifac *= 1.0 / m;
-    double t = ((m & 1) ? 1.0 : -1.0) * ifac;
-    s1 += t * xp;
+  R s1 = 0, s2 = 0, s4 = 0, s5 = 0;
+  R xp = 1;       // x^{m-1}
+  R xm2 = 0;      // x^{m-2}
+  R ifac = 1;     // 1/m!
+#pragma unroll
+  for (int m = 1; m <= SeriesTerms<R>::N; ++m) {
+    ifac *= R(1) / R(m);
+    R tm = ((m & 1) ? R(1) : R(-1)) * ifac;
+    s1 += tm * xp;
     if (m >= 2) {
-      s2 += t * (m - 1) * xm2;
+      s2 += tm * R(m - 1) * xm2;
       if (m >= 3) {
-        s4 += t * (2 - m) * xm2;
-        s5 += t * xm2;
+        s4 += tm * R(2 - m) * xm2;
+        s5 += tm * xm2;
       }
     }
     xm2 = xp;
@@ -148,6 +170,7 @@ UG_HD void time_integrals(double dts, double tau, double q[5]) {
   q[3] = dts * dts * s4;
   q[4] = dts * dts * s5;
 }
+UG_HD void time_integrals(double dts, double tau, double q[5]) { time_integrals_r<double>(dts, tau, q); }
 
 // Micro slope a with int Psi (a.Psi) g = dW (continuous moments of the
 // Maxwellian with N = 2 + Keff thermal components, Psi = (1, u, v,
@@ -157,63 +180,73 @@ UG_HD void time_integrals(double dts, double tau, double q[5]) {
 //   a4 = 8 lam^2/N [dW4/rho - |V|^2 dW1/(2 rho) - (Vx b2 + Vy b3)/(2 lam)
 //                    - N dW1/(4 lam rho)],
 //   b1 = dW1/rho - a4 N/(4 lam), then back to (a1..a4).
-UG_HD void micro_slope(const Prim &g, int Keff, const double dW[4], double a[4]) {
-  double N = 2.0 + Keff;
-  double lam = g.lam, rho = g.rho, U = g.ux, V = g.uy;
-  double d1 = dW[0] / rho, d2 = dW[1] / rho, d3 = dW[2] / rho, d4 = dW[3] / rho;
-  double b2 = 2.0 * lam * (d2 - U * d1);
-  double b3 = 2.0 * lam * (d3 - V * d1);
-  double a4 = 8.0 * lam * lam / N *
-              (d4 - 0.5 * (U * U + V * V) * d1 - (U * b2 + V * b3) / (2.0 * lam) - N * d1 / (4.0 * lam));
-  double b1 = d1 - a4 * N / (4.0 * lam);
-  double a2 = b2 - a4 * U;
-  double a3 = b3 - a4 * V;
-  a[0] = b1 - a2 * U - a3 * V - 0.5 * a4 * (U * U + V * V);
+template <typename R>
+UG_HD void micro_slope_r(const PrimR<R> &g, int Keff, const R dW[4], R a[4]) {
+  R N = R(2) + R(Keff);
+  R lam = g.lam, rho = g.rho, U = g.ux, V = g.uy;
+  R d1 = dW[0] / rho, d2 = dW[1] / rho, d3 = dW[2] / rho, d4 = dW[3] / rho;
+  R b2 = R(2) * lam * (d2 - U * d1);
+  R b3 = R(2) * lam * (d3 - V * d1);
+  R a4 = R(8) * lam * lam / N *
+         (d4 - R(0.5) * (U * U + V * V) * d1 - (U * b2 + V * b3) / (R(2) * lam) - N * d1 / (R(4) * lam));
+  R b1 = d1 - a4 * N / (R(4) * lam);
+  R a2 = b2 - a4 * U;
+  R a3 = b3 - a4 * V;
+  a[0] = b1 - a2 * U - a3 * V - R(0.5) * a4 * (U * U + V * V);
   a[1] = a2;
   a[2] = a3;
   a[3] = a4;
+}
+UG_HD void micro_slope(const Prim &g, int Keff, const double dW[4], double a[4]) {
+  micro_slope_r<double>(g, Keff, dW, a);
 }
 
 // G = int Psi u_dir (a.Psi) g / rho  (dir 0: u = vx, dir 1: u = vy), closed
 // form from the Gaussian moments E[c_x^2] = s2, E[c_x^2 Z] = (N+2) s2^2,
 // E[Z] = N s2, E[Z^2] = N (N+2) s2^2, s2 = 1/(2 lam), Z = c^2 + xi^2.
-UG_HD void flux_moment(const Prim &g, int Keff, const double a[4], int dir, double G[4]) {
-  double N = 2.0 + Keff;
-  double s2 = 1.0 / (2.0 * g.lam);
-  double U = g.ux, V = g.uy, U2 = U * U + V * V;
-  double b2 = a[1] + a[3] * U;
-  double b3 = a[2] + a[3] * V;
-  double b1 = a[0] + a[1] * U + a[2] * V + 0.5 * a[3] * U2;
-  double m0 = b1 + a[3] * N * 0.5 * s2;                  // E[phi]
-  double Ex = b2 * s2, Ey = b3 * s2;                     // E[c phi]
-  double Exx = b1 * s2 + 0.5 * a[3] * (N + 2.0) * s2 * s2; // E[cx^2 phi] = E[cy^2 phi]
-  double EZ = b1 * N * s2 + 0.5 * a[3] * N * (N + 2.0) * s2 * s2;   // E[Z phi]
-  double EP4 = 0.5 * U2 * m0 + U * Ex + V * Ey + 0.5 * EZ;           // E[Psi4 phi]
-  double Euv = U * V * m0 + U * Ey + V * Ex;
+template <typename R>
+UG_HD void flux_moment_r(const PrimR<R> &g, int Keff, const R a[4], int dir, R G[4]) {
+  R N = R(2) + R(Keff);
+  R s2 = R(1) / (R(2) * g.lam);
+  R U = g.ux, V = g.uy, U2 = U * U + V * V;
+  R b2 = a[1] + a[3] * U;
+  R b3 = a[2] + a[3] * V;
+  R b1 = a[0] + a[1] * U + a[2] * V + R(0.5) * a[3] * U2;
+  R m0 = b1 + a[3] * N * R(0.5) * s2;                     // E[phi]
+  R Ex = b2 * s2, Ey = b3 * s2;                           // E[c phi]
+  R Exx = b1 * s2 + R(0.5) * a[3] * (N + R(2)) * s2 * s2;  // E[cx^2 phi] = E[cy^2 phi]
+  R EZ = b1 * N * s2 + R(0.5) * a[3] * N * (N + R(2)) * s2 * s2;   // E[Z phi]
+  R EP4 = R(0.5) * U2 * m0 + U * Ex + V * Ey + R(0.5) * EZ;          // E[Psi4 phi]
+  R Euv = U * V * m0 + U * Ey + V * Ex;
   if (dir == 0) {
     G[0] = U * m0 + Ex;
-    G[1] = U * U * m0 + 2.0 * U * Ex + Exx;
+    G[1] = U * U * m0 + R(2) * U * Ex + Exx;
     G[2] = Euv;
-    G[3] = U * EP4 + 0.5 * U2 * Ex + U * Exx + 0.5 * b2 * (N + 2.0) * s2 * s2;
+    G[3] = U * EP4 + R(0.5) * U2 * Ex + U * Exx + R(0.5) * b2 * (N + R(2)) * s2 * s2;
   } else {
     G[0] = V * m0 + Ey;
     G[1] = Euv;
-    G[2] = V * V * m0 + 2.0 * V * Ey + Exx;
-    G[3] = V * EP4 + 0.5 * U2 * Ey + V * Exx + 0.5 * b3 * (N + 2.0) * s2 * s2;
+    G[2] = V * V * m0 + R(2) * V * Ey + Exx;
+    G[3] = V * EP4 + R(0.5) * U2 * Ey + V * Exx + R(0.5) * b3 * (N + R(2)) * s2 * s2;
   }
 }
 
 // Time slope A from compatibility int Psi [(ax.Psi) wx + (ay.Psi) wy + A.Psi] g
 // = 0 with w = v - U_f:  M A = -(rho Gx + rho Gy - Ufx dWx - Ufy dWy).
+template <typename R>
+UG_HD void time_slope_r(const PrimR<R> &g, int Keff, const R ax[4], const R ay[4], const R dWx[4],
+                        const R dWy[4], R Ufx, R Ufy, R A[4]) {
+  R Gx[4], Gy[4], r[4];
+  flux_moment_r<R>(g, Keff, ax, 0, Gx);
+  flux_moment_r<R>(g, Keff, ay, 1, Gy);
+  for (int m = 0; m < 4; ++m)
+    r[m] = -(g.rho * Gx[m] + g.rho * Gy[m] - Ufx * dWx[m] - Ufy * dWy[m]);
+  micro_slope_r<R>(g, Keff, r, A);
+}
 UG_HD void time_slope(const Prim &g, int Keff, const double ax[4], const double ay[4],
                       const double dWx[4], const double dWy[4], double Ufx, double Ufy,
                       double A[4]) {
-  double Gx[4], Gy[4], r[4];
-  flux_moment(g, Keff, ax, 0, Gx);
-  flux_moment(g, Keff, ay, 1, Gy);
-  for (int m = 0; m < 4; ++m)
-    r[m] = -(g.rho * Gx[m] + g.rho * Gy[m] - Ufx * dWx[m] - Ufy * dWy[m]);
-  micro_slope(g, Keff, r, A);
+  time_slope_r<double>(g, Keff, ax, ay, dWx, dWy, Ufx, Ufy, A);
 }
 
 // Time-integrated interface distribution / dts for one velocity (Eq.

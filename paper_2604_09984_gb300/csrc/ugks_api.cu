@@ -192,6 +192,8 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int nwork, int cap_in
   d.X_ref = c.take<double>(2 * (size_t)s.nn);
   d.X_old = c.take<double>(2 * (size_t)s.nn);
   d.X_new = c.take<double>(2 * (size_t)s.nn);
+  d.Xf = c.take<float2>((size_t)s.nn);
+  d.cbb = c.take<float4>((size_t)s.nc);
   d.vol_old = c.take<double>(s.nc); d.vol_new = c.take<double>(s.nc); d.dts = c.take<double>(s.nc);
   d.xc = c.take<double>(2 * (size_t)s.nc); d.xc_new = c.take<double>(2 * (size_t)s.nc);
   d.period = c.take<double>(2 * (size_t)s.nc);

@@ -54,6 +54,8 @@ struct Dev {
   // per-step geometry
   const double *X_ref;
   double *X_old, *X_new;     // nn*2
+  float2 *Xf;                // nn: X_new rounded to nearest float (overset filters)
+  float4 *cbb;               // nc: cell bounding box at t^{n+1}, rounded outward
   double *vol_old, *vol_new; // nc
   double *xc, *xc_new;       // nc*2
   double *period;            // nc*2

@@ -18,6 +18,10 @@
 //     receptor cells, then (priority desc, block, cell index); stencil =
 //     donor + its non-hole face neighbours (order i-1, i+1, j-1, j+1),
 //     weights d^-2 normalised in that order (Sec. 3.2).
+//
+// The FP64 predicates decide everything; float filters in front of them only
+// skip work whose outcome they already know exactly: with rn() the
+// round-to-nearest map to float (monotone), rn(a) > rn(b) implies a > b.
 #include "ugks_internal.cuh"
 #include "ugks_launch.h"
 
@@ -30,19 +34,53 @@ __device__ __forceinline__ double sb(double a, double b) { return __dsub_rn(a, b
 __device__ __forceinline__ double ml(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double dv(double a, double b) { return __ddiv_rn(a, b); }
 
+// squared distance of (x, y) to wall segment s (exact FP64 expression)
+__device__ __forceinline__ double seg_dist2(const Dev &d, int s, double x, double y) {
+  int a = d.wall_seg[2 * s], b = d.wall_seg[2 * s + 1];
+  double ax = d.X_new[2 * a], ay = d.X_new[2 * a + 1];
+  double ex = sb(d.X_new[2 * b], ax), ey = sb(d.X_new[2 * b + 1], ay);
+  double px = sb(x, ax), py = sb(y, ay);
+  double t = dv(ad(ml(px, ex), ml(py, ey)), ad(ml(ex, ex), ml(ey, ey)));
+  t = fmin(fmax(t, 0.0), 1.0);
+  double dx = sb(px, ml(t, ex)), dy = sb(py, ml(t, ey));
+  return ad(ml(dx, dx), ml(dy, dy));
+}
+
+// Minimum squared distance to the zone's wall segments (+inf without).
+// A float pass picks a near segment, whose exact distance bounds the
+// minimum; then only segments whose float lower bound (distance to their
+// bounding box, shrunk by the float rounding of the coordinates and
+// scaled down) does not exceed that bound are evaluated exactly.  The
+// skipped ones are farther than the minimum, so the result is the exact
+// minimum over all segments.
 __device__ double wall_dist2(const Dev &d, int blk, double x, double y) {
   double best = __longlong_as_double(0x7ff0000000000000LL);   // +inf
   int s0 = d.wall_seg_off[blk], s1 = d.wall_seg_off[blk + 1];
+  if (s1 <= s0) return best;
+  float xf = __double2float_rn(x), yf = __double2float_rn(y);
+  int sg = s0;
+  float gbest = __int_as_float(0x7f800000);
   for (int s = s0; s < s1; ++s) {
-    int a = d.wall_seg[2 * s], b = d.wall_seg[2 * s + 1];
-    double ax = d.X_new[2 * a], ay = d.X_new[2 * a + 1];
-    double ex = sb(d.X_new[2 * b], ax), ey = sb(d.X_new[2 * b + 1], ay);
-    double px = sb(x, ax), py = sb(y, ay);
-    double t = dv(ad(ml(px, ex), ml(py, ey)), ad(ml(ex, ex), ml(ey, ey)));
-    t = fmin(fmax(t, 0.0), 1.0);
-    double dx = sb(px, ml(t, ex)), dy = sb(py, ml(t, ey));
-    double d2 = ad(ml(dx, dx), ml(dy, dy));
-    best = fmin(best, d2);
+    float2 A = d.Xf[d.wall_seg[2 * s]], B = d.Xf[d.wall_seg[2 * s + 1]];
+    float ex = B.x - A.x, ey = B.y - A.y, px = xf - A.x, py = yf - A.y;
+    float ee = ex * ex + ey * ey;
+    float t = ee > 0.f ? fminf(fmaxf((px * ex + py * ey) / ee, 0.f), 1.f) : 0.f;
+    float dx = px - t * ex, dy = py - t * ey, g = dx * dx + dy * dy;
+    if (g < gbest) { gbest = g; sg = s; }
+  }
+  best = seg_dist2(d, sg, x, y);
+  float bestf = __double2float_ru(best);
+  for (int s = s0; s < s1; ++s) {
+    if (s == sg) continue;
+    float2 A = d.Xf[d.wall_seg[2 * s]], B = d.Xf[d.wall_seg[2 * s + 1]];
+    float lx = fminf(A.x, B.x), hx = fmaxf(A.x, B.x), ly = fminf(A.y, B.y), hy = fmaxf(A.y, B.y);
+    float tol = 2.4e-7f * (fabsf(xf) + fabsf(yf) + fabsf(lx) + fabsf(hx) + fabsf(ly) + fabsf(hy));
+    float gx = fmaxf(fmaxf(lx - xf, xf - hx) - tol, 0.f);
+    float gy = fmaxf(fmaxf(ly - yf, yf - hy) - tol, 0.f);
+    float lb = (gx * gx + gy * gy) * 0.99999f;
+    if (lb > bestf) continue;
+    double d2 = seg_dist2(d, s, x, y);
+    if (d2 < best) { best = d2; bestf = __double2float_ru(best); }
   }
   return best;
 }
@@ -64,8 +102,13 @@ __device__ bool inside_body(const Dev &d, int blk, double x, double y) {
   int r0 = d.body_ring_off[blk], r1 = d.body_ring_off[blk + 1];
   int M = r1 - r0;
   bool in = false;
+  float yf = __double2float_rn(y);
   for (int i = 0; i < M; ++i) {
-    int a = d.body_ring[r0 + i], b = d.body_ring[r0 + (i + 1) % M];
+    int a = d.body_ring[r0 + i], b = d.body_ring[r0 + (i + 1 < M ? i + 1 : 0)];
+    // side of y for each end from the floats where they differ, else exactly
+    float af = d.Xf[a].y, bf = d.Xf[b].y;
+    int sa = af > yf ? 1 : (af < yf ? -1 : 0), sbv = bf > yf ? 1 : (bf < yf ? -1 : 0);
+    if (sa != 0 && sa == sbv) continue;                   // both above or both below
     double ax = d.X_new[2 * a], ay = d.X_new[2 * a + 1];
     double bx = d.X_new[2 * b], by = d.X_new[2 * b + 1];
     bool crosses = (ay > y) != (by > y);
@@ -111,6 +154,12 @@ __device__ __forceinline__ int bin_of(const Dev &d, int b, double x, double y) {
   return d.bin_dim[3 * b + 2] + (int)c * nx + (int)a;
 }
 
+__global__ void k_node_f(Dev d) {
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= d.nn) return;
+  d.Xf[n] = make_float2(__double2float_rn(d.X_new[2 * n]), __double2float_rn(d.X_new[2 * n + 1]));
+}
+
 __global__ void k_bin_count(Dev d) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= d.nc) return;
@@ -121,6 +170,8 @@ __global__ void k_bin_count(Dev d) {
     double x = d.X_new[2 * nd[v]], y = d.X_new[2 * nd[v] + 1];
     xl = fmin(xl, x); xh = fmax(xh, x); yl = fmin(yl, y); yh = fmax(yh, y);
   }
+  d.cbb[c] = make_float4(__double2float_rd(xl), __double2float_rd(yl), __double2float_ru(xh),
+                         __double2float_ru(yh));
   int ix0, ix1, iy0, iy1;
   bin_range(d, b, xl, xh, 0, ix0, ix1);
   bin_range(d, b, yl, yh, 1, iy0, iy1);
@@ -183,10 +234,14 @@ __device__ int first_containing(const Dev &d, int b, double x, double y, Pred ok
   int bin = bin_of(d, b, x, y);
   if (bin < 0) return -1;
   int best = 0x7fffffff;
+  float xf = __double2float_rn(x), yf = __double2float_rn(y);
   int q1 = min(d.bin_start[bin + 1], d.bin_cap);
   for (int q = d.bin_start[bin]; q < q1; ++q) {
     int c = d.bin_items[q];
-    if (c < best && ok(c) && inside_quad(d, c, x, y)) best = c;
+    if (c >= best) continue;
+    float4 bb = d.cbb[c];                       // the cell lies inside its box
+    if (xf < bb.x || xf > bb.z || yf < bb.y || yf > bb.w) continue;
+    if (ok(c) && inside_quad(d, c, x, y)) best = c;
   }
   return best == 0x7fffffff ? -1 : best;
 }
@@ -358,6 +413,7 @@ static inline int nblk(size_t n, int b) { return (int)((n + b - 1) / b); }
 void launch_connect(const Dev &d, cudaStream_t s, int *prev_status, const int *blk_order,
                     int *n_orphan) {
   cudaMemsetAsync(d.bin_cnt, 0, sizeof(int) * d.nbins, s);
+  k_node_f<<<nblk(d.nn, 256), 256, 0, s>>>(d);
   k_bin_count<<<nblk(d.nc, 256), 256, 0, s>>>(d);
   k_bin_scan<<<1, 1024, 0, s>>>(d);
   k_bin_fill<<<nblk(d.nc, 256), 256, 0, s>>>(d);

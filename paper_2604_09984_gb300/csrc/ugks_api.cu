@@ -203,6 +203,7 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int nwork, int cap_in
   d.slope_flags = c.take<int>(s.nc);
   d.cmask = c.take<int>(s.nc);
   d.jinv = c.take<double>(4 * (size_t)s.nc);
+  d.jinvf = c.take<float4>((size_t)s.nc);
   d.fgeo = c.take<char>(tsz * NFG * (size_t)s.nf);
   d.srec = c.take<char>(tsz * NSR * (size_t)s.nc);
   d.affine = c.take<double>(6 * (size_t)nb);

@@ -64,6 +64,7 @@ struct Dev {
   int *slope_flags;          // nc: 2 bits per direction (i: bits 0-1, j: 2-3)
   int *cmask;                // nc: bit 0 solved cell, bit 1+s solved neighbour across slot s
   double *jinv;              // nc*4 inverse of [[x_xi, y_xi],[x_eta, y_eta]]
+  float4 *jinvf;             // nc: the same in FP32
   void *fgeo;                // nf*NFG face geometry record (arithmetic type)
   void *srec;                // nc*NSR sweep record (layout at NSR)
   int *mrec_off;             // nblocks+1: first FP32 macro record of each block (diagonal-major)

@@ -247,6 +247,8 @@ __global__ void k_slope_geo(Dev d) {
   d.jinv[4 * c + 1] = -a12 / det;
   d.jinv[4 * c + 2] = -a21 / det;
   d.jinv[4 * c + 3] = a11 / det;
+  d.jinvf[c] = make_float4((float)d.jinv[4 * c + 0], (float)d.jinv[4 * c + 1], (float)d.jinv[4 * c + 2],
+                           (float)d.jinv[4 * c + 3]);
 }
 
 // Ghost states of far-field / outflow faces (reading R6).

@@ -74,7 +74,11 @@ __device__ __forceinline__ void tile_meta(const Dev &d, TileSmem<T> &S, const in
     S.gid[r] = g;
     if (g >= 0) {
       S.flags[r] = d.slope_flags[g] | (d.status[g] << 8);
-      for (int m = 0; m < 4; ++m) S.jinv[4 * r + m] = (T)d.jinv[4 * g + m];
+      if (sizeof(T) == 4) {
+        *reinterpret_cast<float4 *>(S.jinv + 4 * r) = d.jinvf[g];
+      } else {
+        for (int m = 0; m < 4; ++m) S.jinv[4 * r + m] = (T)d.jinv[4 * g + m];
+      }
     } else {
       S.flags[r] = ST_HOLE << 8;
       if (g <= -2) {

@@ -95,21 +95,26 @@ template <typename T>
 __device__ __forceinline__ void tile_load_f(const Dev &d, TileSmem<T> &S, int k, bool kv, T vx, T vy) {
   typedef typename Vec2<T>::type T2;
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // real cells: asynchronous copies, all of a lane's in flight at once;
+  // ghost cells: the Maxwellian of their ghost state; no cell: zero
   for (int r = w; r < NR; r += nw) {
     int g = S.gid[r];
-    T2 v = {T(0), T(0)};
-    if (kv) {
-      if (g >= 0) {
-        v = ldf<T>(d.f, (size_t)g * d.nvp + k);
-      } else if (g <= -2) {
-        const T *p = S.gprim + 4 * r;
-        V2<T> m = maxwellian_pre<T>(p[0], p[1], p[2], p[3], (T)d.Keff / (T(2) * p[3]), vx, vy);
-        v.x = m.h;
-        v.y = m.b;
-      }
+    T2 *dst = &S.F[r * VK + lane];
+    if (kv && g >= 0) {
+      cp_async<(int)sizeof(T2)>(dst, reinterpret_cast<const T2 *>(d.f) + (size_t)g * d.nvp + k);
+      continue;
     }
-    S.F[r * VK + lane] = v;
+    T2 v = {T(0), T(0)};
+    if (kv && g <= -2) {
+      const T *p = S.gprim + 4 * r;
+      V2<T> m = maxwellian_pre<T>(p[0], p[1], p[2], p[3], (T)d.Keff / (T(2) * p[3]), vx, vy);
+      v.x = m.h;
+      v.y = m.b;
+    }
+    *dst = v;
   }
+  cp_async_commit();
+  cp_async_wait<0>();
 }
 
 // limited gradient of region cell r (a real cell) at this lane (reading R1)

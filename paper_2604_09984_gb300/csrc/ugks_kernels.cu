@@ -1309,8 +1309,20 @@ template <typename T> __global__ void k_moments(Dev d) {
   T hpre = sr[SH_HPRE], ux = sr[SH_UX], uy = sr[SH_UY], lam = sr[SH_LAM];
   T bfac = (T)d.Keff * sr[SH_IL];
   Acc<T> a[6];
-  for (int k = lane; k < d.nv; k += 32) {
-    auto fv = ldf<T>(d.f, (size_t)c * d.nvp + k);
+  typedef typename Vec2<T>::type T2;
+  constexpr int NB = 4;                     // loads of a lane in flight per batch
+  for (int kb = lane; kb < d.nv; kb += 32 * NB) {
+    T2 fb[NB];
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      int k = kb + 32 * u;
+      fb[u] = k < d.nv ? ldf<T>(d.f, (size_t)c * d.nvp + k) : T2{T(0), T(0)};
+    }
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+    int k = kb + 32 * u;
+    if (k >= d.nv) break;
+    T2 fv = fb[u];
     T vx = dvx<T>(d, k), vy = dvy<T>(d, k), w = dw<T>(d, k);
     V2<T> g = maxwellian_pre<T>(hpre, ux, uy, lam, bfac, vx, vy);
     T h = fv.x, b = fv.y;
@@ -1324,6 +1336,7 @@ template <typename T> __global__ void k_moments(Dev d) {
     T e = (cx * cx + cy * cy) * h + b;
     a[4].add(T(0.5) * w * cx * e);
     a[5].add(T(0.5) * w * cy * e);
+    }
   }
   // lane m < 6 stores component m (W' + sum for W, the sum for q); lane 0
   // then checks the new state for rho > 0 and a positive internal energy

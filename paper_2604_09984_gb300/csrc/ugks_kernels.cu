@@ -732,7 +732,7 @@ __device__ __forceinline__ void macro_off(const float *rr, const float *dWn, int
   float r = s0.x, m1 = s0.y, m2 = s0.z, E = s0.w;
   float nx = s1.x, ny = s1.y, un = s1.z;
   float dr = dw.x, d1 = dw.y, d2 = dw.z, dE = dw.w;
-  float g1 = 2.0f / (2.0f + (float)Keff);             // gamma - 1
+  float g1 = __fdividef(2.0f, 2.0f + (float)Keff);    // gamma - 1
   float mn = m1 * nx + m2 * ny, dmn = d1 * nx + d2 * ny;
   float den = __fdividef(1.0f, r * (r + dr));          // 1/(rho (rho + drho))
   // d(a b / rho) = [da b rho + a db rho + da db rho - a b drho] / (rho (rho + drho))

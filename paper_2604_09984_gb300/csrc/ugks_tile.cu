@@ -370,32 +370,42 @@ template <typename T> __global__ void __launch_bounds__(TTHREADS) k_flux_tile(De
 // - D^n) / 2 formed on the first inner iteration.  r goes to the sweep buffer.
 template <typename T> __global__ void k_residual(Dev d, int first_iter) {
   typedef typename Vec2<T>::type T2;
-  int c = blockIdx.x, k = blockIdx.y * blockDim.x + threadIdx.x;   // grid: cells x velocity chunks
-  if (k >= d.nv || !(d.cmask[c] & 1)) return;
-  size_t t = (size_t)c * d.nvp + k;
-  T vx = dvx<T>(d, k), vy = dvy<T>(d, k);
-  T2 fv = ldf<T>(d.f, t);
-  T2 D = ldf<T>(d.Dbuf, t);
+  // grid: cells x velocity chunks; a thread takes two adjacent velocities
+  // (nvp is a multiple of 4, so the pair stays inside the cell's row)
+  int c = blockIdx.x, k0 = 2 * (blockIdx.y * blockDim.x + threadIdx.x);
+  if (k0 >= d.nv || !(d.cmask[c] & 1)) return;
   const T *cp = reinterpret_cast<const T *>(d.shp) + (size_t)NSH * c;
   T itau = cp[SH_ITAU];
-  V2<T> fp = shakhov_rec<T>(cp, vx, vy, (T)d.Keff, (T)d.Kint);
   T vol1 = cp[SH_VOL];
   T idt = sizeof(T) == 4 ? (T)d.idt_f : (T)d.idt;
-  T2 tn;
-  if (first_iter) {
-    const T *cn = reinterpret_cast<const T *>(d.shn) + (size_t)NSH * c;
-    T itn = cn[SH_ITAU];
-    V2<T> fn = shakhov_rec<T>(cn, vx, vy, (T)d.Keff, (T)d.Kint);
-    T vol0 = cn[SH_VOL];
-    tn.x = vol0 * idt * fv.x + T(0.5) * (vol0 * (fn.h - fv.x) * itn - D.x);
-    tn.y = vol0 * idt * fv.y + T(0.5) * (vol0 * (fn.b - fv.y) * itn - D.y);
-    stf<T>(d.Tn, t, tn.x, tn.y);
-  } else {
-    tn = ldf<T>(d.Tn, t);
+  const T *cn = reinterpret_cast<const T *>(d.shn) + (size_t)NSH * c;
+  T2 fv[2], D[2], tn[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    size_t t = (size_t)c * d.nvp + k0 + u;
+    fv[u] = ldf<T>(d.f, t);
+    D[u] = ldf<T>(d.Dbuf, t);
+    if (!first_iter) tn[u] = ldf<T>(d.Tn, t);
   }
-  T rh = tn.x - vol1 * idt * fv.x + T(0.5) * (vol1 * (fp.h - fv.x) * itau - D.x);
-  T rb = tn.y - vol1 * idt * fv.y + T(0.5) * (vol1 * (fp.b - fv.y) * itau - D.y);
-  stf<T>(d.dfs, t, rh, rb);
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    int k = k0 + u;
+    if (k >= d.nv) break;
+    size_t t = (size_t)c * d.nvp + k;
+    T vx = dvx<T>(d, k), vy = dvy<T>(d, k);
+    V2<T> fp = shakhov_rec<T>(cp, vx, vy, (T)d.Keff, (T)d.Kint);
+    if (first_iter) {
+      T itn = cn[SH_ITAU];
+      V2<T> fn = shakhov_rec<T>(cn, vx, vy, (T)d.Keff, (T)d.Kint);
+      T vol0 = cn[SH_VOL];
+      tn[u].x = vol0 * idt * fv[u].x + T(0.5) * (vol0 * (fn.h - fv[u].x) * itn - D[u].x);
+      tn[u].y = vol0 * idt * fv[u].y + T(0.5) * (vol0 * (fn.b - fv[u].y) * itn - D[u].y);
+      stf<T>(d.Tn, t, tn[u].x, tn[u].y);
+    }
+    T rh = tn[u].x - vol1 * idt * fv[u].x + T(0.5) * (vol1 * (fp.h - fv[u].x) * itau - D[u].x);
+    T rb = tn[u].y - vol1 * idt * fv[u].y + T(0.5) * (vol1 * (fp.b - fv[u].y) * itau - D[u].y);
+    stf<T>(d.dfs, t, rh, rb);
+  }
 }
 
 // --------------------------------------------------------- face reduction
@@ -537,8 +547,9 @@ void launch_flux_tile(const Dev &d, cudaStream_t s, int fp32) {
   else k_flux_tile<double><<<grid, TTHREADS, rhs_smem<double>(), s>>>(d);
 }
 void launch_residual(const Dev &d, cudaStream_t s, int first_iter, int fp32) {
-  int bt = d.nv >= 256 ? 256 : ((d.nv + 31) / 32) * 32;
-  dim3 grid(d.nc, (d.nv + bt - 1) / bt);
+  int pairs = (d.nv + 1) / 2;
+  int bt = pairs >= 256 ? 256 : ((pairs + 31) / 32) * 32;
+  dim3 grid(d.nc, (pairs + bt - 1) / bt);
   if (fp32) k_residual<float><<<grid, bt, 0, s>>>(d, first_iter);
   else k_residual<double><<<grid, bt, 0, s>>>(d, first_iter);
 }

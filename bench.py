@@ -220,6 +220,92 @@ def e2e_arm(s, steps):
     return ms, h2d, d2h
 
 
+def batch_arm(cases, steps, warmup, device):
+    """Batched serving: one solver (FP32) per instance, each on its own
+    stream, advanced together through ugks_advance_batch.  Device time from
+    an event every instance stream waits on to an event that waits on every
+    instance stream."""
+    import torch
+    from paper_2604_09984_gb300 import ugks as U
+    streams = [torch.cuda.Stream(device=device) for _ in cases]
+    solvers = [U.Solver(c, U.FP32, device=device, stream=st) for c, st in zip(cases, streams)]
+    for _ in range(warmup):
+        U.advance_batch(solvers)
+    torch.cuda.synchronize()
+    nfield = [field_cells(s) for s in solvers]
+    l0 = sum(s.launch_count() for s in solvers)
+    main_st = torch.cuda.current_stream(device)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(main_st)
+    for st in streams:
+        st.wait_event(ev0)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        U.advance_batch(solvers)
+    host_s = time.perf_counter() - t0
+    for st in streams:
+        e = torch.cuda.Event()
+        e.record(st)
+        main_st.wait_event(e)
+    ev1.record(main_st)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = sum(s.launch_count() for s in solvers) - l0
+    units = sum(n * c.nv * c.n_inner for n, c in zip(nfield, cases)) * steps
+    # end to end: motion parameters in, W/q/status/wall loads of every
+    # instance back to pinned host memory each step
+    outs = []
+    for s in solvers:
+        outs.append((torch.empty((s.nc, 4), dtype=torch.float64).pin_memory(),
+                     torch.empty((s.nc, 2), dtype=torch.float64).pin_memory(),
+                     torch.empty(s.nc, dtype=torch.int32).pin_memory(),
+                     torch.empty((len(s.case.blocks), 4), dtype=torch.float64).pin_memory()))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        U.advance_batch(solvers)
+        for s, o in zip(solvers, outs):
+            s.moments(*o)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    h2d = sum(6 * 8 * len(c.blocks) for c in cases)
+    d2h = sum(sum(t.numel() * t.element_size() for t in o) for o in outs)
+    for s in solvers:
+        s.close()
+    return ms, units, launches, host_s, e2e_s, h2d, d2h, sum(nfield)
+
+
+def run_batch(args, world, rank, device):
+    cases = wl.mems_batch(n=args.instances)
+    steps = max(1, args.steps)
+    warmup = max(3, args.warmup)
+    clk = Clocks(int(device.split(":")[1]))
+    clk.start()
+    ms, units, launches, host_s, e2e_s, h2d, d2h, nfield = batch_arm(cases, steps, warmup, device)
+    clocks = clk.stop()
+    value = units * world / (ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "mems_batch: %d independent oscillating-plate instances, %d field cells, "
+                               "%.3g cell-velocities, 20^2-40^2 velocities, Kn 0.01-2, 10 inner/step"
+                               % (len(cases), nfield, sum(c.ncells * c.nv for c in cases)),
+                   "precision": "FP32 f and per-velocity arithmetic, FP64 moments/geometry",
+                   "l2": "inputs larger than L2", "streams": len(cases),
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "host_issue_ms_per_step": host_s * 1e3 / steps,
+        "clocks": clocks,
+        "e2e": {"value": units * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": None,
+        "cpu_baseline": None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def cpu_sample_case(kn):
     # same geometry family, physics and velocity grid as the timed workload,
     # at a background/O-grid resolution the numpy oracle finishes in ~10-30 s
@@ -270,12 +356,16 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mems", choices=["mems", "channel", "tsto"])
+    ap.add_argument("--workload", default="mems", choices=["mems", "channel", "tsto", "mems_batch"])
+    ap.add_argument("--instances", type=int, default=64, help="mems_batch: number of instances")
     ap.add_argument("--kn", type=float, default=0.1)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-plain comparison arm")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--fp64-steps", type=int, default=1)
     args = ap.parse_args()
+    if args.workload == "mems_batch":
+        # one hardware work queue per instance stream (read when CUDA starts)
+        os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -298,6 +388,11 @@ def main():
     from paper_2604_09984_gb300 import ugks as U
     device = "cuda:%d" % local
     torch.cuda.set_device(local)
+    if args.workload == "mems_batch":
+        run_batch(args, world, rank, device)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     case = make_case(args.workload, args.kn)
     steps = max(1, args.steps)
     warmup = max(3, args.warmup)

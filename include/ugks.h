@@ -155,9 +155,13 @@ int ugks_move_mesh(ugks_ctx *ctx, double t_new, const double *affine);
 /* Overset assembly at t^{n+1} (Sec. 3.1): wall distances, node and cell
  * classification with buffer layer, donor search and inverse-distance
  * weights (Sec. 3.2).  Bit-identical to an FP64 evaluation of the same
- * predicates without fused multiply-add.  `stats` is HOST (may be NULL);
- * synchronises the stream.  No-op for a single block.
- * Errors: UGKS_ERR_ORDER (no move since the last step), UGKS_ERR_ORPHAN. */
+ * predicates without fused multiply-add.  The receptor and fresh-cell lists
+ * the interpolation walks are compacted on the device (ascending cell
+ * order).  `stats` is HOST (may be NULL); synchronises the stream once to
+ * read the counters.  No-op for a single block.
+ * Errors: UGKS_ERR_ORDER (no move since the last step), UGKS_ERR_ORPHAN,
+ * UGKS_ERR_WORKSPACE (more receptors than the staging holds, nc/4 cells
+ * but at least min(nc, 1024)). */
 int ugks_overset_connect(ugks_ctx *ctx, ugks_connect_stats *stats);
 
 /* One physical step t^n -> t^{n+1} of the implicit unsteady UGKS (Sec. 2.2
@@ -168,6 +172,25 @@ int ugks_overset_connect(ugks_ctx *ctx, ugks_connect_stats *stats);
  * Errors: UGKS_ERR_ORDER, UGKS_ERR_ARG. */
 int ugks_step(ugks_ctx *ctx, double dt, int n_inner);
 
+/* Batched outer loop over n independent contexts ("instances": different
+ * meshes, velocity grids and gases): for each instance i, ugks_move_mesh to
+ * t_new[i] with the HOST map affine[i] (6 doubles per block of instance i),
+ * the overset assembly, and ugks_step with dt = t_new[i] - t and n_inner
+ * inner iterations.  Work is issued stage by stage across the instances
+ * (all motions, all assemblies, all steps) and never waits on the device:
+ * the assembly counters stay on the device and the interpolation reads them
+ * there, so instances created on distinct streams run concurrently on the
+ * GPU while the host returns at once.  Each instance computes what a
+ * separate ugks_move_mesh / ugks_overset_connect / ugks_step sequence
+ * computes (the face sums' atomic additions may land in another order).
+ * Orphans, staging overflow and non-physical states are reported by the
+ * next synchronising call on the instance (ugks_moments).  `failed` (HOST,
+ * may be NULL) receives the index of the instance whose call failed, or -1.
+ * Errors: UGKS_ERR_ARG, UGKS_ERR_ORDER, and those of ugks_move_mesh and
+ * ugks_step. */
+int ugks_advance_batch(ugks_ctx *const *ctx, int n, const double *t_new,
+                       const double *const *affine, int n_inner, int *failed);
+
 /* Copy the macroscopic fields to caller memory (host or device pointers,
  * cudaMemcpyDefault): W (ncells x 4: rho, rho Vx, rho Vy, rho E), q
  * (ncells x 2), status (ncells int32, UGKS_FIELD/RECEPTOR/HOLE) -- any may be
@@ -175,7 +198,9 @@ int ugks_step(ugks_ctx *ctx, double dt, int n_inner);
  * of S times the wall macro flux (mass, x-momentum, y-momentum, energy) of
  * the last flux evaluation, i.e. the force and heat the gas exerts, Sec. 2.1
  * wall pressure/shear/heat).  Synchronises the stream.  Also reports a
- * pending device error flag: UGKS_ERR_NONPHYSICAL, UGKS_ERR_GEOMETRY. */
+ * pending device error flag: UGKS_ERR_NONPHYSICAL, UGKS_ERR_GEOMETRY, and
+ * from an assembly issued by ugks_advance_batch UGKS_ERR_ORPHAN or
+ * UGKS_ERR_WORKSPACE. */
 int ugks_moments(ugks_ctx *ctx, double *W, double *q, int32_t *status,
                  double *wall_loads);
 

@@ -38,7 +38,7 @@ struct ugks_ctx {
   std::string err;
   int64_t launches = 0;
   std::vector<double> h_affine;
-  std::vector<int> h_lists;
+  bool fresh_pending = false;         // cells uncovered by the last assembly await their first values
   std::vector<double> ref_bbox, h_bin_geo;   // per block reference bbox; bin boxes
   std::vector<int> h_bin_dim;
   // per-kernel-group CUDA-event timing (ugks_profile_*)
@@ -233,8 +233,11 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int nwork, int cap_in
   d.dwgt = c.take<double>(5 * (size_t)s.nc);
   d.rec_list = c.take<int>(s.nc);
   d.fresh_list = c.take<int>(s.nc);
+  d.conn_cnt = c.take<int>(8);
+  d.conn_chunk = c.take<int4>(((size_t)s.nc + 1023) / 1024);
   d.itmp = c.take<char>(pair * (size_t)cap_interp * s.nvp);
   d.itmpW = c.take<double>(6 * (size_t)cap_interp);
+  d.cap_interp = cap_interp;
   d.wall_seg = c.take<int>(2 * (size_t)s.nseg + 2);
   d.wall_seg_off = c.take<int>(nb + 1);
   d.body_ring = c.take<int>((size_t)s.nring + 1);
@@ -414,6 +417,8 @@ int check_err_flag(ugks_ctx *ctx) {
     if (h & EF_NONPHYSICAL) return fail(ctx, UGKS_ERR_NONPHYSICAL, "non-finite or non-positive density/temperature");
     if (h & EF_BINS) return fail(ctx, UGKS_ERR_WORKSPACE, "overset search bins overflowed");
     if (h & EF_TIMEOUT) return fail(ctx, UGKS_ERR_TIMEOUT, "a kernel's bounded wait for its data ran out");
+    if (h & EF_CAPACITY) return fail(ctx, UGKS_ERR_WORKSPACE, "more receptors than the interpolation staging holds");
+    if (h & EF_ORPHAN) return fail(ctx, UGKS_ERR_ORPHAN, "overset receptors without donor");
   }
   return UGKS_OK;
 }
@@ -461,9 +466,15 @@ int prof_drain(ugks_ctx *ctx) {
   return UGKS_OK;
 }
 
-int do_interp(ugks_ctx *ctx, const int *list, int n) {
-  if (n <= 0) return UGKS_OK;
-  { Prof p(ctx, UGKS_PROF_INTERP); launch_interp(ctx->d, ctx->st, list, n, ctx->fp32); }
+// Receptor (fresh = 0) or fresh-cell (fresh = 1) interpolation; the list
+// length lives on the device.
+int do_interp(ugks_ctx *ctx, int fresh) {
+  if (ctx->nblocks < 2) return UGKS_OK;
+  Dev &d = ctx->d;
+  {
+    Prof p(ctx, UGKS_PROF_INTERP);
+    launch_interp(d, ctx->st, fresh ? d.fresh_list : d.rec_list, d.conn_cnt + (fresh ? 1 : 0), ctx->nsm, ctx->fp32);
+  }
   ctx->launches += 2;
   return UGKS_OK;
 }
@@ -480,7 +491,10 @@ void flux_prep(ugks_ctx *ctx, int level_n) {
   ctx->launches += 6;
 }
 
-int do_connect(ugks_ctx *ctx, ugks_connect_stats *stats, bool initial) {
+// Overset assembly (Sec. 3.1) and the device-side receptor / fresh lists.
+// With sync, waits for the counters, fills stats and reports orphans and
+// staging overflow; without, every check is left to the error flag.
+int do_connect(ugks_ctx *ctx, ugks_connect_stats *stats, bool initial, bool sync) {
   Dev &d = ctx->d;
   if (ctx->nblocks < 2) {
     if (stats) { stats->n_field = d.nc; stats->n_receptor = stats->n_hole = stats->n_fresh = stats->n_orphan = 0; }
@@ -519,48 +533,29 @@ int do_connect(ugks_ctx *ctx, ugks_connect_stats *stats, bool initial) {
     d.nbins = base;
     ctx->h_bin_geo = geo;
     ctx->h_bin_dim = dim;
-    CK(cudaMemcpyAsync(d.bin_geo, ctx->h_bin_geo.data(), sizeof(double) * geo.size(), cudaMemcpyHostToDevice, ctx->st));
-    CK(cudaMemcpyAsync(d.bin_dim, ctx->h_bin_dim.data(), sizeof(int) * dim.size(), cudaMemcpyHostToDevice, ctx->st));
+    ctx->launches += launch_upload(d.bin_geo, geo.data(), sizeof(double) * geo.size(), ctx->st);
+    ctx->launches += launch_upload(d.bin_dim, dim.data(), sizeof(int) * dim.size(), ctx->st);
   }
-  { Prof p(ctx, UGKS_PROF_CONNECT); launch_connect(d, ctx->st, ctx->prev_status, ctx->blk_order, ctx->n_orphan); }
-  ctx->launches += 7;
-  int r = launch_status(ctx);
-  if (r) return r;
-  std::vector<int> st(d.nc), fr(d.nc);
-  int norph = 0;
-  CK(cudaMemcpyAsync(st.data(), d.status, sizeof(int) * d.nc, cudaMemcpyDeviceToHost, ctx->st));
-  CK(cudaMemcpyAsync(fr.data(), ctx->prev_status, sizeof(int) * d.nc, cudaMemcpyDeviceToHost, ctx->st));
-  CK(cudaMemcpyAsync(&norph, ctx->n_orphan, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
-  CK(cudaStreamSynchronize(ctx->st));
-  if ((r = check_err_flag(ctx))) return r;
-  std::vector<int> rec, fresh;
-  int nf = 0, nr = 0, nh = 0;
-  for (int c = 0; c < d.nc; ++c) {
-    if (st[c] == ST_FIELD) ++nf;
-    else if (st[c] == ST_RECEPTOR) { ++nr; rec.push_back(c); }
-    else ++nh;
-    if (fr[c]) fresh.push_back(c);
+  {
+    Prof p(ctx, UGKS_PROF_CONNECT);
+    launch_connect(d, ctx->st, ctx->prev_status, ctx->blk_order, ctx->n_orphan);
+    launch_lists(d, ctx->st, ctx->prev_status, ctx->n_orphan);
   }
-  if ((int)rec.size() > ctx->cap_interp || (int)fresh.size() > ctx->cap_interp)
-    return fail(ctx, UGKS_ERR_WORKSPACE, "more receptors than the interpolation staging holds");
-  ctx->h_lists = rec;
-  ctx->h_lists.insert(ctx->h_lists.end(), fresh.begin(), fresh.end());
-  if (!ctx->h_lists.empty()) {
-    CK(cudaMemcpyAsync(d.rec_list, rec.data(), sizeof(int) * rec.size(), cudaMemcpyHostToDevice, ctx->st));
-    if (!fresh.empty())
-      CK(cudaMemcpyAsync(d.fresh_list, fresh.data(), sizeof(int) * fresh.size(), cudaMemcpyHostToDevice, ctx->st));
-    CK(cudaStreamSynchronize(ctx->st));
-  }
-  d.nrec = (int)rec.size();
-  d.nfresh = (int)fresh.size();
   launch_slope_geo(d, ctx->st);     // holes changed
-  ctx->launches += 1;
+  ctx->launches += 10;
+  ctx->fresh_pending = !initial;
+  int r = launch_status(ctx);
+  if (r || !sync) return r;
+  int cnt[8];
+  CK(cudaMemcpyAsync(cnt, d.conn_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
   if (stats) {
-    stats->n_field = nf; stats->n_receptor = nr; stats->n_hole = nh;
-    stats->n_fresh = (int)fresh.size(); stats->n_orphan = norph;
+    stats->n_field = cnt[2]; stats->n_receptor = cnt[0]; stats->n_hole = cnt[3];
+    stats->n_fresh = cnt[1]; stats->n_orphan = cnt[4];
   }
-  if (norph > 0) return fail(ctx, UGKS_ERR_ORPHAN, std::to_string(norph) + " receptors without donor");
-  return launch_status(ctx);
+  r = check_err_flag(ctx);
+  if (r == UGKS_ERR_ORPHAN) return fail(ctx, r, std::to_string(cnt[4]) + " receptors without donor");
+  return r;
 }
 
 }  // namespace
@@ -807,7 +802,7 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
   ctx->mesh_ready = true;
   ctx->t = 0.0;
   ctx->moved = false;
-  r = do_connect(ctx, nullptr, true);
+  r = do_connect(ctx, nullptr, true, true);
   if (r) return r;
   launch_slope_geo(d, ctx->st);
   ctx->launches += 1;
@@ -823,8 +818,7 @@ int ugks_move_mesh(ugks_ctx *ctx, double t_new, const double *affine) {
   Dev &d = ctx->d;
   ctx->h_affine.assign(affine, affine + 6 * (size_t)ctx->nblocks);
   std::swap(d.X_old, d.X_new);
-  CK(cudaMemcpyAsync(d.affine, ctx->h_affine.data(), sizeof(double) * 6 * ctx->nblocks,
-                     cudaMemcpyHostToDevice, ctx->st));
+  ctx->launches += launch_upload(d.affine, ctx->h_affine.data(), sizeof(double) * 6 * ctx->nblocks, ctx->st);
   d.dt = t_new - ctx->t;
   d.idt = 1.0 / d.dt;
   d.idt_f = (float)d.idt;
@@ -845,7 +839,7 @@ int ugks_overset_connect(ugks_ctx *ctx, ugks_connect_stats *stats) {
   if (!ctx->moved) return fail(ctx, UGKS_ERR_ORDER, "ugks_overset_connect needs a preceding ugks_move_mesh");
   int r = check_err_flag(ctx);
   if (r) return r;
-  return do_connect(ctx, stats, false);
+  return do_connect(ctx, stats, false, true);
 }
 
 int ugks_step(ugks_ctx *ctx, double dt, int n_inner) {
@@ -856,15 +850,15 @@ int ugks_step(ugks_ctx *ctx, double dt, int n_inner) {
   if (fabs(dt - d.dt) > 1e-12 * fabs(d.dt)) return fail(ctx, UGKS_ERR_ARG, "dt differs from the move's step");
   cudaStream_t s = ctx->st;
   int fp = ctx->fp32;
-  do_interp(ctx, d.fresh_list, d.nfresh);
-  do_interp(ctx, d.rec_list, d.nrec);
+  if (ctx->fresh_pending) do_interp(ctx, 1);
+  do_interp(ctx, 0);
   // Steps 1-2: level-n flux, extensive level-n macro term, level-n cell record
   flux_prep(ctx, 1);
   { Prof p(ctx, UGKS_PROF_CELL); launch_cell_params(d, s, d.W, d.cparn, fp); }
   ctx->launches += 1;
   for (int it = 0; it < n_inner; ++it) {
     if (it > 0) {
-      do_interp(ctx, d.rec_list, d.nrec);
+      do_interp(ctx, 0);
       flux_prep(ctx, 0);                       // Step 3
     }
     // Step 4 (macro LU-SGS) on the side stream, concurrently with the flux
@@ -881,10 +875,36 @@ int ugks_step(ugks_ctx *ctx, double dt, int n_inner) {
     { Prof p(ctx, UGKS_PROF_MOMENTS); launch_moments(d, s, fp); }                          // Step 7
     ctx->launches += 8;
   }
-  d.nfresh = 0;
+  ctx->fresh_pending = false;
   ctx->t = ctx->t_new;
   ctx->moved = false;
   return launch_status(ctx);
+}
+
+int ugks_advance_batch(ugks_ctx *const *ctx, int n, const double *t_new, const double *const *affine,
+                       int n_inner, int *failed) {
+  if (failed) *failed = -1;
+  if (n < 0 || (n > 0 && (!ctx || !t_new || !affine))) return UGKS_ERR_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!ctx[i] || !ctx[i]->mesh_ready) {
+      if (failed) *failed = i;
+      return UGKS_ERR_ORDER;
+    }
+  // stage-major issue order: every instance's motion, then every assembly,
+  // then every step, so that all streams have work queued early
+  for (int stage = 0; stage < 3; ++stage)
+    for (int i = 0; i < n; ++i) {
+      ugks_ctx *c = ctx[i];
+      int r;
+      if (stage == 0) r = ugks_move_mesh(c, t_new[i], affine[i]);
+      else if (stage == 1) r = c->mesh_ready ? do_connect(c, nullptr, false, false) : UGKS_ERR_ORDER;
+      else r = ugks_step(c, c->d.dt, n_inner);
+      if (r) {
+        if (failed) *failed = i;
+        return r;
+      }
+    }
+  return UGKS_OK;
 }
 
 int ugks_moments(ugks_ctx *ctx, double *W, double *q, int32_t *status, double *wall_loads) {
@@ -940,7 +960,7 @@ int ugks_eval_flux(ugks_ctx *ctx, double *D, double *F) {
   if (!ctx->moved) return fail(ctx, UGKS_ERR_ORDER, "ugks_eval_flux needs a preceding ugks_move_mesh");
   Dev &d = ctx->d;
   if (D && !is_device_ptr(D)) return fail(ctx, UGKS_ERR_ARG, "D must be a device pointer");
-  do_interp(ctx, d.rec_list, d.nrec);
+  do_interp(ctx, 0);
   flux_prep(ctx, 0);
   if (D) { launch_flux_div_all(d, ctx->st, D, ctx->fp32); ctx->launches += 1; }
   if (F) CK(cudaMemcpyAsync(F, d.Fc, sizeof(double) * 4 * d.nc, cudaMemcpyDefault, ctx->st));

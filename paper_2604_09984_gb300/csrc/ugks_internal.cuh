@@ -18,7 +18,7 @@ enum { SL_NONE = 0, SL_M = 1, SL_P = 2, SL_BOTH = 3 };
 // face sums of the velocity-reduction pass
 enum { FS_W0 = 0, FS_FF = 4, FS_WG = 8, NFS = 12 };
 // error flags
-enum { EF_GEOMETRY = 1, EF_NONPHYSICAL = 2, EF_BINS = 4, EF_TIMEOUT = 8 };
+enum { EF_GEOMETRY = 1, EF_NONPHYSICAL = 2, EF_BINS = 4, EF_TIMEOUT = 8, EF_ORPHAN = 16, EF_CAPACITY = 32 };
 
 template <typename T> struct Vec2;
 template <> struct Vec2<double> { typedef double2 type; };
@@ -98,11 +98,12 @@ struct Dev {
   int *cls;                  // nc scratch classification
   int *donors;               // nc*5
   double *dwgt;              // nc*5
-  int *rec_list;             // receptor cells (compacted on the host)
-  int nrec;
-  int *fresh_list;
-  int nfresh;
-  void *itmp;                // interpolation staging: max(nrec, nfresh)*nvp pairs
+  int *rec_list;             // receptor cells, ascending (compacted on the device)
+  int *fresh_list;           // cells uncovered by the motion, ascending
+  int *conn_cnt;             // 8 counters: receptors, fresh, field, hole, orphans
+  int4 *conn_chunk;          // per 1024-cell chunk: receptors, fresh, field, other
+  int cap_interp;            // capacity of the lists' interpolation staging
+  void *itmp;                // interpolation staging: cap_interp*nvp pairs
   double *itmpW;             // ... *6 doubles
   int *wall_seg;             // segments: node id pairs, grouped per block
   int *wall_seg_off;         // nblocks+1

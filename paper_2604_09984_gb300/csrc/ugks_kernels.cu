@@ -3,6 +3,7 @@
 // geometry kernels (Sec. 3 Step 1).  Launch wrappers at the end are the only
 // symbols used by the host orchestration (ugks_api.cu).
 #include <cstdlib>
+#include <cstring>
 #include "ugks_internal.cuh"
 #include "ugks_launch.h"
 
@@ -1445,6 +1446,33 @@ template <typename T> __global__ void k_f_from_double(Dev d, const double *in) {
 static inline int nblk(size_t n, int b) { return (int)((n + b - 1) / b); }
 
 void launch_move_nodes(const Dev &d, cudaStream_t s) { k_move_nodes<<<nblk(d.nn, 256), 256, 0, s>>>(d); }
+
+// Small host->device uploads (motion maps, search-bin boxes) travel as kernel
+// arguments: the bytes are captured when the launch is issued, so the upload
+// neither waits on the stream nor needs pinned staging, and it can be
+// captured in a graph.
+struct UploadBlob {
+  unsigned char b[2048];
+};
+__global__ void k_upload(unsigned char *dst, UploadBlob blob, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = blob.b[i];
+}
+int launch_upload(void *dst, const void *src, size_t n, cudaStream_t s) {
+  const unsigned char *p = static_cast<const unsigned char *>(src);
+  unsigned char *q = static_cast<unsigned char *>(dst);
+  int launches = 0;
+  while (n > 0) {
+    size_t m = n < sizeof(UploadBlob) ? n : sizeof(UploadBlob);
+    UploadBlob blob;
+    memcpy(blob.b, p, m);
+    k_upload<<<1, 256, 0, s>>>(q, blob, (int)m);
+    p += m;
+    q += m;
+    n -= m;
+    ++launches;
+  }
+  return launches;
+}
 void launch_geometry(const Dev &d, cudaStream_t s, int fp32) {
   k_cell_geom<<<nblk(d.nc, 256), 256, 0, s>>>(d);
   k_face_geom<<<nblk(d.nf, 256), 256, 0, s>>>(d);

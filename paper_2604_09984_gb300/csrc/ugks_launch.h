@@ -4,6 +4,7 @@
 #include "ugks_internal.cuh"
 
 namespace ugks {
+int launch_upload(void *dst, const void *src, size_t n, cudaStream_t s);   // kernels launched
 void launch_move_nodes(const Dev &d, cudaStream_t s);
 void launch_geometry(const Dev &d, cudaStream_t s, int fp32);   // 4 kernels
 void launch_slope_geo(const Dev &d, cudaStream_t s);
@@ -24,7 +25,8 @@ void launch_wall_loads(const Dev &d, cudaStream_t s);
 void launch_f_convert(const Dev &d, cudaStream_t s, double *out, const double *in, int fp32);
 void launch_connect(const Dev &d, cudaStream_t s, int *prev_status, const int *blk_order,
                     int *n_orphan);                           // 7 kernels
-void launch_interp(const Dev &d, cudaStream_t s, const int *list, int n, int fp32);  // 2 kernels
+void launch_lists(const Dev &d, cudaStream_t s, const int *fresh_flag, const int *n_orphan);  // 2 kernels
+void launch_interp(const Dev &d, cudaStream_t s, const int *list, const int *cnt, int nsm, int fp32);  // 2 kernels
 // tiled kernels (ugks_tile.cu)
 void tile_setup();
 int tile_count(int ni, int nj);

@@ -22,6 +22,8 @@
 // The FP64 predicates decide everything; float filters in front of them only
 // skip work whose outcome they already know exactly: with rn() the
 // round-to-nearest map to float (monotone), rn(a) > rn(b) implies a > b.
+#include <algorithm>
+
 #include "ugks_internal.cuh"
 #include "ugks_launch.h"
 
@@ -363,48 +365,119 @@ __global__ void k_donor(Dev d, const int *fresh_flag, const int *blk_order, int 
   for (int m = 0; m < ns; ++m) d.dwgt[5 * c + m] = dv(inv[m], tot);
 }
 
-// Jacobi interpolation: gather into staging, then scatter.
-template <typename T> __global__ void k_interp_gather(Dev d, const int *list, int n) {
-  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)n * d.nvp) return;
-  int r = (int)(t / d.nvp), k = (int)(t % d.nvp);
-  int c = list[r];
-  double ah = 0.0, ab = 0.0;
-  for (int m = 0; m < 5; ++m) {
-    int e = d.donors[5 * c + m];
-    if (e < 0) continue;
-    double w = d.dwgt[5 * c + m];
-    auto v = ldf<T>(d.f, (size_t)e * d.nvp + k);
-    ah = ah + w * (double)v.x;
-    ab = ab + w * (double)v.y;
+// Receptor and fresh-cell lists, compacted on the device in ascending cell
+// order (two passes over 1024-cell chunks: count, then scan and write), so
+// that no host round trip sits between the assembly and the step.
+constexpr int LCHUNK = 1024;
+
+__global__ void __launch_bounds__(LCHUNK) k_list_count(Dev d, const int *fresh_flag) {
+  int c = blockIdx.x * LCHUNK + threadIdx.x;
+  bool in = c < d.nc;
+  int st = in ? d.status[c] : -1;
+  int nr = __syncthreads_count(in && st == ST_RECEPTOR);
+  int nfr = __syncthreads_count(in && fresh_flag[c] != 0);
+  int nfd = __syncthreads_count(in && st == ST_FIELD);
+  int no = __syncthreads_count(in && st != ST_FIELD && st != ST_RECEPTOR);
+  if (threadIdx.x == 0) d.conn_chunk[blockIdx.x] = make_int4(nr, nfr, nfd, no);
+}
+
+__global__ void __launch_bounds__(LCHUNK) k_list_write(Dev d, const int *fresh_flag, const int *n_orphan) {
+  __shared__ int base[2];
+  __shared__ int wcnt[2][LCHUNK / 32];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (w == 0) {   // offsets of this chunk: totals of the earlier chunks
+    int a = 0, b = 0;
+    for (int q = lane; q < (int)blockIdx.x; q += 32) {
+      int4 v = d.conn_chunk[q];
+      a += v.x;
+      b += v.y;
+    }
+    for (int o = 16; o >= 1; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) { base[0] = a; base[1] = b; }
   }
-  stf<T>(d.itmp, t, (T)ah, (T)ab);
-  if (k == 0) {
-    double acc[6] = {0, 0, 0, 0, 0, 0};
+  int c = blockIdx.x * LCHUNK + threadIdx.x;
+  bool in = c < d.nc;
+  bool isr = in && d.status[c] == ST_RECEPTOR;
+  bool isf = in && fresh_flag[c] != 0;
+  unsigned mr = __ballot_sync(0xffffffffu, isr), mf = __ballot_sync(0xffffffffu, isf);
+  if (lane == 0) { wcnt[0][w] = __popc(mr); wcnt[1][w] = __popc(mf); }
+  __syncthreads();
+  int orr = base[0], off = base[1];
+  for (int q = 0; q < w; ++q) { orr += wcnt[0][q]; off += wcnt[1][q]; }
+  unsigned below = (1u << lane) - 1u;
+  int ir = orr + __popc(mr & below), jf = off + __popc(mf & below);
+  if (isr && ir < d.cap_interp) d.rec_list[ir] = c;
+  if (isf && jf < d.cap_interp) d.fresh_list[jf] = c;
+  if (blockIdx.x == gridDim.x - 1 && w == 0) {   // totals and their checks
+    int t[4] = {0, 0, 0, 0};
+    for (int q = lane; q < (int)gridDim.x; q += 32) {
+      int4 v = d.conn_chunk[q];
+      t[0] += v.x; t[1] += v.y; t[2] += v.z; t[3] += v.w;
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+      for (int o = 16; o >= 1; o >>= 1) t[m] += __shfl_xor_sync(0xffffffffu, t[m], o);
+    if (lane == 0) {
+      int no = *n_orphan;
+      d.conn_cnt[0] = t[0]; d.conn_cnt[1] = t[1]; d.conn_cnt[2] = t[2]; d.conn_cnt[3] = t[3];
+      d.conn_cnt[4] = no;
+      if (t[0] > d.cap_interp || t[1] > d.cap_interp) atomicOr(d.err, EF_CAPACITY);
+      if (no > 0) atomicOr(d.err, EF_ORPHAN);
+    }
+  }
+}
+
+// Jacobi interpolation: gather into staging, then scatter.  The list length
+// is read on the device (*cnt, clamped to the staging capacity); a fixed grid
+// strides over it.
+template <typename T> __global__ void k_interp_gather(Dev d, const int *list, const int *cnt) {
+  int n = min(*cnt, d.cap_interp);
+  size_t tot = (size_t)n * d.nvp;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (size_t)gridDim.x * blockDim.x) {
+    int r = (int)(t / d.nvp), k = (int)(t % d.nvp);
+    int c = list[r];
+    double ah = 0.0, ab = 0.0;
     for (int m = 0; m < 5; ++m) {
       int e = d.donors[5 * c + m];
       if (e < 0) continue;
       double w = d.dwgt[5 * c + m];
-      for (int q = 0; q < 4; ++q) acc[q] = acc[q] + w * d.W[4 * e + q];
-      acc[4] = acc[4] + w * d.q[2 * e];
-      acc[5] = acc[5] + w * d.q[2 * e + 1];
+      auto v = ldf<T>(d.f, (size_t)e * d.nvp + k);
+      ah = ah + w * (double)v.x;
+      ab = ab + w * (double)v.y;
     }
-    for (int q = 0; q < 6; ++q) d.itmpW[6 * r + q] = acc[q];
+    stf<T>(d.itmp, t, (T)ah, (T)ab);
+    if (k == 0) {
+      double acc[6] = {0, 0, 0, 0, 0, 0};
+      for (int m = 0; m < 5; ++m) {
+        int e = d.donors[5 * c + m];
+        if (e < 0) continue;
+        double w = d.dwgt[5 * c + m];
+        for (int q = 0; q < 4; ++q) acc[q] = acc[q] + w * d.W[4 * e + q];
+        acc[4] = acc[4] + w * d.q[2 * e];
+        acc[5] = acc[5] + w * d.q[2 * e + 1];
+      }
+      for (int q = 0; q < 6; ++q) d.itmpW[6 * r + q] = acc[q];
+    }
   }
 }
 
-template <typename T> __global__ void k_interp_scatter(Dev d, const int *list, int n) {
-  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)n * d.nvp) return;
-  int r = (int)(t / d.nvp), k = (int)(t % d.nvp);
-  int c = list[r];
-  if (d.donors[5 * c] < 0) return;            // orphan: keep its values
-  auto v = ldf<T>(d.itmp, t);
-  stf<T>(d.f, (size_t)c * d.nvp + k, v.x, v.y);
-  if (k == 0) {
-    for (int q = 0; q < 4; ++q) d.W[4 * c + q] = d.itmpW[6 * r + q];
-    d.q[2 * c] = d.itmpW[6 * r + 4];
-    d.q[2 * c + 1] = d.itmpW[6 * r + 5];
+template <typename T> __global__ void k_interp_scatter(Dev d, const int *list, const int *cnt) {
+  int n = min(*cnt, d.cap_interp);
+  size_t tot = (size_t)n * d.nvp;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (size_t)gridDim.x * blockDim.x) {
+    int r = (int)(t / d.nvp), k = (int)(t % d.nvp);
+    int c = list[r];
+    if (d.donors[5 * c] < 0) continue;          // orphan: keep its values
+    auto v = ldf<T>(d.itmp, t);
+    stf<T>(d.f, (size_t)c * d.nvp + k, v.x, v.y);
+    if (k == 0) {
+      for (int q = 0; q < 4; ++q) d.W[4 * c + q] = d.itmpW[6 * r + q];
+      d.q[2 * c] = d.itmpW[6 * r + 4];
+      d.q[2 * c + 1] = d.itmpW[6 * r + 5];
+    }
   }
 }
 
@@ -423,15 +496,21 @@ void launch_connect(const Dev &d, cudaStream_t s, int *prev_status, const int *b
   k_donor<<<nblk(d.nc, 128), 128, 0, s>>>(d, prev_status, blk_order, n_orphan);
 }
 
-void launch_interp(const Dev &d, cudaStream_t s, const int *list, int n, int fp32) {
-  if (n <= 0) return;
-  size_t tot = (size_t)n * d.nvp;
+void launch_lists(const Dev &d, cudaStream_t s, const int *fresh_flag, const int *n_orphan) {
+  int nch = nblk(d.nc, LCHUNK);
+  k_list_count<<<nch, LCHUNK, 0, s>>>(d, fresh_flag);
+  k_list_write<<<nch, LCHUNK, 0, s>>>(d, fresh_flag, n_orphan);
+}
+
+void launch_interp(const Dev &d, cudaStream_t s, const int *list, const int *cnt, int nsm, int fp32) {
+  size_t tot = (size_t)d.cap_interp * d.nvp;
+  int grid = std::max(1, std::min(nblk(tot, 256), 8 * std::max(nsm, 1)));
   if (fp32) {
-    k_interp_gather<float><<<nblk(tot, 256), 256, 0, s>>>(d, list, n);
-    k_interp_scatter<float><<<nblk(tot, 256), 256, 0, s>>>(d, list, n);
+    k_interp_gather<float><<<grid, 256, 0, s>>>(d, list, cnt);
+    k_interp_scatter<float><<<grid, 256, 0, s>>>(d, list, cnt);
   } else {
-    k_interp_gather<double><<<nblk(tot, 256), 256, 0, s>>>(d, list, n);
-    k_interp_scatter<double><<<nblk(tot, 256), 256, 0, s>>>(d, list, n);
+    k_interp_gather<double><<<grid, 256, 0, s>>>(d, list, cnt);
+    k_interp_scatter<double><<<grid, 256, 0, s>>>(d, list, cnt);
   }
 }
 

@@ -55,6 +55,8 @@ SYMBOLS = {
     "ugks_move_mesh": (c_int, [c_void_p, c_double, POINTER(c_double)]),
     "ugks_overset_connect": (c_int, [c_void_p, POINTER(ConnectStats)]),
     "ugks_step": (c_int, [c_void_p, c_double, c_int]),
+    "ugks_advance_batch": (c_int, [POINTER(c_void_p), c_int, POINTER(c_double), POINTER(POINTER(c_double)),
+                                   c_int, POINTER(c_int)]),
     "ugks_moments": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ugks_sizes": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
     "ugks_get_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -285,3 +287,30 @@ class Solver:
         n = (c_int64 * len(PROF_GROUPS))()
         self._check(self.lib.ugks_profile_read(self.ctx, ms, n, int(bool(reset))))
         return {g: (float(ms[i]), int(n[i])) for i, g in enumerate(PROF_GROUPS)}
+
+
+def advance_batch(solvers, n_inner=None):
+    """One physical step of every solver (instance) through
+    ugks_advance_batch: motion from each case's own map at t + dt, overset
+    assembly and the implicit step, issued without waiting on the device.
+    Solvers created on distinct streams run concurrently."""
+    lib = load()
+    n = len(solvers)
+    if n == 0:
+        return
+    inner = {s.case.n_inner if n_inner is None else n_inner for s in solvers}
+    if len(inner) != 1:
+        raise ValueError("one n_inner for the whole batch")
+    ctxs = (c_void_p * n)(*[s.ctx.value for s in solvers])
+    t_new = (c_double * n)(*[s.t + s.case.dt for s in solvers])
+    maps = [np.ascontiguousarray(s.case.motion(t_new[i]), dtype=np.float64) for i, s in enumerate(solvers)]
+    aff = (POINTER(c_double) * n)(*[m.ctypes.data_as(POINTER(c_double)) for m in maps])
+    failed = c_int(-1)
+    r = lib.ugks_advance_batch(ctxs, n, t_new, aff, int(inner.pop()), ctypes.byref(failed))
+    if r != OK:
+        s = solvers[failed.value] if failed.value >= 0 else None
+        msg = lib.ugks_last_error(s.ctx).decode() if s is not None else ""
+        raise UgksError(r, "instance %d: %s" % (failed.value, msg))
+    for i, s in enumerate(solvers):
+        s._t_new = t_new[i]
+        s.t = t_new[i]

@@ -15,6 +15,8 @@ Configurations (nondimensional, rho0 = T0 = R = L = 1):
             plate translating sinusoidally (overset MEMS, Sec. 4.1/4.2).
   tsto      Ma 8 background + two O-grids (wedge and cylinder) with prescribed
             separation and pitch (2D stand-in for the TSTO case of Sec. 4.3).
+  mems_batch  many independent `mems` instances of uneven sizes, velocity
+            grids, Knudsen numbers and wall temperatures (batched serving).
 The paper's own geometries exist only as missing figures; these synthetic
 cases carry their sizes, regimes and motion types.
 """
@@ -136,21 +138,26 @@ def ellipse_contour(center, a, b):
 
 
 def polygon_contour(center, verts):
-    """Closed polygon traversed by arc length; th in (-2 pi, 0] maps to the
-    fraction -th/(2 pi) of the perimeter (clockwise order is the caller's)."""
-    P = [np.asarray(v, dtype=float) + np.asarray(center, dtype=float) for v in verts]
+    """Star-shaped polygon (vertices relative to `center`) parametrised by the
+    angle th of the ray from `center`: the point where that ray leaves the
+    polygon.  Matching the outer circle of an O-grid angle by angle keeps its
+    radial lines from crossing."""
+    P = [np.asarray(v, dtype=float) for v in verts]
     seg = [(P[i], P[(i + 1) % len(P)]) for i in range(len(P))]
-    lens = [float(np.hypot(*(b - a))) for a, b in seg]
-    tot = sum(lens)
 
     def c(th):
-        s = (-th / (2.0 * math.pi)) % 1.0 * tot
-        for (a, b), L in zip(seg, lens):
-            if s <= L:
-                p = a + (b - a) * (s / L)
-                return float(p[0]), float(p[1])
-            s -= L
-        return float(P[0][0]), float(P[0][1])
+        dx, dy = math.cos(th), math.sin(th)
+        best = None
+        for a, b in seg:
+            ex, ey = b[0] - a[0], b[1] - a[1]
+            den = dx * ey - dy * ex
+            if den == 0.0:
+                continue
+            t = (a[0] * ey - a[1] * ex) / den        # distance along the ray
+            s = (a[0] * dy - a[1] * dx) / den        # position along the edge
+            if t > 0.0 and -1e-12 <= s <= 1.0 + 1e-12 and (best is None or t < best):
+                best = t
+        return center[0] + best * dx, center[1] + best * dy
     return c
 
 
@@ -202,7 +209,7 @@ def channel(ni=64, nj=32, nv=24, vmax=5.0, Kn=0.05, n_steps=20, n_inner=10,
 def mems(nbi=256, nbj=128, noi=128, noj=32, nv=32, vmax=6.0, Kn=0.1,
          n_steps=200, n_inner=10, cfl=10.0, Tw=1.5, mach=0.05, amp=0.1,
          plate=(0.1, 0.01), r_out=0.25, stretch=1.1, noise=0.0, seed=0,
-         omega=0.81, Pr=2.0 / 3.0, K=0) -> Case:
+         omega=0.81, Pr=2.0 / 3.0, K=0, n_gap=2) -> Case:
     """Thermal rarefied MEMS with overset grids: closed diffuse box [0,2]x[0,1]
     at T0 = 1, body-fitted O-grid around an elliptic plate (semi-axes
     `plate`, wall temperature Tw) translating y_c = 0.5 + amp sin(2 pi f t)
@@ -215,7 +222,7 @@ def mems(nbi=256, nbj=128, noi=128, noj=32, nv=32, vmax=6.0, Kn=0.1,
     og = BlockSpec(noi, noj, True, (BC_NONE, BC_NONE, BC_WALL, BC_OVERSET),
                    (0.0, 0.0, Tw, 0.0),
                    ogrid_nodes(noi, noj, ellipse_contour(c, *plate), c, r_out, stretch),
-                   priority=1)
+                   priority=1, n_gap=n_gap)
 
     def motion(t):
         M = _affine_identity(2)
@@ -275,6 +282,44 @@ def tsto(nbi=512, nbj=256, noi=192, noj=48, nv=64, vmax=15.0, Kn=0.01,
     return Case("tsto", K, Pr, omega, mu_ref_from_knudsen(Kn, omega), nv, nv,
                 (-vmax, vmax, -vmax, vmax), [bg, wedge, cyl], (1.0, uinf, 0.0, 1.0),
                 dt, n_inner, n_steps, motion, prim, meta=dict(Kn=Kn, uinf=uinf))
+
+
+def overlap_gap_layers(nbi, noj, stretch, r_out, r_body, n_fringe=2, cells=3.0, n_min=2):
+    """Gap layers of an O-grid (radial geometric stretching) such that the
+    rings that do not cut holes span at least `cells` background cells of
+    width 2/nbi between the body (radius r_body at its widest) and r_out, so
+    that the background's buffer receptors around the hole lie inside the
+    body grid.  Pure mesh bookkeeping on the node radii."""
+    h = 2.0 / nbi
+    frac = lambda j: (stretch ** j - 1.0) / (stretch ** noj - 1.0)
+    for g in range(n_min, noj - n_fringe):
+        k = noj - n_fringe - g                 # rings below k cut holes
+        if (1.0 - frac(k)) * (r_out - r_body) >= cells * h:
+            return g
+    return noj - n_fringe - 1
+
+
+def mems_batch(n=64, seed=0, n_steps=200, n_inner=10, ni_range=(48, 192), ntheta_range=(64, 128),
+               nv_range=(20, 40), Kn_range=(0.01, 2.0), Tw_range=(1.0, 2.0)) -> List[Case]:
+    """Serving-style sweep of independent oscillating-plate instances
+    (uneven sizes): background n_i in {48, 56, ..., 192} with n_j = n_i / 2,
+    O-grid n_theta in {64, 72, ..., 128} with n_r = n_theta / 4, N_vx = N_vy
+    in {20, ..., 40}, Kn log-uniform, wall temperature uniform; everything
+    else as `mems`, except that coarse backgrounds get more O-grid gap layers
+    (overlap_gap_layers) so that no receptor is left without a donor.
+    Seeded (numpy PCG64)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(n):
+        nbi = int(rng.integers(ni_range[0] // 8, ni_range[1] // 8 + 1)) * 8
+        nth = int(rng.integers(ntheta_range[0] // 8, ntheta_range[1] // 8 + 1)) * 8
+        nv = int(rng.integers(nv_range[0], nv_range[1] + 1))
+        Kn = float(10.0 ** rng.uniform(math.log10(Kn_range[0]), math.log10(Kn_range[1])))
+        Tw = float(rng.uniform(*Tw_range))
+        gap = overlap_gap_layers(nbi, nth // 4, 1.1, 0.25, 0.1)
+        out.append(mems(nbi=nbi, nbj=nbi // 2, noi=nth, noj=nth // 4, nv=nv, Kn=Kn, Tw=Tw,
+                        n_steps=n_steps, n_inner=n_inner, n_gap=gap))
+    return out
 
 
 def random_prim(case: Case, seed: int, amp_rho=0.2, amp_u=0.3, amp_T=0.2):

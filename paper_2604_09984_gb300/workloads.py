@@ -138,27 +138,48 @@ def ellipse_contour(center, a, b):
 
 
 def polygon_contour(center, verts):
-    """Star-shaped polygon (vertices relative to `center`) parametrised by the
-    angle th of the ray from `center`: the point where that ray leaves the
-    polygon.  Matching the outer circle of an O-grid angle by angle keeps its
-    radial lines from crossing."""
+    """Closed polygon (vertices relative to `center`, clockwise) traversed by
+    arc length: th in (-2 pi, 0] maps to the fraction -th / (2 pi) of the
+    perimeter, measured clockwise from the point where the ray at angle 0
+    from `center` leaves the polygon, so that an O-grid's contour and outer
+    circle start at the same angle and turn the same way."""
     P = [np.asarray(v, dtype=float) for v in verts]
     seg = [(P[i], P[(i + 1) % len(P)]) for i in range(len(P))]
+    lens = [float(np.hypot(*(b - a))) for a, b in seg]
+    tot = sum(lens)
+    s0, acc = 0.0, 0.0
+    for (a, b), L in zip(seg, lens):    # the ray (1, 0) from the centre
+        ey = b[1] - a[1]
+        if ey != 0.0:
+            u = -a[1] / ey                  # edge parameter where y = 0
+            x = a[0] + u * (b[0] - a[0])
+            if 0.0 <= u < 1.0 and x > 0.0:
+                s0 = acc + u * L
+        acc += L
 
     def c(th):
-        dx, dy = math.cos(th), math.sin(th)
-        best = None
-        for a, b in seg:
-            ex, ey = b[0] - a[0], b[1] - a[1]
-            den = dx * ey - dy * ex
-            if den == 0.0:
-                continue
-            t = (a[0] * ey - a[1] * ex) / den        # distance along the ray
-            s = (a[0] * dy - a[1] * dx) / den        # position along the edge
-            if t > 0.0 and -1e-12 <= s <= 1.0 + 1e-12 and (best is None or t < best):
-                best = t
-        return center[0] + best * dx, center[1] + best * dy
+        s = (s0 + (-th / (2.0 * math.pi)) * tot) % tot
+        for (a, b), L in zip(seg, lens):
+            if s <= L:
+                q = a + (b - a) * (s / L)
+                return center[0] + float(q[0]), center[1] + float(q[1])
+            s -= L
+        return center[0] + float(P[0][0]), center[1] + float(P[0][1])
     return c
+
+
+def smallest_cell_width(blocks) -> float:
+    """min over the cells of all blocks of 4 * area / perimeter (the width
+    of a square cell), from the reference nodes."""
+    w = math.inf
+    for b in blocks:
+        X = b.x_ref
+        P = [X[:-1, :-1], X[1:, :-1], X[1:, 1:], X[:-1, 1:]]
+        area = 0.5 * sum(P[m][..., 0] * P[(m + 1) % 4][..., 1] - P[m][..., 1] * P[(m + 1) % 4][..., 0]
+                         for m in range(4))
+        per = sum(np.hypot(*(P[(m + 1) % 4] - P[m]).transpose(2, 0, 1)) for m in range(4))
+        w = min(w, float((4.0 * np.abs(area) / per).min()))
+    return w
 
 
 def _affine_identity(n):
@@ -244,7 +265,8 @@ def tsto(nbi=512, nbj=256, noi=192, noj=48, nv=64, vmax=15.0, Kn=0.01,
     """2D hypersonic two-body separation: free stream Ma 8 from the left,
     far field left/top/bottom, outflow right; a 10-degree half-angle wedge of
     chord 0.3 pitching at 0.5 rad per unit time about its centroid, and a
-    cylinder of radius 0.1 separating in +y at 0.02 u_inf.  Walls at T_inf."""
+    cylinder of radius 0.1 separating in +y at 0.02 u_inf.  Walls at T_inf.
+    Gas initially at rest; time step from the smallest cell of all blocks."""
     gamma = (K + 5.0) / (K + 3.0)
     uinf = mach * math.sqrt(gamma)
     bg = BlockSpec(nbi, nbj, False, (BC_FARFIELD, BC_OUTFLOW, BC_FARFIELD, BC_FARFIELD),
@@ -275,10 +297,14 @@ def tsto(nbi=512, nbj=256, noi=192, noj=48, nv=64, vmax=15.0, Kn=0.01,
         M[2, 5] = 0.02 * uinf * t
         return M
 
-    h = min(2.0 / nbi, 1.0 / nbj)
-    dt = cfl * h / (2.0 * vmax)
+    # time step from the smallest cell of all blocks (the body grids' wall
+    # cells): CFL relative to the fastest discrete velocity there
+    dt = cfl * smallest_cell_width([bg, wedge, cyl]) / (2.0 * vmax)
     n = bg.ncells + wedge.ncells + cyl.ncells
-    prim = _init_noise(n, seed, 0.0, ux=uinf)
+    # start-up from rest: the free stream enters through the far field (an
+    # impulsive start with the stream everywhere and the walls at rest
+    # empties the cells behind the bodies within a step at CFL 10)
+    prim = _init_noise(n, seed, 0.0)
     return Case("tsto", K, Pr, omega, mu_ref_from_knudsen(Kn, omega), nv, nv,
                 (-vmax, vmax, -vmax, vmax), [bg, wedge, cyl], (1.0, uinf, 0.0, 1.0),
                 dt, n_inner, n_steps, motion, prim, meta=dict(Kn=Kn, uinf=uinf))

@@ -64,3 +64,19 @@ def test_argument_validation(lib):
     # misaligned workspace is rejected before any CUDA call
     ctx = ctypes.c_void_p()
     assert lib.ugks_create(ctypes.byref(p), ctypes.c_void_p(8), 100, None, ctypes.byref(ctx)) == -6
+
+
+def test_batch_argument_validation(lib):
+    """ugks_advance_batch checks its arguments before touching any context or
+    the device: an empty batch is a no-op, a negative count or missing arrays
+    are rejected."""
+    failed = ctypes.c_int(7)
+    assert lib.ugks_advance_batch(None, 0, None, None, 10, ctypes.byref(failed)) == 0
+    assert failed.value == -1
+    assert lib.ugks_advance_batch(None, -1, None, None, 10, ctypes.byref(failed)) == -1
+    ctxs = (ctypes.c_void_p * 1)(None)
+    assert lib.ugks_advance_batch(ctxs, 1, None, None, 10, None) == -1
+    t = (ctypes.c_double * 1)(1.0)
+    aff = (ctypes.POINTER(ctypes.c_double) * 1)()
+    assert lib.ugks_advance_batch(ctxs, 1, t, aff, 10, ctypes.byref(failed)) == -7
+    assert failed.value == 0

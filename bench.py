@@ -165,12 +165,15 @@ def ncu_traffic(group):
     return traffic.get(group)
 
 
-def time_arm(case, precision, steps, warmup, device, profile):
+def time_arm(case, precision, steps, warmup, device, profile, tune=True):
     import torch
     from paper_2604_09984_gb300 import ugks as U
     s = U.Solver(case, precision, device=device)
-    for _ in range(warmup):
+    s.tiles = None
+    for n in range(warmup):
         s.advance()
+        if n == 0 and tune:
+            s.autotune()          # sweep tiles for this workload, before the timed steps
     torch.cuda.synchronize()
     nfield = field_cells(s)
     if profile:
@@ -229,9 +232,13 @@ def batch_arm(cases, steps, warmup, device):
     from paper_2604_09984_gb300 import ugks as U
     streams = [torch.cuda.Stream(device=device) for _ in cases]
     solvers = [U.Solver(c, U.FP32, device=device, stream=st) for c, st in zip(cases, streams)]
-    for _ in range(warmup):
+    for n in range(warmup):
         U.advance_batch(solvers)
+        if n == 0:
+            for s in solvers:     # per-instance sweep tiles
+                s.autotune()
     torch.cuda.synchronize()
+    tiles = sorted({s.tiles for s in solvers})
     nfield = [field_cells(s) for s in solvers]
     l0 = sum(s.launch_count() for s in solvers)
     main_st = torch.cuda.current_stream(device)
@@ -273,7 +280,7 @@ def batch_arm(cases, steps, warmup, device):
     d2h = sum(sum(t.numel() * t.element_size() for t in o) for o in outs)
     for s in solvers:
         s.close()
-    return ms, units, launches, host_s, e2e_s, h2d, d2h, sum(nfield)
+    return ms, units, launches, host_s, e2e_s, h2d, d2h, sum(nfield), tiles
 
 
 def run_batch(args, world, rank, device):
@@ -282,7 +289,7 @@ def run_batch(args, world, rank, device):
     warmup = max(3, args.warmup)
     clk = Clocks(int(device.split(":")[1]))
     clk.start()
-    ms, units, launches, host_s, e2e_s, h2d, d2h, nfield = batch_arm(cases, steps, warmup, device)
+    ms, units, launches, host_s, e2e_s, h2d, d2h, nfield, tiles = batch_arm(cases, steps, warmup, device)
     clocks = clk.stop()
     value = units * world / (ms * 1e-3)
     line = {
@@ -294,6 +301,7 @@ def run_batch(args, world, rank, device):
                                % (len(cases), nfield, sum(c.ncells * c.nv for c in cases)),
                    "precision": "FP32 f and per-velocity arithmetic, FP64 moments/geometry",
                    "l2": "inputs larger than L2", "streams": len(cases),
+                   "sweep_tiles": "autotuned per instance (items per CTA and diagonal, ring): %s" % tiles,
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "host_issue_ms_per_step": host_s * 1e3 / steps,
         "clocks": clocks,
@@ -434,6 +442,7 @@ def main():
             breakdown[g]["GBps"] = round(b / (gms / gn * 1e-3) / 1e9, 1)
     e2e_ms, h2d, d2h = e2e_arm(s, steps)
     e2e_val = nfield * case.nv * case.n_inner * steps * world / (e2e_ms * 1e-3)
+    tiles = s.tiles
     s.close()
     del s
     torch.cuda.empty_cache()
@@ -451,6 +460,7 @@ def main():
         "config": {"workload": workload_label(case), "precision": "FP32 f and per-velocity arithmetic, FP64 moments/geometry",
                    "l2": "inputs larger than L2 (f alone %.0f MB)" % (s_bytes(case) / 1e6),
                    "field_cells": nfield, "nv": case.nv, "n_inner": case.n_inner,
+                   "sweep_tiles": "autotuned (items per CTA and diagonal, ring): %s" % (tiles,),
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "per_physical_step": value / case.n_inner,
         "clocks": clocks,

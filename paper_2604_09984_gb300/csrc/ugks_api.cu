@@ -30,6 +30,9 @@ struct ugks_ctx {
   std::vector<int> cell_off, node_off;
   int max_nj = 0;
   int sweep_threads = 32, nwork = 0, nsm = 0;
+  int nwork_cap = 0;                  // work-list capacity (largest tuning candidate)
+  int sweep_items = 0, sweep_ns = 0;  // micro-sweep tile and ring depth (0 = by rule)
+  bool stepped = false;               // a ugks_step has run (sweep records valid)
   int *work = nullptr;
   int *prev_status = nullptr, *n_orphan = nullptr, *blk_order = nullptr;
   int cap_interp = 0;
@@ -128,9 +131,10 @@ struct Carver {
 // tile is sized for about 1024 (cell, velocity) items per diagonal step --
 // enough independent work per step for the SM while the whole sweep stays
 // within about one CTA per SM -- with at most 512 threads and no more
-// velocities than the array holds.  UGKS_VTILE (velocities per CTA)
-// overrides where it fits.
-int block_G(int nj, int nvp, int vpt) {
+// velocities than the array holds.  `items` > 0 replaces the 1024 (the
+// autotuner's candidates); UGKS_SWEEP_ITEMS and UGKS_VTILE (velocities per
+// CTA) override by hand where they fit.
+int block_G(int nj, int nvp, int vpt, int items_req = 0) {
   int r = 1;
   while (r < nj) r <<= 1;
   int items = 1024;                        // (cell, velocity) items per CTA and diagonal
@@ -138,6 +142,7 @@ int block_G(int nj, int nvp, int vpt) {
     int v = atoi(e);
     if (v >= 32 && v <= 8192) items = v;
   }
+  if (items_req > 0) items = items_req;
   int vt = items / r;
   const char *env = getenv("UGKS_VTILE");
   if (env && atoi(env) >= 1) vt = atoi(env);
@@ -156,11 +161,11 @@ int sweep_vpt_for(const ugks_params *p) {
 
 // Threads of a micro-sweep CTA: the widest block's rows x G, rounded up to
 // whole warps.
-int sweep_threads_for(const ugks_params *p, int nb, const ugks_block_desc *b) {
+int sweep_threads_for(const ugks_params *p, int nb, const ugks_block_desc *b, int items = 0) {
   int nvp = (p->nvx * p->nvy + 3) / 4 * 4, vpt = sweep_vpt_for(p);
   int t = 32;
   for (int i = 0; i < nb; ++i) {
-    int w = b[i].nj * block_G(b[i].nj, nvp, vpt);
+    int w = b[i].nj * block_G(b[i].nj, nvp, vpt, items);
     if (w > t) t = w;
   }
   return (t + 31) / 32 * 32;
@@ -263,13 +268,25 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int nwork, int cap_in
 int cap_interp_for(const Sizes &s, int nb) { return nb > 1 ? (s.nc / 4 > 1024 ? s.nc / 4 : (s.nc < 1024 ? s.nc : 1024)) : 0; }
 
 // Micro-sweep work items (block, first velocity, G): one per velocity tile.
-int nwork_for(const ugks_params *p, int nb, const ugks_block_desc *b) {
+int nwork_for(const ugks_params *p, int nb, const ugks_block_desc *b, int items = 0) {
   int nvp = (p->nvx * p->nvy + 3) / 4 * 4, vpt = sweep_vpt_for(p);
   int n = 0;
   for (int i = 0; i < nb; ++i) {
-    int vt = block_G(b[i].nj, nvp, vpt) * vpt;
+    int vt = block_G(b[i].nj, nvp, vpt, items) * vpt;
     n += (nvp + vt - 1) / vt;
   }
+  return n;
+}
+
+// Candidate tile sizes of the sweep autotuner ((cell, velocity) items per CTA
+// and diagonal step) and ring depths.
+constexpr int kTuneItems[] = {256, 512, 1024, 2048};
+constexpr int kTuneRing[] = {2, 3, 4};
+
+// Work-list capacity: the most tiles any candidate (or the default) needs.
+int nwork_cap_for(const ugks_params *p, int nb, const ugks_block_desc *b) {
+  int n = nwork_for(p, nb, b);
+  for (int it : kTuneItems) n = std::max(n, nwork_for(p, nb, b, it));
   return n;
 }
 
@@ -425,6 +442,30 @@ int check_err_flag(ugks_ctx *ctx) {
 
 int launch_status(ugks_ctx *ctx) { return cuda_check(ctx, cudaPeekAtLastError(), "kernel launch"); }
 
+// Micro-sweep work list for a tile size (items per CTA and diagonal, 0 = by
+// rule): (block, first velocity, G) per velocity tile of every block.
+std::vector<int> sweep_work(const ugks_ctx *ctx, int items) {
+  std::vector<int> work;
+  int nvp = ctx->d.nvp, vpt = sweep_vpt_for(&ctx->p);
+  for (int b = 0; b < ctx->nblocks; ++b) {
+    int G = block_G(ctx->blocks[b].nj, nvp, vpt, items);
+    for (int k0 = 0; k0 < nvp; k0 += G * vpt) { work.push_back(b); work.push_back(k0); work.push_back(G); }
+  }
+  return work;
+}
+
+// Switch the micro sweeps to another tile size (uploads the work list).
+int set_sweep_tiles(ugks_ctx *ctx, int items) {
+  std::vector<int> work = sweep_work(ctx, items);
+  if ((int)work.size() / 3 > ctx->nwork_cap) return fail(ctx, UGKS_ERR_WORKSPACE, "sweep work list");
+  CK(cudaMemcpyAsync(ctx->work, work.data(), sizeof(int) * work.size(), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  ctx->nwork = (int)work.size() / 3;
+  ctx->sweep_threads = sweep_threads_for(&ctx->p, ctx->nblocks, ctx->blocks.data(), items);
+  ctx->sweep_items = items;
+  return UGKS_OK;
+}
+
 // Event pair around one launch of a kernel group (only while profiling).
 struct Prof {
   ugks_ctx *c;
@@ -570,7 +611,7 @@ int ugks_workspace_query(const ugks_params *p, int nblocks, const ugks_block_des
   if (!bytes) return UGKS_ERR_ARG;
   Dev d;
   memset(&d, 0, sizeof(d));
-  *bytes = carve(nullptr, s, nblocks, p->precision == UGKS_FP32, nwork_for(p, nblocks, blocks),
+  *bytes = carve(nullptr, s, nblocks, p->precision == UGKS_FP32, nwork_cap_for(p, nblocks, blocks),
                  cap_interp_for(s, nblocks), d);
   return UGKS_OK;
 }
@@ -645,19 +686,20 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
     cudaGetLastError();
   }
   ctx->nwork = nwork_for(&ctx->p, nblocks, blocks);
+  ctx->nwork_cap = nwork_cap_for(&ctx->p, nblocks, blocks);
   ctx->cap_interp = cap_interp_for(s, nblocks);
   Dev &d = ctx->d;
   memset(&d, 0, sizeof(d));
-  size_t need = carve(nullptr, s, nblocks, ctx->fp32, ctx->nwork, ctx->cap_interp, d);
+  size_t need = carve(nullptr, s, nblocks, ctx->fp32, ctx->nwork_cap, ctx->cap_interp, d);
   if (need > ctx->ws_bytes) return fail(ctx, UGKS_ERR_WORKSPACE, "workspace too small: need " + std::to_string(need));
-  carve(ctx->ws, s, nblocks, ctx->fp32, ctx->nwork, ctx->cap_interp, d);
+  carve(ctx->ws, s, nblocks, ctx->fp32, ctx->nwork_cap, ctx->cap_interp, d);
   {
     // the trailing private arrays follow d.err in carve order
     Carver c(ctx->ws);
     Dev tmp;
     memset(&tmp, 0, sizeof(tmp));
     c.off = (size_t)((char *)d.err - ctx->ws) + 4 * sizeof(int) + 16;
-    ctx->work = c.take<int>(3 * (size_t)ctx->nwork + 3);
+    ctx->work = c.take<int>(3 * (size_t)ctx->nwork_cap + 3);
     ctx->prev_status = c.take<int>(s.nc);
     ctx->n_orphan = c.take<int>(4);
     ctx->blk_order = c.take<int>(nblocks);
@@ -716,11 +758,7 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
       if (blocks[order[b]].priority > blocks[order[a]].priority ||
           (blocks[order[b]].priority == blocks[order[a]].priority && order[b] < order[a]))
         std::swap(order[a], order[b]);
-  std::vector<int> work;
-  for (int b = 0; b < nblocks; ++b) {
-    int vpt = sweep_vpt_for(&ctx->p), G = block_G(blocks[b].nj, s.nvp, vpt);
-    for (int k0 = 0; k0 < s.nvp; k0 += G * vpt) { work.push_back(b); work.push_back(k0); work.push_back(G); }
-  }
+  std::vector<int> work = sweep_work(ctx, 0);
   std::vector<int> tiles;
   for (int b = 0; b < nblocks; ++b) {
     std::vector<int> org(2 * (size_t)tile_count(blocks[b].ni, blocks[b].nj));
@@ -870,12 +908,13 @@ int ugks_step(ugks_ctx *ctx, double dt, int n_inner) {
     { Prof p(ctx, UGKS_PROF_RHS); launch_flux_tile(d, s, fp); }                              // Step 3
     CK(cudaStreamWaitEvent(s, ctx->ev_macro, 0));
     { Prof p(ctx, UGKS_PROF_RESIDUAL); launch_residual(d, s, it == 0, fp); }                 // Step 5
-    { Prof p(ctx, UGKS_PROF_MICRO_FWD); launch_micro_fwd(d, s, ctx->work, ctx->nwork, ctx->sweep_threads, ctx->max_nj, ctx->nsm, fp); }  // Step 6
-    { Prof p(ctx, UGKS_PROF_MICRO_BWD); launch_micro_bwd(d, s, ctx->work, ctx->nwork, ctx->sweep_threads, ctx->max_nj, ctx->nsm, fp); }
+    { Prof p(ctx, UGKS_PROF_MICRO_FWD); launch_micro_fwd(d, s, ctx->work, ctx->nwork, ctx->sweep_threads, ctx->max_nj, ctx->nsm, ctx->sweep_ns, fp); }  // Step 6
+    { Prof p(ctx, UGKS_PROF_MICRO_BWD); launch_micro_bwd(d, s, ctx->work, ctx->nwork, ctx->sweep_threads, ctx->max_nj, ctx->nsm, ctx->sweep_ns, fp); }
     { Prof p(ctx, UGKS_PROF_MOMENTS); launch_moments(d, s, fp); }                          // Step 7
     ctx->launches += 8;
   }
   ctx->fresh_pending = false;
+  ctx->stepped = true;
   ctx->t = ctx->t_new;
   ctx->moved = false;
   return launch_status(ctx);
@@ -905,6 +944,51 @@ int ugks_advance_batch(ugks_ctx *const *ctx, int n, const double *t_new, const d
       }
     }
   return UGKS_OK;
+}
+
+int ugks_autotune(ugks_ctx *ctx, int reps, int *items_out, int *ring_out) {
+  if (!ctx || !ctx->mesh_ready) return UGKS_ERR_ORDER;
+  if (!ctx->stepped) return fail(ctx, UGKS_ERR_ORDER, "ugks_autotune needs a preceding ugks_step");
+  if (reps < 1) reps = 3;
+  Dev &d = ctx->d;
+  cudaStream_t s = ctx->st;
+  int fp = ctx->fp32;
+  size_t fbytes = (fp ? 8 : 16) * (size_t)d.nc * d.nvp;
+  // f is restored afterwards; the sweep buffer and the flux divergence are
+  // rewritten by every inner iteration, so the trials may use them
+  CK(cudaMemcpyAsync(d.Dbuf, d.f, fbytes, cudaMemcpyDeviceToDevice, s));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bi = ctx->sweep_items, bn = ctx->sweep_ns;
+  int r = UGKS_OK;
+  for (int items : kTuneItems) {
+    if ((r = set_sweep_tiles(ctx, items))) break;
+    for (int ns : kTuneRing) {
+      for (int rep = 0; rep <= reps; ++rep) {   // the first pass warms up
+        if (rep == 1) cudaEventRecord(e0, s);
+        launch_micro_fwd(d, s, ctx->work, ctx->nwork, ctx->sweep_threads, ctx->max_nj, ctx->nsm, ns, fp);
+        launch_micro_bwd(d, s, ctx->work, ctx->nwork, ctx->sweep_threads, ctx->max_nj, ctx->nsm, ns, fp);
+      }
+      cudaEventRecord(e1, s);
+      if ((r = cuda_check(ctx, cudaEventSynchronize(e1), "autotune"))) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ctx->launches += 2 * (reps + 1);
+      if (ms < best) { best = ms; bi = items; bn = ns; }
+    }
+    if (r) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (r) return r;
+  CK(cudaMemcpyAsync(d.f, d.Dbuf, fbytes, cudaMemcpyDeviceToDevice, s));
+  if ((r = set_sweep_tiles(ctx, bi))) return r;
+  ctx->sweep_ns = bn;
+  if (items_out) *items_out = bi;
+  if (ring_out) *ring_out = bn;
+  return launch_status(ctx);
 }
 
 int ugks_moments(ugks_ctx *ctx, double *W, double *q, int32_t *status, double *wall_loads) {

@@ -1569,12 +1569,12 @@ void sweep_setup() {
   cudaFuncSetAttribute(k_micro_sweep<double, 1, 2, VD>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
 }
 
-// Micro sweeps: the deepest ring (4, 3 or 2 diagonals) with which all the
-// sweep's CTAs are resident at once (nsm SMs), else the deepest that fits
-// one CTA per SM.
+// Micro sweeps: ring depth ns_req (2-4) when it fits, else the deepest ring
+// (4, 3 or 2 diagonals) with which all the sweep's CTAs are resident at once
+// (nsm SMs), else the deepest that fits one CTA per SM.
 template <typename T, int PASS>
 static void micro_sweep(const Dev &d, cudaStream_t s, const int *work, int nwork, int threads, int R,
-                        int nsm) {
+                        int nsm, int ns_req) {
   typedef typename Vec2<T>::type T2;
   constexpr int VPT = sweep_vpt<T>();
   size_t tb = VPT * sizeof(T2), rs = sweep_rec_stride<T>();
@@ -1590,24 +1590,22 @@ static void micro_sweep(const Dev &d, cudaStream_t s, const int *work, int nwork
     if (found) break;
   }
   const char *env = getenv("UGKS_SWEEP_NS");
-  if (env) {
-    int n = atoi(env);
-    if (n >= 2 && n <= 4 && base + n * stage <= kSweepSmem) ns = n;
-  }
+  int want = ns_req >= 2 ? ns_req : (env ? atoi(env) : 0);
+  if (want >= 2 && want <= 4 && base + want * stage <= kSweepSmem) ns = want;
   size_t sm = base + ns * stage;
   if (ns == 4) k_micro_sweep<T, PASS, 4, VPT><<<nwork, threads, sm, s>>>(d, work, R);
   else if (ns == 3) k_micro_sweep<T, PASS, 3, VPT><<<nwork, threads, sm, s>>>(d, work, R);
   else k_micro_sweep<T, PASS, 2, VPT><<<nwork, threads, sm, s>>>(d, work, R);
 }
 void launch_micro_fwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int threads, int rows,
-                      int nsm, int fp32) {
-  if (fp32) micro_sweep<float, 0>(d, s, work, nwork, threads, rows, nsm);
-  else micro_sweep<double, 0>(d, s, work, nwork, threads, rows, nsm);
+                      int nsm, int ns, int fp32) {
+  if (fp32) micro_sweep<float, 0>(d, s, work, nwork, threads, rows, nsm, ns);
+  else micro_sweep<double, 0>(d, s, work, nwork, threads, rows, nsm, ns);
 }
 void launch_micro_bwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int threads, int rows,
-                      int nsm, int fp32) {
-  if (fp32) micro_sweep<float, 1>(d, s, work, nwork, threads, rows, nsm);
-  else micro_sweep<double, 1>(d, s, work, nwork, threads, rows, nsm);
+                      int nsm, int ns, int fp32) {
+  if (fp32) micro_sweep<float, 1>(d, s, work, nwork, threads, rows, nsm, ns);
+  else micro_sweep<double, 1>(d, s, work, nwork, threads, rows, nsm, ns);
 }
 void launch_moments(const Dev &d, cudaStream_t s, int fp32) {
   if (fp32) k_moments<float><<<nblk((size_t)d.nc * 32, 256), 256, 0, s>>>(d);

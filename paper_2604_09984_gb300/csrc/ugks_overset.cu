@@ -254,7 +254,10 @@ __global__ void k_node_classify(Dev d) {
   if (n >= d.nn) return;
   int z = d.node_block[n];
   double x = d.X_new[2 * n], y = d.X_new[2 * n + 1];
-  double dz = wall_dist2(d, z, x, y);
+  // the node's own wall distance is needed only where another zone's core
+  // contains it (most background nodes lie in no other zone)
+  double dz = 0.0;
+  bool have_dz = false;
   bool inact = false;
   for (int b = 0; b < d.nblocks && !inact; ++b) {
     if (b == z) continue;
@@ -270,6 +273,10 @@ __global__ void k_node_classify(Dev d) {
       return !in_layer(bi, loc % ni, loc / ni, L);
     }) >= 0;
     if (hit) {
+      if (!have_dz) {
+        dz = wall_dist2(d, z, x, y);
+        have_dz = true;
+      }
       double db = wall_dist2(d, b, x, y);
       const int *bz = d.blk_info + 8 * z;
       if (db < dz || (db == dz && bi[3] > bz[3])) inact = true;

@@ -58,6 +58,7 @@ SYMBOLS = {
     "ugks_advance_batch": (c_int, [POINTER(c_void_p), c_int, POINTER(c_double), POINTER(POINTER(c_double)),
                                    c_int, POINTER(c_int)]),
     "ugks_moments": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ugks_autotune": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int)]),
     "ugks_sizes": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
     "ugks_get_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "ugks_set_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -222,6 +223,14 @@ class Solver:
         self.move_mesh(self.t + dt)
         self.overset_connect()
         self.step(dt, n_inner)
+
+    def autotune(self, reps=3):
+        """Pick the fastest micro-sweep tile and ring depth on this context's
+        own state (ugks_autotune); returns (items per CTA and diagonal, ring)."""
+        items, ring = c_int(), c_int()
+        self._check(self.lib.ugks_autotune(self.ctx, int(reps), ctypes.byref(items), ctypes.byref(ring)))
+        self.tiles = (items.value, ring.value)
+        return self.tiles
 
     def moments(self, W=None, q=None, status=None, wall=None):
         """Copy W, q, status and wall loads into the given buffers (numpy or

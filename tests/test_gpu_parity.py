@@ -274,3 +274,33 @@ def test_batch_matches_separate_runs(prec, tol):
         field = r.status == 0
         assert rel(Wb[field], r.state.W[field]) < tol
         assert rel(Wb, Ws) < (1e-13 if prec == U.FP64 else 1e-6)
+
+
+def test_autotune_restores_state_and_changes_no_result():
+    """The sweep autotuner times every candidate tile on the live state,
+    restores f bit for bit, and every tile computes the same sweeps: runs on
+    the tuned tile and on the smallest tile match the default one."""
+    case = small_mems()
+    prim = wl.random_prim(case, 21, amp_rho=0.05, amp_u=0.05, amp_T=0.05)
+    a = U.Solver(case, U.FP64, prim=prim)
+    b = U.Solver(case, U.FP64, prim=prim)
+    with pytest.raises(U.UgksError):
+        a.autotune(reps=1)                      # needs a step first
+    os.environ["UGKS_SWEEP_ITEMS"] = "256"
+    try:
+        c = U.Solver(case, U.FP64, prim=prim)
+    finally:
+        del os.environ["UGKS_SWEEP_ITEMS"]
+    for s in (a, b, c):
+        s.advance()
+    f0, _, _ = a.get_state()
+    items, ring = a.autotune(reps=1)
+    assert items in (256, 512, 1024, 2048) and ring in (2, 3, 4)
+    f1, _, _ = a.get_state()
+    assert torch.equal(f0, f1)
+    for _ in range(2):
+        for s in (a, b, c):
+            s.advance()
+    Wb = b.moments()[0]
+    assert rel(a.moments()[0], Wb) < 1e-13
+    assert rel(c.moments()[0], Wb) < 1e-13

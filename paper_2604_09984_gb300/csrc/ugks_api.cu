@@ -41,7 +41,8 @@ struct ugks_ctx {
   std::string err;
   int64_t launches = 0;
   std::vector<double> h_affine;
-  bool fresh_pending = false;         // cells uncovered by the last assembly await their first values
+  bool fresh_pending = false;
+  std::vector<int> h_wall_faces;      // staging of the wall-face list upload         // cells uncovered by the last assembly await their first values
   std::vector<double> ref_bbox, h_bin_geo;   // per block reference bbox; bin boxes
   std::vector<int> h_bin_dim;
   // per-kernel-group CUDA-event timing (ugks_profile_*)
@@ -232,6 +233,7 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int nwork, int cap_in
   d.fflux = c.take<double>(4 * (size_t)s.nf);
   d.gam = c.take<double>(s.nf);
   d.wall_loads = c.take<double>(4 * (size_t)nb);
+  d.wall_faces = c.take<int>(s.nf);
   d.node_active = c.take<int>(s.nn);
   d.cls = c.take<int>(s.nc);
   d.donors = c.take<int>(5 * (size_t)s.nc);
@@ -796,6 +798,14 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
   if ((r = up(ctx, (void *)d.face_a, T.face_a))) return r;
   if ((r = up(ctx, (void *)d.face_b, T.face_b))) return r;
   if ((r = up(ctx, (void *)d.face_kind, T.face_kind))) return r;
+  {
+    std::vector<int> wf;
+    for (int f = 0; f < s.nf; ++f)
+      if (T.face_kind[f] == BC_WALL) wf.push_back(f);
+    d.nwall = (int)wf.size();
+    ctx->h_wall_faces = wf;
+    if ((r = up(ctx, (void *)d.wall_faces, ctx->h_wall_faces))) return r;
+  }
   if ((r = up(ctx, (void *)d.face_block, T.face_block))) return r;
   if ((r = up(ctx, (void *)d.face_shiftL, T.face_shiftL))) return r;
   if ((r = up(ctx, (void *)d.face_Tw, T.face_Tw))) return r;

@@ -93,6 +93,8 @@ struct Dev {
   double *fflux;             // nf*4 S * macro flux (L -> R / outward)
   double *gam;               // nf spectral radius Gamma
   double *wall_loads;        // nblocks*4
+  int *wall_faces;           // ids of the wall faces, ascending
+  int nwall;
   // overset
   int *node_active;          // nn
   int *cls;                  // nc scratch classification

@@ -522,27 +522,29 @@ template <int D> __device__ __forceinline__ float p2_sum(const Poly2<D> &x, cons
 // rounding) sum_ab coef_ab Mx_a My_b with the 1D moments
 // Mx_a = sum_ix wx cx^a Ex(cx), My_b likewise: O(nvx + nvy) work per face
 // instead of O(nvx nvy).  One warp per face; out (all lanes): 4 sums.
+template <int GS>
 __device__ __forceinline__ void face_eq_flux_separable(const Dev &d, const float *P, float snx, float sny,
                                                        float sun, int lane, float out[4]) {
   float ux = P[FP_UX], uy = P[FP_UY], lam = P[FP_LAM];
-  // 1D moments: lane = grid index, a = 0..6 (x) and b = 0..6 (y)
+  // 1D moments: lane of the face's GS-lane group = grid index, a = 0..6 (x)
+  // and b = 0..6 (y); every lane of the warp takes part in the shuffles
   float mx[7], my[7];
 #pragma unroll
   for (int a = 0; a < 7; ++a) { mx[a] = 0.f; my[a] = 0.f; }
-  for (int ix = lane; ix < d.nvx; ix += 32) {
+  for (int ix = lane; ix < d.nvx; ix += GS) {
     float cx = d.vxf[ix] - ux;
     float e = d.wx1f[ix] * __expf(-lam * cx * cx), p = e;
 #pragma unroll
     for (int a = 0; a < 7; ++a) { mx[a] += p; p *= cx; }
   }
-  for (int iy = lane; iy < d.nvy; iy += 32) {
+  for (int iy = lane; iy < d.nvy; iy += GS) {
     float cy = d.vyf[iy * d.nvx] - uy;
     float e = d.wy1f[iy] * __expf(-lam * cy * cy), p = e;
 #pragma unroll
     for (int a = 0; a < 7; ++a) { my[a] += p; p *= cy; }
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
+  for (int o = GS / 2; o > 0; o >>= 1)
 #pragma unroll
     for (int a = 0; a < 7; ++a) {
       mx[a] += __shfl_xor_sync(0xffffffffu, mx[a], o);
@@ -597,10 +599,13 @@ __device__ __forceinline__ void face_eq_flux_separable(const Dev &d, const float
   out[3] = hpre * p2_sum(p2_mul(ws, e3), mx, my);
 }
 
-template <typename T> __global__ void __launch_bounds__(256, 2) k_face_coef(Dev d) {
-  int fid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// Velocity-loop face coefficients: one warp per face of `list` (all faces
+// when null).  The FP32 path runs it over the wall faces only.
+template <typename T> __global__ void __launch_bounds__(256, 2) k_face_coef(Dev d, const int *list, int n) {
+  int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
-  if (fid >= d.nf) return;
+  if (w >= n) return;
+  int fid = list ? list[w] : w;
   int kind = d.face_kind[fid];
   if (!face_needed(d, fid) || kind == BC_OVERSET) {
     if (lane < 4) d.fflux[4 * fid + lane] = 0.0;
@@ -619,16 +624,6 @@ template <typename T> __global__ void __launch_bounds__(256, 2) k_face_coef(Dev 
   else { snx = (T)d.Sn[2 * fid]; sny = (T)d.Sn[2 * fid + 1]; sun = (T)d.SUn[fid]; }
   T tufx = parT[FP_UFX], tufy = parT[FP_UFY], tlamw = parT[FP_LAMW], tK = (T)d.Keff;
   V2<T> zero = {T(0), T(0)};
-  if (sizeof(T) == 4 && !wall) {
-    float o[4];
-    face_eq_flux_separable(d, reinterpret_cast<const float *>(parT), (float)snx, (float)sny, (float)sun,
-                           lane, o);
-    if (lane < 4) {                       // lane m: component m
-      float om = lane == 0 ? o[0] : lane == 1 ? o[1] : lane == 2 ? o[2] : o[3];
-      d.fflux[4 * fid + lane] = P[FP_Q1] * fs[FS_FF + lane] + P[FP_Q2] * fs[FS_WG + lane] + f2d_bits(om);
-    }
-    return;
-  }
   for (int k = lane; k < d.nv; k += 32) {
     T vx = dvx<T>(d, k), vy = dvy<T>(d, k), w = dw<T>(d, k);
     T wS = vx * snx + vy * sny - sun;
@@ -661,6 +656,40 @@ template <typename T> __global__ void __launch_bounds__(256, 2) k_face_coef(Dev 
       for (int m = 0; m < 4; ++m) F[m] += rhow * rs[m];
     }
     for (int m = 0; m < 4; ++m) d.fflux[4 * fid + m] = F[m];
+  }
+}
+
+// FP32 face coefficients of the non-wall faces: FCG lanes per face, the
+// equilibrium part of the macro flux from 1D velocity moments (exact
+// separable rewrite of the tensor-grid sum); faces outside the field get
+// zero flux.
+constexpr int FCG = 8;
+__global__ void __launch_bounds__(256) k_face_coef_sep(Dev d) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int fid = t / FCG, sub = t % FCG;
+  bool in = fid < d.nf;
+  int kind = in ? d.face_kind[fid] : BC_OVERSET;
+  bool need = in && kind != BC_OVERSET && face_needed(d, fid);
+  if (in && !need) {
+    if (sub < 4) d.fflux[4 * fid + sub] = 0.0;
+    if (sub == 0) d.gam[fid] = 0.0;
+  }
+  bool act = need && kind != BC_WALL;
+  if (!__any_sync(0xffffffffu, act)) return;      // warp-uniform
+  __align__(16) float parT[NFP];
+  if (act) {
+    load_rec<float, NFP>(reinterpret_cast<const float *>(d.fparT) + (size_t)NFP * fid, parT);
+  } else {
+#pragma unroll
+    for (int q = 0; q < NFP; ++q) parT[q] = 0.f;
+  }
+  float o[4];
+  face_eq_flux_separable<FCG>(d, parT, parT[FP_SNX], parT[FP_SNY], parT[FP_SUN], sub, o);
+  if (act && sub < 4) {                           // lane m of the group: component m
+    const double *P = d.fpar + (size_t)NFP * fid;
+    const double *fs = d.fsum + NFS * fid;
+    float om = sub == 0 ? o[0] : sub == 1 ? o[1] : sub == 2 ? o[2] : o[3];
+    d.fflux[4 * fid + sub] = P[FP_Q1] * fs[FS_FF + sub] + P[FP_Q2] * fs[FS_WG + sub] + f2d_bits(om);
   }
 }
 
@@ -1490,10 +1519,11 @@ void launch_ghost_gradW(const Dev &d, cudaStream_t s) {
 void launch_face_coef(const Dev &d, cudaStream_t s, int fp32) {
   if (fp32) {
     k_face_scalar<float><<<nblk(d.nf, 128), 128, 0, s>>>(d);
-    k_face_coef<float><<<nblk((size_t)d.nf * 32, 256), 256, 0, s>>>(d);
+    k_face_coef_sep<<<nblk((size_t)d.nf * FCG, 256), 256, 0, s>>>(d);
+    if (d.nwall > 0) k_face_coef<float><<<nblk((size_t)d.nwall * 32, 256), 256, 0, s>>>(d, d.wall_faces, d.nwall);
   } else {
     k_face_scalar<double><<<nblk(d.nf, 128), 128, 0, s>>>(d);
-    k_face_coef<double><<<nblk((size_t)d.nf * 32, 256), 256, 0, s>>>(d);
+    k_face_coef<double><<<nblk((size_t)d.nf * 32, 256), 256, 0, s>>>(d, nullptr, d.nf);
   }
 }
 void launch_cell_macro(const Dev &d, cudaStream_t s, int level_n) {

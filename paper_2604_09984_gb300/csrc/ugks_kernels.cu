@@ -1348,25 +1348,29 @@ template <typename T> __global__ void k_moments(Dev d) {
       int k = kb + 32 * u;
       fb[u] = k < d.nv ? ldf<T>(d.f, (size_t)c * d.nvp + k) : T2{T(0), T(0)};
     }
+    // the batch's terms are summed plainly, the batch sums compensated
+    T p[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
 #pragma unroll
     for (int u = 0; u < NB; ++u) {
-    int k = kb + 32 * u;
-    if (k >= d.nv) break;
-    T2 fv = fb[u];
-    T vx = dvx<T>(d, k), vy = dvy<T>(d, k), w = dw<T>(d, k);
-    V2<T> g = maxwellian_pre<T>(hpre, ux, uy, lam, bfac, vx, vy);
-    T h = fv.x, b = fv.y;
-    T dh = h - g.h, db = b - g.b;
-    T v2 = T(0.5) * (vx * vx + vy * vy);
-    a[0].add(w * dh);
-    a[1].add(w * vx * dh);
-    a[2].add(w * vy * dh);
-    a[3].add(w * (v2 * dh + T(0.5) * db));
-    T cx = vx - ux, cy = vy - uy;
-    T e = (cx * cx + cy * cy) * h + b;
-    a[4].add(T(0.5) * w * cx * e);
-    a[5].add(T(0.5) * w * cy * e);
+      int k = kb + 32 * u;
+      if (k >= d.nv) break;
+      T2 fv = fb[u];
+      T vx = dvx<T>(d, k), vy = dvy<T>(d, k), w = dw<T>(d, k);
+      V2<T> g = maxwellian_pre<T>(hpre, ux, uy, lam, bfac, vx, vy);
+      T h = fv.x, b = fv.y;
+      T dh = h - g.h, db = b - g.b;
+      T v2 = T(0.5) * (vx * vx + vy * vy);
+      p[0] += w * dh;
+      p[1] += w * vx * dh;
+      p[2] += w * vy * dh;
+      p[3] += w * (v2 * dh + T(0.5) * db);
+      T cx = vx - ux, cy = vy - uy;
+      T e = (cx * cx + cy * cy) * h + b;
+      p[4] += T(0.5) * w * cx * e;
+      p[5] += T(0.5) * w * cy * e;
     }
+#pragma unroll
+    for (int m = 0; m < 6; ++m) a[m].add(p[m]);
   }
   // lane m < 6 stores component m (W' + sum for W, the sum for q); lane 0
   // then checks the new state for rho > 0 and a positive internal energy

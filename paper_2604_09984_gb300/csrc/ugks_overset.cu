@@ -446,16 +446,18 @@ template <typename T> __global__ void k_interp_gather(Dev d, const int *list, co
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (size_t)gridDim.x * blockDim.x) {
     int r = (int)(t / d.nvp), k = (int)(t % d.nvp);
     int c = list[r];
-    double ah = 0.0, ab = 0.0;
+    // f in the arithmetic type (its storage type): FP32 weights and sums on
+    // the mixed path keep the FP64 pipe out of the per-velocity loop
+    T ah = T(0), ab = T(0);
     for (int m = 0; m < 5; ++m) {
       int e = d.donors[5 * c + m];
       if (e < 0) continue;
-      double w = d.dwgt[5 * c + m];
+      T w = (T)d.dwgt[5 * c + m];
       auto v = ldf<T>(d.f, (size_t)e * d.nvp + k);
-      ah = ah + w * (double)v.x;
-      ab = ab + w * (double)v.y;
+      ah = ah + w * v.x;
+      ab = ab + w * v.y;
     }
-    stf<T>(d.itmp, t, (T)ah, (T)ab);
+    stf<T>(d.itmp, t, ah, ab);
     if (k == 0) {
       double acc[6] = {0, 0, 0, 0, 0, 0};
       for (int m = 0; m < 5; ++m) {

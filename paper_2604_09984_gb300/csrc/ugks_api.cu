@@ -246,6 +246,8 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int nwork, int cap_in
   d.itmpW = c.take<double>(6 * (size_t)cap_interp);
   d.cap_interp = cap_interp;
   d.wall_seg = c.take<int>(2 * (size_t)s.nseg + 2);
+  d.segf = c.take<float4>((size_t)s.nseg + 1);
+  d.nseg = s.nseg;
   d.wall_seg_off = c.take<int>(nb + 1);
   d.body_ring = c.take<int>((size_t)s.nring + 1);
   d.body_ring_off = c.take<int>(nb + 1);

@@ -108,6 +108,8 @@ struct Dev {
   void *itmp;                // interpolation staging: cap_interp*nvp pairs
   double *itmpW;             // ... *6 doubles
   int *wall_seg;             // segments: node id pairs, grouped per block
+  float4 *segf;              // float endpoints of each wall segment (assembly filters)
+  int nseg;
   int *wall_seg_off;         // nblocks+1
   int *body_ring;            // body polygon node ids, grouped per block
   int *body_ring_off;        // nblocks+1

@@ -55,7 +55,9 @@ __device__ __forceinline__ double seg_dist2(const Dev &d, int s, double x, doubl
 // scaled down) does not exceed that bound are evaluated exactly.  The
 // skipped ones are farther than the minimum, so the result is the exact
 // minimum over all segments.
-__device__ double wall_dist2(const Dev &d, int blk, double x, double y) {
+// `seg` holds the float endpoints (A.x, A.y, B.x, B.y) of every segment
+// (shared memory, or the global copy when they do not fit there).
+__device__ double wall_dist2(const Dev &d, const float4 *seg, int blk, double x, double y) {
   double best = __longlong_as_double(0x7ff0000000000000LL);   // +inf
   int s0 = d.wall_seg_off[blk], s1 = d.wall_seg_off[blk + 1];
   if (s1 <= s0) return best;
@@ -63,7 +65,8 @@ __device__ double wall_dist2(const Dev &d, int blk, double x, double y) {
   int sg = s0;
   float gbest = __int_as_float(0x7f800000);
   for (int s = s0; s < s1; ++s) {
-    float2 A = d.Xf[d.wall_seg[2 * s]], B = d.Xf[d.wall_seg[2 * s + 1]];
+    float4 AB = seg[s];
+    float2 A = make_float2(AB.x, AB.y), B = make_float2(AB.z, AB.w);
     float ex = B.x - A.x, ey = B.y - A.y, px = xf - A.x, py = yf - A.y;
     float ee = ex * ex + ey * ey;
     float t = ee > 0.f ? fminf(fmaxf((px * ex + py * ey) / ee, 0.f), 1.f) : 0.f;
@@ -74,7 +77,8 @@ __device__ double wall_dist2(const Dev &d, int blk, double x, double y) {
   float bestf = __double2float_ru(best);
   for (int s = s0; s < s1; ++s) {
     if (s == sg) continue;
-    float2 A = d.Xf[d.wall_seg[2 * s]], B = d.Xf[d.wall_seg[2 * s + 1]];
+    float4 AB = seg[s];
+    float2 A = make_float2(AB.x, AB.y), B = make_float2(AB.z, AB.w);
     float lx = fminf(A.x, B.x), hx = fmaxf(A.x, B.x), ly = fminf(A.y, B.y), hy = fmaxf(A.y, B.y);
     float tol = 2.4e-7f * (fabsf(xf) + fabsf(yf) + fabsf(lx) + fabsf(hx) + fabsf(ly) + fabsf(hy));
     float gx = fmaxf(fmaxf(lx - xf, xf - hx) - tol, 0.f);
@@ -158,8 +162,13 @@ __device__ __forceinline__ int bin_of(const Dev &d, int b, double x, double y) {
 
 __global__ void k_node_f(Dev d) {
   int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= d.nn) return;
-  d.Xf[n] = make_float2(__double2float_rn(d.X_new[2 * n]), __double2float_rn(d.X_new[2 * n + 1]));
+  if (n < d.nn)
+    d.Xf[n] = make_float2(__double2float_rn(d.X_new[2 * n]), __double2float_rn(d.X_new[2 * n + 1]));
+  if (n < d.nseg) {      // float endpoints of wall segment n, one record each
+    int a = d.wall_seg[2 * n], b = d.wall_seg[2 * n + 1];
+    d.segf[n] = make_float4(__double2float_rn(d.X_new[2 * a]), __double2float_rn(d.X_new[2 * a + 1]),
+                            __double2float_rn(d.X_new[2 * b]), __double2float_rn(d.X_new[2 * b + 1]));
+  }
 }
 
 __global__ void k_bin_count(Dev d) {
@@ -248,8 +257,15 @@ __device__ int first_containing(const Dev &d, int b, double x, double y, Pred ok
   return best == 0x7fffffff ? -1 : best;
 }
 
-// node classification (one thread per node)
-__global__ void k_node_classify(Dev d) {
+// node classification (one thread per node); the wall segments' float
+// records are staged in shared memory when they fit (STAGE)
+template <bool STAGE> __global__ void k_node_classify(Dev d) {
+  extern __shared__ float4 seg_s[];
+  if (STAGE) {
+    for (int q = threadIdx.x; q < d.nseg; q += blockDim.x) seg_s[q] = d.segf[q];
+    __syncthreads();
+  }
+  const float4 *seg = STAGE ? seg_s : d.segf;
   int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= d.nn) return;
   int z = d.node_block[n];
@@ -274,10 +290,10 @@ __global__ void k_node_classify(Dev d) {
     }) >= 0;
     if (hit) {
       if (!have_dz) {
-        dz = wall_dist2(d, z, x, y);
+        dz = wall_dist2(d, seg, z, x, y);
         have_dz = true;
       }
-      double db = wall_dist2(d, b, x, y);
+      double db = wall_dist2(d, seg, b, x, y);
       const int *bz = d.blk_info + 8 * z;
       if (db < dz || (db == dz && bi[3] > bz[3])) inact = true;
     }
@@ -495,11 +511,13 @@ static inline int nblk(size_t n, int b) { return (int)((n + b - 1) / b); }
 void launch_connect(const Dev &d, cudaStream_t s, int *prev_status, const int *blk_order,
                     int *n_orphan) {
   cudaMemsetAsync(d.bin_cnt, 0, sizeof(int) * d.nbins, s);
-  k_node_f<<<nblk(d.nn, 256), 256, 0, s>>>(d);
+  k_node_f<<<nblk(d.nn > d.nseg ? d.nn : d.nseg, 256), 256, 0, s>>>(d);
   k_bin_count<<<nblk(d.nc, 256), 256, 0, s>>>(d);
   k_bin_scan<<<1, 1024, 0, s>>>(d);
   k_bin_fill<<<nblk(d.nc, 256), 256, 0, s>>>(d);
-  k_node_classify<<<nblk(d.nn, 128), 128, 0, s>>>(d);
+  size_t segb = sizeof(float4) * (size_t)d.nseg;
+  if (segb <= 48 * 1024) k_node_classify<true><<<nblk(d.nn, 128), 128, segb, s>>>(d);
+  else k_node_classify<false><<<nblk(d.nn, 128), 128, 0, s>>>(d);
   k_cell_classify<<<nblk(d.nc, 256), 256, 0, s>>>(d);
   k_cell_buffer<<<nblk(d.nc, 256), 256, 0, s>>>(d, prev_status);
   k_donor<<<nblk(d.nc, 128), 128, 0, s>>>(d, prev_status, blk_order, n_orphan);

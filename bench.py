@@ -370,6 +370,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-plain comparison arm")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default sweep tile (for profiler runs, where the tuner's timings are distorted)")
     args = ap.parse_args()
     if args.workload == "mems_batch":
         # one hardware work queue per instance stream (read when CUDA starts)
@@ -409,7 +411,8 @@ def main():
         dist.barrier()
     clk = Clocks(local)
     clk.start()
-    s, ms, nfield, launches, prof = time_arm(case, U.FP32, steps, warmup, device, profile=True)
+    s, ms, nfield, launches, prof = time_arm(case, U.FP32, steps, warmup, device, profile=True,
+                                             tune=not args.no_tune)
     clocks = clk.stop()
     if dist is not None:
         t = torch.tensor([ms], device=device)
@@ -448,7 +451,8 @@ def main():
     torch.cuda.empty_cache()
     fp64 = None
     if not args.no_fp64:
-        s64, ms64, nf64, _, _ = time_arm(case, U.FP64, max(1, args.fp64_steps), 3, device, profile=False)
+        s64, ms64, nf64, _, _ = time_arm(case, U.FP64, max(1, args.fp64_steps), 3, device, profile=False,
+                                         tune=not args.no_tune)
         v64 = nf64 * case.nv * case.n_inner * max(1, args.fp64_steps) / (ms64 * 1e-3)
         fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / max(1, args.fp64_steps),
                 "speedup_fp32_over_fp64": value / world / v64}
@@ -460,7 +464,8 @@ def main():
         "config": {"workload": workload_label(case), "precision": "FP32 f and per-velocity arithmetic, FP64 moments/geometry",
                    "l2": "inputs larger than L2 (f alone %.0f MB)" % (s_bytes(case) / 1e6),
                    "field_cells": nfield, "nv": case.nv, "n_inner": case.n_inner,
-                   "sweep_tiles": "autotuned (items per CTA and diagonal, ring): %s" % (tiles,),
+                   "sweep_tiles": ("autotuned (items per CTA and diagonal, ring): %s" % (tiles,)) if tiles
+                   else "default (1024 items per CTA and diagonal, ring by rule)",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "per_physical_step": value / case.n_inner,
         "clocks": clocks,

@@ -251,6 +251,7 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int nwork, int cap_in
   d.wall_seg_off = c.take<int>(nb + 1);
   d.body_ring = c.take<int>((size_t)s.nring + 1);
   d.body_ring_off = c.take<int>(nb + 1);
+  d.body_bb = c.take<float4>(nb);
   d.cell_off = c.take<int>(nb + 1);
   d.node_off = c.take<int>(nb + 1);
   d.blk_info = c.take<int>(8 * (size_t)nb);
@@ -587,7 +588,7 @@ int do_connect(ugks_ctx *ctx, ugks_connect_stats *stats, bool initial, bool sync
     launch_lists(d, ctx->st, ctx->prev_status, ctx->n_orphan);
   }
   launch_slope_geo(d, ctx->st);     // holes changed
-  ctx->launches += 10;
+  ctx->launches += 12;
   ctx->fresh_pending = !initial;
   int r = launch_status(ctx);
   if (r || !sync) return r;

@@ -113,6 +113,7 @@ struct Dev {
   int *wall_seg_off;         // nblocks+1
   int *body_ring;            // body polygon node ids, grouped per block
   int *body_ring_off;        // nblocks+1
+  float4 *body_bb;           // nblocks: outward-rounded float box of the body polygon
   const int *cell_off;       // nblocks+1 (device copy)
   const int *node_off;       // nblocks+1
   const int *blk_info;       // nblocks*8: ni, nj, periodic, priority, n_fringe, n_gap, bc-overset mask, body?

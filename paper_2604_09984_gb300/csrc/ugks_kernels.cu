@@ -599,61 +599,77 @@ __device__ __forceinline__ void face_eq_flux_separable(const Dev &d, const float
   out[3] = hpre * p2_sum(p2_mul(ws, e3), mx, my);
 }
 
-// Velocity-loop face coefficients: one warp per face of `list` (all faces
-// when null).  The FP32 path runs it over the wall faces only.
+// Velocity-loop face coefficients for the faces of `list` (all faces when
+// null): FCW warps per face split the velocities, their warp totals meet in
+// shared memory (summed in warp order).  The FP32 path runs it over the wall
+// faces only.
+constexpr int FCW = 4;
 template <typename T> __global__ void __launch_bounds__(256, 2) k_face_coef(Dev d, const int *list, int n) {
-  int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (w >= n) return;
-  int fid = list ? list[w] : w;
-  int kind = d.face_kind[fid];
-  if (!face_needed(d, fid) || kind == BC_OVERSET) {
+  __shared__ double part[256 / 32][9];
+  int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int w = wg / FCW, sub = wg - (wg / FCW) * FCW;
+  int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  bool in = w < n;
+  int fid = in ? (list ? list[w] : w) : 0;
+  int kind = in ? d.face_kind[fid] : BC_OVERSET;
+  bool act = in && kind != BC_OVERSET && face_needed(d, fid);
+  if (in && !act && sub == 0) {
     if (lane < 4) d.fflux[4 * fid + lane] = 0.0;
     if (lane == 0) d.gam[fid] = 0.0;
-    return;
   }
   bool wall = kind == BC_WALL;
-  double *P = d.fpar + (size_t)NFP * fid;
-  T *PT = reinterpret_cast<T *>(d.fparT) + (size_t)NFP * fid;
-  const double *fs = d.fsum + NFS * fid;
-  __align__(16) T parT[NFP];
-  load_rec<T, NFP>(PT, parT);
   Acc<T> ags[4], ars[4], aden;
-  T snx, sny, sun;
-  if (sizeof(T) == 4) { snx = parT[FP_SNX]; sny = parT[FP_SNY]; sun = parT[FP_SUN]; }
-  else { snx = (T)d.Sn[2 * fid]; sny = (T)d.Sn[2 * fid + 1]; sun = (T)d.SUn[fid]; }
-  T tufx = parT[FP_UFX], tufy = parT[FP_UFY], tlamw = parT[FP_LAMW], tK = (T)d.Keff;
-  V2<T> zero = {T(0), T(0)};
-  for (int k = lane; k < d.nv; k += 32) {
-    T vx = dvx<T>(d, k), vy = dvy<T>(d, k), w = dw<T>(d, k);
-    T wS = vx * snx + vy * sny - sun;
-    T v2 = T(0.5) * (vx * vx + vy * vy);
-    T cw = w * wS;
-    if (!wall || wS > T(0)) {
-      V2<T> I = interface_integral<T>(parT, vx, vy, zero, zero, tK, (T)d.Kint, (T)d.Pr);
-      ags[0].add(cw * I.h); ags[1].add(cw * vx * I.h); ags[2].add(cw * vy * I.h);
-      ags[3].add(cw * (v2 * I.h + T(0.5) * I.b));
-    } else {
-      T cx = vx - tufx, cy = vy - tufy;
-      T Hw = (tlamw * T(M_1_PI)) * r_exp<T>(-tlamw * (cx * cx + cy * cy));
-      T Bw = tK / (T(2) * tlamw) * Hw;
-      aden.add(cw * Hw);
-      ars[0].add(cw * Hw); ars[1].add(cw * vx * Hw); ars[2].add(cw * vy * Hw);
-      ars[3].add(cw * (v2 * Hw + T(0.5) * Bw));
+  if (act) {
+    T *PT = reinterpret_cast<T *>(d.fparT) + (size_t)NFP * fid;
+    __align__(16) T parT[NFP];
+    load_rec<T, NFP>(PT, parT);
+    T snx, sny, sun;
+    if (sizeof(T) == 4) { snx = parT[FP_SNX]; sny = parT[FP_SNY]; sun = parT[FP_SUN]; }
+    else { snx = (T)d.Sn[2 * fid]; sny = (T)d.Sn[2 * fid + 1]; sun = (T)d.SUn[fid]; }
+    T tufx = parT[FP_UFX], tufy = parT[FP_UFY], tlamw = parT[FP_LAMW], tK = (T)d.Keff;
+    V2<T> zero = {T(0), T(0)};
+    for (int k = sub * 32 + lane; k < d.nv; k += 32 * FCW) {
+      T vx = dvx<T>(d, k), vy = dvy<T>(d, k), w = dw<T>(d, k);
+      T wS = vx * snx + vy * sny - sun;
+      T v2 = T(0.5) * (vx * vx + vy * vy);
+      T cw = w * wS;
+      if (!wall || wS > T(0)) {
+        V2<T> I = interface_integral<T>(parT, vx, vy, zero, zero, tK, (T)d.Kint, (T)d.Pr);
+        ags[0].add(cw * I.h); ags[1].add(cw * vx * I.h); ags[2].add(cw * vy * I.h);
+        ags[3].add(cw * (v2 * I.h + T(0.5) * I.b));
+      } else {
+        T cx = vx - tufx, cy = vy - tufy;
+        T Hw = (tlamw * T(M_1_PI)) * r_exp<T>(-tlamw * (cx * cx + cy * cy));
+        T Bw = tK / (T(2) * tlamw) * Hw;
+        aden.add(cw * Hw);
+        ars[0].add(cw * Hw); ars[1].add(cw * vx * Hw); ars[2].add(cw * vy * Hw);
+        ars[3].add(cw * (v2 * Hw + T(0.5) * Bw));
+      }
     }
   }
-  double gs[4], rs[4];
-  for (int m = 0; m < 4; ++m) { gs[m] = to_double(warp_total(ags[m])); rs[m] = to_double(warp_total(ars[m])); }
-  double den = to_double(warp_total(aden));
-  if (lane == 0) {
+  double tot[9];
+  for (int m = 0; m < 4; ++m) { tot[m] = to_double(warp_total(ags[m])); tot[4 + m] = to_double(warp_total(ars[m])); }
+  tot[8] = to_double(warp_total(aden));
+  if (lane == 0)
+    for (int m = 0; m < 9; ++m) part[wl][m] = tot[m];
+  __syncthreads();
+  if (act && sub == 0 && lane == 0) {
+    double acc[9];
+    for (int m = 0; m < 9; ++m) {
+      acc[m] = part[wl][m];
+      for (int j = 1; j < FCW; ++j) acc[m] += part[wl + j][m];
+    }
+    double *P = d.fpar + (size_t)NFP * fid;
+    T *PT = reinterpret_cast<T *>(d.fparT) + (size_t)NFP * fid;
+    const double *fs = d.fsum + NFS * fid;
     double F[4];
     for (int m = 0; m < 4; ++m)
-      F[m] = P[FP_Q1] * fs[FS_FF + m] + P[FP_Q2] * fs[FS_WG + m] + gs[m];
+      F[m] = P[FP_Q1] * fs[FS_FF + m] + P[FP_Q2] * fs[FS_WG + m] + acc[m];
     if (wall) {
-      double rhow = -F[0] / den;
+      double rhow = -F[0] / acc[8];
       P[FP_RHOW] = rhow;
       PT[FP_RHOW] = (T)rhow;
-      for (int m = 0; m < 4; ++m) F[m] += rhow * rs[m];
+      for (int m = 0; m < 4; ++m) F[m] += rhow * acc[4 + m];
     }
     for (int m = 0; m < 4; ++m) d.fflux[4 * fid + m] = F[m];
   }
@@ -1524,10 +1540,11 @@ void launch_face_coef(const Dev &d, cudaStream_t s, int fp32) {
   if (fp32) {
     k_face_scalar<float><<<nblk(d.nf, 128), 128, 0, s>>>(d);
     k_face_coef_sep<<<nblk((size_t)d.nf * FCG, 256), 256, 0, s>>>(d);
-    if (d.nwall > 0) k_face_coef<float><<<nblk((size_t)d.nwall * 32, 256), 256, 0, s>>>(d, d.wall_faces, d.nwall);
+    if (d.nwall > 0)
+      k_face_coef<float><<<nblk((size_t)d.nwall * 32 * FCW, 256), 256, 0, s>>>(d, d.wall_faces, d.nwall);
   } else {
     k_face_scalar<double><<<nblk(d.nf, 128), 128, 0, s>>>(d);
-    k_face_coef<double><<<nblk((size_t)d.nf * 32, 256), 256, 0, s>>>(d, nullptr, d.nf);
+    k_face_coef<double><<<nblk((size_t)d.nf * 32 * FCW, 256), 256, 0, s>>>(d, nullptr, d.nf);
   }
 }
 void launch_cell_macro(const Dev &d, cudaStream_t s, int level_n) {

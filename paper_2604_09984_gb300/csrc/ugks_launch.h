@@ -24,7 +24,7 @@ void launch_flux_div_all(const Dev &d, cudaStream_t s, double *D, int fp32);
 void launch_wall_loads(const Dev &d, cudaStream_t s);
 void launch_f_convert(const Dev &d, cudaStream_t s, double *out, const double *in, int fp32);
 void launch_connect(const Dev &d, cudaStream_t s, int *prev_status, const int *blk_order,
-                    int *n_orphan);                           // 7 kernels
+                    int *n_orphan);                           // 9 kernels
 void launch_lists(const Dev &d, cudaStream_t s, const int *fresh_flag, const int *n_orphan);  // 2 kernels
 void launch_interp(const Dev &d, cudaStream_t s, const int *list, const int *cnt, int nsm, int fp32);  // 2 kernels
 // tiled kernels (ugks_tile.cu)

@@ -104,7 +104,31 @@ __device__ bool inside_quad(const Dev &d, int c, double x, double y) {
   return true;
 }
 
+// Float box of each block's body polygon, rounded outward (one warp per
+// block): a point outside it is outside the polygon.
+__global__ void k_body_box(Dev d) {
+  int b = blockIdx.x, lane = threadIdx.x;
+  int r0 = d.body_ring_off[b], r1 = d.body_ring_off[b + 1];
+  double xl = 1e300, xh = -1e300, yl = 1e300, yh = -1e300;
+  for (int i = r0 + lane; i < r1; i += 32) {
+    int a = d.body_ring[i];
+    double x = d.X_new[2 * a], y = d.X_new[2 * a + 1];
+    xl = fmin(xl, x); xh = fmax(xh, x); yl = fmin(yl, y); yh = fmax(yh, y);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    xl = fmin(xl, __shfl_xor_sync(0xffffffffu, xl, o));
+    xh = fmax(xh, __shfl_xor_sync(0xffffffffu, xh, o));
+    yl = fmin(yl, __shfl_xor_sync(0xffffffffu, yl, o));
+    yh = fmax(yh, __shfl_xor_sync(0xffffffffu, yh, o));
+  }
+  if (lane == 0)
+    d.body_bb[b] = make_float4(__double2float_rd(xl), __double2float_rd(yl), __double2float_ru(xh),
+                               __double2float_ru(yh));
+}
+
 __device__ bool inside_body(const Dev &d, int blk, double x, double y) {
+  float4 bb = d.body_bb[blk];
+  if (x < (double)bb.x || x > (double)bb.z || y < (double)bb.y || y > (double)bb.w) return false;
   int r0 = d.body_ring_off[blk], r1 = d.body_ring_off[blk + 1];
   int M = r1 - r0;
   bool in = false;
@@ -512,6 +536,7 @@ void launch_connect(const Dev &d, cudaStream_t s, int *prev_status, const int *b
                     int *n_orphan) {
   cudaMemsetAsync(d.bin_cnt, 0, sizeof(int) * d.nbins, s);
   k_node_f<<<nblk(d.nn > d.nseg ? d.nn : d.nseg, 256), 256, 0, s>>>(d);
+  k_body_box<<<d.nblocks, 32, 0, s>>>(d);
   k_bin_count<<<nblk(d.nc, 256), 256, 0, s>>>(d);
   k_bin_scan<<<1, 1024, 0, s>>>(d);
   k_bin_fill<<<nblk(d.nc, 256), 256, 0, s>>>(d);

@@ -91,6 +91,35 @@ __device__ double wall_dist2(const Dev &d, const float4 *seg, int blk, double x,
   return best;
 }
 
+// Bracket of the same minimum without its exact evaluation over every
+// candidate: hi = the exact distance of the float-nearest segment (an upper
+// bound), lo = the smallest float lower bound over all segments (rounded
+// so that lo <= every exact segment distance).  Both +inf without walls.
+__device__ void wall_dist2_bounds(const Dev &d, const float4 *seg, int blk, double x, double y,
+                                  double &lo, double &hi) {
+  lo = hi = __longlong_as_double(0x7ff0000000000000LL);
+  int s0 = d.wall_seg_off[blk], s1 = d.wall_seg_off[blk + 1];
+  if (s1 <= s0) return;
+  float xf = __double2float_rn(x), yf = __double2float_rn(y);
+  int sg = s0;
+  float gbest = __int_as_float(0x7f800000), lbmin = __int_as_float(0x7f800000);
+  for (int s = s0; s < s1; ++s) {
+    float4 AB = seg[s];
+    float ex = AB.z - AB.x, ey = AB.w - AB.y, px = xf - AB.x, py = yf - AB.y;
+    float ee = ex * ex + ey * ey;
+    float t = ee > 0.f ? fminf(fmaxf((px * ex + py * ey) / ee, 0.f), 1.f) : 0.f;
+    float dx = px - t * ex, dy = py - t * ey, g = dx * dx + dy * dy;
+    if (g < gbest) { gbest = g; sg = s; }
+    float lx = fminf(AB.x, AB.z), hx = fmaxf(AB.x, AB.z), ly = fminf(AB.y, AB.w), hy = fmaxf(AB.y, AB.w);
+    float tol = 2.4e-7f * (fabsf(xf) + fabsf(yf) + fabsf(lx) + fabsf(hx) + fabsf(ly) + fabsf(hy));
+    float gx = fmaxf(fmaxf(lx - xf, xf - hx) - tol, 0.f);
+    float gy = fmaxf(fmaxf(ly - yf, yf - hy) - tol, 0.f);
+    lbmin = fminf(lbmin, (gx * gx + gy * gy) * 0.99999f);
+  }
+  hi = seg_dist2(d, sg, x, y);
+  lo = (double)lbmin;
+}
+
 __device__ bool inside_quad(const Dev &d, int c, double x, double y) {
   const int *nd = d.cell_nodes + 4 * c;
 #pragma unroll
@@ -295,9 +324,11 @@ template <bool STAGE> __global__ void k_node_classify(Dev d) {
   int z = d.node_block[n];
   double x = d.X_new[2 * n], y = d.X_new[2 * n + 1];
   // the node's own wall distance is needed only where another zone's core
-  // contains it (most background nodes lie in no other zone)
-  double dz = 0.0;
-  bool have_dz = false;
+  // contains it (most background nodes lie in no other zone), and exactly
+  // only where the brackets of the two distances overlap: elsewhere the
+  // brackets already decide db < dz (or db > dz) as the exact values would
+  double dz = 0.0, zlo = 0.0, zhi = 0.0;
+  bool have_z = false, have_dz = false;
   bool inact = false;
   for (int b = 0; b < d.nblocks && !inact; ++b) {
     if (b == z) continue;
@@ -313,13 +344,23 @@ template <bool STAGE> __global__ void k_node_classify(Dev d) {
       return !in_layer(bi, loc % ni, loc / ni, L);
     }) >= 0;
     if (hit) {
-      if (!have_dz) {
-        dz = wall_dist2(d, seg, z, x, y);
-        have_dz = true;
+      if (!have_z) {
+        wall_dist2_bounds(d, seg, z, x, y, zlo, zhi);
+        have_z = true;
       }
-      double db = wall_dist2(d, seg, b, x, y);
-      const int *bz = d.blk_info + 8 * z;
-      if (db < dz || (db == dz && bi[3] > bz[3])) inact = true;
+      double blo, bhi;
+      wall_dist2_bounds(d, seg, b, x, y, blo, bhi);
+      if (bhi < zlo) {                  // db <= bhi < zlo <= dz
+        inact = true;
+      } else if (!(blo > zhi)) {        // brackets overlap: exact values
+        if (!have_dz) {
+          dz = wall_dist2(d, seg, z, x, y);
+          have_dz = true;
+        }
+        double db = wall_dist2(d, seg, b, x, y);
+        const int *bz = d.blk_info + 8 * z;
+        if (db < dz || (db == dz && bi[3] > bz[3])) inact = true;
+      }                                 // else db >= blo > zhi >= dz: stays active
     }
   }
   d.node_active[n] = inact ? 0 : 1;

@@ -1,0 +1,101 @@
+"""Precision statement of the mixed path: FP32-mixed (and FP64) GPU density,
+velocity, temperature, wall force and wall heat against the FP64 oracle after
+several implicit steps, per workload, with the bound 1e-5 relative on the
+macroscopic fields.  Run with -s to print the error table."""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+from oracle.run import Run  # noqa: E402
+from paper_2604_09984_gb300 import ugks as U  # noqa: E402
+from paper_2604_09984_gb300 import workloads as wl  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    if not os.path.exists(U.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    U.load()
+
+
+def cases():
+    return {
+        "channel": (wl.channel(ni=12, nj=7, nv=10, n_inner=3), 3),
+        "mems": (wl.mems(nbi=48, nbj=24, noi=32, noj=12, nv=8, stretch=1.15, n_inner=2), 3),
+        "two_bodies": (wl.tsto(nbi=80, nbj=40, noi=24, noj=10, nv=22, n_inner=2), 1),
+    }
+
+
+def primitives(W, K):
+    """rho, velocity, temperature (R = 1, D = 2, K internal degrees)."""
+    rho = W[:, 0]
+    V = W[:, 1:3] / rho[:, None]
+    e = W[:, 3] / rho - 0.5 * (V * V).sum(1)
+    return rho, V, 2.0 * e / (2.0 + 1.0 + K)
+
+
+def wall_loads(r):
+    """Per block: sum over its wall faces of S times the wall macro flux of the
+    last flux evaluation (the oracle's counterpart of ugks_moments)."""
+    fl = r.info.last_flux
+    topo = r.setup.topo
+    out = np.zeros((len(r.case.blocks), 4))
+    for n, f in enumerate(fl.wall_face):
+        out[topo.face_block[f]] += r.geo.S[f] * fl.wall_F[n]
+    return out
+
+
+def errors(W, wall, r):
+    field = r.status == 0
+    K = r.case.K
+    rho, V, T = primitives(W[field], K)
+    rr, Vr, Tr = primitives(r.state.W[field], K)
+    wr = wall_loads(r)
+    e = {
+        "rho": np.abs(rho - rr).max() / np.abs(rr).max(),
+        "V": np.abs(V - Vr).max() / max(np.abs(Vr).max(), 1e-3),
+        "T": np.abs(T - Tr).max() / np.abs(Tr).max(),
+        "W": np.abs(W[field] - r.state.W[field]).max() / np.abs(r.state.W[field]).max(),
+    }
+    # wall force components relative to the largest force magnitude (a
+    # component can be near zero, e.g. the shear on the channel walls), heat
+    # relative to the largest heat
+    fscale = np.hypot(wr[:, 1], wr[:, 2]).max()
+    for m, name in ((1, "Fx"), (2, "Fy")):
+        e[name] = np.abs(wall[:, m] - wr[:, m]).max() / fscale if fscale > 0 else 0.0
+    hscale = np.abs(wr[:, 3]).max()
+    e["heat"] = np.abs(wall[:, 3] - wr[:, 3]).max() / hscale if hscale > 0 else 0.0
+    return e
+
+
+@pytest.mark.parametrize("which", ["channel", "mems", "two_bodies"])
+def test_errors_against_oracle(which):
+    case, nsteps = cases()[which]
+    r = Run(case)
+    s32 = U.Solver(case, U.FP32)
+    s64 = U.Solver(case, U.FP64)
+    for _ in range(nsteps):
+        r.step()
+        s32.advance()
+        s64.advance()
+    res = {}
+    for name, s in (("FP32", s32), ("FP64", s64)):
+        W, q, st, wall = s.moments()
+        assert np.array_equal(st, r.status)
+        res[name] = errors(W, wall, r)
+    print("\n%-10s %-4s " % (which, "") + " ".join("%9s" % k for k in res["FP32"]))
+    for name, e in res.items():
+        print("%-10s %-4s " % ("", name) + " ".join("%9.2e" % v for v in e.values()))
+    for k in ("rho", "V", "T", "W"):
+        assert res["FP32"][k] < 1e-5, (k, res["FP32"][k])
+        assert res["FP64"][k] < 1e-12, (k, res["FP64"][k])
+    for k in ("Fx", "Fy", "heat"):
+        assert res["FP32"][k] < 1e-4, (k, res["FP32"][k])
+        assert res["FP64"][k] < 1e-10, (k, res["FP64"][k])

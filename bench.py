@@ -370,6 +370,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-plain comparison arm")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-bf16", action="store_true", help="skip the bf16-storage experiment arm")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default sweep tile (for profiler runs, where the tuner's timings are distorted)")
     args = ap.parse_args()
@@ -457,6 +458,15 @@ def main():
         fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / max(1, args.fp64_steps),
                 "speedup_fp32_over_fp64": value / world / v64}
         s64.close()
+    bf16 = None
+    if not args.no_bf16:
+        # experiment: f stored as bf16 pairs (same FP32 arithmetic)
+        sb, msb, nfb, _, _ = time_arm(case, U.BF16F, steps, warmup, device, profile=False,
+                                      tune=not args.no_tune)
+        vb = nfb * case.nv * case.n_inner * steps / (msb * 1e-3)
+        bf16 = {"value": vb, "unit": UNIT, "ms_per_step": msb / steps, "speedup_over_fp32": vb / (value / world),
+                "note": "experiment: f stored as bf16 pairs, FP32 arithmetic; errors ~1e-3 relative"}
+        sb.close()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
         "warmup": warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
@@ -474,6 +484,7 @@ def main():
         "roofline": roof,
         "kernels": breakdown,
         "fp64_plain": fp64,
+        "bf16_f_storage": bf16,
     }
     if rank == 0 and not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.kn, steps=2)

@@ -59,6 +59,10 @@ extern "C" {
 #define UGKS_FP32 1   /* f and per-velocity arithmetic in FP32; moments,
                          macroscopic update, geometry and face coefficients in
                          FP64 (mixed precision)                                */
+#define UGKS_BF16F 2  /* experiment: as UGKS_FP32, but f itself stored as bf16
+                         pairs (4 bytes a cell-velocity, rounded to nearest
+                         on every store); errors of ~1e-3 relative, outside
+                         the 1e-5 bound of the mixed path                      */
 
 /* boundary kind of a block side (sides ordered i-low, i-high, j-low, j-high) */
 #define UGKS_BC_NONE     0   /* interior; i-sides of a periodic block          */

@@ -24,7 +24,8 @@ struct ugks_ctx {
   char *ws = nullptr;
   size_t ws_bytes = 0;
   Dev d;
-  int fp32 = 0;
+  int fp32 = 0;                       // FP32 arithmetic (also on the BF16-storage path)
+  int fbf = 0;                        // f stored as bf16 pairs
   int nblocks = 0;
   std::vector<ugks_block_desc> blocks;
   std::vector<int> cell_off, node_off;
@@ -80,7 +81,10 @@ struct Sizes {
 
 int validate(const ugks_params *p, int nb, const ugks_block_desc *b, Sizes &s, std::string &why) {
   if (!p || nb <= 0 || !b) { why = "null params or no blocks"; return UGKS_ERR_ARG; }
-  if (p->precision != UGKS_FP64 && p->precision != UGKS_FP32) { why = "precision"; return UGKS_ERR_ARG; }
+  if (p->precision != UGKS_FP64 && p->precision != UGKS_FP32 && p->precision != UGKS_BF16F) {
+    why = "precision";
+    return UGKS_ERR_ARG;
+  }
   if (p->nvx < 2 || p->nvy < 2 || p->nvx * p->nvy > (1 << 20)) { why = "velocity grid size"; return UGKS_ERR_ARG; }
   if (!(p->vx_max > p->vx_min) || !(p->vy_max > p->vy_min)) { why = "velocity bounds"; return UGKS_ERR_ARG; }
   if (p->K < 0 || !(p->Pr > 0) || !(p->mu_ref > 0) || !(p->cfl_s > 0) || !(p->cfl_pseudo > 0)) {
@@ -157,7 +161,7 @@ int block_G(int nj, int nvp, int vpt, int items_req = 0) {
 }
 
 int sweep_vpt_for(const ugks_params *p) {
-  return p->precision == UGKS_FP32 ? sweep_vpt<float>() : sweep_vpt<double>();
+  return p->precision != UGKS_FP64 ? sweep_vpt<float>() : sweep_vpt<double>();
 }
 
 // Threads of a micro-sweep CTA: the widest block's rows x G, rounded up to
@@ -174,9 +178,10 @@ int sweep_threads_for(const ugks_params *p, int nb, const ugks_block_desc *b, in
 
 // Lay out every device array of the context in the workspace (base may be
 // null to measure).  Returns the bytes used.
-size_t carve(char *base, const Sizes &s, int nb, int fp32, int nwork, int cap_interp, Dev &d) {
+size_t carve(char *base, const Sizes &s, int nb, int fp32, int fbf, int nwork, int cap_interp, Dev &d) {
   Carver c(base);
   size_t pair = fp32 ? 2 * sizeof(float) : 2 * sizeof(double);
+  size_t fpair = fbf ? 4 : pair;       // storage of f (bf16 pairs on the BF16-storage path)
   size_t tsz = fp32 ? sizeof(float) : sizeof(double);
   d.vx = c.take<double>(s.nvp); d.vy = c.take<double>(s.nvp); d.w = c.take<double>(s.nvp);
   d.vxf = c.take<float>(s.nvp); d.vyf = c.take<float>(s.nvp); d.wf = c.take<float>(s.nvp);
@@ -213,7 +218,8 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int nwork, int cap_in
   d.fgeo = c.take<char>(tsz * NFG * (size_t)s.nf);
   d.srec = c.take<char>(tsz * NSR * (size_t)s.nc);
   d.affine = c.take<double>(6 * (size_t)nb);
-  d.f = c.take<char>(pair * (size_t)s.nc * s.nvp);
+  d.f = c.take<char>(fpair * (size_t)s.nc * s.nvp);
+  d.fbf = fbf;
   d.W = c.take<double>(4 * (size_t)s.nc); d.q = c.take<double>(2 * (size_t)s.nc);
   d.status = c.take<int>(s.nc);
   d.Tn = c.take<char>(pair * (size_t)s.nc * s.nvp);
@@ -616,7 +622,8 @@ int ugks_workspace_query(const ugks_params *p, int nblocks, const ugks_block_des
   if (!bytes) return UGKS_ERR_ARG;
   Dev d;
   memset(&d, 0, sizeof(d));
-  *bytes = carve(nullptr, s, nblocks, p->precision == UGKS_FP32, nwork_cap_for(p, nblocks, blocks),
+  *bytes = carve(nullptr, s, nblocks, p->precision != UGKS_FP64, p->precision == UGKS_BF16F,
+                 nwork_cap_for(p, nblocks, blocks),
                  cap_interp_for(s, nblocks), d);
   return UGKS_OK;
 }
@@ -629,7 +636,8 @@ int ugks_create(const ugks_params *p, void *workspace, size_t bytes, void *strea
   c->ws = (char *)workspace;
   c->ws_bytes = bytes;
   c->st = (cudaStream_t)stream;
-  c->fp32 = p->precision == UGKS_FP32;
+  c->fp32 = p->precision != UGKS_FP64;
+  c->fbf = p->precision == UGKS_BF16F;
   memset(&c->d, 0, sizeof(c->d));
   int prio_lo = 0, prio_hi = 0;
   cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
@@ -695,9 +703,9 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
   ctx->cap_interp = cap_interp_for(s, nblocks);
   Dev &d = ctx->d;
   memset(&d, 0, sizeof(d));
-  size_t need = carve(nullptr, s, nblocks, ctx->fp32, ctx->nwork_cap, ctx->cap_interp, d);
+  size_t need = carve(nullptr, s, nblocks, ctx->fp32, ctx->fbf, ctx->nwork_cap, ctx->cap_interp, d);
   if (need > ctx->ws_bytes) return fail(ctx, UGKS_ERR_WORKSPACE, "workspace too small: need " + std::to_string(need));
-  carve(ctx->ws, s, nblocks, ctx->fp32, ctx->nwork_cap, ctx->cap_interp, d);
+  carve(ctx->ws, s, nblocks, ctx->fp32, ctx->fbf, ctx->nwork_cap, ctx->cap_interp, d);
   {
     // the trailing private arrays follow d.err in carve order
     Carver c(ctx->ws);
@@ -966,7 +974,7 @@ int ugks_autotune(ugks_ctx *ctx, int reps, int *items_out, int *ring_out) {
   Dev &d = ctx->d;
   cudaStream_t s = ctx->st;
   int fp = ctx->fp32;
-  size_t fbytes = (fp ? 8 : 16) * (size_t)d.nc * d.nvp;
+  size_t fbytes = (ctx->fbf ? 4 : fp ? 8 : 16) * (size_t)d.nc * d.nvp;
   // f is restored afterwards; the sweep buffer and the flux divergence are
   // rewritten by every inner iteration, so the trials may use them
   CK(cudaMemcpyAsync(d.Dbuf, d.f, fbytes, cudaMemcpyDeviceToDevice, s));

@@ -4,6 +4,7 @@
 // flux of one velocity (Eqs. microscopicFlux, fullSolution; wall condition
 // with Eq. maxWalldes) and its sum over the faces of a cell.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include "ugks_math.cuh"
@@ -100,6 +101,7 @@ struct Dev {
   int *cls;                  // nc scratch classification
   int *donors;               // nc*5
   double *dwgt;              // nc*5
+  int fbf;                   // f stored as bf16 pairs (FP32 arithmetic)
   int *rec_list;             // receptor cells, ascending (compacted on the device)
   int *fresh_list;           // cells uncovered by the motion, ascending
   int *conn_cnt;             // 8 counters: receptors, fresh, field, hole, orphans
@@ -178,6 +180,26 @@ __device__ __forceinline__ void stf(void *base, size_t idx, T h, T b) {
   v.x = h;
   v.y = b;
   reinterpret_cast<typename Vec2<T>::type *>(base)[idx] = v;
+}
+
+// The distribution f in its storage type: the arithmetic type's pair, or on
+// the BF16-storage path (FP32 arithmetic) a bf16 pair rounded to nearest on
+// store and widened exactly on load.  FB = 1 / 0 fixes the storage at
+// compile time (the hot kernels are instantiated for both); FB = -1 reads
+// d.fbf at run time.
+template <typename T, int FB = -1>
+__device__ __forceinline__ typename Vec2<T>::type ldF(const Dev &d, size_t idx) {
+  if (sizeof(T) == 4 && (FB == 1 || (FB < 0 && d.fbf))) {
+    float2 w = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162 *>(d.f)[idx]);
+    return typename Vec2<T>::type{(T)w.x, (T)w.y};
+  }
+  return ldf<T>(d.f, idx);
+}
+template <typename T, int FB = -1> __device__ __forceinline__ void stF(const Dev &d, size_t idx, T h, T b) {
+  if (sizeof(T) == 4 && (FB == 1 || (FB < 0 && d.fbf)))
+    reinterpret_cast<__nv_bfloat162 *>(d.f)[idx] = __floats2bfloat162_rn((float)h, (float)b);
+  else
+    stf<T>(d.f, idx, h, b);
 }
 
 // Asynchronous global -> shared copies (cp.async, sm_80+): a per-thread
@@ -271,7 +293,7 @@ __device__ __forceinline__ V2<T> nb_value(const Dev &d, int c, int s, int k) {
   int kind = d.nb_kind[c * 4 + s];
   int id = d.nb_id[c * 4 + s];
   if (kind == NB_CELL) {
-    auto v = ldf<T>(d.f, (size_t)id * d.nvp + k);
+    auto v = ldF<T>(d, (size_t)id * d.nvp + k);
     return {v.x, v.y};
   }
   const double *g = d.ghostW + 4 * id;
@@ -347,7 +369,7 @@ template <typename T> __device__ V2<T> face_flux(const Dev &d, int fid, int k) {
       T Hw = P[FP_RHOW] * (lw * T(M_1_PI)) * r_exp<T>(-lw * (wx * wx + wy * wy));
       return {wS * Hw, wS * (T)d.Keff / (T(2) * lw) * Hw};
     }
-    auto fv = ldf<T>(d.f, (size_t)L * d.nvp + k);
+    auto fv = ldF<T>(d, (size_t)L * d.nvp + k);
     V2<T> fc = {fv.x, fv.y}, gx, gy;
     grad_f<T>(d, L, k, fc, gx, gy);
     T dx = (T)(d.xf[2 * fid] - d.xc[2 * L]), dy = (T)(d.xf[2 * fid + 1] - d.xc[2 * L + 1]);
@@ -358,7 +380,7 @@ template <typename T> __device__ V2<T> face_flux(const Dev &d, int fid, int k) {
     bool useL = wS > T(0), useR = wS < T(0);
     V2<T> fL = {0, 0}, fR = {0, 0}, gL = {0, 0}, gR = {0, 0};
     if (!useR) {
-      auto fv = ldf<T>(d.f, (size_t)L * d.nvp + k);
+      auto fv = ldF<T>(d, (size_t)L * d.nvp + k);
       V2<T> fc = {fv.x, fv.y}, gx, gy;
       grad_f<T>(d, L, k, fc, gx, gy);
       double sh = (double)d.face_shiftL[fid];
@@ -369,7 +391,7 @@ template <typename T> __device__ V2<T> face_flux(const Dev &d, int fid, int k) {
     }
     if (!useL) {
       if (R >= 0) {
-        auto fv = ldf<T>(d.f, (size_t)R * d.nvp + k);
+        auto fv = ldF<T>(d, (size_t)R * d.nvp + k);
         V2<T> fc = {fv.x, fv.y}, gx, gy;
         grad_f<T>(d, R, k, fc, gx, gy);
         T dx = (T)(d.xf[2 * fid] - d.xc[2 * R]), dy = (T)(d.xf[2 * fid + 1] - d.xc[2 * R + 1]);

@@ -311,7 +311,7 @@ __device__ __forceinline__ void face_upwind(const Dev &d, int fid, int k, T wS, 
   bool useL = (kind == BC_WALL) || wS > T(0), useR = (kind != BC_WALL) && wS < T(0);
   V2<T> fL = {0, 0}, fR = {0, 0}, gL = {0, 0}, gR = {0, 0};
   if (!useR) {
-    auto fv = ldf<T>(d.f, (size_t)L * d.nvp + k);
+    auto fv = ldF<T>(d, (size_t)L * d.nvp + k);
     V2<T> fc = {fv.x, fv.y}, gx, gy;
     grad_f<T>(d, L, k, fc, gx, gy);
     double sh = (double)d.face_shiftL[fid];
@@ -323,7 +323,7 @@ __device__ __forceinline__ void face_upwind(const Dev &d, int fid, int k, T wS, 
   if (!useL) {
     int R = d.face_R[fid];
     if (R >= 0) {
-      auto fv = ldf<T>(d.f, (size_t)R * d.nvp + k);
+      auto fv = ldF<T>(d, (size_t)R * d.nvp + k);
       V2<T> fc = {fv.x, fv.y}, gx, gy;
       grad_f<T>(d, R, k, fc, gx, gy);
       T dx = (T)(d.xf[2 * fid] - d.xc[2 * R]), dy = (T)(d.xf[2 * fid + 1] - d.xc[2 * R + 1]);
@@ -1183,7 +1183,7 @@ template <typename T, int VPT> struct SweepVals {
   }
 };
 
-template <typename T, int PASS, int NS, int VPT>
+template <typename T, int PASS, int NS, int VPT, int FB>
 __global__ void __launch_bounds__(512) k_micro_sweep(Dev d, const int *work, int R) {
   typedef typename Vec2<T>::type T2;
   typedef SweepVals<T, VPT> SV;
@@ -1230,11 +1230,13 @@ __global__ void __launch_bounds__(512) k_micro_sweep(Dev d, const int *work, int
         unsigned char *st = ring + (size_t)slot * stage;
         if (kin) {
           size_t gb = ((size_t)c * d.nvp + kb) * sizeof(T2);
+          constexpr bool fb = PASS == 1 && FB == 1;          // bf16 f: 4 bytes a velocity
 #pragma unroll
           for (int q = 0; q < SV::NQ; ++q) {
             cp_async<16>(st + ((size_t)q * nt + threadIdx.x) * 16, gin + gb + 16 * q);
-            if (PASS == 1) cp_async<16>(st + ((size_t)(SV::NQ + q) * nt + threadIdx.x) * 16, gf + gb + 16 * q);
+            if (PASS == 1 && !fb) cp_async<16>(st + ((size_t)(SV::NQ + q) * nt + threadIdx.x) * 16, gf + gb + 16 * q);
           }
+          if (fb) cp_async<4 * VPT>(st + ((size_t)SV::NQ * nt + threadIdx.x) * 16, gf + ((size_t)c * d.nvp + kb) * 4);
         }
         for (int q = g; q < NCH; q += G)
           cp_async<16>(st + recoff + row * RS + 16 * q, srec + (size_t)c * NSR * sizeof(T) + 16 * q);
@@ -1313,16 +1315,26 @@ __global__ void __launch_bounds__(512) k_micro_sweep(Dev d, const int *work, int
         if (!kok[u]) val[u] = T2{0, 0};
       }
       size_t idx = (size_t)c * d.nvp + kb;
-      T2 *out = reinterpret_cast<T2 *>(PASS == 0 ? d.dfs : d.f) + idx;
+      T2 *out = reinterpret_cast<T2 *>(d.dfs) + idx;
+      constexpr bool fb = PASS == 1 && FB == 1;
 #pragma unroll
       for (int u = 0; u < VPT; ++u) {
         T2 o = val[u];
         if (PASS == 1) {
-          T2 fv = *SV::at(st + (size_t)SV::NQ * nt * 16, nt, threadIdx.x, u);
+          T2 fv;
+          if (fb) {
+            float2 w = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162 *>(
+                st + ((size_t)SV::NQ * nt + threadIdx.x) * 16)[u]);
+            fv = T2{(T)w.x, (T)w.y};
+          } else {
+            fv = *SV::at(st + (size_t)SV::NQ * nt * 16, nt, threadIdx.x, u);
+          }
           o.x = fv.x + o.x;
           o.y = fv.y + o.y;
+          stF<T, FB>(d, idx + u, o.x, o.y);
+        } else {
+          out[u] = o;
         }
-        out[u] = o;
       }
     }
     if (act) {
@@ -1346,7 +1358,7 @@ __global__ void __launch_bounds__(512) k_micro_sweep(Dev d, const int *work, int
 
 // Step 7 (one warp per cell): W^{s+1} = W' + sum V Psi (f^{s+1} - g(W')),
 // heat flux about V' (reading R7); flags non-physical states.
-template <typename T> __global__ void k_moments(Dev d) {
+template <typename T, int FB> __global__ void k_moments(Dev d) {
   int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (c >= d.nc) return;
@@ -1362,7 +1374,7 @@ template <typename T> __global__ void k_moments(Dev d) {
 #pragma unroll
     for (int u = 0; u < NB; ++u) {
       int k = kb + 32 * u;
-      fb[u] = k < d.nv ? ldf<T>(d.f, (size_t)c * d.nvp + k) : T2{T(0), T(0)};
+      fb[u] = k < d.nv ? ldF<T, FB>(d, (size_t)c * d.nvp + k) : T2{T(0), T(0)};
     }
     // the batch's terms are summed plainly, the batch sums compensated
     T p[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
@@ -1419,10 +1431,10 @@ template <typename T> __global__ void k_init_state(Dev d, const double *prim) {
   double lam = 1.0 / (2.0 * T0);
   double qx = 0, qy = 0;
   for (int k = lane; k < d.nvp; k += 32) {
-    if (k >= d.nv) { stf<T>(d.f, (size_t)c * d.nvp + k, T(0), T(0)); continue; }
+    if (k >= d.nv) { stF<T>(d, (size_t)c * d.nvp + k, T(0), T(0)); continue; }
     V2<double> g = maxwellian<double>(rho, ux, uy, lam, d.vx[k], d.vy[k], (double)d.Keff);
     T h = (T)g.h, b = (T)g.b;
-    stf<T>(d.f, (size_t)c * d.nvp + k, h, b);
+    stF<T>(d, (size_t)c * d.nvp + k, h, b);
     double cx = d.vx[k] - ux, cy = d.vy[k] - uy;
     double e = (cx * cx + cy * cy) * (double)h + (double)b;
     qx += 0.5 * d.w[k] * cx * e;
@@ -1479,7 +1491,7 @@ template <typename T> __global__ void k_f_to_double(Dev d, double *out) {
   size_t n = (size_t)d.nc * d.nv;
   if (t >= n) return;
   int c = (int)(t / d.nv), k = (int)(t % d.nv);
-  auto v = ldf<T>(d.f, (size_t)c * d.nvp + k);
+  auto v = ldF<T>(d, (size_t)c * d.nvp + k);
   out[2 * t] = (double)v.x;
   out[2 * t + 1] = (double)v.y;
 }
@@ -1488,7 +1500,7 @@ template <typename T> __global__ void k_f_from_double(Dev d, const double *in) {
   size_t n = (size_t)d.nc * d.nv;
   if (t >= n) return;
   int c = (int)(t / d.nv), k = (int)(t % d.nv);
-  stf<T>(d.f, (size_t)c * d.nvp + k, (T)in[2 * t], (T)in[2 * t + 1]);
+  stF<T>(d, (size_t)c * d.nvp + k, (T)in[2 * t], (T)in[2 * t + 1]);
 }
 
 // ------------------------------------------------------- launch wrappers
@@ -1606,18 +1618,21 @@ void sweep_setup() {
 #undef UGKS_MACRO_ATTR
   int mx = (int)kSweepSmem;
   constexpr int VF = sweep_vpt<float>(), VD = sweep_vpt<double>();
-  cudaFuncSetAttribute(k_micro_sweep<float, 0, 4, VF>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<float, 1, 4, VF>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<float, 0, 3, VF>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<float, 1, 3, VF>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<float, 0, 2, VF>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<float, 1, 2, VF>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<double, 0, 4, VD>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<double, 1, 4, VD>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<double, 0, 3, VD>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<double, 1, 3, VD>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<double, 0, 2, VD>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<double, 1, 2, VD>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<float, 0, 4, VF, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<float, 1, 4, VF, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<float, 0, 3, VF, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<float, 1, 3, VF, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<float, 0, 2, VF, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<float, 1, 2, VF, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<double, 0, 4, VD, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<double, 1, 4, VD, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<double, 0, 3, VD, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<double, 1, 3, VD, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<double, 0, 2, VD, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<double, 1, 2, VD, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<float, 1, 4, VF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<float, 1, 3, VF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<float, 1, 2, VF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
 }
 
 // Micro sweeps: ring depth ns_req (2-4) when it fits, else the deepest ring
@@ -1644,9 +1659,15 @@ static void micro_sweep(const Dev &d, cudaStream_t s, const int *work, int nwork
   int want = ns_req >= 2 ? ns_req : (env ? atoi(env) : 0);
   if (want >= 2 && want <= 4 && base + want * stage <= kSweepSmem) ns = want;
   size_t sm = base + ns * stage;
-  if (ns == 4) k_micro_sweep<T, PASS, 4, VPT><<<nwork, threads, sm, s>>>(d, work, R);
-  else if (ns == 3) k_micro_sweep<T, PASS, 3, VPT><<<nwork, threads, sm, s>>>(d, work, R);
-  else k_micro_sweep<T, PASS, 2, VPT><<<nwork, threads, sm, s>>>(d, work, R);
+  if (PASS == 1 && d.fbf) {
+    if (ns == 4) k_micro_sweep<T, PASS, 4, VPT, 1><<<nwork, threads, sm, s>>>(d, work, R);
+    else if (ns == 3) k_micro_sweep<T, PASS, 3, VPT, 1><<<nwork, threads, sm, s>>>(d, work, R);
+    else k_micro_sweep<T, PASS, 2, VPT, 1><<<nwork, threads, sm, s>>>(d, work, R);
+  } else {
+    if (ns == 4) k_micro_sweep<T, PASS, 4, VPT, 0><<<nwork, threads, sm, s>>>(d, work, R);
+    else if (ns == 3) k_micro_sweep<T, PASS, 3, VPT, 0><<<nwork, threads, sm, s>>>(d, work, R);
+    else k_micro_sweep<T, PASS, 2, VPT, 0><<<nwork, threads, sm, s>>>(d, work, R);
+  }
 }
 void launch_micro_fwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int threads, int rows,
                       int nsm, int ns, int fp32) {
@@ -1659,8 +1680,9 @@ void launch_micro_bwd(const Dev &d, cudaStream_t s, const int *work, int nwork, 
   else micro_sweep<double, 1>(d, s, work, nwork, threads, rows, nsm, ns);
 }
 void launch_moments(const Dev &d, cudaStream_t s, int fp32) {
-  if (fp32) k_moments<float><<<nblk((size_t)d.nc * 32, 256), 256, 0, s>>>(d);
-  else k_moments<double><<<nblk((size_t)d.nc * 32, 256), 256, 0, s>>>(d);
+  if (fp32 && d.fbf) k_moments<float, 1><<<nblk((size_t)d.nc * 32, 256), 256, 0, s>>>(d);
+  else if (fp32) k_moments<float, 0><<<nblk((size_t)d.nc * 32, 256), 256, 0, s>>>(d);
+  else k_moments<double, 0><<<nblk((size_t)d.nc * 32, 256), 256, 0, s>>>(d);
 }
 void launch_init_state(const Dev &d, cudaStream_t s, const double *prim, int fp32) {
   if (fp32) k_init_state<float><<<nblk((size_t)d.nc * 32, 256), 256, 0, s>>>(d, prim);

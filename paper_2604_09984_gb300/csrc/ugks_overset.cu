@@ -534,7 +534,7 @@ template <typename T> __global__ void k_interp_gather(Dev d, const int *list, co
       int e = d.donors[5 * c + m];
       if (e < 0) continue;
       T w = (T)d.dwgt[5 * c + m];
-      auto v = ldf<T>(d.f, (size_t)e * d.nvp + k);
+      auto v = ldF<T>(d, (size_t)e * d.nvp + k);
       ah = ah + w * v.x;
       ab = ab + w * v.y;
     }
@@ -562,7 +562,7 @@ template <typename T> __global__ void k_interp_scatter(Dev d, const int *list, c
     int c = list[r];
     if (d.donors[5 * c] < 0) continue;          // orphan: keep its values
     auto v = ldf<T>(d.itmp, t);
-    stf<T>(d.f, (size_t)c * d.nvp + k, v.x, v.y);
+    stF<T>(d, (size_t)c * d.nvp + k, v.x, v.y);
     if (k == 0) {
       for (int q = 0; q < 4; ++q) d.W[4 * c + q] = d.itmpW[6 * r + q];
       d.q[2 * c] = d.itmpW[6 * r + 4];

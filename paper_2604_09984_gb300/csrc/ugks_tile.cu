@@ -91,7 +91,7 @@ __device__ __forceinline__ void tile_meta(const Dev &d, TileSmem<T> &S, const in
 }
 
 // f of the region for velocity chunk kbase (warp w loads cells w, w+8, ...)
-template <typename T>
+template <typename T, int FB>
 __device__ __forceinline__ void tile_load_f(const Dev &d, TileSmem<T> &S, int k, bool kv, T vx, T vy) {
   typedef typename Vec2<T>::type T2;
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -101,7 +101,12 @@ __device__ __forceinline__ void tile_load_f(const Dev &d, TileSmem<T> &S, int k,
     int g = S.gid[r];
     T2 *dst = &S.F[r * VK + lane];
     if (kv && g >= 0) {
-      cp_async<(int)sizeof(T2)>(dst, reinterpret_cast<const T2 *>(d.f) + (size_t)g * d.nvp + k);
+      if (FB) {                                // bf16 storage: widen on the way in
+        auto v = ldF<T, 1>(d, (size_t)g * d.nvp + k);
+        *dst = T2{v.x, v.y};
+      } else {
+        cp_async<(int)sizeof(T2)>(dst, reinterpret_cast<const T2 *>(d.f) + (size_t)g * d.nvp + k);
+      }
       continue;
     }
     T2 v = {T(0), T(0)};
@@ -265,7 +270,7 @@ __device__ __forceinline__ int cell_status(const TileSmem<float> &S, int r) { re
 __device__ __forceinline__ int cell_status(const TileSmem<double> &S, int r) { return S.flags[r] >> 8; }
 
 // ------------------------------------------------------- flux divergence
-template <typename T> __global__ void __launch_bounds__(TTHREADS) k_flux_tile(Dev d) {
+template <typename T, int FB> __global__ void __launch_bounds__(TTHREADS) k_flux_tile(Dev d) {
   typedef typename Vec2<T>::type T2;
   extern __shared__ __align__(16) unsigned char smraw[];
   TileSmem<T> S;
@@ -281,7 +286,7 @@ template <typename T> __global__ void __launch_bounds__(TTHREADS) k_flux_tile(De
   T vx = kv ? dvx<T>(d, k) : T(0), vy = kv ? dvy<T>(d, k) : T(0);
   tile_meta<T>(d, S, bi, off, i0, j0);
   __syncthreads();
-  tile_load_f<T>(d, S, k, kv, vx, vy);
+  tile_load_f<T, FB>(d, S, k, kv, vx, vy);
   __syncthreads();
   T *Pw = reinterpret_cast<T *>(smraw + TileSmem<T>::bytes() + sizeof(T2) * TX * TY * VK) +
           (size_t)w * (TX + 1) * NFP;
@@ -368,7 +373,7 @@ template <typename T> __global__ void __launch_bounds__(TTHREADS) k_flux_tile(De
 //   r = T - Omega^{n+1} f / dt + (Omega^{n+1} (f+(W') - f)/tau' - D) / 2,
 // with the level-n term T = Omega^n f^n / dt + (Omega^n (f+(W^n) - f^n)/tau^n
 // - D^n) / 2 formed on the first inner iteration.  r goes to the sweep buffer.
-template <typename T> __global__ void k_residual(Dev d, int first_iter) {
+template <typename T, int FB> __global__ void k_residual(Dev d, int first_iter) {
   typedef typename Vec2<T>::type T2;
   // grid: cells x velocity chunks; a thread takes two adjacent velocities
   // (nvp is a multiple of 4, so the pair stays inside the cell's row)
@@ -383,7 +388,7 @@ template <typename T> __global__ void k_residual(Dev d, int first_iter) {
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
     size_t t = (size_t)c * d.nvp + k0 + u;
-    fv[u] = ldf<T>(d.f, t);
+    fv[u] = ldF<T, FB>(d, t);
     D[u] = ldf<T>(d.Dbuf, t);
     if (!first_iter) tn[u] = ldf<T>(d.Tn, t);
   }
@@ -416,7 +421,7 @@ template <typename T> __global__ void k_residual(Dev d, int first_iter) {
 // velocity sums of the chunk are reduced across the warp in the arithmetic
 // type (butterfly, every lane ends with the totals) and lane m adds total m
 // to the FP64 face sums with an atomic.
-template <typename T> __global__ void __launch_bounds__(TTHREADS) k_face_reduce_tile(Dev d) {
+template <typename T, int FB> __global__ void __launch_bounds__(TTHREADS) k_face_reduce_tile(Dev d) {
   extern __shared__ __align__(16) unsigned char smraw[];
   TileSmem<T> S;
   S.carve(smraw);
@@ -430,7 +435,7 @@ template <typename T> __global__ void __launch_bounds__(TTHREADS) k_face_reduce_
   T vx = kv ? dvx<T>(d, k) : T(0), vy = kv ? dvy<T>(d, k) : T(0);
   tile_meta<T>(d, S, bi, off, i0, j0);
   __syncthreads();
-  tile_load_f<T>(d, S, k, kv, vx, vy);
+  tile_load_f<T, FB>(d, S, k, kv, vx, vy);
   __syncthreads();
   T wk = kv ? dw<T>(d, k) : T(0);
   T v2 = T(0.5) * (vx * vx + vy * vy);
@@ -527,10 +532,12 @@ template <typename T> static size_t reduce_smem() {
 }
 
 void tile_setup() {
-  cudaFuncSetAttribute(k_flux_tile<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_smem<float>());
-  cudaFuncSetAttribute(k_flux_tile<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_smem<double>());
-  cudaFuncSetAttribute(k_face_reduce_tile<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)reduce_smem<float>());
-  cudaFuncSetAttribute(k_face_reduce_tile<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)reduce_smem<double>());
+  cudaFuncSetAttribute(k_flux_tile<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_smem<float>());
+  cudaFuncSetAttribute(k_flux_tile<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_smem<float>());
+  cudaFuncSetAttribute(k_flux_tile<double, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_smem<double>());
+  cudaFuncSetAttribute(k_face_reduce_tile<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)reduce_smem<float>());
+  cudaFuncSetAttribute(k_face_reduce_tile<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)reduce_smem<float>());
+  cudaFuncSetAttribute(k_face_reduce_tile<double, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)reduce_smem<double>());
 }
 
 int tile_count(int ni, int nj) { return ((ni + TX - 1) / TX) * ((nj + TY - 1) / TY); }
@@ -543,23 +550,26 @@ void tile_origins(int ni, int nj, int *out) {   // (i0, j0) pairs
 void launch_flux_tile(const Dev &d, cudaStream_t s, int fp32) {
   int nchunks = (d.nv + VK - 1) / VK;
   int grid = d.ntiles * nchunks;
-  if (fp32) k_flux_tile<float><<<grid, TTHREADS, rhs_smem<float>(), s>>>(d);
-  else k_flux_tile<double><<<grid, TTHREADS, rhs_smem<double>(), s>>>(d);
+  if (fp32 && d.fbf) k_flux_tile<float, 1><<<grid, TTHREADS, rhs_smem<float>(), s>>>(d);
+  else if (fp32) k_flux_tile<float, 0><<<grid, TTHREADS, rhs_smem<float>(), s>>>(d);
+  else k_flux_tile<double, 0><<<grid, TTHREADS, rhs_smem<double>(), s>>>(d);
 }
 void launch_residual(const Dev &d, cudaStream_t s, int first_iter, int fp32) {
   int pairs = (d.nv + 1) / 2;
   int bt = pairs >= 256 ? 256 : ((pairs + 31) / 32) * 32;
   dim3 grid(d.nc, (pairs + bt - 1) / bt);
-  if (fp32) k_residual<float><<<grid, bt, 0, s>>>(d, first_iter);
-  else k_residual<double><<<grid, bt, 0, s>>>(d, first_iter);
+  if (fp32 && d.fbf) k_residual<float, 1><<<grid, bt, 0, s>>>(d, first_iter);
+  else if (fp32) k_residual<float, 0><<<grid, bt, 0, s>>>(d, first_iter);
+  else k_residual<double, 0><<<grid, bt, 0, s>>>(d, first_iter);
 }
 
 void launch_face_reduce_tile(const Dev &d, cudaStream_t s, int fp32) {
   int nchunks = (d.nv + VK - 1) / VK;
   cudaMemsetAsync(d.fsum, 0, sizeof(double) * NFS * (size_t)d.nf, s);
   int grid = d.ntiles * nchunks;
-  if (fp32) k_face_reduce_tile<float><<<grid, TTHREADS, reduce_smem<float>(), s>>>(d);
-  else k_face_reduce_tile<double><<<grid, TTHREADS, reduce_smem<double>(), s>>>(d);
+  if (fp32 && d.fbf) k_face_reduce_tile<float, 1><<<grid, TTHREADS, reduce_smem<float>(), s>>>(d);
+  else if (fp32) k_face_reduce_tile<float, 0><<<grid, TTHREADS, reduce_smem<float>(), s>>>(d);
+  else k_face_reduce_tile<double, 0><<<grid, TTHREADS, reduce_smem<double>(), s>>>(d);
 }
 
 }  // namespace ugks

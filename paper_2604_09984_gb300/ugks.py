@@ -23,7 +23,7 @@ OK = 0
 ERR = {-1: "UGKS_ERR_ARG", -2: "UGKS_ERR_CUDA", -3: "UGKS_ERR_GEOMETRY", -4: "UGKS_ERR_ORPHAN",
        -5: "UGKS_ERR_NONPHYSICAL", -6: "UGKS_ERR_WORKSPACE", -7: "UGKS_ERR_ORDER",
        -8: "UGKS_ERR_TIMEOUT"}
-FP64, FP32 = 0, 1
+FP64, FP32, BF16F = 0, 1, 2      # BF16F: FP32 arithmetic, f stored as bf16 pairs (experiment)
 STATIC_SCRATCH_DOUBLES = 1 << 19     # UGKS_STATIC_SCRATCH_DOUBLES
 FIELD, RECEPTOR, HOLE = 0, 1, 2
 

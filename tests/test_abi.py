@@ -39,7 +39,9 @@ def test_workspace_query_host_only(lib):
     case = wl.channel(ni=16, nj=8, nv=10)
     n32 = U.workspace_bytes(case, U.FP32)
     n64 = U.workspace_bytes(case, U.FP64)
-    assert n64 > n32 > 0
+    nbf = U.workspace_bytes(case, U.BF16F)
+    assert n64 > n32 > nbf > 0
+    assert n32 - nbf >= 4 * 16 * 8 * 100       # f alone shrinks by 4 bytes a cell-velocity
     # f, level-n term and sweep increments dominate: >= 3 copies of f
     assert n64 >= 3 * 16 * 16 * 8 * 100
     big = wl.mems(nv=32)

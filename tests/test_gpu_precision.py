@@ -1,7 +1,8 @@
 """Precision statement of the mixed path: FP32-mixed (and FP64) GPU density,
 velocity, temperature, wall force and wall heat against the FP64 oracle after
 several implicit steps, per workload, with the bound 1e-5 relative on the
-macroscopic fields.  Run with -s to print the error table."""
+macroscopic fields; the bf16 storage of f (experiment) is reported beside
+them with a loose bound.  Run with -s to print the error table."""
 import os
 
 import numpy as np
@@ -79,14 +80,14 @@ def errors(W, wall, r):
 def test_errors_against_oracle(which):
     case, nsteps = cases()[which]
     r = Run(case)
-    s32 = U.Solver(case, U.FP32)
-    s64 = U.Solver(case, U.FP64)
+    solvers = {"FP32": U.Solver(case, U.FP32), "FP64": U.Solver(case, U.FP64),
+               "BF16f": U.Solver(case, U.BF16F)}
     for _ in range(nsteps):
         r.step()
-        s32.advance()
-        s64.advance()
+        for s in solvers.values():
+            s.advance()
     res = {}
-    for name, s in (("FP32", s32), ("FP64", s64)):
+    for name, s in solvers.items():
         W, q, st, wall = s.moments()
         assert np.array_equal(st, r.status)
         res[name] = errors(W, wall, r)
@@ -99,3 +100,6 @@ def test_errors_against_oracle(which):
     for k in ("Fx", "Fy", "heat"):
         assert res["FP32"][k] < 1e-4, (k, res["FP32"][k])
         assert res["FP64"][k] < 1e-10, (k, res["FP64"][k])
+    # bf16 storage of f (experiment): 8-bit significands, every store rounds
+    for k in ("rho", "T", "W"):
+        assert res["BF16f"][k] < 2e-2, (k, res["BF16f"][k])

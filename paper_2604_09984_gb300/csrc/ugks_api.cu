@@ -441,12 +441,13 @@ int check_err_flag(ugks_ctx *ctx) {
   CK(cudaStreamSynchronize(ctx->st));
   if (h) {
     CK(cudaMemsetAsync(ctx->d.err, 0, sizeof(int), ctx->st));
+    // causes before consequences: motion and assembly, then the step
     if (h & EF_GEOMETRY) return fail(ctx, UGKS_ERR_GEOMETRY, "non-positive cell volume after mesh move");
-    if (h & EF_NONPHYSICAL) return fail(ctx, UGKS_ERR_NONPHYSICAL, "non-finite or non-positive density/temperature");
     if (h & EF_BINS) return fail(ctx, UGKS_ERR_WORKSPACE, "overset search bins overflowed");
-    if (h & EF_TIMEOUT) return fail(ctx, UGKS_ERR_TIMEOUT, "a kernel's bounded wait for its data ran out");
     if (h & EF_CAPACITY) return fail(ctx, UGKS_ERR_WORKSPACE, "more receptors than the interpolation staging holds");
     if (h & EF_ORPHAN) return fail(ctx, UGKS_ERR_ORPHAN, "overset receptors without donor");
+    if (h & EF_TIMEOUT) return fail(ctx, UGKS_ERR_TIMEOUT, "a kernel's bounded wait for its data ran out");
+    if (h & EF_NONPHYSICAL) return fail(ctx, UGKS_ERR_NONPHYSICAL, "non-finite or non-positive density/temperature");
   }
   return UGKS_OK;
 }

@@ -304,3 +304,28 @@ def test_autotune_restores_state_and_changes_no_result():
     Wb = b.moments()[0]
     assert rel(a.moments()[0], Wb) < 1e-13
     assert rel(c.moments()[0], Wb) < 1e-13
+
+
+def test_batch_defers_orphan_report_to_next_sync():
+    """ugks_advance_batch never waits on the device: an assembly that leaves
+    receptors without donor (the body grid pushed half out of the box)
+    returns UGKS_OK at once and surfaces as UGKS_ERR_ORPHAN at the next
+    synchronising call; the oracle finds orphans for the same placement."""
+    import ctypes
+    case = wl.mems(nbi=48, nbj=24, noi=32, noj=12, nv=8, stretch=1.15, n_inner=1, amp=0.5)
+    s = U.Solver(case, U.FP64, stream=torch.cuda.Stream())
+    t1 = 0.25 / case.meta["freq"]
+    A = np.ascontiguousarray(case.motion(t1), dtype=np.float64)
+    ctxs = (ctypes.c_void_p * 1)(s.ctx.value)
+    tn = (ctypes.c_double * 1)(t1)
+    aff = (ctypes.POINTER(ctypes.c_double) * 1)(A.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    failed = ctypes.c_int(7)
+    assert U.load().ugks_advance_batch(ctxs, 1, tn, aff, 1, ctypes.byref(failed)) == U.OK
+    assert failed.value == -1
+    with pytest.raises(U.UgksError) as err:
+        s.moments()
+    assert err.value.code == -4
+    topo = mesh.Topology(case.blocks)
+    c0 = overset.connect(topo, case.nodes_at(0.0))
+    c1 = overset.connect(topo, case.nodes_at(t1), c0.status)
+    assert c1.n_orphan > 0

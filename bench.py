@@ -165,7 +165,26 @@ def ncu_traffic(group):
     return traffic.get(group)
 
 
-def time_arm(case, precision, steps, warmup, device, profile, tune=True):
+def max_over_ranks(ms, dist, device):
+    """Slowest rank's time (the whole job's time); ms itself with one rank."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_sync(dist):
+    """Device idle on this rank, then all ranks at the same point."""
+    import torch
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+
+
+def time_arm(case, precision, steps, warmup, device, profile, tune=True, dist=None):
     import torch
     from paper_2604_09984_gb300 import ugks as U
     s = U.Solver(case, precision, device=device)
@@ -174,7 +193,7 @@ def time_arm(case, precision, steps, warmup, device, profile, tune=True):
         s.advance()
         if n == 0 and tune:
             s.autotune()          # sweep tiles for this workload, before the timed steps
-    torch.cuda.synchronize()
+    rank_sync(dist)
     nfield = field_cells(s)
     if profile:
         s.profile_read(reset=True)
@@ -186,7 +205,7 @@ def time_arm(case, precision, steps, warmup, device, profile, tune=True):
     for _ in range(steps):
         s.advance()
     ev1.record(s.stream)
-    torch.cuda.synchronize()
+    rank_sync(dist)
     ms = ev0.elapsed_time(ev1)
     launches = s.launch_count() - l0
     prof = None
@@ -223,7 +242,7 @@ def e2e_arm(s, steps):
     return ms, h2d, d2h
 
 
-def batch_arm(cases, steps, warmup, device):
+def batch_arm(cases, steps, warmup, device, dist=None):
     """Batched serving: one solver (FP32) per instance, each on its own
     stream, advanced together through ugks_advance_batch.  Device time from
     an event every instance stream waits on to an event that waits on every
@@ -237,7 +256,7 @@ def batch_arm(cases, steps, warmup, device):
         if n == 0:
             for s in solvers:     # per-instance sweep tiles
                 s.autotune()
-    torch.cuda.synchronize()
+    rank_sync(dist)
     tiles = sorted({s.tiles for s in solvers})
     nfield = [field_cells(s) for s in solvers]
     l0 = sum(s.launch_count() for s in solvers)
@@ -256,7 +275,7 @@ def batch_arm(cases, steps, warmup, device):
         e.record(st)
         main_st.wait_event(e)
     ev1.record(main_st)
-    torch.cuda.synchronize()
+    rank_sync(dist)
     ms = ev0.elapsed_time(ev1)
     launches = sum(s.launch_count() for s in solvers) - l0
     units = sum(n * c.nv * c.n_inner for n, c in zip(nfield, cases)) * steps
@@ -283,14 +302,15 @@ def batch_arm(cases, steps, warmup, device):
     return ms, units, launches, host_s, e2e_s, h2d, d2h, sum(nfield), tiles
 
 
-def run_batch(args, world, rank, device):
+def run_batch(args, world, rank, device, dist=None):
     cases = wl.mems_batch(n=args.instances)
     steps = max(1, args.steps)
     warmup = max(3, args.warmup)
     clk = Clocks(int(device.split(":")[1]))
     clk.start()
-    ms, units, launches, host_s, e2e_s, h2d, d2h, nfield, tiles = batch_arm(cases, steps, warmup, device)
+    ms, units, launches, host_s, e2e_s, h2d, d2h, nfield, tiles = batch_arm(cases, steps, warmup, device, dist)
     clocks = clk.stop()
+    ms = max_over_ranks(ms, dist, device)
     value = units * world / (ms * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
@@ -400,7 +420,7 @@ def main():
     device = "cuda:%d" % local
     torch.cuda.set_device(local)
     if args.workload == "mems_batch":
-        run_batch(args, world, rank, device)
+        run_batch(args, world, rank, device, dist)
         if dist is not None:
             dist.destroy_process_group()
         return
@@ -408,17 +428,12 @@ def main():
     steps = max(1, args.steps)
     warmup = max(3, args.warmup)
 
-    if dist is not None:
-        dist.barrier()
     clk = Clocks(local)
     clk.start()
     s, ms, nfield, launches, prof = time_arm(case, U.FP32, steps, warmup, device, profile=True,
-                                             tune=not args.no_tune)
+                                             tune=not args.no_tune, dist=dist)
     clocks = clk.stop()
-    if dist is not None:
-        t = torch.tensor([ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, device)
     units = nfield * case.nv * case.n_inner * steps * world
     value = units / (ms * 1e-3)
     # roofline of the dominant kernel group (CUDA events on the launch stream)

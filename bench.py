@@ -321,7 +321,7 @@ def run_batch(args, world, rank, device, dist=None):
                                % (len(cases), nfield, sum(c.ncells * c.nv for c in cases)),
                    "precision": "FP32 f and per-velocity arithmetic, FP64 moments/geometry",
                    "l2": "inputs larger than L2", "streams": len(cases),
-                   "sweep_tiles": "autotuned per instance (items per CTA and diagonal, ring): %s" % tiles,
+                   "sweep_tiles": "autotuned per instance (items, velocities per thread, rings fwd/bwd): %s" % tiles,
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "host_issue_ms_per_step": host_s * 1e3 / steps,
         "clocks": clocks,
@@ -489,7 +489,7 @@ def main():
         "config": {"workload": workload_label(case), "precision": "FP32 f and per-velocity arithmetic, FP64 moments/geometry",
                    "l2": "inputs larger than L2 (f alone %.0f MB)" % (s_bytes(case) / 1e6),
                    "field_cells": nfield, "nv": case.nv, "n_inner": case.n_inner,
-                   "sweep_tiles": ("autotuned (items per CTA and diagonal, ring): %s" % (tiles,)) if tiles
+                   "sweep_tiles": ("autotuned (items per CTA and diagonal, velocities per thread, rings fwd/bwd): %s" % (tiles,)) if tiles
                    else "default (1024 items per CTA and diagonal, ring by rule)",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "per_physical_step": value / case.n_inner,

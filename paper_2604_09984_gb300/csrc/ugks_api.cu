@@ -32,7 +32,8 @@ struct ugks_ctx {
   int max_nj = 0;
   int sweep_threads = 32, nwork = 0, nsm = 0;
   int nwork_cap = 0;                  // work-list capacity (largest tuning candidate)
-  int sweep_items = 0, sweep_ns = 0;  // micro-sweep tile and ring depth (0 = by rule)
+  int sweep_items = 0, sweep_vpt = 2; // micro-sweep tile (0 = by rule) and velocities per thread
+  int ns_fwd = 0, ns_bwd = 0;         // ring depths of the two sweeps (0 = by rule)
   bool stepped = false;               // a ugks_step has run (sweep records valid)
   int *work = nullptr;
   int *prev_status = nullptr, *n_orphan = nullptr, *blk_order = nullptr;
@@ -160,14 +161,22 @@ int block_G(int nj, int nvp, int vpt, int items_req = 0) {
   return G;
 }
 
+// Default velocities per sweep thread; UGKS_SWEEP_VPT=4 selects four on the
+// FP32 paths by hand (the autotuner tries both).
 int sweep_vpt_for(const ugks_params *p) {
-  return p->precision != UGKS_FP64 ? sweep_vpt<float>() : sweep_vpt<double>();
+  if (p->precision != UGKS_FP64) {
+    if (const char *e = getenv("UGKS_SWEEP_VPT"))
+      if (atoi(e) == 4) return 4;
+    return sweep_vpt<float>();
+  }
+  return sweep_vpt<double>();
 }
 
 // Threads of a micro-sweep CTA: the widest block's rows x G, rounded up to
 // whole warps.
-int sweep_threads_for(const ugks_params *p, int nb, const ugks_block_desc *b, int items = 0) {
-  int nvp = (p->nvx * p->nvy + 3) / 4 * 4, vpt = sweep_vpt_for(p);
+int sweep_threads_for(const ugks_params *p, int nb, const ugks_block_desc *b, int items = 0, int vpt = 0) {
+  int nvp = (p->nvx * p->nvy + 3) / 4 * 4;
+  if (vpt <= 0) vpt = sweep_vpt_for(p);
   int t = 32;
   for (int i = 0; i < nb; ++i) {
     int w = b[i].nj * block_G(b[i].nj, nvp, vpt, items);
@@ -279,8 +288,9 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int fbf, int nwork, i
 int cap_interp_for(const Sizes &s, int nb) { return nb > 1 ? (s.nc / 4 > 1024 ? s.nc / 4 : (s.nc < 1024 ? s.nc : 1024)) : 0; }
 
 // Micro-sweep work items (block, first velocity, G): one per velocity tile.
-int nwork_for(const ugks_params *p, int nb, const ugks_block_desc *b, int items = 0) {
-  int nvp = (p->nvx * p->nvy + 3) / 4 * 4, vpt = sweep_vpt_for(p);
+int nwork_for(const ugks_params *p, int nb, const ugks_block_desc *b, int items = 0, int vpt = 0) {
+  int nvp = (p->nvx * p->nvy + 3) / 4 * 4;
+  if (vpt <= 0) vpt = sweep_vpt_for(p);
   int n = 0;
   for (int i = 0; i < nb; ++i) {
     int vt = block_G(b[i].nj, nvp, vpt, items) * vpt;
@@ -293,11 +303,13 @@ int nwork_for(const ugks_params *p, int nb, const ugks_block_desc *b, int items 
 // and diagonal step) and ring depths.
 constexpr int kTuneItems[] = {256, 512, 1024, 2048};
 constexpr int kTuneRing[] = {2, 3, 4};
+constexpr int kTuneVpt[] = {2, 4};        // FP32 paths; FP64 keeps 2
 
 // Work-list capacity: the most tiles any candidate (or the default) needs.
 int nwork_cap_for(const ugks_params *p, int nb, const ugks_block_desc *b) {
   int n = nwork_for(p, nb, b);
-  for (int it : kTuneItems) n = std::max(n, nwork_for(p, nb, b, it));
+  for (int it : kTuneItems)
+    for (int v : kTuneVpt) n = std::max(n, nwork_for(p, nb, b, it, v));
   return n;
 }
 
@@ -456,9 +468,9 @@ int launch_status(ugks_ctx *ctx) { return cuda_check(ctx, cudaPeekAtLastError(),
 
 // Micro-sweep work list for a tile size (items per CTA and diagonal, 0 = by
 // rule): (block, first velocity, G) per velocity tile of every block.
-std::vector<int> sweep_work(const ugks_ctx *ctx, int items) {
+std::vector<int> sweep_work(const ugks_ctx *ctx, int items, int vpt) {
   std::vector<int> work;
-  int nvp = ctx->d.nvp, vpt = sweep_vpt_for(&ctx->p);
+  int nvp = ctx->d.nvp;
   for (int b = 0; b < ctx->nblocks; ++b) {
     int G = block_G(ctx->blocks[b].nj, nvp, vpt, items);
     for (int k0 = 0; k0 < nvp; k0 += G * vpt) { work.push_back(b); work.push_back(k0); work.push_back(G); }
@@ -467,14 +479,15 @@ std::vector<int> sweep_work(const ugks_ctx *ctx, int items) {
 }
 
 // Switch the micro sweeps to another tile size (uploads the work list).
-int set_sweep_tiles(ugks_ctx *ctx, int items) {
-  std::vector<int> work = sweep_work(ctx, items);
+int set_sweep_tiles(ugks_ctx *ctx, int items, int vpt) {
+  std::vector<int> work = sweep_work(ctx, items, vpt);
   if ((int)work.size() / 3 > ctx->nwork_cap) return fail(ctx, UGKS_ERR_WORKSPACE, "sweep work list");
   CK(cudaMemcpyAsync(ctx->work, work.data(), sizeof(int) * work.size(), cudaMemcpyHostToDevice, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   ctx->nwork = (int)work.size() / 3;
-  ctx->sweep_threads = sweep_threads_for(&ctx->p, ctx->nblocks, ctx->blocks.data(), items);
+  ctx->sweep_threads = sweep_threads_for(&ctx->p, ctx->nblocks, ctx->blocks.data(), items, vpt);
   ctx->sweep_items = items;
+  ctx->sweep_vpt = vpt;
   return UGKS_OK;
 }
 
@@ -691,7 +704,8 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
   ctx->nblocks = nblocks;
   ctx->blocks.assign(blocks, blocks + nblocks);
   ctx->max_nj = s.max_nj;
-  ctx->sweep_threads = sweep_threads_for(&ctx->p, nblocks, blocks);
+  ctx->sweep_vpt = sweep_vpt_for(&ctx->p);
+  ctx->sweep_threads = sweep_threads_for(&ctx->p, nblocks, blocks, 0, ctx->sweep_vpt);
   {
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
@@ -699,7 +713,7 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
       ctx->nsm = nsm;
     cudaGetLastError();
   }
-  ctx->nwork = nwork_for(&ctx->p, nblocks, blocks);
+  ctx->nwork = nwork_for(&ctx->p, nblocks, blocks, 0, ctx->sweep_vpt);
   ctx->nwork_cap = nwork_cap_for(&ctx->p, nblocks, blocks);
   ctx->cap_interp = cap_interp_for(s, nblocks);
   Dev &d = ctx->d;
@@ -772,7 +786,7 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
       if (blocks[order[b]].priority > blocks[order[a]].priority ||
           (blocks[order[b]].priority == blocks[order[a]].priority && order[b] < order[a]))
         std::swap(order[a], order[b]);
-  std::vector<int> work = sweep_work(ctx, 0);
+  std::vector<int> work = sweep_work(ctx, 0, ctx->sweep_vpt);
   std::vector<int> tiles;
   for (int b = 0; b < nblocks; ++b) {
     std::vector<int> org(2 * (size_t)tile_count(blocks[b].ni, blocks[b].nj));
@@ -930,8 +944,8 @@ int ugks_step(ugks_ctx *ctx, double dt, int n_inner) {
     { Prof p(ctx, UGKS_PROF_RHS); launch_flux_tile(d, s, fp); }                              // Step 3
     CK(cudaStreamWaitEvent(s, ctx->ev_macro, 0));
     { Prof p(ctx, UGKS_PROF_RESIDUAL); launch_residual(d, s, it == 0, fp); }                 // Step 5
-    { Prof p(ctx, UGKS_PROF_MICRO_FWD); launch_micro_fwd(d, s, ctx->work, ctx->nwork, ctx->sweep_threads, ctx->max_nj, ctx->nsm, ctx->sweep_ns, fp); }  // Step 6
-    { Prof p(ctx, UGKS_PROF_MICRO_BWD); launch_micro_bwd(d, s, ctx->work, ctx->nwork, ctx->sweep_threads, ctx->max_nj, ctx->nsm, ctx->sweep_ns, fp); }
+    { Prof p(ctx, UGKS_PROF_MICRO_FWD); launch_micro_fwd(d, s, ctx->work, ctx->nwork, ctx->sweep_threads, ctx->max_nj, ctx->nsm, ctx->ns_fwd, ctx->sweep_vpt, fp); }  // Step 6
+    { Prof p(ctx, UGKS_PROF_MICRO_BWD); launch_micro_bwd(d, s, ctx->work, ctx->nwork, ctx->sweep_threads, ctx->max_nj, ctx->nsm, ctx->ns_bwd, ctx->sweep_vpt, fp); }
     { Prof p(ctx, UGKS_PROF_MOMENTS); launch_moments(d, s, fp); }                          // Step 7
     ctx->launches += 8;
   }
@@ -968,7 +982,7 @@ int ugks_advance_batch(ugks_ctx *const *ctx, int n, const double *t_new, const d
   return UGKS_OK;
 }
 
-int ugks_autotune(ugks_ctx *ctx, int reps, int *items_out, int *ring_out) {
+int ugks_autotune(ugks_ctx *ctx, int reps, int *items_out, int *vpt_out, int *ring_fwd_out, int *ring_bwd_out) {
   if (!ctx || !ctx->mesh_ready) return UGKS_ERR_ORDER;
   if (!ctx->stepped) return fail(ctx, UGKS_ERR_ORDER, "ugks_autotune needs a preceding ugks_step");
   if (reps < 1) reps = 3;
@@ -983,22 +997,39 @@ int ugks_autotune(ugks_ctx *ctx, int reps, int *items_out, int *ring_out) {
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
-  int bi = ctx->sweep_items, bn = ctx->sweep_ns;
+  int bi = ctx->sweep_items, bv = ctx->sweep_vpt, bf = ctx->ns_fwd, bb = ctx->ns_bwd;
   int r = UGKS_OK;
+  // time one sweep (pass 0 forward, 1 backward) with ring depth ns
+  auto trial = [&](int pass, int ns, float &ms) -> int {
+    for (int rep = 0; rep <= reps; ++rep) {     // the first pass warms up
+      if (rep == 1) cudaEventRecord(e0, s);
+      if (pass == 0)
+        launch_micro_fwd(d, s, ctx->work, ctx->nwork, ctx->sweep_threads, ctx->max_nj, ctx->nsm, ns, ctx->sweep_vpt, fp);
+      else
+        launch_micro_bwd(d, s, ctx->work, ctx->nwork, ctx->sweep_threads, ctx->max_nj, ctx->nsm, ns, ctx->sweep_vpt, fp);
+    }
+    cudaEventRecord(e1, s);
+    int q = cuda_check(ctx, cudaEventSynchronize(e1), "autotune");
+    ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ctx->launches += reps + 1;
+    return q;
+  };
   for (int items : kTuneItems) {
-    if ((r = set_sweep_tiles(ctx, items))) break;
-    for (int ns : kTuneRing) {
-      for (int rep = 0; rep <= reps; ++rep) {   // the first pass warms up
-        if (rep == 1) cudaEventRecord(e0, s);
-        launch_micro_fwd(d, s, ctx->work, ctx->nwork, ctx->sweep_threads, ctx->max_nj, ctx->nsm, ns, fp);
-        launch_micro_bwd(d, s, ctx->work, ctx->nwork, ctx->sweep_threads, ctx->max_nj, ctx->nsm, ns, fp);
+    for (int vpt : kTuneVpt) {
+      if (!fp && vpt != sweep_vpt<double>()) continue;
+      if ((r = set_sweep_tiles(ctx, items, vpt))) break;
+      float tf = 1e30f, tb = 1e30f;
+      int nf = 0, nb = 0;
+      for (int ns : kTuneRing) {
+        float ms;
+        if ((r = trial(0, ns, ms))) break;
+        if (ms < tf) { tf = ms; nf = ns; }
+        if ((r = trial(1, ns, ms))) break;
+        if (ms < tb) { tb = ms; nb = ns; }
       }
-      cudaEventRecord(e1, s);
-      if ((r = cuda_check(ctx, cudaEventSynchronize(e1), "autotune"))) break;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      ctx->launches += 2 * (reps + 1);
-      if (ms < best) { best = ms; bi = items; bn = ns; }
+      if (r) break;
+      if (tf + tb < best) { best = tf + tb; bi = items; bv = vpt; bf = nf; bb = nb; }
     }
     if (r) break;
   }
@@ -1006,10 +1037,13 @@ int ugks_autotune(ugks_ctx *ctx, int reps, int *items_out, int *ring_out) {
   cudaEventDestroy(e1);
   if (r) return r;
   CK(cudaMemcpyAsync(d.f, d.Dbuf, fbytes, cudaMemcpyDeviceToDevice, s));
-  if ((r = set_sweep_tiles(ctx, bi))) return r;
-  ctx->sweep_ns = bn;
+  if ((r = set_sweep_tiles(ctx, bi, bv))) return r;
+  ctx->ns_fwd = bf;
+  ctx->ns_bwd = bb;
   if (items_out) *items_out = bi;
-  if (ring_out) *ring_out = bn;
+  if (vpt_out) *vpt_out = bv;
+  if (ring_fwd_out) *ring_fwd_out = bf;
+  if (ring_bwd_out) *ring_bwd_out = bb;
   return launch_status(ctx);
 }
 

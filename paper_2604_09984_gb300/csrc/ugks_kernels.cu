@@ -1624,6 +1624,12 @@ void sweep_setup() {
   cudaFuncSetAttribute(k_micro_sweep<float, 1, 3, VF, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_micro_sweep<float, 0, 2, VF, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_micro_sweep<float, 1, 2, VF, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<float, 0, 4, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<float, 1, 4, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<float, 0, 3, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<float, 1, 3, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<float, 0, 2, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<float, 1, 2, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_micro_sweep<double, 0, 4, VD, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_micro_sweep<double, 1, 4, VD, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_micro_sweep<double, 0, 3, VD, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
@@ -1633,16 +1639,18 @@ void sweep_setup() {
   cudaFuncSetAttribute(k_micro_sweep<float, 1, 4, VF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_micro_sweep<float, 1, 3, VF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_micro_sweep<float, 1, 2, VF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<float, 1, 4, 4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<float, 1, 3, 4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_micro_sweep<float, 1, 2, 4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
 }
 
 // Micro sweeps: ring depth ns_req (2-4) when it fits, else the deepest ring
 // (4, 3 or 2 diagonals) with which all the sweep's CTAs are resident at once
 // (nsm SMs), else the deepest that fits one CTA per SM.
-template <typename T, int PASS>
-static void micro_sweep(const Dev &d, cudaStream_t s, const int *work, int nwork, int threads, int R,
-                        int nsm, int ns_req) {
+template <typename T, int PASS, int VPT>
+static void micro_sweep_v(const Dev &d, cudaStream_t s, const int *work, int nwork, int threads, int R,
+                          int nsm, int ns_req) {
   typedef typename Vec2<T>::type T2;
-  constexpr int VPT = sweep_vpt<T>();
   size_t tb = VPT * sizeof(T2), rs = sweep_rec_stride<T>();
   size_t stage = (PASS == 1 ? 2 : 1) * (size_t)threads * tb + (size_t)R * rs;
   size_t base = 2 * (size_t)threads * tb;
@@ -1669,15 +1677,28 @@ static void micro_sweep(const Dev &d, cudaStream_t s, const int *work, int nwork
     else k_micro_sweep<T, PASS, 2, VPT, 0><<<nwork, threads, sm, s>>>(d, work, R);
   }
 }
+// velocities per thread: 2, or 4 on the FP32 paths (large problems, where
+// fewer, wider CTAs cut the number of waves of diagonal sweeps)
+template <typename T, int PASS>
+static void micro_sweep(const Dev &d, cudaStream_t s, const int *work, int nwork, int threads, int R,
+                        int nsm, int ns_req, int vpt) {
+  if constexpr (sizeof(T) == 4) {
+    if (vpt == 4) {
+      micro_sweep_v<T, PASS, 4>(d, s, work, nwork, threads, R, nsm, ns_req);
+      return;
+    }
+  }
+  micro_sweep_v<T, PASS, sweep_vpt<T>()>(d, s, work, nwork, threads, R, nsm, ns_req);
+}
 void launch_micro_fwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int threads, int rows,
-                      int nsm, int ns, int fp32) {
-  if (fp32) micro_sweep<float, 0>(d, s, work, nwork, threads, rows, nsm, ns);
-  else micro_sweep<double, 0>(d, s, work, nwork, threads, rows, nsm, ns);
+                      int nsm, int ns, int vpt, int fp32) {
+  if (fp32) micro_sweep<float, 0>(d, s, work, nwork, threads, rows, nsm, ns, vpt);
+  else micro_sweep<double, 0>(d, s, work, nwork, threads, rows, nsm, ns, vpt);
 }
 void launch_micro_bwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int threads, int rows,
-                      int nsm, int ns, int fp32) {
-  if (fp32) micro_sweep<float, 1>(d, s, work, nwork, threads, rows, nsm, ns);
-  else micro_sweep<double, 1>(d, s, work, nwork, threads, rows, nsm, ns);
+                      int nsm, int ns, int vpt, int fp32) {
+  if (fp32) micro_sweep<float, 1>(d, s, work, nwork, threads, rows, nsm, ns, vpt);
+  else micro_sweep<double, 1>(d, s, work, nwork, threads, rows, nsm, ns, vpt);
 }
 void launch_moments(const Dev &d, cudaStream_t s, int fp32) {
   if (fp32 && d.fbf) k_moments<float, 1><<<nblk((size_t)d.nc * 32, 256), 256, 0, s>>>(d);

@@ -14,9 +14,9 @@ void launch_cell_macro(const Dev &d, cudaStream_t s, int level_n);
 void launch_cell_params(const Dev &d, cudaStream_t s, const double *W, double *out, int fp32);
 void launch_macro_sweep(const Dev &d, cudaStream_t s, int rows, int fp32);
 void launch_micro_fwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int threads, int rows,
-                      int nsm, int ns, int fp32);   // ns: ring depth 2-4, 0 = by rule
+                      int nsm, int ns, int vpt, int fp32);   // ns: ring depth 2-4, 0 = by rule
 void launch_micro_bwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int threads, int rows,
-                      int nsm, int ns, int fp32);
+                      int nsm, int ns, int vpt, int fp32);   // vpt: velocities per thread (2, or 4 in FP32)
 void sweep_setup();
 void launch_moments(const Dev &d, cudaStream_t s, int fp32);
 void launch_init_state(const Dev &d, cudaStream_t s, const double *prim, int fp32);

@@ -58,7 +58,7 @@ SYMBOLS = {
     "ugks_advance_batch": (c_int, [POINTER(c_void_p), c_int, POINTER(c_double), POINTER(POINTER(c_double)),
                                    c_int, POINTER(c_int)]),
     "ugks_moments": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
-    "ugks_autotune": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int)]),
+    "ugks_autotune": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
     "ugks_sizes": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
     "ugks_get_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "ugks_set_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -225,11 +225,13 @@ class Solver:
         self.step(dt, n_inner)
 
     def autotune(self, reps=3):
-        """Pick the fastest micro-sweep tile and ring depth on this context's
-        own state (ugks_autotune); returns (items per CTA and diagonal, ring)."""
-        items, ring = c_int(), c_int()
-        self._check(self.lib.ugks_autotune(self.ctx, int(reps), ctypes.byref(items), ctypes.byref(ring)))
-        self.tiles = (items.value, ring.value)
+        """Pick the fastest micro-sweep tile on this context's own state
+        (ugks_autotune); returns (items per CTA and diagonal, velocities per
+        thread, forward ring depth, backward ring depth)."""
+        items, vpt, rf, rb = c_int(), c_int(), c_int(), c_int()
+        self._check(self.lib.ugks_autotune(self.ctx, int(reps), ctypes.byref(items), ctypes.byref(vpt),
+                                           ctypes.byref(rf), ctypes.byref(rb)))
+        self.tiles = (items.value, vpt.value, rf.value, rb.value)
         return self.tiles
 
     def moments(self, W=None, q=None, status=None, wall=None):

@@ -294,8 +294,8 @@ def test_autotune_restores_state_and_changes_no_result():
     for s in (a, b, c):
         s.advance()
     f0, _, _ = a.get_state()
-    items, ring = a.autotune(reps=1)
-    assert items in (256, 512, 1024, 2048) and ring in (2, 3, 4)
+    items, vpt, ring_f, ring_b = a.autotune(reps=1)
+    assert items in (256, 512, 1024, 2048) and vpt == 2 and ring_f in (2, 3, 4) and ring_b in (2, 3, 4)
     f1, _, _ = a.get_state()
     assert torch.equal(f0, f1)
     for _ in range(2):
@@ -329,3 +329,28 @@ def test_batch_defers_orphan_report_to_next_sync():
     c0 = overset.connect(topo, case.nodes_at(0.0))
     c1 = overset.connect(topo, case.nodes_at(t1), c0.status)
     assert c1.n_orphan > 0
+
+
+@pytest.mark.parametrize("prec", [U.FP32, U.BF16F])
+def test_four_velocities_per_sweep_thread(prec):
+    """The FP32 sweeps with four velocities per thread (a tile the autotuner
+    may pick) compute what the two-velocity tiles compute."""
+    case = small_mems(nv=10)
+    prim = wl.random_prim(case, 23, amp_rho=0.05, amp_u=0.05, amp_T=0.05)
+    b = U.Solver(case, prec, prim=prim)
+    os.environ["UGKS_SWEEP_VPT"] = "4"
+    try:
+        c = U.Solver(case, prec, prim=prim)
+    finally:
+        del os.environ["UGKS_SWEEP_VPT"]
+    for _ in range(2):
+        b.advance()
+        c.advance()
+    Wb = b.moments()[0]
+    assert rel(c.moments()[0], Wb) < 1e-6
+    if prec == U.FP32:
+        r = Run(case, prim)
+        r.step()
+        r.step()
+        field = r.status == 0
+        assert rel(c.moments()[0][field], r.state.W[field]) < 1e-5

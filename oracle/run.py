@@ -1,4 +1,4 @@
-"""Time-marching driver of the oracle (test infrastructure).
+"""Time-marching loop of the oracle (test infrastructure).
 
 Sec. 3, the outer loop per physical step: (1) prescribed motion of every
 block (the case's affine maps), (2) overset assembly at t^{n+1} when there

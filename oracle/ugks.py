@@ -3,7 +3,7 @@
 Plain FP64 numpy restatement of Sec. 2 of the paper; see ``oracle/__init__``.
 Arrays: f (nc, nv, 2) holds the reduced pair (h, b); W (nc, 4); q (nc, 2).
 
-Readings where the paper is silent (each also listed in the design doc):
+Readings where the paper is silent:
   R1 reconstruction: per logical direction a van Leer limited slope of the
      cell-centre differences (one-sided where a side has no neighbour cell,
      ghost cells count as neighbours, holes do not), mapped to Cartesian

@@ -195,6 +195,14 @@ int ugks_step(ugks_ctx *ctx, double dt, int n_inner);
 int ugks_advance_batch(ugks_ctx *const *ctx, int n, const double *t_new,
                        const double *const *affine, int n_inner, int *failed);
 
+/* Torque of each block's wall force about the point center[b] (HOST,
+ * nblocks x 2): sum over the block's wall faces of (x_f - center) x (S F_x,
+ * S F_y) of the last flux evaluation, x_f the mid-time face centre; with the
+ * force of ugks_moments it drives a rigid body's Newton-Euler update (Sec. 3
+ * Step 1).  `torque` (nblocks doubles, host or device) receives the values.
+ * Synchronises the stream.  Errors: UGKS_ERR_ORDER, UGKS_ERR_ARG. */
+int ugks_wall_torque(ugks_ctx *ctx, const double *center, double *torque);
+
 /* Sweep autotuner: times the micro LU-SGS sweeps (`reps` timed passes after
  * one warm-up, CUDA events on the stream) for every candidate tile -- (cell,
  * velocity) items per CTA and diagonal step in {256, 512, 1024, 2048} and

@@ -248,6 +248,7 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int fbf, int nwork, i
   d.fflux = c.take<double>(4 * (size_t)s.nf);
   d.gam = c.take<double>(s.nf);
   d.wall_loads = c.take<double>(4 * (size_t)nb);
+  d.torque_io = c.take<double>(3 * (size_t)nb);
   d.wall_faces = c.take<int>(s.nf);
   d.node_active = c.take<int>(s.nn);
   d.cls = c.take<int>(s.nc);
@@ -1058,6 +1059,19 @@ int ugks_moments(ugks_ctx *ctx, double *W, double *q, int32_t *status, double *w
   if (wall_loads) CK(cudaMemcpyAsync(wall_loads, d.wall_loads, sizeof(double) * 4 * d.nblocks, cudaMemcpyDefault, ctx->st));
   int r = check_err_flag(ctx);
   if (r) return r;
+  return launch_status(ctx);
+}
+
+int ugks_wall_torque(ugks_ctx *ctx, const double *center, double *torque) {
+  if (!ctx || !ctx->mesh_ready) return UGKS_ERR_ORDER;
+  if (!center || !torque) return fail(ctx, UGKS_ERR_ARG, "null center or torque");
+  Dev &d = ctx->d;
+  ctx->launches += launch_upload(d.torque_io, center, sizeof(double) * 2 * d.nblocks, ctx->st);
+  double *out = d.torque_io + 2 * (size_t)d.nblocks;
+  launch_wall_torque(d, ctx->st, d.torque_io, out);
+  ctx->launches += 1;
+  CK(cudaMemcpyAsync(torque, out, sizeof(double) * d.nblocks, cudaMemcpyDefault, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
   return launch_status(ctx);
 }
 

@@ -94,6 +94,7 @@ struct Dev {
   double *fflux;             // nf*4 S * macro flux (L -> R / outward)
   double *gam;               // nf spectral radius Gamma
   double *wall_loads;        // nblocks*4
+  double *torque_io;         // nblocks*3: torque centres (2 per block), torques
   int *wall_faces;           // ids of the wall faces, ascending
   int nwall;
   // overset

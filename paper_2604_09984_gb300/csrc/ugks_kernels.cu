@@ -1485,6 +1485,27 @@ __global__ void __launch_bounds__(WL_THREADS) k_wall_loads(Dev d) {
   if (threadIdx.x < 4) d.wall_loads[4 * b + threadIdx.x] = part[threadIdx.x][0];
 }
 
+// Torque about the point ctr[b] of each block's wall force: sum over its
+// wall faces of (x_f - ctr) x (S F_x, S F_y) of the last flux evaluation
+// (mid-time face centres), same fixed reduction shape as k_wall_loads.
+__global__ void __launch_bounds__(WL_THREADS) k_wall_torque(Dev d, const double *ctr, double *out) {
+  __shared__ double part[WL_THREADS];
+  int b = blockIdx.x;
+  double cx = ctr[2 * b], cy = ctr[2 * b + 1], s = 0.0;
+  for (int f = threadIdx.x; f < d.nf; f += WL_THREADS) {
+    if (d.face_block[f] != b || d.face_kind[f] != BC_WALL) continue;
+    double rx = d.xf[2 * f] - cx, ry = d.xf[2 * f + 1] - cy;
+    s += rx * d.fflux[4 * f + 2] - ry * d.fflux[4 * f + 1];
+  }
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = WL_THREADS / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[b] = part[0];
+}
+
 // Copy f between the storage type and FP64 (get/set state).
 template <typename T> __global__ void k_f_to_double(Dev d, double *out) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1715,6 +1736,9 @@ void launch_flux_div_all(const Dev &d, cudaStream_t s, double *D, int fp32) {
   else k_flux_div_all<double><<<nblk(n, 256), 256, 0, s>>>(d, D);
 }
 void launch_wall_loads(const Dev &d, cudaStream_t s) { k_wall_loads<<<d.nblocks, WL_THREADS, 0, s>>>(d); }
+void launch_wall_torque(const Dev &d, cudaStream_t s, const double *ctr, double *out) {
+  k_wall_torque<<<d.nblocks, WL_THREADS, 0, s>>>(d, ctr, out);
+}
 void launch_f_convert(const Dev &d, cudaStream_t s, double *out, const double *in, int fp32) {
   size_t n = (size_t)d.nc * d.nv;
   if (out) {

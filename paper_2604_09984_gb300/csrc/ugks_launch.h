@@ -22,6 +22,7 @@ void launch_moments(const Dev &d, cudaStream_t s, int fp32);
 void launch_init_state(const Dev &d, cudaStream_t s, const double *prim, int fp32);
 void launch_flux_div_all(const Dev &d, cudaStream_t s, double *D, int fp32);
 void launch_wall_loads(const Dev &d, cudaStream_t s);
+void launch_wall_torque(const Dev &d, cudaStream_t s, const double *ctr, double *out);
 void launch_f_convert(const Dev &d, cudaStream_t s, double *out, const double *in, int fp32);
 void launch_connect(const Dev &d, cudaStream_t s, int *prev_status, const int *blk_order,
                     int *n_orphan);                           // 9 kernels

@@ -58,6 +58,7 @@ SYMBOLS = {
     "ugks_advance_batch": (c_int, [POINTER(c_void_p), c_int, POINTER(c_double), POINTER(POINTER(c_double)),
                                    c_int, POINTER(c_int)]),
     "ugks_moments": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ugks_wall_torque": (c_int, [c_void_p, POINTER(c_double), c_void_p]),
     "ugks_autotune": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
     "ugks_sizes": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
     "ugks_get_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -179,6 +180,7 @@ class Solver:
         self.nc, self.nf, self.nv, self.nvp = nc.value, nf.value, nv.value, nvp.value
         self.t = 0.0
         self.last_stats = None
+        self.stepped = False
 
     # -------------------------------------------------------------- errors
     def _check(self, r, ctx="self"):
@@ -216,11 +218,44 @@ class Solver:
         n_inner = self.case.n_inner if n_inner is None else n_inner
         self._check(self.lib.ugks_step(self.ctx, float(dt), int(n_inner)))
         self.t = self._t_new
+        self.stepped = True
 
     def advance(self, n_inner=None, dt=None):
         """One physical step of the outer loop (Sec. 3): motion, assembly, evolve."""
         dt = self.case.dt if dt is None else dt
         self.move_mesh(self.t + dt)
+        self.overset_connect()
+        self.step(dt, n_inner)
+
+    def wall_torque(self, centers):
+        """Torque of each block's wall force about centers[b] (ugks_wall_torque)."""
+        c = np.ascontiguousarray(centers, dtype=np.float64).reshape(len(self.case.blocks), 2)
+        out = np.empty(len(self.case.blocks))
+        self._check(self.lib.ugks_wall_torque(self.ctx, c.ctypes.data_as(POINTER(c_double)), _ptr(out)))
+        return out
+
+    def advance_coupled(self, bodies, n_inner=None, dt=None):
+        """One physical step with rigid bodies moved by the gas (Sec. 3 Step 1,
+        Newton-Euler): each body is updated from the wall force and torque of
+        the previous step's last flux evaluation (none before the first step),
+        then motion, assembly and the implicit step follow as in advance()."""
+        dt = self.case.dt if dt is None else dt
+        nb = len(self.case.blocks)
+        if self.stepped:
+            _, _, _, wall = self.moments()
+            ctr = np.zeros((nb, 2))
+            for b in bodies:
+                ctr[b.block] = b.center()
+            tq = self.wall_torque(ctr)
+            for b in bodies:
+                b.update(dt, wall[b.block, 1:3], tq[b.block])
+        else:
+            for b in bodies:
+                b.update(dt, np.zeros(2), 0.0)
+        A = np.array(self.case.motion(self.t + dt), dtype=np.float64)
+        for b in bodies:
+            A[b.block] = b.affine()
+        self.move_mesh(self.t + dt, A)
         self.overset_connect()
         self.step(dt, n_inner)
 
@@ -325,3 +360,37 @@ def advance_batch(solvers, n_inner=None):
     for i, s in enumerate(solvers):
         s._t_new = t_new[i]
         s.t = t_new[i]
+
+
+class RigidBody:
+    """Rigid body carried by one block (3 degrees of freedom in 2D): the
+    displacement of its reference centre, its rotation angle and their
+    rates.  update() applies the gas force and torque per unit depth over one
+    step, rates first, then positions (semi-implicit Euler); affine() is the
+    block's map x = R (x_ref - c) + c + displacement."""
+
+    def __init__(self, block, mass, inertia, center, velocity=(0.0, 0.0), omega=0.0):
+        self.block = int(block)
+        self.mass = float(mass)
+        self.inertia = float(inertia)
+        self.c_ref = np.asarray(center, dtype=np.float64)
+        self.disp = np.zeros(2)
+        self.angle = 0.0
+        self.vel = np.asarray(velocity, dtype=np.float64).copy()
+        self.omega = float(omega)
+
+    def center(self):
+        return self.c_ref + self.disp
+
+    def update(self, dt, force, torque):
+        self.vel = self.vel + dt * np.asarray(force, dtype=np.float64) / self.mass
+        self.omega = self.omega + dt * float(torque) / self.inertia
+        self.disp = self.disp + dt * self.vel
+        self.angle = self.angle + dt * self.omega
+
+    def affine(self):
+        co, si = np.cos(self.angle), np.sin(self.angle)
+        cx, cy = self.c_ref
+        b0 = cx + self.disp[0] - (co * cx - si * cy)
+        b1 = cy + self.disp[1] - (si * cx + co * cy)
+        return np.array([co, -si, si, co, b0, b1])

@@ -17,6 +17,8 @@ Configurations (nondimensional, rho0 = T0 = R = L = 1):
             separation and pitch (2D stand-in for the TSTO case of Sec. 4.3).
   mems_batch  many independent `mems` instances of uneven sizes, velocity
             grids, Knudsen numbers and wall temperatures (batched serving).
+  particle  a free rigid cylinder released in a closed box of gas at rest,
+            moved by the gas force and torque (Newton-Euler coupling).
 The paper's own geometries exist only as missing figures; these synthetic
 cases carry their sizes, regimes and motion types.
 """
@@ -308,6 +310,37 @@ def tsto(nbi=512, nbj=256, noi=192, noj=48, nv=64, vmax=15.0, Kn=0.01,
     return Case("tsto", K, Pr, omega, mu_ref_from_knudsen(Kn, omega), nv, nv,
                 (-vmax, vmax, -vmax, vmax), [bg, wedge, cyl], (1.0, uinf, 0.0, 1.0),
                 dt, n_inner, n_steps, motion, prim, meta=dict(Kn=Kn, uinf=uinf))
+
+
+def particle(nbi=128, nbj=64, noi=64, noj=16, nv=24, vmax=5.0, Kn=0.1, radius=0.1, r_out=0.3,
+             stretch=1.08, u0=(0.3, 0.0), omega0=0.0, density_ratio=10.0, n_steps=100, n_inner=10,
+             cfl=10.0, seed=0, omega=0.81, Pr=2.0 / 3.0, K=0) -> Case:
+    """Free particle: a rigid cylinder (radius `radius`, density
+    `density_ratio` times the gas density) in a closed diffuse box
+    [0,2]x[0,1] of gas at rest at T0 = 1, released from the box centre with
+    velocity u0 and spin omega0; its motion follows the gas force and torque
+    (Newton-Euler, Sec. 3 Step 1), so `motion` is the identity and the
+    caller supplies the body's map.  meta: mass and moment of inertia per
+    unit depth, reference centre, initial velocity and spin."""
+    c = (1.0, 0.5)
+    bg = BlockSpec(nbi, nbj, False, (BC_WALL,) * 4, (1.0,) * 4,
+                   cartesian_nodes(nbi, nbj, 0.0, 2.0, 0.0, 1.0), priority=0)
+    og = BlockSpec(noi, noj, True, (BC_NONE, BC_NONE, BC_WALL, BC_OVERSET), (0.0, 0.0, 1.0, 0.0),
+                   ogrid_nodes(noi, noj, ellipse_contour(c, radius, radius), c, r_out, stretch),
+                   priority=1)
+
+    def motion(t):
+        return _affine_identity(2)
+
+    h = min(2.0 / nbi, 1.0 / nbj)
+    dt = cfl * h / (2.0 * vmax)
+    n = bg.ncells + og.ncells
+    mass = density_ratio * math.pi * radius * radius
+    return Case("particle", K, Pr, omega, mu_ref_from_knudsen(Kn, omega), nv, nv,
+                (-vmax, vmax, -vmax, vmax), [bg, og], (1.0, 0.0, 0.0, 1.0), dt, n_inner, n_steps,
+                motion, _init_noise(n, seed, 0.0),
+                meta=dict(Kn=Kn, mass=mass, inertia=0.5 * mass * radius * radius, center=c,
+                          u0=tuple(u0), omega0=omega0, body_block=1))
 
 
 def overlap_gap_layers(nbi, noj, stretch, r_out, r_body, n_fringe=2, cells=3.0, n_min=2):

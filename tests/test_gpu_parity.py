@@ -354,3 +354,31 @@ def test_four_velocities_per_sweep_thread(prec):
         r.step()
         field = r.status == 0
         assert rel(c.moments()[0][field], r.state.W[field]) < 1e-5
+
+
+@pytest.mark.parametrize("u0,omega0", [((0.3, 0.1), 0.0), ((0.0, 0.0), 2.0)])
+def test_free_particle_coupled_motion(u0, omega0):
+    """Newton-Euler coupling (Sec. 3 Step 1): a rigid particle moved by the
+    wall force and torque from the library (ugks_moments, ugks_wall_torque)
+    follows the oracle's coupled run -- same trajectory, connectivity and
+    field after three physical steps."""
+    from oracle import coupling
+    case = wl.particle(nbi=48, nbj=24, noi=32, noj=10, nv=8, r_out=0.3, n_inner=2, u0=u0,
+                       omega0=omega0)
+    m = case.meta
+    body = U.RigidBody(m["body_block"], m["mass"], m["inertia"], m["center"], m["u0"], m["omega0"])
+    ref_body = coupling.Body(m["body_block"], m["mass"], m["inertia"], m["center"], velocity=m["u0"],
+                             omega=m["omega0"])
+    s = U.Solver(case, U.FP64)
+    r = coupling.CoupledRun(case, [ref_body])
+    for _ in range(3):
+        s.advance_coupled([body])
+        r.step_coupled()
+    assert np.allclose(body.vel, ref_body.V, rtol=1e-10, atol=1e-13)
+    assert abs(body.omega - ref_body.w) < 1e-10 * max(abs(ref_body.w), 1e-3)
+    assert np.allclose(body.disp, ref_body.d, rtol=1e-10, atol=1e-14)
+    assert abs(body.angle - ref_body.a) < 1e-12
+    W, q, st, wall = s.moments()
+    assert np.array_equal(st, r.status)
+    field = r.status == 0
+    assert rel(W[field], r.state.W[field]) < 1e-11

@@ -82,7 +82,7 @@ typedef struct ugks_ctx ugks_ctx;
 
 /* Gas, velocity space and solver constants (Sec. 2.1, 2.2). */
 typedef struct {
-  int precision;            /* UGKS_FP64 or UGKS_FP32                         */
+  int precision;            /* UGKS_FP64, UGKS_FP32 or UGKS_BF16F              */
   int nvx, nvy;             /* uniform tensor velocity grid, trapezoid weights */
   double vx_min, vx_max, vy_min, vy_max;
   int K;                    /* internal degrees of freedom (Keff = 1 + K)     */

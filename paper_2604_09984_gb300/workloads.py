@@ -263,11 +263,12 @@ def mems(nbi=256, nbj=128, noi=128, noj=32, nv=32, vmax=6.0, Kn=0.1,
 
 def tsto(nbi=512, nbj=256, noi=192, noj=48, nv=64, vmax=15.0, Kn=0.01,
          mach=8.0, n_steps=500, n_inner=15, cfl=10.0, seed=0,
-         omega=0.74, Pr=0.72, K=2) -> Case:
+         omega=0.74, Pr=0.72, K=2, pitch_rate=0.5, separation=0.02) -> Case:
     """2D hypersonic two-body separation: free stream Ma 8 from the left,
     far field left/top/bottom, outflow right; a 10-degree half-angle wedge of
-    chord 0.3 pitching at 0.5 rad per unit time about its centroid, and a
-    cylinder of radius 0.1 separating in +y at 0.02 u_inf.  Walls at T_inf.
+    chord 0.3 pitching at `pitch_rate` (0.5 rad per unit time) about its
+    centroid, and a cylinder of radius 0.1 separating in +y at `separation`
+    (0.02) times u_inf.  Walls at T_inf.
     Gas initially at rest; time step from the smallest cell of all blocks."""
     gamma = (K + 5.0) / (K + 3.0)
     uinf = mach * math.sqrt(gamma)
@@ -291,12 +292,12 @@ def tsto(nbi=512, nbj=256, noi=192, noj=48, nv=64, vmax=15.0, Kn=0.01,
 
     def motion(t):
         M = _affine_identity(3)
-        a = 0.5 * t
+        a = pitch_rate * t
         ca, sa = math.cos(a), math.sin(a)
         M[1, 0], M[1, 1], M[1, 2], M[1, 3] = ca, -sa, sa, ca
         M[1, 4] = cw[0] - (ca * cw[0] - sa * cw[1])
         M[1, 5] = cw[1] - (sa * cw[0] + ca * cw[1])
-        M[2, 5] = 0.02 * uinf * t
+        M[2, 5] = separation * uinf * t
         return M
 
     # time step from the smallest cell of all blocks (the body grids' wall

@@ -467,11 +467,20 @@ def main():
     torch.cuda.empty_cache()
     fp64 = None
     if not args.no_fp64:
-        s64, ms64, nf64, _, _ = time_arm(case, U.FP64, max(1, args.fp64_steps), 3, device, profile=False,
-                                         tune=not args.no_tune)
+        s64, ms64, nf64, _, prof64 = time_arm(case, U.FP64, max(1, args.fp64_steps), 3, device, profile=True,
+                                              tune=not args.no_tune)
         v64 = nf64 * case.nv * case.n_inner * max(1, args.fp64_steps) / (ms64 * 1e-3)
         fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / max(1, args.fp64_steps),
                 "speedup_fp32_over_fp64": value / world / v64}
+        # %HBM of the FP64 path's dominant streaming group (16-byte pairs)
+        g64 = {g: v for g, v in prof64.items() if v[1] > 0 and algorithmic_bytes(g, 16, nf64, case.nv, s64.nc)}
+        if g64:
+            dom64 = max(g64, key=lambda g: g64[g][0])
+            ms_l = g64[dom64][0] / g64[dom64][1]
+            ach64 = algorithmic_bytes(dom64, 16, nf64, case.nv, s64.nc) / (ms_l * 1e-3) / 1e9
+            fp64["roofline"] = {"kernel": dom64, "bound": "hbm", "achieved": ach64, "peak": peak,
+                                "unit": "GB/s", "frac": ach64 / peak, "ms_per_launch": ms_l,
+                                "note": "the FP64 path is bound by the FP64 pipe, not by HBM"}
         s64.close()
     bf16 = None
     if not args.no_bf16:

@@ -151,7 +151,8 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks,
  * levels, mid-time face lengths / normals / centres, face velocities
  * U_f = mean node velocity and S U.n (so Omega^{n+1} - Omega^n =
  * dt sum S U.n), and the explicit flux-averaging step dt_s per cell.  Call
- * once before every ugks_step (identity for a static mesh).
+ * once before every ugks_step (identity for a static mesh); a second call
+ * before the step replaces the pending move (the old level stays at t).
  * Errors: UGKS_ERR_ARG (t_new <= t), UGKS_ERR_GEOMETRY (some Omega <= 0,
  * detected on the device and reported by the next synchronising call). */
 int ugks_move_mesh(ugks_ctx *ctx, double t_new, const double *affine);

@@ -892,7 +892,9 @@ int ugks_move_mesh(ugks_ctx *ctx, double t_new, const double *affine) {
   if (!(t_new > ctx->t)) return fail(ctx, UGKS_ERR_ARG, "t_new must exceed the current time");
   Dev &d = ctx->d;
   ctx->h_affine.assign(affine, affine + 6 * (size_t)ctx->nblocks);
-  std::swap(d.X_old, d.X_new);
+  // the nodes at t become the old level; a second move before the step
+  // replaces the pending one and keeps the nodes at t
+  if (!ctx->moved) std::swap(d.X_old, d.X_new);
   ctx->launches += launch_upload(d.affine, ctx->h_affine.data(), sizeof(double) * 6 * ctx->nblocks, ctx->st);
   d.dt = t_new - ctx->t;
   d.idt = 1.0 / d.dt;

@@ -407,3 +407,18 @@ def test_full_size_rest_state_stays_at_rest(which):
     assert np.abs(rho - 1.0).max() < 1e-5
     assert np.abs(T - 1.0).max() < 1e-5
     assert np.abs(V).max() < 1e-5
+
+
+def test_second_move_replaces_the_pending_one():
+    """Moving twice before a step keeps the old level at t: the geometry
+    equals that of the second move alone (discrete GCL intact)."""
+    case = small_mems()
+    a = U.Solver(case, U.FP64)
+    b = U.Solver(case, U.FP64)
+    t1, t2 = 0.3 * case.dt, case.dt
+    a.move_mesh(t1)
+    a.move_mesh(t2)
+    b.move_mesh(t2)
+    ga, gb = a.geometry(), b.geometry()
+    for k in ("vol_old", "vol_new", "Sn", "SUn", "dts"):
+        assert np.array_equal(ga[k], gb[k]), k

@@ -422,3 +422,18 @@ def test_second_move_replaces_the_pending_one():
     ga, gb = a.geometry(), b.geometry()
     for k in ("vol_old", "vol_new", "Sn", "SUn", "dts"):
         assert np.array_equal(ga[k], gb[k]), k
+
+
+def test_channel_full_configuration_fp64():
+    """The plain-FP64 channel configuration at its full size (64x32 cells,
+    24x24 velocities on [-5, 5], 10 inner iterations, seeded density noise,
+    oscillating top wall): one physical step agrees with the oracle field by
+    field."""
+    case = wl.channel()
+    s = U.Solver(case, U.FP64)
+    r = Run(case)
+    s.advance()
+    r.step()
+    f, W, q = s.get_state()
+    assert rel(W, r.state.W) < 1e-11
+    assert rel(f.cpu().numpy(), r.state.f) < 1e-11

@@ -73,3 +73,13 @@ def test_spinning_particle_feels_braking_torque():
     assert np.hypot(*F) < 1e-2 * abs(M) / 0.1
     run.step_coupled()
     assert 0.0 < body.w < 2.0 and body.a > 0.0
+
+
+def test_node_placement_matches_prescribed_motion():
+    """The coupled run places nodes with the same affine formula as a
+    prescribed motion: identical coordinates for the same maps."""
+    case = wl.mems(nbi=16, nbj=8, noi=16, noj=6)
+    t = 0.37 / case.meta["freq"]
+    got = coupling.nodes(case, case.motion(t))
+    for a, b in zip(got, case.nodes_at(t)):
+        assert np.array_equal(a, b)

@@ -34,8 +34,6 @@ if ROOT not in sys.path:
 for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
-import numpy as np  # noqa: E402
-
 from paper_2604_09984_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "cell·velocity updates/s per implicit step, FP32-mixed vs FP64 plain; %HBM peak"

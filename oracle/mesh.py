@@ -23,8 +23,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from paper_2604_09984_gb300.workloads import (BC_FARFIELD, BC_NONE, BC_OUTFLOW,
-                                              BC_OVERSET, BC_WALL)
+from paper_2604_09984_gb300.workloads import BC_FARFIELD, BC_NONE, BC_OUTFLOW
 
 NB_CELL, NB_GHOST, NB_NONE = 0, 1, 2
 IM, IP, JM, JP = 0, 1, 2, 3

@@ -38,7 +38,7 @@ import numpy as np
 
 from . import kinetic as kn
 from .mesh import IM, IP, JM, JP, NB_CELL, NB_GHOST, Geometry, Topology
-from paper_2604_09984_gb300.workloads import BC_FARFIELD, BC_NONE, BC_OUTFLOW, BC_WALL
+from paper_2604_09984_gb300.workloads import BC_FARFIELD, BC_OUTFLOW, BC_WALL
 
 FIELD, RECEPTOR, HOLE = 0, 1, 2
 

@@ -175,3 +175,63 @@ def test_overset_run_finite():
     assert np.isfinite(f).all()
     W = run.state.W[run.status == FIELD]
     assert (W[:, 0] > 0).all()
+
+
+def test_idw_weights_follow_inverse_square_law():
+    """Sec. 3.2: the weight of stencil cell j of a receptor is
+    d_j^-2 / sum_l d_l^-2, d the Euclidean distance between the receptor's
+    and the stencil cell's centres at t^{n+1} (vertex centres, computed here
+    with hypot).  A d^-1 law, or equal weights, fail on most rows."""
+    case = small_mems()
+    run = Run(case)
+    conn = run.conn
+    topo = run.topo
+    Xn = topo.concat_nodes(case.nodes_at(0.0))
+    xc = Xn[topo.cell_nodes].mean(axis=1)
+    n_multi = 0
+    n_discriminating = 0
+    for r, cell in enumerate(conn.receptors):
+        row = conn.donors[r]
+        valid = row >= 0
+        assert valid[0]
+        d = np.hypot(xc[row[valid], 0] - xc[cell, 0], xc[row[valid], 1] - xc[cell, 1])
+        want = d ** -2 / (d ** -2).sum()
+        np.testing.assert_allclose(conn.weights[r, valid], want, rtol=1e-12, atol=0)
+        assert np.all(conn.weights[r, ~valid] == 0.0)
+        if valid.sum() > 1:
+            n_multi += 1
+            inv1 = d ** -1 / (d ** -1).sum()
+            if np.abs(inv1 - want).max() > 1e-3:
+                n_discriminating += 1
+    assert n_multi > 0.9 * conn.receptors.size
+    assert n_discriminating > 0.5 * n_multi
+
+
+def test_idw_exact_on_constructed_stencil():
+    """Sec. 3.2 on a hand-placed receptor: a Cartesian donor grid of spacing
+    h, receptor point at (x_d + 0.3 h, y_d - 0.1 h) of donor cell d; the five
+    stencil distances are sqrt(0.3^2+0.1^2) h, and those to the four face
+    neighbours, and the weights are their inverse squares normalised."""
+    h = 0.1
+    ni, nj = 6, 5
+    X = wl.cartesian_nodes(ni, nj, 0.0, ni * h, 0.0, nj * h)
+    bg = wl.BlockSpec(ni, nj, False, (wl.BC_WALL,) * 4, (1.0,) * 4, X)
+    # a one-cell component grid whose only cell is a receptor placed by hand
+    ci, cj = 2, 2
+    xd = np.array([(ci + 0.5) * h, (cj + 0.5) * h])
+    p = xd + np.array([0.3 * h, -0.1 * h])
+    s = 0.02
+    Y = wl.cartesian_nodes(1, 1, p[0] - s, p[0] + s, p[1] - s, p[1] + s)
+    comp = wl.BlockSpec(1, 1, False, (wl.BC_OVERSET,) * 4, (0.0,) * 4, Y, priority=1, n_fringe=1)
+    topo = mesh.Topology([bg, comp])
+    Xn = topo.concat_nodes([X, Y])
+    xc_new = Xn[topo.cell_nodes].mean(axis=1)
+    status = np.zeros(topo.nc, dtype=np.int64)
+    cells = np.array([topo.cell_off[1]])
+    donors, weights, orphan = overset._donors(topo, Xn, xc_new, status, cells)
+    assert orphan == 0
+    d0 = cj * ni + ci
+    assert list(donors[0]) == [d0, d0 - 1, d0 + 1, d0 - ni, d0 + ni]
+    off = [(0.3, -0.1), (1.3, -0.1), (-0.7, -0.1), (0.3, 0.9), (0.3, -1.1)]
+    inv = np.array([1.0 / ((a * a + b * b) * h * h) for a, b in off])
+    np.testing.assert_allclose(weights[0], inv / inv.sum(), rtol=1e-13)

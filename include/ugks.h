@@ -56,9 +56,17 @@ extern "C" {
 
 /* arithmetic of the per-(cell, velocity) path */
 #define UGKS_FP64 0   /* f, fluxes and sweeps in FP64                          */
-#define UGKS_FP32 1   /* f and per-velocity arithmetic in FP32; moments,
-                         macroscopic update, geometry and face coefficients in
-                         FP64 (mixed precision)                                */
+#define UGKS_FP32 1   /* mixed precision: f, the per-velocity flux,
+                         collision, sweep and interpolation arithmetic and the
+                         lane sums of the velocity reductions in FP32 (sums
+                         compensated, combined error-free); in FP64: the
+                         velocity moments W, q and face sums once combined,
+                         the macroscopic update (W', step-7 fix), the per-face
+                         interface state (g0 primitives, micro and time slopes,
+                         collision time, Shakhov heat-flux prefactor, time
+                         integrals q1..q5, rounded once to FP32 for the
+                         velocity loops), the per-cell Shakhov records and all
+                         geometry (volumes, S n, S U.n, dt_s)                  */
 #define UGKS_BF16F 2  /* experiment: as UGKS_FP32, but f itself stored as bf16
                          pairs (4 bytes a cell-velocity, rounded to nearest
                          on every store); errors of ~1e-3 relative, outside

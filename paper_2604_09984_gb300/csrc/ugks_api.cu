@@ -940,6 +940,7 @@ int ugks_step(ugks_ctx *ctx, double dt, int n_inner) {
     }
     // Step 4 (macro LU-SGS) on the side stream, concurrently with the flux
     // divergence of Step 3 on the main stream; Step 5 joins both
+    { Prof p(ctx, UGKS_PROF_MACRO_SWEEP); launch_macro_prep(d, s, fp); }
     CK(cudaEventRecord(ctx->ev_flux, s));
     CK(cudaStreamWaitEvent(ctx->side, ctx->ev_flux, 0));
     { Prof p(ctx, UGKS_PROF_MACRO_SWEEP, ctx->side); launch_macro_sweep(d, ctx->side, ctx->max_nj, fp); }

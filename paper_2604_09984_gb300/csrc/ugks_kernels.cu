@@ -299,51 +299,6 @@ __device__ __forceinline__ bool face_needed(const Dev &d, int f) {
   return d.status[L] == ST_FIELD || (R >= 0 && d.status[R] == ST_FIELD);
 }
 
-// Upwind face value and w.grad f of the upwind cell for velocity k (walls:
-// the interior side only); shared by the reduction pass.
-template <typename T>
-__device__ __forceinline__ void face_upwind(const Dev &d, int fid, int k, T wS, V2<T> &ff,
-                                            V2<T> &wgf) {
-  T vx = dvx<T>(d, k), vy = dvy<T>(d, k);
-  T wx = vx - (T)d.Uf[2 * fid], wy = vy - (T)d.Uf[2 * fid + 1];
-  int kind = d.face_kind[fid];
-  int L = d.face_L[fid];
-  bool useL = (kind == BC_WALL) || wS > T(0), useR = (kind != BC_WALL) && wS < T(0);
-  V2<T> fL = {0, 0}, fR = {0, 0}, gL = {0, 0}, gR = {0, 0};
-  if (!useR) {
-    auto fv = ldF<T>(d, (size_t)L * d.nvp + k);
-    V2<T> fc = {fv.x, fv.y}, gx, gy;
-    grad_f<T>(d, L, k, fc, gx, gy);
-    double sh = (double)d.face_shiftL[fid];
-    T dx = (T)(d.xf[2 * fid] - (d.xc[2 * L] + sh * d.period[2 * L]));
-    T dy = (T)(d.xf[2 * fid + 1] - (d.xc[2 * L + 1] + sh * d.period[2 * L + 1]));
-    fL = {fc.h + dx * gx.h + dy * gy.h, fc.b + dx * gx.b + dy * gy.b};
-    gL = {wx * gx.h + wy * gy.h, wx * gx.b + wy * gy.b};
-  }
-  if (!useL) {
-    int R = d.face_R[fid];
-    if (R >= 0) {
-      auto fv = ldF<T>(d, (size_t)R * d.nvp + k);
-      V2<T> fc = {fv.x, fv.y}, gx, gy;
-      grad_f<T>(d, R, k, fc, gx, gy);
-      T dx = (T)(d.xf[2 * fid] - d.xc[2 * R]), dy = (T)(d.xf[2 * fid + 1] - d.xc[2 * R + 1]);
-      fR = {fc.h + dx * gx.h + dy * gy.h, fc.b + dx * gx.b + dy * gy.b};
-      gR = {wx * gx.h + wy * gy.h, wx * gx.b + wy * gy.b};
-    } else {
-      Prim p = primitive(d.ghostW + 4 * fid, d.Keff);
-      fR = maxwellian<T>((T)p.rho, (T)p.ux, (T)p.uy, (T)p.lam, vx, vy, (T)d.Keff);
-    }
-  }
-  if (useL) {
-    ff = fL; wgf = gL;
-  } else if (useR) {
-    ff = fR; wgf = gR;
-  } else {
-    ff = {T(0.5) * (fL.h + fR.h), T(0.5) * (fL.b + fR.b)};
-    wgf = {T(0.5) * (gL.h + gR.h), T(0.5) * (gL.b + gR.b)};
-  }
-}
-
 __device__ __forceinline__ double spectral_radius(const double *Wf, double nx, double ny, double un,
                                                   int Keff) {
   Prim p = primitive(Wf, Keff);
@@ -411,9 +366,10 @@ template <typename T> __global__ void k_face_scalar(Dev d) {
       gy[m] = avy + jump * (ty / t2);
     }
   }
-  // face state, slopes and time integrals in the arithmetic type (the FP64
-  // pipe of this GPU is a small fraction of the FP32 one)
-  typedef T RT;
+  // face state, slopes, collision time and time integrals in FP64 on every
+  // path (per face, not per velocity); the mixed path rounds the finished
+  // record once to FP32 for its velocity loops
+  typedef double RT;
   RT W0r[4], gxr[4], gyr[4];
   for (int m = 0; m < 4; ++m) { W0r[m] = (RT)W0[m]; gxr[m] = (RT)gx[m]; gyr[m] = (RT)gy[m]; }
   PrimR<RT> p0 = primitive_r<RT>(W0r, d.Keff);
@@ -448,7 +404,7 @@ template <typename T> __global__ void k_face_scalar(Dev d) {
     par[FP_DXRX] = (R >= 0) ? (RT)(d.xf[2 * fid] - d.xc[2 * R]) : RT(0);
     par[FP_DXRY] = (R >= 0) ? (RT)(d.xf[2 * fid + 1] - d.xc[2 * R + 1]) : RT(0);
   }
-  for (int m = 0; m < NFP; ++m) { P[m] = to_double(par[m]); PT[m] = par[m]; }
+  for (int m = 0; m < NFP; ++m) { P[m] = par[m]; PT[m] = (T)par[m]; }
   // Gamma from the mean of the two cells' W (boundary: the cell)
   RT Wf[4];
   for (int m = 0; m < 4; ++m)
@@ -457,7 +413,7 @@ template <typename T> __global__ void k_face_scalar(Dev d) {
   RT pr = pf.rho / (RT(2) * pf.lam);
   RT gamma = (RT(4) + RT(d.Keff)) / (RT(2) + RT(d.Keff));
   RT un = (RT)d.SUn[fid] / (RT)d.S[fid];
-  d.gam[fid] = to_double(fabs(pf.ux * (RT)nx + pf.uy * (RT)ny - un) + sqrt(gamma * pr / pf.rho));
+  d.gam[fid] = fabs(pf.ux * nx + pf.uy * ny - un) + sqrt(gamma * pr / pf.rho);
 }
 
 // Face coefficients, velocity part (one warp per face): the g-part of the
@@ -1590,10 +1546,17 @@ void launch_cell_params(const Dev &d, cudaStream_t s, const double *W, double *o
 // dynamic shared memory of the sweeps: up to the 227 KB a CTA may use
 constexpr size_t kMacroSmem = 227 * 1024;
 constexpr size_t kSweepSmem = 227 * 1024;
+// The sweep records are gathered on the caller's stream before the fork, so
+// the sweep kernel is the first work of the side stream: it then takes its
+// empty SMs before the flux kernel launched beside it fills the GPU.
+void launch_macro_prep(const Dev &d, cudaStream_t s, int fp32) {
+  if (fp32) k_macro_prep<float><<<nblk(d.nc, 256), 256, 0, s>>>(d, reinterpret_cast<float *>(d.mrec));
+  else k_macro_prep<double><<<nblk(d.nc, 256), 256, 0, s>>>(d, reinterpret_cast<double *>(d.mrec));
+}
+
 void launch_macro_sweep(const Dev &d, cudaStream_t s, int rows, int fp32) {
   if (fp32) {
     float *rec = reinterpret_cast<float *>(d.mrec);
-    k_macro_prep<float><<<nblk(d.nc, 256), 256, 0, s>>>(d, rec);
     size_t per = (size_t)rows * NMR32 * sizeof(float);
     size_t base = (MACRO_SMEM_HEAD + 8 * (size_t)rows) * sizeof(float);
     int NS = (int)((kMacroSmem - base) / per);
@@ -1621,7 +1584,6 @@ void launch_macro_sweep(const Dev &d, cudaStream_t s, int rows, int fp32) {
 #undef UGKS_MACRO_F32
   } else {
     double *rec = reinterpret_cast<double *>(d.mrec);
-    k_macro_prep<double><<<nblk(d.nc, 256), 256, 0, s>>>(d, rec);
     k_macro_sweep<double><<<d.nblocks, rows, kMacroSmem, s>>>(d, rec);
   }
   if (fp32) k_macro_post<float><<<nblk(d.nc, 256), 256, 0, s>>>(d);

@@ -12,7 +12,8 @@ void launch_ghost_gradW(const Dev &d, cudaStream_t s);                      // 2
 void launch_face_coef(const Dev &d, cudaStream_t s, int fp32);
 void launch_cell_macro(const Dev &d, cudaStream_t s, int level_n);
 void launch_cell_params(const Dev &d, cudaStream_t s, const double *W, double *out, int fp32);
-void launch_macro_sweep(const Dev &d, cudaStream_t s, int rows, int fp32);
+void launch_macro_prep(const Dev &d, cudaStream_t s, int fp32);
+void launch_macro_sweep(const Dev &d, cudaStream_t s, int rows, int fp32);   // sweep + post (after launch_macro_prep)
 void launch_micro_fwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int threads, int rows,
                       int nsm, int ns, int vpt, int fp32);   // ns: ring depth 2-4, 0 = by rule
 void launch_micro_bwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int threads, int rows,

@@ -1,25 +1,46 @@
-// ugks_tile.cu -- shared-memory tiled kernels for the two velocity-resolved
-// passes over f of every inner iteration (arXiv 2604.09984 Sec. 2.2, Steps 3
-// and 5):
-//   k_face_reduce_tile  velocity sums per face: W0 of the interface
-//                       equilibrium and the f-dependent parts of the macro
-//                       flux (Eq. macroscopicFlux);
-//   k_flux_tile         flux divergence D = sum_faces S F_hat (Eqs.
-//                       microscopicFlux, fullSolution, wall condition), which
-//                       does not depend on the macro predictor, so it runs
-//                       while the macro LU-SGS sweep runs on another stream;
-//   k_residual          the micro residual r from D (reading R4).
-// A CTA stages f of an 8x8 cell tile plus a two-cell halo (ghost cells hold
-// the Maxwellian of their ghost state) for 32 velocities in shared memory,
-// reconstructs from there and evaluates each face of the tile once (one warp
-// per tile row for i-faces, per tile column for j-faces).  Lane = velocity.
+// ugks_tile.cu -- the two velocity-resolved passes over f of every inner
+// iteration (arXiv 2604.09984 Sec. 2.2, Steps 3 and 5) and the micro residual:
+//   k_face_reduce  per face, the velocity sums of W0 (the interface
+//                  equilibrium's moments) and of the f-dependent parts of the
+//                  macro flux (Eq. macroscopicFlux);
+//   k_flux         flux divergence D = sum_faces S F_hat per (cell, velocity)
+//                  (Eqs. microscopicFlux, fullSolution, wall condition); it
+//                  does not depend on the macro predictor, so it runs while
+//                  the macro LU-SGS sweep runs on another stream;
+//   k_residual     the micro residual r from D (reading R4).
+//
+// One CTA per 8x8 cell tile of a block walks all velocity chunks of VK
+// velocities.  Per chunk, f of the tile plus a two-cell halo (ghost cells
+// hold the Maxwellian of their ghost state) is staged in shared memory with
+// asynchronous copies, double-buffered so the next chunk arrives while the
+// current one is reconstructed.  A thread owns one face slot of the tile and
+// one half of every chunk's velocities: everything that does not depend on
+// the velocity -- the face geometry, which region cells are its two sides,
+// their slope cases and inverse Jacobians, and for the flux the interface
+// record of Eq. fullSolution -- is loaded once and kept in registers for the
+// whole velocity loop.  The reduction accumulates its 12 face sums in
+// registers across all chunks (per-chunk partial sums added with an
+// error-free transformation on the FP32 path) and writes them once, with no
+// atomics: the result does not depend on scheduling.
+#include <cstdlib>
 #include "ugks_internal.cuh"
 #include "ugks_launch.h"
 
 namespace ugks {
 
-constexpr int TX = 8, TY = 8, RW = TX + 4, RH = TY + 4, NR = RW * RH, VK = 32;
-constexpr int TTHREADS = 256;   // 8 warps: one per tile row / column
+constexpr int TX = 8, TY = 8, RW = TX + 4, RH = TY + 4, NR = RW * RH;
+constexpr int NSI = (TX + 1) * TY;          // i-face slots: tile row w, column x = 0..TX
+constexpr int NSLOT = NSI + TX * (TY + 1);  // + j-face slots: tile column w, row y = 0..TY
+constexpr int NHALF = 2;                    // threads per face slot (halves of a chunk)
+constexpr int FTHREADS = NSLOT * NHALF;
+
+// velocities per chunk (VK); row strides of the staged region (VKP: rows of
+// whole 16-byte copies) and of the gradient and face-flux rows (VKG: odd, so
+// the lanes of a warp, which read different cells at one velocity, fall in
+// different banks)
+template <typename T> struct Chunk;
+template <> struct Chunk<float> { static constexpr int VK = 16, VKP = VK + 2, VKG = VK + 1; };
+template <> struct Chunk<double> { static constexpr int VK = 8, VKP = VK, VKG = VK + 1; };
 
 // region cell (i, j) of block b -> cell id (>= 0), ghost (-2 - face id) or
 // none (-1).  Periodic blocks wrap in i.
@@ -41,189 +62,9 @@ __device__ __forceinline__ int region_gid(const Dev &d, const int *bi, int off, 
   return -1;
 }
 
-template <typename T> struct TileSmem {
-  typedef typename Vec2<T>::type T2;
-  T2 *F;        // NR * VK
-  int *gid;     // NR
-  int *flags;   // NR: slope flags | status << 8
-  T *jinv;      // NR * 4
-  T *gprim;     // NR * 4 ghost (rho, ux, uy, lam)
-  __host__ __device__ static constexpr size_t bytes() {
-    return sizeof(T2) * NR * VK + sizeof(int) * 2 * NR + sizeof(T) * 8 * NR;
-  }
-  __device__ void carve(unsigned char *p) {
-    F = reinterpret_cast<T2 *>(p);
-    p += sizeof(T2) * NR * VK;
-    jinv = reinterpret_cast<T *>(p);
-    p += sizeof(T) * 4 * NR;
-    gprim = reinterpret_cast<T *>(p);
-    p += sizeof(T) * 4 * NR;
-    gid = reinterpret_cast<int *>(p);
-    p += sizeof(int) * NR;
-    flags = reinterpret_cast<int *>(p);
-  }
-};
-
-// metadata of the region cells (all threads)
-template <typename T>
-__device__ __forceinline__ void tile_meta(const Dev &d, TileSmem<T> &S, const int *bi, int off, int i0,
-                                          int j0) {
-  for (int r = threadIdx.x; r < NR; r += blockDim.x) {
-    int rx = r % RW, ry = r / RW;
-    int g = region_gid(d, bi, off, i0 - 2 + rx, j0 - 2 + ry);
-    S.gid[r] = g;
-    if (g >= 0) {
-      S.flags[r] = d.slope_flags[g] | (d.status[g] << 8);
-      if (sizeof(T) == 4) {
-        *reinterpret_cast<float4 *>(S.jinv + 4 * r) = d.jinvf[g];
-      } else {
-        for (int m = 0; m < 4; ++m) S.jinv[4 * r + m] = (T)d.jinv[4 * g + m];
-      }
-    } else {
-      S.flags[r] = ST_HOLE << 8;
-      if (g <= -2) {
-        Prim p = primitive(d.ghostW + 4 * (-2 - g), d.Keff);
-        S.gprim[4 * r] = (T)(p.rho * p.lam * M_1_PI); S.gprim[4 * r + 1] = (T)p.ux;
-        S.gprim[4 * r + 2] = (T)p.uy; S.gprim[4 * r + 3] = (T)p.lam;
-      }
-    }
-  }
-}
-
-// f of the region for velocity chunk kbase (warp w loads cells w, w+8, ...)
-template <typename T, int FB>
-__device__ __forceinline__ void tile_load_f(const Dev &d, TileSmem<T> &S, int k, bool kv, T vx, T vy) {
-  typedef typename Vec2<T>::type T2;
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  // real cells: asynchronous copies, all of a lane's in flight at once;
-  // ghost cells: the Maxwellian of their ghost state; no cell: zero
-  for (int r = w; r < NR; r += nw) {
-    int g = S.gid[r];
-    T2 *dst = &S.F[r * VK + lane];
-    if (kv && g >= 0) {
-      if (FB) {                                // bf16 storage: widen on the way in
-        auto v = ldF<T, 1>(d, (size_t)g * d.nvp + k);
-        *dst = T2{v.x, v.y};
-      } else {
-        cp_async<(int)sizeof(T2)>(dst, reinterpret_cast<const T2 *>(d.f) + (size_t)g * d.nvp + k);
-      }
-      continue;
-    }
-    T2 v = {T(0), T(0)};
-    if (kv && g <= -2) {
-      const T *p = S.gprim + 4 * r;
-      V2<T> m = maxwellian_pre<T>(p[0], p[1], p[2], p[3], (T)d.Keff / (T(2) * p[3]), vx, vy);
-      v.x = m.h;
-      v.y = m.b;
-    }
-    *dst = v;
-  }
-  cp_async_commit();
-  cp_async_wait<0>();
-}
-
-// limited gradient of region cell r (a real cell) at this lane (reading R1)
-template <typename T>
-__device__ __forceinline__ void tile_grad(const TileSmem<T> &S, int r, int lane, V2<T> fc, V2<T> &gx,
-                                          V2<T> &gy) {
-  int fl = S.flags[r];
-  V2<T> s[2];
-#pragma unroll
-  for (int dir = 0; dir < 2; ++dir) {
-    int cs = (fl >> (2 * dir)) & 3;
-    int st = dir == 0 ? 1 : RW;
-    V2<T> o = {T(0), T(0)};
-    if (cs == SL_BOTH) {
-      auto m = S.F[(r - st) * VK + lane], p = S.F[(r + st) * VK + lane];
-      o.h = vanleer<T>(fc.h - m.x, p.x - fc.h);
-      o.b = vanleer<T>(fc.b - m.y, p.y - fc.b);
-    } else if (cs == SL_P) {
-      auto p = S.F[(r + st) * VK + lane];
-      o.h = p.x - fc.h;
-      o.b = p.y - fc.b;
-    } else if (cs == SL_M) {
-      auto m = S.F[(r - st) * VK + lane];
-      o.h = fc.h - m.x;
-      o.b = fc.b - m.y;
-    }
-    s[dir] = o;
-  }
-  const T *J = S.jinv + 4 * r;
-  gx.h = J[0] * s[0].h + J[1] * s[1].h;
-  gx.b = J[0] * s[0].b + J[1] * s[1].b;
-  gy.h = J[2] * s[0].h + J[3] * s[1].h;
-  gy.b = J[2] * s[0].b + J[3] * s[1].b;
-}
-
-// Reconstructed value of region cell r at the face (offset dx, dy from its
-// centre) and w.grad f; ghost or missing cells carry no gradient.
-template <typename T>
-__device__ __forceinline__ void tile_side(const TileSmem<T> &S, int r, int lane, T dx, T dy, T wx, T wy,
-                                          V2<T> &f, V2<T> &g) {
-  auto v = S.F[r * VK + lane];
-  V2<T> fc = {v.x, v.y};
-  if (S.gid[r] >= 0) {
-    V2<T> gx, gy;
-    tile_grad<T>(S, r, lane, fc, gx, gy);
-    f = {fc.h + dx * gx.h + dy * gy.h, fc.b + dx * gx.b + dy * gy.b};
-    g = {wx * gx.h + wy * gy.h, wx * gx.b + wy * gy.b};
-  } else {
-    f = fc;       // ghost Maxwellian, no gradient
-    g = {T(0), T(0)};
-  }
-}
-
-// upwind face value and w.grad f for face fid between region cells Lr and Rr
-// (walls: interior side, incident velocities only).  Each lane reconstructs
-// its own upwind cell, so lanes of one face with opposite signs of w.S do not
-// run both sides; only w.S = 0 exactly averages the two sides.
-template <typename T>
-__device__ __forceinline__ void tile_upwind(const Dev &d, const TileSmem<T> &S, const T *P, int kind,
-                                            int Lr, int Rr, int lane, T vx, T vy, T wS, V2<T> &ff,
-                                            V2<T> &wg) {
-  (void)d;
-  T wx = vx - P[FP_UFX], wy = vy - P[FP_UFY];
-  bool wall = kind == BC_WALL;
-  bool useR = !wall && wS < T(0);
-  int U = useR ? Rr : Lr;
-  T dx = useR ? P[FP_DXRX] : P[FP_DXLX], dy = useR ? P[FP_DXRY] : P[FP_DXLY];
-  tile_side<T>(S, U, lane, dx, dy, wx, wy, ff, wg);
-  if (!wall && wS == T(0)) {
-    V2<T> f2, g2;
-    tile_side<T>(S, Rr, lane, P[FP_DXRX], P[FP_DXRY], wx, wy, f2, g2);
-    ff = {T(0.5) * (ff.h + f2.h), T(0.5) * (ff.b + f2.b)};
-    wg = {T(0.5) * (wg.h + g2.h), T(0.5) * (wg.b + g2.b)};
-  }
-}
-
-// S * F_hat of a face at this lane (oriented along the face normal) from its
-// staged record Ps (shared memory), kind and left cell Lg.
-template <typename T>
-__device__ __forceinline__ V2<T> tile_face_flux(const Dev &d, const TileSmem<T> &S, const T *Ps, int kind,
-                                                int Lg, int A, int B, int lane, T vx, T vy) {
-  if (kind == BC_OVERSET) return {T(0), T(0)};
-  __align__(16) T P[NFP];
-#pragma unroll
-  for (int q = 0; q < (int)(NFP * sizeof(T) / 16); ++q)
-    reinterpret_cast<float4 *>(P)[q] = reinterpret_cast<const float4 *>(Ps)[q];
-  int Lr = (S.gid[A] == Lg) ? A : B;
-  int Rr = (Lr == A) ? B : A;
-  T wS = vx * P[FP_SNX] + vy * P[FP_SNY] - P[FP_SUN];
-  if (kind == BC_WALL && !(wS > T(0))) {
-    T wx = vx - P[FP_UFX], wy = vy - P[FP_UFY];
-    T lw = P[FP_LAMW];
-    T Hw = P[FP_RHOW] * (lw * T(M_1_PI)) * r_exp<T>(-lw * (wx * wx + wy * wy));
-    return {wS * Hw, wS * (T)d.Keff / (T(2) * lw) * Hw};
-  }
-  V2<T> ff, wg;
-  tile_upwind<T>(d, S, P, kind, Lr, Rr, lane, vx, vy, wS, ff, wg);
-  V2<T> I = interface_integral<T>(P, vx, vy, ff, wg, (T)d.Keff, (T)d.Kint, (T)d.Pr);
-  return {wS * I.h, wS * I.b};
-}
-
-// Face id, kind and left cell of face `x` of a tile row (dir 0: the i-face
-// left of region column x + 2) or column (dir 1: the j-face below region row
-// x + 2); -1 where the face lies outside the block.
+// Face id of slot (dir, w, x): dir 0 the i-face left of tile column x of tile
+// row w (x = TX: right of the last column), dir 1 the j-face below tile row
+// x of tile column w; -1 where the face lies outside the block.
 __device__ __forceinline__ int tile_face_id(const Dev &d, int dir, int off, int ni, int nj, int i0, int j0,
                                             int w, int x) {
   if (dir == 0) {
@@ -236,136 +77,473 @@ __device__ __forceinline__ int tile_face_id(const Dev &d, int dir, int off, int 
   return (j < nj) ? d.cell_faces[4 * (off + j * ni + i) + 2] : d.cell_faces[4 * (off + (nj - 1) * ni + i) + 3];
 }
 
-// Stage per warp the scalars and the records (N values each, from `src`) of
-// the up to 9 faces a warp walks: lane x keeps face x's id, kind and left
-// cell (read back with shuffles), the records go to the warp's buffer `buf`.
-// Every global load of the walk is issued here, side by side, instead of one
-// dependent chain per face.
-template <typename T, int N>
-__device__ __forceinline__ void tile_stage_faces(const Dev &d, const T *src, int my_fid, int &my_kind,
-                                                 int &my_L, T *buf, int lane) {
-  my_kind = BC_OVERSET;
-  my_L = -1;
-  if (my_fid >= 0) {
-    my_kind = d.face_kind[my_fid];
-    my_L = d.face_L[my_fid];
-  }
-  constexpr int NQ = (int)(N * sizeof(T) / 16);
-  constexpr int ROUNDS = ((TX + 1) * NQ + 31) / 32;
-#pragma unroll
-  for (int r = 0; r < ROUNDS; ++r) {
-    int q = r * 32 + lane;
-    int x = q / NQ, ch = q - (q / NQ) * NQ;
-    bool in = x <= TX;
-    int f = __shfl_sync(0xffffffffu, my_fid, in ? x : 0);
-    int kd = __shfl_sync(0xffffffffu, my_kind, in ? x : 0);
-    if (in && f >= 0 && kd != BC_OVERSET)
-      reinterpret_cast<float4 *>(buf + (size_t)x * N)[ch] =
-          __ldg(reinterpret_cast<const float4 *>(src + (size_t)f * N) + ch);
-  }
-  __syncwarp();
+// Gradient cells: the 10x10 block of region cells (rows and columns 1..10)
+// that can be the upwind side of a tile face; g = (ry - 1) * GW + rx - 1.
+constexpr int GW = TX + 2, NG = GW * (TY + 2);
+__device__ __forceinline__ int region_of_g(int g) {
+  int gy = g / GW;
+  return (gy + 1) * RW + (g - gy * GW) + 1;
+}
+__device__ __forceinline__ int g_of_region(int r) {
+  int ry = r / RW;
+  return (ry - 1) * GW + (r - ry * RW) - 1;
 }
 
-__device__ __forceinline__ int cell_status(const TileSmem<float> &S, int r) { return S.flags[r] >> 8; }
-__device__ __forceinline__ int cell_status(const TileSmem<double> &S, int r) { return S.flags[r] >> 8; }
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { typedef float4 type; };
+template <> struct Vec4<double> { typedef double4 type; };
 
-// ------------------------------------------------------- flux divergence
-template <typename T, int FB> __global__ void __launch_bounds__(TTHREADS) k_flux_tile(Dev d) {
+// Shared memory of both kernels: the double-buffered region of f, the limited
+// Cartesian gradients of the chunk, the velocity table of both buffered
+// chunks, and per region cell its id, slope cases and inverse Jacobian (the
+// ghost Maxwellian's parameters for ghost cells).
+template <typename T> struct FaceSmem {
   typedef typename Vec2<T>::type T2;
+  typedef typename Vec4<T>::type T4;
+  static constexpr int VK = Chunk<T>::VK, VKP = Chunk<T>::VKP, VKG = Chunk<T>::VKG;
+  T2 *F;         // [2][NR][VKP]
+  T4 *G;         // [NG][VKG]: (d_x h, d_x b, d_y h, d_y b)
+  T4 *vt;        // [2][VK]: vx, vy, weight, |v|^2 / 2
+  T4 *J;         // [NR]: inverse Jacobian (real cells), ghost state rho lam / pi, Vx, Vy, lam (ghosts)
+  int *gid;      // [NR]
+  int *fl;       // [NR]: slope cases, 0 for ghost / missing cells
+  __host__ __device__ static constexpr size_t bytes() {
+    return sizeof(T2) * 2 * NR * VKP + sizeof(T4) * NG * VKG + sizeof(T4) * 2 * VK + sizeof(T4) * NR +
+           sizeof(int) * 2 * NR;
+  }
+  __device__ void carve(unsigned char *p) {
+    F = reinterpret_cast<T2 *>(p);
+    p += sizeof(T2) * 2 * NR * VKP;
+    G = reinterpret_cast<T4 *>(p);
+    p += sizeof(T4) * NG * VKG;
+    vt = reinterpret_cast<T4 *>(p);
+    p += sizeof(T4) * 2 * VK;
+    J = reinterpret_cast<T4 *>(p);
+    p += sizeof(T4) * NR;
+    gid = reinterpret_cast<int *>(p);
+    p += sizeof(int) * NR;
+    fl = reinterpret_cast<int *>(p);
+  }
+};
+
+// region ids, slope cases, inverse Jacobians and ghost states (once per CTA)
+template <typename T>
+__device__ __forceinline__ void region_meta(const Dev &d, FaceSmem<T> &S, const int *bi, int off, int i0, int j0) {
+  typedef typename Vec4<T>::type T4;
+  for (int r = threadIdx.x; r < NR; r += blockDim.x) {
+    int rx = r % RW, ry = r / RW;
+    int g = region_gid(d, bi, off, i0 - 2 + rx, j0 - 2 + ry);
+    S.gid[r] = g;
+    T4 J = {T(0), T(0), T(0), T(0)};
+    int fl = 0;
+    if (g >= 0) {
+      fl = d.slope_flags[g];
+      if (sizeof(T) == 4) {
+        float4 j = d.jinvf[g];
+        J.x = (T)j.x; J.y = (T)j.y; J.z = (T)j.z; J.w = (T)j.w;
+      } else {
+        J.x = (T)d.jinv[4 * g]; J.y = (T)d.jinv[4 * g + 1]; J.z = (T)d.jinv[4 * g + 2]; J.w = (T)d.jinv[4 * g + 3];
+      }
+    } else if (g <= -2) {
+      Prim p = primitive(d.ghostW + 4 * (-2 - g), d.Keff);
+      J.x = (T)(p.rho * p.lam * M_1_PI); J.y = (T)p.ux; J.z = (T)p.uy; J.w = (T)p.lam;
+    }
+    S.J[r] = J;
+    S.fl[r] = fl;
+  }
+}
+
+// Issue the copies of velocity chunk `ch` into buffer `buf`: real cells by
+// asynchronous 16-byte copies (bf16 storage: load and widen), ghost cells the
+// Maxwellian of their ghost state, no cell / padding velocities zero; and the
+// chunk's velocity table.  EP velocities per copy.
+template <typename T, int FB>
+__device__ __forceinline__ void stage_chunk(const Dev &d, FaceSmem<T> &S, int ch, int buf) {
+  typedef typename Vec2<T>::type T2;
+  typedef typename Vec4<T>::type T4;
+  constexpr int VK = Chunk<T>::VK, VKP = Chunk<T>::VKP, EP = 16 / (int)sizeof(T2), NP = VK / EP;
+  const int kb = ch * VK;
+  T2 *Fb = S.F + (size_t)buf * NR * VKP;
+  for (int it = threadIdx.x; it < NR * NP; it += blockDim.x) {
+    int r = it / NP, kp = it - (it / NP) * NP;
+    int kk = kp * EP, k = kb + kk;
+    int g = S.gid[r];
+    T2 *dst = Fb + r * VKP + kk;
+    if (k < d.nv && g >= 0) {
+      if (FB) {
+#pragma unroll
+        for (int e = 0; e < EP; ++e) {
+          auto v = ldF<T, 1>(d, (size_t)g * d.nvp + k + e);
+          dst[e] = T2{v.x, v.y};
+        }
+      } else {
+        // k < nv <= nvp, nvp a multiple of 4 and k even: the pair stays in
+        // the cell's row (padding velocities hold zero)
+        cp_async<16>(dst, reinterpret_cast<const T2 *>(d.f) + (size_t)g * d.nvp + k);
+      }
+      continue;
+    }
+#pragma unroll
+    for (int e = 0; e < EP; ++e) {
+      T2 v = {T(0), T(0)};
+      if (k + e < d.nv && g <= -2) {
+        T4 p = S.J[r];
+        V2<T> m = maxwellian_pre<T>(p.x, p.y, p.z, p.w, (T)d.Keff / (T(2) * p.w), dvx<T>(d, k + e), dvy<T>(d, k + e));
+        v.x = m.h;
+        v.y = m.b;
+      }
+      dst[e] = v;
+    }
+  }
+  for (int kk = threadIdx.x; kk < VK; kk += blockDim.x) {
+    int k = kb + kk;
+    T vx = k < d.nv ? dvx<T>(d, k) : T(0), vy = k < d.nv ? dvy<T>(d, k) : T(0);
+    T4 t = {vx, vy, k < d.nv ? dw<T>(d, k) : T(0), T(0.5) * (vx * vx + vy * vy)};
+    S.vt[buf * VK + kk] = t;
+  }
+  cp_async_commit();
+}
+
+// limited slope of one logical direction from the backward / forward
+// differences a, b (reading R1: van Leer where both neighbours exist,
+// one-sided where one does)
+template <typename T> __device__ __forceinline__ T lim_slope(T a, T b, bool hm, bool hp) {
+  T v = vanleer<T>(a, b);
+  return hm ? (hp ? v : a) : (hp ? b : T(0));
+}
+
+// Phase A of a chunk: the limited Cartesian gradient of (h, b) of every
+// gradient cell and chunk velocity (lanes run over velocities; ghost and
+// missing cells carry none).
+template <typename T>
+__device__ __forceinline__ void chunk_gradients(FaceSmem<T> &S, int buf) {
+  typedef typename Vec2<T>::type T2;
+  typedef typename Vec4<T>::type T4;
+  constexpr int VK = Chunk<T>::VK, VKP = Chunk<T>::VKP, VKG = Chunk<T>::VKG;
+  const T2 *Fb = S.F + (size_t)buf * NR * VKP;
+  for (int it = threadIdx.x; it < NG * VK; it += blockDim.x) {
+    int g = it / VK, kk = it - (it / VK) * VK;
+    int r = region_of_g(g);
+    int fl = S.fl[r];
+    T4 G = {T(0), T(0), T(0), T(0)};
+    if (fl) {
+      T4 J = S.J[r];
+      const T2 *c = Fb + r * VKP + kk;
+      T2 fc = c[0], im = c[-VKP], ip = c[VKP], jm = c[-RW * VKP], jp = c[RW * VKP];
+      bool him = fl & 1, hip = fl & 2, hjm = fl & 4, hjp = fl & 8;
+      T sih = lim_slope<T>(fc.x - im.x, ip.x - fc.x, him, hip);
+      T sib = lim_slope<T>(fc.y - im.y, ip.y - fc.y, him, hip);
+      T sjh = lim_slope<T>(fc.x - jm.x, jp.x - fc.x, hjm, hjp);
+      T sjb = lim_slope<T>(fc.y - jm.y, jp.y - fc.y, hjm, hjp);
+      G.x = J.x * sih + J.y * sjh;
+      G.y = J.x * sib + J.y * sjb;
+      G.z = J.z * sih + J.w * sjh;
+      G.w = J.z * sib + J.w * sjb;
+    }
+    S.G[g * VKG + kk] = G;
+  }
+}
+
+// One side of a face: its region cell, its gradient cell, and the vector
+// from its centre to the face centre.
+template <typename T> struct Side {
+  int r, g;
+  T dx, dy;
+};
+
+template <typename T> __device__ __forceinline__ Side<T> make_side(int r, T dx, T dy) {
+  Side<T> s;
+  s.r = r;
+  s.g = g_of_region(r);
+  s.dx = dx;
+  s.dy = dy;
+  return s;
+}
+
+// Reconstructed face value f + dx.grad f and w.grad f of side s at chunk
+// velocity kk.
+template <typename T>
+__device__ __forceinline__ void side_value(const FaceSmem<T> &S, const typename Vec2<T>::type *Fb, int r, int g,
+                                           T dx, T dy, int kk, T wx, T wy, V2<T> &ff, V2<T> &wg) {
+  constexpr int VKP = Chunk<T>::VKP, VKG = Chunk<T>::VKG;
+  auto fc = Fb[r * VKP + kk];
+  auto G = S.G[g * VKG + kk];
+  ff.h = fc.x + dx * G.x + dy * G.z;
+  ff.b = fc.y + dx * G.y + dy * G.w;
+  wg.h = wx * G.x + wy * G.z;
+  wg.b = wx * G.y + wy * G.w;
+}
+
+// Upwind face value and w.grad f (walls: the interior side L only); only
+// w.S = 0 exactly averages the two sides.
+template <typename T>
+__device__ __forceinline__ void upwind(const FaceSmem<T> &S, const typename Vec2<T>::type *Fb, const Side<T> &L,
+                                       const Side<T> &R, bool wall, int kk, T wS, T wx, T wy, V2<T> &ff,
+                                       V2<T> &wg) {
+  if (!wall && wS == T(0)) {
+    V2<T> f1, g1, f2, g2;
+    side_value<T>(S, Fb, L.r, L.g, L.dx, L.dy, kk, wx, wy, f1, g1);
+    side_value<T>(S, Fb, R.r, R.g, R.dx, R.dy, kk, wx, wy, f2, g2);
+    ff = {T(0.5) * (f1.h + f2.h), T(0.5) * (f1.b + f2.b)};
+    wg = {T(0.5) * (g1.h + g2.h), T(0.5) * (g1.b + g2.b)};
+    return;
+  }
+  bool useR = !wall && wS < T(0);
+  side_value<T>(S, Fb, useR ? R.r : L.r, useR ? R.g : L.g, useR ? R.dx : L.dx, useR ? R.dy : L.dy, kk, wx, wy,
+                ff, wg);
+}
+
+// Slot -> (direction, tile row / column w, position x) and the region cells
+// A (lower logical side) and B of the face.
+__device__ __forceinline__ void slot_geom(int slot, int &dir, int &w, int &x, int &A, int &B) {
+  if (slot < NSI) {
+    dir = 0;
+    w = slot / (TX + 1);
+    x = slot - w * (TX + 1);
+    A = (x + 1) + (w + 2) * RW;
+    B = A + 1;
+  } else {
+    int s = slot - NSI;
+    dir = 1;
+    w = s / (TY + 1);
+    x = s - w * (TY + 1);
+    A = (w + 2) + (x + 1) * RW;
+    B = A + RW;
+  }
+}
+
+// error-free sum (Knuth): s + e = a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// ------------------------------------------------------------ face reduction
+// Per owned face (the i- and j-faces on the low side of the tile's cells, and
+// the closing faces at a non-periodic block end) the 12 sums over all
+// velocities: W0 = sum V Psi f_face (interior faces), and the incident-part
+// sums sum V Psi w.S f_face and sum V Psi w.S (w.grad f) (Eq. macroscopicFlux
+// with the time integrals q1, q2 applied afterwards).  Per chunk: staging of
+// the next chunk, gradients (phase A), face sums (phase B); FP32 partial sums
+// of two chunks are folded into a (sum, error) pair by an error-free sum.
+template <typename T, int FB, int MINB> __global__ void __launch_bounds__(FTHREADS, MINB) k_face_reduce(Dev d) {
+  typedef typename Vec2<T>::type T2;
+  typedef typename Vec4<T>::type T4;
+  constexpr int VK = Chunk<T>::VK, VKP = Chunk<T>::VKP, VH = VK / NHALF;
   extern __shared__ __align__(16) unsigned char smraw[];
-  TileSmem<T> S;
+  FaceSmem<T> S;
   S.carve(smraw);
-  T2 *Ds = reinterpret_cast<T2 *>(smraw + TileSmem<T>::bytes());   // TX*TY*VK
-  int tile = blockIdx.x % d.ntiles, vc = blockIdx.x / d.ntiles;
+  int tile = blockIdx.x;
+  int b = d.tiles[3 * tile], i0 = d.tiles[3 * tile + 1], j0 = d.tiles[3 * tile + 2];
+  const int *bi = d.blk_info + 8 * b;
+  int ni = bi[0], nj = bi[1], per = bi[2], off = d.cell_off[b];
+  region_meta<T>(d, S, bi, off, i0, j0);
+  __syncthreads();
+  const int nch = (d.nv + VK - 1) / VK;
+  stage_chunk<T, FB>(d, S, 0, 0);
+  // this thread's face
+  int slot = threadIdx.x % NSLOT, half = threadIdx.x / NSLOT;
+  int dir, w, x, A, B;
+  slot_geom(slot, dir, w, x, A, B);
+  int fid = tile_face_id(d, dir, off, ni, nj, i0, j0, w, x);
+  bool act = false;
+  if (fid >= 0) {
+    int i = dir == 0 ? i0 + x : i0 + w, j = dir == 0 ? j0 + w : j0 + x;
+    bool own = dir == 0 ? ((i < ni && x < TX) || (!per && i == ni)) : ((j < nj && x < TY) || j == nj);
+    act = own && d.face_kind[fid] != BC_OVERSET;
+    if (act) {
+      int Lg = d.face_L[fid], Rg = d.face_R[fid];
+      act = d.status[Lg] == ST_FIELD || (Rg >= 0 && d.status[Rg] == ST_FIELD);
+    }
+  }
+  bool wall = false;
+  T snx = T(0), sny = T(0), sun = T(0), ufx = T(0), ufy = T(0);
+  Side<T> L = make_side<T>(A, T(0), T(0)), R = L;
+  if (act) {
+    wall = d.face_kind[fid] == BC_WALL;
+    __align__(16) T Gr[NFG];
+    load_rec<T, NFG>(reinterpret_cast<const T *>(d.fgeo) + (size_t)fid * NFG, Gr);
+    snx = Gr[FG_SNX]; sny = Gr[FG_SNY]; sun = Gr[FG_SUN]; ufx = Gr[FG_UFX]; ufy = Gr[FG_UFY];
+    int Lr = (S.gid[A] == d.face_L[fid]) ? A : B, Rr = (Lr == A) ? B : A;
+    L = make_side<T>(Lr, Gr[FG_DXLX], Gr[FG_DXLY]);
+    R = make_side<T>(Rr, Gr[FG_DXRX], Gr[FG_DXRY]);
+  }
+  T hi[NFS], lo[NFS], acc[NFS];
+#pragma unroll
+  for (int m = 0; m < NFS; ++m) { hi[m] = T(0); lo[m] = T(0); acc[m] = T(0); }
+  for (int ch = 0; ch < nch; ++ch) {
+    int buf = ch & 1;
+    cp_async_wait<0>();
+    __syncthreads();                       // chunk ch visible; phase B of ch-1 done everywhere
+    if (ch + 1 < nch) stage_chunk<T, FB>(d, S, ch + 1, buf ^ 1);
+    chunk_gradients<T>(S, buf);
+    __syncthreads();
+    if (act) {
+      const T2 *Fb = S.F + (size_t)buf * NR * VKP;
+      const T4 *vt = S.vt + buf * VK;
+#pragma unroll 2
+      for (int q = 0; q < VH; ++q) {
+        int kk = half * VH + q;
+        T4 v = vt[kk];
+        T vx = v.x, vy = v.y, wk = v.z, v2 = v.w;
+        T wS = vx * snx + vy * sny - sun;
+        if (wk == T(0) || (wall && !(wS > T(0)))) continue;
+        V2<T> ff, wg;
+        upwind<T>(S, Fb, L, R, wall, kk, wS, vx - ufx, vy - ufy, ff, wg);
+        T a = wk * ff.h, bb = T(0.5) * wk * ff.b;
+        T p0 = a, p1 = vx * a, p2 = vy * a, p3 = v2 * a + bb;
+        T ga = wk * wg.h, gb = T(0.5) * wk * wg.b;
+        T g0 = ga, g1 = vx * ga, g2 = vy * ga, g3 = v2 * ga + gb;
+        acc[FS_W0 + 0] += p0; acc[FS_W0 + 1] += p1; acc[FS_W0 + 2] += p2; acc[FS_W0 + 3] += p3;
+        acc[FS_FF + 0] += wS * p0; acc[FS_FF + 1] += wS * p1; acc[FS_FF + 2] += wS * p2; acc[FS_FF + 3] += wS * p3;
+        acc[FS_WG + 0] += wS * g0; acc[FS_WG + 1] += wS * g1; acc[FS_WG + 2] += wS * g2; acc[FS_WG + 3] += wS * g3;
+      }
+      if ((ch & 1) || ch + 1 == nch) {
+        if (sizeof(T) == 4) {
+#pragma unroll
+          for (int m = 0; m < NFS; ++m) {
+            float s, e;
+            two_sum((float)hi[m], (float)acc[m], s, e);
+            hi[m] = (T)s;
+            lo[m] += (T)e;
+            acc[m] = T(0);
+          }
+        } else {
+#pragma unroll
+          for (int m = 0; m < NFS; ++m) { hi[m] += acc[m]; acc[m] = T(0); }
+        }
+      }
+    }
+  }
+  // the two halves of a face meet in shared memory (the region buffers are
+  // free once every thread has passed the barrier)
+  __syncthreads();
+  T *xs = reinterpret_cast<T *>(S.F);
+  if (half == 1) {
+#pragma unroll
+    for (int m = 0; m < NFS; ++m) { xs[(2 * m) * NSLOT + slot] = hi[m]; xs[(2 * m + 1) * NSLOT + slot] = lo[m]; }
+  }
+  __syncthreads();
+  if (half == 0 && act) {
+    double *out = d.fsum + (size_t)NFS * fid;
+#pragma unroll
+    for (int m = 0; m < NFS; ++m) {
+      T h2 = xs[(2 * m) * NSLOT + slot], l2 = xs[(2 * m + 1) * NSLOT + slot];
+      double v;
+      if (sizeof(T) == 4) {
+        float s, e;
+        two_sum((float)hi[m], (float)h2, s, e);
+        v = to_double(s) + (to_double(e) + (to_double(lo[m]) + to_double(l2)));
+      } else {
+        v = (double)hi[m] + (double)h2;
+      }
+      out[m] = (wall && m < FS_FF) ? 0.0 : v;     // walls take W0 from the interior cell
+    }
+  }
+}
+
+// -------------------------------------------------------- flux divergence
+// Every face slot of the tile (faces shared with a neighbouring tile are
+// evaluated by both) computes S F_hat per velocity into shared memory; then
+// each (tile cell, velocity) sums its four faces with the cell's orientation
+// signs and stores D.
+template <typename T, int FB> __global__ void __launch_bounds__(FTHREADS) k_flux(Dev d) {
+  typedef typename Vec2<T>::type T2;
+  typedef typename Vec4<T>::type T4;
+  constexpr int VK = Chunk<T>::VK, VKP = Chunk<T>::VKP, VKG = Chunk<T>::VKG, VH = VK / NHALF;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  FaceSmem<T> S;
+  S.carve(smraw);
+  T2 *Fs = reinterpret_cast<T2 *>(smraw + FaceSmem<T>::bytes());        // [NSLOT][VKG]
+  int *cinf = reinterpret_cast<int *>(Fs + (size_t)NSLOT * VKG);          // [TX*TY]: cell id or -1
+  char4 *csg = reinterpret_cast<char4 *>(cinf + TX * TY);                 // [TX*TY]: face signs
+  int tile = blockIdx.x;
   int b = d.tiles[3 * tile], i0 = d.tiles[3 * tile + 1], j0 = d.tiles[3 * tile + 2];
   const int *bi = d.blk_info + 8 * b;
   int ni = bi[0], nj = bi[1], off = d.cell_off[b];
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int k = vc * VK + lane;
-  bool kv = k < d.nv;
-  T vx = kv ? dvx<T>(d, k) : T(0), vy = kv ? dvy<T>(d, k) : T(0);
-  tile_meta<T>(d, S, bi, off, i0, j0);
+  region_meta<T>(d, S, bi, off, i0, j0);
+  for (int c = threadIdx.x; c < TX * TY; c += blockDim.x) {
+    int tx = c % TX, ty = c / TX, i = i0 + tx, j = j0 + ty;
+    int g = (i < ni && j < nj) ? off + j * ni + i : -1;
+    if (g >= 0 && d.status[g] != ST_FIELD) g = -1;
+    cinf[c] = g;
+    csg[c] = g >= 0 ? reinterpret_cast<const char4 *>(d.cell_sgn)[g] : make_char4(0, 0, 0, 0);
+  }
   __syncthreads();
-  tile_load_f<T, FB>(d, S, k, kv, vx, vy);
-  __syncthreads();
-  T *Pw = reinterpret_cast<T *>(smraw + TileSmem<T>::bytes() + sizeof(T2) * TX * TY * VK) +
-          (size_t)w * (TX + 1) * NFP;
-  const T *fparT_base = reinterpret_cast<const T *>(d.fparT);
-  int my_kind, my_L;
-  // i-faces of tile row w
-  {
-    int ty = w, j = j0 + ty;
-    int my_fid = lane <= TX ? tile_face_id(d, 0, off, ni, nj, i0, j0, w, lane) : -1;
-    tile_stage_faces<T, NFP>(d, fparT_base, my_fid, my_kind, my_L, Pw, lane);
-    T2 carry = {T(0), T(0)};
-    if (j < nj) {
-      for (int x = 0; x <= TX; ++x) {
-        int i = i0 + x;
-        if (i > ni) break;
-        int kind = __shfl_sync(0xffffffffu, my_kind, x);
-        int Lg = __shfl_sync(0xffffffffu, my_L, x);
-        int A = (x + 1) + (ty + 2) * RW, B = A + 1;
-        bool lin = x >= 1, rin = x < TX && i < ni;
-        bool need = (lin && cell_status(S, A) == ST_FIELD) || (rin && cell_status(S, B) == ST_FIELD);
-        V2<T> F = {T(0), T(0)};
-        if (need && kv) {
-          F = tile_face_flux<T>(d, S, Pw + (size_t)x * NFP, kind, Lg, A, B, lane, vx, vy);
-          T sA = (S.gid[A] == Lg) ? T(1) : T(-1);
-          if (lin) { carry.x += sA * F.h; carry.y += sA * F.b; }
-          if (lin) Ds[(ty * TX + x - 1) * VK + lane] = carry;
-          carry.x = -sA * F.h;     // the other side sees the opposite orientation
-          carry.y = -sA * F.b;
+  const int nch = (d.nv + VK - 1) / VK;
+  stage_chunk<T, FB>(d, S, 0, 0);
+  int slot = threadIdx.x % NSLOT, half = threadIdx.x / NSLOT;
+  int dir, w, x, A, B;
+  slot_geom(slot, dir, w, x, A, B);
+  int fid = tile_face_id(d, dir, off, ni, nj, i0, j0, w, x);
+  bool act = false;
+  if (fid >= 0 && d.face_kind[fid] != BC_OVERSET) {
+    int Lg = d.face_L[fid], Rg = d.face_R[fid];
+    act = d.status[Lg] == ST_FIELD || (Rg >= 0 && d.status[Rg] == ST_FIELD);
+  }
+  bool wall = false;
+  __align__(16) T P[NFP];
+  Side<T> L = make_side<T>(A, T(0), T(0)), R = L;
+  if (act) {
+    wall = d.face_kind[fid] == BC_WALL;
+    load_rec<T, NFP>(reinterpret_cast<const T *>(d.fparT) + (size_t)fid * NFP, P);
+    int Lr = (S.gid[A] == d.face_L[fid]) ? A : B, Rr = (Lr == A) ? B : A;
+    L = make_side<T>(Lr, P[FP_DXLX], P[FP_DXLY]);
+    R = make_side<T>(Rr, P[FP_DXRX], P[FP_DXRY]);
+  } else {
+#pragma unroll
+    for (int m = 0; m < NFP; ++m) P[m] = T(0);
+  }
+  const T Keff = (T)d.Keff, Kint = (T)d.Kint, Pr = (T)d.Pr;
+  for (int ch = 0; ch < nch; ++ch) {
+    int buf = ch & 1;
+    cp_async_wait<0>();
+    __syncthreads();               // chunk ch visible; the face fluxes of ch-1 consumed
+    if (ch + 1 < nch) stage_chunk<T, FB>(d, S, ch + 1, buf ^ 1);
+    chunk_gradients<T>(S, buf);
+    __syncthreads();
+    const T2 *Fb = S.F + (size_t)buf * NR * VKP;
+    const T4 *vt = S.vt + buf * VK;
+#pragma unroll 2
+    for (int q = 0; q < VH; ++q) {
+      int kk = half * VH + q;
+      T2 Fo = {T(0), T(0)};
+      if (act) {
+        T4 v = vt[kk];
+        T vx = v.x, vy = v.y;
+        T wS = vx * P[FP_SNX] + vy * P[FP_SNY] - P[FP_SUN];
+        T wx = vx - P[FP_UFX], wy = vy - P[FP_UFY];
+        if (wall && !(wS > T(0))) {
+          // reflected part: wall Maxwellian at the face velocity (Eq. maxWalldes)
+          T lw = P[FP_LAMW];
+          T Hw = P[FP_RHOW] * (lw * T(M_1_PI)) * r_exp<T>(-lw * (wx * wx + wy * wy));
+          Fo.x = wS * Hw;
+          Fo.y = wS * Keff / (T(2) * lw) * Hw;
         } else {
-          if (lin) Ds[(ty * TX + x - 1) * VK + lane] = carry;
-          carry.x = T(0);
-          carry.y = T(0);
+          V2<T> ff, wg;
+          upwind<T>(S, Fb, L, R, wall, kk, wS, wx, wy, ff, wg);
+          V2<T> I = interface_integral<T>(P, vx, vy, ff, wg, Keff, Kint, Pr);
+          Fo.x = wS * I.h;
+          Fo.y = wS * I.b;
         }
       }
+      Fs[slot * VKG + kk] = Fo;
     }
-  }
-  __syncthreads();
-  // j-faces of tile column w
-  {
-    int tx = w, i = i0 + tx;
-    int my_fid = lane <= TY ? tile_face_id(d, 1, off, ni, nj, i0, j0, w, lane) : -1;
-    tile_stage_faces<T, NFP>(d, fparT_base, my_fid, my_kind, my_L, Pw, lane);
-    if (i < ni) {
-      for (int y = 0; y <= TY; ++y) {
-        int j = j0 + y;
-        if (j > nj) break;
-        int kind = __shfl_sync(0xffffffffu, my_kind, y);
-        int Lg = __shfl_sync(0xffffffffu, my_L, y);
-        int A = (tx + 2) + (y + 1) * RW, B = A + RW;
-        bool lin = y >= 1, rin = y < TY && j < nj;
-        bool need = (lin && cell_status(S, A) == ST_FIELD) || (rin && cell_status(S, B) == ST_FIELD);
-        if (!(need && kv)) continue;
-        V2<T> F = tile_face_flux<T>(d, S, Pw + (size_t)y * NFP, kind, Lg, A, B, lane, vx, vy);
-        T sA = (S.gid[A] == Lg) ? T(1) : T(-1);
-        if (lin) {
-          T2 &q = Ds[((y - 1) * TX + tx) * VK + lane];
-          q.x += sA * F.h;
-          q.y += sA * F.b;
-        }
-        if (rin) {
-          T2 &q = Ds[(y * TX + tx) * VK + lane];
-          q.x -= sA * F.h;
-          q.y -= sA * F.b;
-        }
-      }
+    __syncthreads();
+    const int kb = ch * VK;
+    for (int it = threadIdx.x; it < TX * TY * VK; it += blockDim.x) {
+      int c = it / VK, kk = it - (it / VK) * VK;
+      int g = cinf[c];
+      if (g < 0 || kb + kk >= d.nv) continue;
+      int tx = c % TX, ty = c / TX;
+      char4 sg = csg[c];
+      T2 a = Fs[(ty * (TX + 1) + tx) * VKG + kk], bq = Fs[(ty * (TX + 1) + tx + 1) * VKG + kk];
+      T2 cq = Fs[(NSI + tx * (TY + 1) + ty) * VKG + kk], dq = Fs[(NSI + tx * (TY + 1) + ty + 1) * VKG + kk];
+      T Dh = (T)sg.x * a.x + (T)sg.y * bq.x + (T)sg.z * cq.x + (T)sg.w * dq.x;
+      T Db = (T)sg.x * a.y + (T)sg.y * bq.y + (T)sg.z * cq.y + (T)sg.w * dq.y;
+      stf<T>(d.Dbuf, (size_t)g * d.nvp + kb + kk, Dh, Db);
     }
-  }
-  __syncthreads();
-  // flux divergence of the tile cells of row w
-  if (!kv) return;
-  int ty = w, j = j0 + ty;
-  if (j >= nj) return;
-  for (int x = 0; x < TX; ++x) {
-    int i = i0 + x;
-    if (i >= ni) break;
-    int r = (x + 2) + (ty + 2) * RW;
-    if (cell_status(S, r) != ST_FIELD) continue;
-    T2 D = Ds[(ty * TX + x) * VK + lane];
-    stf<T>(d.Dbuf, (size_t)S.gid[r] * d.nvp + k, D.x, D.y);
   }
 }
 
@@ -413,131 +591,34 @@ template <typename T, int FB> __global__ void k_residual(Dev d, int first_iter) 
   }
 }
 
-// --------------------------------------------------------- face reduction
-// One CTA per (tile, 32-velocity chunk), like the residual kernel.  Each tile
-// owns the i-faces on the low side of its cells (plus the block's closing
-// face of a non-periodic block when the tile reaches it) and the j-faces on
-// the low side of its cells (plus the closing face).  Per owned face the 12
-// velocity sums of the chunk are reduced across the warp in the arithmetic
-// type (butterfly, every lane ends with the totals) and lane m adds total m
-// to the FP64 face sums with an atomic.
-template <typename T, int FB> __global__ void __launch_bounds__(TTHREADS) k_face_reduce_tile(Dev d) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  TileSmem<T> S;
-  S.carve(smraw);
-  int tile = blockIdx.x % d.ntiles, vc = blockIdx.x / d.ntiles;
-  int b = d.tiles[3 * tile], i0 = d.tiles[3 * tile + 1], j0 = d.tiles[3 * tile + 2];
-  const int *bi = d.blk_info + 8 * b;
-  int ni = bi[0], nj = bi[1], per = bi[2], off = d.cell_off[b];
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int k = vc * VK + lane;
-  bool kv = k < d.nv;
-  T vx = kv ? dvx<T>(d, k) : T(0), vy = kv ? dvy<T>(d, k) : T(0);
-  tile_meta<T>(d, S, bi, off, i0, j0);
-  __syncthreads();
-  tile_load_f<T, FB>(d, S, k, kv, vx, vy);
-  __syncthreads();
-  T wk = kv ? dw<T>(d, k) : T(0);
-  T v2 = T(0.5) * (vx * vx + vy * vy);
-  T *Gw = reinterpret_cast<T *>(smraw + TileSmem<T>::bytes()) + (size_t)w * (TX + 1) * NFG;
-  const T *fgeo = reinterpret_cast<const T *>(d.fgeo);
-  for (int dir = 0; dir < 2; ++dir) {
-    // dir 0: i-faces of tile row w; dir 1: j-faces of tile column w.  Lane x
-    // stages face x: id, kind, left cell, whether a field cell touches it,
-    // and its geometry record.
-    int my_fid = lane <= TX ? tile_face_id(d, dir, off, ni, nj, i0, j0, w, lane) : -1;
-    if (my_fid >= 0) {
-      int i = dir == 0 ? i0 + lane : i0 + w, j = dir == 0 ? j0 + w : j0 + lane;
-      bool own = dir == 0 ? ((i < ni && lane < TX) || (!per && i == ni))   // closing face of a ragged tile too
-                          : ((j < nj && lane < TY) || j == nj);
-      if (!own) my_fid = -1;
-    }
-    int my_need = 0;
-    if (my_fid >= 0) {
-      int Lg = d.face_L[my_fid], Rg = d.face_R[my_fid];
-      my_need = d.status[Lg] == ST_FIELD || (Rg >= 0 && d.status[Rg] == ST_FIELD);
-      if (!my_need) my_fid = -1;
-    }
-    int my_kind, my_L;
-    tile_stage_faces<T, NFG>(d, fgeo, my_fid, my_kind, my_L, Gw, lane);
-    for (int x = 0; x <= (dir == 0 ? TX : TY); ++x) {
-      int fid = __shfl_sync(0xffffffffu, my_fid, x);
-      int kind = __shfl_sync(0xffffffffu, my_kind, x);
-      int Lg = __shfl_sync(0xffffffffu, my_L, x);
-      if (fid < 0 || kind == BC_OVERSET) continue;
-      int A, B;
-      if (dir == 0) { A = (x + 1) + (w + 2) * RW; B = A + 1; }
-      else { A = (w + 2) + (x + 1) * RW; B = A + RW; }
-      T sums[NFS];
-#pragma unroll
-      for (int m = 0; m < NFS; ++m) sums[m] = T(0);
-      bool wall = kind == BC_WALL;
-      if (kv) {
-        __align__(16) T G[NFG];
-#pragma unroll
-        for (int q = 0; q < (int)(NFG * sizeof(T) / 16); ++q)
-          reinterpret_cast<float4 *>(G)[q] = reinterpret_cast<const float4 *>(Gw + (size_t)x * NFG)[q];
-        T wS = vx * G[FG_SNX] + vy * G[FG_SNY] - G[FG_SUN];
-        if (!wall || wS > T(0)) {
-          T Pg[NFP];
-          Pg[FP_UFX] = G[FG_UFX];
-          Pg[FP_UFY] = G[FG_UFY];
-          Pg[FP_DXLX] = G[FG_DXLX];
-          Pg[FP_DXLY] = G[FG_DXLY];
-          Pg[FP_DXRX] = G[FG_DXRX];
-          Pg[FP_DXRY] = G[FG_DXRY];
-          int Lr = (S.gid[A] == Lg) ? A : B;
-          int Rr = (Lr == A) ? B : A;
-          V2<T> ff, wg;
-          tile_upwind<T>(d, S, Pg, kind, Lr, Rr, lane, vx, vy, wS, ff, wg);
-          T p[4] = {wk * ff.h, wk * vx * ff.h, wk * vy * ff.h, wk * (v2 * ff.h + T(0.5) * ff.b)};
-          T g[4] = {wk * wg.h, wk * vx * wg.h, wk * vy * wg.h, wk * (v2 * wg.h + T(0.5) * wg.b)};
-#pragma unroll
-          for (int m = 0; m < 4; ++m) {
-            sums[FS_W0 + m] = wall ? T(0) : p[m];
-            sums[FS_FF + m] = wS * p[m];
-            sums[FS_WG + m] = wS * g[m];
-          }
-        }
-      }
-      // transposed butterfly: 16 slots (12 used) halve at every level, so
-      // 16 shuffles replace 12 x 5; lane pairs end with the total of slot
-      // 8 b4 + 4 b3 + 2 b2 + b1 (b_n = bit n of the lane)
-      T v16[16];
-#pragma unroll
-      for (int m = 0; m < 16; ++m) v16[m] = m < NFS ? sums[m] : T(0);
-#pragma unroll
-      for (int half = 8; half >= 1; half >>= 1) {
-        bool up = lane & (2 * half);
-#pragma unroll
-        for (int q = 0; q < half; ++q) {
-          T send = up ? v16[q] : v16[q + half];
-          T keep = up ? v16[q + half] : v16[q];
-          v16[q] = keep + __shfl_xor_sync(0xffffffffu, send, 2 * half);
-        }
-      }
-      v16[0] += __shfl_xor_sync(0xffffffffu, v16[0], 1);
-      int slotm = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
-      if (!(lane & 1) && slotm < NFS) atomicAdd(&d.fsum[NFS * fid + slotm], to_double(v16[0]));
-    }
-  }
-}
-
-template <typename T> static size_t rhs_smem() {
-  return TileSmem<T>::bytes() + sizeof(typename Vec2<T>::type) * TX * TY * VK +
-         sizeof(T) * (TTHREADS / 32) * (TX + 1) * NFP;
+template <typename T> static size_t flux_smem() {
+  return FaceSmem<T>::bytes() + sizeof(typename Vec2<T>::type) * NSLOT * Chunk<T>::VKG + sizeof(int) * TX * TY +
+         sizeof(char4) * TX * TY;
 }
 template <typename T> static size_t reduce_smem() {
-  return TileSmem<T>::bytes() + sizeof(T) * (TTHREADS / 32) * (TX + 1) * NFG;
+  size_t a = FaceSmem<T>::bytes(), b = sizeof(T) * 2 * NFS * NSLOT;
+  return a > b ? a : b;
+}
+
+// CTAs per SM the face reduction is compiled for: 2 (no register limit
+// below the 96 it uses) or 3 (72 registers, with a few spills); UGKS_REDUCE_MINB
+// selects the variant at context creation (measured choice: see the launcher)
+static int g_reduce_minb = 2;
+
+template <typename T, int FB, int MB> static void reduce_attr() {
+  cudaFuncSetAttribute(k_face_reduce<T, FB, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)reduce_smem<T>());
 }
 
 void tile_setup() {
-  cudaFuncSetAttribute(k_flux_tile<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_smem<float>());
-  cudaFuncSetAttribute(k_flux_tile<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_smem<float>());
-  cudaFuncSetAttribute(k_flux_tile<double, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhs_smem<double>());
-  cudaFuncSetAttribute(k_face_reduce_tile<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)reduce_smem<float>());
-  cudaFuncSetAttribute(k_face_reduce_tile<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)reduce_smem<float>());
-  cudaFuncSetAttribute(k_face_reduce_tile<double, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)reduce_smem<double>());
+  cudaFuncSetAttribute(k_flux<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)flux_smem<float>());
+  cudaFuncSetAttribute(k_flux<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)flux_smem<float>());
+  cudaFuncSetAttribute(k_flux<double, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)flux_smem<double>());
+  reduce_attr<float, 0, 2>();
+  reduce_attr<float, 1, 2>();
+  reduce_attr<double, 0, 2>();
+  reduce_attr<float, 0, 3>();
+  reduce_attr<float, 1, 3>();
+  if (const char *e = getenv("UGKS_REDUCE_MINB")) g_reduce_minb = atoi(e) == 3 ? 3 : 2;
 }
 
 int tile_count(int ni, int nj) { return ((ni + TX - 1) / TX) * ((nj + TY - 1) / TY); }
@@ -548,11 +629,9 @@ void tile_origins(int ni, int nj, int *out) {   // (i0, j0) pairs
 }
 
 void launch_flux_tile(const Dev &d, cudaStream_t s, int fp32) {
-  int nchunks = (d.nv + VK - 1) / VK;
-  int grid = d.ntiles * nchunks;
-  if (fp32 && d.fbf) k_flux_tile<float, 1><<<grid, TTHREADS, rhs_smem<float>(), s>>>(d);
-  else if (fp32) k_flux_tile<float, 0><<<grid, TTHREADS, rhs_smem<float>(), s>>>(d);
-  else k_flux_tile<double, 0><<<grid, TTHREADS, rhs_smem<double>(), s>>>(d);
+  if (fp32 && d.fbf) k_flux<float, 1><<<d.ntiles, FTHREADS, flux_smem<float>(), s>>>(d);
+  else if (fp32) k_flux<float, 0><<<d.ntiles, FTHREADS, flux_smem<float>(), s>>>(d);
+  else k_flux<double, 0><<<d.ntiles, FTHREADS, flux_smem<double>(), s>>>(d);
 }
 void launch_residual(const Dev &d, cudaStream_t s, int first_iter, int fp32) {
   int pairs = (d.nv + 1) / 2;
@@ -564,12 +643,16 @@ void launch_residual(const Dev &d, cudaStream_t s, int first_iter, int fp32) {
 }
 
 void launch_face_reduce_tile(const Dev &d, cudaStream_t s, int fp32) {
-  int nchunks = (d.nv + VK - 1) / VK;
-  cudaMemsetAsync(d.fsum, 0, sizeof(double) * NFS * (size_t)d.nf, s);
-  int grid = d.ntiles * nchunks;
-  if (fp32 && d.fbf) k_face_reduce_tile<float, 1><<<grid, TTHREADS, reduce_smem<float>(), s>>>(d);
-  else if (fp32) k_face_reduce_tile<float, 0><<<grid, TTHREADS, reduce_smem<float>(), s>>>(d);
-  else k_face_reduce_tile<double, 0><<<grid, TTHREADS, reduce_smem<double>(), s>>>(d);
+  size_t sm = fp32 ? reduce_smem<float>() : reduce_smem<double>();
+  if (fp32 && g_reduce_minb == 3) {
+    if (d.fbf) k_face_reduce<float, 1, 3><<<d.ntiles, FTHREADS, sm, s>>>(d);
+    else k_face_reduce<float, 0, 3><<<d.ntiles, FTHREADS, sm, s>>>(d);
+  } else if (fp32) {
+    if (d.fbf) k_face_reduce<float, 1, 2><<<d.ntiles, FTHREADS, sm, s>>>(d);
+    else k_face_reduce<float, 0, 2><<<d.ntiles, FTHREADS, sm, s>>>(d);
+  } else {
+    k_face_reduce<double, 0, 2><<<d.ntiles, FTHREADS, sm, s>>>(d);
+  }
 }
 
 }  // namespace ugks

@@ -352,6 +352,123 @@ template <typename T> __device__ __forceinline__ const T *fparT(const Dev &d, in
   return reinterpret_cast<const T *>(d.fparT) + (size_t)f * NFP;
 }
 
+// Bivariate polynomials sum_{a+b<=D} c_ab cx^a cy^b, coefficients stored
+// degree-major (index (a+b)(a+b+1)/2 + b), for the equilibrium parts of the
+// interface flux: on the tensor velocity grid every such term is the face
+// Maxwellian times a polynomial in c = v - U0.
+template <int D, typename R = float> struct Poly2 {
+  static constexpr int N = (D + 1) * (D + 2) / 2;
+  R c[N];
+  __host__ __device__ static constexpr int idx(int a, int b) { return (a + b) * (a + b + 1) / 2 + b; }
+};
+template <int D, typename R = float> __device__ __forceinline__ Poly2<D, R> p2_zero() {
+  Poly2<D, R> r;
+#pragma unroll
+  for (int i = 0; i < Poly2<D, R>::N; ++i) r.c[i] = R(0);
+  return r;
+}
+// a0 + ax cx + ay cy
+template <typename R = float> __device__ __forceinline__ Poly2<1, R> p2_lin(R a0, R ax, R ay) {
+  Poly2<1, R> r;
+  r.c[0] = a0; r.c[Poly2<1, R>::idx(1, 0)] = ax; r.c[Poly2<1, R>::idx(0, 1)] = ay;
+  return r;
+}
+template <int D1, int D2, typename R>
+__device__ __forceinline__ Poly2<D1 + D2, R> p2_mul(const Poly2<D1, R> &x, const Poly2<D2, R> &y) {
+  Poly2<D1 + D2, R> r = p2_zero<D1 + D2, R>();
+#pragma unroll
+  for (int s1 = 0; s1 <= D1; ++s1)
+#pragma unroll
+    for (int b1 = 0; b1 <= s1; ++b1)
+#pragma unroll
+      for (int s2 = 0; s2 <= D2; ++s2)
+#pragma unroll
+        for (int b2 = 0; b2 <= s2; ++b2)
+          r.c[Poly2<D1 + D2, R>::idx(s1 - b1 + s2 - b2, b1 + b2)] +=
+              x.c[Poly2<D1, R>::idx(s1 - b1, b1)] * y.c[Poly2<D2, R>::idx(s2 - b2, b2)];
+  return r;
+}
+// alpha x + beta y (degrees D1 <= D2)
+template <int D1, int D2, typename R>
+__device__ __forceinline__ Poly2<D2, R> p2_axpby(R alpha, const Poly2<D1, R> &x, R beta, const Poly2<D2, R> &y) {
+  Poly2<D2, R> r;
+#pragma unroll
+  for (int i = 0; i < Poly2<D2, R>::N; ++i) r.c[i] = beta * y.c[i] + (i < Poly2<D1, R>::N ? alpha * x.c[i] : R(0));
+  return r;
+}
+// sum_ab c_ab Mx[a] My[b]
+template <int D, typename R>
+__device__ __forceinline__ R p2_sum(const Poly2<D, R> &x, const R *Mx, const R *My) {
+  R s = R(0);
+#pragma unroll
+  for (int t = 0; t <= D; ++t)
+#pragma unroll
+    for (int b = 0; b <= t; ++b) s += x.c[Poly2<D, R>::idx(t - b, b)] * (Mx[t - b] * My[b]);
+  return s;
+}
+// value at (x, y) of a cubic in the layout above (Horner, 9 fused multiply-adds)
+template <typename R> __device__ __forceinline__ R poly3_at(const R *c, R x, R y) {
+  R yy = c[0] + y * (c[2] + y * (c[5] + y * c[9]));
+  R u = c[1] + y * (c[4] + y * c[8]);
+  R w = c[3] + y * c[7] + x * c[6];
+  return yy + x * (u + x * w);
+}
+
+// Equilibrium factors of the time-integrated interface distribution (Eq.
+// fullSolution averaged over dt_s, Shakhov g0+ of Sec. 2.1) as cubics in
+// c = v - U0 from a face record P: the interface distribution of one
+// velocity is
+//   h: q1 f + q2 w.grad f + H ih(c),   b: q1 f_b + q2 w.grad f_b + H ib(c),
+// with H = rho0 lam0/pi exp(-lam0 c^2): ih = q3 (1 + g0+/g0) + q4 (w.(a.Psi))
+// + q5 (A.Psi) in reduced form, ib the same for b (including its B/H =
+// Keff/(2 lam0) factor).
+template <typename R>
+__device__ __forceinline__ void interface_polys(const R *P, R Keff, R Kint, Poly2<3, R> &ih, Poly2<3, R> &ib) {
+  R ux = P[FP_UX], uy = P[FP_UY], lam = P[FP_LAM], il = P[FP_IL];
+  const R *ax = P + FP_AX, *ay = P + FP_AY, *at = P + FP_AT;
+  Poly2<1, R> vxp = p2_lin<R>(ux, R(1), R(0)), vyp = p2_lin<R>(uy, R(0), R(1));
+  Poly2<2, R> v2 = p2_axpby(R(1), p2_mul(vxp, vxp), R(1), p2_mul(vyp, vyp));
+  Poly2<2, R> c2 = p2_zero<2, R>();
+  c2.c[Poly2<2, R>::idx(2, 0)] = R(1);
+  c2.c[Poly2<2, R>::idx(0, 2)] = R(1);
+  auto slope = [&](const R *s) {     // s0 + s1 vx + s2 vy + s3 v^2 / 2
+    Poly2<2, R> r = p2_axpby(s[1], vxp, R(0.5) * s[3], v2);
+    r = p2_axpby(s[2], vyp, R(1), r);
+    r.c[0] += s[0];
+    return r;
+  };
+  Poly2<2, R> bx = slope(ax), by = slope(ay), bt = slope(at);
+  Poly2<1, R> wxp = p2_lin<R>(ux - P[FP_UFX], R(1), R(0)), wyp = p2_lin<R>(uy - P[FP_UFY], R(0), R(1));
+  R eh = P[FP_EH], eb = P[FP_EB];
+  Poly2<2, R> bxh = bx, byh = by, bxb = bx, byb = by;
+  bxh.c[0] += ax[3] * eh; byh.c[0] += ay[3] * eh;
+  bxb.c[0] += ax[3] * eb; byb.c[0] += ay[3] * eb;
+  Poly2<3, R> sgh = p2_axpby(R(1), p2_mul(wxp, bxh), R(1), p2_mul(wyp, byh));
+  Poly2<3, R> sgb = p2_axpby(R(1), p2_mul(wxp, bxb), R(1), p2_mul(wyp, byb));
+  Poly2<2, R> sth = bt, stb = bt;
+  sth.c[0] += at[3] * eh;
+  stb.c[0] += at[3] * eb;
+  Poly2<1, R> pc = p2_lin<R>(R(0), P[FP_PREF] * P[FP_QX], P[FP_PREF] * P[FP_QY]);
+  Poly2<2, R> th = p2_axpby(R(0), c2, R(2) * lam, c2);
+  th.c[0] -= R(4);                                        // 2 lam c^2 - 4
+  Poly2<2, R> tb = p2_axpby(R(0), c2, R(2) * lam * Keff * il, c2);
+  tb.c[0] += (-R(2) * Keff - R(2) * Kint) * il;           // ((2 lam c^2 - 2) Keff - 2 Kint) / (2 lam)
+  R q3 = P[FP_Q3], q4 = P[FP_Q4], q5 = P[FP_Q5];
+  ih = p2_axpby(q3, p2_mul(pc, th), q4, sgh);
+  ih = p2_axpby(q5, sth, R(1), ih);
+  ih.c[0] += q3;
+  R kil = Keff * il;
+  ib = p2_axpby(q3, p2_mul(pc, tb), q4 * kil, sgb);
+  ib = p2_axpby(q5 * kil, stb, R(1), ib);
+  ib.c[0] += q3 * kil;
+}
+
+// Store the two cubics into a face record (FP_IH, FP_IB).
+template <typename R> __device__ __forceinline__ void store_polys(R *P, const Poly2<3, R> &ih, const Poly2<3, R> &ib) {
+#pragma unroll
+  for (int m = 0; m < 10; ++m) { P[FP_IH + m] = ih.c[m]; P[FP_IB + m] = ib.c[m]; }
+}
+
 // S * time-averaged interface flux of velocity k through face fid, oriented
 // along the face normal (L -> R, outward for boundary faces).
 template <typename T> __device__ V2<T> face_flux(const Dev &d, int fid, int k) {

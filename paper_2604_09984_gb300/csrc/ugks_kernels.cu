@@ -382,6 +382,7 @@ template <typename T> __global__ void k_face_scalar(Dev d) {
   RT qi[5];
   time_integrals_r<RT>(dtsr, tau, qi);
   RT par[NFP];
+  for (int m = 0; m < NFP; ++m) par[m] = RT(0);
   par[FP_RHO] = p0.rho; par[FP_UX] = p0.ux; par[FP_UY] = p0.uy; par[FP_LAM] = p0.lam;
   par[FP_QX] = (RT)q0x; par[FP_QY] = (RT)q0y;
   for (int m = 0; m < 4; ++m) { par[FP_AX + m] = ax[m]; par[FP_AY + m] = ay[m]; par[FP_AT + m] = At[m]; }
@@ -419,57 +420,6 @@ template <typename T> __global__ void k_face_scalar(Dev d) {
 // Face coefficients, velocity part (one warp per face): the g-part of the
 // macro flux by a sum over the discrete velocities, the wall density rho_w
 // (Eq. maxWalldes) and the total S-weighted macro flux (Eq. macroscopicFlux).
-// Bivariate polynomials sum_{a+b<=D} c_ab cx^a cy^b (FP32) for the
-// separable velocity sums of the interior-face equilibrium flux below.
-template <int D> struct Poly2 {
-  static constexpr int N = (D + 1) * (D + 2) / 2;
-  float c[N];
-  __device__ static constexpr int idx(int a, int b) { return (a + b) * (a + b + 1) / 2 + b; }
-};
-template <int D> __device__ __forceinline__ Poly2<D> p2_zero() {
-  Poly2<D> r;
-#pragma unroll
-  for (int i = 0; i < Poly2<D>::N; ++i) r.c[i] = 0.f;
-  return r;
-}
-// a0 + ax cx + ay cy
-__device__ __forceinline__ Poly2<1> p2_lin(float a0, float ax, float ay) {
-  Poly2<1> r;
-  r.c[0] = a0; r.c[Poly2<1>::idx(1, 0)] = ax; r.c[Poly2<1>::idx(0, 1)] = ay;
-  return r;
-}
-template <int D1, int D2> __device__ __forceinline__ Poly2<D1 + D2> p2_mul(const Poly2<D1> &x, const Poly2<D2> &y) {
-  Poly2<D1 + D2> r = p2_zero<D1 + D2>();
-#pragma unroll
-  for (int s1 = 0; s1 <= D1; ++s1)
-#pragma unroll
-    for (int b1 = 0; b1 <= s1; ++b1)
-#pragma unroll
-      for (int s2 = 0; s2 <= D2; ++s2)
-#pragma unroll
-        for (int b2 = 0; b2 <= s2; ++b2)
-          r.c[Poly2<D1 + D2>::idx(s1 - b1 + s2 - b2, b1 + b2)] +=
-              x.c[Poly2<D1>::idx(s1 - b1, b1)] * y.c[Poly2<D2>::idx(s2 - b2, b2)];
-  return r;
-}
-// alpha x + beta y (degrees D1 <= D2)
-template <int D1, int D2>
-__device__ __forceinline__ Poly2<D2> p2_axpby(float alpha, const Poly2<D1> &x, float beta, const Poly2<D2> &y) {
-  Poly2<D2> r;
-#pragma unroll
-  for (int i = 0; i < Poly2<D2>::N; ++i) r.c[i] = beta * y.c[i] + (i < Poly2<D1>::N ? alpha * x.c[i] : 0.f);
-  return r;
-}
-// sum_ab c_ab Mx[a] My[b]
-template <int D> __device__ __forceinline__ float p2_sum(const Poly2<D> &x, const float *Mx, const float *My) {
-  float s = 0.f;
-#pragma unroll
-  for (int t = 0; t <= D; ++t)
-#pragma unroll
-    for (int b = 0; b <= t; ++b) s += x.c[Poly2<D>::idx(t - b, b)] * (Mx[t - b] * My[b]);
-  return s;
-}
-
 // Equilibrium part of the macro flux of an interior face (the velocity sum
 // of w wS Psi (q3 (g + g+) + q4 g (a.w Psi) + q5 g (A Psi)) in reduced form,
 // Eqs. fullSolution / macroscopicFlux) through the tensor structure of the
@@ -506,45 +456,10 @@ __device__ __forceinline__ void face_eq_flux_separable(const Dev &d, const float
       mx[a] += __shfl_xor_sync(0xffffffffu, mx[a], o);
       my[a] += __shfl_xor_sync(0xffffffffu, my[a], o);
     }
-  // polynomial factors in c (v = c + U0)
-  float Keff = (float)d.Keff, Kint = (float)d.Kint, il = P[FP_IL];
-  const float *ax = P + FP_AX, *ay = P + FP_AY, *at = P + FP_AT;
+  Poly2<3> ih, ib;
+  interface_polys<float>(P, (float)d.Keff, (float)d.Kint, ih, ib);
   Poly2<1> vxp = p2_lin(ux, 1.f, 0.f), vyp = p2_lin(uy, 0.f, 1.f);
   Poly2<2> v2 = p2_axpby(1.f, p2_mul(vxp, vxp), 1.f, p2_mul(vyp, vyp));
-  Poly2<2> c2 = p2_zero<2>();
-  c2.c[Poly2<2>::idx(2, 0)] = 1.f;
-  c2.c[Poly2<2>::idx(0, 2)] = 1.f;
-  auto slope = [&](const float *s) {     // s0 + s1 vx + s2 vy + s3 v^2 / 2
-    Poly2<2> r = p2_axpby(s[1], vxp, 0.5f * s[3], v2);
-    r = p2_axpby(s[2], vyp, 1.f, r);
-    r.c[0] += s[0];
-    return r;
-  };
-  Poly2<2> bx = slope(ax), by = slope(ay), bt = slope(at);
-  Poly2<1> wxp = p2_lin(ux - P[FP_UFX], 1.f, 0.f), wyp = p2_lin(uy - P[FP_UFY], 0.f, 1.f);
-  float eh = P[FP_EH], eb = P[FP_EB];
-  Poly2<2> bxh = bx, byh = by, bxb = bx, byb = by;
-  bxh.c[0] += ax[3] * eh; byh.c[0] += ay[3] * eh;
-  bxb.c[0] += ax[3] * eb; byb.c[0] += ay[3] * eb;
-  Poly2<3> sgh = p2_axpby(1.f, p2_mul(wxp, bxh), 1.f, p2_mul(wyp, byh));
-  Poly2<3> sgb = p2_axpby(1.f, p2_mul(wxp, bxb), 1.f, p2_mul(wyp, byb));
-  Poly2<2> sth = bt, stb = bt;
-  sth.c[0] += at[3] * eh;
-  stb.c[0] += at[3] * eb;
-  Poly2<1> pc = p2_lin(0.f, P[FP_PREF] * P[FP_QX], P[FP_PREF] * P[FP_QY]);
-  Poly2<2> th = p2_axpby(0.f, c2, 2.f * lam, c2);
-  th.c[0] -= 4.f;                                         // 2 lam c^2 - 4
-  Poly2<2> tb = p2_axpby(0.f, c2, 2.f * lam * Keff * il, c2);
-  tb.c[0] += (-2.f * Keff - 2.f * Kint) * il;             // ((2 lam c^2 - 2) Keff - 2 Kint) / (2 lam)
-  float q3 = P[FP_Q3], q4 = P[FP_Q4], q5 = P[FP_Q5];
-  // Ih / g and Ib / g
-  Poly2<3> ih = p2_axpby(q3, p2_mul(pc, th), q4, sgh);
-  ih = p2_axpby(q5, sth, 1.f, ih);
-  ih.c[0] += q3;
-  float kil = Keff * il;
-  Poly2<3> ib = p2_axpby(q3, p2_mul(pc, tb), q4 * kil, sgb);
-  ib = p2_axpby(q5 * kil, stb, 1.f, ib);
-  ib.c[0] += q3 * kil;
   Poly2<1> ws = p2_lin(snx * ux + sny * uy - sun, snx, sny);
   Poly2<4> m0 = p2_mul(ws, ih);
   float hpre = P[FP_HPRE];
@@ -627,6 +542,13 @@ template <typename T> __global__ void __launch_bounds__(256, 2) k_face_coef(Dev 
       PT[FP_RHOW] = (T)rhow;
       for (int m = 0; m < 4; ++m) F[m] += rhow * acc[4 + m];
     }
+    {
+      __align__(16) T pr[NFP];
+      load_rec<T, NFP>(PT, pr);
+      Poly2<3, T> ih, ib;
+      interface_polys<T>(pr, (T)d.Keff, (T)d.Kint, ih, ib);
+      store_polys<T>(PT, ih, ib);
+    }
     for (int m = 0; m < 4; ++m) d.fflux[4 * fid + m] = F[m];
   }
 }
@@ -657,6 +579,16 @@ __global__ void __launch_bounds__(256) k_face_coef_sep(Dev d) {
   }
   float o[4];
   face_eq_flux_separable<FCG>(d, parT, parT[FP_SNX], parT[FP_SNY], parT[FP_SUN], sub, o);
+  if (act) {
+    // the cubics of the interface distribution for the flux pass (lane sub
+    // of the face's group writes coefficients sub, sub + FCG, ...)
+    Poly2<3> ih, ib;
+    interface_polys<float>(parT, (float)d.Keff, (float)d.Kint, ih, ib);
+    float *PT = reinterpret_cast<float *>(d.fparT) + (size_t)NFP * fid;
+#pragma unroll
+    for (int m = 0; m < 20; ++m)
+      if (m % FCG == sub) PT[FP_IH + m] = m < 10 ? ih.c[m] : ib.c[m - 10];
+  }
   if (act && sub < 4) {                           // lane m of the group: component m
     const double *P = d.fpar + (size_t)NFP * fid;
     const double *fs = d.fsum + NFS * fid;

@@ -111,7 +111,10 @@ enum {
   // per-face constants of the velocity loops: rho lam / pi, 1/(2 lam),
   // Keff/(4 lam), (Keff+2)/(4 lam)
   FP_HPRE = 35, FP_IL, FP_EH, FP_EB,
-  NFP = 40
+  // the equilibrium factors of the interface distribution as cubics in
+  // c = v - U0 (10 coefficients each, written by the face-coefficient pass)
+  FP_IH = 40, FP_IB = 50,
+  NFP = 60
 };
 
 // Time integrals q_m = int_0^dts c_m(t) dt (Eq. fullSolution), x = dts/tau;

@@ -214,15 +214,18 @@ template <typename T> __device__ __forceinline__ T lim_slope(T a, T b, bool hm, 
 
 // Phase A of a chunk: the limited Cartesian gradient of (h, b) of every
 // gradient cell and chunk velocity (lanes run over velocities; ghost and
-// missing cells carry none).
+// missing cells carry none).  A thread keeps one chunk velocity and walks
+// the gradient cells with a fixed stride; cells with all four neighbours take
+// the two-sided limiter without the one-sided selections.
 template <typename T>
 __device__ __forceinline__ void chunk_gradients(FaceSmem<T> &S, int buf) {
   typedef typename Vec2<T>::type T2;
   typedef typename Vec4<T>::type T4;
-  constexpr int VK = Chunk<T>::VK, VKP = Chunk<T>::VKP, VKG = Chunk<T>::VKG;
+  constexpr int VK = Chunk<T>::VK, VKP = Chunk<T>::VKP, VKG = Chunk<T>::VKG, GS = FTHREADS / VK;
+  static_assert(FTHREADS % VK == 0, "whole velocity rows per pass");
   const T2 *Fb = S.F + (size_t)buf * NR * VKP;
-  for (int it = threadIdx.x; it < NG * VK; it += blockDim.x) {
-    int g = it / VK, kk = it - (it / VK) * VK;
+  const int kk = threadIdx.x % VK;
+  for (int g = threadIdx.x / VK; g < NG; g += GS) {
     int r = region_of_g(g);
     int fl = S.fl[r];
     T4 G = {T(0), T(0), T(0), T(0)};
@@ -230,11 +233,19 @@ __device__ __forceinline__ void chunk_gradients(FaceSmem<T> &S, int buf) {
       T4 J = S.J[r];
       const T2 *c = Fb + r * VKP + kk;
       T2 fc = c[0], im = c[-VKP], ip = c[VKP], jm = c[-RW * VKP], jp = c[RW * VKP];
-      bool him = fl & 1, hip = fl & 2, hjm = fl & 4, hjp = fl & 8;
-      T sih = lim_slope<T>(fc.x - im.x, ip.x - fc.x, him, hip);
-      T sib = lim_slope<T>(fc.y - im.y, ip.y - fc.y, him, hip);
-      T sjh = lim_slope<T>(fc.x - jm.x, jp.x - fc.x, hjm, hjp);
-      T sjb = lim_slope<T>(fc.y - jm.y, jp.y - fc.y, hjm, hjp);
+      T sih, sib, sjh, sjb;
+      if (fl == 15) {
+        sih = vanleer<T>(fc.x - im.x, ip.x - fc.x);
+        sib = vanleer<T>(fc.y - im.y, ip.y - fc.y);
+        sjh = vanleer<T>(fc.x - jm.x, jp.x - fc.x);
+        sjb = vanleer<T>(fc.y - jm.y, jp.y - fc.y);
+      } else {
+        bool him = fl & 1, hip = fl & 2, hjm = fl & 4, hjp = fl & 8;
+        sih = lim_slope<T>(fc.x - im.x, ip.x - fc.x, him, hip);
+        sib = lim_slope<T>(fc.y - im.y, ip.y - fc.y, him, hip);
+        sjh = lim_slope<T>(fc.x - jm.x, jp.x - fc.x, hjm, hjp);
+        sjb = lim_slope<T>(fc.y - jm.y, jp.y - fc.y, hjm, hjp);
+      }
       G.x = J.x * sih + J.y * sjh;
       G.y = J.x * sib + J.y * sjb;
       G.z = J.z * sih + J.w * sjh;
@@ -382,13 +393,14 @@ template <typename T, int FB, int MINB> __global__ void __launch_bounds__(FTHREA
     if (act) {
       const T2 *Fb = S.F + (size_t)buf * NR * VKP;
       const T4 *vt = S.vt + buf * VK;
-#pragma unroll 2
+#pragma unroll 4
       for (int q = 0; q < VH; ++q) {
         int kk = half * VH + q;
         T4 v = vt[kk];
-        T vx = v.x, vy = v.y, wk = v.z, v2 = v.w;
+        T vx = v.x, vy = v.y, v2 = v.w;
         T wS = vx * snx + vy * sny - sun;
-        if (wk == T(0) || (wall && !(wS > T(0)))) continue;
+        // reflected velocities of a wall carry no f (zero weight, no branch)
+        T wk = (wall && !(wS > T(0))) ? T(0) : v.z;
         V2<T> ff, wg;
         upwind<T>(S, Fb, L, R, wall, kk, wS, vx - ufx, vy - ufy, ff, wg);
         T a = wk * ff.h, bb = T(0.5) * wk * ff.b;
@@ -495,7 +507,7 @@ template <typename T, int FB> __global__ void __launch_bounds__(FTHREADS) k_flux
 #pragma unroll
     for (int m = 0; m < NFP; ++m) P[m] = T(0);
   }
-  const T Keff = (T)d.Keff, Kint = (T)d.Kint, Pr = (T)d.Pr;
+  const T Keff = (T)d.Keff;
   for (int ch = 0; ch < nch; ++ch) {
     int buf = ch & 1;
     cp_async_wait<0>();
@@ -505,7 +517,7 @@ template <typename T, int FB> __global__ void __launch_bounds__(FTHREADS) k_flux
     __syncthreads();
     const T2 *Fb = S.F + (size_t)buf * NR * VKP;
     const T4 *vt = S.vt + buf * VK;
-#pragma unroll 2
+#pragma unroll 4
     for (int q = 0; q < VH; ++q) {
       int kk = half * VH + q;
       T2 Fo = {T(0), T(0)};
@@ -523,9 +535,14 @@ template <typename T, int FB> __global__ void __launch_bounds__(FTHREADS) k_flux
         } else {
           V2<T> ff, wg;
           upwind<T>(S, Fb, L, R, wall, kk, wS, wx, wy, ff, wg);
-          V2<T> I = interface_integral<T>(P, vx, vy, ff, wg, Keff, Kint, Pr);
-          Fo.x = wS * I.h;
-          Fo.y = wS * I.b;
+          // Eq. fullSolution averaged over dt_s: q1 f + q2 w.grad f + H ih(c)
+          // (and b), the equilibrium factors as per-face cubics in c = v - U0
+          T cx = vx - P[FP_UX], cy = vy - P[FP_UY];
+          T H = P[FP_HPRE] * r_exp<T>(-P[FP_LAM] * (cx * cx + cy * cy));
+          T Ih = P[FP_Q1] * ff.h + P[FP_Q2] * wg.h + H * poly3_at<T>(P + FP_IH, cx, cy);
+          T Ib = P[FP_Q1] * ff.b + P[FP_Q2] * wg.b + H * poly3_at<T>(P + FP_IB, cx, cy);
+          Fo.x = wS * Ih;
+          Fo.y = wS * Ib;
         }
       }
       Fs[slot * VKG + kk] = Fo;

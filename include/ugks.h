@@ -213,17 +213,19 @@ int ugks_advance_batch(ugks_ctx *const *ctx, int n, const double *t_new,
 int ugks_wall_torque(ugks_ctx *ctx, const double *center, double *torque);
 
 /* Sweep autotuner: times the micro LU-SGS sweeps (`reps` timed passes after
- * one warm-up, CUDA events on the stream) for every candidate tile -- (cell,
- * velocity) items per CTA and diagonal step in {256, 512, 1024, 2048} and
- * velocities per thread in {2, 4} (FP32 paths; 2 in FP64) -- with the
- * cp.async ring depth in {2, 3, 4} diagonals chosen separately for the
- * forward and the backward sweep, on the context's own state, and keeps the
- * fastest pair.  Every tile computes the same sweeps (each velocity is swept
- * in the same order), so only the time changes.  f is saved before the
- * trials and restored after them.  Needs a preceding ugks_step (the sweeps
- * read per-cell records the step writes).  `items`, `vpt`, `ring_fwd`,
- * `ring_bwd` (HOST, each may be NULL) receive the choice.  Synchronises the
- * stream.  Errors: UGKS_ERR_ORDER, UGKS_ERR_CUDA. */
+ * one warm-up, CUDA events on the stream) for every candidate -- velocities
+ * per lane in {2, 4} (FP32 paths; 2 in FP64) and, for each, the prefetch ring
+ * depth in {2, 4, 6} steps chosen separately for the forward and the backward
+ * sweep (shallower where shared memory is short) -- on the context's own
+ * state, and keeps the fastest.  The sweeps run as skewed wavefronts (a warp
+ * takes a band of 8 rows, 4 lanes a row; 16 rows, 2 lanes a row when a
+ * block is taller than 256 cells); every candidate sweeps each velocity in
+ * the same lexicographic order, so only the time changes.  f is saved before
+ * the trials and restored after them.  Needs a preceding ugks_step (the
+ * sweeps read per-cell records the step writes).  `items` (the (cell,
+ * velocity) items of one warp step, 32 x velocities per lane), `vpt`,
+ * `ring_fwd`, `ring_bwd` (HOST, each may be NULL) receive the choice.
+ * Synchronises the stream.  Errors: UGKS_ERR_ORDER, UGKS_ERR_CUDA. */
 int ugks_autotune(ugks_ctx *ctx, int reps, int *items, int *vpt, int *ring_fwd, int *ring_bwd);
 
 /* Copy the macroscopic fields to caller memory (host or device pointers,

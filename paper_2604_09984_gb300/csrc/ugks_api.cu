@@ -30,10 +30,10 @@ struct ugks_ctx {
   std::vector<ugks_block_desc> blocks;
   std::vector<int> cell_off, node_off;
   int max_nj = 0;
-  int sweep_threads = 32, nwork = 0, nsm = 0;
+  int sweep_nw = 1, sweep_ql = 4, nwork = 0, nsm = 0;  // micro sweeps: warps per CTA, lanes per row, CTAs
   int nwork_cap = 0;                  // work-list capacity (largest tuning candidate)
-  int sweep_items = 0, sweep_vpt = 2; // micro-sweep tile (0 = by rule) and velocities per thread
-  int ns_fwd = 0, ns_bwd = 0;         // ring depths of the two sweeps (0 = by rule)
+  int sweep_vpt = 2;                  // micro sweeps: velocities per lane
+  int ns_fwd = 4, ns_bwd = 4;         // prefetch ring depths (steps) of the two sweeps
   bool stepped = false;               // a ugks_step has run (sweep records valid)
   int *work = nullptr;
   int *prev_status = nullptr, *n_orphan = nullptr, *blk_order = nullptr;
@@ -131,58 +131,62 @@ struct Carver {
     return ptr;
   }
 };
-
-// Micro-sweep CTA shape for a block of height nj: G threads per row, each
-// with vpt consecutive velocities, so a CTA covers G * vpt velocities.  The
-// tile is sized for about 1024 (cell, velocity) items per diagonal step --
-// enough independent work per step for the SM while the whole sweep stays
-// within about one CTA per SM -- with at most 512 threads and no more
-// velocities than the array holds.  `items` > 0 replaces the 1024 (the
-// autotuner's candidates); UGKS_SWEEP_ITEMS and UGKS_VTILE (velocities per
-// CTA) override by hand where they fit.
-int block_G(int nj, int nvp, int vpt, int items_req = 0) {
-  int r = 1;
-  while (r < nj) r <<= 1;
-  int items = 1024;                        // (cell, velocity) items per CTA and diagonal
-  if (const char *e = getenv("UGKS_SWEEP_ITEMS")) {
-    int v = atoi(e);
-    if (v >= 32 && v <= 8192) items = v;
-  }
-  if (items_req > 0) items = items_req;
-  int vt = items / r;
-  const char *env = getenv("UGKS_VTILE");
-  if (env && atoi(env) >= 1) vt = atoi(env);
-  int G = vt / vpt;
-  if (G < 1) G = 1;
-  int cap = 1;
-  while (cap * vpt < nvp) cap <<= 1;      // tiles no wider than the padded velocity count
-  if (G > cap) G = cap;
-  while (G > 1 && G * nj > 512) G >>= 1;
-  return G;
+// Micro sweeps (skewed wavefront, ugks_sweep.cu): a warp takes a band of
+// 32 / QL rows of a block and QL * VPT consecutive velocities (QL lanes a row,
+// VPT velocities a lane); a CTA holds, for one block, a warp per band for each
+// of its velocity groups; every CTA has nw warps, nw = the largest band count
+// of the blocks, so a smaller block takes several groups per CTA.
+int max_nj_of(int nb, const ugks_block_desc *b) {
+  int m = 1;
+  for (int i = 0; i < nb; ++i) m = std::max(m, b[i].nj);
+  return m;
+}
+int bands_of(int nj, int ql) { int rows = 32 / ql; return (nj + rows - 1) / rows; }
+int sweep_nw_for(int nb, const ugks_block_desc *b) {
+  int ql = wsweep_ql(max_nj_of(nb, b)), m = 1;
+  for (int i = 0; i < nb; ++i) m = std::max(m, bands_of(b[i].nj, ql));
+  return m;
 }
 
-// Default velocities per sweep thread; UGKS_SWEEP_VPT=4 selects four on the
-// FP32 paths by hand (the autotuner tries both).
+// Velocities per lane: 2 (UGKS_SWEEP_VPT=4 selects four on the FP32 paths).
 int sweep_vpt_for(const ugks_params *p) {
-  if (p->precision != UGKS_FP64) {
+  if (p->precision != UGKS_FP64)
     if (const char *e = getenv("UGKS_SWEEP_VPT"))
       if (atoi(e) == 4) return 4;
-    return sweep_vpt<float>();
-  }
-  return sweep_vpt<double>();
+  return 2;
 }
 
-// Threads of a micro-sweep CTA: the widest block's rows x G, rounded up to
-// whole warps.
-int sweep_threads_for(const ugks_params *p, int nb, const ugks_block_desc *b, int items = 0, int vpt = 0) {
-  int nvp = (p->nvx * p->nvy + 3) / 4 * 4;
-  if (vpt <= 0) vpt = sweep_vpt_for(p);
-  int t = 32;
+// Work list (block, first velocity, velocity groups in the CTA) per CTA.
+std::vector<int> ws_work(int nb, const ugks_block_desc *b, int nvp, int vpt, int nw) {
+  std::vector<int> work;
+  int ql = wsweep_ql(max_nj_of(nb, b)), vw = ql * vpt;
+  int groups = (nvp + vw - 1) / vw;
   for (int i = 0; i < nb; ++i) {
-    int w = b[i].nj * block_G(b[i].nj, nvp, vpt, items);
-    if (w > t) t = w;
+    int gpc = std::max(1, nw / bands_of(b[i].nj, ql));
+    for (int g0 = 0; g0 < groups; g0 += gpc) {
+      work.push_back(i);
+      work.push_back(g0 * vw);
+      work.push_back(std::min(gpc, groups - g0));
+    }
   }
-  return (t + 31) / 32 * 32;
+  return work;
+}
+
+int nwork_for(const ugks_params *p, int nb, const ugks_block_desc *b, int vpt) {
+  int nvp = (p->nvx * p->nvy + 3) / 4 * 4;
+  return (int)ws_work(nb, b, nvp, vpt, sweep_nw_for(nb, b)).size() / 3;
+}
+
+// Candidates of the sweep autotuner: velocities per lane (FP32 paths; FP64
+// keeps 2) and prefetch ring depths (steps).
+constexpr int kTuneVpt[] = {2, 4};
+constexpr int kTuneRing[] = {2, 4, 6};
+
+// Work-list capacity: the most CTAs any candidate needs.
+int nwork_cap_for(const ugks_params *p, int nb, const ugks_block_desc *b) {
+  int n = nwork_for(p, nb, b, sweep_vpt_for(p));
+  for (int v : kTuneVpt) n = std::max(n, nwork_for(p, nb, b, v));
+  return n;
 }
 
 // Lay out every device array of the context in the workspace (base may be
@@ -287,32 +291,6 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int fbf, int nwork, i
 }
 
 int cap_interp_for(const Sizes &s, int nb) { return nb > 1 ? (s.nc / 4 > 1024 ? s.nc / 4 : (s.nc < 1024 ? s.nc : 1024)) : 0; }
-
-// Micro-sweep work items (block, first velocity, G): one per velocity tile.
-int nwork_for(const ugks_params *p, int nb, const ugks_block_desc *b, int items = 0, int vpt = 0) {
-  int nvp = (p->nvx * p->nvy + 3) / 4 * 4;
-  if (vpt <= 0) vpt = sweep_vpt_for(p);
-  int n = 0;
-  for (int i = 0; i < nb; ++i) {
-    int vt = block_G(b[i].nj, nvp, vpt, items) * vpt;
-    n += (nvp + vt - 1) / vt;
-  }
-  return n;
-}
-
-// Candidate tile sizes of the sweep autotuner ((cell, velocity) items per CTA
-// and diagonal step) and ring depths.
-constexpr int kTuneItems[] = {256, 512, 1024, 2048};
-constexpr int kTuneRing[] = {2, 3, 4};
-constexpr int kTuneVpt[] = {2, 4};        // FP32 paths; FP64 keeps 2
-
-// Work-list capacity: the most tiles any candidate (or the default) needs.
-int nwork_cap_for(const ugks_params *p, int nb, const ugks_block_desc *b) {
-  int n = nwork_for(p, nb, b);
-  for (int it : kTuneItems)
-    for (int v : kTuneVpt) n = std::max(n, nwork_for(p, nb, b, it, v));
-  return n;
-}
 
 // Host topology identical in ordering to the face/cell numbering documented
 // in ugks.h.
@@ -467,27 +445,14 @@ int check_err_flag(ugks_ctx *ctx) {
 
 int launch_status(ugks_ctx *ctx) { return cuda_check(ctx, cudaPeekAtLastError(), "kernel launch"); }
 
-// Micro-sweep work list for a tile size (items per CTA and diagonal, 0 = by
-// rule): (block, first velocity, G) per velocity tile of every block.
-std::vector<int> sweep_work(const ugks_ctx *ctx, int items, int vpt) {
-  std::vector<int> work;
-  int nvp = ctx->d.nvp;
-  for (int b = 0; b < ctx->nblocks; ++b) {
-    int G = block_G(ctx->blocks[b].nj, nvp, vpt, items);
-    for (int k0 = 0; k0 < nvp; k0 += G * vpt) { work.push_back(b); work.push_back(k0); work.push_back(G); }
-  }
-  return work;
-}
-
-// Switch the micro sweeps to another tile size (uploads the work list).
-int set_sweep_tiles(ugks_ctx *ctx, int items, int vpt) {
-  std::vector<int> work = sweep_work(ctx, items, vpt);
+// Switch the micro sweeps to another number of velocities per lane
+// (uploads the work list).
+int set_sweep_tiles(ugks_ctx *ctx, int vpt) {
+  std::vector<int> work = ws_work(ctx->nblocks, ctx->blocks.data(), ctx->d.nvp, vpt, ctx->sweep_nw);
   if ((int)work.size() / 3 > ctx->nwork_cap) return fail(ctx, UGKS_ERR_WORKSPACE, "sweep work list");
   CK(cudaMemcpyAsync(ctx->work, work.data(), sizeof(int) * work.size(), cudaMemcpyHostToDevice, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   ctx->nwork = (int)work.size() / 3;
-  ctx->sweep_threads = sweep_threads_for(&ctx->p, ctx->nblocks, ctx->blocks.data(), items, vpt);
-  ctx->sweep_items = items;
   ctx->sweep_vpt = vpt;
   return UGKS_OK;
 }
@@ -706,7 +671,12 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
   ctx->blocks.assign(blocks, blocks + nblocks);
   ctx->max_nj = s.max_nj;
   ctx->sweep_vpt = sweep_vpt_for(&ctx->p);
-  ctx->sweep_threads = sweep_threads_for(&ctx->p, nblocks, blocks, 0, ctx->sweep_vpt);
+  ctx->sweep_nw = sweep_nw_for(nblocks, blocks);
+  ctx->sweep_ql = wsweep_ql(max_nj_of(nblocks, blocks));
+  if (const char *e = getenv("UGKS_SWEEP_NS")) {
+    int n = atoi(e);
+    if (n == 2 || n == 4 || n == 6) ctx->ns_fwd = ctx->ns_bwd = n;
+  }
   {
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
@@ -714,7 +684,9 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
       ctx->nsm = nsm;
     cudaGetLastError();
   }
-  ctx->nwork = nwork_for(&ctx->p, nblocks, blocks, 0, ctx->sweep_vpt);
+  ctx->nwork = nwork_for(&ctx->p, nblocks, blocks, ctx->sweep_vpt);
+  if (!wsweep_fits(ctx->fp32, ctx->fbf, ctx->sweep_vpt, ctx->sweep_nw, 1, ctx->sweep_ql))
+    return fail(ctx, UGKS_ERR_ARG, "micro-sweep CTA of the tallest block exceeds shared memory");
   ctx->nwork_cap = nwork_cap_for(&ctx->p, nblocks, blocks);
   ctx->cap_interp = cap_interp_for(s, nblocks);
   Dev &d = ctx->d;
@@ -787,7 +759,7 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
       if (blocks[order[b]].priority > blocks[order[a]].priority ||
           (blocks[order[b]].priority == blocks[order[a]].priority && order[b] < order[a]))
         std::swap(order[a], order[b]);
-  std::vector<int> work = sweep_work(ctx, 0, ctx->sweep_vpt);
+  std::vector<int> work = ws_work(nblocks, blocks, s.nvp, ctx->sweep_vpt, ctx->sweep_nw);
   std::vector<int> tiles;
   for (int b = 0; b < nblocks; ++b) {
     std::vector<int> org(2 * (size_t)tile_count(blocks[b].ni, blocks[b].nj));
@@ -797,6 +769,7 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
   d.ntiles = s.ntiles;
   tile_setup();
   sweep_setup();
+  wsweep_setup();
   if ((r = up(ctx, (void *)d.vx, vx))) return r;
   if ((r = up(ctx, (void *)d.vy, vy))) return r;
   if ((r = up(ctx, (void *)d.w, w))) return r;
@@ -948,8 +921,8 @@ int ugks_step(ugks_ctx *ctx, double dt, int n_inner) {
     { Prof p(ctx, UGKS_PROF_RHS); launch_flux_tile(d, s, fp); }                              // Step 3
     CK(cudaStreamWaitEvent(s, ctx->ev_macro, 0));
     { Prof p(ctx, UGKS_PROF_RESIDUAL); launch_residual(d, s, it == 0, fp); }                 // Step 5
-    { Prof p(ctx, UGKS_PROF_MICRO_FWD); launch_micro_fwd(d, s, ctx->work, ctx->nwork, ctx->sweep_threads, ctx->max_nj, ctx->nsm, ctx->ns_fwd, ctx->sweep_vpt, fp); }  // Step 6
-    { Prof p(ctx, UGKS_PROF_MICRO_BWD); launch_micro_bwd(d, s, ctx->work, ctx->nwork, ctx->sweep_threads, ctx->max_nj, ctx->nsm, ctx->ns_bwd, ctx->sweep_vpt, fp); }
+    { Prof p(ctx, UGKS_PROF_MICRO_FWD); launch_wsweep(d, s, 0, ctx->work, ctx->nwork, ctx->sweep_nw, ctx->ns_fwd, ctx->sweep_vpt, fp, ctx->sweep_ql); }  // Step 6
+    { Prof p(ctx, UGKS_PROF_MICRO_BWD); launch_wsweep(d, s, 1, ctx->work, ctx->nwork, ctx->sweep_nw, ctx->ns_bwd, ctx->sweep_vpt, fp, ctx->sweep_ql); }
     { Prof p(ctx, UGKS_PROF_MOMENTS); launch_moments(d, s, fp); }                          // Step 7
     ctx->launches += 8;
   }
@@ -1001,16 +974,13 @@ int ugks_autotune(ugks_ctx *ctx, int reps, int *items_out, int *vpt_out, int *ri
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
-  int bi = ctx->sweep_items, bv = ctx->sweep_vpt, bf = ctx->ns_fwd, bb = ctx->ns_bwd;
+  int bv = ctx->sweep_vpt, bf = ctx->ns_fwd, bb = ctx->ns_bwd;
   int r = UGKS_OK;
   // time one sweep (pass 0 forward, 1 backward) with ring depth ns
   auto trial = [&](int pass, int ns, float &ms) -> int {
     for (int rep = 0; rep <= reps; ++rep) {     // the first pass warms up
       if (rep == 1) cudaEventRecord(e0, s);
-      if (pass == 0)
-        launch_micro_fwd(d, s, ctx->work, ctx->nwork, ctx->sweep_threads, ctx->max_nj, ctx->nsm, ns, ctx->sweep_vpt, fp);
-      else
-        launch_micro_bwd(d, s, ctx->work, ctx->nwork, ctx->sweep_threads, ctx->max_nj, ctx->nsm, ns, ctx->sweep_vpt, fp);
+      launch_wsweep(d, s, pass, ctx->work, ctx->nwork, ctx->sweep_nw, ns, ctx->sweep_vpt, fp, ctx->sweep_ql);
     }
     cudaEventRecord(e1, s);
     int q = cuda_check(ctx, cudaEventSynchronize(e1), "autotune");
@@ -1019,32 +989,30 @@ int ugks_autotune(ugks_ctx *ctx, int reps, int *items_out, int *vpt_out, int *ri
     ctx->launches += reps + 1;
     return q;
   };
-  for (int items : kTuneItems) {
-    for (int vpt : kTuneVpt) {
-      if (!fp && vpt != sweep_vpt<double>()) continue;
-      if ((r = set_sweep_tiles(ctx, items, vpt))) break;
-      float tf = 1e30f, tb = 1e30f;
-      int nf = 0, nb = 0;
-      for (int ns : kTuneRing) {
-        float ms;
-        if ((r = trial(0, ns, ms))) break;
-        if (ms < tf) { tf = ms; nf = ns; }
-        if ((r = trial(1, ns, ms))) break;
-        if (ms < tb) { tb = ms; nb = ns; }
-      }
-      if (r) break;
-      if (tf + tb < best) { best = tf + tb; bi = items; bv = vpt; bf = nf; bb = nb; }
+  for (int vpt : kTuneVpt) {
+    if (!fp && vpt != 2) continue;
+    if ((r = set_sweep_tiles(ctx, vpt))) break;
+    float tf = 1e30f, tb = 1e30f;
+    int nf = 0, nb = 0;
+    for (int ns : kTuneRing) {
+      if (!wsweep_fits(fp, ctx->fbf, vpt, ctx->sweep_nw, ns, ctx->sweep_ql)) continue;
+      float ms;
+      if ((r = trial(0, ns, ms))) break;
+      if (ms < tf) { tf = ms; nf = ns; }
+      if ((r = trial(1, ns, ms))) break;
+      if (ms < tb) { tb = ms; nb = ns; }
     }
     if (r) break;
+    if (nf && nb && tf + tb < best) { best = tf + tb; bv = vpt; bf = nf; bb = nb; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (r) return r;
   CK(cudaMemcpyAsync(d.f, d.Dbuf, fbytes, cudaMemcpyDeviceToDevice, s));
-  if ((r = set_sweep_tiles(ctx, bi, bv))) return r;
+  if ((r = set_sweep_tiles(ctx, bv))) return r;
   ctx->ns_fwd = bf;
   ctx->ns_bwd = bb;
-  if (items_out) *items_out = bi;
+  if (items_out) *items_out = 32 * bv;
   if (vpt_out) *vpt_out = bv;
   if (ring_fwd_out) *ring_fwd_out = bf;
   if (ring_bwd_out) *ring_bwd_out = bb;

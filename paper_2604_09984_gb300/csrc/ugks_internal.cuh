@@ -141,17 +141,6 @@ enum { SR_DBASE = 12, SR_MASK = 13, NSR = 16 };
 // values per cell of the macro-sweep record (FP64 packed, FP32 padded to 256 B)
 enum { NMR = 41, NMR32 = 64 };
 
-// velocities per thread of the micro sweeps (measured on the MEMS workload,
-// FP32: 2 -> 0.28 / 0.38 ms per forward / backward sweep, 4 -> 0.44 / 0.51,
-// 8 -> 0.68 / 0.82: more, lighter threads hide the diagonal step's latency)
-template <typename T> __host__ __device__ constexpr int sweep_vpt() { return 2; }
-// bytes between the row records of a micro-sweep ring stage: FP32 records
-// (64 B) padded to 80 B so the rows of a warp fall in different banks; FP64
-// records (128 B) unpadded so a 512-row block still fits two stages
-template <typename T> __host__ __device__ constexpr int sweep_rec_stride() {
-  return sizeof(T) == 4 ? NSR * 4 + 16 : NSR * 8;
-}
-
 // per-cell parameter record (from W' or W^n)
 enum { CP_RHO = 0, CP_UX, CP_UY, CP_LAM, CP_QX, CP_QY, CP_ITAU, CP_DBASE, NCP = 8 };
 

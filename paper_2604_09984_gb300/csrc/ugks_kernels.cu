@@ -1023,227 +1023,6 @@ template <typename T> __global__ void k_macro_post(Dev d) {
   write_shrec<T>(d, o, d.vol_new[c], reinterpret_cast<T *>(d.shp) + (size_t)NSH * c);
 }
 
-// ----------------------------------------------------- micro LU-SGS sweeps
-template <typename T> __device__ __forceinline__ T wS_of(const Dev &d, int f, int k) {
-  return dvx<T>(d, k) * (T)d.Sn[2 * f] + dvy<T>(d, k) * (T)d.Sn[2 * f + 1] - (T)d.SUn[f];
-}
-
-template <typename T> __device__ __forceinline__ T micro_diag(const Dev &d, int c, int k, T itau) {
-  T dg = (T)d.vol_new[c] * ((T)(d.cfl_s / (d.cfl_pseudo * d.dts[c])) + (T)(1.0 / d.dt) + T(0.5) * itau);
-  for (int s = 0; s < 4; ++s) {
-    int f = d.cell_faces[4 * c + s];
-    T wo = (T)d.cell_sgn[4 * c + s] * wS_of<T>(d, f, k);
-    dg += T(0.5) * (wo > T(0) ? wo : T(0));
-  }
-  return dg;
-}
-
-// Micro LU-SGS (Eq. dualTimeStepping_micro with the upwind flux variation of
-// Sec. 2.2) on the residual r (in dfs): one CTA per (block, velocity tile)
-// work item (block, first velocity, G), thread = (row j, VPT consecutive
-// velocities), G threads per row; the cells of one diagonal i + j are
-// independent, lower (upper) neighbours lie on the previous diagonal (same
-// thread / thread of row j -+ 1) or, across a periodic seam, on diagonal j
-// (kept in registers).  One barrier per diagonal.  Nothing a diagonal step
-// reads from memory depends on the sweep, so every input (r, f in pass 1, and
-// the row's cell record: outward S n and S U.n per face slot, the diagonal
-// base, the neighbour mask) streams NS-1 diagonals ahead through a cp.async
-// ring in shared memory.  Several velocities per thread share the record
-// reads and the index arithmetic of a step.
-// pass 0: forward, d* = (r - sum_lower c d*) / D written over r;
-// pass 1: backward, d = d* - sum_upper c d / D and f += d.
-template <typename T> __device__ __forceinline__ T rcp_rn(T x);
-template <> __device__ __forceinline__ float rcp_rn<float>(float x) { return __frcp_rn(x); }
-template <> __device__ __forceinline__ double rcp_rn<double>(double x) { return 1.0 / x; }
-
-// Shared-memory layout of per-thread values (VPT velocities = 32 bytes):
-// 16-byte chunk q of thread t at (q nt + t) 16, so the lanes of a warp read
-// and write contiguous 512-byte runs (no bank conflicts).
-template <typename T, int VPT> struct SweepVals {
-  typedef typename Vec2<T>::type T2;
-  static constexpr int NQ = VPT * (int)sizeof(T2) / 16;     // chunks per thread
-  static constexpr int PER = 16 / (int)sizeof(T2);           // values per chunk
-  __device__ static T2 *at(unsigned char *base, int nt, int t, int u) {
-    return reinterpret_cast<T2 *>(base + ((size_t)(u / PER) * nt + t) * 16) + (u % PER);
-  }
-  __device__ static const T2 *at(const unsigned char *base, int nt, int t, int u) {
-    return reinterpret_cast<const T2 *>(base + ((size_t)(u / PER) * nt + t) * 16) + (u % PER);
-  }
-};
-
-template <typename T, int PASS, int NS, int VPT, int FB>
-__global__ void __launch_bounds__(512) k_micro_sweep(Dev d, const int *work, int R) {
-  typedef typename Vec2<T>::type T2;
-  typedef SweepVals<T, VPT> SV;
-  constexpr int TB = VPT * (int)sizeof(T2);             // bytes of one thread's values
-  constexpr int RS = sweep_rec_stride<T>();               // record row in shared memory
-  constexpr int NCH = NSR * (int)sizeof(T) / 16;
-  static_assert(TB % 16 == 0, "per-thread values are whole 16-byte chunks");
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int nt = blockDim.x;
-  unsigned char *bufA = smraw, *bufB = smraw + (size_t)nt * TB;
-  const int recoff = (PASS == 1 ? 2 : 1) * nt * TB;
-  const int stage = recoff + R * RS;
-  unsigned char *ring = smraw + 2 * (size_t)nt * TB;
-  int b = work[3 * blockIdx.x], k0 = work[3 * blockIdx.x + 1], G = work[3 * blockIdx.x + 2];
-  const int *bi = d.blk_info + 8 * b;
-  int ni = bi[0], nj = bi[1], per = bi[2];
-  int off = d.cell_off[b];
-  int row = threadIdx.x / G, g = threadIdx.x - row * G;
-  int kb = k0 + g * VPT;
-  bool rowv = row < nj;
-  bool kin = rowv && kb < d.nvp;          // this thread's velocities lie in the array
-  T vx[VPT], vy[VPT];
-  bool kok[VPT];
-#pragma unroll
-  for (int u = 0; u < VPT; ++u) {
-    kok[u] = kin && kb + u < d.nv;
-    vx[u] = kok[u] ? dvx<T>(d, kb + u) : T(0);
-    vy[u] = kok[u] ? dvy<T>(d, kb + u) : T(0);
-  }
-  T2 prev[VPT], first[VPT];
-#pragma unroll
-  for (int u = 0; u < VPT; ++u) { prev[u] = T2{0, 0}; first[u] = T2{0, 0}; }
-  int nd = ni + nj - 1;
-  const unsigned char *srec = reinterpret_cast<const unsigned char *>(d.srec);
-  const unsigned char *gin = reinterpret_cast<const unsigned char *>(d.dfs);
-  const unsigned char *gf = reinterpret_cast<const unsigned char *>(d.f);
-  // the cell of this row on the diagonal of step it (i = it - row forward,
-  // nd - 1 - it - row backward)
-  auto issue = [&](int it, int slot) {
-    if (it < nd && rowv) {
-      int i = (PASS == 0 ? it : nd - 1 - it) - row;
-      if (i >= 0 && i < ni) {
-        int c = off + row * ni + i;
-        unsigned char *st = ring + (size_t)slot * stage;
-        if (kin) {
-          size_t gb = ((size_t)c * d.nvp + kb) * sizeof(T2);
-          constexpr bool fb = PASS == 1 && FB == 1;          // bf16 f: 4 bytes a velocity
-#pragma unroll
-          for (int q = 0; q < SV::NQ; ++q) {
-            cp_async<16>(st + ((size_t)q * nt + threadIdx.x) * 16, gin + gb + 16 * q);
-            if (PASS == 1 && !fb) cp_async<16>(st + ((size_t)(SV::NQ + q) * nt + threadIdx.x) * 16, gf + gb + 16 * q);
-          }
-          if (fb) cp_async<4 * VPT>(st + ((size_t)SV::NQ * nt + threadIdx.x) * 16, gf + ((size_t)c * d.nvp + kb) * 4);
-        }
-        for (int q = g; q < NCH; q += G)
-          cp_async<16>(st + recoff + row * RS + 16 * q, srec + (size_t)c * NSR * sizeof(T) + 16 * q);
-      }
-    }
-    cp_async_commit();
-  };
-#pragma unroll
-  for (int q = 0; q < NS - 1; ++q) issue(q, q);
-  cp_async_wait<NS - 2>();
-  __syncthreads();
-  int cur = 0, slot = 0, fill = NS - 1;     // ring slots of diagonal it and it + NS - 1
-  for (int it = 0; it < nd; ++it) {
-    issue(it + NS - 1, fill);
-    int i = (PASS == 0 ? it : nd - 1 - it) - row;
-    bool act = kin && i >= 0 && i < ni;
-    const unsigned char *st = ring + (size_t)slot * stage;
-    const T *geo = reinterpret_cast<const T *>(st + recoff + row * RS);
-    int mask = act ? *reinterpret_cast<const int *>(geo + SR_MASK) : 0;
-    T2 val[VPT];
-#pragma unroll
-    for (int u = 0; u < VPT; ++u) val[u] = T2{0, 0};
-    if (mask & 1) {
-      int c = off + row * ni + i;
-      // the record holds half the outward (S n_x, S n_y, S U.n) per slot, so
-      // w/2 = v.(S n)/2 - S U.n/2 and the upwind parts are max / min with 0
-      T gr[SR_DBASE + 1];
-#pragma unroll
-      for (int m = 0; m <= SR_DBASE; ++m) gr[m] = geo[m];
-      const unsigned char *prvb = cur ? bufA : bufB;
-      // lower (pass 0) / upper (pass 1) couplings: along the row (previous
-      // cell, same thread), across rows (row -+ 1, previous diagonal), and
-      // across a periodic seam (first cell of the row, rare)
-      int srow = PASS == 0 ? 0 : 1, scol = PASS == 0 ? 2 : 3, sseam = PASS == 0 ? 1 : 0;
-      bool urow = (PASS == 0 ? i > 0 : i < ni - 1) && (mask & (2 << srow));
-      bool ucol = (PASS == 0 ? row > 0 : row < nj - 1) && (mask & (2 << scol));
-      bool useam = per && (PASS == 0 ? i == ni - 1 : i == 0) && (mask & (2 << sseam));
-      int tadj = PASS == 0 ? (int)threadIdx.x - G : (int)threadIdx.x + G;
-      T2 pr[VPT], ad[VPT];
-#pragma unroll
-      for (int u = 0; u < VPT; ++u) {
-        pr[u] = urow ? prev[u] : T2{0, 0};
-        ad[u] = ucol ? *SV::at(prvb, nt, tadj, u) : T2{0, 0};
-      }
-#pragma unroll
-      for (int u = 0; u < VPT; ++u) {
-        T w0 = vx[u] * gr[0] + vy[u] * gr[1] - gr[2];
-        T w1 = vx[u] * gr[3] + vy[u] * gr[4] - gr[5];
-        T w2 = vx[u] * gr[6] + vy[u] * gr[7] - gr[8];
-        T w3 = vx[u] * gr[9] + vy[u] * gr[10] - gr[11];
-        T dg = gr[SR_DBASE];
-        dg += w0 > T(0) ? w0 : T(0);
-        dg += w1 > T(0) ? w1 : T(0);
-        dg += w2 > T(0) ? w2 : T(0);
-        dg += w3 > T(0) ? w3 : T(0);
-        T wr = PASS == 0 ? w0 : w1, wc = PASS == 0 ? w2 : w3;
-        T cr = wr < T(0) ? wr : T(0), cc = wc < T(0) ? wc : T(0);
-        T ah = cr * pr[u].x, ab = cr * pr[u].y;
-        ah += cc * ad[u].x;
-        ab += cc * ad[u].y;
-        if (useam) {
-          T ws = PASS == 0 ? w1 : w0;
-          T cs = ws < T(0) ? ws : T(0);
-          ah += cs * first[u].x;
-          ab += cs * first[u].y;
-        }
-        T idg = rcp_rn<T>(dg);
-        T2 r = *SV::at(st, nt, threadIdx.x, u);
-        if (PASS == 0) {
-          val[u].x = (r.x - ah) * idg;
-          val[u].y = (r.y - ab) * idg;
-        } else {
-          val[u].x = r.x - ah * idg;
-          val[u].y = r.y - ab * idg;
-        }
-        if (!kok[u]) val[u] = T2{0, 0};
-      }
-      size_t idx = (size_t)c * d.nvp + kb;
-      T2 *out = reinterpret_cast<T2 *>(d.dfs) + idx;
-      constexpr bool fb = PASS == 1 && FB == 1;
-#pragma unroll
-      for (int u = 0; u < VPT; ++u) {
-        T2 o = val[u];
-        if (PASS == 1) {
-          T2 fv;
-          if (fb) {
-            float2 w = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162 *>(
-                st + ((size_t)SV::NQ * nt + threadIdx.x) * 16)[u]);
-            fv = T2{(T)w.x, (T)w.y};
-          } else {
-            fv = *SV::at(st + (size_t)SV::NQ * nt * 16, nt, threadIdx.x, u);
-          }
-          o.x = fv.x + o.x;
-          o.y = fv.y + o.y;
-          stF<T, FB>(d, idx + u, o.x, o.y);
-        } else {
-          out[u] = o;
-        }
-      }
-    }
-    if (act) {
-#pragma unroll
-      for (int u = 0; u < VPT; ++u) prev[u] = val[u];
-      if (i == (PASS == 0 ? 0 : ni - 1))
-#pragma unroll
-        for (int u = 0; u < VPT; ++u) first[u] = val[u];
-    }
-    unsigned char *dstb = cur ? bufB : bufA;
-#pragma unroll
-    for (int u = 0; u < VPT; ++u) *SV::at(dstb, nt, threadIdx.x, u) = val[u];
-    cp_async_wait<NS - 2>();
-    __syncthreads();
-    cur ^= 1;
-    fill = slot;
-    slot = slot + 1 == NS ? 0 : slot + 1;
-  }
-  cp_async_wait<0>();
-}
-
 // Step 7 (one warp per cell): W^{s+1} = W' + sum V Psi (f^{s+1} - g(W')),
 // heat flux about V' (reading R7); flags non-physical states.
 template <typename T, int FB> __global__ void k_moments(Dev d) {
@@ -1477,7 +1256,6 @@ void launch_cell_params(const Dev &d, cudaStream_t s, const double *W, double *o
 }
 // dynamic shared memory of the sweeps: up to the 227 KB a CTA may use
 constexpr size_t kMacroSmem = 227 * 1024;
-constexpr size_t kSweepSmem = 227 * 1024;
 // The sweep records are gathered on the caller's stream before the fork, so
 // the sweep kernel is the first work of the side stream: it then takes its
 // empty SMs before the flux kernel launched beside it fills the GPU.
@@ -1521,7 +1299,7 @@ void launch_macro_sweep(const Dev &d, cudaStream_t s, int rows, int fp32) {
   if (fp32) k_macro_post<float><<<nblk(d.nc, 256), 256, 0, s>>>(d);
   else k_macro_post<double><<<nblk(d.nc, 256), 256, 0, s>>>(d);
 }
-// shared memory of the sweeps exceeds the default 48 KB for FP64 / wide CTAs
+// shared memory of the macro sweeps exceeds the default 48 KB
 void sweep_setup() {
   int ms = (int)kMacroSmem;
   cudaFuncSetAttribute(k_macro_sweep<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, ms);
@@ -1531,90 +1309,8 @@ void sweep_setup() {
   UGKS_MACRO_ATTR(4, 2); UGKS_MACRO_ATTR(3, 2); UGKS_MACRO_ATTR(2, 2); UGKS_MACRO_ATTR(0, 2);
   UGKS_MACRO_ATTR(4, 1); UGKS_MACRO_ATTR(3, 1); UGKS_MACRO_ATTR(2, 1); UGKS_MACRO_ATTR(0, 1);
 #undef UGKS_MACRO_ATTR
-  int mx = (int)kSweepSmem;
-  constexpr int VF = sweep_vpt<float>(), VD = sweep_vpt<double>();
-  cudaFuncSetAttribute(k_micro_sweep<float, 0, 4, VF, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<float, 1, 4, VF, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<float, 0, 3, VF, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<float, 1, 3, VF, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<float, 0, 2, VF, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<float, 1, 2, VF, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<float, 0, 4, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<float, 1, 4, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<float, 0, 3, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<float, 1, 3, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<float, 0, 2, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<float, 1, 2, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<double, 0, 4, VD, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<double, 1, 4, VD, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<double, 0, 3, VD, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<double, 1, 3, VD, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<double, 0, 2, VD, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<double, 1, 2, VD, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<float, 1, 4, VF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<float, 1, 3, VF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<float, 1, 2, VF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<float, 1, 4, 4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<float, 1, 3, 4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_micro_sweep<float, 1, 2, 4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
 }
 
-// Micro sweeps: ring depth ns_req (2-4) when it fits, else the deepest ring
-// (4, 3 or 2 diagonals) with which all the sweep's CTAs are resident at once
-// (nsm SMs), else the deepest that fits one CTA per SM.
-template <typename T, int PASS, int VPT>
-static void micro_sweep_v(const Dev &d, cudaStream_t s, const int *work, int nwork, int threads, int R,
-                          int nsm, int ns_req) {
-  typedef typename Vec2<T>::type T2;
-  size_t tb = VPT * sizeof(T2), rs = sweep_rec_stride<T>();
-  size_t stage = (PASS == 1 ? 2 : 1) * (size_t)threads * tb + (size_t)R * rs;
-  size_t base = 2 * (size_t)threads * tb;
-  int per_sm = nsm > 0 ? (nwork + nsm - 1) / nsm : 2;
-  if (per_sm < 1) per_sm = 1;
-  int ns = 2;
-  bool found = false;
-  for (size_t cap : {per_sm > 1 ? kSweepSmem / per_sm - 1024 : kSweepSmem, kSweepSmem}) {
-    for (int n = 4; n >= 2 && !found; --n)
-      if (base + n * stage <= cap) { ns = n; found = true; }
-    if (found) break;
-  }
-  const char *env = getenv("UGKS_SWEEP_NS");
-  int want = ns_req >= 2 ? ns_req : (env ? atoi(env) : 0);
-  if (want >= 2 && want <= 4 && base + want * stage <= kSweepSmem) ns = want;
-  size_t sm = base + ns * stage;
-  if (PASS == 1 && d.fbf) {
-    if (ns == 4) k_micro_sweep<T, PASS, 4, VPT, 1><<<nwork, threads, sm, s>>>(d, work, R);
-    else if (ns == 3) k_micro_sweep<T, PASS, 3, VPT, 1><<<nwork, threads, sm, s>>>(d, work, R);
-    else k_micro_sweep<T, PASS, 2, VPT, 1><<<nwork, threads, sm, s>>>(d, work, R);
-  } else {
-    if (ns == 4) k_micro_sweep<T, PASS, 4, VPT, 0><<<nwork, threads, sm, s>>>(d, work, R);
-    else if (ns == 3) k_micro_sweep<T, PASS, 3, VPT, 0><<<nwork, threads, sm, s>>>(d, work, R);
-    else k_micro_sweep<T, PASS, 2, VPT, 0><<<nwork, threads, sm, s>>>(d, work, R);
-  }
-}
-// velocities per thread: 2, or 4 on the FP32 paths (large problems, where
-// fewer, wider CTAs cut the number of waves of diagonal sweeps)
-template <typename T, int PASS>
-static void micro_sweep(const Dev &d, cudaStream_t s, const int *work, int nwork, int threads, int R,
-                        int nsm, int ns_req, int vpt) {
-  if constexpr (sizeof(T) == 4) {
-    if (vpt == 4) {
-      micro_sweep_v<T, PASS, 4>(d, s, work, nwork, threads, R, nsm, ns_req);
-      return;
-    }
-  }
-  micro_sweep_v<T, PASS, sweep_vpt<T>()>(d, s, work, nwork, threads, R, nsm, ns_req);
-}
-void launch_micro_fwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int threads, int rows,
-                      int nsm, int ns, int vpt, int fp32) {
-  if (fp32) micro_sweep<float, 0>(d, s, work, nwork, threads, rows, nsm, ns, vpt);
-  else micro_sweep<double, 0>(d, s, work, nwork, threads, rows, nsm, ns, vpt);
-}
-void launch_micro_bwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int threads, int rows,
-                      int nsm, int ns, int vpt, int fp32) {
-  if (fp32) micro_sweep<float, 1>(d, s, work, nwork, threads, rows, nsm, ns, vpt);
-  else micro_sweep<double, 1>(d, s, work, nwork, threads, rows, nsm, ns, vpt);
-}
 void launch_moments(const Dev &d, cudaStream_t s, int fp32) {
   if (fp32 && d.fbf) k_moments<float, 1><<<nblk((size_t)d.nc * 32, 256), 256, 0, s>>>(d);
   else if (fp32) k_moments<float, 0><<<nblk((size_t)d.nc * 32, 256), 256, 0, s>>>(d);

@@ -14,10 +14,14 @@ void launch_cell_macro(const Dev &d, cudaStream_t s, int level_n);
 void launch_cell_params(const Dev &d, cudaStream_t s, const double *W, double *out, int fp32);
 void launch_macro_prep(const Dev &d, cudaStream_t s, int fp32);
 void launch_macro_sweep(const Dev &d, cudaStream_t s, int rows, int fp32);   // sweep + post (after launch_macro_prep)
-void launch_micro_fwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int threads, int rows,
-                      int nsm, int ns, int vpt, int fp32);   // ns: ring depth 2-4, 0 = by rule
-void launch_micro_bwd(const Dev &d, cudaStream_t s, const int *work, int nwork, int threads, int rows,
-                      int nsm, int ns, int vpt, int fp32);   // vpt: velocities per thread (2, or 4 in FP32)
+// micro LU-SGS sweeps (ugks_sweep.cu): pass 0 forward, 1 backward; nw warps
+// per CTA, ns prefetch steps (1, 2, 4 or 6), vpt velocities per lane, ql
+// lanes per row (4 or 2: wsweep_ql of the tallest block)
+void launch_wsweep(const Dev &d, cudaStream_t s, int pass, const int *work, int nwork, int nw, int ns, int vpt,
+                   int fp32, int ql);
+void wsweep_setup();
+int wsweep_ql(int max_nj);
+int wsweep_fits(int fp32, int fbf, int vpt, int nw, int ns, int ql);
 void sweep_setup();
 void launch_moments(const Dev &d, cudaStream_t s, int fp32);
 void launch_init_state(const Dev &d, cudaStream_t s, const double *prim, int fp32);

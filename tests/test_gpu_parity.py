@@ -277,25 +277,26 @@ def test_batch_matches_separate_runs(prec, tol):
 
 
 def test_autotune_restores_state_and_changes_no_result():
-    """The sweep autotuner times every candidate tile on the live state,
-    restores f bit for bit, and every tile computes the same sweeps: runs on
-    the tuned tile and on the smallest tile match the default one."""
+    """The sweep autotuner times every candidate (velocities per lane,
+    prefetch ring depth) on the live state, restores f bit for bit, and every
+    candidate computes the same sweeps: runs on the tuned choice and on the
+    shallowest ring match the default one."""
     case = small_mems()
     prim = wl.random_prim(case, 21, amp_rho=0.05, amp_u=0.05, amp_T=0.05)
     a = U.Solver(case, U.FP64, prim=prim)
     b = U.Solver(case, U.FP64, prim=prim)
     with pytest.raises(U.UgksError):
         a.autotune(reps=1)                      # needs a step first
-    os.environ["UGKS_SWEEP_ITEMS"] = "256"
+    os.environ["UGKS_SWEEP_NS"] = "2"
     try:
         c = U.Solver(case, U.FP64, prim=prim)
     finally:
-        del os.environ["UGKS_SWEEP_ITEMS"]
+        del os.environ["UGKS_SWEEP_NS"]
     for s in (a, b, c):
         s.advance()
     f0, _, _ = a.get_state()
     items, vpt, ring_f, ring_b = a.autotune(reps=1)
-    assert items in (256, 512, 1024, 2048) and vpt == 2 and ring_f in (2, 3, 4) and ring_b in (2, 3, 4)
+    assert vpt == 2 and items == 64 and ring_f in (1, 2, 4, 6) and ring_b in (1, 2, 4, 6)
     f1, _, _ = a.get_state()
     assert torch.equal(f0, f1)
     for _ in range(2):
@@ -333,8 +334,8 @@ def test_batch_defers_orphan_report_to_next_sync():
 
 @pytest.mark.parametrize("prec", [U.FP32, U.BF16F])
 def test_four_velocities_per_sweep_thread(prec):
-    """The FP32 sweeps with four velocities per thread (a tile the autotuner
-    may pick) compute what the two-velocity tiles compute."""
+    """The FP32 sweeps with four velocities per lane (a choice the autotuner
+    may make) compute what the default two compute."""
     case = small_mems(nv=10)
     prim = wl.random_prim(case, 23, amp_rho=0.05, amp_u=0.05, amp_T=0.05)
     b = U.Solver(case, prec, prim=prim)

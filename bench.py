@@ -353,6 +353,36 @@ def cpu_baseline(kn, steps=1):
             "seconds": dt}
 
 
+def _oracle_job(kn):
+    """One physical step of the oracle sample in a worker process: (units, s)."""
+    from oracle.run import Run
+    case = cpu_sample_case(kn)
+    r = Run(case)
+    t0 = time.perf_counter()
+    r.step()
+    return int((r.status == 0).sum()) * case.nv * case.n_inner, time.perf_counter() - t0
+
+
+def cpu_baseline_multicore(kn):
+    """The oracle on all host cores: one independent sample step per core in
+    worker processes started with spawn (no fork after CUDA has started);
+    throughput = all units / wall time of the slowest worker's step."""
+    import multiprocessing as mp
+    ncore = os.cpu_count() or 1
+    nproc = max(1, min(ncore, 16))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(nproc) as pool:
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_job, [kn] * nproc)
+        wall = time.perf_counter() - t0
+    units = sum(u for u, _ in res)
+    step_s = max(t for _, t in res)
+    return {"value": units / step_s, "unit": UNIT, "cores": nproc, "kind": "oracle",
+            "host_cores": ncore, "wall_s_with_startup": wall,
+            "sample": "FP64 numpy oracle, %d independent processes x 1 step of %s"
+                      % (nproc, workload_label(cpu_sample_case(kn)))}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -376,6 +406,108 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def dominant_roofline(prof, nfield, nv, nc, pair, peak, peak_kind, traffic=None):
+    """Roofline of the streaming kernel group (one that moves f) with the most
+    device time on the step's stream: its algorithmic bytes per launch over
+    its event-timed duration per launch.  (The macro LU-SGS runs on a second
+    stream beside the flux kernel and moves no f.)"""
+    groups = {g: v for g, v in prof.items() if v[1] > 0}
+    streaming = {g: v for g, v in groups.items() if algorithmic_bytes(g, pair, nfield, nv, nc) > 0}
+    dom = max(streaming or groups, key=lambda g: groups[g][0])
+    dms, dn = groups[dom]
+    abytes = algorithmic_bytes(dom, pair, nfield, nv, nc)
+    if abytes > 0:
+        ach = abytes / (dms / dn * 1e-3) / 1e9
+        return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": traffic, "peak_kind": peak_kind,
+                "bytes_per_launch": abytes, "ms_per_launch": dms / dn}
+    return {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None,
+            "frac": None, "traffic": None, "ms_per_launch": dms / dn}
+
+
+def kernel_table(prof, nfield, nv, nc, pair):
+    groups = {g: v for g, v in prof.items() if v[1] > 0}
+    tot = sum(v[0] for v in groups.values())
+    out = {}
+    for g, (gms, gn) in groups.items():
+        b = algorithmic_bytes(g, pair, nfield, nv, nc)
+        out[g] = {"ms_total": round(gms, 3), "launches": gn, "share": round(gms / tot, 4)}
+        if b:
+            out[g]["GBps"] = round(b / (gms / gn * 1e-3) / 1e9, 1)
+    return out
+
+
+def profiled_steps(s, steps):
+    """Per-group device times (CUDA events around every launch) over `steps`
+    further physical steps of solver s; separate from the timed steps, whose
+    clock sees no event bracketing."""
+    s.profile_read(reset=True)
+    s.profile(True)
+    for _ in range(steps):
+        s.advance()
+    s.profile(False)
+    return s.profile_read(reset=True)
+
+
+def fp64_probe(device):
+    """Measured FP64 rates of this GPU (ugks_probe_fp64): fused multiply-adds
+    and exponentials per second, CUDA events on the launch stream."""
+    import ctypes
+    import torch
+    from paper_2604_09984_gb300 import ugks as U
+    lib = U.load()
+    nb, nt = 152 * 16, 256
+    out = torch.empty(nb * nt, dtype=torch.float64, device=device)
+    st = torch.cuda.current_stream(device)
+    res = {}
+    for kind, iters, per in ((0, 2048, 16), (1, 256, 4)):
+        ms = None
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            r = lib.ugks_probe_fp64(ctypes.c_void_p(out.data_ptr()), kind, nb, nt, iters,
+                                    ctypes.c_void_p(st.cuda_stream))
+            e1.record(st)
+            torch.cuda.synchronize()
+            if r != U.OK:
+                return None
+            t = e0.elapsed_time(e1)
+            ms = t if ms is None else min(ms, t)
+        res[kind] = nb * nt * iters * per / (ms * 1e-3)
+    return {"fma_tflops": res[0] / 1e12, "exp_per_s": res[1], "threads": nb * nt,
+            "how": "independent FP64 FMA / exp chains, best of 3 launches, CUDA events"}
+
+
+def extra_workload(name, device, steps, warmup, peak, peak_kind, tune):
+    """Whole-step rate of another paper-shaped workload (reported beside the
+    headline): the two-body separation (C3-like) or the batched MEMS sweep."""
+    import torch
+    from paper_2604_09984_gb300 import ugks as U
+    if name == "mems_batch":
+        cases = wl.mems_batch()
+        ms, units, launches, host_s, e2e_s, h2d, d2h, nfield, tiles = batch_arm(cases, steps, warmup, device)
+        torch.cuda.empty_cache()
+        return {"workload": "mems_batch: %d instances, %d field cells, 20^2-40^2 velocities, Kn 0.01-2"
+                            % (len(cases), nfield),
+                "value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+                "e2e": {"value": units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches, "roofline": None,
+                "note": "per-instance kernels on 64 streams; roofline of the single-instance headline applies"}
+    case = make_case(name, 0.01)
+    s, ms, nfield, launches, _ = time_arm(case, U.FP32, steps, warmup, device, profile=False, tune=tune)
+    prof = profiled_steps(s, 1)
+    value = nfield * case.nv * case.n_inner * steps / (ms * 1e-3)
+    roof = dominant_roofline(prof, nfield, case.nv, s.nc, 8, peak, peak_kind)
+    tab = kernel_table(prof, nfield, case.nv, s.nc, 8)
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    return {"workload": workload_label(case), "value": value, "unit": UNIT, "ms_per_step": ms / steps,
+            "steps": steps, "gpu_launches": launches, "roofline": roof, "kernels": tab}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -387,12 +519,15 @@ def main():
     ap.add_argument("--kn", type=float, default=0.1)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-plain comparison arm")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
-    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-bf16", action="store_true", help="skip the bf16-storage experiment arm")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the two-body and batched workloads reported beside the headline")
+    ap.add_argument("--extra-steps", type=int, default=2)
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default sweep tile (for profiler runs, where the tuner's timings are distorted)")
     args = ap.parse_args()
-    if args.workload == "mems_batch":
+    if args.workload == "mems_batch" or not args.no_extra:
         # one hardware work queue per instance stream (read when CUDA starts)
         os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
@@ -425,38 +560,26 @@ def main():
     case = make_case(args.workload, args.kn)
     steps = max(1, args.steps)
     warmup = max(3, args.warmup)
+    peak, peak_kind = peaks()
 
+    # the headline: timed steps with no per-launch event bracketing
     clk = Clocks(local)
     clk.start()
-    s, ms, nfield, launches, prof = time_arm(case, U.FP32, steps, warmup, device, profile=True,
-                                             tune=not args.no_tune, dist=dist)
+    s, ms, nfield, launches, _ = time_arm(case, U.FP32, steps, warmup, device, profile=False,
+                                          tune=not args.no_tune, dist=dist)
     clocks = clk.stop()
     ms = max_over_ranks(ms, dist, device)
     units = nfield * case.nv * case.n_inner * steps * world
     value = units / (ms * 1e-3)
-    # roofline of the dominant kernel group (CUDA events on the launch stream)
-    peak, peak_kind = peaks()
-    groups = {g: v for g, v in prof.items() if v[1] > 0}
-    dom = max(groups, key=lambda g: groups[g][0])
-    dms, dn = groups[dom]
+    # per-group table and the dominant kernel's roofline from separate
+    # profiled steps (CUDA events on the stream each group is launched on)
+    prof = profiled_steps(s, min(steps, 5))
     pair = 8
-    abytes = algorithmic_bytes(dom, pair, nfield, case.nv, s.nc)
-    if abytes > 0:
-        ach = abytes / (dms / dn * 1e-3) / 1e9
-        default = args.workload == "mems" and args.kn == 0.1
-        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "traffic": ncu_traffic(dom) if default else None,
-                "peak_kind": peak_kind, "bytes_per_launch": abytes, "ms_per_launch": dms / dn}
-    else:
-        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None,
-                "frac": None, "traffic": None, "ms_per_launch": dms / dn}
-    # per-group table for the streaming kernels
-    breakdown = {}
-    for g, (gms, gn) in groups.items():
-        b = algorithmic_bytes(g, pair, nfield, case.nv, s.nc)
-        breakdown[g] = {"ms_total": round(gms, 3), "launches": gn, "share": round(gms / sum(v[0] for v in groups.values()), 4)}
-        if b:
-            breakdown[g]["GBps"] = round(b / (gms / gn * 1e-3) / 1e9, 1)
+    default = args.workload == "mems" and args.kn == 0.1
+    dom_tab = kernel_table(prof, nfield, case.nv, s.nc, pair)
+    roof = dominant_roofline(prof, nfield, case.nv, s.nc, pair, peak, peak_kind)
+    if default and roof.get("kernel"):
+        roof["traffic"] = ncu_traffic(roof["kernel"])
     e2e_ms, h2d, d2h = e2e_arm(s, steps)
     e2e_val = nfield * case.nv * case.n_inner * steps * world / (e2e_ms * 1e-3)
     tiles = s.tiles
@@ -465,21 +588,20 @@ def main():
     torch.cuda.empty_cache()
     fp64 = None
     if not args.no_fp64:
-        s64, ms64, nf64, _, prof64 = time_arm(case, U.FP64, max(1, args.fp64_steps), 3, device, profile=True,
-                                              tune=not args.no_tune)
-        v64 = nf64 * case.nv * case.n_inner * max(1, args.fp64_steps) / (ms64 * 1e-3)
-        fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / max(1, args.fp64_steps),
-                "speedup_fp32_over_fp64": value / world / v64}
-        # %HBM of the FP64 path's dominant streaming group (16-byte pairs)
-        g64 = {g: v for g, v in prof64.items() if v[1] > 0 and algorithmic_bytes(g, 16, nf64, case.nv, s64.nc)}
-        if g64:
-            dom64 = max(g64, key=lambda g: g64[g][0])
-            ms_l = g64[dom64][0] / g64[dom64][1]
-            ach64 = algorithmic_bytes(dom64, 16, nf64, case.nv, s64.nc) / (ms_l * 1e-3) / 1e9
-            fp64["roofline"] = {"kernel": dom64, "bound": "hbm", "achieved": ach64, "peak": peak,
-                                "unit": "GB/s", "frac": ach64 / peak, "ms_per_launch": ms_l,
-                                "note": "the FP64 path is bound by the FP64 pipe, not by HBM"}
+        n64 = max(3, args.fp64_steps)
+        s64, ms64, nf64, _, _ = time_arm(case, U.FP64, n64, 3, device, profile=False, tune=not args.no_tune)
+        prof64 = profiled_steps(s64, 1)
+        v64 = nf64 * case.nv * case.n_inner * n64 / (ms64 * 1e-3)
+        fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / n64, "steps": n64,
+                "speedup_fp32_over_fp64": value / world / v64,
+                "kernels": kernel_table(prof64, nf64, case.nv, s64.nc, 16)}
+        r64 = dominant_roofline(prof64, nf64, case.nv, s64.nc, 16, peak, peak_kind)
+        r64["note"] = "the FP64 path is bound by the FP64 pipe (probe below), not by HBM"
+        fp64["roofline"] = r64
         s64.close()
+        del s64
+        torch.cuda.empty_cache()
+        fp64["fp64_probe"] = fp64_probe(device)
     bf16 = None
     if not args.no_bf16:
         # experiment: f stored as bf16 pairs (same FP32 arithmetic)
@@ -489,27 +611,43 @@ def main():
         bf16 = {"value": vb, "unit": UNIT, "ms_per_step": msb / steps, "speedup_over_fp32": vb / (value / world),
                 "note": "experiment: f stored as bf16 pairs, FP32 arithmetic; errors ~1e-3 relative"}
         sb.close()
+        del sb
+        torch.cuda.empty_cache()
+    extra = None
+    if not args.no_extra and args.workload == "mems" and world == 1:
+        extra = {}
+        for name in ("tsto", "mems_batch"):
+            extra[name] = extra_workload(name, device, max(1, args.extra_steps), 3, peak, peak_kind,
+                                         not args.no_tune)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
         "warmup": warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_label(case), "precision": "FP32 f and per-velocity arithmetic, FP64 moments/geometry",
+        "config": {"workload": workload_label(case),
+                   "precision": "FP32 f and per-velocity arithmetic; FP64 moments, macroscopic update, "
+                                "per-face interface state and geometry",
                    "l2": "inputs larger than L2 (f alone %.0f MB)" % (s_bytes(case) / 1e6),
                    "field_cells": nfield, "nv": case.nv, "n_inner": case.n_inner,
-                   "sweep_tiles": ("autotuned (items per CTA and diagonal, velocities per thread, rings fwd/bwd): %s" % (tiles,)) if tiles
-                   else "default (1024 items per CTA and diagonal, ring by rule)",
+                   "sweep_tiles": ("autotuned (items per warp step, velocities per lane, rings fwd/bwd): %s" % (tiles,))
+                   if tiles else "default (2 velocities per lane, rings of 4 steps)",
+                   "timing": "headline steps without per-launch events; kernel table and roofline from "
+                             "separate profiled steps",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "per_physical_step": value / case.n_inner,
         "clocks": clocks,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "roofline": roof,
-        "kernels": breakdown,
+        "kernels": dom_tab,
         "fp64_plain": fp64,
         "bf16_f_storage": bf16,
+        "other_workloads": extra,
     }
     if rank == 0 and not args.no_cpu and world == 1:
-        line["cpu_baseline"] = cpu_baseline(args.kn, steps=2)
+        single = cpu_baseline(args.kn, steps=2)
+        multi = cpu_baseline_multicore(args.kn)
+        multi["single_core"] = single
+        line["cpu_baseline"] = multi
     elif rank == 0:
         line["cpu_baseline"] = None
     if rank == 0:

@@ -279,6 +279,19 @@ int ugks_get_geometry(ugks_ctx *ctx, double *vol_old, double *vol_new,
  * (counted on the host at each launch). */
 int64_t ugks_launch_count(const ugks_ctx *ctx);
 
+/* Bounded waits.  The only device-side waits of a step are those of the
+ * wavefront sweeps: the macro LU-SGS CTA waits (mbarrier) for the bulk copy of
+ * the next diagonal's records, the bands of a micro-sweep CTA wait for the
+ * band before them (shared-memory progress counters, Sec. 2.2 sweep order).
+ * Each wait polls at most `polls` times (0 restores the default, 2^21); a wait
+ * that runs out sets a flag, the CTA stops its sweep at the end of the
+ * current step, waits (default bound) for every copy it issued, and exits;
+ * the step's results are then invalid and the next synchronising call
+ * returns UGKS_ERR_TIMEOUT (and clears the flag, leaving the context usable:
+ * set a valid state with ugks_set_state before stepping again).  Takes effect
+ * for work issued after the call.  Errors: UGKS_ERR_ARG (polls < 0). */
+int ugks_set_wait_limit(ugks_ctx *ctx, int polls);
+
 /* Kernel groups timed by the profiler (CUDA events around every launch of the
  * group, on the stream it is launched on: the context's stream, or for the
  * macro sweep the library's internal side stream that overlaps it with the
@@ -307,6 +320,16 @@ int ugks_profile_enable(ugks_ctx *ctx, int on);
  * UGKS_NPROF entries, either may be NULL); reset != 0 clears the totals. */
 int ugks_profile_read(ugks_ctx *ctx, double *ms, int64_t *launches, int reset);
 
+/* FP64 throughput probe (measurement, no counterpart in the paper): the FP64
+ * path of the scheme is bound by the FP64 pipe of the GPU, so its roofline is
+ * the measured FP64 rate.  kind 0: nblocks x nthreads threads each run 8
+ * independent fused-multiply-add chains for `iters` rounds (16 * iters flops
+ * a thread); kind 1: 4 independent exp chains (4 * iters exponentials a
+ * thread).  `out` is a DEVICE buffer of nblocks * nthreads doubles (the
+ * results, so no work is dead).  Asynchronous on `stream`; the caller times
+ * it with events on that stream.  Errors: UGKS_ERR_ARG, UGKS_ERR_CUDA. */
+int ugks_probe_fp64(double *out, int kind, int nblocks, int nthreads, int iters, void *stream);
+
 /* Allocation-free receptor interpolation.  No counterpart in the paper: it
  * exists for callers that cannot allocate device memory at all (a host
  * framework that owns every device allocation, or code that must not call
@@ -322,20 +345,24 @@ int ugks_profile_read(ugks_ctx *ctx, double *ms, int64_t *launches, int reset);
  * pairs of every cell, k = iy*nvx + ix), W (ncells x 4) and q (ncells x 2)
  * updated in place (W and q may be NULL); receptors: nrec cell ids whose rows
  * are overwritten; donors / weights: nrec x 5 stencils and weights, row r for
- * receptors[r], donor -1 unused (the layout of ugks_get_connectivity rows);
- * a row whose first donor is -1 is left unchanged; donor or receptor ids
- * outside [0, ncells) are skipped.  Every receptor reads its donors' values
- * from before the call (Jacobi).  stream: a cudaStream_t (NULL = default).
- * Asynchronous; allocates nothing and calls no allocating routine.
+ * receptors[r], donor -1 unused (the layout of ugks_get_connectivity rows).
+ * A row whose first donor is -1 is left unchanged (an orphan).  Donor ids
+ * outside [0, ncells) other than -1 are skipped and the remaining weights of
+ * that row are renormalised to their sum; a row with no valid donor left,
+ * and a row whose receptor id lies outside [0, ncells), is left unchanged.
+ * Every receptor reads its donors' values from before the call (Jacobi).
+ * stream: a cudaStream_t (NULL = default).  Asynchronous; allocates nothing
+ * and calls no allocating routine.
  *
  * Errors: UGKS_ERR_ARG when a pointer is NULL or
- * 2*nrec*nv + 6*nrec > UGKS_STATIC_SCRATCH_DOUBLES (nothing is launched);
+ * 2*nrec*nv + 7*nrec > UGKS_STATIC_SCRATCH_DOUBLES (nothing is launched);
  * UGKS_ERR_CUDA when the device lookup of the scratch or a launch fails.
- * The first call on a device looks up the scratch address with
- * cudaGetSymbolAddress (with that device current); make that first call
- * before any stream capture.  All calls on a device share the one scratch
- * array, which keeps the last call's contents: calls that overlap on the GPU
- * (different streams, no ordering between them) race. */
+ * The first call in each CUDA context looks up the scratch address with
+ * cudaGetSymbolAddress (with that context's device current; a device reset
+ * creates a new context and the next call looks the address up again); make
+ * that first call before any stream capture.  All calls on a device share
+ * the one scratch array, which keeps the last call's contents: calls that
+ * overlap on the GPU (different streams, no ordering between them) race. */
 #define UGKS_STATIC_SCRATCH_DOUBLES (1 << 19)
 int ugks_idw_interpolate_static(double *f, double *W, double *q, int ncells, int nv,
                                 const int32_t *receptors, int nrec,

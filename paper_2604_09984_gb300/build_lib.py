@@ -12,7 +12,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "libugks.so")
-SOURCES = ["ugks_kernels.cu", "ugks_tile.cu", "ugks_sweep.cu", "ugks_overset.cu", "ugks_api.cu", "ugks_static.cu"]
+SOURCES = ["ugks_kernels.cu", "ugks_tile.cu", "ugks_sweep.cu", "ugks_overset.cu", "ugks_api.cu", "ugks_static.cu",
+           "ugks_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -ftz=true: FP32 subnormals flush to zero (none of the path's FP32 values is
 # meaningful below 1e-38; the FP32 intrinsics then need no subnormal fix-ups)

@@ -650,6 +650,13 @@ const char *ugks_last_error(const ugks_ctx *ctx) { return ctx ? ctx->err.c_str()
 
 int64_t ugks_launch_count(const ugks_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
+int ugks_set_wait_limit(ugks_ctx *ctx, int polls) {
+  if (!ctx) return UGKS_ERR_ARG;
+  if (polls < 0) return fail(ctx, UGKS_ERR_ARG, "negative poll limit");
+  ctx->d.wait_polls = polls == 0 ? kWaitPolls : polls;
+  return UGKS_OK;
+}
+
 int ugks_sizes(const ugks_ctx *ctx, int *ncells, int *nfaces, int *nv, int *nv_stride) {
   if (!ctx || !ctx->mesh_ready) return UGKS_ERR_ORDER;
   if (ncells) *ncells = ctx->d.nc;
@@ -710,6 +717,7 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
   d.Kint = ctx->p.K; d.Keff = 1 + ctx->p.K;
   d.Pr = ctx->p.Pr; d.omega = ctx->p.omega; d.mu_ref = ctx->p.mu_ref;
   d.cfl_s = ctx->p.cfl_s; d.cfl_pseudo = ctx->p.cfl_pseudo; d.dt = 1.0;
+  d.wait_polls = kWaitPolls;
   d.vbox[0] = ctx->p.vx_min; d.vbox[1] = ctx->p.vx_max; d.vbox[2] = ctx->p.vy_min; d.vbox[3] = ctx->p.vy_max;
   {
     double lam = 1.0 / (2.0 * ctx->p.farfield[3]);

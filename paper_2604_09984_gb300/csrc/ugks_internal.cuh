@@ -129,7 +129,12 @@ struct Dev {
   const int *tiles;          // ntiles*3: block, i0, j0 of the 8x8 cell tiles
   int ntiles;
   int *err;                  // error flags
+  int wait_polls;            // bounded waits (sweeps): polls before giving up (EF_TIMEOUT)
 };
+
+// Polls of a bounded wait before it gives up; the drain of a CTA's own copies
+// after a timeout always uses the default.
+constexpr int kWaitPolls = 1 << 21;
 
 // face geometry record / per-cell sweep record
 enum { FG_SNX = 0, FG_SNY, FG_SUN, FG_UFX, FG_UFY, FG_DXLX, FG_DXLY, FG_DXRX, FG_DXRY, NFG = 12 };
@@ -242,10 +247,10 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *mb, unsigned p
       : "memory");
   return ok != 0;
 }
-// Wait for a phase of an mbarrier with a bounded number of polls; false
-// (and EF_TIMEOUT in *err) when the limit runs out.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *mb, unsigned parity, int *err) {
-  for (int n = 0; n < (1 << 21); ++n)
+// Wait for a phase of an mbarrier with at most `polls` polls; false (and
+// EF_TIMEOUT in *err) when the limit runs out.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *mb, unsigned parity, int *err, int polls = kWaitPolls) {
+  for (int n = 0; n < polls; ++n)
     if (mbar_try_wait(mb, parity)) return true;
   atomicOr(err, EF_TIMEOUT);
   return false;

@@ -786,6 +786,8 @@ template <int NS, int TPR> __global__ void __launch_bounds__(512) k_macro_sweep_
     for (int m = 0; m < 4; ++m) { buf0[4 * row + m] = 0.f; buf1[4 * row + m] = 0.f; }
   __syncthreads();
   const unsigned diag_bytes = (unsigned)nj * NMR32 * sizeof(float);
+  bool to = false;                   // this thread's bounded wait ran out
+  int issued = -1, waited = -1;      // thread 0: last stage copied into / waited for
   for (int pass = 0; pass < 2; ++pass) {
     float4 prev = make_float4(0.f, 0.f, 0.f, 0.f), first = prev;
     // diagonal of step it, and its position in the ring (g = steps so far)
@@ -798,11 +800,15 @@ template <int NS, int TPR> __global__ void __launch_bounds__(512) k_macro_sweep_
       fence_proxy_async_shared();
       mbar_arrive_expect_tx(&mb[s], diag_bytes);
       bulk_g2s(ring + (size_t)s * rows * NMR32, rb + (size_t)diag_of(it) * nj * NMR32, diag_bytes, &mb[s]);
+      issued = gstep(it);
     };
+    // a bounded wait; a thread that gives up marks `to`, and the CTA stops
+    // at the end of the diagonal (uniform decision at the barrier)
     auto wait_stage = [&](int it) {
       if (NS == 0 || it >= nd) return;
       int g = gstep(it);
-      mbar_wait(&mb[g % NSR_], (unsigned)(g / NSR_) & 1u, d.err);
+      if (!mbar_wait(&mb[g % NSR_], (unsigned)(g / NSR_) & 1u, d.err, d.wait_polls)) to = true;
+      else if (threadIdx.x == 0) waited = g;
     };
     // registers of the next diagonal: mask, this thread's slot records,
     // R (pass 0) or the forward increment (pass 1), 1/diag
@@ -885,9 +891,10 @@ template <int NS, int TPR> __global__ void __launch_bounds__(512) k_macro_sweep_
       // the next diagonal's records, read into registers before the barrier
       wait_stage(it + 1);
       fetch(it + 1);
-      __syncthreads();
+      if (__syncthreads_or(to)) break;
       cur ^= 1;
     }
+    if (__syncthreads_or(to)) break;
     // the increments stored above are read by the next pass's bulk copies
     fence_proxy_async_global();
     __threadfence_block();
@@ -895,6 +902,11 @@ template <int NS, int TPR> __global__ void __launch_bounds__(512) k_macro_sweep_
       for (int m = 0; m < 4; ++m) { buf0[4 * row + m] = 0.f; buf1[4 * row + m] = 0.f; }
     __syncthreads();
   }
+  // after a timeout: no copy of this CTA may still be in flight when it
+  // exits, so thread 0 waits (default bound) for every stage it issued and
+  // nobody waited for; the results of the step are invalid (EF_TIMEOUT)
+  if (NS > 0 && threadIdx.x == 0 && issued > waited)
+    for (int g = waited + 1; g <= issued; ++g) mbar_wait(&mb[g % NSR_], (unsigned)(g / NSR_) & 1u, d.err);
 }
 
 // LU-SGS of Eq. dualTimeStepping_macro (Sec. 2.2), one CTA per block,

@@ -26,7 +26,6 @@ namespace ugks {
 constexpr int WS_LR = 64;            // most ring entries between two bands (cells): the next band
                                      // trails by ROWS steps, the rest of the ring is slack; fewer
                                      // (a power of two >= 2) where shared memory is short
-constexpr int WS_POLLS = 1 << 22;    // bounded wait on a neighbour band
 
 // A warp: ROWS = 32 / QL rows of a block, QL lanes per row, VPT velocities a
 // lane (QL * VPT consecutive velocities a warp).
@@ -148,7 +147,7 @@ __global__ void __launch_bounds__(1024) k_wsweep(Dev d, const int *work, int lr)
       int n = 0;
       while (prog[w - 1] <= il && ok) {
         __nanosleep(32);                 // leave the issue slots to the other warps
-        if (++n > WS_POLLS) { ok = false; atomicOr(d.err, EF_TIMEOUT); }
+        if (++n > d.wait_polls) { ok = false; atomicOr(d.err, EF_TIMEOUT); }
       }
       __threadfence_block();
       const T2 *src = lin + (size_t)(il & (lr - 1)) * VW;
@@ -242,7 +241,7 @@ __global__ void __launch_bounds__(1024) k_wsweep(Dev d, const int *work, int lr)
       int n = 0;
       while (cons[w] + lr <= il && ok) {
         __nanosleep(32);
-        if (++n > WS_POLLS) { ok = false; atomicOr(d.err, EF_TIMEOUT); }
+        if (++n > d.wait_polls) { ok = false; atomicOr(d.err, EF_TIMEOUT); }
       }
       T2 *dst = lout + (size_t)(il & (lr - 1)) * VW;
 #pragma unroll

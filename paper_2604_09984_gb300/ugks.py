@@ -67,6 +67,8 @@ SYMBOLS = {
     "ugks_get_connectivity": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "ugks_get_geometry": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ugks_launch_count": (c_int64, [c_void_p]),
+    "ugks_set_wait_limit": (c_int, [c_void_p, c_int]),
+    "ugks_probe_fp64": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p]),
     "ugks_profile_enable": (c_int, [c_void_p, c_int]),
     "ugks_profile_read": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int64), c_int]),
     "ugks_idw_interpolate_static": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p,
@@ -324,6 +326,10 @@ class Solver:
 
     def launch_count(self):
         return int(self.lib.ugks_launch_count(self.ctx))
+
+    def set_wait_limit(self, polls):
+        """Polls of the sweeps' bounded waits (ugks_set_wait_limit; 0 = default)."""
+        self._check(self.lib.ugks_set_wait_limit(self.ctx, int(polls)))
 
     def profile(self, on: bool):
         self._check(self.lib.ugks_profile_enable(self.ctx, int(bool(on))))

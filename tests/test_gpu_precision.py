@@ -27,11 +27,18 @@ def built():
 
 
 def cases():
-    return {
+    c = {
         "channel": (wl.channel(ni=12, nj=7, nv=10, n_inner=3), 3),
         "mems": (wl.mems(nbi=48, nbj=24, noi=32, noj=12, nv=8, stretch=1.15, n_inner=2), 3),
         "two_bodies": (wl.tsto(nbi=80, nbj=40, noi=24, noj=10, nv=22, n_inner=2), 1),
     }
+    # the MEMS Knudsen numbers of the paper-shaped sweep (0.1, 0.5, 1.0), the
+    # ends of the batched range (0.01, 2) and a near-continuum case (0.001,
+    # dt_s / tau ~ 2 on the background cells, below 1 on the O-grid), so both
+    # branches of the time integrals q1..q5 run
+    for kn in (0.001, 0.01, 0.5, 1.0, 2.0):
+        c["mems_kn%g" % kn] = (wl.mems(nbi=48, nbj=24, noi=32, noj=12, nv=16, stretch=1.15, n_inner=2, Kn=kn), 2)
+    return c
 
 
 def primitives(W, K):
@@ -76,7 +83,8 @@ def errors(W, wall, r):
     return e
 
 
-@pytest.mark.parametrize("which", ["channel", "mems", "two_bodies"])
+@pytest.mark.parametrize("which", ["channel", "mems", "two_bodies", "mems_kn0.001", "mems_kn0.01", "mems_kn0.5",
+                                   "mems_kn1", "mems_kn2"])
 def test_errors_against_oracle(which):
     case, nsteps = cases()[which]
     r = Run(case)

@@ -319,7 +319,8 @@ def run_batch(args, world, rank, device, dist=None):
                                % (len(cases), nfield, sum(c.ncells * c.nv for c in cases)),
                    "precision": "FP32 f and per-velocity arithmetic, FP64 moments/geometry",
                    "l2": "inputs larger than L2", "streams": len(cases),
-                   "sweep_tiles": "autotuned per instance (items, velocities per thread, rings fwd/bwd): %s" % tiles,
+                   "tiles": "autotuned per instance (sweep items, velocities per lane, rings fwd/bwd, face chunk, "
+                            "threads per face): %s" % tiles,
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "host_issue_ms_per_step": host_s * 1e3 / steps,
         "clocks": clocks,
@@ -628,8 +629,9 @@ def main():
                                 "per-face interface state and geometry",
                    "l2": "inputs larger than L2 (f alone %.0f MB)" % (s_bytes(case) / 1e6),
                    "field_cells": nfield, "nv": case.nv, "n_inner": case.n_inner,
-                   "sweep_tiles": ("autotuned (items per warp step, velocities per lane, rings fwd/bwd): %s" % (tiles,))
-                   if tiles else "default (2 velocities per lane, rings of 4 steps)",
+                   "tiles": ("autotuned (sweeps: items per warp step, velocities per lane, rings fwd/bwd; "
+                             "face kernels: velocities per chunk, threads per face): %s" % (tiles,))
+                   if tiles else "default (sweeps: 2 velocities per lane, rings of 4 steps; face kernels: 16, 2)",
                    "timing": "headline steps without per-launch events; kernel table and roofline from "
                              "separate profiled steps",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},

@@ -212,21 +212,27 @@ int ugks_advance_batch(ugks_ctx *const *ctx, int n, const double *t_new,
  * Synchronises the stream.  Errors: UGKS_ERR_ORDER, UGKS_ERR_ARG. */
 int ugks_wall_torque(ugks_ctx *ctx, const double *center, double *torque);
 
-/* Sweep autotuner: times the micro LU-SGS sweeps (`reps` timed passes after
- * one warm-up, CUDA events on the stream) for every candidate -- velocities
- * per lane in {2, 4} (FP32 paths; 2 in FP64) and, for each, the prefetch ring
- * depth in {2, 4, 6} steps chosen separately for the forward and the backward
- * sweep (shallower where shared memory is short) -- on the context's own
- * state, and keeps the fastest.  The sweeps run as skewed wavefronts (a warp
- * takes a band of 8 rows, 4 lanes a row; 16 rows, 2 lanes a row when a
- * block is taller than 256 cells); every candidate sweeps each velocity in
- * the same lexicographic order, so only the time changes.  f is saved before
- * the trials and restored after them.  Needs a preceding ugks_step (the
- * sweeps read per-cell records the step writes).  `items` (the (cell,
- * velocity) items of one warp step, 32 x velocities per lane), `vpt`,
- * `ring_fwd`, `ring_bwd` (HOST, each may be NULL) receive the choice.
- * Synchronises the stream.  Errors: UGKS_ERR_ORDER, UGKS_ERR_CUDA. */
-int ugks_autotune(ugks_ctx *ctx, int reps, int *items, int *vpt, int *ring_fwd, int *ring_bwd);
+/* Tile autotuner, on the context's own state (`reps` timed passes after one
+ * warm-up of each candidate, CUDA events on the stream), keeping the fastest:
+ *  - the face kernels (velocity reduction and flux divergence, FP32 paths):
+ *    their tile of 8x8 cells walks the velocities in chunks of `face_vk` in
+ *    {8, 16, 32} with `face_nh` in {1, 2} threads per face slot (each takes
+ *    face_vk / face_nh velocities of a chunk); the FP64 path keeps (8, 2);
+ *  - the micro LU-SGS sweeps, skewed wavefronts (a warp takes a band of 8
+ *    rows, 4 lanes a row; 16 rows, 2 lanes a row when a block is taller than
+ *    256 cells): velocities per lane `vpt` in {2, 4} (FP32 paths; 2 in FP64)
+ *    and, per sweep, the prefetch ring depth in {2, 4, 6} steps (shallower
+ *    where shared memory is short).
+ * The candidates differ only in the grouping of the FP32 face sums over the
+ * velocities (partial sums per thread and chunk, folded error-free), i.e. in
+ * rounding; the sweeps take each velocity in the same lexicographic order.  f is saved before the trials and restored after them.  Needs
+ * a preceding ugks_step (the kernels read records the step writes).  `items`
+ * (the (cell, velocity) items of one sweep warp step, 32 x vpt), `vpt`,
+ * `ring_fwd`, `ring_bwd`, `face_vk`, `face_nh` (HOST, each may be NULL)
+ * receive the choice.  Synchronises the stream.  Errors: UGKS_ERR_ORDER,
+ * UGKS_ERR_CUDA. */
+int ugks_autotune(ugks_ctx *ctx, int reps, int *items, int *vpt, int *ring_fwd, int *ring_bwd, int *face_vk,
+                  int *face_nh);
 
 /* Copy the macroscopic fields to caller memory (host or device pointers,
  * cudaMemcpyDefault): W (ncells x 4: rho, rho Vx, rho Vy, rho E), q

@@ -34,6 +34,7 @@ struct ugks_ctx {
   int nwork_cap = 0;                  // work-list capacity (largest tuning candidate)
   int sweep_vpt = 2;                  // micro sweeps: velocities per lane
   int ns_fwd = 4, ns_bwd = 4;         // prefetch ring depths (steps) of the two sweeps
+  int face_tile = 0;                  // tile shape of the face kernels (face_tile_shape)
   bool stepped = false;               // a ugks_step has run (sweep records valid)
   int *work = nullptr;
   int *prev_status = nullptr, *n_orphan = nullptr, *blk_order = nullptr;
@@ -517,7 +518,7 @@ void flux_prep(ugks_ctx *ctx, int level_n) {
   Dev &d = ctx->d;
   cudaStream_t s = ctx->st;
   { Prof p(ctx, UGKS_PROF_CELL); launch_ghost_gradW(d, s); }
-  { Prof p(ctx, UGKS_PROF_FACE_REDUCE); launch_face_reduce_tile(d, s, ctx->fp32); }
+  { Prof p(ctx, UGKS_PROF_FACE_REDUCE); launch_face_reduce_tile(d, s, ctx->fp32, ctx->face_tile); }
   { Prof p(ctx, UGKS_PROF_FACE_COEF); launch_face_coef(d, s, ctx->fp32); }
   { Prof p(ctx, UGKS_PROF_CELL); launch_cell_macro(d, s, level_n); }
   ctx->launches += 6;
@@ -680,6 +681,11 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
   ctx->sweep_vpt = sweep_vpt_for(&ctx->p);
   ctx->sweep_nw = sweep_nw_for(nblocks, blocks);
   ctx->sweep_ql = wsweep_ql(max_nj_of(nblocks, blocks));
+  ctx->face_tile = face_tile_default();
+  if (const char *e = getenv("UGKS_FACE_TILE")) {      // tuning by hand: index of face_tile_shape
+    int v = atoi(e);
+    if (v >= 0 && v < face_tile_count()) ctx->face_tile = v;
+  }
   if (const char *e = getenv("UGKS_SWEEP_NS")) {
     int n = atoi(e);
     if (n == 2 || n == 4 || n == 6) ctx->ns_fwd = ctx->ns_bwd = n;
@@ -926,7 +932,7 @@ int ugks_step(ugks_ctx *ctx, double dt, int n_inner) {
     CK(cudaStreamWaitEvent(ctx->side, ctx->ev_flux, 0));
     { Prof p(ctx, UGKS_PROF_MACRO_SWEEP, ctx->side); launch_macro_sweep(d, ctx->side, ctx->max_nj, fp); }
     CK(cudaEventRecord(ctx->ev_macro, ctx->side));
-    { Prof p(ctx, UGKS_PROF_RHS); launch_flux_tile(d, s, fp); }                              // Step 3
+    { Prof p(ctx, UGKS_PROF_RHS); launch_flux_tile(d, s, fp, ctx->face_tile); }              // Step 3
     CK(cudaStreamWaitEvent(s, ctx->ev_macro, 0));
     { Prof p(ctx, UGKS_PROF_RESIDUAL); launch_residual(d, s, it == 0, fp); }                 // Step 5
     { Prof p(ctx, UGKS_PROF_MICRO_FWD); launch_wsweep(d, s, 0, ctx->work, ctx->nwork, ctx->sweep_nw, ctx->ns_fwd, ctx->sweep_vpt, fp, ctx->sweep_ql); }  // Step 6
@@ -967,7 +973,8 @@ int ugks_advance_batch(ugks_ctx *const *ctx, int n, const double *t_new, const d
   return UGKS_OK;
 }
 
-int ugks_autotune(ugks_ctx *ctx, int reps, int *items_out, int *vpt_out, int *ring_fwd_out, int *ring_bwd_out) {
+int ugks_autotune(ugks_ctx *ctx, int reps, int *items_out, int *vpt_out, int *ring_fwd_out, int *ring_bwd_out,
+                  int *face_vk_out, int *face_nh_out) {
   if (!ctx || !ctx->mesh_ready) return UGKS_ERR_ORDER;
   if (!ctx->stepped) return fail(ctx, UGKS_ERR_ORDER, "ugks_autotune needs a preceding ugks_step");
   if (reps < 1) reps = 3;
@@ -975,20 +982,19 @@ int ugks_autotune(ugks_ctx *ctx, int reps, int *items_out, int *vpt_out, int *ri
   cudaStream_t s = ctx->st;
   int fp = ctx->fp32;
   size_t fbytes = (ctx->fbf ? 4 : fp ? 8 : 16) * (size_t)d.nc * d.nvp;
-  // f is restored afterwards; the sweep buffer and the flux divergence are
-  // rewritten by every inner iteration, so the trials may use them
-  CK(cudaMemcpyAsync(d.Dbuf, d.f, fbytes, cudaMemcpyDeviceToDevice, s));
+  // f is restored afterwards (kept in the level-n term's buffer, which the
+  // next step rewrites); the sweep buffer, the flux divergence and the face
+  // sums are rewritten by every inner iteration, so the trials may use them
+  CK(cudaMemcpyAsync(d.Tn, d.f, fbytes, cudaMemcpyDeviceToDevice, s));
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  float best = 1e30f;
-  int bv = ctx->sweep_vpt, bf = ctx->ns_fwd, bb = ctx->ns_bwd;
   int r = UGKS_OK;
-  // time one sweep (pass 0 forward, 1 backward) with ring depth ns
-  auto trial = [&](int pass, int ns, float &ms) -> int {
-    for (int rep = 0; rep <= reps; ++rep) {     // the first pass warms up
+  // time `launch` (reps passes after one warm-up)
+  auto timed = [&](auto launch, float &ms) -> int {
+    for (int rep = 0; rep <= reps; ++rep) {
       if (rep == 1) cudaEventRecord(e0, s);
-      launch_wsweep(d, s, pass, ctx->work, ctx->nwork, ctx->sweep_nw, ns, ctx->sweep_vpt, fp, ctx->sweep_ql);
+      launch();
     }
     cudaEventRecord(e1, s);
     int q = cuda_check(ctx, cudaEventSynchronize(e1), "autotune");
@@ -997,7 +1003,22 @@ int ugks_autotune(ugks_ctx *ctx, int reps, int *items_out, int *vpt_out, int *ri
     ctx->launches += reps + 1;
     return q;
   };
+  // face kernels: reduction + flux divergence for every tile shape (FP32)
+  int bt = ctx->face_tile;
+  if (fp) {
+    float best = 1e30f;
+    for (int v = 0; v < face_tile_count() && !r; ++v) {
+      float m1, m2;
+      if ((r = timed([&] { launch_face_reduce_tile(d, s, fp, v); }, m1))) break;
+      if ((r = timed([&] { launch_flux_tile(d, s, fp, v); }, m2))) break;
+      if (m1 + m2 < best) { best = m1 + m2; bt = v; }
+    }
+  }
+  // micro sweeps: velocities per lane, and per sweep the ring depth
+  float best = 1e30f;
+  int bv = ctx->sweep_vpt, bf = ctx->ns_fwd, bb = ctx->ns_bwd;
   for (int vpt : kTuneVpt) {
+    if (r) break;
     if (!fp && vpt != 2) continue;
     if ((r = set_sweep_tiles(ctx, vpt))) break;
     float tf = 1e30f, tb = 1e30f;
@@ -1005,9 +1026,9 @@ int ugks_autotune(ugks_ctx *ctx, int reps, int *items_out, int *vpt_out, int *ri
     for (int ns : kTuneRing) {
       if (!wsweep_fits(fp, ctx->fbf, vpt, ctx->sweep_nw, ns, ctx->sweep_ql)) continue;
       float ms;
-      if ((r = trial(0, ns, ms))) break;
+      if ((r = timed([&] { launch_wsweep(d, s, 0, ctx->work, ctx->nwork, ctx->sweep_nw, ns, vpt, fp, ctx->sweep_ql); }, ms))) break;
       if (ms < tf) { tf = ms; nf = ns; }
-      if ((r = trial(1, ns, ms))) break;
+      if ((r = timed([&] { launch_wsweep(d, s, 1, ctx->work, ctx->nwork, ctx->sweep_nw, ns, vpt, fp, ctx->sweep_ql); }, ms))) break;
       if (ms < tb) { tb = ms; nb = ns; }
     }
     if (r) break;
@@ -1016,14 +1037,20 @@ int ugks_autotune(ugks_ctx *ctx, int reps, int *items_out, int *vpt_out, int *ri
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (r) return r;
-  CK(cudaMemcpyAsync(d.f, d.Dbuf, fbytes, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(d.f, d.Tn, fbytes, cudaMemcpyDeviceToDevice, s));
   if ((r = set_sweep_tiles(ctx, bv))) return r;
   ctx->ns_fwd = bf;
   ctx->ns_bwd = bb;
+  ctx->face_tile = bt;
+  int vk, nh;
+  face_tile_shape(fp ? bt : -1, &vk, &nh);
+  if (!fp) { vk = 8; nh = 2; }
   if (items_out) *items_out = 32 * bv;
   if (vpt_out) *vpt_out = bv;
   if (ring_fwd_out) *ring_fwd_out = bf;
   if (ring_bwd_out) *ring_bwd_out = bb;
+  if (face_vk_out) *face_vk_out = vk;
+  if (face_nh_out) *face_nh_out = nh;
   return launch_status(ctx);
 }
 

@@ -37,7 +37,12 @@ void launch_interp(const Dev &d, cudaStream_t s, const int *list, const int *cnt
 void tile_setup();
 int tile_count(int ni, int nj);
 void tile_origins(int ni, int nj, int *out);
-void launch_flux_tile(const Dev &d, cudaStream_t s, int fp32);
+// face kernels: `tile` indexes the tile shapes (velocities per chunk, threads
+// per face slot) of face_tile_shape; the FP64 path has one shape
+void launch_flux_tile(const Dev &d, cudaStream_t s, int fp32, int tile);
 void launch_residual(const Dev &d, cudaStream_t s, int first_iter, int fp32);
-void launch_face_reduce_tile(const Dev &d, cudaStream_t s, int fp32);
+void launch_face_reduce_tile(const Dev &d, cudaStream_t s, int fp32, int tile);
+int face_tile_count();
+int face_tile_default();
+void face_tile_shape(int tile, int *vk, int *nh);
 }  // namespace ugks

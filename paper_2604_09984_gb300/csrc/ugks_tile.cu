@@ -22,7 +22,6 @@
 // registers across all chunks (per-chunk partial sums added with an
 // error-free transformation on the FP32 path) and writes them once, with no
 // atomics: the result does not depend on scheduling.
-#include <cstdlib>
 #include "ugks_internal.cuh"
 #include "ugks_launch.h"
 
@@ -31,16 +30,17 @@ namespace ugks {
 constexpr int TX = 8, TY = 8, RW = TX + 4, RH = TY + 4, NR = RW * RH;
 constexpr int NSI = (TX + 1) * TY;          // i-face slots: tile row w, column x = 0..TX
 constexpr int NSLOT = NSI + TX * (TY + 1);  // + j-face slots: tile column w, row y = 0..TY
-constexpr int NHALF = 2;                    // threads per face slot (halves of a chunk)
-constexpr int FTHREADS = NSLOT * NHALF;
-
-// velocities per chunk (VK); row strides of the staged region (VKP: rows of
+// Tile shape of the two face kernels (the autotuner's choice): VK velocities
+// per chunk, NH threads per face slot (each takes VK / NH velocities of a
+// chunk), NT threads a CTA; row strides of the staged region (VKP: rows of
 // whole 16-byte copies) and of the gradient and face-flux rows (VKG: odd, so
 // the lanes of a warp, which read different cells at one velocity, fall in
-// different banks)
-template <typename T> struct Chunk;
-template <> struct Chunk<float> { static constexpr int VK = 16, VKP = VK + 2, VKG = VK + 1; };
-template <> struct Chunk<double> { static constexpr int VK = 8, VKP = VK, VKG = VK + 1; };
+// different banks).
+template <typename T, int VK_, int NH_> struct FCfg {
+  static constexpr int VK = VK_, NH = NH_, NT = NSLOT * NH_;
+  static constexpr int VKP = sizeof(T) == 4 ? VK_ + 2 : VK_, VKG = VK_ + 1;
+  static_assert(NT % VK == 0 && VK % NH == 0, "tile shape");
+};
 
 // region cell (i, j) of block b -> cell id (>= 0), ghost (-2 - face id) or
 // none (-1).  Periodic blocks wrap in i.
@@ -97,10 +97,10 @@ template <> struct Vec4<double> { typedef double4 type; };
 // Cartesian gradients of the chunk, the velocity table of both buffered
 // chunks, and per region cell its id, slope cases and inverse Jacobian (the
 // ghost Maxwellian's parameters for ghost cells).
-template <typename T> struct FaceSmem {
+template <typename T, typename C> struct FaceSmem {
   typedef typename Vec2<T>::type T2;
   typedef typename Vec4<T>::type T4;
-  static constexpr int VK = Chunk<T>::VK, VKP = Chunk<T>::VKP, VKG = Chunk<T>::VKG;
+  static constexpr int VK = C::VK, VKP = C::VKP, VKG = C::VKG;
   T2 *F;         // [2][NR][VKP]
   T4 *G;         // [NG][VKG]: (d_x h, d_x b, d_y h, d_y b)
   T4 *vt;        // [2][VK]: vx, vy, weight, |v|^2 / 2
@@ -127,8 +127,8 @@ template <typename T> struct FaceSmem {
 };
 
 // region ids, slope cases, inverse Jacobians and ghost states (once per CTA)
-template <typename T>
-__device__ __forceinline__ void region_meta(const Dev &d, FaceSmem<T> &S, const int *bi, int off, int i0, int j0) {
+template <typename T, typename C>
+__device__ __forceinline__ void region_meta(const Dev &d, FaceSmem<T, C> &S, const int *bi, int off, int i0, int j0) {
   typedef typename Vec4<T>::type T4;
   for (int r = threadIdx.x; r < NR; r += blockDim.x) {
     int rx = r % RW, ry = r / RW;
@@ -157,11 +157,11 @@ __device__ __forceinline__ void region_meta(const Dev &d, FaceSmem<T> &S, const 
 // asynchronous 16-byte copies (bf16 storage: load and widen), ghost cells the
 // Maxwellian of their ghost state, no cell / padding velocities zero; and the
 // chunk's velocity table.  EP velocities per copy.
-template <typename T, int FB>
-__device__ __forceinline__ void stage_chunk(const Dev &d, FaceSmem<T> &S, int ch, int buf) {
+template <typename T, int FB, typename C>
+__device__ __forceinline__ void stage_chunk(const Dev &d, FaceSmem<T, C> &S, int ch, int buf) {
   typedef typename Vec2<T>::type T2;
   typedef typename Vec4<T>::type T4;
-  constexpr int VK = Chunk<T>::VK, VKP = Chunk<T>::VKP, EP = 16 / (int)sizeof(T2), NP = VK / EP;
+  constexpr int VK = C::VK, VKP = C::VKP, EP = 16 / (int)sizeof(T2), NP = VK / EP;
   const int kb = ch * VK;
   T2 *Fb = S.F + (size_t)buf * NR * VKP;
   for (int it = threadIdx.x; it < NR * NP; it += blockDim.x) {
@@ -217,12 +217,11 @@ template <typename T> __device__ __forceinline__ T lim_slope(T a, T b, bool hm, 
 // missing cells carry none).  A thread keeps one chunk velocity and walks
 // the gradient cells with a fixed stride; cells with all four neighbours take
 // the two-sided limiter without the one-sided selections.
-template <typename T>
-__device__ __forceinline__ void chunk_gradients(FaceSmem<T> &S, int buf) {
+template <typename T, typename C>
+__device__ __forceinline__ void chunk_gradients(FaceSmem<T, C> &S, int buf) {
   typedef typename Vec2<T>::type T2;
   typedef typename Vec4<T>::type T4;
-  constexpr int VK = Chunk<T>::VK, VKP = Chunk<T>::VKP, VKG = Chunk<T>::VKG, GS = FTHREADS / VK;
-  static_assert(FTHREADS % VK == 0, "whole velocity rows per pass");
+  constexpr int VK = C::VK, VKP = C::VKP, VKG = C::VKG, GS = C::NT / VK;
   const T2 *Fb = S.F + (size_t)buf * NR * VKP;
   const int kk = threadIdx.x % VK;
   for (int g = threadIdx.x / VK; g < NG; g += GS) {
@@ -273,10 +272,10 @@ template <typename T> __device__ __forceinline__ Side<T> make_side(int r, T dx, 
 
 // Reconstructed face value f + dx.grad f and w.grad f of side s at chunk
 // velocity kk.
-template <typename T>
-__device__ __forceinline__ void side_value(const FaceSmem<T> &S, const typename Vec2<T>::type *Fb, int r, int g,
+template <typename T, typename C>
+__device__ __forceinline__ void side_value(const FaceSmem<T, C> &S, const typename Vec2<T>::type *Fb, int r, int g,
                                            T dx, T dy, int kk, T wx, T wy, V2<T> &ff, V2<T> &wg) {
-  constexpr int VKP = Chunk<T>::VKP, VKG = Chunk<T>::VKG;
+  constexpr int VKP = C::VKP, VKG = C::VKG;
   auto fc = Fb[r * VKP + kk];
   auto G = S.G[g * VKG + kk];
   ff.h = fc.x + dx * G.x + dy * G.z;
@@ -287,21 +286,21 @@ __device__ __forceinline__ void side_value(const FaceSmem<T> &S, const typename 
 
 // Upwind face value and w.grad f (walls: the interior side L only); only
 // w.S = 0 exactly averages the two sides.
-template <typename T>
-__device__ __forceinline__ void upwind(const FaceSmem<T> &S, const typename Vec2<T>::type *Fb, const Side<T> &L,
+template <typename T, typename C>
+__device__ __forceinline__ void upwind(const FaceSmem<T, C> &S, const typename Vec2<T>::type *Fb, const Side<T> &L,
                                        const Side<T> &R, bool wall, int kk, T wS, T wx, T wy, V2<T> &ff,
                                        V2<T> &wg) {
   if (!wall && wS == T(0)) {
     V2<T> f1, g1, f2, g2;
-    side_value<T>(S, Fb, L.r, L.g, L.dx, L.dy, kk, wx, wy, f1, g1);
-    side_value<T>(S, Fb, R.r, R.g, R.dx, R.dy, kk, wx, wy, f2, g2);
+    side_value<T, C>(S, Fb, L.r, L.g, L.dx, L.dy, kk, wx, wy, f1, g1);
+    side_value<T, C>(S, Fb, R.r, R.g, R.dx, R.dy, kk, wx, wy, f2, g2);
     ff = {T(0.5) * (f1.h + f2.h), T(0.5) * (f1.b + f2.b)};
     wg = {T(0.5) * (g1.h + g2.h), T(0.5) * (g1.b + g2.b)};
     return;
   }
   bool useR = !wall && wS < T(0);
-  side_value<T>(S, Fb, useR ? R.r : L.r, useR ? R.g : L.g, useR ? R.dx : L.dx, useR ? R.dy : L.dy, kk, wx, wy,
-                ff, wg);
+  side_value<T, C>(S, Fb, useR ? R.r : L.r, useR ? R.g : L.g, useR ? R.dx : L.dx, useR ? R.dy : L.dy, kk, wx, wy,
+                   ff, wg);
 }
 
 // Slot -> (direction, tile row / column w, position x) and the region cells
@@ -338,21 +337,23 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
 // with the time integrals q1, q2 applied afterwards).  Per chunk: staging of
 // the next chunk, gradients (phase A), face sums (phase B); FP32 partial sums
 // of two chunks are folded into a (sum, error) pair by an error-free sum.
-template <typename T, int FB, int MINB> __global__ void __launch_bounds__(FTHREADS, MINB) k_face_reduce(Dev d) {
+template <typename T, int FB, int VKT, int NHT>
+__global__ void __launch_bounds__(NSLOT * NHT) k_face_reduce(Dev d) {
   typedef typename Vec2<T>::type T2;
   typedef typename Vec4<T>::type T4;
-  constexpr int VK = Chunk<T>::VK, VKP = Chunk<T>::VKP, VH = VK / NHALF;
+  typedef FCfg<T, VKT, NHT> C;
+  constexpr int VK = C::VK, VKP = C::VKP, NH = C::NH, VH = VK / NH;
   extern __shared__ __align__(16) unsigned char smraw[];
-  FaceSmem<T> S;
+  FaceSmem<T, C> S;
   S.carve(smraw);
   int tile = blockIdx.x;
   int b = d.tiles[3 * tile], i0 = d.tiles[3 * tile + 1], j0 = d.tiles[3 * tile + 2];
   const int *bi = d.blk_info + 8 * b;
   int ni = bi[0], nj = bi[1], per = bi[2], off = d.cell_off[b];
-  region_meta<T>(d, S, bi, off, i0, j0);
+  region_meta<T, C>(d, S, bi, off, i0, j0);
   __syncthreads();
   const int nch = (d.nv + VK - 1) / VK;
-  stage_chunk<T, FB>(d, S, 0, 0);
+  stage_chunk<T, FB, C>(d, S, 0, 0);
   // this thread's face
   int slot = threadIdx.x % NSLOT, half = threadIdx.x / NSLOT;
   int dir, w, x, A, B;
@@ -387,8 +388,8 @@ template <typename T, int FB, int MINB> __global__ void __launch_bounds__(FTHREA
     int buf = ch & 1;
     cp_async_wait<0>();
     __syncthreads();                       // chunk ch visible; phase B of ch-1 done everywhere
-    if (ch + 1 < nch) stage_chunk<T, FB>(d, S, ch + 1, buf ^ 1);
-    chunk_gradients<T>(S, buf);
+    if (ch + 1 < nch) stage_chunk<T, FB, C>(d, S, ch + 1, buf ^ 1);
+    chunk_gradients<T, C>(S, buf);
     __syncthreads();
     if (act) {
       const T2 *Fb = S.F + (size_t)buf * NR * VKP;
@@ -402,7 +403,7 @@ template <typename T, int FB, int MINB> __global__ void __launch_bounds__(FTHREA
         // reflected velocities of a wall carry no f (zero weight, no branch)
         T wk = (wall && !(wS > T(0))) ? T(0) : v.z;
         V2<T> ff, wg;
-        upwind<T>(S, Fb, L, R, wall, kk, wS, vx - ufx, vy - ufy, ff, wg);
+        upwind<T, C>(S, Fb, L, R, wall, kk, wS, vx - ufx, vy - ufy, ff, wg);
         T a = wk * ff.h, bb = T(0.5) * wk * ff.b;
         T p0 = a, p1 = vx * a, p2 = vy * a, p3 = v2 * a + bb;
         T ga = wk * wg.h, gb = T(0.5) * wk * wg.b;
@@ -428,27 +429,34 @@ template <typename T, int FB, int MINB> __global__ void __launch_bounds__(FTHREA
       }
     }
   }
-  // the two halves of a face meet in shared memory (the region buffers are
-  // free once every thread has passed the barrier)
+  // the NH parts of a face meet in shared memory (the region buffers are
+  // free once every thread has passed the barrier), summed in part order
   __syncthreads();
   T *xs = reinterpret_cast<T *>(S.F);
-  if (half == 1) {
+  if (half > 0) {
+    T *o = xs + (size_t)(half - 1) * 2 * NFS * NSLOT;
 #pragma unroll
-    for (int m = 0; m < NFS; ++m) { xs[(2 * m) * NSLOT + slot] = hi[m]; xs[(2 * m + 1) * NSLOT + slot] = lo[m]; }
+    for (int m = 0; m < NFS; ++m) { o[(2 * m) * NSLOT + slot] = hi[m]; o[(2 * m + 1) * NSLOT + slot] = lo[m]; }
   }
   __syncthreads();
   if (half == 0 && act) {
     double *out = d.fsum + (size_t)NFS * fid;
 #pragma unroll
     for (int m = 0; m < NFS; ++m) {
-      T h2 = xs[(2 * m) * NSLOT + slot], l2 = xs[(2 * m + 1) * NSLOT + slot];
       double v;
       if (sizeof(T) == 4) {
-        float s, e;
-        two_sum((float)hi[m], (float)h2, s, e);
-        v = to_double(s) + (to_double(e) + (to_double(lo[m]) + to_double(l2)));
+        float h = (float)hi[m], l = (float)lo[m];
+        for (int p = 1; p < NH; ++p) {
+          const T *o = xs + (size_t)(p - 1) * 2 * NFS * NSLOT;
+          float s, e;
+          two_sum(h, (float)o[(2 * m) * NSLOT + slot], s, e);
+          h = s;
+          l = (l + e) + (float)o[(2 * m + 1) * NSLOT + slot];
+        }
+        v = to_double(h) + to_double(l);
       } else {
-        v = (double)hi[m] + (double)h2;
+        v = (double)hi[m];
+        for (int p = 1; p < NH; ++p) v += (double)xs[(size_t)(p - 1) * 2 * NFS * NSLOT + (2 * m) * NSLOT + slot];
       }
       out[m] = (wall && m < FS_FF) ? 0.0 : v;     // walls take W0 from the interior cell
     }
@@ -460,21 +468,22 @@ template <typename T, int FB, int MINB> __global__ void __launch_bounds__(FTHREA
 // evaluated by both) computes S F_hat per velocity into shared memory; then
 // each (tile cell, velocity) sums its four faces with the cell's orientation
 // signs and stores D.
-template <typename T, int FB> __global__ void __launch_bounds__(FTHREADS) k_flux(Dev d) {
+template <typename T, int FB, int VKT, int NHT> __global__ void __launch_bounds__(NSLOT * NHT) k_flux(Dev d) {
   typedef typename Vec2<T>::type T2;
   typedef typename Vec4<T>::type T4;
-  constexpr int VK = Chunk<T>::VK, VKP = Chunk<T>::VKP, VKG = Chunk<T>::VKG, VH = VK / NHALF;
+  typedef FCfg<T, VKT, NHT> C;
+  constexpr int VK = C::VK, VKP = C::VKP, VKG = C::VKG, VH = VK / C::NH;
   extern __shared__ __align__(16) unsigned char smraw[];
-  FaceSmem<T> S;
+  FaceSmem<T, C> S;
   S.carve(smraw);
-  T2 *Fs = reinterpret_cast<T2 *>(smraw + FaceSmem<T>::bytes());        // [NSLOT][VKG]
+  T2 *Fs = reinterpret_cast<T2 *>(smraw + FaceSmem<T, C>::bytes());     // [NSLOT][VKG]
   int *cinf = reinterpret_cast<int *>(Fs + (size_t)NSLOT * VKG);          // [TX*TY]: cell id or -1
   char4 *csg = reinterpret_cast<char4 *>(cinf + TX * TY);                 // [TX*TY]: face signs
   int tile = blockIdx.x;
   int b = d.tiles[3 * tile], i0 = d.tiles[3 * tile + 1], j0 = d.tiles[3 * tile + 2];
   const int *bi = d.blk_info + 8 * b;
   int ni = bi[0], nj = bi[1], off = d.cell_off[b];
-  region_meta<T>(d, S, bi, off, i0, j0);
+  region_meta<T, C>(d, S, bi, off, i0, j0);
   for (int c = threadIdx.x; c < TX * TY; c += blockDim.x) {
     int tx = c % TX, ty = c / TX, i = i0 + tx, j = j0 + ty;
     int g = (i < ni && j < nj) ? off + j * ni + i : -1;
@@ -484,7 +493,7 @@ template <typename T, int FB> __global__ void __launch_bounds__(FTHREADS) k_flux
   }
   __syncthreads();
   const int nch = (d.nv + VK - 1) / VK;
-  stage_chunk<T, FB>(d, S, 0, 0);
+  stage_chunk<T, FB, C>(d, S, 0, 0);
   int slot = threadIdx.x % NSLOT, half = threadIdx.x / NSLOT;
   int dir, w, x, A, B;
   slot_geom(slot, dir, w, x, A, B);
@@ -512,8 +521,8 @@ template <typename T, int FB> __global__ void __launch_bounds__(FTHREADS) k_flux
     int buf = ch & 1;
     cp_async_wait<0>();
     __syncthreads();               // chunk ch visible; the face fluxes of ch-1 consumed
-    if (ch + 1 < nch) stage_chunk<T, FB>(d, S, ch + 1, buf ^ 1);
-    chunk_gradients<T>(S, buf);
+    if (ch + 1 < nch) stage_chunk<T, FB, C>(d, S, ch + 1, buf ^ 1);
+    chunk_gradients<T, C>(S, buf);
     __syncthreads();
     const T2 *Fb = S.F + (size_t)buf * NR * VKP;
     const T4 *vt = S.vt + buf * VK;
@@ -534,7 +543,7 @@ template <typename T, int FB> __global__ void __launch_bounds__(FTHREADS) k_flux
           Fo.y = wS * Keff / (T(2) * lw) * Hw;
         } else {
           V2<T> ff, wg;
-          upwind<T>(S, Fb, L, R, wall, kk, wS, wx, wy, ff, wg);
+          upwind<T, C>(S, Fb, L, R, wall, kk, wS, wx, wy, ff, wg);
           // Eq. fullSolution averaged over dt_s: q1 f + q2 w.grad f + H ih(c)
           // (and b), the equilibrium factors as per-face cubics in c = v - U0
           T cx = vx - P[FP_UX], cy = vy - P[FP_UY];
@@ -608,34 +617,46 @@ template <typename T, int FB> __global__ void k_residual(Dev d, int first_iter) 
   }
 }
 
-template <typename T> static size_t flux_smem() {
-  return FaceSmem<T>::bytes() + sizeof(typename Vec2<T>::type) * NSLOT * Chunk<T>::VKG + sizeof(int) * TX * TY +
+template <typename T, typename C> static size_t flux_smem() {
+  return FaceSmem<T, C>::bytes() + sizeof(typename Vec2<T>::type) * NSLOT * C::VKG + sizeof(int) * TX * TY +
          sizeof(char4) * TX * TY;
 }
-template <typename T> static size_t reduce_smem() {
-  size_t a = FaceSmem<T>::bytes(), b = sizeof(T) * 2 * NFS * NSLOT;
+template <typename T, typename C> static size_t reduce_smem() {
+  size_t a = FaceSmem<T, C>::bytes(), b = sizeof(T) * 2 * NFS * NSLOT * (C::NH > 1 ? C::NH - 1 : 1);
   return a > b ? a : b;
 }
 
-// CTAs per SM the face reduction is compiled for: 2 (no register limit
-// below the 96 it uses) or 3 (72 registers, with a few spills); UGKS_REDUCE_MINB
-// selects the variant at context creation (measured choice: see the launcher)
-static int g_reduce_minb = 2;
+// Candidate tile shapes of the FP32 face kernels (velocities per chunk,
+// threads per face slot); the FP64 path keeps (8, 2).
+constexpr int kFaceVK[] = {8, 8, 16, 16, 32};
+constexpr int kFaceNH[] = {1, 2, 1, 2, 2};
+constexpr int kFaceDefault = 3;     // (16, 2)
+int face_tile_count() { return 5; }
+void face_tile_shape(int v, int *vk, int *nh) {
+  if (v < 0 || v >= face_tile_count()) v = kFaceDefault;
+  *vk = kFaceVK[v];
+  *nh = kFaceNH[v];
+}
+int face_tile_default() { return kFaceDefault; }
 
-template <typename T, int FB, int MB> static void reduce_attr() {
-  cudaFuncSetAttribute(k_face_reduce<T, FB, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)reduce_smem<T>());
+template <typename T, int FB, int VK, int NH> static void face_attr() {
+  typedef FCfg<T, VK, NH> C;
+  cudaFuncSetAttribute(k_flux<T, FB, VK, NH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)flux_smem<T, C>());
+  cudaFuncSetAttribute(k_face_reduce<T, FB, VK, NH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)reduce_smem<T, C>());
+}
+template <int FB> static void face_attr_f32() {
+  face_attr<float, FB, 8, 1>();
+  face_attr<float, FB, 8, 2>();
+  face_attr<float, FB, 16, 1>();
+  face_attr<float, FB, 16, 2>();
+  face_attr<float, FB, 32, 2>();
 }
 
 void tile_setup() {
-  cudaFuncSetAttribute(k_flux<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)flux_smem<float>());
-  cudaFuncSetAttribute(k_flux<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)flux_smem<float>());
-  cudaFuncSetAttribute(k_flux<double, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)flux_smem<double>());
-  reduce_attr<float, 0, 2>();
-  reduce_attr<float, 1, 2>();
-  reduce_attr<double, 0, 2>();
-  reduce_attr<float, 0, 3>();
-  reduce_attr<float, 1, 3>();
-  if (const char *e = getenv("UGKS_REDUCE_MINB")) g_reduce_minb = atoi(e) == 3 ? 3 : 2;
+  face_attr_f32<0>();
+  face_attr_f32<1>();
+  face_attr<double, 0, 8, 2>();
 }
 
 int tile_count(int ni, int nj) { return ((ni + TX - 1) / TX) * ((nj + TY - 1) / TY); }
@@ -645,10 +666,29 @@ void tile_origins(int ni, int nj, int *out) {   // (i0, j0) pairs
     for (int ti = 0; ti < (ni + TX - 1) / TX; ++ti) { out[q++] = ti * TX; out[q++] = tj * TY; }
 }
 
-void launch_flux_tile(const Dev &d, cudaStream_t s, int fp32) {
-  if (fp32 && d.fbf) k_flux<float, 1><<<d.ntiles, FTHREADS, flux_smem<float>(), s>>>(d);
-  else if (fp32) k_flux<float, 0><<<d.ntiles, FTHREADS, flux_smem<float>(), s>>>(d);
-  else k_flux<double, 0><<<d.ntiles, FTHREADS, flux_smem<double>(), s>>>(d);
+template <typename T, int FB, int VK, int NH> static void face_launch(const Dev &d, cudaStream_t s, int which) {
+  typedef FCfg<T, VK, NH> C;
+  if (which == 0) k_face_reduce<T, FB, VK, NH><<<d.ntiles, C::NT, reduce_smem<T, C>(), s>>>(d);
+  else k_flux<T, FB, VK, NH><<<d.ntiles, C::NT, flux_smem<T, C>(), s>>>(d);
+}
+template <int FB> static void face_launch_f32(const Dev &d, cudaStream_t s, int which, int v) {
+  switch (v) {
+    case 0: face_launch<float, FB, 8, 1>(d, s, which); break;
+    case 1: face_launch<float, FB, 8, 2>(d, s, which); break;
+    case 2: face_launch<float, FB, 16, 1>(d, s, which); break;
+    case 4: face_launch<float, FB, 32, 2>(d, s, which); break;
+    default: face_launch<float, FB, 16, 2>(d, s, which); break;
+  }
+}
+static void face_dispatch(const Dev &d, cudaStream_t s, int which, int fp32, int v) {
+  if (!fp32) face_launch<double, 0, 8, 2>(d, s, which);
+  else if (d.fbf) face_launch_f32<1>(d, s, which, v);
+  else face_launch_f32<0>(d, s, which, v);
+}
+
+void launch_flux_tile(const Dev &d, cudaStream_t s, int fp32, int tile) { face_dispatch(d, s, 1, fp32, tile); }
+void launch_face_reduce_tile(const Dev &d, cudaStream_t s, int fp32, int tile) {
+  face_dispatch(d, s, 0, fp32, tile);
 }
 void launch_residual(const Dev &d, cudaStream_t s, int first_iter, int fp32) {
   int pairs = (d.nv + 1) / 2;
@@ -657,19 +697,6 @@ void launch_residual(const Dev &d, cudaStream_t s, int first_iter, int fp32) {
   if (fp32 && d.fbf) k_residual<float, 1><<<grid, bt, 0, s>>>(d, first_iter);
   else if (fp32) k_residual<float, 0><<<grid, bt, 0, s>>>(d, first_iter);
   else k_residual<double, 0><<<grid, bt, 0, s>>>(d, first_iter);
-}
-
-void launch_face_reduce_tile(const Dev &d, cudaStream_t s, int fp32) {
-  size_t sm = fp32 ? reduce_smem<float>() : reduce_smem<double>();
-  if (fp32 && g_reduce_minb == 3) {
-    if (d.fbf) k_face_reduce<float, 1, 3><<<d.ntiles, FTHREADS, sm, s>>>(d);
-    else k_face_reduce<float, 0, 3><<<d.ntiles, FTHREADS, sm, s>>>(d);
-  } else if (fp32) {
-    if (d.fbf) k_face_reduce<float, 1, 2><<<d.ntiles, FTHREADS, sm, s>>>(d);
-    else k_face_reduce<float, 0, 2><<<d.ntiles, FTHREADS, sm, s>>>(d);
-  } else {
-    k_face_reduce<double, 0, 2><<<d.ntiles, FTHREADS, sm, s>>>(d);
-  }
 }
 
 }  // namespace ugks

@@ -59,7 +59,8 @@ SYMBOLS = {
                                    c_int, POINTER(c_int)]),
     "ugks_moments": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ugks_wall_torque": (c_int, [c_void_p, POINTER(c_double), c_void_p]),
-    "ugks_autotune": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
+    "ugks_autotune": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int),
+                              POINTER(c_int), POINTER(c_int)]),
     "ugks_sizes": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
     "ugks_get_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "ugks_set_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -262,13 +263,13 @@ class Solver:
         self.step(dt, n_inner)
 
     def autotune(self, reps=3):
-        """Pick the fastest micro-sweep tile on this context's own state
-        (ugks_autotune); returns (items per CTA and diagonal, velocities per
-        thread, forward ring depth, backward ring depth)."""
-        items, vpt, rf, rb = c_int(), c_int(), c_int(), c_int()
-        self._check(self.lib.ugks_autotune(self.ctx, int(reps), ctypes.byref(items), ctypes.byref(vpt),
-                                           ctypes.byref(rf), ctypes.byref(rb)))
-        self.tiles = (items.value, vpt.value, rf.value, rb.value)
+        """Pick the fastest tiles on this context's own state (ugks_autotune);
+        returns (sweep items per warp step, sweep velocities per lane, forward
+        ring depth, backward ring depth, face-kernel velocities per chunk,
+        face-kernel threads per face slot)."""
+        v = [c_int() for _ in range(6)]
+        self._check(self.lib.ugks_autotune(self.ctx, int(reps), *[ctypes.byref(x) for x in v]))
+        self.tiles = tuple(x.value for x in v)
         return self.tiles
 
     def moments(self, W=None, q=None, status=None, wall=None):

@@ -53,7 +53,7 @@ def test_fp32_bench_velocity_grid_after_autotune():
     r = Run(case)
     s.advance()
     tiles = s.autotune(reps=1)
-    assert tiles[1] in (2, 4) and tiles[0] == 32 * tiles[1]
+    assert tiles[1] in (2, 4) and tiles[0] == 32 * tiles[1] and tiles[4] in (8, 16, 32) and tiles[5] in (1, 2)
     s.advance()
     r.step()
     r.step()

@@ -295,8 +295,9 @@ def test_autotune_restores_state_and_changes_no_result():
     for s in (a, b, c):
         s.advance()
     f0, _, _ = a.get_state()
-    items, vpt, ring_f, ring_b = a.autotune(reps=1)
+    items, vpt, ring_f, ring_b, fvk, fnh = a.autotune(reps=1)
     assert vpt == 2 and items == 64 and ring_f in (1, 2, 4, 6) and ring_b in (1, 2, 4, 6)
+    assert (fvk, fnh) == (8, 2)
     f1, _, _ = a.get_state()
     assert torch.equal(f0, f1)
     for _ in range(2):
@@ -330,6 +331,30 @@ def test_batch_defers_orphan_report_to_next_sync():
     c0 = overset.connect(topo, case.nodes_at(0.0))
     c1 = overset.connect(topo, case.nodes_at(t1), c0.status)
     assert c1.n_orphan > 0
+
+
+@pytest.mark.parametrize("tile", range(5))
+def test_face_tile_shapes_agree(tile):
+    """Every tile shape the autotuner may give the FP32 face kernels
+    (velocities per chunk x threads per face slot) computes the same step up
+    to the rounding of the face sums, and matches the oracle."""
+    case = small_mems(nv=12)
+    prim = wl.random_prim(case, 29, amp_rho=0.05, amp_u=0.05, amp_T=0.05)
+    b = U.Solver(case, U.FP32, prim=prim)
+    os.environ["UGKS_FACE_TILE"] = str(tile)
+    try:
+        c = U.Solver(case, U.FP32, prim=prim)
+    finally:
+        del os.environ["UGKS_FACE_TILE"]
+    r = Run(case, prim)
+    for _ in range(2):
+        b.advance()
+        c.advance()
+        r.step()
+    Wc = c.moments()[0]
+    field = r.status == 0
+    assert rel(Wc, b.moments()[0]) < 1e-6
+    assert rel(Wc[field], r.state.W[field]) < 1e-5
 
 
 @pytest.mark.parametrize("prec", [U.FP32, U.BF16F])

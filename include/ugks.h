@@ -100,6 +100,10 @@ typedef struct {
   double cfl_s;             /* CFL of the flux-averaging step dt_s (0.5)      */
   double cfl_pseudo;        /* CFL of the pseudo time step dt' (100)          */
   double farfield[4];       /* free stream rho, Vx, Vy, T (far-field ghosts)  */
+  int shard_iy0, shard_iy1; /* velocity sharding: this context holds the rows
+                               shard_iy0 <= iy < shard_iy1 of the velocity
+                               grid (k = iy*nvx + ix, whole rows); 0, 0 = all.
+                               A sharded context needs ugks_shard_set_exchange */
 } ugks_params;
 
 /* One structured block: ni x nj quad cells, nodes (ni+1) x (nj+1).  Cell
@@ -280,6 +284,34 @@ int ugks_get_connectivity(ugks_ctx *ctx, int32_t *status, int32_t *donors,
  * logical index; boundary faces point out of the block. */
 int ugks_get_geometry(ugks_ctx *ctx, double *vol_old, double *vol_new,
                       double *xc, double *dts, double *Sn, double *SUn);
+
+/* Velocity-space sharding (the per-velocity work of a step -- flux
+ * divergence, residual, both LU-SGS sweeps, interpolation -- is independent
+ * per discrete velocity, Sec. 2.2; only velocity sums couple velocities).  A
+ * context created with shard_iy0 < shard_iy1 holds those rows of the velocity
+ * grid.  Twice per flux evaluation / inner iteration it needs the sums over
+ * all shards of a buffer of partial velocity sums, and asks for them through
+ * the caller's exchange function:
+ *   which 0: the per-face sums of the velocity reduction (W0 and the f-parts
+ *            of the macro flux), face_count doubles;
+ *   which 1: the per-cell partial sums of the step-7 moment fix and of the
+ *            heat flux, cell_count doubles.
+ * fn(which, stream, user) is called on the host; the buffer's partial sums
+ * are complete once `stream` (a cudaStream_t) has reached the call point.  It
+ * must replace the buffer, in stream order, by the sum over all shards of the
+ * same buffer -- the same bits on every shard (a fixed summation order) --
+ * before it returns or through work it enqueues on `stream`, and return 0;
+ * anything else fails the calling ugks_* function with UGKS_ERR_ARG.  All
+ * other quantities (face states, equilibrium and wall fluxes, macroscopic
+ * update, geometry) are computed identically on every shard.  Errors:
+ * UGKS_ERR_ARG (context not sharded or fn NULL). */
+typedef int (*ugks_exchange_fn)(int which, void *stream, void *user);
+int ugks_shard_set_exchange(ugks_ctx *ctx, ugks_exchange_fn fn, void *user);
+
+/* Where the two exchange buffers of a sharded context lie: byte offsets from
+ * the start of the caller's workspace and lengths in doubles (FP64). */
+int ugks_shard_buffers(const ugks_ctx *ctx, size_t *face_off, size_t *face_count, size_t *cell_off,
+                       size_t *cell_count);
 
 /* Number of kernel launches issued on the context's stream since creation
  * (counted on the host at each launch). */

@@ -35,6 +35,9 @@ struct ugks_ctx {
   int sweep_vpt = 2;                  // micro sweeps: velocities per lane
   int ns_fwd = 4, ns_bwd = 4;         // prefetch ring depths (steps) of the two sweeps
   int face_tile = 0;                  // tile shape of the face kernels (face_tile_shape)
+  ugks_exchange_fn xfn = nullptr;     // velocity sharding: the caller's exchange
+  void *xuser = nullptr;
+  bool debug_sync = false, debug_failed = false;   // UGKS_DEBUG_SYNC
   bool stepped = false;               // a ugks_step has run (sweep records valid)
   int *work = nullptr;
   int *prev_status = nullptr, *n_orphan = nullptr, *blk_order = nullptr;
@@ -78,6 +81,7 @@ int cuda_check(ugks_ctx *c, cudaError_t e, const char *what) {
 struct Sizes {
   int nc = 0, nf = 0, nn = 0, nv = 0, nvp = 0, nseg = 0, nring = 0, max_nj = 0, ntiles = 0;
   int nvx = 0, nvy = 0;
+  int iy0 = 0, nv_all = 0, nvp_all = 0;   // velocity shard: first row; the whole grid
   size_t nmrec32 = 0;   // FP32 macro records: (ni + nj - 1) nj per block (diagonal-major)
 };
 
@@ -92,8 +96,20 @@ int validate(const ugks_params *p, int nb, const ugks_block_desc *b, Sizes &s, s
   if (p->K < 0 || !(p->Pr > 0) || !(p->mu_ref > 0) || !(p->cfl_s > 0) || !(p->cfl_pseudo > 0)) {
     why = "gas or solver constant"; return UGKS_ERR_ARG;
   }
-  s.nv = p->nvx * p->nvy;
+  int iy0 = 0, iy1 = p->nvy;
+  if (p->shard_iy0 != 0 || p->shard_iy1 != 0) {
+    if (p->shard_iy0 < 0 || p->shard_iy1 > p->nvy || p->shard_iy0 >= p->shard_iy1) {
+      why = "velocity shard rows";
+      return UGKS_ERR_ARG;
+    }
+    iy0 = p->shard_iy0;
+    iy1 = p->shard_iy1;
+  }
+  s.iy0 = iy0;
+  s.nv = p->nvx * (iy1 - iy0);
   s.nvp = (s.nv + 3) / 4 * 4;
+  s.nv_all = p->nvx * p->nvy;
+  s.nvp_all = (s.nv_all + 3) / 4 * 4;
   s.nvx = p->nvx;
   s.nvy = p->nvy;
   for (int i = 0; i < nb; ++i) {
@@ -173,8 +189,8 @@ std::vector<int> ws_work(int nb, const ugks_block_desc *b, int nvp, int vpt, int
   return work;
 }
 
-int nwork_for(const ugks_params *p, int nb, const ugks_block_desc *b, int vpt) {
-  int nvp = (p->nvx * p->nvy + 3) / 4 * 4;
+// CTAs of the sweeps (nvp: the context's padded velocity count)
+int nwork_for(int nvp, int nb, const ugks_block_desc *b, int vpt) {
   return (int)ws_work(nb, b, nvp, vpt, sweep_nw_for(nb, b)).size() / 3;
 }
 
@@ -183,10 +199,12 @@ int nwork_for(const ugks_params *p, int nb, const ugks_block_desc *b, int vpt) {
 constexpr int kTuneVpt[] = {2, 4};
 constexpr int kTuneRing[] = {2, 4, 6};
 
-// Work-list capacity: the most CTAs any candidate needs.
+// Work-list capacity: the most CTAs any candidate needs (sized for the
+// whole velocity grid, which covers any shard of it).
 int nwork_cap_for(const ugks_params *p, int nb, const ugks_block_desc *b) {
-  int n = nwork_for(p, nb, b, sweep_vpt_for(p));
-  for (int v : kTuneVpt) n = std::max(n, nwork_for(p, nb, b, v));
+  int nvp = (p->nvx * p->nvy + 3) / 4 * 4;
+  int n = nwork_for(nvp, nb, b, sweep_vpt_for(p));
+  for (int v : kTuneVpt) n = std::max(n, nwork_for(nvp, nb, b, v));
   return n;
 }
 
@@ -200,6 +218,10 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int fbf, int nwork, i
   d.vx = c.take<double>(s.nvp); d.vy = c.take<double>(s.nvp); d.w = c.take<double>(s.nvp);
   d.vxf = c.take<float>(s.nvp); d.vyf = c.take<float>(s.nvp); d.wf = c.take<float>(s.nvp);
   d.wx1f = c.take<float>((size_t)s.nvx); d.wy1f = c.take<float>((size_t)s.nvy);
+  d.vy1f = c.take<float>((size_t)s.nvy);
+  d.vxa = c.take<double>(s.nvp_all); d.vya = c.take<double>(s.nvp_all); d.wa = c.take<double>(s.nvp_all);
+  d.vxaf = c.take<float>(s.nvp_all); d.vyaf = c.take<float>(s.nvp_all); d.waf = c.take<float>(s.nvp_all);
+  d.msum = c.take<double>(6 * (size_t)s.nc);
   d.cell_nodes = c.take<int>(4 * (size_t)s.nc);
   d.cell_faces = c.take<int>(4 * (size_t)s.nc);
   d.cell_sgn = c.take<int8_t>(4 * (size_t)s.nc);
@@ -459,11 +481,15 @@ int set_sweep_tiles(ugks_ctx *ctx, int vpt) {
 }
 
 // Event pair around one launch of a kernel group (only while profiling).
+// With UGKS_DEBUG_SYNC=1 in the environment at context creation, every
+// launch group is followed by a stream synchronisation and an error check, and
+// the first failing group is named on stderr (diagnosis of device faults).
 struct Prof {
   ugks_ctx *c;
   cudaStream_t s;
+  int g;
   size_t slot = (size_t)-1;
-  Prof(ugks_ctx *ctx, int group, cudaStream_t stream = nullptr) : c(ctx), s(stream ? stream : ctx->st) {
+  Prof(ugks_ctx *ctx, int group, cudaStream_t stream = nullptr) : c(ctx), s(stream ? stream : ctx->st), g(group) {
     if (!c->prof_on) return;
     if (c->ev_used + 2 > c->ev.size()) {
       for (int i = 0; i < 256; ++i) {
@@ -480,6 +506,14 @@ struct Prof {
   }
   ~Prof() {
     if (slot != (size_t)-1) cudaEventRecord(c->ev[slot + 1], s);
+    if (c->debug_sync) {
+      cudaError_t e = cudaStreamSynchronize(s);
+      if (e == cudaSuccess) e = cudaGetLastError();
+      if (e != cudaSuccess && !c->debug_failed) {
+        c->debug_failed = true;
+        fprintf(stderr, "ugks debug sync: kernel group %d failed: %s\n", g, cudaGetErrorString(e));
+      }
+    }
   }
 };
 
@@ -512,16 +546,28 @@ int do_interp(ugks_ctx *ctx, int fresh) {
   return UGKS_OK;
 }
 
+// Sharded context: the caller's exchange turns the partial sums of buffer
+// `which` into the sums over all shards (no-op when not sharded).
+int shard_exchange(ugks_ctx *ctx, int which) {
+  if (!ctx->d.shard) return UGKS_OK;
+  if (!ctx->xfn) return fail(ctx, UGKS_ERR_ORDER, "sharded context without an exchange function");
+  if (ctx->xfn(which, (void *)ctx->st, ctx->xuser) != 0) return fail(ctx, UGKS_ERR_ARG, "shard exchange failed");
+  return UGKS_OK;
+}
+
 // Ghost states, W gradients, face reduction, face coefficients, per-cell
 // macro flux sum (Steps 1 / 3 up to the velocity-resolved flux).
-void flux_prep(ugks_ctx *ctx, int level_n) {
+int flux_prep(ugks_ctx *ctx, int level_n) {
   Dev &d = ctx->d;
   cudaStream_t s = ctx->st;
   { Prof p(ctx, UGKS_PROF_CELL); launch_ghost_gradW(d, s); }
   { Prof p(ctx, UGKS_PROF_FACE_REDUCE); launch_face_reduce_tile(d, s, ctx->fp32, ctx->face_tile); }
+  int r = shard_exchange(ctx, 0);
+  if (r) return r;
   { Prof p(ctx, UGKS_PROF_FACE_COEF); launch_face_coef(d, s, ctx->fp32); }
   { Prof p(ctx, UGKS_PROF_CELL); launch_cell_macro(d, s, level_n); }
   ctx->launches += 6;
+  return UGKS_OK;
 }
 
 // Overset assembly (Sec. 3.1) and the device-side receptor / fresh lists.
@@ -618,6 +664,7 @@ int ugks_create(const ugks_params *p, void *workspace, size_t bytes, void *strea
   c->ws_bytes = bytes;
   c->st = (cudaStream_t)stream;
   c->fp32 = p->precision != UGKS_FP64;
+  if (const char *e = getenv("UGKS_DEBUG_SYNC")) c->debug_sync = atoi(e) != 0;
   c->fbf = p->precision == UGKS_BF16F;
   memset(&c->d, 0, sizeof(c->d));
   int prio_lo = 0, prio_hi = 0;
@@ -650,6 +697,26 @@ int ugks_destroy(ugks_ctx *ctx) {
 const char *ugks_last_error(const ugks_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 int64_t ugks_launch_count(const ugks_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+int ugks_shard_set_exchange(ugks_ctx *ctx, ugks_exchange_fn fn, void *user) {
+  if (!ctx || !ctx->mesh_ready) return UGKS_ERR_ORDER;
+  if (!ctx->d.shard) return fail(ctx, UGKS_ERR_ARG, "context holds the whole velocity grid");
+  if (!fn) return fail(ctx, UGKS_ERR_ARG, "null exchange function");
+  ctx->xfn = fn;
+  ctx->xuser = user;
+  return UGKS_OK;
+}
+
+int ugks_shard_buffers(const ugks_ctx *ctx, size_t *face_off, size_t *face_count, size_t *cell_off,
+                       size_t *cell_count) {
+  if (!ctx || !ctx->mesh_ready) return UGKS_ERR_ORDER;
+  const Dev &d = ctx->d;
+  if (face_off) *face_off = (size_t)((const char *)d.fsum - ctx->ws);
+  if (face_count) *face_count = (size_t)NFS * d.nf;
+  if (cell_off) *cell_off = (size_t)((const char *)d.msum - ctx->ws);
+  if (cell_count) *cell_count = 6 * (size_t)d.nc;
+  return UGKS_OK;
+}
 
 int ugks_set_wait_limit(ugks_ctx *ctx, int polls) {
   if (!ctx) return UGKS_ERR_ARG;
@@ -697,7 +764,7 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
       ctx->nsm = nsm;
     cudaGetLastError();
   }
-  ctx->nwork = nwork_for(&ctx->p, nblocks, blocks, ctx->sweep_vpt);
+  ctx->nwork = nwork_for(s.nvp, nblocks, blocks, ctx->sweep_vpt);
   if (!wsweep_fits(ctx->fp32, ctx->fbf, ctx->sweep_vpt, ctx->sweep_nw, 1, ctx->sweep_ql))
     return fail(ctx, UGKS_ERR_ARG, "micro-sweep CTA of the tallest block exceeds shared memory");
   ctx->nwork_cap = nwork_cap_for(&ctx->p, nblocks, blocks);
@@ -719,6 +786,7 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
     ctx->blk_order = c.take<int>(nblocks);
   }
   d.nc = s.nc; d.nf = s.nf; d.nn = s.nn; d.nv = s.nv; d.nvp = s.nvp; d.nblocks = nblocks;
+  d.nv_all = s.nv_all; d.iy0 = s.iy0; d.shard = s.nv != s.nv_all;
   d.nvx = ctx->p.nvx; d.nvy = ctx->p.nvy;
   d.Kint = ctx->p.K; d.Keff = 1 + ctx->p.K;
   d.Pr = ctx->p.Pr; d.omega = ctx->p.omega; d.mu_ref = ctx->p.mu_ref;
@@ -734,16 +802,26 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
   std::vector<float> vxf(s.nvp, 0.f), vyf(s.nvp, 0.f), wf(s.nvp, 0.f);
   const ugks_params &P = ctx->p;
   double hx = (P.vx_max - P.vx_min) / (P.nvx - 1), hy = (P.vy_max - P.vy_min) / (P.nvy - 1);
-  for (int iy = 0; iy < P.nvy; ++iy)
+  // the whole grid, and this context's rows of it (all rows unless sharded)
+  std::vector<double> vxa(s.nvp_all, 0.0), vya(s.nvp_all, 0.0), wa(s.nvp_all, 0.0);
+  std::vector<float> vxaf(s.nvp_all, 0.f), vyaf(s.nvp_all, 0.f), waf(s.nvp_all, 0.f), vy1(P.nvy);
+  for (int iy = 0; iy < P.nvy; ++iy) {
+    vy1[iy] = (float)(P.vy_min + (P.vy_max - P.vy_min) * iy / (P.nvy - 1));
     for (int ix = 0; ix < P.nvx; ++ix) {
       int k = iy * P.nvx + ix;
-      vx[k] = P.vx_min + (P.vx_max - P.vx_min) * ix / (P.nvx - 1);
-      vy[k] = P.vy_min + (P.vy_max - P.vy_min) * iy / (P.nvy - 1);
+      vxa[k] = P.vx_min + (P.vx_max - P.vx_min) * ix / (P.nvx - 1);
+      vya[k] = P.vy_min + (P.vy_max - P.vy_min) * iy / (P.nvy - 1);
       double wx = hx * ((ix == 0 || ix == P.nvx - 1) ? 0.5 : 1.0);
       double wy = hy * ((iy == 0 || iy == P.nvy - 1) ? 0.5 : 1.0);
-      w[k] = wy * wx;
-      vxf[k] = (float)vx[k]; vyf[k] = (float)vy[k]; wf[k] = (float)w[k];
+      wa[k] = wy * wx;
+      vxaf[k] = (float)vxa[k]; vyaf[k] = (float)vya[k]; waf[k] = (float)wa[k];
     }
+  }
+  for (int k = 0; k < s.nv; ++k) {
+    int ka = s.iy0 * P.nvx + k;
+    vx[k] = vxa[ka]; vy[k] = vya[ka]; w[k] = wa[ka];
+    vxf[k] = vxaf[ka]; vyf[k] = vyaf[ka]; wf[k] = waf[ka];
+  }
   // topology
   ctx->cell_off.assign(1, 0);
   ctx->node_off.assign(1, 0);
@@ -774,6 +852,8 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
           (blocks[order[b]].priority == blocks[order[a]].priority && order[b] < order[a]))
         std::swap(order[a], order[b]);
   std::vector<int> work = ws_work(nblocks, blocks, s.nvp, ctx->sweep_vpt, ctx->sweep_nw);
+  if ((int)work.size() / 3 != ctx->nwork || ctx->nwork > ctx->nwork_cap)
+    return fail(ctx, UGKS_ERR_WORKSPACE, "sweep work list");
   std::vector<int> tiles;
   for (int b = 0; b < nblocks; ++b) {
     std::vector<int> org(2 * (size_t)tile_count(blocks[b].ni, blocks[b].nj));
@@ -790,6 +870,13 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
   if ((r = up(ctx, (void *)d.vxf, vxf))) return r;
   if ((r = up(ctx, (void *)d.vyf, vyf))) return r;
   if ((r = up(ctx, (void *)d.wf, wf))) return r;
+  if ((r = up(ctx, (void *)d.vxa, vxa))) return r;
+  if ((r = up(ctx, (void *)d.vya, vya))) return r;
+  if ((r = up(ctx, (void *)d.wa, wa))) return r;
+  if ((r = up(ctx, (void *)d.vxaf, vxaf))) return r;
+  if ((r = up(ctx, (void *)d.vyaf, vyaf))) return r;
+  if ((r = up(ctx, (void *)d.waf, waf))) return r;
+  if ((r = up(ctx, (void *)d.vy1f, vy1))) return r;
   {
     // 1D trapezoid weights of the tensor grid (w_k = wy(iy) wx(ix))
     std::vector<float> wx1(ctx->p.nvx), wy1(ctx->p.nvy);
@@ -917,13 +1004,14 @@ int ugks_step(ugks_ctx *ctx, double dt, int n_inner) {
   if (ctx->fresh_pending) do_interp(ctx, 1);
   do_interp(ctx, 0);
   // Steps 1-2: level-n flux, extensive level-n macro term, level-n cell record
-  flux_prep(ctx, 1);
+  int rx = flux_prep(ctx, 1);
+  if (rx) return rx;
   { Prof p(ctx, UGKS_PROF_CELL); launch_cell_params(d, s, d.W, d.cparn, fp); }
   ctx->launches += 1;
   for (int it = 0; it < n_inner; ++it) {
     if (it > 0) {
       do_interp(ctx, 0);
-      flux_prep(ctx, 0);                       // Step 3
+      if ((rx = flux_prep(ctx, 0))) return rx;   // Step 3
     }
     // Step 4 (macro LU-SGS) on the side stream, concurrently with the flux
     // divergence of Step 3 on the main stream; Step 5 joins both
@@ -938,6 +1026,11 @@ int ugks_step(ugks_ctx *ctx, double dt, int n_inner) {
     { Prof p(ctx, UGKS_PROF_MICRO_FWD); launch_wsweep(d, s, 0, ctx->work, ctx->nwork, ctx->sweep_nw, ctx->ns_fwd, ctx->sweep_vpt, fp, ctx->sweep_ql); }  // Step 6
     { Prof p(ctx, UGKS_PROF_MICRO_BWD); launch_wsweep(d, s, 1, ctx->work, ctx->nwork, ctx->sweep_nw, ctx->ns_bwd, ctx->sweep_vpt, fp, ctx->sweep_ql); }
     { Prof p(ctx, UGKS_PROF_MOMENTS); launch_moments(d, s, fp); }                          // Step 7
+    if (d.shard) {
+      if ((rx = shard_exchange(ctx, 1))) return rx;
+      { Prof p(ctx, UGKS_PROF_MOMENTS); launch_moments_finish(d, s); }
+      ctx->launches += 1;
+    }
     ctx->launches += 8;
   }
   ctx->fresh_pending = false;
@@ -951,11 +1044,16 @@ int ugks_advance_batch(ugks_ctx *const *ctx, int n, const double *t_new, const d
                        int n_inner, int *failed) {
   if (failed) *failed = -1;
   if (n < 0 || (n > 0 && (!ctx || !t_new || !affine))) return UGKS_ERR_ARG;
-  for (int i = 0; i < n; ++i)
+  for (int i = 0; i < n; ++i) {
     if (!ctx[i] || !ctx[i]->mesh_ready) {
       if (failed) *failed = i;
       return UGKS_ERR_ORDER;
     }
+    if (ctx[i]->d.shard) {
+      if (failed) *failed = i;
+      return fail(ctx[i], UGKS_ERR_ARG, "velocity shards are stepped one context per call (ugks_step)");
+    }
+  }
   // stage-major issue order: every instance's motion, then every assembly,
   // then every step, so that all streams have work queued early
   for (int stage = 0; stage < 3; ++stage)
@@ -1121,7 +1219,8 @@ int ugks_eval_flux(ugks_ctx *ctx, double *D, double *F) {
   Dev &d = ctx->d;
   if (D && !is_device_ptr(D)) return fail(ctx, UGKS_ERR_ARG, "D must be a device pointer");
   do_interp(ctx, 0);
-  flux_prep(ctx, 0);
+  int r = flux_prep(ctx, 0);
+  if (r) return r;
   if (D) { launch_flux_div_all(d, ctx->st, D, ctx->fp32); ctx->launches += 1; }
   if (F) CK(cudaMemcpyAsync(F, d.Fc, sizeof(double) * 4 * d.nc, cudaMemcpyDefault, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));

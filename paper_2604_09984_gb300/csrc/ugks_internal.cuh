@@ -37,8 +37,16 @@ struct Dev {
   // velocity space (double and float copies), length nvp (padding weight 0)
   const double *vx, *vy, *w;
   const float *vxf, *vyf, *wf;
-  int nvx, nvy;              // tensor grid: k = iy nvx + ix, w_k = wy1(iy) wx1(ix)
-  const float *wx1f, *wy1f;  // 1D trapezoid weights
+  int nvx, nvy;              // tensor grid: k = iy nvx + ix, w_k = wy1(iy) wx1(ix); nvy of the whole grid
+  const float *wx1f, *wy1f;  // 1D trapezoid weights (whole grid)
+  const float *vy1f;         // 1D y nodes of the whole grid
+  // velocity sharding: this context holds the rows iy0 <= iy < iy0 + nv / nvx
+  // of the grid; the arrays above (vx, vy, w and copies) are its own rows, the
+  // ones below the whole grid (the same arrays when not sharded)
+  int shard, iy0, nv_all;
+  const double *vxa, *vya, *wa;
+  const float *vxaf, *vyaf, *waf;
+  double *msum;              // nc*6: partial moment sums of a sharded step (W fix 4, q 2)
   // static topology
   const int *cell_nodes;     // nc*4
   const int *cell_faces;     // nc*4 (IM, IP, JM, JP)
@@ -280,6 +288,16 @@ template <> __device__ __forceinline__ float dvy<float>(const Dev &d, int k) { r
 template <typename T> __device__ __forceinline__ T dw(const Dev &d, int k);
 template <> __device__ __forceinline__ double dw<double>(const Dev &d, int k) { return d.w[k]; }
 template <> __device__ __forceinline__ float dw<float>(const Dev &d, int k) { return d.wf[k]; }
+// the whole velocity grid (k < nv_all), also on a sharded context
+template <typename T> __device__ __forceinline__ T dvxa(const Dev &d, int k);
+template <> __device__ __forceinline__ double dvxa<double>(const Dev &d, int k) { return d.vxa[k]; }
+template <> __device__ __forceinline__ float dvxa<float>(const Dev &d, int k) { return d.vxaf[k]; }
+template <typename T> __device__ __forceinline__ T dvya(const Dev &d, int k);
+template <> __device__ __forceinline__ double dvya<double>(const Dev &d, int k) { return d.vya[k]; }
+template <> __device__ __forceinline__ float dvya<float>(const Dev &d, int k) { return d.vyaf[k]; }
+template <typename T> __device__ __forceinline__ T dwa(const Dev &d, int k);
+template <> __device__ __forceinline__ double dwa<double>(const Dev &d, int k) { return d.wa[k]; }
+template <> __device__ __forceinline__ float dwa<float>(const Dev &d, int k) { return d.waf[k]; }
 
 // value of the cell field f at velocity k for neighbour slot `s` of cell c
 // (cell neighbour or ghost Maxwellian of the ghost state)

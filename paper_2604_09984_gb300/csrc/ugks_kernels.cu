@@ -443,8 +443,8 @@ __device__ __forceinline__ void face_eq_flux_separable(const Dev &d, const float
 #pragma unroll
     for (int a = 0; a < 7; ++a) { mx[a] += p; p *= cx; }
   }
-  for (int iy = lane; iy < d.nvy; iy += GS) {
-    float cy = d.vyf[iy * d.nvx] - uy;
+  for (int iy = lane; iy < d.nvy; iy += GS) {     // the whole grid (also when sharded)
+    float cy = d.vy1f[iy] - uy;
     float e = d.wy1f[iy] * __expf(-lam * cy * cy), p = e;
 #pragma unroll
     for (int a = 0; a < 7; ++a) { my[a] += p; p *= cy; }
@@ -499,8 +499,10 @@ template <typename T> __global__ void __launch_bounds__(256, 2) k_face_coef(Dev 
     else { snx = (T)d.Sn[2 * fid]; sny = (T)d.Sn[2 * fid + 1]; sun = (T)d.SUn[fid]; }
     T tufx = parT[FP_UFX], tufy = parT[FP_UFY], tlamw = parT[FP_LAMW], tK = (T)d.Keff;
     V2<T> zero = {T(0), T(0)};
-    for (int k = sub * 32 + lane; k < d.nv; k += 32 * FCW) {
-      T vx = dvx<T>(d, k), vy = dvy<T>(d, k), w = dw<T>(d, k);
+    // the equilibrium and reflected parts depend on no f: the whole grid
+    // (also on a sharded context, so every shard gets the same totals)
+    for (int k = sub * 32 + lane; k < d.nv_all; k += 32 * FCW) {
+      T vx = dvxa<T>(d, k), vy = dvya<T>(d, k), w = dwa<T>(d, k);
       T wS = vx * snx + vy * sny - sun;
       T v2 = T(0.5) * (vx * vx + vy * vy);
       T cw = w * wS;
@@ -1085,6 +1087,10 @@ template <typename T, int FB> __global__ void k_moments(Dev d) {
   auto tot = [&](int m) { return to_double(warp_total(a[m])); };
   double t0 = tot(0), t1 = tot(1), t2 = tot(2), t3 = tot(3), t4 = tot(4), t5 = tot(5);
   double mine = lane == 0 ? t0 : lane == 1 ? t1 : lane == 2 ? t2 : lane == 3 ? t3 : lane == 4 ? t4 : t5;
+  if (d.shard) {        // this shard's sums; k_moments_finish completes them after the exchange
+    if (lane < 6) d.msum[6 * c + lane] = mine;
+    return;
+  }
   double wn = 0.0;
   if (lane < 4) {
     wn = d.Wp[4 * c + lane] + mine;
@@ -1101,6 +1107,23 @@ template <typename T, int FB> __global__ void k_moments(Dev d) {
   }
 }
 
+// Step 7 of a sharded step after the exchange: msum holds the sums over the
+// whole velocity grid; W = W' + the fix, q the heat flux, checked as above.
+__global__ void k_moments_finish(Dev d) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.nc || d.status[c] != ST_FIELD) return;
+  const double *m = d.msum + 6 * (size_t)c;
+  double w[4];
+  for (int i = 0; i < 4; ++i) {
+    w[i] = d.Wp[4 * c + i] + m[i];
+    d.W[4 * c + i] = w[i];
+  }
+  d.q[2 * c] = m[4];
+  d.q[2 * c + 1] = m[5];
+  double ei2 = 2.0 * w[0] * w[3] - (w[1] * w[1] + w[2] * w[2]);
+  if (!(w[0] > 0.0) || !(ei2 > 0.0) || !isfinite(w[0]) || !isfinite(ei2)) atomicOr(d.err, EF_NONPHYSICAL);
+}
+
 // Initial state: f = reduced Maxwellian of the primitive field, W, and q from f.
 template <typename T> __global__ void k_init_state(Dev d, const double *prim) {
   int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1108,16 +1131,21 @@ template <typename T> __global__ void k_init_state(Dev d, const double *prim) {
   if (c >= d.nc) return;
   double rho = prim[4 * c], ux = prim[4 * c + 1], uy = prim[4 * c + 2], T0 = prim[4 * c + 3];
   double lam = 1.0 / (2.0 * T0);
-  double qx = 0, qy = 0;
   for (int k = lane; k < d.nvp; k += 32) {
     if (k >= d.nv) { stF<T>(d, (size_t)c * d.nvp + k, T(0), T(0)); continue; }
     V2<double> g = maxwellian<double>(rho, ux, uy, lam, d.vx[k], d.vy[k], (double)d.Keff);
+    stF<T>(d, (size_t)c * d.nvp + k, (T)g.h, (T)g.b);
+  }
+  // q from the stored values over the whole grid (a shard recomputes the
+  // other shards' Maxwellian values, so no exchange is needed)
+  double qx = 0, qy = 0;
+  for (int k = lane; k < d.nv_all; k += 32) {
+    V2<double> g = maxwellian<double>(rho, ux, uy, lam, d.vxa[k], d.vya[k], (double)d.Keff);
     T h = (T)g.h, b = (T)g.b;
-    stF<T>(d, (size_t)c * d.nvp + k, h, b);
-    double cx = d.vx[k] - ux, cy = d.vy[k] - uy;
+    double cx = d.vxa[k] - ux, cy = d.vya[k] - uy;
     double e = (cx * cx + cy * cy) * (double)h + (double)b;
-    qx += 0.5 * d.w[k] * cx * e;
-    qy += 0.5 * d.w[k] * cy * e;
+    qx += 0.5 * d.wa[k] * cx * e;
+    qy += 0.5 * d.wa[k] * cy * e;
   }
   qx = warp_sum(qx);
   qy = warp_sum(qy);
@@ -1323,6 +1351,7 @@ void sweep_setup() {
 #undef UGKS_MACRO_ATTR
 }
 
+void launch_moments_finish(const Dev &d, cudaStream_t s) { k_moments_finish<<<nblk(d.nc, 256), 256, 0, s>>>(d); }
 void launch_moments(const Dev &d, cudaStream_t s, int fp32) {
   if (fp32 && d.fbf) k_moments<float, 1><<<nblk((size_t)d.nc * 32, 256), 256, 0, s>>>(d);
   else if (fp32) k_moments<float, 0><<<nblk((size_t)d.nc * 32, 256), 256, 0, s>>>(d);

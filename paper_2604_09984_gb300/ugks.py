@@ -32,7 +32,8 @@ class Params(ctypes.Structure):
     _fields_ = [("precision", c_int), ("nvx", c_int), ("nvy", c_int),
                 ("vx_min", c_double), ("vx_max", c_double), ("vy_min", c_double), ("vy_max", c_double),
                 ("K", c_int), ("Pr", c_double), ("omega", c_double), ("mu_ref", c_double),
-                ("cfl_s", c_double), ("cfl_pseudo", c_double), ("farfield", c_double * 4)]
+                ("cfl_s", c_double), ("cfl_pseudo", c_double), ("farfield", c_double * 4),
+                ("shard_iy0", c_int), ("shard_iy1", c_int)]
 
 
 class BlockDesc(ctypes.Structure):
@@ -45,6 +46,9 @@ class ConnectStats(ctypes.Structure):
     _fields_ = [("n_field", c_int), ("n_receptor", c_int), ("n_hole", c_int),
                 ("n_fresh", c_int), ("n_orphan", c_int)]
 
+
+# exchange of a velocity-sharded context: fn(which, stream, user) -> 0
+EXCHANGE_FN = ctypes.CFUNCTYPE(c_int, c_int, c_void_p, c_void_p)
 
 SYMBOLS = {
     "ugks_workspace_query": (c_int, [POINTER(Params), c_int, POINTER(BlockDesc), POINTER(c_size_t)]),
@@ -69,6 +73,9 @@ SYMBOLS = {
     "ugks_get_geometry": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ugks_launch_count": (c_int64, [c_void_p]),
     "ugks_set_wait_limit": (c_int, [c_void_p, c_int]),
+    "ugks_shard_set_exchange": (c_int, [c_void_p, EXCHANGE_FN, c_void_p]),
+    "ugks_shard_buffers": (c_int, [c_void_p, POINTER(c_size_t), POINTER(c_size_t), POINTER(c_size_t),
+                                   POINTER(c_size_t)]),
     "ugks_probe_fp64": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p]),
     "ugks_profile_enable": (c_int, [c_void_p, c_int]),
     "ugks_profile_read": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int64), c_int]),
@@ -103,8 +110,10 @@ class UgksError(RuntimeError):
         self.code = code
 
 
-def make_params(case: wl.Case, precision: int) -> Params:
+def make_params(case: wl.Case, precision: int, shard=None) -> Params:
     p = Params()
+    if shard is not None:
+        p.shard_iy0, p.shard_iy1 = int(shard[0]), int(shard[1])
     p.precision = precision
     p.nvx, p.nvy = case.nvx, case.nvy
     p.vx_min, p.vx_max, p.vy_min, p.vy_max = case.vbox
@@ -155,15 +164,16 @@ class Solver:
     """One libugks context for a workload: owns the device workspace (a torch
     uint8 tensor) and runs on the current torch CUDA stream."""
 
-    def __init__(self, case: wl.Case, precision: int = FP64, device="cuda", stream=None, prim=None):
+    def __init__(self, case: wl.Case, precision: int = FP64, device="cuda", stream=None, prim=None, shard=None):
         import torch
         self.torch = torch
         self.lib = load()
         self.case = case
         self.precision = precision
+        self.shard = shard
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        self._p = make_params(case, precision)
+        self._p = make_params(case, precision, shard)
         self._descs, self._keep = make_blocks(case)
         nbytes = c_size_t(0)
         self._check(self.lib.ugks_workspace_query(ctypes.byref(self._p), len(case.blocks),
@@ -190,6 +200,10 @@ class Solver:
         if r != OK:
             c = self.ctx if ctx == "self" else None
             msg = self.lib.ugks_last_error(c).decode() if c is not None else ""
+            xerr = getattr(self, "_xerr", None)
+            if xerr:
+                msg += " (exchange: %s)" % xerr
+                self._xerr = None
             raise UgksError(r, msg)
 
     def close(self):
@@ -328,6 +342,35 @@ class Solver:
     def launch_count(self):
         return int(self.lib.ugks_launch_count(self.ctx))
 
+    def set_exchange(self, fn):
+        """Exchange of a velocity-sharded context (ugks_shard_set_exchange):
+        fn(which) -> None turns this shard's partial sums in
+        shard_views()[which] into the sums over all shards."""
+        import weakref
+        me = weakref.ref(self)           # no reference cycle through the callback
+
+        def cb(which, stream, user):
+            try:
+                fn(int(which))
+                return 0
+            except Exception as e:  # reported as UGKS_ERR_ARG by the library
+                s = me()
+                if s is not None:
+                    s._xerr = repr(e)
+                return 1
+        self._xfn = EXCHANGE_FN(cb)      # keep a reference while the context lives
+        self._check(self.lib.ugks_shard_set_exchange(self.ctx, self._xfn, None))
+
+    def shard_views(self):
+        """The two exchange buffers (face sums, cell moment sums) as FP64
+        views of this context's workspace."""
+        fo, fc, co, cc = c_size_t(), c_size_t(), c_size_t(), c_size_t()
+        self._check(self.lib.ugks_shard_buffers(self.ctx, ctypes.byref(fo), ctypes.byref(fc),
+                                                ctypes.byref(co), ctypes.byref(cc)))
+        f = self.ws[fo.value:fo.value + 8 * fc.value].view(self.torch.float64)
+        c = self.ws[co.value:co.value + 8 * cc.value].view(self.torch.float64)
+        return f, c
+
     def set_wait_limit(self, polls):
         """Polls of the sweeps' bounded waits (ugks_set_wait_limit; 0 = default)."""
         self._check(self.lib.ugks_set_wait_limit(self.ctx, int(polls)))
@@ -401,3 +444,123 @@ class RigidBody:
         b0 = cx + self.disp[0] - (co * cx - si * cy)
         b1 = cy + self.disp[1] - (si * cx + co * cy)
         return np.array([co, -si, si, co, b0, b1])
+
+
+# ------------------------------------------------------ velocity sharding
+def shard_rows(nvy, n):
+    """Contiguous, balanced row ranges [iy0, iy1) of the velocity grid for n
+    shards (the first nvy % n shards take one row more)."""
+    if not 1 <= n <= nvy:
+        raise ValueError("1 <= shards <= velocity rows")
+    q, r = divmod(nvy, n)
+    out, iy = [], 0
+    for i in range(n):
+        m = q + (1 if i < r else 0)
+        out.append((iy, iy + m))
+        iy += m
+    return out
+
+
+def fixed_order_allreduce(t, group=None):
+    """Sum of tensor t over the ranks of a torch.distributed group, summed in
+    rank order (so every rank gets the same bits), written back into t."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    parts = [torch.empty_like(t) for _ in range(world)]
+    dist.all_gather(parts, t.contiguous(), group=group)
+    acc = parts[0].clone()
+    for p in parts[1:]:
+        acc += p
+    t.copy_(acc)
+    return t
+
+
+def distributed_exchange(solver, group=None):
+    """Exchange of a shard held by this rank: fixed-order all-reduce of its
+    buffers over the ranks of `group` (one shard per rank, NCCL on GPUs)."""
+    views = solver.shard_views()
+
+    def fn(which):
+        solver.stream.synchronize()
+        fixed_order_allreduce(views[which], group)
+        solver.torch.cuda.current_stream(solver.device).synchronize()
+    solver.set_exchange(fn)
+
+
+class ShardSet:
+    """Velocity shards of one case on one GPU, stepped together: every shard
+    context runs its ugks_* call in its own host thread, and the exchange sums
+    the shards' buffers in shard order (the same bits on every shard).  This
+    is the sharded data path of several GPUs with the collective replaced by
+    an in-process sum."""
+
+    def __init__(self, case, precision, nshards, device="cuda", prim=None):
+        import threading
+        import torch
+        self.case = case
+        self.rows = shard_rows(case.nvy, nshards)
+        self.solvers = [Solver(case, precision, device=device, prim=prim, shard=r,
+                               stream=torch.cuda.Stream(device=device)) for r in self.rows]
+        self.views = [s.shard_views() for s in self.solvers]
+        self._bar = threading.Barrier(nshards)
+        self._torch = torch
+        for i, s in enumerate(self.solvers):
+            s.set_exchange(self._make_fn(i))
+
+    def _make_fn(self, i):
+        # the closure holds the buffers, the barrier and the shard's stream,
+        # not the set itself (no cycle set -> solver -> callback -> set)
+        torch, views, bar, stream = self._torch, self.views, self._bar, self.solvers[i].stream
+
+        def fn(which):
+            stream.synchronize()
+            bar.wait()
+            if i == 0:
+                acc = views[0][which].clone()
+                for v in views[1:]:
+                    acc += v[which]
+                for v in views:
+                    v[which].copy_(acc)
+                torch.cuda.synchronize()
+            bar.wait()
+        return fn
+
+    def close(self):
+        for s in self.solvers:
+            s.close()
+
+    def _parallel(self, name, *args):
+        import threading
+        errs = [None] * len(self.solvers)
+
+        def run(i):
+            try:
+                getattr(self.solvers[i], name)(*args)
+            except BaseException as e:       # noqa: BLE001 (re-raised below)
+                errs[i] = e
+                self._bar.abort()
+        ts = [threading.Thread(target=run, args=(i,)) for i in range(len(self.solvers))]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+        for e in errs:
+            if e is not None:
+                raise e
+
+    def advance(self, n_inner=None):
+        """One physical step of every shard (motion and assembly per shard,
+        then the sharded implicit step)."""
+        dt = self.case.dt
+        for s in self.solvers:
+            s.move_mesh(s.t + dt)
+            s.overset_connect()
+        self._parallel("step", dt, n_inner)
+
+    def moments(self):
+        return self.solvers[0].moments()
+
+    def get_f(self):
+        """f of the whole velocity grid (the shards' rows side by side)."""
+        return self._torch.cat([s.get_state()[0] for s in self.solvers], dim=1)

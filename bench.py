@@ -41,8 +41,13 @@ UNIT = "cell·vel·iter/s"
 FALLBACK_HBM = 6800.0
 
 
-def make_case(name, kn):
+def make_case(name, kn, mesh=None):
     if name == "mems":
+        if mesh:       # "NBIxNBJ+NOIxNOJ": a reduced MEMS mesh (profiler captures)
+            bg, og = mesh.split("+")
+            nbi, nbj = (int(v) for v in bg.split("x"))
+            noi, noj = (int(v) for v in og.split("x"))
+            return wl.mems(nbi=nbi, nbj=nbj, noi=noi, noj=noj, Kn=kn)
         return wl.mems(Kn=kn)
     if name == "channel":
         return wl.channel()
@@ -518,6 +523,8 @@ def main():
     ap.add_argument("--workload", default="mems", choices=["mems", "channel", "tsto", "mems_batch"])
     ap.add_argument("--instances", type=int, default=64, help="mems_batch: number of instances")
     ap.add_argument("--kn", type=float, default=0.1)
+    ap.add_argument("--mesh", default=None,
+                    help="mems: background and O-grid cells as NBIxNBJ+NOIxNOJ (default 256x128+128x32)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-plain comparison arm")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--fp64-steps", type=int, default=3)
@@ -558,7 +565,7 @@ def main():
         if dist is not None:
             dist.destroy_process_group()
         return
-    case = make_case(args.workload, args.kn)
+    case = make_case(args.workload, args.kn, args.mesh)
     steps = max(1, args.steps)
     warmup = max(3, args.warmup)
     peak, peak_kind = peaks()
@@ -576,7 +583,7 @@ def main():
     # profiled steps (CUDA events on the stream each group is launched on)
     prof = profiled_steps(s, min(steps, 5))
     pair = 8
-    default = args.workload == "mems" and args.kn == 0.1
+    default = args.workload == "mems" and args.kn == 0.1 and not args.mesh
     dom_tab = kernel_table(prof, nfield, case.nv, s.nc, pair)
     roof = dominant_roofline(prof, nfield, case.nv, s.nc, pair, peak, peak_kind)
     if default and roof.get("kernel"):

@@ -220,7 +220,7 @@ int ugks_wall_torque(ugks_ctx *ctx, const double *center, double *torque);
  * warm-up of each candidate, CUDA events on the stream), keeping the fastest:
  *  - the face kernels (velocity reduction and flux divergence, FP32 paths):
  *    their tile of 8x8 cells walks the velocities in chunks of `face_vk` in
- *    {8, 16, 32} with `face_nh` in {1, 2} threads per face slot (each takes
+ *    {8, 16, 32} with `face_nh` = 2 threads per face slot (each takes
  *    face_vk / face_nh velocities of a chunk); the FP64 path keeps (8, 2);
  *  - the micro LU-SGS sweeps, skewed wavefronts (a warp takes a band of 8
  *    rows, 4 lanes a row; 16 rows, 2 lanes a row when a block is taller than

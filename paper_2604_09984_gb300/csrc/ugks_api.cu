@@ -261,6 +261,7 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int fbf, int nwork, i
   d.Tn = c.take<char>(pair * (size_t)s.nc * s.nvp);
   d.dfs = c.take<char>(pair * (size_t)s.nc * s.nvp);
   d.Dbuf = c.take<char>(pair * (size_t)s.nc * s.nvp);
+  d.fval = c.take<char>(2 * pair * (size_t)s.nf * s.nvp);
   d.TW = c.take<double>(4 * (size_t)s.nc); d.Fc = c.take<double>(4 * (size_t)s.nc);
   d.dW = c.take<double>(4 * (size_t)s.nc); d.Wp = c.take<double>(4 * (size_t)s.nc);
   d.mrec = c.take<char>(fp32 ? sizeof(float) * NMR32 * s.nmrec32 : sizeof(double) * NMR * (size_t)s.nc);

@@ -86,6 +86,7 @@ struct Dev {
   // work
   void *Tn, *dfs;            // nc*nvp pairs: level-n term, forward-sweep result
   void *Dbuf;                // nc*nvp pairs: flux divergence of the inner iteration
+  void *fval;                // nf*nvp 4-vectors: upwind face value (h, b) and w.grad f (h, b) of the face pass
   double *TW;                // nc*4 extensive level-n macro term
   double *Fc;                // nc*4 macro flux divergence of the last flux
   double *dW;                // nc*4 macro increment
@@ -245,6 +246,14 @@ __device__ __forceinline__ void mbar_fence_init() {
 __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *mb, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(mb)), "r"(bytes)
                : "memory");
+}
+// raise the expected transaction bytes of the current phase (no arrival)
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *mb, unsigned bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(mb)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *mb) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(mb)) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long *mb, unsigned parity) {
   unsigned ok;

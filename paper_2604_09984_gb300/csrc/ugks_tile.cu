@@ -4,24 +4,28 @@
 //                  equilibrium's moments) and of the f-dependent parts of the
 //                  macro flux (Eq. macroscopicFlux);
 //   k_flux         flux divergence D = sum_faces S F_hat per (cell, velocity)
-//                  (Eqs. microscopicFlux, fullSolution, wall condition); it
-//                  does not depend on the macro predictor, so it runs while
-//                  the macro LU-SGS sweep runs on another stream;
+//                  (Eqs. microscopicFlux, fullSolution, wall condition) from
+//                  the face reconstruction the reduction stored; it does not
+//                  depend on the macro predictor, so it runs while the macro
+//                  LU-SGS sweep runs on another stream;
 //   k_residual     the micro residual r from D (reading R4).
 //
 // One CTA per 8x8 cell tile of a block walks all velocity chunks of VK
-// velocities.  Per chunk, f of the tile plus a two-cell halo (ghost cells
-// hold the Maxwellian of their ghost state) is staged in shared memory with
-// asynchronous copies, double-buffered so the next chunk arrives while the
-// current one is reconstructed.  A thread owns one face slot of the tile and
-// one half of every chunk's velocities: everything that does not depend on
-// the velocity -- the face geometry, which region cells are its two sides,
-// their slope cases and inverse Jacobians, and for the flux the interface
-// record of Eq. fullSolution -- is loaded once and kept in registers for the
-// whole velocity loop.  The reduction accumulates its 12 face sums in
-// registers across all chunks (per-chunk partial sums added with an
-// error-free transformation on the FP32 path) and writes them once, with no
-// atomics: the result does not depend on scheduling.
+// velocities.  In the reduction, per chunk, f of the tile plus a two-cell
+// halo (ghost cells hold the Maxwellian of their ghost state) is staged in
+// shared memory with asynchronous copies, double-buffered so the next chunk
+// arrives while the current one is reconstructed.  A thread owns one face
+// slot of the tile and one half of every chunk's velocities: everything that
+// does not depend on the velocity -- the face geometry, which region cells
+// are its two sides, their slope cases and inverse Jacobians, and for the
+// flux the interface record of Eq. fullSolution -- is loaded once and kept
+// in registers for the whole velocity loop.  The reduction accumulates its
+// 12 face sums in registers across all chunks (per-chunk partial sums added
+// with an error-free transformation on the FP32 path) and writes them once,
+// with no atomics: the result does not depend on scheduling.  It also stores
+// the reconstruction of every (face, velocity), so the flux pass reads one
+// 4-vector per (face, velocity) instead of re-staging f and recomputing the
+// limited gradients.
 #include "ugks_internal.cuh"
 #include "ugks_launch.h"
 
@@ -31,15 +35,18 @@ constexpr int TX = 8, TY = 8, RW = TX + 4, RH = TY + 4, NR = RW * RH;
 constexpr int NSI = (TX + 1) * TY;          // i-face slots: tile row w, column x = 0..TX
 constexpr int NSLOT = NSI + TX * (TY + 1);  // + j-face slots: tile column w, row y = 0..TY
 // Tile shape of the two face kernels (the autotuner's choice): VK velocities
-// per chunk, NH threads per face slot (each takes VK / NH velocities of a
-// chunk), NT threads a CTA; row strides of the staged region (VKP: rows of
-// whole 16-byte copies) and of the gradient and face-flux rows (VKG: odd, so
-// the lanes of a warp, which read different cells at one velocity, fall in
-// different banks).
+// per chunk, NH threads per face slot, NT threads a CTA.  The NH threads of a
+// slot are adjacent lanes and take interleaved velocities (kk = part + NH q),
+// so the NH of them store NH consecutive reconstructions -- whole 32-byte
+// sectors for NH = 2.  Row strides (in elements) of the staged region (VKP:
+// rows of whole 16-byte copies), of the gradient rows and face-flux rows
+// (VKG) and of the staged face reconstructions (VKF), chosen so that the
+// lanes of a quarter warp -- NH velocities of 8 / NH neighbouring cells or
+// faces -- fall in different banks.
 template <typename T, int VK_, int NH_> struct FCfg {
-  static constexpr int VK = VK_, NH = NH_, NT = NSLOT * NH_;
-  static constexpr int VKP = sizeof(T) == 4 ? VK_ + 2 : VK_, VKG = VK_ + 1;
-  static_assert(NT % VK == 0 && VK % NH == 0, "tile shape");
+  static constexpr int VK = VK_, NH = NH_, NT = NSLOT * NH_, VH = VK_ / NH_;
+  static constexpr int VKP = sizeof(T) == 4 ? VK_ + 2 : VK_, VKG = VK_ + 2, VKF = VK_ + 2;
+  static_assert(NT % VK == 0 && VK % NH == 0 && NH == 2, "tile shape");
 };
 
 // region cell (i, j) of block b -> cell id (>= 0), ghost (-2 - face id) or
@@ -322,6 +329,20 @@ __device__ __forceinline__ void slot_geom(int slot, int &dir, int &w, int &x, in
   }
 }
 
+// The stored reconstruction of one (face, velocity): (f_face h, f_face b,
+// w.grad f h, w.grad f b).
+template <typename T>
+__device__ __forceinline__ void st_fval(typename Vec4<T>::type *p, const V2<T> &ff, const V2<T> &wg) {
+  typename Vec4<T>::type v;
+  v.x = ff.h; v.y = ff.b; v.z = wg.h; v.w = wg.b;
+  *p = v;
+}
+
+// bytes of the flux pass's face-flux rows (a multiple of 32)
+template <typename T, typename C> __host__ __device__ constexpr size_t flux_fs_bytes() {
+  return (sizeof(typename Vec2<T>::type) * NSLOT * C::VKG + 31) / 32 * 32;
+}
+
 // error-free sum (Knuth): s + e = a + b exactly
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   s = a + b;
@@ -337,6 +358,9 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
 // with the time integrals q1, q2 applied afterwards).  Per chunk: staging of
 // the next chunk, gradients (phase A), face sums (phase B); FP32 partial sums
 // of two chunks are folded into a (sum, error) pair by an error-free sum.
+// The reconstruction of every (face, velocity) -- the upwind face value and
+// w.grad f of Eq. fullSolution -- is stored for the flux pass, which then
+// needs neither f nor its gradients.
 template <typename T, int FB, int VKT, int NHT>
 __global__ void __launch_bounds__(NSLOT * NHT) k_face_reduce(Dev d) {
   typedef typename Vec2<T>::type T2;
@@ -354,8 +378,8 @@ __global__ void __launch_bounds__(NSLOT * NHT) k_face_reduce(Dev d) {
   __syncthreads();
   const int nch = (d.nv + VK - 1) / VK;
   stage_chunk<T, FB, C>(d, S, 0, 0);
-  // this thread's face
-  int slot = threadIdx.x % NSLOT, half = threadIdx.x / NSLOT;
+  // this thread's face (the NH threads of a slot are adjacent lanes)
+  int slot = threadIdx.x / NH, half = threadIdx.x % NH;
   int dir, w, x, A, B;
   slot_geom(slot, dir, w, x, A, B);
   int fid = tile_face_id(d, dir, off, ni, nj, i0, j0, w, x);
@@ -394,9 +418,11 @@ __global__ void __launch_bounds__(NSLOT * NHT) k_face_reduce(Dev d) {
     if (act) {
       const T2 *Fb = S.F + (size_t)buf * NR * VKP;
       const T4 *vt = S.vt + buf * VK;
+      const int kb = ch * VK;
+      T4 *fv = reinterpret_cast<T4 *>(d.fval) + (size_t)fid * d.nvp + kb;
 #pragma unroll 4
       for (int q = 0; q < VH; ++q) {
-        int kk = half * VH + q;
+        int kk = half + NH * q;
         T4 v = vt[kk];
         T vx = v.x, vy = v.y, v2 = v.w;
         T wS = vx * snx + vy * sny - sun;
@@ -404,6 +430,8 @@ __global__ void __launch_bounds__(NSLOT * NHT) k_face_reduce(Dev d) {
         T wk = (wall && !(wS > T(0))) ? T(0) : v.z;
         V2<T> ff, wg;
         upwind<T, C>(S, Fb, L, R, wall, kk, wS, vx - ufx, vy - ufy, ff, wg);
+        // the flux pass reads the reconstruction from here
+        if (kb + kk < d.nv) st_fval<T>(fv + kk, ff, wg);
         T a = wk * ff.h, bb = T(0.5) * wk * ff.b;
         T p0 = a, p1 = vx * a, p2 = vy * a, p3 = v2 * a + bb;
         T ga = wk * wg.h, gb = T(0.5) * wk * wg.b;
@@ -465,109 +493,189 @@ __global__ void __launch_bounds__(NSLOT * NHT) k_face_reduce(Dev d) {
 
 // -------------------------------------------------------- flux divergence
 // Every face slot of the tile (faces shared with a neighbouring tile are
-// evaluated by both) computes S F_hat per velocity into shared memory; then
-// each (tile cell, velocity) sums its four faces with the cell's orientation
-// signs and stores D.
-template <typename T, int FB, int VKT, int NHT> __global__ void __launch_bounds__(NSLOT * NHT) k_flux(Dev d) {
+// evaluated by both) computes S F_hat per velocity into shared memory from
+// the reconstruction the reduction pass stored; then each (tile cell,
+// velocity) sums its four faces with the cell's orientation signs and stores
+// D.  A streaming pass: the reconstructions of a chunk arrive in shared
+// memory as one bulk copy per face row (VK 4-vectors, issued by the face's
+// own thread, completing on the buffer's mbarrier; double-buffered), each
+// (face, velocity) adds the equilibrium part from the face's cubics, and each
+// (cell, velocity) makes one store.  ROW: the chunk lies in one row of the
+// velocity grid (VK divides N_vx), so c_y is fixed over it: the cubics
+// become cubics in c_x with coefficients formed once per chunk, and the
+// c_y factor of the Maxwellian is one exponential per chunk.
+template <typename T, typename C> __host__ __device__ constexpr size_t flux_fv_bytes() {
+  return sizeof(typename Vec4<T>::type) * 2 * NSLOT * C::VKF;
+}
+
+template <typename T, int VKT, int NHT, bool ROW> __global__ void __launch_bounds__(NSLOT * NHT) k_flux(Dev d) {
   typedef typename Vec2<T>::type T2;
   typedef typename Vec4<T>::type T4;
   typedef FCfg<T, VKT, NHT> C;
-  constexpr int VK = C::VK, VKP = C::VKP, VKG = C::VKG, VH = VK / C::NH;
+  constexpr int VK = C::VK, VKG = C::VKG, VKF = C::VKF, NH = C::NH, VH = C::VH;
   extern __shared__ __align__(16) unsigned char smraw[];
-  FaceSmem<T, C> S;
-  S.carve(smraw);
-  T2 *Fs = reinterpret_cast<T2 *>(smraw + FaceSmem<T, C>::bytes());     // [NSLOT][VKG]
-  int *cinf = reinterpret_cast<int *>(Fs + (size_t)NSLOT * VKG);          // [TX*TY]: cell id or -1
-  char4 *csg = reinterpret_cast<char4 *>(cinf + TX * TY);                 // [TX*TY]: face signs
+  T4 *FV = reinterpret_cast<T4 *>(smraw);                                    // [2][NSLOT][VKF]
+  T2 *Fs = reinterpret_cast<T2 *>(smraw + flux_fv_bytes<T, C>());            // [NSLOT][VKG]
+  T4 *sgn = reinterpret_cast<T4 *>(smraw + flux_fv_bytes<T, C>() + flux_fs_bytes<T, C>());  // [TX*TY]
+  T2 *vt = reinterpret_cast<T2 *>(sgn + TX * TY);                           // [2][VK]: vx, vy
+  unsigned long long *mb = reinterpret_cast<unsigned long long *>(vt + 2 * VK);  // [2]
+  int *cinf = reinterpret_cast<int *>(mb + 2);                              // [TX*TY]: cell id or -1
   int tile = blockIdx.x;
   int b = d.tiles[3 * tile], i0 = d.tiles[3 * tile + 1], j0 = d.tiles[3 * tile + 2];
   const int *bi = d.blk_info + 8 * b;
   int ni = bi[0], nj = bi[1], off = d.cell_off[b];
-  region_meta<T, C>(d, S, bi, off, i0, j0);
+  if (threadIdx.x == 0) {
+    mbar_init(&mb[0], 1);
+    mbar_init(&mb[1], 1);
+    mbar_fence_init();
+  }
   for (int c = threadIdx.x; c < TX * TY; c += blockDim.x) {
     int tx = c % TX, ty = c / TX, i = i0 + tx, j = j0 + ty;
     int g = (i < ni && j < nj) ? off + j * ni + i : -1;
     if (g >= 0 && d.status[g] != ST_FIELD) g = -1;
     cinf[c] = g;
-    csg[c] = g >= 0 ? reinterpret_cast<const char4 *>(d.cell_sgn)[g] : make_char4(0, 0, 0, 0);
+    char4 sc = g >= 0 ? reinterpret_cast<const char4 *>(d.cell_sgn)[g] : make_char4(0, 0, 0, 0);
+    sgn[c] = T4{(T)sc.x, (T)sc.y, (T)sc.z, (T)sc.w};
   }
-  __syncthreads();
-  const int nch = (d.nv + VK - 1) / VK;
-  stage_chunk<T, FB, C>(d, S, 0, 0);
-  int slot = threadIdx.x % NSLOT, half = threadIdx.x / NSLOT;
-  int dir, w, x, A, B;
-  slot_geom(slot, dir, w, x, A, B);
-  int fid = tile_face_id(d, dir, off, ni, nj, i0, j0, w, x);
+  const int nv = d.nv, nch = (nv + VK - 1) / VK;
+  int slot = threadIdx.x / NH, half = threadIdx.x % NH;
   bool act = false;
-  if (fid >= 0 && d.face_kind[fid] != BC_OVERSET) {
-    int Lg = d.face_L[fid], Rg = d.face_R[fid];
-    act = d.status[Lg] == ST_FIELD || (Rg >= 0 && d.status[Rg] == ST_FIELD);
+  int fid;
+  {
+    int dir, w, x, A, B;
+    slot_geom(slot, dir, w, x, A, B);
+    fid = tile_face_id(d, dir, off, ni, nj, i0, j0, w, x);
+    if (fid >= 0 && d.face_kind[fid] != BC_OVERSET) {
+      int Lg = d.face_L[fid], Rg = d.face_R[fid];
+      act = d.status[Lg] == ST_FIELD || (Rg >= 0 && d.status[Rg] == ST_FIELD);
+    }
   }
+  const T4 *frow = reinterpret_cast<const T4 *>(d.fval) + (size_t)(act ? fid : 0) * d.nvp;
+  // velocity table of chunk ch into buffer ch & 1
+  auto stage_v = [&](int ch) {
+    for (int kk = threadIdx.x; kk < VK; kk += blockDim.x) {
+      int k = ch * VK + kk;
+      T2 t = {T(0), T(0)};
+      if (k < nv) { t.x = dvx<T>(d, k); t.y = dvy<T>(d, k); }
+      vt[(ch & 1) * VK + kk] = t;
+    }
+  };
+  // this face's row of chunk ch into buffer ch & 1 (the slot's first thread)
+  auto stage_row = [&](int ch) {
+    if (act && half == 0) {
+      int kb = ch * VK;
+      unsigned bytes = (unsigned)(sizeof(T4) * (nv - kb < VK ? nv - kb : VK));
+      unsigned long long *m = &mb[ch & 1];
+      mbar_expect_tx(m, bytes);
+      bulk_g2s(FV + ((ch & 1) * NSLOT + slot) * VKF, frow + kb, bytes, m);
+    }
+  };
   bool wall = false;
   __align__(16) T P[NFP];
-  Side<T> L = make_side<T>(A, T(0), T(0)), R = L;
   if (act) {
     wall = d.face_kind[fid] == BC_WALL;
     load_rec<T, NFP>(reinterpret_cast<const T *>(d.fparT) + (size_t)fid * NFP, P);
-    int Lr = (S.gid[A] == d.face_L[fid]) ? A : B, Rr = (Lr == A) ? B : A;
-    L = make_side<T>(Lr, P[FP_DXLX], P[FP_DXLY]);
-    R = make_side<T>(Rr, P[FP_DXRX], P[FP_DXRY]);
   } else {
 #pragma unroll
     for (int m = 0; m < NFP; ++m) P[m] = T(0);
   }
+  stage_v(0);
+  __syncthreads();                 // mbarriers initialised; cinf, sgn, vt of chunk 0 visible
+  stage_row(0);
+  __syncthreads();                 // every expectation of chunk 0 registered
+  if (threadIdx.x == 0) mbar_arrive(&mb[0]);
   const T Keff = (T)d.Keff;
   for (int ch = 0; ch < nch; ++ch) {
-    int buf = ch & 1;
-    cp_async_wait<0>();
+    const int buf = ch & 1, kb = ch * VK;
+    // one warp polls the chunk's mbarrier (bounded; after a timeout, flagged,
+    // a second wait drains the copies), the others wait at the barrier
+    // without taking issue slots
+    if (threadIdx.x < 32)
+      if (!mbar_wait(&mb[buf], (ch >> 1) & 1, d.err)) mbar_wait(&mb[buf], (ch >> 1) & 1, d.err);
     __syncthreads();               // chunk ch visible; the face fluxes of ch-1 consumed
-    if (ch + 1 < nch) stage_chunk<T, FB, C>(d, S, ch + 1, buf ^ 1);
-    chunk_gradients<T, C>(S, buf);
-    __syncthreads();
-    const T2 *Fb = S.F + (size_t)buf * NR * VKP;
-    const T4 *vt = S.vt + buf * VK;
-#pragma unroll 4
-    for (int q = 0; q < VH; ++q) {
-      int kk = half * VH + q;
-      T2 Fo = {T(0), T(0)};
-      if (act) {
-        T4 v = vt[kk];
-        T vx = v.x, vy = v.y;
-        T wS = vx * P[FP_SNX] + vy * P[FP_SNY] - P[FP_SUN];
-        T wx = vx - P[FP_UFX], wy = vy - P[FP_UFY];
-        if (wall && !(wS > T(0))) {
-          // reflected part: wall Maxwellian at the face velocity (Eq. maxWalldes)
-          T lw = P[FP_LAMW];
-          T Hw = P[FP_RHOW] * (lw * T(M_1_PI)) * r_exp<T>(-lw * (wx * wx + wy * wy));
-          Fo.x = wS * Hw;
-          Fo.y = wS * Keff / (T(2) * lw) * Hw;
-        } else {
-          V2<T> ff, wg;
-          upwind<T, C>(S, Fb, L, R, wall, kk, wS, wx, wy, ff, wg);
-          // Eq. fullSolution averaged over dt_s: q1 f + q2 w.grad f + H ih(c)
-          // (and b), the equilibrium factors as per-face cubics in c = v - U0
-          T cx = vx - P[FP_UX], cy = vy - P[FP_UY];
-          T H = P[FP_HPRE] * r_exp<T>(-P[FP_LAM] * (cx * cx + cy * cy));
-          T Ih = P[FP_Q1] * ff.h + P[FP_Q2] * wg.h + H * poly3_at<T>(P + FP_IH, cx, cy);
-          T Ib = P[FP_Q1] * ff.b + P[FP_Q2] * wg.b + H * poly3_at<T>(P + FP_IB, cx, cy);
-          Fo.x = wS * Ih;
-          Fo.y = wS * Ib;
-        }
-      }
-      Fs[slot * VKG + kk] = Fo;
+    if (ch + 1 < nch) {            // buffer buf ^ 1 was last read before the previous combine
+      stage_row(ch + 1);
+      stage_v(ch + 1);
     }
-    __syncthreads();
-    const int kb = ch * VK;
+    const T4 *fvb = FV + (buf * NSLOT + slot) * VKF;
+    const T2 *vtb = vt + buf * VK;
+    T2 *fso = Fs + slot * VKG;
+    // the loops below are uniform per thread: walls (reflected part for
+    // w.n <= 0), interior faces of a chunk inside one velocity row (ROW, no
+    // ragged tail: N_v is a multiple of VK), other interior faces
+    if (act && !wall && ROW) {
+      // per-chunk factors: the c_y parts of the cubics and of the Maxwellian
+      const T vy = vtb[0].y, cy = vy - P[FP_UY];
+      const T *ch3 = P + FP_IH, *cb3 = P + FP_IB;
+      const T ah0 = ch3[0] + cy * (ch3[2] + cy * (ch3[5] + cy * ch3[9]));
+      const T ah1 = ch3[1] + cy * (ch3[4] + cy * ch3[8]);
+      const T ah2 = ch3[3] + cy * ch3[7], ah3 = ch3[6];
+      const T ab0 = cb3[0] + cy * (cb3[2] + cy * (cb3[5] + cy * cb3[9]));
+      const T ab1 = cb3[1] + cy * (cb3[4] + cy * cb3[8]);
+      const T ab2 = cb3[3] + cy * cb3[7], ab3 = cb3[6];
+      const T ey = P[FP_HPRE] * r_exp<T>(-P[FP_LAM] * (cy * cy));
+      const T wsy = vy * P[FP_SNY] - P[FP_SUN];
+      const T snx = P[FP_SNX], ux = P[FP_UX], nlam = -P[FP_LAM], q1 = P[FP_Q1], q2 = P[FP_Q2];
+#pragma unroll
+      for (int q = 0; q < VH; ++q) {
+        const int kk = half + NH * q;
+        const T4 fv = fvb[kk];
+        const T vx = vtb[kk].x;
+        // Eq. fullSolution averaged over dt_s: q1 f + q2 w.grad f + H ih(c)
+        // (and b), the equilibrium factors as per-face cubics in c = v - U0
+        const T wS = vx * snx + wsy, cx = vx - ux;
+        const T H = ey * r_exp<T>(nlam * (cx * cx));
+        const T ph = ah0 + cx * (ah1 + cx * (ah2 + cx * ah3));
+        const T pb = ab0 + cx * (ab1 + cx * (ab2 + cx * ab3));
+        T2 Fo;
+        Fo.x = wS * (q1 * fv.x + q2 * fv.z + H * ph);
+        Fo.y = wS * (q1 * fv.y + q2 * fv.w + H * pb);
+        fso[kk] = Fo;
+      }
+    } else if (act) {
+#pragma unroll 4
+      for (int q = 0; q < VH; ++q) {
+        const int kk = half + NH * q, k = kb + kk;
+        T2 Fo = {T(0), T(0)};
+        if (k < nv) {
+          const T4 fv = fvb[kk];
+          const T2 v = vtb[kk];
+          const T vx = v.x, vy = v.y;
+          const T wS = vx * P[FP_SNX] + vy * P[FP_SNY] - P[FP_SUN];
+          if (wall && !(wS > T(0))) {
+            // reflected part: wall Maxwellian at the face velocity (Eq. maxWalldes)
+            T wx = vx - P[FP_UFX], wy = vy - P[FP_UFY];
+            T lw = P[FP_LAMW];
+            T Hw = P[FP_RHOW] * (lw * T(M_1_PI)) * r_exp<T>(-lw * (wx * wx + wy * wy));
+            Fo.x = wS * Hw;
+            Fo.y = wS * Keff / (T(2) * lw) * Hw;
+          } else {
+            T cx = vx - P[FP_UX], cy = vy - P[FP_UY];
+            T H = P[FP_HPRE] * r_exp<T>(-P[FP_LAM] * (cx * cx + cy * cy));
+            T Ih = P[FP_Q1] * fv.x + P[FP_Q2] * fv.z + H * poly3_at<T>(P + FP_IH, cx, cy);
+            T Ib = P[FP_Q1] * fv.y + P[FP_Q2] * fv.w + H * poly3_at<T>(P + FP_IB, cx, cy);
+            Fo.x = wS * Ih;
+            Fo.y = wS * Ib;
+          }
+        }
+        fso[kk] = Fo;
+      }
+    } else {
+#pragma unroll 4
+      for (int q = 0; q < VH; ++q) fso[half + NH * q] = T2{T(0), T(0)};
+    }
+    __syncthreads();               // face fluxes complete; expectations of chunk ch + 1 registered
+    if (threadIdx.x == 0 && ch + 1 < nch) mbar_arrive(&mb[buf ^ 1]);
     for (int it = threadIdx.x; it < TX * TY * VK; it += blockDim.x) {
       int c = it / VK, kk = it - (it / VK) * VK;
       int g = cinf[c];
-      if (g < 0 || kb + kk >= d.nv) continue;
+      if (g < 0 || kb + kk >= nv) continue;
       int tx = c % TX, ty = c / TX;
-      char4 sg = csg[c];
+      T4 sg = sgn[c];
       T2 a = Fs[(ty * (TX + 1) + tx) * VKG + kk], bq = Fs[(ty * (TX + 1) + tx + 1) * VKG + kk];
       T2 cq = Fs[(NSI + tx * (TY + 1) + ty) * VKG + kk], dq = Fs[(NSI + tx * (TY + 1) + ty + 1) * VKG + kk];
-      T Dh = (T)sg.x * a.x + (T)sg.y * bq.x + (T)sg.z * cq.x + (T)sg.w * dq.x;
-      T Db = (T)sg.x * a.y + (T)sg.y * bq.y + (T)sg.z * cq.y + (T)sg.w * dq.y;
+      T Dh = sg.x * a.x + sg.y * bq.x + sg.z * cq.x + sg.w * dq.x;
+      T Db = sg.x * a.y + sg.y * bq.y + sg.z * cq.y + sg.w * dq.y;
       stf<T>(d.Dbuf, (size_t)g * d.nvp + kb + kk, Dh, Db);
     }
   }
@@ -618,8 +726,8 @@ template <typename T, int FB> __global__ void k_residual(Dev d, int first_iter) 
 }
 
 template <typename T, typename C> static size_t flux_smem() {
-  return FaceSmem<T, C>::bytes() + sizeof(typename Vec2<T>::type) * NSLOT * C::VKG + sizeof(int) * TX * TY +
-         sizeof(char4) * TX * TY;
+  return flux_fv_bytes<T, C>() + flux_fs_bytes<T, C>() + sizeof(typename Vec4<T>::type) * TX * TY +
+         sizeof(typename Vec2<T>::type) * 2 * C::VK + 2 * sizeof(unsigned long long) + sizeof(int) * TX * TY;
 }
 template <typename T, typename C> static size_t reduce_smem() {
   size_t a = FaceSmem<T, C>::bytes(), b = sizeof(T) * 2 * NFS * NSLOT * (C::NH > 1 ? C::NH - 1 : 1);
@@ -628,10 +736,10 @@ template <typename T, typename C> static size_t reduce_smem() {
 
 // Candidate tile shapes of the FP32 face kernels (velocities per chunk,
 // threads per face slot); the FP64 path keeps (8, 2).
-constexpr int kFaceVK[] = {8, 8, 16, 16, 32};
-constexpr int kFaceNH[] = {1, 2, 1, 2, 2};
-constexpr int kFaceDefault = 3;     // (16, 2)
-int face_tile_count() { return 5; }
+constexpr int kFaceVK[] = {8, 16, 32};
+constexpr int kFaceNH[] = {2, 2, 2};
+constexpr int kFaceDefault = 1;     // (16, 2)
+int face_tile_count() { return 3; }
 void face_tile_shape(int v, int *vk, int *nh) {
   if (v < 0 || v >= face_tile_count()) v = kFaceDefault;
   *vk = kFaceVK[v];
@@ -641,14 +749,13 @@ int face_tile_default() { return kFaceDefault; }
 
 template <typename T, int FB, int VK, int NH> static void face_attr() {
   typedef FCfg<T, VK, NH> C;
-  cudaFuncSetAttribute(k_flux<T, FB, VK, NH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)flux_smem<T, C>());
+  cudaFuncSetAttribute(k_flux<T, VK, NH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)flux_smem<T, C>());
+  cudaFuncSetAttribute(k_flux<T, VK, NH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)flux_smem<T, C>());
   cudaFuncSetAttribute(k_face_reduce<T, FB, VK, NH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)reduce_smem<T, C>());
 }
 template <int FB> static void face_attr_f32() {
-  face_attr<float, FB, 8, 1>();
   face_attr<float, FB, 8, 2>();
-  face_attr<float, FB, 16, 1>();
   face_attr<float, FB, 16, 2>();
   face_attr<float, FB, 32, 2>();
 }
@@ -669,14 +776,13 @@ void tile_origins(int ni, int nj, int *out) {   // (i0, j0) pairs
 template <typename T, int FB, int VK, int NH> static void face_launch(const Dev &d, cudaStream_t s, int which) {
   typedef FCfg<T, VK, NH> C;
   if (which == 0) k_face_reduce<T, FB, VK, NH><<<d.ntiles, C::NT, reduce_smem<T, C>(), s>>>(d);
-  else k_flux<T, FB, VK, NH><<<d.ntiles, C::NT, flux_smem<T, C>(), s>>>(d);
+  else if (d.nvx % VK == 0) k_flux<T, VK, NH, true><<<d.ntiles, C::NT, flux_smem<T, C>(), s>>>(d);
+  else k_flux<T, VK, NH, false><<<d.ntiles, C::NT, flux_smem<T, C>(), s>>>(d);
 }
 template <int FB> static void face_launch_f32(const Dev &d, cudaStream_t s, int which, int v) {
   switch (v) {
-    case 0: face_launch<float, FB, 8, 1>(d, s, which); break;
-    case 1: face_launch<float, FB, 8, 2>(d, s, which); break;
-    case 2: face_launch<float, FB, 16, 1>(d, s, which); break;
-    case 4: face_launch<float, FB, 32, 2>(d, s, which); break;
+    case 0: face_launch<float, FB, 8, 2>(d, s, which); break;
+    case 2: face_launch<float, FB, 32, 2>(d, s, which); break;
     default: face_launch<float, FB, 16, 2>(d, s, which); break;
   }
 }

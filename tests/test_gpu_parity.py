@@ -333,7 +333,7 @@ def test_batch_defers_orphan_report_to_next_sync():
     assert c1.n_orphan > 0
 
 
-@pytest.mark.parametrize("tile", range(5))
+@pytest.mark.parametrize("tile", range(3))
 def test_face_tile_shapes_agree(tile):
     """Every tile shape the autotuner may give the FP32 face kernels
     (velocities per chunk x threads per face slot) computes the same step up

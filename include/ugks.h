@@ -186,8 +186,25 @@ int ugks_overset_connect(ugks_ctx *ctx, ugks_connect_stats *stats);
  * {receptor interpolation, flux, macro LU-SGS, micro residual, micro LU-SGS,
  * step-7 moment fix}.  In place on f, W, q.  `dt` must equal t_new - t of
  * the preceding ugks_move_mesh.  Asynchronous.
- * Errors: UGKS_ERR_ORDER, UGKS_ERR_ARG. */
+ * The step's launches (both streams) are captured into a CUDA graph on the
+ * first step with a given configuration and replayed by one graph launch on
+ * later steps; a change of step size, inner count, tiles or wait limit, and
+ * the first step after an assembly that uncovered cells (one more
+ * interpolation), select or capture another graph.  Not graphed: while
+ * profiling (ugks_profile_enable), on a velocity shard (its exchange runs on
+ * the host), after ugks_set_graphs(ctx, 0) or with UGKS_NO_GRAPH=1 in the
+ * environment at creation.  Graphed and direct steps issue the same kernels
+ * with the same arguments.
+ * Errors: UGKS_ERR_ORDER, UGKS_ERR_ARG, UGKS_ERR_CUDA (capture). */
 int ugks_step(ugks_ctx *ctx, double dt, int n_inner);
+
+/* Turn the CUDA-graph path of ugks_step on (default) or off.  Errors:
+ * UGKS_ERR_ARG (null context). */
+int ugks_set_graphs(ugks_ctx *ctx, int on);
+
+/* Graph captures (or updates) and graph replays of ugks_step since creation
+ * (HOST outputs, each may be NULL).  Errors: UGKS_ERR_ARG. */
+int ugks_graph_stats(const ugks_ctx *ctx, int64_t *captures, int64_t *replays);
 
 /* Batched outer loop over n independent contexts ("instances": different
  * meshes, velocity grids and gases): for each instance i, ugks_move_mesh to

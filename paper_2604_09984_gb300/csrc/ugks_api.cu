@@ -20,6 +20,7 @@ struct ugks_ctx {
   ugks_params p;
   cudaStream_t st = nullptr;
   cudaStream_t side = nullptr;        // macro LU-SGS runs here, overlapped with the flux kernel
+  cudaStream_t cap = nullptr;         // step graphs are captured here (the caller's stream may be the legacy one)
   cudaEvent_t ev_flux = nullptr, ev_macro = nullptr;
   char *ws = nullptr;
   size_t ws_bytes = 0;
@@ -38,6 +39,21 @@ struct ugks_ctx {
   ugks_exchange_fn xfn = nullptr;     // velocity sharding: the caller's exchange
   void *xuser = nullptr;
   bool debug_sync = false, debug_failed = false;   // UGKS_DEBUG_SYNC
+  // CUDA graphs of ugks_step: captured on the first step with a
+  // configuration (key: the device struct the kernels take by value -- whose
+  // node buffers alternate from step to step --, the launch configuration and
+  // whether the step starts with the extra interpolation of uncovered cells)
+  // and replayed while it recurs; a few are kept, the least recently used is
+  // replaced
+  struct StepGraph {
+    std::vector<unsigned char> key;
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;             // kernel launches one replay stands for
+    int64_t used = 0;
+  };
+  bool graphs = true;
+  std::vector<StepGraph> gcache;
+  int64_t gclock = 0, gcaptures = 0, greplays = 0;
   bool stepped = false;               // a ugks_step has run (sweep records valid)
   int *work = nullptr;
   int *prev_status = nullptr, *n_orphan = nullptr, *blk_order = nullptr;
@@ -262,6 +278,7 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int fbf, int nwork, i
   d.dfs = c.take<char>(pair * (size_t)s.nc * s.nvp);
   d.Dbuf = c.take<char>(pair * (size_t)s.nc * s.nvp);
   d.fval = c.take<char>(2 * pair * (size_t)s.nf * s.nvp);
+  d.stepc = c.take<double>(4);
   d.TW = c.take<double>(4 * (size_t)s.nc); d.Fc = c.take<double>(4 * (size_t)s.nc);
   d.dW = c.take<double>(4 * (size_t)s.nc); d.Wp = c.take<double>(4 * (size_t)s.nc);
   d.mrec = c.take<char>(fp32 ? sizeof(float) * NMR32 * s.nmrec32 : sizeof(double) * NMR * (size_t)s.nc);
@@ -556,6 +573,13 @@ int shard_exchange(ugks_ctx *ctx, int which) {
   return UGKS_OK;
 }
 
+// The step size where the step's kernels read it (stream-ordered upload).
+int upload_step_size(ugks_ctx *ctx) {
+  const Dev &d = ctx->d;
+  double v[4] = {d.dt, d.idt, (double)d.idt_f, 0.0};
+  return launch_upload(const_cast<double *>(d.stepc), v, sizeof(v), ctx->st);
+}
+
 // Ghost states, W gradients, face reduction, face coefficients, per-cell
 // macro flux sum (Steps 1 / 3 up to the velocity-resolved flux).
 int flux_prep(ugks_ctx *ctx, int level_n) {
@@ -638,6 +662,129 @@ int do_connect(ugks_ctx *ctx, ugks_connect_stats *stats, bool initial, bool sync
   return r;
 }
 
+// Steps 1-8 of one physical step (after the motion and the assembly),
+// issued on the context's streams without any host synchronisation.
+int step_body(ugks_ctx *ctx, int n_inner) {
+  Dev &d = ctx->d;
+  cudaStream_t s = ctx->st;
+  int fp = ctx->fp32;
+  if (ctx->fresh_pending) do_interp(ctx, 1);
+  do_interp(ctx, 0);
+  // Steps 1-2: level-n flux, extensive level-n macro term, level-n cell record
+  int rx = flux_prep(ctx, 1);
+  if (rx) return rx;
+  { Prof p(ctx, UGKS_PROF_CELL); launch_cell_params(d, s, d.W, d.cparn, fp); }
+  ctx->launches += 1;
+  for (int it = 0; it < n_inner; ++it) {
+    if (it > 0) {
+      do_interp(ctx, 0);
+      if ((rx = flux_prep(ctx, 0))) return rx;   // Step 3
+    }
+    // Step 4 (macro LU-SGS) on the side stream, concurrently with the flux
+    // divergence of Step 3 on the main stream; Step 5 joins both
+    { Prof p(ctx, UGKS_PROF_MACRO_SWEEP); launch_macro_prep(d, s, fp); }
+    CK(cudaEventRecord(ctx->ev_flux, s));
+    CK(cudaStreamWaitEvent(ctx->side, ctx->ev_flux, 0));
+    { Prof p(ctx, UGKS_PROF_MACRO_SWEEP, ctx->side); launch_macro_sweep(d, ctx->side, ctx->max_nj, fp); }
+    CK(cudaEventRecord(ctx->ev_macro, ctx->side));
+    { Prof p(ctx, UGKS_PROF_RHS); launch_flux_tile(d, s, fp, ctx->face_tile); }              // Step 3
+    CK(cudaStreamWaitEvent(s, ctx->ev_macro, 0));
+    { Prof p(ctx, UGKS_PROF_RESIDUAL); launch_residual(d, s, it == 0, fp); }                 // Step 5
+    { Prof p(ctx, UGKS_PROF_MICRO_FWD); launch_wsweep(d, s, 0, ctx->work, ctx->nwork, ctx->sweep_nw, ctx->ns_fwd, ctx->sweep_vpt, fp, ctx->sweep_ql); }  // Step 6
+    { Prof p(ctx, UGKS_PROF_MICRO_BWD); launch_wsweep(d, s, 1, ctx->work, ctx->nwork, ctx->sweep_nw, ctx->ns_bwd, ctx->sweep_vpt, fp, ctx->sweep_ql); }
+    { Prof p(ctx, UGKS_PROF_MOMENTS); launch_moments(d, s, fp); }                          // Step 7
+    if (d.shard) {
+      if ((rx = shard_exchange(ctx, 1))) return rx;
+      { Prof p(ctx, UGKS_PROF_MOMENTS); launch_moments_finish(d, s); }
+      ctx->launches += 1;
+    }
+    ctx->launches += 8;
+  }
+  return UGKS_OK;
+}
+
+// What the captured kernels depend on beyond device memory: the device
+// struct they take by value and the launch configuration.
+std::vector<unsigned char> graph_key(const ugks_ctx *c, int n_inner) {
+  int cfg[] = {n_inner, c->fresh_pending ? 1 : 0, c->face_tile, c->sweep_vpt, c->ns_fwd, c->ns_bwd, c->sweep_nw,
+               c->sweep_ql, c->nwork, c->nsm, c->max_nj, c->fp32};
+  // (the step size is read from device memory; the bin count belongs to the
+  // assembly, which is not part of the step)
+  Dev d = c->d;
+  d.dt = d.idt = 0.0;
+  d.idt_f = 0.f;
+  d.nbins = 0;
+  std::vector<unsigned char> k(sizeof(Dev) + sizeof(cfg));
+  memcpy(k.data(), &d, sizeof(Dev));
+  memcpy(k.data() + sizeof(Dev), cfg, sizeof(cfg));
+  return k;
+}
+
+constexpr size_t kStepGraphs = 4;     // executable step graphs kept per context
+
+// The step through a CUDA graph: replay the cached graph of this key, or
+// capture the step and instantiate it (or update the least recently used
+// cached graph with it), then one graph launch on the context's stream.
+int step_graph(ugks_ctx *ctx, int n_inner) {
+  std::vector<unsigned char> key = graph_key(ctx, n_inner);
+  ugks_ctx::StepGraph *hit = nullptr;
+  for (auto &g : ctx->gcache)
+    if (g.key == key) hit = &g;
+  if (!hit) {
+    // captured on the context's private stream (the caller's may be the
+    // legacy default stream, which cannot be captured); launched on the
+    // caller's stream below
+    cudaGraph_t g = nullptr;
+    cudaStream_t user = ctx->st;
+    CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+    ctx->st = ctx->cap;
+    int64_t l0 = ctx->launches;
+    int r = step_body(ctx, n_inner);
+    ctx->st = user;
+    cudaError_t e = cudaStreamEndCapture(ctx->cap, &g);
+    int64_t nl = ctx->launches - l0;
+    ctx->launches = l0;
+    if (r != UGKS_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return r != UGKS_OK ? r : cuda_check(ctx, e, "step capture");
+    }
+    if (ctx->gcache.size() < kStepGraphs) {
+      ctx->gcache.emplace_back();
+      hit = &ctx->gcache.back();
+    } else {
+      hit = &ctx->gcache[0];
+      for (auto &c : ctx->gcache)
+        if (c.used < hit->used) hit = &c;
+      cudaGraphExecUpdateResultInfo info;
+      if (hit->exec && cudaGraphExecUpdate(hit->exec, g, &info) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(hit->exec);
+        hit->exec = nullptr;
+      }
+    }
+    if (!hit->exec) {
+      cudaError_t ie = cudaGraphInstantiate(&hit->exec, g, 0);
+      if (ie != cudaSuccess) {
+        cudaGraphDestroy(g);
+        hit->exec = nullptr;
+        hit->key.clear();
+        return cuda_check(ctx, ie, "graph instantiate");
+      }
+    }
+    cudaGraphDestroy(g);
+    hit->key.swap(key);
+    hit->launches = nl;
+    ++ctx->gcaptures;
+  } else {
+    ++ctx->greplays;
+  }
+  hit->used = ++ctx->gclock;
+  CK(cudaGraphLaunch(hit->exec, ctx->st));
+  ctx->launches += hit->launches;
+  return UGKS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -666,6 +813,7 @@ int ugks_create(const ugks_params *p, void *workspace, size_t bytes, void *strea
   c->st = (cudaStream_t)stream;
   c->fp32 = p->precision != UGKS_FP64;
   if (const char *e = getenv("UGKS_DEBUG_SYNC")) c->debug_sync = atoi(e) != 0;
+  if (const char *e = getenv("UGKS_NO_GRAPH")) c->graphs = atoi(e) == 0;
   c->fbf = p->precision == UGKS_BF16F;
   memset(&c->d, 0, sizeof(c->d));
   int prio_lo = 0, prio_hi = 0;
@@ -673,6 +821,7 @@ int ugks_create(const ugks_params *p, void *workspace, size_t bytes, void *strea
   // the macro sweep is a latency-bound wavefront on a few SMs: give its
   // stream the highest priority so its CTAs are placed as soon as a slot frees
   if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_flux, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_macro, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
@@ -686,10 +835,14 @@ int ugks_create(const ugks_params *p, void *workspace, size_t bytes, void *strea
 int ugks_destroy(ugks_ctx *ctx) {
   if (ctx) {
     if (ctx->side) cudaStreamSynchronize(ctx->side);
+    if (ctx->st) cudaStreamSynchronize(ctx->st);
+    for (auto &g : ctx->gcache)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     if (ctx->ev_flux) cudaEventDestroy(ctx->ev_flux);
     if (ctx->ev_macro) cudaEventDestroy(ctx->ev_macro);
     if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
   }
   delete ctx;
   return UGKS_OK;
@@ -791,7 +944,9 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
   d.nvx = ctx->p.nvx; d.nvy = ctx->p.nvy;
   d.Kint = ctx->p.K; d.Keff = 1 + ctx->p.K;
   d.Pr = ctx->p.Pr; d.omega = ctx->p.omega; d.mu_ref = ctx->p.mu_ref;
-  d.cfl_s = ctx->p.cfl_s; d.cfl_pseudo = ctx->p.cfl_pseudo; d.dt = 1.0;
+  d.cfl_s = ctx->p.cfl_s; d.cfl_pseudo = ctx->p.cfl_pseudo;
+  d.dt = 1.0; d.idt = 1.0; d.idt_f = 1.0f;
+  ctx->launches += upload_step_size(ctx);
   d.wait_polls = kWaitPolls;
   d.vbox[0] = ctx->p.vx_min; d.vbox[1] = ctx->p.vx_max; d.vbox[2] = ctx->p.vy_min; d.vbox[3] = ctx->p.vy_max;
   {
@@ -974,6 +1129,7 @@ int ugks_move_mesh(ugks_ctx *ctx, double t_new, const double *affine) {
   d.dt = t_new - ctx->t;
   d.idt = 1.0 / d.dt;
   d.idt_f = (float)d.idt;
+  ctx->launches += upload_step_size(ctx);
   ctx->t_new = t_new;
   {
     Prof p(ctx, UGKS_PROF_GEOMETRY);
@@ -1000,45 +1156,29 @@ int ugks_step(ugks_ctx *ctx, double dt, int n_inner) {
   if (n_inner < 1) return fail(ctx, UGKS_ERR_ARG, "n_inner must be >= 1");
   Dev &d = ctx->d;
   if (fabs(dt - d.dt) > 1e-12 * fabs(d.dt)) return fail(ctx, UGKS_ERR_ARG, "dt differs from the move's step");
-  cudaStream_t s = ctx->st;
-  int fp = ctx->fp32;
-  if (ctx->fresh_pending) do_interp(ctx, 1);
-  do_interp(ctx, 0);
-  // Steps 1-2: level-n flux, extensive level-n macro term, level-n cell record
-  int rx = flux_prep(ctx, 1);
+  // graphs need a step free of host work: not while profiling or checking
+  // each launch, and not on a velocity shard (its exchange runs on the host)
+  bool graph = ctx->graphs && !ctx->prof_on && !ctx->debug_sync && !d.shard;
+  int rx = graph ? step_graph(ctx, n_inner) : step_body(ctx, n_inner);
   if (rx) return rx;
-  { Prof p(ctx, UGKS_PROF_CELL); launch_cell_params(d, s, d.W, d.cparn, fp); }
-  ctx->launches += 1;
-  for (int it = 0; it < n_inner; ++it) {
-    if (it > 0) {
-      do_interp(ctx, 0);
-      if ((rx = flux_prep(ctx, 0))) return rx;   // Step 3
-    }
-    // Step 4 (macro LU-SGS) on the side stream, concurrently with the flux
-    // divergence of Step 3 on the main stream; Step 5 joins both
-    { Prof p(ctx, UGKS_PROF_MACRO_SWEEP); launch_macro_prep(d, s, fp); }
-    CK(cudaEventRecord(ctx->ev_flux, s));
-    CK(cudaStreamWaitEvent(ctx->side, ctx->ev_flux, 0));
-    { Prof p(ctx, UGKS_PROF_MACRO_SWEEP, ctx->side); launch_macro_sweep(d, ctx->side, ctx->max_nj, fp); }
-    CK(cudaEventRecord(ctx->ev_macro, ctx->side));
-    { Prof p(ctx, UGKS_PROF_RHS); launch_flux_tile(d, s, fp, ctx->face_tile); }              // Step 3
-    CK(cudaStreamWaitEvent(s, ctx->ev_macro, 0));
-    { Prof p(ctx, UGKS_PROF_RESIDUAL); launch_residual(d, s, it == 0, fp); }                 // Step 5
-    { Prof p(ctx, UGKS_PROF_MICRO_FWD); launch_wsweep(d, s, 0, ctx->work, ctx->nwork, ctx->sweep_nw, ctx->ns_fwd, ctx->sweep_vpt, fp, ctx->sweep_ql); }  // Step 6
-    { Prof p(ctx, UGKS_PROF_MICRO_BWD); launch_wsweep(d, s, 1, ctx->work, ctx->nwork, ctx->sweep_nw, ctx->ns_bwd, ctx->sweep_vpt, fp, ctx->sweep_ql); }
-    { Prof p(ctx, UGKS_PROF_MOMENTS); launch_moments(d, s, fp); }                          // Step 7
-    if (d.shard) {
-      if ((rx = shard_exchange(ctx, 1))) return rx;
-      { Prof p(ctx, UGKS_PROF_MOMENTS); launch_moments_finish(d, s); }
-      ctx->launches += 1;
-    }
-    ctx->launches += 8;
-  }
   ctx->fresh_pending = false;
   ctx->stepped = true;
   ctx->t = ctx->t_new;
   ctx->moved = false;
   return launch_status(ctx);
+}
+
+int ugks_set_graphs(ugks_ctx *ctx, int on) {
+  if (!ctx) return UGKS_ERR_ARG;
+  ctx->graphs = on != 0;
+  return UGKS_OK;
+}
+
+int ugks_graph_stats(const ugks_ctx *ctx, int64_t *captures, int64_t *replays) {
+  if (!ctx) return UGKS_ERR_ARG;
+  if (captures) *captures = ctx->gcaptures;
+  if (replays) *replays = ctx->greplays;
+  return UGKS_OK;
 }
 
 int ugks_advance_batch(ugks_ctx *const *ctx, int n, const double *t_new, const double *const *affine,

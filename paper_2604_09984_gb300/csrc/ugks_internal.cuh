@@ -87,6 +87,8 @@ struct Dev {
   void *Tn, *dfs;            // nc*nvp pairs: level-n term, forward-sweep result
   void *Dbuf;                // nc*nvp pairs: flux divergence of the inner iteration
   void *fval;                // nf*nvp 4-vectors: upwind face value (h, b) and w.grad f (h, b) of the face pass
+  const double *stepc;       // [4]: dt, 1/dt, (float)(1/dt) of the pending step, on the device (the step's
+                             // kernels read it there, so a captured step graph stays valid when dt changes)
   double *TW;                // nc*4 extensive level-n macro term
   double *Fc;                // nc*4 macro flux divergence of the last flux
   double *dW;                // nc*4 macro increment

@@ -613,7 +613,7 @@ __global__ void k_cell_macro(Dev d, int level_n) {
   }
   for (int m = 0; m < 4; ++m) d.Fc[4 * c + m] = F[m];
   if (level_n)
-    for (int m = 0; m < 4; ++m) d.TW[4 * c + m] = d.vol_old[c] / d.dt * d.W[4 * c + m] - 0.5 * F[m];
+    for (int m = 0; m < 4; ++m) d.TW[4 * c + m] = d.vol_old[c] / d.stepc[0] * d.W[4 * c + m] - 0.5 * F[m];
 }
 
 // Cell parameter record (prim, q, 1/tau) from W and q, and its Shakhov
@@ -722,7 +722,7 @@ template <typename MT> __global__ void k_macro_prep(Dev d, MT *rec) {
   int mask = d.cmask[c];
   if (sizeof(MT) == 4) o[M32_MASK] = __int_as_float(mask);
   if (!(mask & 1)) return;
-  double vol = d.vol_new[c], idt = 1.0 / d.dt;
+  double vol = d.vol_new[c], idt = 1.0 / d.stepc[0];
   for (int m = 0; m < 4; ++m)
     o[L::R + m] = (MT)(d.TW[4 * c + m] - vol * idt * d.W[4 * c + m] - 0.5 * d.Fc[4 * c + m]);
   double diag = vol * (d.cfl_s / (d.cfl_pseudo * d.dts[c]) + idt);
@@ -1032,7 +1032,7 @@ template <typename T> __global__ void k_macro_post(Dev d) {
   o[CP_RHO] = p.rho; o[CP_UX] = p.ux; o[CP_UY] = p.uy; o[CP_LAM] = p.lam;
   o[CP_QX] = d.q[2 * c]; o[CP_QY] = d.q[2 * c + 1];
   o[CP_ITAU] = 1.0 / collision_time(p.rho, p.lam, d.mu_ref, d.omega);
-  o[CP_DBASE] = d.vol_new[c] * (d.cfl_s / (d.cfl_pseudo * d.dts[c]) + 1.0 / d.dt + 0.5 * o[CP_ITAU]);
+  o[CP_DBASE] = d.vol_new[c] * (d.cfl_s / (d.cfl_pseudo * d.dts[c]) + 1.0 / d.stepc[0] + 0.5 * o[CP_ITAU]);
   sr[SR_DBASE] = (T)o[CP_DBASE];
   write_shrec<T>(d, o, d.vol_new[c], reinterpret_cast<T *>(d.shp) + (size_t)NSH * c);
 }

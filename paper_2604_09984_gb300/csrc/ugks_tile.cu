@@ -694,7 +694,7 @@ template <typename T, int FB> __global__ void k_residual(Dev d, int first_iter) 
   const T *cp = reinterpret_cast<const T *>(d.shp) + (size_t)NSH * c;
   T itau = cp[SH_ITAU];
   T vol1 = cp[SH_VOL];
-  T idt = sizeof(T) == 4 ? (T)d.idt_f : (T)d.idt;
+  T idt = sizeof(T) == 4 ? (T)(float)d.stepc[2] : (T)d.stepc[1];
   const T *cn = reinterpret_cast<const T *>(d.shn) + (size_t)NSH * c;
   T2 fv[2], D[2], tn[2];
 #pragma unroll

@@ -59,6 +59,8 @@ SYMBOLS = {
     "ugks_move_mesh": (c_int, [c_void_p, c_double, POINTER(c_double)]),
     "ugks_overset_connect": (c_int, [c_void_p, POINTER(ConnectStats)]),
     "ugks_step": (c_int, [c_void_p, c_double, c_int]),
+    "ugks_set_graphs": (c_int, [c_void_p, c_int]),
+    "ugks_graph_stats": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int64)]),
     "ugks_advance_batch": (c_int, [POINTER(c_void_p), c_int, POINTER(c_double), POINTER(POINTER(c_double)),
                                    c_int, POINTER(c_int)]),
     "ugks_moments": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -341,6 +343,16 @@ class Solver:
 
     def launch_count(self):
         return int(self.lib.ugks_launch_count(self.ctx))
+
+    def set_graphs(self, on: bool):
+        """CUDA-graph path of ugks_step on or off (ugks_set_graphs)."""
+        self._check(self.lib.ugks_set_graphs(self.ctx, int(bool(on))))
+
+    def graph_stats(self):
+        """(captures, replays) of the step's CUDA graphs (ugks_graph_stats)."""
+        c, r = c_int64(), c_int64()
+        self._check(self.lib.ugks_graph_stats(self.ctx, ctypes.byref(c), ctypes.byref(r)))
+        return int(c.value), int(r.value)
 
     def set_exchange(self, fn):
         """Exchange of a velocity-sharded context (ugks_shard_set_exchange):

@@ -1,0 +1,50 @@
+"""CUDA graphs of ugks_step (GPU).  A context that captures its step into a
+graph and replays it equals, bit for bit, a context that launches every
+kernel directly, over physical steps of an overset MEMS case with a moving
+body (a step after an assembly that uncovered cells runs one more
+interpolation and has a graph of its own), on the FP32 and FP64 paths.  Later steps
+are replays; a change of the wait limit (part of the device struct the
+kernels take by value) makes a new capture, whose replay still matches."""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+from paper_2604_09984_gb300 import ugks as U  # noqa: E402
+from paper_2604_09984_gb300 import workloads as wl  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    if not os.path.exists(U.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    U.load()
+
+
+@pytest.mark.parametrize("prec", [U.FP32, U.FP64])
+def test_graph_replay_matches_direct_launches(prec):
+    case = wl.mems(nbi=48, nbj=24, noi=32, noj=12, nv=8, stretch=1.15, n_inner=2)
+    prim = wl.random_prim(case, 41, amp_rho=0.05, amp_u=0.05, amp_T=0.05)
+    g = U.Solver(case, prec, prim=prim)
+    n = U.Solver(case, prec, prim=prim)
+    n.set_graphs(False)
+    for step in range(6):
+        if step == 3:
+            for s in (g, n):
+                s.set_wait_limit(1 << 20)     # a new by-value argument: new capture
+        for s in (g, n):
+            s.advance()
+    captures, replays = g.graph_stats()
+    assert replays >= 2 and captures >= 2
+    assert captures + replays == 6
+    assert n.graph_stats() == (0, 0)
+    assert g.launch_count() == n.launch_count()
+    for a, b in zip(g.moments(), n.moments()):
+        assert np.array_equal(a, b)
+    assert torch.equal(g.get_state()[0], n.get_state()[0])

@@ -357,13 +357,14 @@ template <typename T> __global__ void k_face_scalar(Dev d) {
       q0y = 0.5 * d.q[2 * L + 1];
       dts = d.dts[L];
     }
-    double tx = xRx - xLx, ty = xRy - xLy, t2 = tx * tx + ty * ty;
+    double tx = xRx - xLx, ty = xRy - xLy, it2 = 1.0 / (tx * tx + ty * ty);
+    double ex = tx * it2, ey = ty * it2;
     for (int m = 0; m < 4; ++m) {
       W0[m] = fs[FS_W0 + m];
       double avx = 0.5 * (dL[2 * m] + dR[2 * m]), avy = 0.5 * (dL[2 * m + 1] + dR[2 * m + 1]);
       double jump = (WR[m] - WL[m]) - (avx * tx + avy * ty);
-      gx[m] = avx + jump * (tx / t2);
-      gy[m] = avy + jump * (ty / t2);
+      gx[m] = avx + jump * ex;
+      gy[m] = avy + jump * ey;
     }
   }
   // face state, slopes, collision time and time integrals in FP64 on every
@@ -373,10 +374,11 @@ template <typename T> __global__ void k_face_scalar(Dev d) {
   RT W0r[4], gxr[4], gyr[4];
   for (int m = 0; m < 4; ++m) { W0r[m] = (RT)W0[m]; gxr[m] = (RT)gx[m]; gyr[m] = (RT)gy[m]; }
   PrimR<RT> p0 = primitive_r<RT>(W0r, d.Keff);
+  const SlopeInv<RT> inv = slope_inv<RT>(p0, d.Keff);
   RT ax[4], ay[4], At[4];
-  micro_slope_r<RT>(p0, d.Keff, gxr, ax);
-  micro_slope_r<RT>(p0, d.Keff, gyr, ay);
-  time_slope_r<RT>(p0, d.Keff, ax, ay, gxr, gyr, (RT)ufx, (RT)ufy, At);
+  micro_slope_r<RT>(p0, d.Keff, inv, gxr, ax);
+  micro_slope_r<RT>(p0, d.Keff, inv, gyr, ay);
+  time_slope_r<RT>(p0, d.Keff, inv, ax, ay, gxr, gyr, (RT)ufx, (RT)ufy, At);
   RT tau = collision_time_r<RT>(p0.rho, p0.lam, (RT)d.mu_ref, (RT)d.omega);
   RT dtsr = (RT)dts;
   RT qi[5];
@@ -386,11 +388,12 @@ template <typename T> __global__ void k_face_scalar(Dev d) {
   par[FP_RHO] = p0.rho; par[FP_UX] = p0.ux; par[FP_UY] = p0.uy; par[FP_LAM] = p0.lam;
   par[FP_QX] = (RT)q0x; par[FP_QY] = (RT)q0y;
   for (int m = 0; m < 4; ++m) { par[FP_AX + m] = ax[m]; par[FP_AY + m] = ay[m]; par[FP_AT + m] = At[m]; }
-  for (int m = 0; m < 5; ++m) par[FP_Q1 + m] = qi[m] / dtsr;
+  const RT idts = RT(1) / dtsr;
+  for (int m = 0; m < 5; ++m) par[FP_Q1 + m] = qi[m] * idts;
   par[FP_UFX] = (RT)ufx; par[FP_UFY] = (RT)ufy;
-  par[FP_PREF] = RT(4) * (RT(1) - (RT)d.Pr) * p0.lam * p0.lam / (RT(5) * p0.rho);
+  par[FP_PREF] = RT(0.8) * (RT(1) - (RT)d.Pr) * p0.lam * p0.lam * inv.irho;
   par[FP_HPRE] = p0.rho * p0.lam * RT(M_1_PI);
-  par[FP_IL] = RT(1) / (RT(2) * p0.lam);
+  par[FP_IL] = inv.il;
   par[FP_EH] = RT(0.5) * RT(d.Keff) * par[FP_IL];
   par[FP_EB] = RT(0.5) * (RT(d.Keff) + RT(2)) * par[FP_IL];
   par[FP_LAMW] = wall ? (RT)(1.0 / (2.0 * d.face_Tw[fid])) : RT(0);

@@ -38,8 +38,9 @@ typedef PrimR<double> Prim;
 template <typename R> UG_HD PrimR<R> primitive_r(const R W[4], int Keff) {
   PrimR<R> p;
   p.rho = W[0];
-  p.ux = W[1] / W[0];
-  p.uy = W[2] / W[0];
+  R irho = R(1) / W[0];
+  p.ux = W[1] * irho;
+  p.uy = W[2] * irho;
   R eint = W[3] - R(0.5) * p.rho * (p.ux * p.ux + p.uy * p.uy);
   p.lam = (R(2) + R(Keff)) * p.rho / (R(4) * eint);
   return p;
@@ -183,16 +184,24 @@ UG_HD void time_integrals(double dts, double tau, double q[5]) { time_integrals_
 //   a4 = 8 lam^2/N [dW4/rho - |V|^2 dW1/(2 rho) - (Vx b2 + Vy b3)/(2 lam)
 //                    - N dW1/(4 lam rho)],
 //   b1 = dW1/rho - a4 N/(4 lam), then back to (a1..a4).
+// The reciprocals a face's slope solves share (1/rho, 1/(2 lam), 1/N), so
+// the three solves of a face (two micro slopes, the time slope) divide once.
+template <typename R> struct SlopeInv { R irho, il, iN; };
+template <typename R> UG_HD SlopeInv<R> slope_inv(const PrimR<R> &g, int Keff) {
+  return {R(1) / g.rho, R(1) / (R(2) * g.lam), R(1) / (R(2) + R(Keff))};
+}
+
 template <typename R>
-UG_HD void micro_slope_r(const PrimR<R> &g, int Keff, const R dW[4], R a[4]) {
+UG_HD void micro_slope_r(const PrimR<R> &g, int Keff, const SlopeInv<R> &v, const R dW[4], R a[4]) {
   R N = R(2) + R(Keff);
-  R lam = g.lam, rho = g.rho, U = g.ux, V = g.uy;
-  R d1 = dW[0] / rho, d2 = dW[1] / rho, d3 = dW[2] / rho, d4 = dW[3] / rho;
+  R lam = g.lam, U = g.ux, V = g.uy;
+  R d1 = dW[0] * v.irho, d2 = dW[1] * v.irho, d3 = dW[2] * v.irho, d4 = dW[3] * v.irho;
   R b2 = R(2) * lam * (d2 - U * d1);
   R b3 = R(2) * lam * (d3 - V * d1);
-  R a4 = R(8) * lam * lam / N *
-         (d4 - R(0.5) * (U * U + V * V) * d1 - (U * b2 + V * b3) / (R(2) * lam) - N * d1 / (R(4) * lam));
-  R b1 = d1 - a4 * N / (R(4) * lam);
+  // 1/(4 lam) = il / 2
+  R a4 = R(8) * lam * lam * v.iN *
+         (d4 - R(0.5) * (U * U + V * V) * d1 - (U * b2 + V * b3) * v.il - N * d1 * (R(0.5) * v.il));
+  R b1 = d1 - a4 * N * (R(0.5) * v.il);
   R a2 = b2 - a4 * U;
   R a3 = b3 - a4 * V;
   a[0] = b1 - a2 * U - a3 * V - R(0.5) * a4 * (U * U + V * V);
@@ -200,17 +209,14 @@ UG_HD void micro_slope_r(const PrimR<R> &g, int Keff, const R dW[4], R a[4]) {
   a[2] = a3;
   a[3] = a4;
 }
-UG_HD void micro_slope(const Prim &g, int Keff, const double dW[4], double a[4]) {
-  micro_slope_r<double>(g, Keff, dW, a);
-}
 
 // G = int Psi u_dir (a.Psi) g / rho  (dir 0: u = vx, dir 1: u = vy), closed
 // form from the Gaussian moments E[c_x^2] = s2, E[c_x^2 Z] = (N+2) s2^2,
 // E[Z] = N s2, E[Z^2] = N (N+2) s2^2, s2 = 1/(2 lam), Z = c^2 + xi^2.
 template <typename R>
-UG_HD void flux_moment_r(const PrimR<R> &g, int Keff, const R a[4], int dir, R G[4]) {
+UG_HD void flux_moment_r(const PrimR<R> &g, int Keff, R il, const R a[4], int dir, R G[4]) {
   R N = R(2) + R(Keff);
-  R s2 = R(1) / (R(2) * g.lam);
+  R s2 = il;                      // 1/(2 lam)
   R U = g.ux, V = g.uy, U2 = U * U + V * V;
   R b2 = a[1] + a[3] * U;
   R b3 = a[2] + a[3] * V;
@@ -237,19 +243,14 @@ UG_HD void flux_moment_r(const PrimR<R> &g, int Keff, const R a[4], int dir, R G
 // Time slope A from compatibility int Psi [(ax.Psi) wx + (ay.Psi) wy + A.Psi] g
 // = 0 with w = v - U_f:  M A = -(rho Gx + rho Gy - Ufx dWx - Ufy dWy).
 template <typename R>
-UG_HD void time_slope_r(const PrimR<R> &g, int Keff, const R ax[4], const R ay[4], const R dWx[4],
-                        const R dWy[4], R Ufx, R Ufy, R A[4]) {
+UG_HD void time_slope_r(const PrimR<R> &g, int Keff, const SlopeInv<R> &v, const R ax[4], const R ay[4],
+                        const R dWx[4], const R dWy[4], R Ufx, R Ufy, R A[4]) {
   R Gx[4], Gy[4], r[4];
-  flux_moment_r<R>(g, Keff, ax, 0, Gx);
-  flux_moment_r<R>(g, Keff, ay, 1, Gy);
+  flux_moment_r<R>(g, Keff, v.il, ax, 0, Gx);
+  flux_moment_r<R>(g, Keff, v.il, ay, 1, Gy);
   for (int m = 0; m < 4; ++m)
     r[m] = -(g.rho * Gx[m] + g.rho * Gy[m] - Ufx * dWx[m] - Ufy * dWy[m]);
-  micro_slope_r<R>(g, Keff, r, A);
-}
-UG_HD void time_slope(const Prim &g, int Keff, const double ax[4], const double ay[4],
-                      const double dWx[4], const double dWy[4], double Ufx, double Ufy,
-                      double A[4]) {
-  time_slope_r<double>(g, Keff, ax, ay, dWx, dWy, Ufx, Ufy, A);
+  micro_slope_r<R>(g, Keff, v, r, A);
 }
 
 // Time-integrated interface distribution / dts for one velocity (Eq.

@@ -63,8 +63,8 @@ struct ugks_ctx {
   std::string err;
   int64_t launches = 0;
   std::vector<double> h_affine;
-  bool fresh_pending = false;
-  std::vector<int> h_wall_faces;      // staging of the wall-face list upload         // cells uncovered by the last assembly await their first values
+  bool fresh_pending = false;         // cells uncovered by the last assembly await their first values
+  std::vector<int> h_wall_faces;      // staging of the wall-face list upload
   std::vector<double> ref_bbox, h_bin_geo;   // per block reference bbox; bin boxes
   std::vector<int> h_bin_dim;
   // per-kernel-group CUDA-event timing (ugks_profile_*)
@@ -235,6 +235,8 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int fbf, int nwork, i
   d.vxf = c.take<float>(s.nvp); d.vyf = c.take<float>(s.nvp); d.wf = c.take<float>(s.nvp);
   d.wx1f = c.take<float>((size_t)s.nvx); d.wy1f = c.take<float>((size_t)s.nvy);
   d.vy1f = c.take<float>((size_t)s.nvy);
+  d.vx1 = c.take<double>((size_t)s.nvx); d.vy1 = c.take<double>((size_t)s.nvy);
+  d.wx1 = c.take<double>((size_t)s.nvx); d.wy1 = c.take<double>((size_t)s.nvy);
   d.vxa = c.take<double>(s.nvp_all); d.vya = c.take<double>(s.nvp_all); d.wa = c.take<double>(s.nvp_all);
   d.vxaf = c.take<float>(s.nvp_all); d.vyaf = c.take<float>(s.nvp_all); d.waf = c.take<float>(s.nvp_all);
   d.msum = c.take<double>(6 * (size_t)s.nc);
@@ -1040,6 +1042,20 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
     for (int iy = 0; iy < ctx->p.nvy; ++iy) wy1[iy] = (float)(hy * ((iy == 0 || iy == ctx->p.nvy - 1) ? 0.5 : 1.0));
     if ((r = up(ctx, (void *)d.wx1f, wx1))) return r;
     if ((r = up(ctx, (void *)d.wy1f, wy1))) return r;
+    // and in FP64 with the nodes (the FP64 path's separable velocity sums)
+    std::vector<double> vx1d(ctx->p.nvx), vy1d(ctx->p.nvy), wx1d(ctx->p.nvx), wy1d(ctx->p.nvy);
+    for (int ix = 0; ix < ctx->p.nvx; ++ix) {
+      vx1d[ix] = vxa[ix];
+      wx1d[ix] = hx * ((ix == 0 || ix == ctx->p.nvx - 1) ? 0.5 : 1.0);
+    }
+    for (int iy = 0; iy < ctx->p.nvy; ++iy) {
+      vy1d[iy] = vya[(size_t)iy * ctx->p.nvx];
+      wy1d[iy] = hy * ((iy == 0 || iy == ctx->p.nvy - 1) ? 0.5 : 1.0);
+    }
+    if ((r = up(ctx, (void *)d.vx1, vx1d))) return r;
+    if ((r = up(ctx, (void *)d.vy1, vy1d))) return r;
+    if ((r = up(ctx, (void *)d.wx1, wx1d))) return r;
+    if ((r = up(ctx, (void *)d.wy1, wy1d))) return r;
   }
   if ((r = up(ctx, (void *)d.cell_nodes, T.cell_nodes))) return r;
   if ((r = up(ctx, (void *)d.cell_faces, T.cell_faces))) return r;

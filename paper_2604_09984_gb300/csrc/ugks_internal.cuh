@@ -40,6 +40,7 @@ struct Dev {
   int nvx, nvy;              // tensor grid: k = iy nvx + ix, w_k = wy1(iy) wx1(ix); nvy of the whole grid
   const float *wx1f, *wy1f;  // 1D trapezoid weights (whole grid)
   const float *vy1f;         // 1D y nodes of the whole grid
+  const double *vx1, *vy1, *wx1, *wy1;   // 1D nodes and trapezoid weights of the whole grid (FP64)
   // velocity sharding: this context holds the rows iy0 <= iy < iy0 + nv / nvx
   // of the grid; the arrays above (vx, vy, w and copies) are its own rows, the
   // ones below the whole grid (the same arrays when not sharded)

@@ -431,24 +431,42 @@ template <typename T> __global__ void k_face_scalar(Dev d) {
 // rounding) sum_ab coef_ab Mx_a My_b with the 1D moments
 // Mx_a = sum_ix wx cx^a Ex(cx), My_b likewise: O(nvx + nvy) work per face
 // instead of O(nvx nvy).  One warp per face; out (all lanes): 4 sums.
-template <int GS>
-__device__ __forceinline__ void face_eq_flux_separable(const Dev &d, const float *P, float snx, float sny,
-                                                       float sun, int lane, float out[4]) {
-  float ux = P[FP_UX], uy = P[FP_UY], lam = P[FP_LAM];
+// 1D grids of the separable sums in the arithmetic type
+template <typename R> struct Grid1;
+template <> struct Grid1<float> {
+  __device__ static float vx(const Dev &d, int i) { return d.vxf[i]; }
+  __device__ static float vy(const Dev &d, int i) { return d.vy1f[i]; }
+  __device__ static float wx(const Dev &d, int i) { return d.wx1f[i]; }
+  __device__ static float wy(const Dev &d, int i) { return d.wy1f[i]; }
+  __device__ static float ex(float x) { return __expf(x); }
+};
+template <> struct Grid1<double> {
+  __device__ static double vx(const Dev &d, int i) { return d.vx1[i]; }
+  __device__ static double vy(const Dev &d, int i) { return d.vy1[i]; }
+  __device__ static double wx(const Dev &d, int i) { return d.wx1[i]; }
+  __device__ static double wy(const Dev &d, int i) { return d.wy1[i]; }
+  __device__ static double ex(double x) { return exp(x); }
+};
+
+template <typename R, int GS>
+__device__ __forceinline__ void face_eq_flux_separable(const Dev &d, const R *P, R snx, R sny, R sun, int lane,
+                                                       R out[4]) {
+  typedef Grid1<R> G;
+  R ux = P[FP_UX], uy = P[FP_UY], lam = P[FP_LAM];
   // 1D moments: lane of the face's GS-lane group = grid index, a = 0..6 (x)
   // and b = 0..6 (y); every lane of the warp takes part in the shuffles
-  float mx[7], my[7];
+  R mx[7], my[7];
 #pragma unroll
-  for (int a = 0; a < 7; ++a) { mx[a] = 0.f; my[a] = 0.f; }
+  for (int a = 0; a < 7; ++a) { mx[a] = R(0); my[a] = R(0); }
   for (int ix = lane; ix < d.nvx; ix += GS) {
-    float cx = d.vxf[ix] - ux;
-    float e = d.wx1f[ix] * __expf(-lam * cx * cx), p = e;
+    R cx = G::vx(d, ix) - ux;
+    R e = G::wx(d, ix) * G::ex(-lam * cx * cx), p = e;
 #pragma unroll
     for (int a = 0; a < 7; ++a) { mx[a] += p; p *= cx; }
   }
   for (int iy = lane; iy < d.nvy; iy += GS) {     // the whole grid (also when sharded)
-    float cy = d.vy1f[iy] - uy;
-    float e = d.wy1f[iy] * __expf(-lam * cy * cy), p = e;
+    R cy = G::vy(d, iy) - uy;
+    R e = G::wy(d, iy) * G::ex(-lam * cy * cy), p = e;
 #pragma unroll
     for (int a = 0; a < 7; ++a) { my[a] += p; p *= cy; }
   }
@@ -459,17 +477,17 @@ __device__ __forceinline__ void face_eq_flux_separable(const Dev &d, const float
       mx[a] += __shfl_xor_sync(0xffffffffu, mx[a], o);
       my[a] += __shfl_xor_sync(0xffffffffu, my[a], o);
     }
-  Poly2<3> ih, ib;
-  interface_polys<float>(P, (float)d.Keff, (float)d.Kint, ih, ib);
-  Poly2<1> vxp = p2_lin(ux, 1.f, 0.f), vyp = p2_lin(uy, 0.f, 1.f);
-  Poly2<2> v2 = p2_axpby(1.f, p2_mul(vxp, vxp), 1.f, p2_mul(vyp, vyp));
-  Poly2<1> ws = p2_lin(snx * ux + sny * uy - sun, snx, sny);
-  Poly2<4> m0 = p2_mul(ws, ih);
-  float hpre = P[FP_HPRE];
+  Poly2<3, R> ih, ib;
+  interface_polys<R>(P, (R)d.Keff, (R)d.Kint, ih, ib);
+  Poly2<1, R> vxp = p2_lin<R>(ux, R(1), R(0)), vyp = p2_lin<R>(uy, R(0), R(1));
+  Poly2<2, R> v2 = p2_axpby(R(1), p2_mul(vxp, vxp), R(1), p2_mul(vyp, vyp));
+  Poly2<1, R> ws = p2_lin<R>(snx * ux + sny * uy - sun, snx, sny);
+  Poly2<4, R> m0 = p2_mul(ws, ih);
+  R hpre = P[FP_HPRE];
   out[0] = hpre * p2_sum(m0, mx, my);
   out[1] = hpre * p2_sum(p2_mul(m0, vxp), mx, my);
   out[2] = hpre * p2_sum(p2_mul(m0, vyp), mx, my);
-  Poly2<5> e3 = p2_axpby(0.5f, ib, 0.5f, p2_mul(v2, ih));
+  Poly2<5, R> e3 = p2_axpby(R(0.5), ib, R(0.5), p2_mul(v2, ih));
   out[3] = hpre * p2_sum(p2_mul(ws, e3), mx, my);
 }
 
@@ -558,12 +576,12 @@ template <typename T> __global__ void __launch_bounds__(256, 2) k_face_coef(Dev 
   }
 }
 
-// FP32 face coefficients of the non-wall faces: FCG lanes per face, the
+// Face coefficients of the non-wall faces: FCG lanes per face, the
 // equilibrium part of the macro flux from 1D velocity moments (exact
 // separable rewrite of the tensor-grid sum); faces outside the field get
 // zero flux.
 constexpr int FCG = 8;
-__global__ void __launch_bounds__(256) k_face_coef_sep(Dev d) {
+template <typename T> __global__ void __launch_bounds__(256) k_face_coef_sep(Dev d) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int fid = t / FCG, sub = t % FCG;
   bool in = fid < d.nf;
@@ -575,21 +593,21 @@ __global__ void __launch_bounds__(256) k_face_coef_sep(Dev d) {
   }
   bool act = need && kind != BC_WALL;
   if (!__any_sync(0xffffffffu, act)) return;      // warp-uniform
-  __align__(16) float parT[NFP];
+  __align__(16) T parT[NFP];
   if (act) {
-    load_rec<float, NFP>(reinterpret_cast<const float *>(d.fparT) + (size_t)NFP * fid, parT);
+    load_rec<T, NFP>(reinterpret_cast<const T *>(d.fparT) + (size_t)NFP * fid, parT);
   } else {
 #pragma unroll
-    for (int q = 0; q < NFP; ++q) parT[q] = 0.f;
+    for (int q = 0; q < NFP; ++q) parT[q] = T(0);
   }
-  float o[4];
-  face_eq_flux_separable<FCG>(d, parT, parT[FP_SNX], parT[FP_SNY], parT[FP_SUN], sub, o);
+  T o[4];
+  face_eq_flux_separable<T, FCG>(d, parT, parT[FP_SNX], parT[FP_SNY], parT[FP_SUN], sub, o);
   if (act) {
     // the cubics of the interface distribution for the flux pass (lane sub
     // of the face's group writes coefficients sub, sub + FCG, ...)
-    Poly2<3> ih, ib;
-    interface_polys<float>(parT, (float)d.Keff, (float)d.Kint, ih, ib);
-    float *PT = reinterpret_cast<float *>(d.fparT) + (size_t)NFP * fid;
+    Poly2<3, T> ih, ib;
+    interface_polys<T>(parT, (T)d.Keff, (T)d.Kint, ih, ib);
+    T *PT = reinterpret_cast<T *>(d.fparT) + (size_t)NFP * fid;
 #pragma unroll
     for (int m = 0; m < 20; ++m)
       if (m % FCG == sub) PT[FP_IH + m] = m < 10 ? ih.c[m] : ib.c[m - 10];
@@ -597,8 +615,8 @@ __global__ void __launch_bounds__(256) k_face_coef_sep(Dev d) {
   if (act && sub < 4) {                           // lane m of the group: component m
     const double *P = d.fpar + (size_t)NFP * fid;
     const double *fs = d.fsum + NFS * fid;
-    float om = sub == 0 ? o[0] : sub == 1 ? o[1] : sub == 2 ? o[2] : o[3];
-    d.fflux[4 * fid + sub] = P[FP_Q1] * fs[FS_FF + sub] + P[FP_Q2] * fs[FS_WG + sub] + f2d_bits(om);
+    T om = sub == 0 ? o[0] : sub == 1 ? o[1] : sub == 2 ? o[2] : o[3];
+    d.fflux[4 * fid + sub] = P[FP_Q1] * fs[FS_FF + sub] + P[FP_Q2] * fs[FS_WG + sub] + to_double(om);
   }
 }
 
@@ -1282,12 +1300,14 @@ void launch_ghost_gradW(const Dev &d, cudaStream_t s) {
 void launch_face_coef(const Dev &d, cudaStream_t s, int fp32) {
   if (fp32) {
     k_face_scalar<float><<<nblk(d.nf, 128), 128, 0, s>>>(d);
-    k_face_coef_sep<<<nblk((size_t)d.nf * FCG, 256), 256, 0, s>>>(d);
+    k_face_coef_sep<float><<<nblk((size_t)d.nf * FCG, 256), 256, 0, s>>>(d);
     if (d.nwall > 0)
       k_face_coef<float><<<nblk((size_t)d.nwall * 32 * FCW, 256), 256, 0, s>>>(d, d.wall_faces, d.nwall);
   } else {
     k_face_scalar<double><<<nblk(d.nf, 128), 128, 0, s>>>(d);
-    k_face_coef<double><<<nblk((size_t)d.nf * 32 * FCW, 256), 256, 0, s>>>(d, nullptr, d.nf);
+    k_face_coef_sep<double><<<nblk((size_t)d.nf * FCG, 256), 256, 0, s>>>(d);
+    if (d.nwall > 0)
+      k_face_coef<double><<<nblk((size_t)d.nwall * 32 * FCW, 256), 256, 0, s>>>(d, d.wall_faces, d.nwall);
   }
 }
 void launch_cell_macro(const Dev &d, cudaStream_t s, int level_n) {

@@ -1003,9 +1003,10 @@ template <typename MT> __global__ void __launch_bounds__(512) k_macro_sweep(Dev 
               else if (s == 3 && row < nj - 1) dv = prv + 4 * (row + 1);
             }
           }
-          // a zero increment gives exactly zero (both forms), so all four
-          // slots are evaluated without branches
-          macro_off(r + MR_SLOT + MR_SW * s, dv, d.Keff, o[s]);
+          // a zero increment couples to zero: only slots with a neighbour
+          // increment are evaluated (the FP64 pipe is this kernel's bound)
+          if (dv != zero4) macro_off(r + MR_SLOT + MR_SW * s, dv, d.Keff, o[s]);
+          else o[s][0] = o[s][1] = o[s][2] = o[s][3] = MT(0);
         }
 #pragma unroll
         for (int s = 0; s < 4; ++s)

@@ -652,18 +652,6 @@ template <typename T> __global__ void k_cell_params(Dev d, const double *Wsrc, d
 }
 
 // ----------------------------------------------------- macro LU-SGS sweep
-__device__ __forceinline__ void euler_flux(const double *W, double nx, double ny, double un,
-                                           int Keff, double F[4]) {
-  Prim p = primitive(W, Keff);
-  double pr = p.rho / (2.0 * p.lam);
-  double vabs = p.ux * nx + p.uy * ny;
-  double vn = vabs - un;
-  F[0] = p.rho * vn;
-  F[1] = W[1] * vn + pr * nx;
-  F[2] = W[2] * vn + pr * ny;
-  F[3] = W[3] * vn + pr * vabs;
-}
-
 // Per-cell record of the macro sweep (gathered in parallel before it):
 // R (4), 1/diag, then per face slot: neighbour W (4), outward normal (2),
 // U.n, S/4, Gamma.
@@ -673,13 +661,32 @@ enum { MR_R = 0, MR_IDIAG = 4, MR_SLOT = 5, MR_SW = 9 };
 // the difference F_E(W + dW) - F_E(W) evaluated directly.  FP32 (mixed
 // path): the same difference rewritten exactly in terms of dW (every term is
 // O(dW)), so no cancellation occurs when dW << W.
-__device__ __forceinline__ void macro_off(const double *r, const double *dW, int Keff,
-                                          double out[4]) {
-  double Wa[4], Wb[4], Fa[4], Fb[4];
-  for (int m = 0; m < 4; ++m) { Wb[m] = r[m]; Wa[m] = Wb[m] + dW[m]; }
-  euler_flux(Wa, r[4], r[5], r[6], Keff, Fa);
-  euler_flux(Wb, r[4], r[5], r[6], Keff, Fb);
-  for (int m = 0; m < 4; ++m) out[m] = r[7] * ((Fa[m] - Fb[m]) - r[8] * dW[m]);
+// Off-diagonal coupling (1/4 S)(Delta F_E . n - Gamma dW) of a neighbour
+// with state W (slot record r: W (4), n (2), U.n, S/4, Gamma) and increment
+// dW, the flux variation written out as a difference (one division, no
+// cancellation between the two fluxes): with d(ab/rho) = (da b rho + a db
+// rho + da db rho - a b drho) / (rho (rho + drho)) and p = (gamma-1)(E -
+// |m|^2/(2 rho)).
+__device__ __forceinline__ void macro_off(const double *r, const double *dW, int Keff, double out[4]) {
+  const double rho = r[0], m1 = r[1], m2 = r[2], E = r[3], nx = r[4], ny = r[5], un = r[6];
+  const double dr = dW[0], d1 = dW[1], d2 = dW[2], dE = dW[3];
+  const double g1 = 2.0 / (2.0 + (double)Keff);          // gamma - 1
+  const double mn = m1 * nx + m2 * ny, dmn = d1 * nx + d2 * ny;
+  const double den = 1.0 / (rho * (rho + dr));
+  const double dq11 = (2.0 * (m1 * d1 + m2 * d2) * rho + (d1 * d1 + d2 * d2) * rho - (m1 * m1 + m2 * m2) * dr) * den;
+  const double dp = g1 * (dE - 0.5 * dq11);
+  const double p = g1 * (E - 0.5 * (m1 * m1 + m2 * m2) * ((rho + dr) * den));
+  const double dv = (dmn * rho - mn * dr) * den;
+  const double dF0 = dmn - dr * un;
+  const double dF1 = (d1 * mn * rho + m1 * dmn * rho + d1 * dmn * rho - m1 * mn * dr) * den - d1 * un + dp * nx;
+  const double dF2 = (d2 * mn * rho + m2 * dmn * rho + d2 * dmn * rho - m2 * mn * dr) * den - d2 * un + dp * ny;
+  const double dF3 = (dE * mn * rho + E * dmn * rho + dE * dmn * rho - E * mn * dr) * den - dE * un +
+                     dp * (mn + dmn) * (rho * den) + p * dv;
+  const double q = r[7], g = r[8];
+  out[0] = q * (dF0 - g * dr);
+  out[1] = q * (dF1 - g * d1);
+  out[2] = q * (dF2 - g * d2);
+  out[3] = q * (dF3 - g * dE);
 }
 
 __device__ __forceinline__ void macro_off(const float *rr, const float *dWn, int Keff, float out[4]) {

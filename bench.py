@@ -205,10 +205,14 @@ def time_arm(case, precision, steps, warmup, device, profile, tune=True, dist=No
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(s.stream)
+    # motion, assembly and implicit step issued without waiting on the device
+    # (ugks_advance_batch with one instance; an assembly error would surface
+    # at the next synchronising call, the rank barrier below)
     for _ in range(steps):
-        s.advance()
+        U.advance_batch([s])
     ev1.record(s.stream)
     rank_sync(dist)
+    s.moments()                              # synchronising call: reports any deferred error
     ms = ev0.elapsed_time(ev1)
     launches = s.launch_count() - l0
     prof = None
@@ -231,11 +235,12 @@ def e2e_arm(s, steps):
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    from paper_2604_09984_gb300 import ugks as U
     t0 = time.perf_counter()
     ev0.record(s.stream)
     for _ in range(steps):
-        s.advance()
-        s.moments(W, q, st, wall)
+        U.advance_batch([s])                 # no wait until the results are read
+        s.moments(W, q, st, wall)            # synchronises: W, q, status, wall loads on the host
     ev1.record(s.stream)
     torch.cuda.synchronize()
     wall_s = time.perf_counter() - t0

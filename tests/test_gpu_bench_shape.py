@@ -1,6 +1,8 @@
 """GPU parity at the shape the bench times (32x32 velocities on [-6, 6],
-overset MEMS meshes, micro-sweep tiles picked by the autotuner) and
-bit-exact overset connectivity at the full MEMS and two-body sizes.
+overset MEMS meshes, micro-sweep tiles picked by the autotuner), one flux
+evaluation on a random non-equilibrium state at the full bench size compared
+output by output, and bit-exact overset connectivity at the full MEMS and
+two-body sizes.
 
 The field comparison scales every component of W and q by that component's
 own largest magnitude (a global maximum would hide errors in the small
@@ -13,6 +15,9 @@ import pytest
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
+from oracle import kinetic as kn  # noqa: E402
+from oracle import overset  # noqa: E402
+from oracle import ugks as ou  # noqa: E402
 from oracle.run import Run  # noqa: E402
 from paper_2604_09984_gb300 import ugks as U  # noqa: E402
 from paper_2604_09984_gb300 import workloads as wl  # noqa: E402
@@ -93,3 +98,53 @@ def test_connectivity_full_size_bit_exact(name):
         assert np.array_equal(np.nonzero(st == U.RECEPTOR)[0], rec)
         assert np.array_equal(dn[rec], g[tag + "_donors"])
         assert np.array_equal(w[rec].view(np.int64), g[tag + "_weight_bits"])
+
+
+@pytest.fixture(scope="module")
+def full_size_flux():
+    """The oracle's flux evaluation (Eqs. microscopicFlux, macroscopicFlux, the
+    wall condition) on the full MEMS bench mesh (256x128 + 128x32 cells, 32x32
+    velocities) in a random non-equilibrium state (Maxwellians of perturbed
+    primitives times seeded noise on f), with the receptors interpolated from
+    the assembly at t = 0 and the geometry of the move to t = dt."""
+    case = wl.mems()
+    prim = wl.random_prim(case, 7, amp_rho=0.1, amp_u=0.1, amp_T=0.1)
+    r = Run(case, prim)
+    rng = np.random.Generator(np.random.PCG64(8))
+    st = r.state
+    st.f = st.f * (1.0 + rng.uniform(-0.05, 0.05, st.f.shape))
+    st.W = kn.moments(st.f, r.dvs)
+    rho, Vx, Vy, lam = kn.primitive(st.W, r.gas)
+    st.q = kn.heat_flux(st.f, Vx, Vy, r.dvs)
+    f0, W0, q0 = st.f.copy(), st.W.copy(), st.q.copy()
+    conn = r.conn
+    overset.interpolate(st, conn.receptors, conn.donors, conn.weights)
+    geo = r.geometry(0.0, case.dt)
+    wS = ou.normal_velocity(r.setup, geo)
+    dts = ou.explicit_dt(r.setup, geo, wS)
+    fl = ou.flux(r.setup, geo, st, r.status, dts, wS)
+    wall = np.zeros((len(case.blocks), 4))
+    for n, f in enumerate(fl.wall_face):
+        wall[r.setup.topo.face_block[f]] += geo.S[f] * fl.wall_F[n]
+    return case, prim, (f0, W0, q0), r.status, fl, wall
+
+
+@pytest.mark.parametrize("prec,tol", [(U.FP64, 1e-11), (U.FP32, 2e-5)])
+def test_flux_full_size_matches_oracle(full_size_flux, prec, tol):
+    """At the full bench size, every (cell, velocity) of the flux divergence
+    D, every cell's macro flux F and every block's wall loads equal the
+    oracle's (FP64 to 1e-11, FP32-mixed to 2e-5 of the largest magnitude)."""
+    case, prim, (f0, W0, q0), status, fl, wall_ref = full_size_flux
+    s = U.Solver(case, prec, prim=prim)
+    st, _, _ = s.connectivity()
+    assert np.array_equal(st, status.astype(np.int32))
+    s.set_state(torch.as_tensor(f0), W0, q0)
+    s.move_mesh(case.dt)
+    D, F = s.eval_flux()
+    field = status == 0
+    Dg = D.cpu().numpy()
+    assert np.abs(Dg[field] - fl.D[field]).max() / np.abs(fl.D[field]).max() < tol
+    assert np.abs(F[field] - fl.F[field]).max() / np.abs(fl.F[field]).max() < tol
+    _, _, _, wall = s.moments()
+    assert np.abs(wall - wall_ref).max() / np.abs(wall_ref).max() < tol
+    del D

@@ -278,6 +278,21 @@ int ugks_sizes(const ugks_ctx *ctx, int *ncells, int *nfaces, int *nv,
 int ugks_get_state(ugks_ctx *ctx, double *f, double *W, double *q);
 int ugks_set_state(ugks_ctx *ctx, const double *f, const double *W, const double *q);
 
+/* Checkpoint of what a context carries from one physical step to the next
+ * besides f, W and q (ugks_get_state / ugks_set_state): the time t, the node
+ * coordinates at t (nnodes x 2 FP64, nnodes = sum over blocks of
+ * (ni + 1)(nj + 1) in block order, the layout of ugks_init_mesh) and the cell
+ * status of the last assembly (ncells int32; the next assembly's previous
+ * status, from which it finds uncovered cells).  Everything else a step uses
+ * is recomputed by the next ugks_move_mesh / ugks_overset_connect, so a
+ * context restored from (f, W, q, t, nodes, status) continues bit for bit as
+ * the one the checkpoint was taken from.  Only between steps (no pending
+ * move).  `t`, `nodes`, `status` are HOST (each may be NULL on get);
+ * ugks_get_checkpoint synchronises the stream.  Errors: UGKS_ERR_ORDER (a
+ * move is pending), UGKS_ERR_ARG (null input on set). */
+int ugks_get_checkpoint(ugks_ctx *ctx, double *t, double *nodes, int32_t *status);
+int ugks_set_checkpoint(ugks_ctx *ctx, double t, const double *nodes, const int32_t *status);
+
 /* Diagnostic of Steps 1/3: evaluate the time-averaged interface flux of the
  * current state with the current geometry (after ugks_move_mesh) and write
  * D = sum_faces S F_hat (ncells x nv x 2, outward positive, Eq.

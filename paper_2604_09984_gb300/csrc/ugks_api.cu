@@ -1370,6 +1370,29 @@ int ugks_set_state(ugks_ctx *ctx, const double *f, const double *W, const double
   return launch_status(ctx);
 }
 
+int ugks_get_checkpoint(ugks_ctx *ctx, double *t, double *nodes, int32_t *status) {
+  if (!ctx || !ctx->mesh_ready || ctx->moved) return UGKS_ERR_ORDER;
+  Dev &d = ctx->d;
+  if (t) *t = ctx->t;
+  if (nodes) CK(cudaMemcpyAsync(nodes, d.X_new, sizeof(double) * 2 * d.nn, cudaMemcpyDefault, ctx->st));
+  if (status) CK(cudaMemcpyAsync(status, d.status, sizeof(int) * d.nc, cudaMemcpyDefault, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return launch_status(ctx);
+}
+
+int ugks_set_checkpoint(ugks_ctx *ctx, double t, const double *nodes, const int32_t *status) {
+  if (!ctx || !ctx->mesh_ready || ctx->moved) return UGKS_ERR_ORDER;
+  if (!nodes || !status) return fail(ctx, UGKS_ERR_ARG, "null nodes or status");
+  Dev &d = ctx->d;
+  // the nodes at t become the old level of the next move
+  CK(cudaMemcpyAsync(d.X_new, nodes, sizeof(double) * 2 * d.nn, cudaMemcpyDefault, ctx->st));
+  CK(cudaMemcpyAsync(d.status, status, sizeof(int) * d.nc, cudaMemcpyDefault, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  ctx->t = t;
+  ctx->fresh_pending = false;
+  return launch_status(ctx);
+}
+
 int ugks_eval_flux(ugks_ctx *ctx, double *D, double *F) {
   if (!ctx || !ctx->mesh_ready) return UGKS_ERR_ORDER;
   if (!ctx->moved) return fail(ctx, UGKS_ERR_ORDER, "ugks_eval_flux needs a preceding ugks_move_mesh");

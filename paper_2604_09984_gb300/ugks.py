@@ -70,6 +70,8 @@ SYMBOLS = {
     "ugks_sizes": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
     "ugks_get_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "ugks_set_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ugks_get_checkpoint": (c_int, [c_void_p, POINTER(c_double), c_void_p, c_void_p]),
+    "ugks_set_checkpoint": (c_int, [c_void_p, c_double, c_void_p, c_void_p]),
     "ugks_eval_flux": (c_int, [c_void_p, c_void_p, c_void_p]),
     "ugks_get_connectivity": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "ugks_get_geometry": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -319,6 +321,26 @@ class Solver:
         Wn = None if W is None else np.ascontiguousarray(W, dtype=np.float64)
         qn = None if q is None else np.ascontiguousarray(q, dtype=np.float64)
         self._check(self.lib.ugks_set_state(self.ctx, _ptr(ft), _ptr(Wn), _ptr(qn)))
+
+    def checkpoint(self):
+        """Everything needed to continue bit for bit from between two steps:
+        f (device, FP64), W, q, t, the node coordinates at t and the cell
+        status (ugks_get_state, ugks_get_checkpoint)."""
+        f, W, q = self.get_state()
+        nn = sum((b.ni + 1) * (b.nj + 1) for b in self.case.blocks)
+        nodes = np.empty((nn, 2))
+        status = np.empty(self.nc, dtype=np.int32)
+        t = c_double()
+        self._check(self.lib.ugks_get_checkpoint(self.ctx, ctypes.byref(t), _ptr(nodes), _ptr(status)))
+        return {"f": f, "W": W, "q": q, "t": float(t.value), "nodes": nodes, "status": status}
+
+    def restore(self, ck):
+        """Continue from a checkpoint() of a context of the same case."""
+        nodes = np.ascontiguousarray(ck["nodes"], dtype=np.float64)
+        status = np.ascontiguousarray(ck["status"], dtype=np.int32)
+        self._check(self.lib.ugks_set_checkpoint(self.ctx, float(ck["t"]), _ptr(nodes), _ptr(status)))
+        self.set_state(ck["f"], ck["W"], ck["q"])
+        self.t = float(ck["t"])
 
     def eval_flux(self):
         torch = self.torch

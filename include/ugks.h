@@ -131,6 +131,24 @@ typedef struct {
   int n_orphan;             /* receptors/fresh cells without donor            */
 } ugks_connect_stats;
 
+/* Metrics of one physical step (Sec. 2.2), sums over the solved cells of the
+ * last inner iteration, each a fixed-order reduction (the same bits on every
+ * run of a mesh):
+ *   res_macro_sq  sum |R|^2, R = T_W - Omega^{n+1} W / dt - F / 2 the
+ *                 right-hand side of the macro LU-SGS (Step 4, before W is
+ *                 updated), 4 components per cell;
+ *   res_micro_sq  sum |r|^2 of the micro residual (Step 5) over the cell's
+ *                 velocities and both reduced distributions (on a velocity
+ *                 shard: over this shard's velocities; add the shards' sums);
+ *   fix_sq        sum |W^{s+1} - W'|^2, the Step-7 moment fix of the
+ *                 macroscopic predictor (zero once micro and macro agree);
+ *   total         sum Omega^{n+1} W over the field cells (mass, momentum,
+ *                 energy), for the conservation defect between steps. */
+typedef struct {
+  double res_macro_sq, res_micro_sq, fix_sq;
+  double total[4];
+} ugks_step_metrics;
+
 /* Device bytes of the workspace for these parameters and blocks.  Host-only,
  * no CUDA call.  Errors: UGKS_ERR_ARG for invalid sizes or BC combinations. */
 int ugks_workspace_query(const ugks_params *p, int nblocks,
@@ -201,6 +219,17 @@ int ugks_step(ugks_ctx *ctx, double dt, int n_inner);
 /* Turn the CUDA-graph path of ugks_step on (default) or off.  Errors:
  * UGKS_ERR_ARG (null context). */
 int ugks_set_graphs(ugks_ctx *ctx, int on);
+
+/* Record ugks_step_metrics in the steps that follow (on != 0; off at
+ * creation).  When on, the last inner iteration of a step runs four small
+ * reduction kernels more (on graphs too: a graph of its own).  Errors:
+ * UGKS_ERR_ARG. */
+int ugks_set_metrics(ugks_ctx *ctx, int on);
+
+/* Metrics of the last ugks_step (HOST output); synchronises the stream.
+ * Errors: UGKS_ERR_ORDER (the last step ran with metrics off, or no step
+ * yet), UGKS_ERR_ARG (null out). */
+int ugks_get_metrics(ugks_ctx *ctx, ugks_step_metrics *out);
 
 /* Graph captures (or updates) and graph replays of ugks_step since creation
  * (HOST outputs, each may be NULL).  Errors: UGKS_ERR_ARG. */

@@ -427,6 +427,21 @@ class StepInfo:
     dts: np.ndarray
     flux_n: FluxResult
     last_flux: FluxResult
+    R: Optional[np.ndarray] = None       # Step-4 macro residual of the last inner iteration
+    rhs: Optional[np.ndarray] = None     # Step-5 micro residual of the last inner iteration
+    fix: Optional[np.ndarray] = None     # Step-7 moment fix W^{s+1} - W' of the last inner iteration
+
+
+def step_metrics(geo: Geometry, st: State, info: StepInfo, status):
+    """Per-step metrics of the implicit step (Sec. 2.2): squared L2 norms
+    over the solved cells of the macro residual R (Step 4), the micro
+    residual r (Step 5) and the moment fix W^{s+1} - W' (Step 7) of the last
+    inner iteration, and the field totals of Omega^{n+1} W."""
+    field = status == FIELD
+    return {"res_macro_sq": float((info.R[field] ** 2).sum()),
+            "res_micro_sq": float((info.rhs[field] ** 2).sum()),
+            "fix_sq": float((info.fix[field] ** 2).sum()),
+            "total": (geo.vol_new[field, None] * st.W[field]).sum(axis=0)}
 
 
 def implicit_step(setup: Setup, geo: Geometry, st: State, dt: float, n_inner: int,
@@ -500,4 +515,4 @@ def implicit_step(setup: Setup, geo: Geometry, st: State, dt: float, n_inner: in
         st.f = fnew
         st.W = np.where(field[:, None], Wnew, st.W)
         st.q = np.where(field[:, None], qnew, st.q)
-    return st, StepInfo(dts, fl_n, fl)
+    return st, StepInfo(dts, fl_n, fl, R, rhs, Wnew - Wp)

@@ -55,6 +55,8 @@ struct ugks_ctx {
   std::vector<StepGraph> gcache;
   int64_t gclock = 0, gcaptures = 0, greplays = 0;
   bool stepped = false;               // a ugks_step has run (sweep records valid)
+  bool metrics = false;               // steps record their metrics (ugks_set_metrics)
+  bool metered = false;               // the last step recorded them
   int *work = nullptr;
   int *prev_status = nullptr, *n_orphan = nullptr, *blk_order = nullptr;
   int cap_interp = 0;
@@ -281,6 +283,8 @@ size_t carve(char *base, const Sizes &s, int nb, int fp32, int fbf, int nwork, i
   d.Dbuf = c.take<char>(pair * (size_t)s.nc * s.nvp);
   d.fval = c.take<char>(2 * pair * (size_t)s.nf * s.nvp);
   d.stepc = c.take<double>(4);
+  d.mpart = c.take<double>((size_t)MET_NQ * MET_BLOCKS);
+  d.mout = c.take<double>(MET_NQ);
   d.TW = c.take<double>(4 * (size_t)s.nc); d.Fc = c.take<double>(4 * (size_t)s.nc);
   d.dW = c.take<double>(4 * (size_t)s.nc); d.Wp = c.take<double>(4 * (size_t)s.nc);
   d.mrec = c.take<char>(fp32 ? sizeof(float) * NMR32 * s.nmrec32 : sizeof(double) * NMR * (size_t)s.nc);
@@ -684,14 +688,17 @@ int step_body(ugks_ctx *ctx, int n_inner) {
     }
     // Step 4 (macro LU-SGS) on the side stream, concurrently with the flux
     // divergence of Step 3 on the main stream; Step 5 joins both
+    bool met = ctx->metrics && it == n_inner - 1;    // metrics of the last inner iteration
     { Prof p(ctx, UGKS_PROF_MACRO_SWEEP); launch_macro_prep(d, s, fp); }
     CK(cudaEventRecord(ctx->ev_flux, s));
     CK(cudaStreamWaitEvent(ctx->side, ctx->ev_flux, 0));
+    if (met) launch_metrics(d, s, 0, fp);
     { Prof p(ctx, UGKS_PROF_MACRO_SWEEP, ctx->side); launch_macro_sweep(d, ctx->side, ctx->max_nj, fp); }
     CK(cudaEventRecord(ctx->ev_macro, ctx->side));
     { Prof p(ctx, UGKS_PROF_RHS); launch_flux_tile(d, s, fp, ctx->face_tile); }              // Step 3
     CK(cudaStreamWaitEvent(s, ctx->ev_macro, 0));
     { Prof p(ctx, UGKS_PROF_RESIDUAL); launch_residual(d, s, it == 0, fp); }                 // Step 5
+    if (met) launch_metrics(d, s, 1, fp);
     { Prof p(ctx, UGKS_PROF_MICRO_FWD); launch_wsweep(d, s, 0, ctx->work, ctx->nwork, ctx->sweep_nw, ctx->ns_fwd, ctx->sweep_vpt, fp, ctx->sweep_ql); }  // Step 6
     { Prof p(ctx, UGKS_PROF_MICRO_BWD); launch_wsweep(d, s, 1, ctx->work, ctx->nwork, ctx->sweep_nw, ctx->ns_bwd, ctx->sweep_vpt, fp, ctx->sweep_ql); }
     { Prof p(ctx, UGKS_PROF_MOMENTS); launch_moments(d, s, fp); }                          // Step 7
@@ -699,6 +706,10 @@ int step_body(ugks_ctx *ctx, int n_inner) {
       if ((rx = shard_exchange(ctx, 1))) return rx;
       { Prof p(ctx, UGKS_PROF_MOMENTS); launch_moments_finish(d, s); }
       ctx->launches += 1;
+    }
+    if (met) {
+      launch_metrics(d, s, 2, fp);
+      ctx->launches += 4;
     }
     ctx->launches += 8;
   }
@@ -709,7 +720,7 @@ int step_body(ugks_ctx *ctx, int n_inner) {
 // struct they take by value and the launch configuration.
 std::vector<unsigned char> graph_key(const ugks_ctx *c, int n_inner) {
   int cfg[] = {n_inner, c->fresh_pending ? 1 : 0, c->face_tile, c->sweep_vpt, c->ns_fwd, c->ns_bwd, c->sweep_nw,
-               c->sweep_ql, c->nwork, c->nsm, c->max_nj, c->fp32};
+               c->sweep_ql, c->nwork, c->nsm, c->max_nj, c->fp32, c->metrics ? 1 : 0};
   // (the step size is read from device memory; the bin count belongs to the
   // assembly, which is not part of the step)
   Dev d = c->d;
@@ -1179,8 +1190,29 @@ int ugks_step(ugks_ctx *ctx, double dt, int n_inner) {
   if (rx) return rx;
   ctx->fresh_pending = false;
   ctx->stepped = true;
+  ctx->metered = ctx->metrics;
   ctx->t = ctx->t_new;
   ctx->moved = false;
+  return launch_status(ctx);
+}
+
+int ugks_set_metrics(ugks_ctx *ctx, int on) {
+  if (!ctx) return UGKS_ERR_ARG;
+  ctx->metrics = on != 0;
+  return UGKS_OK;
+}
+
+int ugks_get_metrics(ugks_ctx *ctx, ugks_step_metrics *out) {
+  if (!ctx || !ctx->mesh_ready) return UGKS_ERR_ORDER;
+  if (!out) return fail(ctx, UGKS_ERR_ARG, "null output");
+  if (!ctx->metered) return fail(ctx, UGKS_ERR_ORDER, "the last ugks_step recorded no metrics");
+  double m[MET_NQ];
+  CK(cudaMemcpyAsync(m, ctx->d.mout, sizeof(m), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  out->res_macro_sq = m[MET_R2];
+  out->res_micro_sq = m[MET_RMICRO2];
+  out->fix_sq = m[MET_FIX2];
+  for (int i = 0; i < 4; ++i) out->total[i] = m[MET_TOT + i];
   return launch_status(ctx);
 }
 

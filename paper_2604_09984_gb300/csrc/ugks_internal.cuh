@@ -142,7 +142,16 @@ struct Dev {
   int ntiles;
   int *err;                  // error flags
   int wait_polls;            // bounded waits (sweeps): polls before giving up (EF_TIMEOUT)
+  double *mpart;             // MET_NQ*MET_BLOCKS per-block partial sums of the step metrics
+  double *mout;              // MET_NQ step metrics of the last metered step
 };
+
+// Step metrics (sums over the solved cells, fixed-order reductions):
+// squared norms of the macro residual R and the micro residual r of the last
+// inner iteration, of the Step-7 moment fix W^{s+1} - W', and the totals of
+// Omega^{n+1} W.
+enum { MET_R2 = 0, MET_RMICRO2 = 1, MET_FIX2 = 2, MET_TOT = 3, MET_NQ = 7 };
+constexpr int MET_BLOCKS = 304, MET_THREADS = 256;
 
 // Polls of a bounded wait before it gives up; the drain of a CTA's own copies
 // after a timeout always uses the default.

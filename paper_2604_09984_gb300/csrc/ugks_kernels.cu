@@ -1263,6 +1263,87 @@ template <typename T> __global__ void k_f_from_double(Dev d, const double *in) {
 // ------------------------------------------------------- launch wrappers
 static inline int nblk(size_t n, int b) { return (int)((n + b - 1) / b); }
 
+// ---------------------------------------------------------------- metrics
+// Per-block sums in a fixed order (each thread strides over its items, then
+// a shared-memory tree), finished by one block in the same way: the metrics
+// are the same bits on every run of a given mesh and launch shape.
+__device__ __forceinline__ void met_block_sum(double *sh, double v, double *out) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int h = MET_THREADS / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+  __syncthreads();
+}
+
+// |R|^2 of Step 4: R = T_W - Omega^{n+1} W / dt - F / 2 (the right-hand side
+// of the macro LU-SGS, before W changes in this iteration)
+__global__ void __launch_bounds__(MET_THREADS) k_met_macro(Dev d) {
+  __shared__ double sh[MET_THREADS];
+  double idt = 1.0 / d.stepc[0], acc = 0.0;
+  for (int c = blockIdx.x * MET_THREADS + threadIdx.x; c < d.nc; c += MET_BLOCKS * MET_THREADS) {
+    if (!(d.cmask[c] & 1)) continue;
+    double vol = d.vol_new[c];
+    for (int m = 0; m < 4; ++m) {
+      double r = d.TW[4 * c + m] - vol * idt * d.W[4 * c + m] - 0.5 * d.Fc[4 * c + m];
+      acc += r * r;
+    }
+  }
+  met_block_sum(sh, acc, d.mpart + MET_R2 * MET_BLOCKS + blockIdx.x);
+}
+
+// |r|^2 of Step 5 over the solved cells and this context's velocities
+template <typename T> __global__ void __launch_bounds__(MET_THREADS) k_met_micro(Dev d) {
+  __shared__ double sh[MET_THREADS];
+  double acc = 0.0;
+  size_t n = (size_t)d.nc * d.nvp;
+  for (size_t t = (size_t)blockIdx.x * MET_THREADS + threadIdx.x; t < n; t += (size_t)MET_BLOCKS * MET_THREADS) {
+    int c = (int)(t / d.nvp), k = (int)(t - (size_t)c * d.nvp);
+    if (k >= d.nv || !(d.cmask[c] & 1)) continue;
+    typename Vec2<T>::type r = ldf<T>(d.dfs, t);
+    acc += (double)r.x * (double)r.x + (double)r.y * (double)r.y;
+  }
+  met_block_sum(sh, acc, d.mpart + MET_RMICRO2 * MET_BLOCKS + blockIdx.x);
+}
+
+// |W^{s+1} - W'|^2 (Step 7) and the totals of Omega^{n+1} W over the field
+__global__ void __launch_bounds__(MET_THREADS) k_met_fix(Dev d) {
+  __shared__ double sh[MET_THREADS];
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int c = blockIdx.x * MET_THREADS + threadIdx.x; c < d.nc; c += MET_BLOCKS * MET_THREADS) {
+    if (d.status[c] != ST_FIELD) continue;
+    double vol = d.vol_new[c];
+    for (int m = 0; m < 4; ++m) {
+      double w = d.W[4 * c + m], e = w - d.Wp[4 * c + m];
+      acc[0] += e * e;
+      acc[1 + m] += vol * w;
+    }
+  }
+  for (int q = 0; q < 5; ++q) met_block_sum(sh, acc[q], d.mpart + (MET_FIX2 + q) * MET_BLOCKS + blockIdx.x);
+}
+
+__global__ void __launch_bounds__(MET_THREADS) k_met_final(Dev d) {
+  __shared__ double sh[MET_THREADS];
+  for (int q = 0; q < MET_NQ; ++q) {
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < MET_BLOCKS; b += MET_THREADS) acc += d.mpart[q * MET_BLOCKS + b];
+    met_block_sum(sh, acc, d.mout + q);
+  }
+}
+
+void launch_metrics(const Dev &d, cudaStream_t s, int stage, int fp32) {
+  if (stage == 0) k_met_macro<<<MET_BLOCKS, MET_THREADS, 0, s>>>(d);
+  else if (stage == 1) {
+    if (fp32) k_met_micro<float><<<MET_BLOCKS, MET_THREADS, 0, s>>>(d);
+    else k_met_micro<double><<<MET_BLOCKS, MET_THREADS, 0, s>>>(d);
+  } else {
+    k_met_fix<<<MET_BLOCKS, MET_THREADS, 0, s>>>(d);
+    k_met_final<<<1, MET_THREADS, 0, s>>>(d);
+  }
+}
+
 void launch_move_nodes(const Dev &d, cudaStream_t s) { k_move_nodes<<<nblk(d.nn, 256), 256, 0, s>>>(d); }
 
 // Small host->device uploads (motion maps, search-bin boxes) travel as kernel

@@ -25,6 +25,9 @@ int wsweep_fits(int fp32, int fbf, int vpt, int nw, int ns, int ql);
 void sweep_setup();
 void launch_moments(const Dev &d, cudaStream_t s, int fp32);
 void launch_moments_finish(const Dev &d, cudaStream_t s);   // sharded step, after the exchange
+// step metrics: stage 0 after the macro prep (|R|^2), 1 after the residual
+// (|r|^2), 2 after the moments (|W - W'|^2, totals; 2 kernels)
+void launch_metrics(const Dev &d, cudaStream_t s, int stage, int fp32);
 void launch_init_state(const Dev &d, cudaStream_t s, const double *prim, int fp32);
 void launch_flux_div_all(const Dev &d, cudaStream_t s, double *D, int fp32);
 void launch_wall_loads(const Dev &d, cudaStream_t s);

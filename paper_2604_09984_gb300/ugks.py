@@ -47,6 +47,11 @@ class ConnectStats(ctypes.Structure):
                 ("n_fresh", c_int), ("n_orphan", c_int)]
 
 
+class StepMetrics(ctypes.Structure):
+    _fields_ = [("res_macro_sq", c_double), ("res_micro_sq", c_double), ("fix_sq", c_double),
+                ("total", c_double * 4)]
+
+
 # exchange of a velocity-sharded context: fn(which, stream, user) -> 0
 EXCHANGE_FN = ctypes.CFUNCTYPE(c_int, c_int, c_void_p, c_void_p)
 
@@ -60,6 +65,8 @@ SYMBOLS = {
     "ugks_overset_connect": (c_int, [c_void_p, POINTER(ConnectStats)]),
     "ugks_step": (c_int, [c_void_p, c_double, c_int]),
     "ugks_set_graphs": (c_int, [c_void_p, c_int]),
+    "ugks_set_metrics": (c_int, [c_void_p, c_int]),
+    "ugks_get_metrics": (c_int, [c_void_p, POINTER(StepMetrics)]),
     "ugks_graph_stats": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int64)]),
     "ugks_advance_batch": (c_int, [POINTER(c_void_p), c_int, POINTER(c_double), POINTER(POINTER(c_double)),
                                    c_int, POINTER(c_int)]),
@@ -370,6 +377,20 @@ class Solver:
         """CUDA-graph path of ugks_step on or off (ugks_set_graphs)."""
         self._check(self.lib.ugks_set_graphs(self.ctx, int(bool(on))))
 
+    def set_metrics(self, on: bool):
+        """Record step metrics in the following steps (ugks_set_metrics)."""
+        self._check(self.lib.ugks_set_metrics(self.ctx, int(bool(on))))
+
+    def metrics(self):
+        """Metrics of the last step (ugks_get_metrics): the L2 norms of the
+        macro residual R, the micro residual r and the Step-7 moment fix of
+        the last inner iteration, and the totals of Omega W over the field."""
+        m = StepMetrics()
+        self._check(self.lib.ugks_get_metrics(self.ctx, ctypes.byref(m)))
+        return {"res_macro": m.res_macro_sq ** 0.5, "res_micro": m.res_micro_sq ** 0.5,
+                "fix": m.fix_sq ** 0.5, "total": [float(x) for x in m.total],
+                "res_macro_sq": m.res_macro_sq, "res_micro_sq": m.res_micro_sq, "fix_sq": m.fix_sq}
+
     def graph_stats(self):
         """(captures, replays) of the step's CUDA graphs (ugks_graph_stats)."""
         c, r = c_int64(), c_int64()
@@ -417,6 +438,49 @@ class Solver:
         n = (c_int64 * len(PROF_GROUPS))()
         self._check(self.lib.ugks_profile_read(self.ctx, ms, n, int(bool(reset))))
         return {g: (float(ms[i]), int(n[i])) for i, g in enumerate(PROF_GROUPS)}
+
+
+class StepLog:
+    """Per-step metrics as JSON lines, one object per physical step: step
+    index, t, the L2 norms of R, r and the moment fix of the last inner
+    iteration, the field totals of Omega W, the relative change of the field
+    mass since the previous logged step (the conservation defect; null on the
+    first line), the last assembly's counters and the step's wall time in ms
+    (host clock around the step and the metrics read, which synchronises).
+    The solver records metrics from the first advance() on."""
+
+    def __init__(self, out):
+        self._own = isinstance(out, (str, os.PathLike))
+        self.fh = open(out, "w") if self._own else out
+        self.n = 0
+        self._mass = None
+
+    def record(self, solver, ms=None, m=None):
+        import json
+        m = solver.metrics() if m is None else m
+        mass = m["total"][0]
+        line = {"step": self.n, "t": solver.t, "res_macro": m["res_macro"], "res_micro": m["res_micro"],
+                "fix": m["fix"], "total": m["total"],
+                "mass_defect": None if self._mass is None else (mass - self._mass) / self._mass,
+                "ms": ms}
+        line.update(getattr(solver, "last_stats", None) or {})
+        self.fh.write(json.dumps(line) + "\n")
+        self.fh.flush()
+        self._mass = mass
+        self.n += 1
+        return line
+
+    def advance(self, solver, **kw):
+        import time
+        solver.set_metrics(True)
+        t0 = time.perf_counter()
+        solver.advance(**kw)
+        m = solver.metrics()            # synchronises: the step is done
+        return self.record(solver, 1e3 * (time.perf_counter() - t0), m)
+
+    def close(self):
+        if self._own:
+            self.fh.close()
 
 
 def advance_batch(solvers, n_inner=None):

@@ -352,3 +352,38 @@ def test_continuum_navier_stokes_fluxes(which):
     else:
         kappa = mu * 2.5 / gas.Pr
         assert Fface[3] == pytest.approx(-kappa * G, rel=0.02)
+
+
+def test_step_metrics_vanish_at_rest_and_at_dual_time_convergence():
+    """The step metrics (Sec. 2.2): at a rest Maxwellian every residual and
+    the moment fix are zero; on a moving channel the macro residual R, the
+    micro residual r and the Step-7 fix shrink with the inner iterations and
+    vanish at the fixed point (the iteration drives exactly these quantities
+    to zero, so a wrong sign or a dropped term in either leaves a finite
+    norm), and the field total of Omega^{n+1} rho equals the level-n mass there
+    (the conservation of the converged step)."""
+    b = block(6, 5)
+    setup = make_setup([b], GAS, WIDE)
+    st = ugks.initial_state(setup, uniform_prim(30))
+    geo = mesh.geometry(setup.topo, [deform(b.x_ref, 0.0)], [deform(b.x_ref, 0.25)], 0.25)
+    st2, info = ugks.implicit_step(setup, geo, st, 0.25, 2)
+    m = ugks.step_metrics(geo, st2, info, np.zeros(30, dtype=np.int64))
+    assert m["res_macro_sq"] < 1e-24 and m["res_micro_sq"] < 1e-24 and m["fix_sq"] < 1e-24
+    np.testing.assert_allclose(m["total"], (geo.vol_new[:, None] * st.W).sum(axis=0), rtol=1e-13, atol=1e-14)
+
+    b = block(5, 4)
+    gas = kn.Gas(0, 2 / 3, 0.81, 0.1)
+    setup = make_setup([b], gas, kn.make_dvs(36, 36, -9, 9, -9, 9))
+    st = random_state(setup, 7, amp=0.1)
+    geo = moving_channel_geo(b, 0.05)
+    status = np.zeros(setup.topo.nc, dtype=np.int64)
+    ms = []
+    for n_inner in (1, 4, 40):
+        st2, info = ugks.implicit_step(setup, geo, st, 0.05, n_inner)
+        ms.append(ugks.step_metrics(geo, st2, info, status))
+    for k in ("res_macro_sq", "res_micro_sq", "fix_sq"):
+        v = [m[k] for m in ms]
+        assert v[0] > 0 and v[1] < v[0] and v[2] < 1e-20 * v[0], (k, v)
+    m0 = (geo.vol_old * st.W[:, 0]).sum()
+    assert abs(ms[2]["total"][0] - m0) < 1e-11 * m0
+    assert abs(ms[0]["total"][0] - m0) > abs(ms[2]["total"][0] - m0)

@@ -4,11 +4,13 @@ iteration, and the field totals of Omega^{n+1} W, computed by the reduction
 kernels behind ugks_get_metrics, agree with the oracle's on a deforming
 channel and an overset MEMS case.  Each norm is compared with a bound on its
 error from the path's own error on the terms it sums: the FP64 path agrees
-with the oracle to ~1e-11 of f, W and the fluxes, the FP32 path to ~2e-5, so
-|Delta |X|| <= tol * S_X with S_X the norm of the largest term of X
-(Omega W / dt for R and the fix's W scale, Omega f / dt for r), tol 1e-9 and
-1e-4.  Recording metrics changes no result, and the JSON-lines log writes
-one line per step."""
+with the oracle to ~1e-11 of f, W and the fluxes, the FP32 path to ~2e-5 of
+f and the fluxes and 1e-5 of W, so |Delta |X|| <= tol * S_X with S_X the norm
+of the largest term of X (Omega W / dt for R, Omega f / dt for r, W for the
+fix), tol 1e-9 / 1e-4 for the residuals and 1e-9 / 5e-5 for the fix (FP64 /
+FP32); every oracle norm is more than twice its bound, so a missing or zero
+value fails.  Recording metrics changes no result, and the JSON-lines log
+writes one line per step."""
 import io
 import json
 import os
@@ -41,9 +43,9 @@ def make_case(which):
     return wl.mems(nbi=48, nbj=24, noi=32, noj=12, nv=8, stretch=1.15, n_inner=2), 9
 
 
-@pytest.mark.parametrize("prec,tol", [(U.FP64, 1e-9), (U.FP32, 1e-4)])
+@pytest.mark.parametrize("prec,tol,tol_w", [(U.FP64, 1e-9, 1e-9), (U.FP32, 1e-4, 5e-5)])
 @pytest.mark.parametrize("which", ["channel", "mems"])
-def test_metrics_match_oracle(which, prec, tol):
+def test_metrics_match_oracle(which, prec, tol, tol_w):
     case, seed = make_case(which)
     prim = wl.random_prim(case, seed, amp_rho=0.1, amp_u=0.1, amp_T=0.1)
     s = U.Solver(case, prec, prim=prim)
@@ -59,12 +61,17 @@ def test_metrics_match_oracle(which, prec, tol):
     SR = np.sqrt(((vol[:, None] / case.dt * r.state.W[field]) ** 2).sum())
     Sr = np.sqrt(((vol[:, None, None] / case.dt * r.state.f[field]) ** 2).sum())
     SW = np.sqrt((r.state.W[field] ** 2).sum())
-    for key, scale in (("res_macro_sq", SR), ("res_micro_sq", Sr), ("fix_sq", SW)):
-        a, b = np.sqrt(g[key]), np.sqrt(o[key])
-        assert b > 1e-3 * scale, key          # a norm well above the bound
-        assert abs(a - b) <= tol * scale, (key, a, b, scale)
+    rows = []
+    for key, bound in (("res_macro_sq", tol * SR), ("res_micro_sq", tol * Sr), ("fix_sq", tol_w * SW)):
+        rows.append((key, np.sqrt(g[key]), np.sqrt(o[key]), bound))
     tot = np.abs(o["total"]).max()
-    assert np.abs(np.array(g["total"]) - o["total"]).max() <= tol * tot
+    dtot = np.abs(np.array(g["total"]) - o["total"]).max()
+    print("\n", which, prec, ["%s gpu %.6e oracle %.6e diff %.2e bound %.2e" % (k, a, b, abs(a - b), e)
+                               for k, a, b, e in rows], "totals diff %.2e of %.3e" % (dtot, tot))
+    for key, a, b, bound in rows:
+        assert b > 2 * bound, key
+        assert abs(a - b) <= bound, (key, a, b, bound)
+    assert dtot <= tol_w * tot
 
 
 def test_metrics_change_no_result_and_log_lines():

@@ -21,7 +21,14 @@ struct ugks_ctx {
   cudaStream_t st = nullptr;
   cudaStream_t side = nullptr;        // macro LU-SGS runs here, overlapped with the flux kernel
   cudaStream_t cap = nullptr;         // step graphs are captured here (the caller's stream may be the legacy one)
+  cudaStream_t tail = nullptr;        // split tail (lowest priority: it fills the reduction's free slots)
   cudaEvent_t ev_flux = nullptr, ev_macro = nullptr;
+  cudaEvent_t ev_bwd = nullptr, ev_tail = nullptr;   // fork / join of the inner iteration's tail
+  // Step 7 of an inner iteration, the receptors' W and q and the W gradients
+  // run on the tail stream beside the next iteration's velocity reduction
+  // (which reads none of them); not where an outflow ghost state follows W
+  // or on a velocity shard (whose Step 7 waits for the host exchange)
+  bool split_tail = false;
   char *ws = nullptr;
   size_t ws_bytes = 0;
   Dev d;
@@ -559,12 +566,14 @@ int prof_drain(ugks_ctx *ctx) {
 
 // Receptor (fresh = 0) or fresh-cell (fresh = 1) interpolation; the list
 // length lives on the device.
-int do_interp(ugks_ctx *ctx, int fresh) {
+int do_interp(ugks_ctx *ctx, int fresh, int parts = 3, cudaStream_t s = nullptr) {
   if (ctx->nblocks < 2) return UGKS_OK;
   Dev &d = ctx->d;
+  if (!s) s = ctx->st;
   {
-    Prof p(ctx, UGKS_PROF_INTERP);
-    launch_interp(d, ctx->st, fresh ? d.fresh_list : d.rec_list, d.conn_cnt + (fresh ? 1 : 0), ctx->nsm, ctx->fp32);
+    Prof p(ctx, UGKS_PROF_INTERP, s);
+    launch_interp(d, s, fresh ? d.fresh_list : d.rec_list, d.conn_cnt + (fresh ? 1 : 0), ctx->nsm, ctx->fp32,
+                  parts);
   }
   ctx->launches += 2;
   return UGKS_OK;
@@ -588,16 +597,21 @@ int upload_step_size(ugks_ctx *ctx) {
 
 // Ghost states, W gradients, face reduction, face coefficients, per-cell
 // macro flux sum (Steps 1 / 3 up to the velocity-resolved flux).
-int flux_prep(ugks_ctx *ctx, int level_n) {
+// joined: the W gradients ran on the tail stream (split tail); the face
+// state waits for them after the velocity reduction
+int flux_prep(ugks_ctx *ctx, int level_n, bool joined = false) {
   Dev &d = ctx->d;
   cudaStream_t s = ctx->st;
-  { Prof p(ctx, UGKS_PROF_CELL); launch_ghost_gradW(d, s); }
+  if (!joined) { Prof p(ctx, UGKS_PROF_CELL); launch_ghost_gradW(d, s); }
   { Prof p(ctx, UGKS_PROF_FACE_REDUCE); launch_face_reduce_tile(d, s, ctx->fp32, ctx->face_tile); }
   int r = shard_exchange(ctx, 0);
   if (r) return r;
+  if (joined) CK(cudaStreamWaitEvent(s, ctx->ev_tail, 0));
   { Prof p(ctx, UGKS_PROF_FACE_COEF); launch_face_coef(d, s, ctx->fp32); }
   { Prof p(ctx, UGKS_PROF_CELL); launch_cell_macro(d, s, level_n); }
-  ctx->launches += 6;
+  // ghost states and gradients (or the wait), reduction, face state and
+  // coefficients (the wall kernel where there are walls), cell terms
+  ctx->launches += (joined ? 0 : 2) + 1 + 2 + (d.nwall > 0 ? 1 : 0) + 1;
   return UGKS_OK;
 }
 
@@ -683,8 +697,15 @@ int step_body(ugks_ctx *ctx, int n_inner) {
   ctx->launches += 1;
   for (int it = 0; it < n_inner; ++it) {
     if (it > 0) {
-      do_interp(ctx, 0);
-      if ((rx = flux_prep(ctx, 0))) return rx;   // Step 3
+      if (ctx->split_tail) {
+        // the previous iteration's Step 7 is still running on the tail
+        // stream: interpolate the receptors' f, reduce, then join
+        do_interp(ctx, 0, 1);
+        if ((rx = flux_prep(ctx, 0, true))) return rx;   // Step 3
+      } else {
+        do_interp(ctx, 0);
+        if ((rx = flux_prep(ctx, 0))) return rx;   // Step 3
+      }
     }
     // Step 4 (macro LU-SGS) on the side stream, concurrently with the flux
     // divergence of Step 3 on the main stream; Step 5 joins both
@@ -701,6 +722,18 @@ int step_body(ugks_ctx *ctx, int n_inner) {
     if (met) launch_metrics(d, s, 1, fp);
     { Prof p(ctx, UGKS_PROF_MICRO_FWD); launch_wsweep(d, s, 0, ctx->work, ctx->nwork, ctx->sweep_nw, ctx->ns_fwd, ctx->sweep_vpt, fp, ctx->sweep_ql); }  // Step 6
     { Prof p(ctx, UGKS_PROF_MICRO_BWD); launch_wsweep(d, s, 1, ctx->work, ctx->nwork, ctx->sweep_nw, ctx->ns_bwd, ctx->sweep_vpt, fp, ctx->sweep_ql); }
+    if (ctx->split_tail && it + 1 < n_inner) {
+      // Step 7, the receptors' W and q and the W gradients of the next
+      // iteration on the tail stream, beside its velocity reduction
+      CK(cudaEventRecord(ctx->ev_bwd, s));
+      CK(cudaStreamWaitEvent(ctx->tail, ctx->ev_bwd, 0));
+      { Prof p(ctx, UGKS_PROF_MOMENTS, ctx->tail); launch_moments(d, ctx->tail, fp); }      // Step 7
+      do_interp(ctx, 0, 2, ctx->tail);
+      { Prof p(ctx, UGKS_PROF_CELL, ctx->tail); launch_gradW(d, ctx->tail); }
+      CK(cudaEventRecord(ctx->ev_tail, ctx->tail));
+      ctx->launches += 9;
+      continue;
+    }
     { Prof p(ctx, UGKS_PROF_MOMENTS); launch_moments(d, s, fp); }                          // Step 7
     if (d.shard) {
       if ((rx = shard_exchange(ctx, 1))) return rx;
@@ -720,7 +753,7 @@ int step_body(ugks_ctx *ctx, int n_inner) {
 // struct they take by value and the launch configuration.
 std::vector<unsigned char> graph_key(const ugks_ctx *c, int n_inner) {
   int cfg[] = {n_inner, c->fresh_pending ? 1 : 0, c->face_tile, c->sweep_vpt, c->ns_fwd, c->ns_bwd, c->sweep_nw,
-               c->sweep_ql, c->nwork, c->nsm, c->max_nj, c->fp32, c->metrics ? 1 : 0};
+               c->sweep_ql, c->nwork, c->nsm, c->max_nj, c->fp32, c->metrics ? 1 : 0, c->split_tail ? 1 : 0};
   // (the step size is read from device memory; the bin count belongs to the
   // assembly, which is not part of the step)
   Dev d = c->d;
@@ -835,8 +868,11 @@ int ugks_create(const ugks_params *p, void *workspace, size_t bytes, void *strea
   // stream the highest priority so its CTAs are placed as soon as a slot frees
   if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&c->tail, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_flux, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_macro, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c->ev_macro, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_bwd, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_tail, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     delete c;
     return UGKS_ERR_CUDA;
@@ -848,14 +884,18 @@ int ugks_create(const ugks_params *p, void *workspace, size_t bytes, void *strea
 int ugks_destroy(ugks_ctx *ctx) {
   if (ctx) {
     if (ctx->side) cudaStreamSynchronize(ctx->side);
+    if (ctx->tail) cudaStreamSynchronize(ctx->tail);
     if (ctx->st) cudaStreamSynchronize(ctx->st);
     for (auto &g : ctx->gcache)
       if (g.exec) cudaGraphExecDestroy(g.exec);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     if (ctx->ev_flux) cudaEventDestroy(ctx->ev_flux);
     if (ctx->ev_macro) cudaEventDestroy(ctx->ev_macro);
+    if (ctx->ev_bwd) cudaEventDestroy(ctx->ev_bwd);
+    if (ctx->ev_tail) cudaEventDestroy(ctx->ev_tail);
     if (ctx->side) cudaStreamDestroy(ctx->side);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    if (ctx->tail) cudaStreamDestroy(ctx->tail);
   }
   delete ctx;
   return UGKS_OK;
@@ -1082,6 +1122,12 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
   if ((r = up(ctx, (void *)d.face_a, T.face_a))) return r;
   if ((r = up(ctx, (void *)d.face_b, T.face_b))) return r;
   if ((r = up(ctx, (void *)d.face_kind, T.face_kind))) return r;
+  {
+    bool outflow = false;
+    for (int f = 0; f < s.nf; ++f) outflow = outflow || T.face_kind[f] == BC_OUTFLOW;
+    const char *e = getenv("UGKS_SERIAL_TAIL");      // 1: Step 7 and the gradients in line
+    ctx->split_tail = !outflow && !d.shard && !(e && atoi(e) != 0);
+  }
   {
     std::vector<int> wf;
     for (int f = 0; f < s.nf; ++f)

@@ -1386,6 +1386,7 @@ void launch_ghost_gradW(const Dev &d, cudaStream_t s) {
   k_ghost<<<nblk(d.nf, 256), 256, 0, s>>>(d);
   k_gradW<<<nblk(d.nc, 256), 256, 0, s>>>(d);
 }
+void launch_gradW(const Dev &d, cudaStream_t s) { k_gradW<<<nblk(d.nc, 256), 256, 0, s>>>(d); }
 void launch_face_coef(const Dev &d, cudaStream_t s, int fp32) {
   if (fp32) {
     k_face_scalar<float><<<nblk(d.nf, 128), 128, 0, s>>>(d);
@@ -1464,10 +1465,14 @@ void sweep_setup() {
 }
 
 void launch_moments_finish(const Dev &d, cudaStream_t s) { k_moments_finish<<<nblk(d.nc, 256), 256, 0, s>>>(d); }
+// Two cells (warps) a CTA: small CTAs fit beside the velocity reduction's
+// two CTAs an SM, with which this Step 7 runs concurrently.
+constexpr int MOM_THREADS = 64;
 void launch_moments(const Dev &d, cudaStream_t s, int fp32) {
-  if (fp32 && d.fbf) k_moments<float, 1><<<nblk((size_t)d.nc * 32, 256), 256, 0, s>>>(d);
-  else if (fp32) k_moments<float, 0><<<nblk((size_t)d.nc * 32, 256), 256, 0, s>>>(d);
-  else k_moments<double, 0><<<nblk((size_t)d.nc * 32, 256), 256, 0, s>>>(d);
+  int g = nblk((size_t)d.nc * 32, MOM_THREADS);
+  if (fp32 && d.fbf) k_moments<float, 1><<<g, MOM_THREADS, 0, s>>>(d);
+  else if (fp32) k_moments<float, 0><<<g, MOM_THREADS, 0, s>>>(d);
+  else k_moments<double, 0><<<g, MOM_THREADS, 0, s>>>(d);
 }
 void launch_init_state(const Dev &d, cudaStream_t s, const double *prim, int fp32) {
   if (fp32) k_init_state<float><<<nblk((size_t)d.nc * 32, 256), 256, 0, s>>>(d, prim);

@@ -9,6 +9,7 @@ void launch_move_nodes(const Dev &d, cudaStream_t s);
 void launch_geometry(const Dev &d, cudaStream_t s, int fp32);   // 4 kernels
 void launch_slope_geo(const Dev &d, cudaStream_t s);
 void launch_ghost_gradW(const Dev &d, cudaStream_t s);                      // 2 kernels
+void launch_gradW(const Dev &d, cudaStream_t s);                            // the gradients alone
 void launch_face_coef(const Dev &d, cudaStream_t s, int fp32);
 void launch_cell_macro(const Dev &d, cudaStream_t s, int level_n);
 void launch_cell_params(const Dev &d, cudaStream_t s, const double *W, double *out, int fp32);
@@ -36,7 +37,9 @@ void launch_f_convert(const Dev &d, cudaStream_t s, double *out, const double *i
 void launch_connect(const Dev &d, cudaStream_t s, int *prev_status, const int *blk_order,
                     int *n_orphan);                           // 9 kernels
 void launch_lists(const Dev &d, cudaStream_t s, const int *fresh_flag, const int *n_orphan);  // 2 kernels
-void launch_interp(const Dev &d, cudaStream_t s, const int *list, const int *cnt, int nsm, int fp32);  // 2 kernels
+// parts: 1 the distributions, 2 W and q, 3 both
+void launch_interp(const Dev &d, cudaStream_t s, const int *list, const int *cnt, int nsm, int fp32,
+                   int parts = 3);   // 2 kernels
 // tiled kernels (ugks_tile.cu)
 void tile_setup();
 int tile_count(int ni, int nj);

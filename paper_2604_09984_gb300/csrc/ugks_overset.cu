@@ -521,25 +521,30 @@ __global__ void __launch_bounds__(LCHUNK) k_list_write(Dev d, const int *fresh_f
 // Jacobi interpolation: gather into staging, then scatter.  The list length
 // is read on the device (*cnt, clamped to the staging capacity); a fixed grid
 // strides over it.
-template <typename T> __global__ void k_interp_gather(Dev d, const int *list, const int *cnt) {
+// parts: bit 0 the distributions, bit 1 W and q (the two may run apart: the
+// distributions right after the micro sweep, W and q after Step 7)
+template <typename T> __global__ void k_interp_gather(Dev d, const int *list, const int *cnt, int parts) {
   int n = min(*cnt, d.cap_interp);
-  size_t tot = (size_t)n * d.nvp;
+  size_t nk = (parts & 1) ? (size_t)d.nvp : 1;
+  size_t tot = (size_t)n * nk;
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (size_t)gridDim.x * blockDim.x) {
-    int r = (int)(t / d.nvp), k = (int)(t % d.nvp);
+    int r = (int)(t / nk), k = (int)(t % nk);
     int c = list[r];
-    // f in the arithmetic type (its storage type): FP32 weights and sums on
-    // the mixed path keep the FP64 pipe out of the per-velocity loop
-    T ah = T(0), ab = T(0);
-    for (int m = 0; m < 5; ++m) {
-      int e = d.donors[5 * c + m];
-      if (e < 0) continue;
-      T w = (T)d.dwgt[5 * c + m];
-      auto v = ldF<T>(d, (size_t)e * d.nvp + k);
-      ah = ah + w * v.x;
-      ab = ab + w * v.y;
+    if (parts & 1) {
+      // f in the arithmetic type (its storage type): FP32 weights and sums on
+      // the mixed path keep the FP64 pipe out of the per-velocity loop
+      T ah = T(0), ab = T(0);
+      for (int m = 0; m < 5; ++m) {
+        int e = d.donors[5 * c + m];
+        if (e < 0) continue;
+        T w = (T)d.dwgt[5 * c + m];
+        auto v = ldF<T>(d, (size_t)e * d.nvp + k);
+        ah = ah + w * v.x;
+        ab = ab + w * v.y;
+      }
+      stf<T>(d.itmp, (size_t)r * d.nvp + k, ah, ab);
     }
-    stf<T>(d.itmp, t, ah, ab);
-    if (k == 0) {
+    if ((parts & 2) && k == 0) {
       double acc[6] = {0, 0, 0, 0, 0, 0};
       for (int m = 0; m < 5; ++m) {
         int e = d.donors[5 * c + m];
@@ -554,16 +559,19 @@ template <typename T> __global__ void k_interp_gather(Dev d, const int *list, co
   }
 }
 
-template <typename T> __global__ void k_interp_scatter(Dev d, const int *list, const int *cnt) {
+template <typename T> __global__ void k_interp_scatter(Dev d, const int *list, const int *cnt, int parts) {
   int n = min(*cnt, d.cap_interp);
-  size_t tot = (size_t)n * d.nvp;
+  size_t nk = (parts & 1) ? (size_t)d.nvp : 1;
+  size_t tot = (size_t)n * nk;
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (size_t)gridDim.x * blockDim.x) {
-    int r = (int)(t / d.nvp), k = (int)(t % d.nvp);
+    int r = (int)(t / nk), k = (int)(t % nk);
     int c = list[r];
     if (d.donors[5 * c] < 0) continue;          // orphan: keep its values
-    auto v = ldf<T>(d.itmp, t);
-    stF<T>(d, (size_t)c * d.nvp + k, v.x, v.y);
-    if (k == 0) {
+    if (parts & 1) {
+      auto v = ldf<T>(d.itmp, (size_t)r * d.nvp + k);
+      stF<T>(d, (size_t)c * d.nvp + k, v.x, v.y);
+    }
+    if ((parts & 2) && k == 0) {
       for (int q = 0; q < 4; ++q) d.W[4 * c + q] = d.itmpW[6 * r + q];
       d.q[2 * c] = d.itmpW[6 * r + 4];
       d.q[2 * c + 1] = d.itmpW[6 * r + 5];
@@ -595,15 +603,15 @@ void launch_lists(const Dev &d, cudaStream_t s, const int *fresh_flag, const int
   k_list_write<<<nch, LCHUNK, 0, s>>>(d, fresh_flag, n_orphan);
 }
 
-void launch_interp(const Dev &d, cudaStream_t s, const int *list, const int *cnt, int nsm, int fp32) {
-  size_t tot = (size_t)d.cap_interp * d.nvp;
+void launch_interp(const Dev &d, cudaStream_t s, const int *list, const int *cnt, int nsm, int fp32, int parts) {
+  size_t tot = (size_t)d.cap_interp * ((parts & 1) ? d.nvp : 1);
   int grid = std::max(1, std::min(nblk(tot, 256), 8 * std::max(nsm, 1)));
   if (fp32) {
-    k_interp_gather<float><<<grid, 256, 0, s>>>(d, list, cnt);
-    k_interp_scatter<float><<<grid, 256, 0, s>>>(d, list, cnt);
+    k_interp_gather<float><<<grid, 256, 0, s>>>(d, list, cnt, parts);
+    k_interp_scatter<float><<<grid, 256, 0, s>>>(d, list, cnt, parts);
   } else {
-    k_interp_gather<double><<<grid, 256, 0, s>>>(d, list, cnt);
-    k_interp_scatter<double><<<grid, 256, 0, s>>>(d, list, cnt);
+    k_interp_gather<double><<<grid, 256, 0, s>>>(d, list, cnt, parts);
+    k_interp_scatter<double><<<grid, 256, 0, s>>>(d, list, cnt, parts);
   }
 }
 

@@ -48,3 +48,29 @@ def test_graph_replay_matches_direct_launches(prec):
     for a, b in zip(g.moments(), n.moments()):
         assert np.array_equal(a, b)
     assert torch.equal(g.get_state()[0], n.get_state()[0])
+
+
+@pytest.mark.parametrize("prec", [U.FP32, U.FP64])
+def test_split_tail_matches_serial_tail(prec):
+    """Step 7, the receptors' W and q and the W gradients of an inner
+    iteration run on the side stream beside the next iteration's velocity
+    reduction; the result equals, bit for bit, the same step with that tail
+    in line on the main stream (UGKS_SERIAL_TAIL=1), with and without graphs."""
+    case = wl.mems(nbi=48, nbj=24, noi=32, noj=12, nv=8, stretch=1.15, n_inner=3)
+    prim = wl.random_prim(case, 17, amp_rho=0.05, amp_u=0.05, amp_T=0.05)
+    split = U.Solver(case, prec, prim=prim)
+    os.environ["UGKS_SERIAL_TAIL"] = "1"
+    try:
+        serial = U.Solver(case, prec, prim=prim)
+    finally:
+        del os.environ["UGKS_SERIAL_TAIL"]
+    direct = U.Solver(case, prec, prim=prim)
+    direct.set_graphs(False)
+    for _ in range(3):
+        for s in (split, serial, direct):
+            s.advance()
+    ref = serial.moments()
+    for s in (split, direct):
+        for a, b in zip(s.moments(), ref):
+            assert np.array_equal(a, b)
+        assert torch.equal(s.get_state()[0], serial.get_state()[0])

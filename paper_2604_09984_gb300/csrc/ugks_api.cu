@@ -29,6 +29,9 @@ struct ugks_ctx {
   // (which reads none of them); not where an outflow ghost state follows W
   // or on a velocity shard (whose Step 7 waits for the host exchange)
   bool split_tail = false;
+  // FP32 path: the residual's predictor-free part beside the macro sweep
+  // (on the FP64 path the flux pass alone outlasts the sweep)
+  bool split_residual = false;
   char *ws = nullptr;
   size_t ws_bytes = 0;
   Dev d;
@@ -717,8 +720,16 @@ int step_body(ugks_ctx *ctx, int n_inner) {
     { Prof p(ctx, UGKS_PROF_MACRO_SWEEP, ctx->side); launch_macro_sweep(d, ctx->side, ctx->max_nj, fp); }
     CK(cudaEventRecord(ctx->ev_macro, ctx->side));
     { Prof p(ctx, UGKS_PROF_RHS); launch_flux_tile(d, s, fp, ctx->face_tile); }              // Step 3
-    CK(cudaStreamWaitEvent(s, ctx->ev_macro, 0));
-    { Prof p(ctx, UGKS_PROF_RESIDUAL); launch_residual(d, s, it == 0, fp); }                 // Step 5
+    if (ctx->split_residual) {
+      // Step 5 without the predictor's collision term while the sweep runs
+      { Prof p(ctx, UGKS_PROF_RESIDUAL); launch_residual(d, s, it == 0, fp, 1); }
+      CK(cudaStreamWaitEvent(s, ctx->ev_macro, 0));
+      { Prof p(ctx, UGKS_PROF_RESIDUAL); launch_residual(d, s, it == 0, fp, 2); }
+      ctx->launches += 1;
+    } else {
+      CK(cudaStreamWaitEvent(s, ctx->ev_macro, 0));
+      { Prof p(ctx, UGKS_PROF_RESIDUAL); launch_residual(d, s, it == 0, fp); }               // Step 5
+    }
     if (met) launch_metrics(d, s, 1, fp);
     { Prof p(ctx, UGKS_PROF_MICRO_FWD); launch_wsweep(d, s, 0, ctx->work, ctx->nwork, ctx->sweep_nw, ctx->ns_fwd, ctx->sweep_vpt, fp, ctx->sweep_ql); }  // Step 6
     { Prof p(ctx, UGKS_PROF_MICRO_BWD); launch_wsweep(d, s, 1, ctx->work, ctx->nwork, ctx->sweep_nw, ctx->ns_bwd, ctx->sweep_vpt, fp, ctx->sweep_ql); }
@@ -753,7 +764,8 @@ int step_body(ugks_ctx *ctx, int n_inner) {
 // struct they take by value and the launch configuration.
 std::vector<unsigned char> graph_key(const ugks_ctx *c, int n_inner) {
   int cfg[] = {n_inner, c->fresh_pending ? 1 : 0, c->face_tile, c->sweep_vpt, c->ns_fwd, c->ns_bwd, c->sweep_nw,
-               c->sweep_ql, c->nwork, c->nsm, c->max_nj, c->fp32, c->metrics ? 1 : 0, c->split_tail ? 1 : 0};
+               c->sweep_ql, c->nwork, c->nsm, c->max_nj, c->fp32, c->metrics ? 1 : 0, c->split_tail ? 1 : 0,
+               c->split_residual ? 1 : 0};
   // (the step size is read from device memory; the bin count belongs to the
   // assembly, which is not part of the step)
   Dev d = c->d;
@@ -1127,6 +1139,8 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
     for (int f = 0; f < s.nf; ++f) outflow = outflow || T.face_kind[f] == BC_OUTFLOW;
     const char *e = getenv("UGKS_SERIAL_TAIL");      // 1: Step 7 and the gradients in line
     ctx->split_tail = !outflow && !d.shard && !(e && atoi(e) != 0);
+    const char *e1 = getenv("UGKS_RESIDUAL_ONE_PASS");   // 1: the residual in one pass
+    ctx->split_residual = ctx->fp32 && !(e1 && atoi(e1) != 0);
   }
   {
     std::vector<int> wf;

@@ -47,7 +47,9 @@ void tile_origins(int ni, int nj, int *out);
 // face kernels: `tile` indexes the tile shapes (velocities per chunk, threads
 // per face slot) of face_tile_shape; the FP64 path has one shape
 void launch_flux_tile(const Dev &d, cudaStream_t s, int fp32, int tile);
-void launch_residual(const Dev &d, cudaStream_t s, int first_iter, int fp32);
+// part 0: the residual in one pass; 1: its part without the predictor W'
+// (beside the macro sweep); 2: the collision term at W' added (after it)
+void launch_residual(const Dev &d, cudaStream_t s, int first_iter, int fp32, int part = 0);
 void launch_face_reduce_tile(const Dev &d, cudaStream_t s, int fp32, int tile);
 int face_tile_count();
 int face_tile_default();

@@ -725,6 +725,70 @@ template <typename T, int FB> __global__ void k_residual(Dev d, int first_iter) 
   }
 }
 
+// The residual in two passes (FP32 path): the part without the predictor W'
+// of Step 4, P = T_n - Omega^{n+1} f / dt - D / 2, runs right after the flux
+// divergence, beside the macro LU-SGS (the level-n term T_n is formed and
+// stored on the first inner iteration); after the macro sweep the second
+// pass adds the collision term at W': r = P + Omega^{n+1} (f+(W') - f) / (2 tau').
+template <typename T, int FB> __global__ void k_residual_pre(Dev d, int first_iter) {
+  typedef typename Vec2<T>::type T2;
+  int c = blockIdx.x, k0 = 2 * (blockIdx.y * blockDim.x + threadIdx.x);
+  if (k0 >= d.nv || !(d.cmask[c] & 1)) return;
+  T vol1 = (T)d.vol_new[c];                 // the value the cell record holds
+  T idt = sizeof(T) == 4 ? (T)(float)d.stepc[2] : (T)d.stepc[1];
+  const T *cn = reinterpret_cast<const T *>(d.shn) + (size_t)NSH * c;
+  T2 fv[2], D[2], tn[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    size_t t = (size_t)c * d.nvp + k0 + u;
+    fv[u] = ldF<T, FB>(d, t);
+    D[u] = ldf<T>(d.Dbuf, t);
+    if (!first_iter) tn[u] = ldf<T>(d.Tn, t);
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    int k = k0 + u;
+    if (k >= d.nv) break;
+    size_t t = (size_t)c * d.nvp + k;
+    if (first_iter) {
+      T vx = dvx<T>(d, k), vy = dvy<T>(d, k);
+      T itn = cn[SH_ITAU];
+      V2<T> fn = shakhov_rec<T>(cn, vx, vy, (T)d.Keff, (T)d.Kint);
+      T vol0 = cn[SH_VOL];
+      tn[u].x = vol0 * idt * fv[u].x + T(0.5) * (vol0 * (fn.h - fv[u].x) * itn - D[u].x);
+      tn[u].y = vol0 * idt * fv[u].y + T(0.5) * (vol0 * (fn.b - fv[u].y) * itn - D[u].y);
+      stf<T>(d.Tn, t, tn[u].x, tn[u].y);
+    }
+    stf<T>(d.dfs, t, tn[u].x - vol1 * idt * fv[u].x - T(0.5) * D[u].x,
+           tn[u].y - vol1 * idt * fv[u].y - T(0.5) * D[u].y);
+  }
+}
+
+template <typename T, int FB> __global__ void k_residual_post(Dev d) {
+  typedef typename Vec2<T>::type T2;
+  int c = blockIdx.x, k0 = 2 * (blockIdx.y * blockDim.x + threadIdx.x);
+  if (k0 >= d.nv || !(d.cmask[c] & 1)) return;
+  const T *cp = reinterpret_cast<const T *>(d.shp) + (size_t)NSH * c;
+  T itau = cp[SH_ITAU];
+  T hv = T(0.5) * cp[SH_VOL];
+  T2 fv[2], P[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    size_t t = (size_t)c * d.nvp + k0 + u;
+    fv[u] = ldF<T, FB>(d, t);
+    P[u] = ldf<T>(d.dfs, t);
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    int k = k0 + u;
+    if (k >= d.nv) break;
+    T vx = dvx<T>(d, k), vy = dvy<T>(d, k);
+    V2<T> fp = shakhov_rec<T>(cp, vx, vy, (T)d.Keff, (T)d.Kint);
+    stf<T>(d.dfs, (size_t)c * d.nvp + k, P[u].x + hv * (fp.h - fv[u].x) * itau,
+           P[u].y + hv * (fp.b - fv[u].y) * itau);
+  }
+}
+
 template <typename T, typename C> static size_t flux_smem() {
   return flux_fv_bytes<T, C>() + flux_fs_bytes<T, C>() + sizeof(typename Vec4<T>::type) * TX * TY +
          sizeof(typename Vec2<T>::type) * 2 * C::VK + 2 * sizeof(unsigned long long) + sizeof(int) * TX * TY;
@@ -796,11 +860,19 @@ void launch_flux_tile(const Dev &d, cudaStream_t s, int fp32, int tile) { face_d
 void launch_face_reduce_tile(const Dev &d, cudaStream_t s, int fp32, int tile) {
   face_dispatch(d, s, 0, fp32, tile);
 }
-void launch_residual(const Dev &d, cudaStream_t s, int first_iter, int fp32) {
+void launch_residual(const Dev &d, cudaStream_t s, int first_iter, int fp32, int part) {
   int pairs = (d.nv + 1) / 2;
   int bt = pairs >= 256 ? 256 : ((pairs + 31) / 32) * 32;
   dim3 grid(d.nc, (pairs + bt - 1) / bt);
-  if (fp32 && d.fbf) k_residual<float, 1><<<grid, bt, 0, s>>>(d, first_iter);
+  if (part == 1) {
+    if (fp32 && d.fbf) k_residual_pre<float, 1><<<grid, bt, 0, s>>>(d, first_iter);
+    else if (fp32) k_residual_pre<float, 0><<<grid, bt, 0, s>>>(d, first_iter);
+    else k_residual_pre<double, 0><<<grid, bt, 0, s>>>(d, first_iter);
+  } else if (part == 2) {
+    if (fp32 && d.fbf) k_residual_post<float, 1><<<grid, bt, 0, s>>>(d);
+    else if (fp32) k_residual_post<float, 0><<<grid, bt, 0, s>>>(d);
+    else k_residual_post<double, 0><<<grid, bt, 0, s>>>(d);
+  } else if (fp32 && d.fbf) k_residual<float, 1><<<grid, bt, 0, s>>>(d, first_iter);
   else if (fp32) k_residual<float, 0><<<grid, bt, 0, s>>>(d, first_iter);
   else k_residual<double, 0><<<grid, bt, 0, s>>>(d, first_iter);
 }

@@ -691,6 +691,9 @@ int step_body(ugks_ctx *ctx, int n_inner) {
   Dev &d = ctx->d;
   cudaStream_t s = ctx->st;
   int fp = ctx->fp32;
+  // per-kernel event timing wants each group alone on its stream: profiled
+  // steps run the tail in line
+  const bool split = ctx->split_tail && !ctx->prof_on;
   if (ctx->fresh_pending) do_interp(ctx, 1);
   do_interp(ctx, 0);
   // Steps 1-2: level-n flux, extensive level-n macro term, level-n cell record
@@ -700,7 +703,7 @@ int step_body(ugks_ctx *ctx, int n_inner) {
   ctx->launches += 1;
   for (int it = 0; it < n_inner; ++it) {
     if (it > 0) {
-      if (ctx->split_tail) {
+      if (split) {
         // the previous iteration's Step 7 is still running on the tail
         // stream: interpolate the receptors' f, reduce, then join
         do_interp(ctx, 0, 1);
@@ -733,7 +736,7 @@ int step_body(ugks_ctx *ctx, int n_inner) {
     if (met) launch_metrics(d, s, 1, fp);
     { Prof p(ctx, UGKS_PROF_MICRO_FWD); launch_wsweep(d, s, 0, ctx->work, ctx->nwork, ctx->sweep_nw, ctx->ns_fwd, ctx->sweep_vpt, fp, ctx->sweep_ql); }  // Step 6
     { Prof p(ctx, UGKS_PROF_MICRO_BWD); launch_wsweep(d, s, 1, ctx->work, ctx->nwork, ctx->sweep_nw, ctx->ns_bwd, ctx->sweep_vpt, fp, ctx->sweep_ql); }
-    if (ctx->split_tail && it + 1 < n_inner) {
+    if (split && it + 1 < n_inner) {
       // Step 7, the receptors' W and q and the W gradients of the next
       // iteration on the tail stream, beside its velocity reduction
       CK(cudaEventRecord(ctx->ev_bwd, s));

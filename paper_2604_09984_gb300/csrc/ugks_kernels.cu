@@ -792,8 +792,16 @@ __device__ __forceinline__ void macro_off_v(float4 s0, float4 s1, float gam, flo
   macro_off(rr, dv, Keff, out);
 }
 
-template <int NS, int TPR> __global__ void __launch_bounds__(512) k_macro_sweep_f32(Dev d, float *rec) {
-  constexpr int NSL = 4 / TPR;                  // face slots per thread
+// PM (with TPR = 2): the two threads of a row take the two face slots that
+// couple in this pass -- forward the lower neighbours (slots 0 and 2),
+// backward the upper ones (1 and 3) -- and the first thread also the
+// periodic wrap slot (1 forward at i = n_i - 1, 0 backward at i = 0) where it
+// applies; couplings that are not evaluated are exact zeros in the TPR = 4
+// form, so the sums are the same.
+template <int NS, int TPR, bool PM = false>
+__global__ void __launch_bounds__(512) k_macro_sweep_f32(Dev d, float *rec) {
+  static_assert(!PM || TPR == 2, "pass-dependent slots pair two threads a row");
+  constexpr int NSL = PM ? 1 : 4 / TPR;         // face slots per thread (PM: plus the wrap)
   constexpr int NSR_ = NS > 0 ? NS : 1;
   extern __shared__ __align__(16) float smf[];
   unsigned long long *mb = reinterpret_cast<unsigned long long *>(smf);   // one mbarrier per stage
@@ -820,6 +828,11 @@ template <int NS, int TPR> __global__ void __launch_bounds__(512) k_macro_sweep_
   int issued = -1, waited = -1;      // thread 0: last stage copied into / waited for
   for (int pass = 0; pass < 2; ++pass) {
     float4 prev = make_float4(0.f, 0.f, 0.f, 0.f), first = prev;
+    // face slot of this thread's q-th coupling
+    auto slot_of = [&](int q) {
+      if (!PM) return q * TPR + sub;
+      return sub == 0 ? (pass == 0 ? 0 : 1) : (pass == 0 ? 2 : 3);
+    };
     // diagonal of step it, and its position in the ring (g = steps so far)
     auto diag_of = [&](int it) { return pass == 0 ? it : nd - 1 - it; };
     auto gstep = [&](int it) { return pass * nd + it; };
@@ -855,7 +868,7 @@ template <int NS, int TPR> __global__ void __launch_bounds__(512) k_macro_sweep_
       nmask = __float_as_int(r[M32_MASK]);
 #pragma unroll
       for (int q = 0; q < NSL; ++q) {
-        const float *sr = r + M32_SLOT + M32_SW * (q * TPR + sub);
+        const float *sr = r + M32_SLOT + M32_SW * slot_of(q);
         nsa[q] = *reinterpret_cast<const float4 *>(sr);
         nsb[q] = *reinterpret_cast<const float4 *>(sr + 4);
         ngam[q] = sr[8];
@@ -880,22 +893,39 @@ template <int NS, int TPR> __global__ void __launch_bounds__(512) k_macro_sweep_
         float acc[4] = {0, 0, 0, 0};
 #pragma unroll
         for (int q = 0; q < NSL; ++q) {
-          int s = q * TPR + sub;
+          int s = slot_of(q);
           float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
+          bool use = !PM;                        // PM: only the couplings of this pass
           if (mask & (2 << s)) {
             if (pass == 0) {
-              if (s == 0 && i > 0) dv = prev;
-              else if (s == 1 && per && i == ni - 1) dv = first;
-              else if (s == 2 && row > 0) dv = *reinterpret_cast<const float4 *>(prv + 4 * (row - 1));
+              if (s == 0 && i > 0) { dv = prev; use = true; }
+              else if (s == 1 && per && i == ni - 1) { dv = first; use = true; }
+              else if (s == 2 && row > 0) { dv = *reinterpret_cast<const float4 *>(prv + 4 * (row - 1)); use = true; }
             } else {
-              if (s == 1 && i < ni - 1) dv = prev;
-              else if (s == 0 && per && i == 0) dv = first;
-              else if (s == 3 && row < nj - 1) dv = *reinterpret_cast<const float4 *>(prv + 4 * (row + 1));
+              if (s == 1 && i < ni - 1) { dv = prev; use = true; }
+              else if (s == 0 && per && i == 0) { dv = first; use = true; }
+              else if (s == 3 && row < nj - 1) { dv = *reinterpret_cast<const float4 *>(prv + 4 * (row + 1)); use = true; }
             }
           }
+          if (use) {
+            float o[4];
+            macro_off_v(nsa[q], nsb[q], ngam[q], dv, d.Keff, o);
+            // a plain (never contracted) sum: the same bits as the lanes'
+            // shuffle sums of the four-slot form
+            for (int m = 0; m < 4; ++m) acc[m] = __fadd_rn(acc[m], o[m]);
+          }
+        }
+        // PM: the periodic wrap (slot 1 forward at i = n_i - 1, slot 0
+        // backward at i = 0), rare: its record is read where it lies (the
+        // ring stage of this step is not reissued before the next step)
+        if (PM && sub == 0 && per && i == (pass == 0 ? ni - 1 : 0) && (mask & (2 << (pass == 0 ? 1 : 0)))) {
+          const float *r = NS > 0 ? ring + ((size_t)(gstep(it) % NSR_) * rows + row) * NMR32
+                                  : rb + ((size_t)t * nj + row) * NMR32;
+          const float *sr = r + M32_SLOT + M32_SW * (pass == 0 ? 1 : 0);
           float o[4];
-          macro_off_v(nsa[q], nsb[q], ngam[q], dv, d.Keff, o);
-          for (int m = 0; m < 4; ++m) acc[m] += o[m];
+          macro_off_v(*reinterpret_cast<const float4 *>(sr), *reinterpret_cast<const float4 *>(sr + 4), sr[8],
+                      first, d.Keff, o);
+          for (int m = 0; m < 4; ++m) acc[m] = __fadd_rn(acc[m], o[m]);
         }
 #pragma unroll
         for (int w = 1; w < TPR; w <<= 1)
@@ -1424,17 +1454,23 @@ void launch_macro_sweep(const Dev &d, cudaStream_t s, int rows, int fp32) {
     size_t base = (MACRO_SMEM_HEAD + 8 * (size_t)rows) * sizeof(float);
     int NS = (int)((kMacroSmem - base) / per);
     NS = NS > 4 ? 4 : (NS < 2 ? 0 : NS);
-    int tpr = rows <= 128 ? 4 : (rows <= 256 ? 2 : 1);
-    if (const char *env = getenv("UGKS_MACRO_TPR")) {   // tuning: threads per row (1, 2 or 4)
+    // two threads a row on the slots of the pass (PM) where the rows fit
+    int tpr = rows <= 256 ? 2 : 1;
+    bool pm = tpr == 2;
+    if (const char *env = getenv("UGKS_MACRO_TPR")) {   // tuning: threads per row (1, 2 or 4; plain slots)
       int t = atoi(env);
-      if ((t == 1 || t == 2 || t == 4) && t * rows <= 512) tpr = t;
+      if ((t == 1 || t == 2 || t == 4) && t * rows <= 512) { tpr = t; pm = false; }
     }
     // the whole shared memory of an SM: the sweep's SMs take no CTA of the
     // kernels running beside it on the main stream
     size_t sm = kMacroSmem;
     int th = tpr * rows;
 #define UGKS_MACRO_F32(ns, tp) k_macro_sweep_f32<ns, tp><<<d.nblocks, th, sm, s>>>(d, rec)
-    if (tpr == 4) {
+#define UGKS_MACRO_PM(ns) k_macro_sweep_f32<ns, 2, true><<<d.nblocks, th, sm, s>>>(d, rec)
+    if (pm) {
+      if (NS == 4) UGKS_MACRO_PM(4); else if (NS == 3) UGKS_MACRO_PM(3);
+      else if (NS == 2) UGKS_MACRO_PM(2); else UGKS_MACRO_PM(0);
+    } else if (tpr == 4) {
       if (NS == 4) UGKS_MACRO_F32(4, 4); else if (NS == 3) UGKS_MACRO_F32(3, 4);
       else if (NS == 2) UGKS_MACRO_F32(2, 4); else UGKS_MACRO_F32(0, 4);
     } else if (tpr == 2) {
@@ -1445,6 +1481,7 @@ void launch_macro_sweep(const Dev &d, cudaStream_t s, int rows, int fp32) {
       else if (NS == 2) UGKS_MACRO_F32(2, 1); else UGKS_MACRO_F32(0, 1);
     }
 #undef UGKS_MACRO_F32
+#undef UGKS_MACRO_PM
   } else {
     double *rec = reinterpret_cast<double *>(d.mrec);
     k_macro_sweep<double><<<d.nblocks, rows, kMacroSmem, s>>>(d, rec);
@@ -1462,6 +1499,10 @@ void sweep_setup() {
   UGKS_MACRO_ATTR(4, 2); UGKS_MACRO_ATTR(3, 2); UGKS_MACRO_ATTR(2, 2); UGKS_MACRO_ATTR(0, 2);
   UGKS_MACRO_ATTR(4, 1); UGKS_MACRO_ATTR(3, 1); UGKS_MACRO_ATTR(2, 1); UGKS_MACRO_ATTR(0, 1);
 #undef UGKS_MACRO_ATTR
+#define UGKS_MACRO_ATTR_PM(ns) \
+  cudaFuncSetAttribute(k_macro_sweep_f32<ns, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ms)
+  UGKS_MACRO_ATTR_PM(4); UGKS_MACRO_ATTR_PM(3); UGKS_MACRO_ATTR_PM(2); UGKS_MACRO_ATTR_PM(0);
+#undef UGKS_MACRO_ATTR_PM
 }
 
 void launch_moments_finish(const Dev &d, cudaStream_t s) { k_moments_finish<<<nblk(d.nc, 256), 256, 0, s>>>(d); }

@@ -16,6 +16,12 @@
 
 using namespace ugks;
 
+// (cell, velocity) items per diagonal step of the longest macro sweep below
+// which the flux pass plus the residual's first pass end within the sweep,
+// from the rates measured on GB300: ~1.0e-11 s and ~4.8e-12 s per item for
+// the two, ~0.8 us per diagonal step of the sweep
+constexpr double kResidualWindow = 5.3e4;
+
 struct ugks_ctx {
   ugks_params p;
   cudaStream_t st = nullptr;
@@ -29,9 +35,13 @@ struct ugks_ctx {
   // (which reads none of them); not where an outflow ghost state follows W
   // or on a velocity shard (whose Step 7 waits for the host exchange)
   bool split_tail = false;
-  // FP32 path: the residual's predictor-free part beside the macro sweep
-  // (on the FP64 path the flux pass alone outlasts the sweep)
+  // FP32 path: the residual's predictor-free part beside the macro sweep,
+  // where the flux pass and that part end within the sweep (not on the FP64
+  // path, where the flux pass alone outlasts it, nor for velocity grids large
+  // against the sweep's length); not within a batch of several instances,
+  // whose other steps fill the SMs the sweep leaves
   bool split_residual = false;
+  bool in_batch = false;
   char *ws = nullptr;
   size_t ws_bytes = 0;
   Dev d;
@@ -723,7 +733,7 @@ int step_body(ugks_ctx *ctx, int n_inner) {
     { Prof p(ctx, UGKS_PROF_MACRO_SWEEP, ctx->side); launch_macro_sweep(d, ctx->side, ctx->max_nj, fp); }
     CK(cudaEventRecord(ctx->ev_macro, ctx->side));
     { Prof p(ctx, UGKS_PROF_RHS); launch_flux_tile(d, s, fp, ctx->face_tile); }              // Step 3
-    if (ctx->split_residual) {
+    if (ctx->split_residual && !ctx->in_batch) {
       // Step 5 without the predictor's collision term while the sweep runs
       { Prof p(ctx, UGKS_PROF_RESIDUAL); launch_residual(d, s, it == 0, fp, 1); }
       CK(cudaStreamWaitEvent(s, ctx->ev_macro, 0));
@@ -768,7 +778,7 @@ int step_body(ugks_ctx *ctx, int n_inner) {
 std::vector<unsigned char> graph_key(const ugks_ctx *c, int n_inner) {
   int cfg[] = {n_inner, c->fresh_pending ? 1 : 0, c->face_tile, c->sweep_vpt, c->ns_fwd, c->ns_bwd, c->sweep_nw,
                c->sweep_ql, c->nwork, c->nsm, c->max_nj, c->fp32, c->metrics ? 1 : 0, c->split_tail ? 1 : 0,
-               c->split_residual ? 1 : 0};
+               c->split_residual && !c->in_batch ? 1 : 0};
   // (the step size is read from device memory; the bin count belongs to the
   // assembly, which is not part of the step)
   Dev d = c->d;
@@ -1143,7 +1153,10 @@ int ugks_init_mesh(ugks_ctx *ctx, int nblocks, const ugks_block_desc *blocks, co
     const char *e = getenv("UGKS_SERIAL_TAIL");      // 1: Step 7 and the gradients in line
     ctx->split_tail = !outflow && !d.shard && !(e && atoi(e) != 0);
     const char *e1 = getenv("UGKS_RESIDUAL_ONE_PASS");   // 1: the residual in one pass
-    ctx->split_residual = ctx->fp32 && !(e1 && atoi(e1) != 0);
+    long steps = 0;                                       // diagonal steps of the longest macro sweep
+    for (int b = 0; b < nblocks; ++b) steps = std::max(steps, 2L * (blocks[b].ni + blocks[b].nj - 1));
+    double items = (double)s.nc * s.nv;
+    ctx->split_residual = ctx->fp32 && !(e1 && atoi(e1) != 0) && items < kResidualWindow * (double)steps;
   }
   {
     std::vector<int> wf;
@@ -1314,7 +1327,11 @@ int ugks_advance_batch(ugks_ctx *const *ctx, int n, const double *t_new, const d
       int r;
       if (stage == 0) r = ugks_move_mesh(c, t_new[i], affine[i]);
       else if (stage == 1) r = c->mesh_ready ? do_connect(c, nullptr, false, false) : UGKS_ERR_ORDER;
-      else r = ugks_step(c, c->d.dt, n_inner);
+      else {
+        c->in_batch = n > 1;
+        r = ugks_step(c, c->d.dt, n_inner);
+        c->in_batch = false;
+      }
       if (r) {
         if (failed) *failed = i;
         return r;

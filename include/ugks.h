@@ -316,7 +316,8 @@ int ugks_set_state(ugks_ctx *ctx, const double *f, const double *W, const double
  * is recomputed by the next ugks_move_mesh / ugks_overset_connect, so a
  * context restored from (f, W, q, t, nodes, status) continues bit for bit as
  * the one the checkpoint was taken from.  Only between steps (no pending
- * move).  `t`, `nodes`, `status` are HOST (each may be NULL on get);
+ * move).  Until that next step, the geometry, connectivity and wall-load
+ * accessors still describe this context's own last step.  `t`, `nodes`, `status` are HOST (each may be NULL on get);
  * ugks_get_checkpoint synchronises the stream.  Errors: UGKS_ERR_ORDER (a
  * move is pending), UGKS_ERR_ARG (null input on set). */
 int ugks_get_checkpoint(ugks_ctx *ctx, double *t, double *nodes, int32_t *status);

@@ -22,6 +22,9 @@ Modules
             (Sec. 2.2, Eqs. dualTimeStepping_macro/micro, Steps 1-8).
   overset   overset assembly (Sec. 3.1) and inverse-distance interpolation
             (Sec. 3.2).
+  adjoint   transposes of the step's linear operators (micro LU-SGS solve,
+            receptor interpolation, velocity moments): first pieces of a
+            discrete adjoint.
 
 Parity status
   Every function is pinned by ``tests/test_oracle_*.py`` against closed forms,

@@ -1,0 +1,126 @@
+"""Pins of the oracle's transposed operators (CPU only): each transpose A^T
+returned by ``oracle.adjoint`` satisfies <A x, y> = <x, A^T y> for random x,
+y against the forward operator of the oracle, and on a tiny mesh equals the
+transpose of the dense matrix assembled column by column from the forward
+operator (a transposed coupling, a wrong sweep order or a dropped diagonal
+scaling fails these)."""
+import numpy as np
+
+from oracle import adjoint, kinetic as kn, mesh, overset, ugks
+from oracle.ugks import FIELD, HOLE, RECEPTOR
+from paper_2604_09984_gb300 import workloads as wl
+
+
+def block(ni, nj, periodic):
+    return wl.BlockSpec(ni, nj, periodic, (0, 0, wl.BC_WALL, wl.BC_WALL), (0, 0, 1.0, 1.0),
+                        wl.cartesian_nodes(ni, nj, 0.0, 2.0, 0.0, 1.0))
+
+
+def setup_for(blocks, nv=4):
+    gas = kn.Gas(0, 2.0 / 3.0, 0.81, 0.05)
+    dvs = kn.make_dvs(nv, nv, -3.0, 3.0, -3.0, 3.0)
+    topo = mesh.Topology(blocks)
+    return ugks.Setup(topo, gas, dvs, kn.conservative(1.0, 0.0, 0.0, 0.5, gas))
+
+
+def moving_geo(setup, blocks, rng, dt=0.05):
+    X0 = [b.x_ref for b in blocks]
+    X1 = []
+    for b in blocks:
+        X = b.x_ref.copy()
+        X[..., 1] += 0.02 * np.sin(np.pi * X[..., 0]) * np.sin(np.pi * X[..., 1])
+        X1.append(X)
+    return mesh.geometry(setup.topo, X0, X1, dt)
+
+
+def micro_case(ni, nj, periodic, seed, holes=()):
+    rng = np.random.default_rng(seed)
+    blocks = [block(ni, nj, periodic)]
+    setup = setup_for(blocks)
+    geo = moving_geo(setup, blocks, rng)
+    wS = ugks.normal_velocity(setup, geo)
+    nc, nv = setup.topo.nc, setup.dvs.nv
+    status = np.full(nc, FIELD)
+    for c in holes:
+        status[c] = HOLE
+    outsum = np.zeros((nc, nv))
+    for d in range(4):
+        fid = setup.topo.cell_faces[:, d]
+        sgn = setup.topo.cell_face_sign[:, d]
+        outsum += np.maximum(sgn[:, None] * wS[fid], 0.0)
+    diag = geo.vol_new[:, None] * rng.uniform(5.0, 20.0, (nc, 1)) + 0.5 * outsum
+    return setup, wS, diag, status
+
+
+def field_random(rng, shape, status):
+    x = rng.standard_normal(shape)
+    x[status != FIELD] = 0.0
+    return x
+
+
+def test_micro_lusgs_transpose_dot_product():
+    for ni, nj, per, holes in ((5, 4, False, (7,)), (6, 3, True, (2, 9)), (2, 3, True, ())):
+        setup, wS, diag, status = micro_case(ni, nj, per, 3, holes)
+        rng = np.random.default_rng(11)
+        shape = (setup.topo.nc, setup.dvs.nv, 2)
+        x, y = field_random(rng, shape, status), field_random(rng, shape, status)
+        Mx = ugks.micro_lusgs(setup, wS, x, diag, status)
+        MTy = adjoint.micro_lusgs_transpose(setup, wS, y, diag, status)
+        lhs, rhs = (Mx * y).sum(), (x * MTy).sum()
+        assert abs(lhs - rhs) <= 1e-12 * (np.abs(Mx * y).sum() + np.abs(x * MTy).sum())
+        assert np.all(MTy[status != FIELD] == 0.0)
+
+
+def test_micro_lusgs_transpose_equals_dense_transpose():
+    # a periodic row of two cells: the two cells share two faces
+    for ni, nj, per in ((3, 2, False), (2, 2, True)):
+        setup, wS, diag, status = micro_case(ni, nj, per, 5)
+        nc, nv = setup.topo.nc, setup.dvs.nv
+        n = nc * nv * 2
+        A = np.zeros((n, n))
+        for col in range(n):
+            e = np.zeros(n)
+            e[col] = 1.0
+            A[:, col] = ugks.micro_lusgs(setup, wS, e.reshape(nc, nv, 2), diag, status).ravel()
+        y = np.random.default_rng(2).standard_normal(n)
+        got = adjoint.micro_lusgs_transpose(setup, wS, y.reshape(nc, nv, 2), diag, status).ravel()
+        np.testing.assert_allclose(got, A.T @ y, rtol=1e-12, atol=1e-14 * np.abs(A.T @ y).max())
+
+
+def test_interpolate_transpose_dot_product_and_dense():
+    rng = np.random.default_rng(4)
+    nc, nv = 12, 3
+    cells = np.array([1, 4, 7, 10])
+    donors = np.array([[0, 2, 5, -1, -1], [3, 5, 6, 8, -1], [-1, -1, -1, -1, -1], [9, 11, 1, 4, 0]])
+    weights = np.where(donors >= 0, rng.uniform(0.1, 1.0, donors.shape), 0.0)
+    weights /= np.maximum(weights.sum(1, keepdims=True), 1e-300)
+
+    def forward(f):
+        st = ugks.State(f.copy(), np.zeros((nc, 4)), np.zeros((nc, 2)))
+        overset.interpolate(st, cells, donors, weights)
+        return st.f
+
+    n = nc * nv * 2
+    A = np.zeros((n, n))
+    for col in range(n):
+        e = np.zeros(n)
+        e[col] = 1.0
+        A[:, col] = forward(e.reshape(nc, nv, 2)).ravel()
+    y = rng.standard_normal((nc, nv, 2))
+    got = adjoint.interpolate_transpose(y, cells, donors, weights)
+    np.testing.assert_allclose(got.ravel(), A.T @ y.ravel(), rtol=1e-13, atol=1e-15)
+    x = rng.standard_normal((nc, nv, 2))
+    assert abs((forward(x) * y).sum() - (x * got).sum()) < 1e-12 * np.abs(x * got).sum()
+    # the orphan row (third receptor) keeps its value and its cotangent
+    assert np.array_equal(got[7], y[7] + sum(weights[r, k] * y[cells[r]] for r in range(4)
+                                             for k in range(5) if donors[r, k] == 7))
+
+
+def test_moments_transpose_dot_product():
+    dvs = kn.make_dvs(5, 4, -3.0, 3.0, -2.0, 2.0)
+    rng = np.random.default_rng(6)
+    f = rng.standard_normal((7, dvs.nv, 2))
+    Wbar = rng.standard_normal((7, 4))
+    lhs = (kn.moments(f, dvs) * Wbar).sum()
+    rhs = (f * adjoint.moments_transpose(Wbar, dvs)).sum()
+    assert abs(lhs - rhs) < 1e-12 * (np.abs(f).sum() * np.abs(Wbar).sum())

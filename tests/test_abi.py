@@ -82,3 +82,17 @@ def test_batch_argument_validation(lib):
     aff = (ctypes.POINTER(ctypes.c_double) * 1)()
     assert lib.ugks_advance_batch(ctxs, 1, t, aff, 10, ctypes.byref(failed)) == -7
     assert failed.value == 0
+
+
+def test_null_context_is_rejected_without_cuda(lib):
+    """The checkpoint, metrics and graph entry points check their context
+    before any CUDA call: a null context is an argument or ordering error."""
+    t = ctypes.c_double(0.0)
+    m = U.StepMetrics()
+    assert lib.ugks_get_checkpoint(None, ctypes.byref(t), None, None) == -7
+    assert lib.ugks_set_checkpoint(None, 0.0, None, None) == -7
+    assert lib.ugks_set_metrics(None, 1) == -1
+    assert lib.ugks_get_metrics(None, ctypes.byref(m)) == -7
+    assert lib.ugks_set_graphs(None, 1) == -1
+    c, r = ctypes.c_int64(), ctypes.c_int64()
+    assert lib.ugks_graph_stats(None, ctypes.byref(c), ctypes.byref(r)) == -1

@@ -124,3 +124,76 @@ def test_moments_transpose_dot_product():
     lhs = (kn.moments(f, dvs) * Wbar).sum()
     rhs = (f * adjoint.moments_transpose(Wbar, dvs)).sum()
     assert abs(lhs - rhs) < 1e-12 * (np.abs(f).sum() * np.abs(Wbar).sum())
+
+
+def macro_case(ni, nj, per, seed, holes=()):
+    rng = np.random.default_rng(seed)
+    blocks = [block(ni, nj, per)]
+    setup = setup_for(blocks)
+    geo = moving_geo(setup, blocks, rng)
+    nc = setup.topo.nc
+    prim = np.empty((nc, 4))
+    prim[:, 0] = 1.0 + rng.uniform(-0.2, 0.2, nc)
+    prim[:, 1] = rng.uniform(-0.3, 0.3, nc)
+    prim[:, 2] = rng.uniform(-0.3, 0.3, nc)
+    prim[:, 3] = 1.0 + rng.uniform(-0.2, 0.2, nc)
+    W = kn.conservative(prim[:, 0], prim[:, 1], prim[:, 2], 1.0 / (2.0 * prim[:, 3]), setup.gas)
+    Gam = ugks.face_gamma(setup, geo, W)
+    status = np.full(nc, FIELD)
+    for c in holes:
+        status[c] = HOLE
+    gsum = np.zeros(nc)
+    for d in range(4):
+        gsum += geo.S[setup.topo.cell_faces[:, d]] * Gam[setup.topo.cell_faces[:, d]]
+    diag = geo.vol_new * rng.uniform(2.0, 6.0, nc) + 0.25 * gsum
+    # a right-hand side large enough that F_E(W + dW) is far from linear
+    R = rng.standard_normal((nc, 4)) * 0.2 * diag[:, None] * np.array([1.0, 0.5, 0.5, 1.5])
+    R[status != FIELD] = 0.0
+    return setup, geo, W, R, diag, Gam, status
+
+
+def test_euler_flux_jacobian_matches_central_differences():
+    gas = kn.Gas(0, 2.0 / 3.0, 0.81, 0.05)
+    rng = np.random.default_rng(8)
+    for _ in range(5):
+        W = kn.conservative(1.0 + rng.uniform(-0.3, 0.3), rng.uniform(-0.5, 0.5), rng.uniform(-0.5, 0.5),
+                            1.0 / (2.0 * (1.0 + rng.uniform(-0.3, 0.3))), gas)
+        th = rng.uniform(0, 2 * np.pi)
+        nx, ny, un = np.cos(th), np.sin(th), rng.uniform(-0.4, 0.4)
+        A = adjoint.euler_flux_jacobian(W, nx, ny, un, gas)
+        h = 1e-6
+        for j in range(4):
+            e = np.zeros(4)
+            e[j] = h * max(1.0, abs(W[j]))
+            fd = (ugks.euler_flux(W + e, nx, ny, un, gas) - ugks.euler_flux(W - e, nx, ny, un, gas)) / (2 * e[j])
+            np.testing.assert_allclose(A[:, j], fd, rtol=1e-7, atol=1e-8)
+
+
+def test_macro_lusgs_tangent_matches_central_differences():
+    for ni, nj, per, holes in ((5, 4, False, (6,)), (4, 3, True, ())):
+        setup, geo, W, R, diag, Gam, status = macro_case(ni, nj, per, 9, holes)
+        rng = np.random.default_rng(1)
+        dR = rng.standard_normal(R.shape) * np.abs(R).max()
+        dR[status != FIELD] = 0.0
+        t = adjoint.macro_lusgs_tangent(setup, geo, W, R, diag, Gam, status, dR)
+        h = 1e-5
+        fd = (ugks.macro_lusgs(setup, geo, W, R + h * dR, diag, Gam, status)
+              - ugks.macro_lusgs(setup, geo, W, R - h * dR, diag, Gam, status)) / (2 * h)
+        np.testing.assert_allclose(t, fd, rtol=1e-6, atol=1e-8 * np.abs(fd).max())
+        # the map is nonlinear here: the tangent at R differs from the one at 0
+        t0 = adjoint.macro_lusgs_tangent(setup, geo, W, 0.0 * R, diag, Gam, status, dR)
+        assert np.abs(t - t0).max() > 1e-4 * np.abs(t).max()
+
+
+def test_macro_lusgs_adjoint_dot_product():
+    for ni, nj, per, holes in ((5, 4, False, (6, 13)), (4, 3, True, ()), (2, 3, True, ())):
+        setup, geo, W, R, diag, Gam, status = macro_case(ni, nj, per, 10, holes)
+        rng = np.random.default_rng(3)
+        x, y = rng.standard_normal(R.shape), rng.standard_normal(R.shape)
+        x[status != FIELD] = 0.0
+        y[status != FIELD] = 0.0
+        Tx = adjoint.macro_lusgs_tangent(setup, geo, W, R, diag, Gam, status, x)
+        ATy = adjoint.macro_lusgs_adjoint(setup, geo, W, R, diag, Gam, status, y)
+        lhs, rhs = (Tx * y).sum(), (x * ATy).sum()
+        assert abs(lhs - rhs) <= 1e-12 * (np.abs(Tx * y).sum() + np.abs(x * ATy).sum()), (lhs, rhs)
+        assert np.all(ATy[status != FIELD] == 0.0)

@@ -23,8 +23,9 @@ Modules
   overset   overset assembly (Sec. 3.1) and inverse-distance interpolation
             (Sec. 3.2).
   adjoint   transposes of the step's linear operators (micro LU-SGS solve,
-            receptor interpolation, velocity moments) and the tangent and
-            adjoint of the macro LU-SGS: first pieces of a discrete adjoint.
+            receptor interpolation, velocity moments) and the tangents and
+            adjoints of the macro LU-SGS and of Step 7: first pieces of a
+            discrete adjoint.
 
 Parity status
   Every function is pinned by ``tests/test_oracle_*.py`` against closed forms,

@@ -36,6 +36,15 @@ i.e. A^T y for the linear map A the forward call applies:
                          tangent applies it to dR, the adjoint its transpose
                          (D + L')^{-T} D (D + U')^{-T} to a cotangent of dW.
 
+  moment_fix,            Step 7, W^{s+1} = W' + sum V Psi (f^{s+1} - g(W')),
+  moment_fix_tangent,    as a map of (W', f^{s+1}); the derivative of g(W')
+  moment_fix_adjoint     along dW' is (a.Psi) g with the micro slope a of
+                         int Psi (a.Psi) g = dW' (exact for the Maxwellian),
+                         so the tangent is dW' + sum V Psi (df - (a.Psi) g)
+                         and the adjoint returns (Wbar - G^T Wbar, the
+                         moments' transpose of Wbar) with G the 4 x 4 map
+                         dW' -> sum V Psi (a.Psi) g of each cell.
+
 The flux, the interface state and the geometry have no transpose here.
 """
 from __future__ import annotations
@@ -240,3 +249,36 @@ def macro_lusgs_adjoint(setup, geo, W, R, diag, Gam, status, ybar):
             acc -= J.T @ z[nb]
         z[c] = acc / diag[c]
     return z
+
+
+def moment_fix(setup, Wp, f):
+    """Step 7 of the oracle's step as a function: W' + sum V Psi (f - g(W'))."""
+    gas, dvs = setup.gas, setup.dvs
+    rho, Vx, Vy, lam = kn.primitive(Wp, gas)
+    g = kn.maxwellian(rho, Vx, Vy, lam, dvs, gas)
+    return Wp + kn.moments(f - g, dvs)
+
+
+def _fix_dg(setup, Wp, dWp):
+    gas, dvs = setup.gas, setup.dvs
+    rho, Vx, Vy, lam = kn.primitive(Wp, gas)
+    g = kn.maxwellian(rho, Vx, Vy, lam, dvs, gas)
+    return kn.slope_times_g(kn.micro_slope(Wp, dWp, gas), g, lam, dvs, gas)
+
+
+def moment_fix_tangent(setup, Wp, dWp, df):
+    """Derivative of ``moment_fix`` at (Wp, f) in the direction (dWp, df)."""
+    return dWp + kn.moments(df - _fix_dg(setup, Wp, dWp), setup.dvs)
+
+
+def moment_fix_adjoint(setup, Wp, Wbar):
+    """Cotangents (of W', of f) of ``moment_fix`` for a cotangent Wbar of its
+    result."""
+    nc = Wp.shape[0]
+    G = np.zeros((nc, 4, 4))
+    for j in range(4):
+        e = np.zeros((nc, 4))
+        e[:, j] = 1.0
+        G[:, :, j] = kn.moments(_fix_dg(setup, Wp, e), setup.dvs)
+    Wpbar = Wbar - np.einsum("cij,ci->cj", G, Wbar)
+    return Wpbar, moments_transpose(Wbar, setup.dvs)

@@ -197,3 +197,58 @@ def test_macro_lusgs_adjoint_dot_product():
         lhs, rhs = (Tx * y).sum(), (x * ATy).sum()
         assert abs(lhs - rhs) <= 1e-12 * (np.abs(Tx * y).sum() + np.abs(x * ATy).sum()), (lhs, rhs)
         assert np.all(ATy[status != FIELD] == 0.0)
+
+
+def fix_case(seed):
+    setup = setup_for([block(4, 3, False)], nv=14)
+    rng = np.random.default_rng(seed)
+    nc = setup.topo.nc
+    prim = np.empty((nc, 4))
+    prim[:, 0] = 1.0 + rng.uniform(-0.2, 0.2, nc)
+    prim[:, 1] = rng.uniform(-0.3, 0.3, nc)
+    prim[:, 2] = rng.uniform(-0.3, 0.3, nc)
+    prim[:, 3] = 1.0 + rng.uniform(-0.2, 0.2, nc)
+    st = ugks.initial_state(setup, prim)
+    f = st.f * (1.0 + rng.uniform(-0.05, 0.05, st.f.shape))
+    Wp = st.W * (1.0 + rng.uniform(-0.02, 0.02, st.W.shape))
+    return setup, Wp, f
+
+
+def test_moment_fix_is_the_steps_fix():
+    """moment_fix restates Step 7 of the oracle's step: applied to the step's
+    predictor W' (= W^{s+1} - fix) and f^{s+1} it returns the step's W."""
+    b = block(5, 4, True)
+    setup = setup_for([b], nv=12)
+    prim = np.empty((setup.topo.nc, 4))
+    rng = np.random.default_rng(12)
+    prim[:] = (1.0, 0.1, -0.05, 1.0)
+    prim[:, 0] *= 1.0 + rng.uniform(-0.1, 0.1, setup.topo.nc)
+    st = ugks.initial_state(setup, prim)
+    geo = moving_geo(setup, [b], rng)
+    st2, info = ugks.implicit_step(setup, geo, st, 0.05, 2)
+    Wp = st2.W - info.fix
+    np.testing.assert_allclose(adjoint.moment_fix(setup, Wp, st2.f), st2.W, rtol=1e-13, atol=1e-15)
+
+
+def test_moment_fix_tangent_matches_central_differences():
+    setup, Wp, f = fix_case(14)
+    rng = np.random.default_rng(15)
+    dWp = rng.standard_normal(Wp.shape) * np.abs(Wp).mean(0)
+    df = rng.standard_normal(f.shape) * np.abs(f).mean()
+    t = adjoint.moment_fix_tangent(setup, Wp, dWp, df)
+    h = 1e-6
+    fd = (adjoint.moment_fix(setup, Wp + h * dWp, f + h * df)
+          - adjoint.moment_fix(setup, Wp - h * dWp, f - h * df)) / (2 * h)
+    np.testing.assert_allclose(t, fd, rtol=1e-6, atol=1e-8 * np.abs(fd).max())
+
+
+def test_moment_fix_adjoint_dot_product():
+    setup, Wp, f = fix_case(16)
+    rng = np.random.default_rng(17)
+    dWp, df = rng.standard_normal(Wp.shape), rng.standard_normal(f.shape)
+    Wbar = rng.standard_normal(Wp.shape)
+    t = adjoint.moment_fix_tangent(setup, Wp, dWp, df)
+    Wpbar, fbar = adjoint.moment_fix_adjoint(setup, Wp, Wbar)
+    lhs = (t * Wbar).sum()
+    rhs = (dWp * Wpbar).sum() + (df * fbar).sum()
+    assert abs(lhs - rhs) <= 1e-12 * (np.abs(t * Wbar).sum() + np.abs(dWp * Wpbar).sum() + np.abs(df * fbar).sum())
